@@ -1,0 +1,327 @@
+"""Benchmark: Tersoff NVE molecular dynamics on one GB300.
+
+Workload: Si diamond 40x40x40 cells = 512,000 atoms, Gaussian sigma 0.05 A,
+Maxwell-Boltzmann 1000 K, Si(C) parameters, skin 0.3 A, dt = 1 fs.  One bench
+step is one full velocity-Verlet step (force gather + kicks + drift, neighbour
+list rebuild when some atom moved more than skin/2, Tersoff energy/force
+evaluation).  The headline is mixed precision; the FP64 path is timed the same
+way and reported beside it.
+
+Timing: CUDA events on the library's stream around each step; between timed
+steps a 256 MB buffer is written on the same stream so every step starts with a
+cold L2 (the flush is outside the events).  Under torchrun each rank runs its own
+replica of the workload on its own GPU (the path does not shard across GPUs);
+the value is the sum over ranks of atoms x steps divided by the slowest rank's time.
+
+--impl reference times the FP64 CPU oracle (the baseline) on the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Tersoff atom-steps/s, NVE velocity Verlet, mixed precision (FP64 path beside it)"
+WORKLOAD = "Si diamond 40x40x40 = 512,000 atoms, sigma 0.05 A, 1000 K, Si(C), skin 0.3 A, dt 1 fs"
+SKIN = 0.3
+DT = 1e-3
+
+# Algorithmic float32 operation counts of the force kernel (flops; FMA = 2), per
+# Verlet-list entry tested, per in-cutoff pair and per ordered triplet; counted from
+# force.cu (filter + pass A + pass B + outputs), transcendentals counted as 1 each.
+C_ENTRY = 12
+C_PAIR = 96
+C_TRIPLET = 74
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x 2 x max SM clock
+FP64_PEAK_TFLOPS = 1.25                              # GB300 nominal FP64
+
+
+def env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def dist_setup():
+    ws = env_int("WORLD_SIZE", 1)
+    rank = env_int("RANK", 0)
+    local = env_int("LOCAL_RANK", 0)
+    if ws > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("gloo")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(ws, x):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def workload_counts(s, rc):
+    """Verlet-list entries (r < rc + skin), in-cutoff ordered pairs P and ordered
+    triplets T of the starting configuration, counted with a periodic k-d tree."""
+    from scipy.spatial import cKDTree
+    pos = np.mod(s.pos, s.box)
+    tree = cKDTree(pos, boxsize=s.box)
+    n_list = tree.query_pairs(rc + SKIN, output_type="ndarray").shape[0] * 2
+    pairs = tree.query_pairs(rc, output_type="ndarray")
+    deg = np.bincount(pairs.ravel(), minlength=s.n)
+    P = int(deg.sum())
+    T = int(np.sum(deg * (deg - 1)))
+    return n_list, P, T
+
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle samples while the timed region runs."""
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def start(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in self.samples:
+            try:
+                sm.append(float(s[0]))
+                mx = float(s[1])
+                for k, n in enumerate(names):
+                    if s[3 + k].lower().startswith("active"):
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_gpu(args, ws, rank, local):
+    import torch
+    from paper_1710_00882_gb300 import params as pp
+    from paper_1710_00882_gb300 import tersoff as T
+    from paper_1710_00882_gb300 import workloads as wl
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    ctx = T.Context(local, stream.cuda_stream)
+    s = wl.si_512k(seed=3 + rank)
+    tab, masses = pp.for_species(s.species)
+    P = T.Params(ctx, tab, masses)
+    n_list, npair, ntrip = workload_counts(s, P.cutoff)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
+
+    def timed(prec, steps, warmup, profile):
+        md = T.MD(ctx, P, s.pos, s.vel, s.types, s.box, dt=DT, skin=SKIN, prec=prec)
+        md.step_async(warmup)
+        md.sync()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        if profile:
+            md.profile(True)
+        barrier(ws)
+        torch.cuda.synchronize()
+        for k in range(steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(k))
+                evs[k][0].record(stream)
+            md.step_async(1)
+            with torch.cuda.stream(stream):
+                evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        barrier(ws)
+        ms = [a.elapsed_time(b) for a, b in evs]
+        prof = md.profile_read() if profile else None
+        md.sync()
+        st = md.stats()
+        return ms, prof, st, md
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms_mix, prof_mix, st_mix, md_mix = timed(T.MIXED, args.steps, args.warmup, True)
+    ms_64, prof_64, st_64, md_64 = timed(T.FP64, max(3, args.steps // 4), args.warmup, True)
+    clk = clocks.stop()
+
+    tot_mix = allreduce_max(ws, sum(ms_mix))
+    tot_64 = allreduce_max(ws, sum(ms_64))
+    value = ws * s.n * len(ms_mix) / (tot_mix / 1e3)
+    value64 = ws * s.n * len(ms_64) / (tot_64 / 1e3)
+
+    # roofline of the dominant kernel (the force kernel), achieved from algorithmic flops
+    flops = C_ENTRY * n_list + C_PAIR * npair + C_TRIPLET * ntrip
+    f_ms = prof_mix[0][2] / max(1, prof_mix[1][2])
+    f64_ms = prof_64[0][2] / max(1, prof_64[1][2])
+    achieved = flops / (f_ms / 1e3) / 1e12
+    achieved64 = flops / (f64_ms / 1e3) / 1e12
+
+    # end to end through the C ABI with host buffers: one tersoff_md_run call of 100 steps
+    e2e = None
+    if not args.no_e2e:
+        n_e2e = 100
+        pos = np.array(s.pos)
+        vel = np.array(s.vel)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        T.md_run(ctx, P, pos, vel, s.types, s.box, DT, n_e2e, SKIN, prec=T.MIXED, trace=False)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        e2e = {"value": s.n * n_e2e / (t1 - t0), "unit": "atom-steps/s",
+               "h2d_bytes_per_step": (pos.nbytes + vel.nbytes + s.types.nbytes) / n_e2e,
+               "d2h_bytes_per_step": (pos.nbytes + vel.nbytes) / n_e2e,
+               "call": "tersoff_md_run(host pos/vel/types, 100 steps, mixed)", "seconds": t1 - t0}
+
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "force_kernel_traffic.json")
+    if os.path.exists(tr_path):
+        try:
+            traffic = json.load(open(tr_path)).get("mixed_si512k_bytes_per_launch")
+        except (OSError, ValueError):
+            traffic = None
+
+    launches_per_step = int(sum(prof_mix[1])) / len(ms_mix)
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "atom-steps/s",
+        "n_gpus": ws,
+        "steps": len(ms_mix),
+        "warmup": args.warmup,
+        "ms_per_step": tot_mix / len(ms_mix),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "atoms": s.n, "precision": "mixed",
+                   "l2": "flushed between timed steps (256 MB write outside the events)",
+                   "parallelism": "replicas" if ws > 1 else "single GPU",
+                   "rebuilds_in_timed_steps": None},
+        "fp64": {"value": value64, "unit": "atom-steps/s", "steps": len(ms_64), "ms_per_step": tot_64 / len(ms_64),
+                 "mixed_over_fp64": value / value64,
+                 "force_kernel_ms": f64_ms, "force_kernel_achieved_tflops": achieved64,
+                 "peak_tflops": FP64_PEAK_TFLOPS, "frac_of_fp64_peak": achieved64 / FP64_PEAK_TFLOPS},
+        "phases_ms_per_step": {"integrator": prof_mix[0][0] / len(ms_mix), "list_build": prof_mix[0][1] / len(ms_mix),
+                               "force": prof_mix[0][2] / len(ms_mix), "bookkeeping": prof_mix[0][3] / len(ms_mix)},
+        "roofline": {"bound": "alu", "kernel": "k_force<float> (mixed)", "achieved": achieved,
+                     "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                     "traffic": traffic, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                     "algorithmic_flops_per_launch": flops, "force_kernel_ms": f_ms,
+                     "counts": {"list_entries": n_list, "pairs": npair, "triplets": ntrip}},
+        "gpu_launches": int(sum(prof_mix[1])),
+        "launches_per_step": launches_per_step,
+        "rebuilds": {"mixed": st_mix["rebuilds"], "fp64": st_64["rebuilds"]},
+        "clocks": clk,
+    }
+    if e2e:
+        line["e2e"] = e2e
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(args, s, quick=True)
+    return line
+
+
+def cpu_baseline(args, s=None, quick=True, steps=None):
+    """The FP64 oracle as it stands, single-threaded, on a bounded sample of the workload:
+    velocity-Verlet steps of the full 512,000-atom box (neighbour list rebuilt every step)."""
+    from oracle import oracle, params as op
+    from paper_1710_00882_gb300 import workloads as wl
+    if s is None:
+        s = wl.si_512k()
+    tab, m = op.si_table(), op.masses(["Si"])
+    n = steps if steps is not None else 8
+    t0 = time.perf_counter()
+    oracle.md_run(s.pos, s.vel, s.types, s.box, tab, m, DT, n)
+    dt = time.perf_counter() - t0
+    return {"value": s.n * n / dt, "unit": "atom-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} velocity-Verlet steps of the full {s.n}-atom box (FP64 oracle, list rebuilt each step)",
+            "seconds": dt}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return None
+    from paper_1710_00882_gb300 import workloads as wl
+    s = wl.si_512k()
+    # the whole --steps K --warmup W run stays within a few minutes: each step is one
+    # oracle MD step of the full box (~1-2 s)
+    steps = max(1, min(args.steps, 40))
+    cb = cpu_baseline(args, s, steps=steps)
+    v = cb["value"]
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "atom-steps/s", "n_gpus": ws,
+            "steps": steps, "warmup": 0, "ms_per_step": cb["seconds"] / steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "atoms": s.n, "precision": "fp64 (oracle)"},
+            "cpu_baseline": {"value": v, "unit": "atom-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": cb["sample"]},
+            "e2e": {"value": v, "unit": "atom-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        line = run_reference(args, ws, rank)
+    else:
+        line = run_gpu(args, ws, rank, local)
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

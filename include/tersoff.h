@@ -1,0 +1,180 @@
+/*
+ * tersoff.h -- C ABI of libtersoff.so: the Tersoff many-body potential on one
+ * GB300 (sm_103a).
+ *
+ * The operations follow Sec. 2 of Hoehnerbach, Ismail & Bientinesi, "The
+ * Tersoff many-body potential: sustainable performance through vectorization":
+ *
+ *   E       = 1/2 sum_i sum_{j: r_ij < r_C} f_C(r_ij) [f_R(r_ij) + b_ij f_A(r_ij)]   (Eq. 1)
+ *   b_ij    = (1 + beta^n zeta_ij^n)^(-1/(2n))                                       (Eq. 2)
+ *   zeta_ij = sum_{k != i,j: r_ik < r_C} f_C(r_ik) g(theta_ijk) exp(lambda3 (r_ij - r_ik))   (Eq. 3)
+ *
+ * and the forces of Algorithm 1 (per i and in-cutoff neighbour j: accumulate
+ * zeta_ij over neighbours k, apply V(i,j,zeta_ij) and its r-derivative, then
+ * scatter dV/dzeta * dzeta(i,j,k)/dx to i, j and k).  The 1/2 of Eq. 1 is
+ * Tersoff's convention (the paper prints Eq. 1 without it).  f_C, f_R, f_A and
+ * g, which the paper omits as "trivial definitions", are Tersoff's forms:
+ *   f_C(r) = 1 (r < R-D), 1/2 - 1/2 sin(pi (r-R)/(2D)) (|r-R| <= D), 0 (r > R+D)
+ *   f_R(r) = A exp(-lambda1 r),  f_A(r) = -B exp(-lambda2 r)
+ *   g      = gamma (1 + c^2/d^2 - c^2/(d^2 + (h - cos theta)^2))
+ * The cutoff test of Sec. 3 (pack in-cutoff neighbours, skip skin atoms) runs
+ * inside the force kernel on every evaluation.
+ *
+ * Units: Angstrom, eV, amu, ps (forces eV/A, velocities A/ps).  Boxes are
+ * orthorhombic and periodic in x, y and z (minimum image); every side must be
+ * at least 2 * (cutoff + skin), else TERSOFF_ERR_BOX_TOO_SMALL.
+ *
+ * Conventions for every call:
+ *  - The caller owns every array it passes; the library copies inputs and
+ *    writes results into caller buffers.  Opaque handles are freed only by
+ *    their *_destroy call.
+ *  - Array pointers are host pointers unless the call takes `flags` and
+ *    TERSOFF_DEVICE_PTRS is set, in which case they are device pointers on the
+ *    context's device (e.g. from torch.cuda), used in place.
+ *  - Calls are synchronous with respect to the host unless stated otherwise:
+ *    they return after their results are in the caller's buffers.
+ *  - No exception crosses the ABI.  A negative return is an error; outputs are
+ *    then unspecified and tersoff_last_error(ctx) holds a message.
+ *  - Positions may lie outside the box (|x| < 1e6 box lengths); every distance
+ *    is a minimum image.  They are stored as given, not wrapped.
+ *  - Arrays of atoms are AoS: pos[N][3], forces[N][3], vel[N][3] (float64),
+ *    types[N] (int32, in [0, ntypes)).
+ */
+#ifndef TERSOFF_H
+#define TERSOFF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define TERSOFF_OK 0
+#define TERSOFF_ERR_ARG (-1)              /* bad argument (null pointer, N < 0, type out of range, ...) */
+#define TERSOFF_ERR_NOMEM (-2)            /* device or host allocation failed / budget exceeded */
+#define TERSOFF_ERR_CUDA (-3)             /* a CUDA runtime call failed */
+#define TERSOFF_ERR_NLIST_OVERFLOW (-4)   /* neighbour list longer than its capacity */
+#define TERSOFF_ERR_NONFINITE (-5)        /* NaN or Inf in energy or forces */
+#define TERSOFF_ERR_TIMEOUT (-6)          /* a bounded wait ran out */
+#define TERSOFF_ERR_BOX_TOO_SMALL (-7)    /* a box side < 2 * (cutoff + skin) */
+#define TERSOFF_ERR_BUSY (-8)             /* server: no slot free and queue full */
+#define TERSOFF_ERR_NOT_FOUND (-9)        /* server: unknown job id */
+
+/* precision of the force evaluation (Sec. 4 of the paper names single, double
+ * and mixed modes; it does not define "mixed").  TERSOFF_FP64: all arithmetic
+ * in float64.  TERSOFF_MIXED: relative vectors formed exactly from 32-bit
+ * fixed-point positions and rounded once to float32; f_C, g, exp, pow and all
+ * per-term arithmetic in float32; each atom's contribution to a neighbour's
+ * force (a float32 sum of at most 2 n_c terms) is added into float64 per-atom
+ * force accumulators; energy and virial are summed over atoms in float64;
+ * integration is float64. */
+typedef enum { TERSOFF_FP64 = 0, TERSOFF_MIXED = 1 } tersoff_precision;
+
+/* flags */
+#define TERSOFF_HOST_PTRS 0
+#define TERSOFF_DEVICE_PTRS 1     /* array arguments are device pointers */
+#define TERSOFF_DETERMINISTIC 2   /* reverse-accumulation scatter: run-to-run bitwise identical */
+
+typedef struct tersoff_ctx tersoff_ctx;
+typedef struct tersoff_params tersoff_params;
+typedef struct tersoff_nlist tersoff_nlist;
+typedef struct tersoff_md tersoff_md;
+typedef struct tersoff_server tersoff_server;
+
+/* ---- context ---------------------------------------------------------------
+ * A context binds a CUDA device and a stream (NULL: the library creates its
+ * own non-blocking stream).  `stream` is a cudaStream_t passed as void*; it
+ * must outlive the context.  Not thread safe: one host thread per context. */
+int tersoff_ctx_create(int device, void *stream, tersoff_ctx **out);
+void tersoff_ctx_destroy(tersoff_ctx *ctx);
+/* last error message of this context ("" if none); valid until the next call */
+const char *tersoff_last_error(const tersoff_ctx *ctx);
+/* library version string */
+const char *tersoff_version(void);
+
+/* ---- parameters ------------------------------------------------------------
+ * entries: ntypes^3 rows of 14 float64 in the order
+ *   {m, gamma, lambda3, c, d, h, n, beta, lambda2, B, R, D, lambda1, A}
+ * row (ti,tj,tk) at index (ti*ntypes + tj)*ntypes + tk.  Two-body terms of the
+ * pair (i,j) read row (ti,tj,tj); zeta(i,j,k) (Eq. 3) reads row (ti,tj,tk) for
+ * gamma, lambda3, m, c, d, h and the cutoff R, D of f_C(r_ik), which must equal
+ * those of row (ti,tk,tk) (true of Tersoff's combination rules; otherwise
+ * TERSOFF_ERR_ARG).  m is 1 (Eq. 3 as printed) or 3 (exp((lambda3 dr)^3)).
+ * masses_amu: ntypes masses (used by the MD calls).  1 <= ntypes <= 4.
+ * The table is copied; the caller may free its buffers on return. */
+int tersoff_params_create(tersoff_ctx *ctx, int ntypes, const double *entries, const double *masses_amu,
+                          tersoff_params **out);
+void tersoff_params_destroy(tersoff_params *p);
+/* largest r_C = R + D in the table */
+double tersoff_params_cutoff(const tersoff_params *p);
+
+/* ---- neighbour list (Sec. 3: Verlet list with skin) ------------------------
+ * Builds, on the GPU, for every atom i the list of j != i with minimum-image
+ * distance < cutoff + skin (cell list with 27-cell stencil; all pairs when a
+ * box side holds fewer than 3 cells).  Each list is sorted by j.  *inout is
+ * created when NULL, else reused (its capacity grows as needed).  `cutoff` is
+ * normally tersoff_params_cutoff(); `skin` >= 0. */
+int tersoff_neighbor_build(tersoff_ctx *ctx, const double *pos, int64_t N, const double box[3], double cutoff,
+                           double skin, int flags, tersoff_nlist **inout);
+void tersoff_nlist_destroy(tersoff_nlist *nl);
+/* copy a built list to host arrays: counts[N] and idx[N * (*stride)] (row i
+ * at idx + i*stride, first counts[i] entries valid).  Call with idx == NULL to
+ * read N and the stride only. */
+int tersoff_nlist_get(tersoff_ctx *ctx, const tersoff_nlist *nl, int64_t *N, int32_t *stride, int32_t *counts,
+                      int32_t *idx);
+
+/* ---- one energy + force evaluation (Algorithm 1) ---------------------------
+ * nl: a list built for these positions (or positions within skin/2 of them);
+ * NULL builds one internally with skin 0.  energy: eV (may be NULL).
+ * forces: [N][3] eV/A, overwritten (may be NULL).  virial: 6 float64
+ * (xx, yy, zz, xy, xz, yz) = sum over terms of d_a F_b with d relative to atom
+ * i, in eV (may be NULL).  Returns TERSOFF_ERR_NONFINITE if E or F is not
+ * finite. */
+int tersoff_compute(tersoff_ctx *ctx, const double *pos, const int32_t *types, int64_t N, const double box[3],
+                    const tersoff_params *params, const tersoff_nlist *nl, tersoff_precision prec, int flags,
+                    double *energy, double *forces, double *virial);
+
+/* ---- velocity-Verlet NVE molecular dynamics --------------------------------
+ * One step: v += dt/2 F/m; x += dt v; (rebuild the list on the GPU when some
+ * atom moved more than skin/2 since the last build); F = F(x); v += dt/2 F/m.
+ * Integration is float64 in both precisions.
+ *
+ * tersoff_md_create uploads the state, builds the list and evaluates F(x0).
+ * tersoff_md_step advances nsteps steps; energy_trace (nullable, host,
+ * [nsteps+1][2]) receives (potential, kinetic) energy in eV after each step,
+ * row 0 = the state before the call.  tersoff_md_step_async only enqueues the
+ * steps on the context's stream (no trace, no error check; follow with
+ * tersoff_md_sync).  tersoff_md_get copies positions/velocities out (host or,
+ * with TERSOFF_DEVICE_PTRS, device buffers). */
+int tersoff_md_create(tersoff_ctx *ctx, const double *pos, const double *vel, const int32_t *types, int64_t N,
+                      const double box[3], const tersoff_params *params, double dt_ps, double skin,
+                      tersoff_precision prec, int flags, tersoff_md **out);
+int tersoff_md_step(tersoff_md *md, int64_t nsteps, double *energy_trace);
+int tersoff_md_step_async(tersoff_md *md, int64_t nsteps);
+int tersoff_md_sync(tersoff_md *md);
+int tersoff_md_get(tersoff_md *md, double *pos, double *vel, double *forces, int flags);
+/* counters: steps done, list rebuilds, current list stride */
+int tersoff_md_stats(tersoff_md *md, int64_t *steps, int64_t *rebuilds, int32_t *stride);
+/* Per-phase device time.  With profiling on, every step enqueued afterwards is
+ * bracketed phase by phase with CUDA events on the context's stream.
+ * tersoff_md_profile(md, 1) starts (and resets) recording, (md, 0) stops it.
+ * tersoff_md_profile_read waits for the stream and returns, summed over the
+ * recorded steps, ms[4] = {integrator (force gather, kicks, drift), neighbour-
+ * list build (launched every step, skipped on the device when no atom moved
+ * skin/2), force kernel, step bookkeeping} and launches[4] = kernel launches of
+ * each phase. */
+int tersoff_md_profile(tersoff_md *md, int enable);
+int tersoff_md_profile_read(tersoff_md *md, double ms[4], int64_t launches[4]);
+void tersoff_md_destroy(tersoff_md *md);
+
+/* one call: create, step nsteps, copy pos/vel back in place, destroy */
+int tersoff_md_run(tersoff_ctx *ctx, double *pos, double *vel, const int32_t *types, int64_t N,
+                   const double box[3], const tersoff_params *params, double dt_ps, int64_t nsteps, double skin,
+                   tersoff_precision prec, int flags, double *energy_trace);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TERSOFF_H */

@@ -1,0 +1,300 @@
+// Ingest, reverse force gather, float64 velocity Verlet and step bookkeeping.
+//
+// Force gather: the force kernel leaves, for each atom i, the sum of the force
+// contributions of i's terms on each in-cutoff neighbour in slot s of i's list
+// (contrib[s][i]), the force on i itself (selfF[i]) and the set of in-cutoff
+// slots (mask[i]).  The force on atom m is selfF[m] plus, for each in-cutoff slot
+// s of m's list with neighbour j, contrib[rev[s][m]][j]: the slot of m in j's
+// list.  In-cutoff is symmetric (the minimum-image r^2 is bitwise symmetric and
+// r_C(i,j) = r_C(j,i)), so exactly the slots the force kernel wrote are read.
+// The sum is taken in float64 in list order: deterministic.
+#include "internal.cuh"
+
+namespace tsf {
+
+template <class R> struct V4g;
+template <> struct V4g<float> { using type = float4; };
+template <> struct V4g<double> { using type = dbl4; };
+
+template <class R>
+__device__ __forceinline__ void gather_force(int m, int N, const typename V4g<R>::type *__restrict__ contrib,
+                                             const typename V4g<R>::type *__restrict__ selfF,
+                                             const unsigned long long *__restrict__ mask, const int *__restrict__ nbr,
+                                             const int *__restrict__ rev, double &fx, double &fy, double &fz)
+{
+  const auto s0 = selfF[m];
+  fx = (double)s0.x;
+  fy = (double)s0.y;
+  fz = (double)s0.z;
+  unsigned long long mb = mask[m];
+  while (mb) {
+    const int s = __ffsll((long long)mb) - 1;
+    mb &= mb - 1;
+    const int j = nbr[(size_t)s * N + m];
+    const int s2 = rev[(size_t)s * N + m];
+    const auto c = contrib[(size_t)s2 * N + j];
+    fx += (double)c.x;
+    fy += (double)c.y;
+    fz += (double)c.z;
+  }
+}
+
+__device__ __forceinline__ double warp_sum_d(double v)
+{
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// AoS float64 input -> dbl4 positions (type in w's bits) + fixed-point int4
+// (type in w).  Positions are kept as given (not wrapped): every distance is a
+// minimum image, and an MD state copied out and back in reproduces the same
+// float64 values.  The fixed-point copy wraps by construction (mod 2^32).
+__global__ void k_ingest(int N, const double *__restrict__ pos, const int *__restrict__ types, int nt, Geom geo,
+                         dbl4 *__restrict__ x, int4 *__restrict__ q, RunState *rs)
+{
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  int t = types[i];
+  if (t < 0 || t >= nt) {
+    atomicOr(&rs->status, ST_BAD_TYPE);
+    t = 0;
+  }
+  double p[3];
+  int qq[3];
+  for (int a = 0; a < 3; ++a) {
+    double v = pos[3 * (size_t)i + a];
+    if (!isfinite(v) || fabs(v * geo.invL[a]) > 1e6) {
+      atomicOr(&rs->status, ST_NONFINITE);
+      v = 0.0;
+    }
+    p[a] = v;
+    qq[a] = (int)(unsigned)(unsigned long long)__double2ll_rn(v * geo.to_q[a]);
+  }
+  x[i] = make_dbl4(p[0], p[1], p[2], __longlong_as_double((long long)t));
+  q[i] = make_int4(qq[0], qq[1], qq[2], t);
+}
+
+// AoS float64 velocities -> dbl4
+__global__ void k_ingest_vel(int N, const double *__restrict__ vel, dbl4 *__restrict__ v)
+{
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  v[i] = make_dbl4(vel[3 * (size_t)i], vel[3 * (size_t)i + 1], vel[3 * (size_t)i + 2], 0.0);
+}
+
+// reverse gather into AoS float64 forces; flags non-finite values
+template <class R>
+__global__ void k_gather_out(int N, const typename V4g<R>::type *__restrict__ contrib,
+                             const typename V4g<R>::type *__restrict__ selfF,
+                             const unsigned long long *__restrict__ mask, const int *__restrict__ nbr,
+                             const int *__restrict__ rev, double *__restrict__ out, RunState *rs)
+{
+  if (rs->status != 0) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double fx, fy, fz;
+  gather_force<R>(i, N, contrib, selfF, mask, nbr, rev, fx, fy, fz);
+  if (!isfinite(fx) || !isfinite(fy) || !isfinite(fz)) atomicOr(&rs->status, ST_NONFINITE);
+  out[3 * (size_t)i] = fx;
+  out[3 * (size_t)i + 1] = fy;
+  out[3 * (size_t)i + 2] = fz;
+}
+
+enum { VV_FINISH = 1, VV_START = 2 };
+
+// Velocity Verlet around the force evaluation, float64.
+//   FINISH: v += dt/2 F/m          (second half kick of the previous step)
+//   START:  v += dt/2 F/m; x += dt v; refresh fixed-point q; flag a rebuild when
+//           some atom moved more than skin/2 since the last build
+// KE: accumulate sum m v^2 of the full-step velocity (after FINISH, before START).
+template <class R, bool KE>
+__global__ void k_vv(int N, int mode, dbl4 *__restrict__ x, dbl4 *__restrict__ v, int4 *__restrict__ q,
+                     const int4 *__restrict__ qref, const typename V4g<R>::type *__restrict__ contrib,
+                     const typename V4g<R>::type *__restrict__ selfF, const unsigned long long *__restrict__ mask,
+                     const int *__restrict__ nbr, const int *__restrict__ rev, const double *__restrict__ kick,
+                     const double *__restrict__ mass, double dt, Geom geo, float disp2_lim, RunState *rs)
+{
+  if (rs->status != 0) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  bool active = i < N;
+  double ke = 0.0;
+  bool moved = false;
+  if (active) {
+    int4 qi = q[i];
+    const int t = qi.w;
+    const double c = kick[t];
+    double fx, fy, fz;
+    gather_force<R>(i, N, contrib, selfF, mask, nbr, rev, fx, fy, fz);
+    dbl4 vi = v[i];
+    if (mode & VV_FINISH) {
+      vi.x = fma(c, fx, vi.x);
+      vi.y = fma(c, fy, vi.y);
+      vi.z = fma(c, fz, vi.z);
+    }
+    if (KE) ke = mass[t] * (vi.x * vi.x + vi.y * vi.y + vi.z * vi.z);
+    if (mode & VV_START) {
+      vi.x = fma(c, fx, vi.x);
+      vi.y = fma(c, fy, vi.y);
+      vi.z = fma(c, fz, vi.z);
+      dbl4 xi = x[i];
+      xi.x = fma(dt, vi.x, xi.x);
+      xi.y = fma(dt, vi.y, xi.y);
+      xi.z = fma(dt, vi.z, xi.z);
+      x[i] = xi;
+      qi.x = (int)(unsigned)(unsigned long long)__double2ll_rn(xi.x * geo.to_q[0]);
+      qi.y = (int)(unsigned)(unsigned long long)__double2ll_rn(xi.y * geo.to_q[1]);
+      qi.z = (int)(unsigned)(unsigned long long)__double2ll_rn(xi.z * geo.to_q[2]);
+      q[i] = qi;
+      const int4 qr = qref[i];
+      const float dx = (float)qdiff(qi.x, qr.x) * geo.q_to_f[0];
+      const float dy = (float)qdiff(qi.y, qr.y) * geo.q_to_f[1];
+      const float dz = (float)qdiff(qi.z, qr.z) * geo.q_to_f[2];
+      moved = dx * dx + dy * dy + dz * dz > disp2_lim;
+    }
+    v[i] = vi;
+  }
+  if (__any_sync(0xffffffffu, moved) && (threadIdx.x & 31) == 0) atomicOr(&rs->rebuild, 1);
+  if (KE) {
+    double s = warp_sum_d(ke);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&rs->ekin2, s);
+  }
+}
+
+// AoS copies out of the device state
+__global__ void k_extract(int N, const dbl4 *__restrict__ x, const dbl4 *__restrict__ v, double *__restrict__ pos,
+                          double *__restrict__ vel)
+{
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  if (pos) {
+    dbl4 a = x[i];
+    pos[3 * (size_t)i] = a.x;
+    pos[3 * (size_t)i + 1] = a.y;
+    pos[3 * (size_t)i + 2] = a.z;
+  }
+  if (vel) {
+    dbl4 b = v[i];
+    vel[3 * (size_t)i] = b.x;
+    vel[3 * (size_t)i + 1] = b.y;
+    vel[3 * (size_t)i + 2] = b.z;
+  }
+}
+
+// End of an MD step: record (PE_k, KE_{k-1}) in the trace, roll the accumulators.
+__global__ void k_step_end(RunState *rs, double *trace, long long k)
+{
+  if (rs->status != 0) return;
+  if (trace) {
+    if (k == 1) trace[0] = rs->epot_last;
+    trace[2 * k] = rs->epot;
+    trace[2 * k - 1] = 0.5 * rs->ekin2 / ACCEL;
+  }
+  rs->epot_last = rs->epot;
+  rs->epot = 0.0;
+  rs->ekin2 = 0.0;
+  for (int c = 0; c < 6; ++c) rs->virial[c] = 0.0;
+  rs->step += 1;
+}
+
+// after the closing half kick: KE of the last step
+__global__ void k_final(RunState *rs, double *trace, long long n)
+{
+  if (rs->status != 0) return;
+  if (trace) trace[2 * n + 1] = 0.5 * rs->ekin2 / ACCEL;
+  rs->ekin2 = 0.0;
+}
+
+// after a standalone force evaluation: keep its energy as the current PE
+__global__ void k_force_done(RunState *rs)
+{
+  if (rs->status != 0) return;
+  rs->epot_last = rs->epot;
+  rs->epot = 0.0;
+  for (int c = 0; c < 6; ++c) rs->virial[c] = 0.0;
+}
+
+cudaError_t launch_vv(cudaStream_t st, bool mixed, bool ke, int N, int mode, dbl4 *x, dbl4 *v, int4 *q,
+                      const int4 *qref, const void *contrib, const void *selfF, const unsigned long long *mask,
+                      const int *nbr, const int *rev, const double *kick, const double *mass, double dt,
+                      const Geom &geo, float disp2_lim, RunState *rs)
+{
+  if (N == 0) return cudaSuccess;
+  const int T = 256, B = (N + T - 1) / T;
+  if (mixed) {
+    if (ke)
+      k_vv<float, true><<<B, T, 0, st>>>(N, mode, x, v, q, qref, (const float4 *)contrib, (const float4 *)selfF,
+                                         mask, nbr, rev, kick, mass, dt, geo, disp2_lim, rs);
+    else
+      k_vv<float, false><<<B, T, 0, st>>>(N, mode, x, v, q, qref, (const float4 *)contrib, (const float4 *)selfF,
+                                          mask, nbr, rev, kick, mass, dt, geo, disp2_lim, rs);
+  } else {
+    if (ke)
+      k_vv<double, true><<<B, T, 0, st>>>(N, mode, x, v, q, qref, (const dbl4 *)contrib, (const dbl4 *)selfF,
+                                          mask, nbr, rev, kick, mass, dt, geo, disp2_lim, rs);
+    else
+      k_vv<double, false><<<B, T, 0, st>>>(N, mode, x, v, q, qref, (const dbl4 *)contrib,
+                                           (const dbl4 *)selfF, mask, nbr, rev, kick, mass, dt, geo, disp2_lim, rs);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_out(cudaStream_t st, bool mixed, int N, const void *contrib, const void *selfF,
+                              const unsigned long long *mask, const int *nbr, const int *rev, double *out,
+                              RunState *rs)
+{
+  if (N == 0) return cudaSuccess;
+  const int T = 256, B = (N + T - 1) / T;
+  if (mixed)
+    k_gather_out<float><<<B, T, 0, st>>>(N, (const float4 *)contrib, (const float4 *)selfF, mask, nbr, rev, out, rs);
+  else
+    k_gather_out<double><<<B, T, 0, st>>>(N, (const dbl4 *)contrib, (const dbl4 *)selfF, mask, nbr, rev, out,
+                                          rs);
+  return cudaGetLastError();
+}
+
+}  // namespace tsf
+
+namespace tsf {
+
+cudaError_t launch_ingest(cudaStream_t st, int N, const double *pos, const int *types, int nt, const Geom &geo,
+                          dbl4 *x, int4 *q, RunState *rs)
+{
+  if (N == 0) return cudaSuccess;
+  k_ingest<<<(N + 255) / 256, 256, 0, st>>>(N, pos, types, nt, geo, x, q, rs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ingest_vel(cudaStream_t st, int N, const double *vel, dbl4 *v)
+{
+  if (N == 0) return cudaSuccess;
+  k_ingest_vel<<<(N + 255) / 256, 256, 0, st>>>(N, vel, v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_extract(cudaStream_t st, int N, const dbl4 *x, const dbl4 *v, double *pos, double *vel)
+{
+  if (N == 0) return cudaSuccess;
+  k_extract<<<(N + 255) / 256, 256, 0, st>>>(N, x, v, pos, vel);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_end(cudaStream_t st, RunState *rs, double *trace, long long k)
+{
+  k_step_end<<<1, 1, 0, st>>>(rs, trace, k);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_final(cudaStream_t st, RunState *rs, double *trace, long long n)
+{
+  k_final<<<1, 1, 0, st>>>(rs, trace, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_force_done(cudaStream_t st, RunState *rs)
+{
+  k_force_done<<<1, 1, 0, st>>>(rs);
+  return cudaGetLastError();
+}
+
+}  // namespace tsf

@@ -1,0 +1,98 @@
+// Internal device-side definitions shared by the kernels and the host runtime
+// of libtersoff.so.  Nothing here is part of the C ABI.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace tsf {
+
+// 32-byte aligned float64 quadruple (one 256-bit access)
+using dbl4 = double4_32a;
+__host__ __device__ __forceinline__ dbl4 make_dbl4(double x, double y, double z, double w)
+{
+  return make_double4_32a(x, y, z, w);
+}
+
+constexpr int MAX_TYPES = 4;
+constexpr int MAX_CAP = 64;       // neighbour-list capacity limit per atom (64-bit in-cutoff mask)
+constexpr int NFIELDS = 14;       // {m, gamma, lambda3, c, d, h, n, beta, lambda2, B, R, D, lambda1, A}
+enum Field { F_M = 0, F_GAMMA, F_LAM3, F_C, F_D, F_H, F_N, F_BETA, F_LAM2, F_B, F_R, F_DD, F_LAM1, F_A };
+
+// sticky device status bits
+enum : int {
+  ST_NLIST_OVERFLOW = 1,   // an atom has more list entries than the list capacity
+  ST_NC_OVERFLOW = 2,      // an atom has more in-cutoff neighbours than the force kernel's slot count
+  ST_REV_MISSING = 4,      // reverse slot of a list entry not found (list not symmetric)
+  ST_NONFINITE = 8,
+  ST_ALLPAIRS_TOO_BIG = 16,
+};
+
+// Pair part of the table (row (ti,tj,tj)), derived constants in the kernel's precision.
+template <class R>
+struct PairP {
+  R A, lam1, B, lam2;     // f_R = A e^{-lam1 r}, f_A = -B e^{-lam2 r}
+  R beta, n, neg_inv2n;   // b = (1 + (beta zeta)^n)^(-1/(2n))
+  R Rc, Dc;               // cutoff centre and half width
+  R r_in, r_out, rc2;     // R - D, R + D, (R + D)^2
+  R inv2D, dfc_scale;     // 1/(2D), -pi/(4D)
+};
+
+// Angular part of the table (row (ti,tj,tk)).
+template <class R>
+struct TripP {
+  R gamma, lam3, K, G2, d2, h;   // g = gamma + K u^2/(d2 + u^2), dg/dcos = -G2 u/(d2 + u^2)^2, u = h - cos
+  R m3;                          // 1 when the lambda3 exponent is cubed (m = 3), else 0
+  R pad;
+};
+
+// Box geometry.  Positions are also kept as 32-bit fixed point per axis:
+// q = round(x / L * 2^32) mod 2^32, so q_j - q_i taken as int32 is the minimum
+// image of x_j - x_i in units of L / 2^32, exact in integer arithmetic.
+struct Geom {
+  double L[3], invL[3];
+  double to_q[3];     // 2^32 / L
+  double q_to_d[3];   // L / 2^32
+  float q_to_f[3];    // L / 2^32 rounded to float
+};
+
+// Device-resident run bookkeeping (one per MD state / computation).
+struct RunState {
+  int status;            // sticky ST_* bits
+  int rebuild;           // nonzero: rebuild the list in this step
+  int maxcount;          // max list length seen at the last build
+  int maxnc;             // max in-cutoff count seen by the force kernel
+  long long step;        // MD steps completed
+  long long nrebuild;    // list builds done
+  double epot;           // potential energy accumulator (force kernel)
+  double ekin2;          // sum m v^2 accumulator (integrator), amu A^2/ps^2
+  double virial[6];
+  double epot_last;      // potential energy of the last completed step
+  double *trace;         // device trace [..][2] or null
+  long long trace_k;     // next trace row
+};
+
+// minimum-image difference of two fixed-point coordinates, in units of L / 2^32
+__host__ __device__ __forceinline__ int qdiff(int qj, int qi)
+{
+  return (int)((unsigned)qj - (unsigned)qi);
+}
+
+constexpr int ST_BAD_TYPE = 32;
+constexpr double ACCEL = 1.602176634e-19 / 1.66053906660e-27 * 1e-4;   // (eV/A)/amu in A/ps^2
+
+struct CellGrid {
+  int nc[3];
+  int ncell;
+  int allpairs;   // 1: fewer than 3 cells in some dimension, scan all atoms
+  float rl2;      // (cutoff + skin)^2 with a small safety margin
+};
+
+// Per-state list / scatter buffers.
+struct ListBuf {
+  int *nbr;        // [cap][N] list entries (atom index j), slot-major
+  int *rev;        // [cap][N] slot of i in j's list
+  int *cnt;        // [N]
+  int cap;
+};
+
+}  // namespace tsf

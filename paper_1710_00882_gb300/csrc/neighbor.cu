@@ -1,0 +1,277 @@
+// Cell-list / Verlet neighbour build with skin (the list the paper's Sec. 3
+// packing works on).  Everything here runs on 32-bit fixed-point positions:
+// the minimum image is the int32 difference of two fixed-point coordinates, so
+// the list is exactly symmetric (j in list(i) <=> i in list(j)) and needs no
+// float64 arithmetic.
+//
+// Build sequence (all launches are skipped on the device unless rs->rebuild is
+// set, so an MD step can enqueue them unconditionally):
+//   k_cell_count  -> cell of each atom, rank inside its cell (atomic)
+//   k_scan_*      -> exclusive scan of the cell counts (three-phase block scan)
+//   k_cell_fill   -> atoms in cell order
+//   k_build       -> per atom: 27-cell stencil, keep r < r_list, sort by j
+//   k_reverse     -> for each entry (i,s) the slot of i in j's list
+#include "internal.cuh"
+
+namespace tsf {
+
+__device__ __forceinline__ bool skip_build(const RunState *rs, int gated)
+{
+  return rs->status != 0 || (gated && rs->rebuild == 0);
+}
+
+__device__ __forceinline__ int cell_coord(uint32_t qa, int nc)
+{
+  return (int)(((unsigned long long)qa * (unsigned long long)nc) >> 32);
+}
+
+__global__ void k_cell_count(int N, const int4 *__restrict__ q, CellGrid g, int *__restrict__ cell_of,
+                             int *__restrict__ rank, int *__restrict__ cell_count, const RunState *rs, int gated)
+{
+  if (skip_build(rs, gated)) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  int4 p = q[i];
+  int cx = cell_coord((uint32_t)p.x, g.nc[0]);
+  int cy = cell_coord((uint32_t)p.y, g.nc[1]);
+  int cz = cell_coord((uint32_t)p.z, g.nc[2]);
+  int c = (cz * g.nc[1] + cy) * g.nc[0] + cx;
+  cell_of[i] = c;
+  rank[i] = atomicAdd(&cell_count[c], 1);
+}
+
+// ---- exclusive scan over n ints: SCAN_ITEMS per thread, SCAN_THREADS per block
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 4;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+__device__ __forceinline__ int block_exclusive_scan(int v, int *total)
+{
+  __shared__ int warp_sums[SCAN_THREADS / 32];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_sums[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int s = lane < SCAN_THREADS / 32 ? warp_sums[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < SCAN_THREADS / 32) warp_sums[lane] = s;
+  }
+  __syncthreads();
+  int prefix = (w > 0 ? warp_sums[w - 1] : 0) + x - v;
+  *total = warp_sums[SCAN_THREADS / 32 - 1];
+  __syncthreads();
+  return prefix;
+}
+
+// phase 1: scan each tile, write tile totals
+__global__ void k_scan_tiles(int n, const int *__restrict__ in, int *__restrict__ out, int *__restrict__ tile_sums,
+                             const RunState *rs, int gated)
+{
+  if (skip_build(rs, gated)) return;
+  int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+  int v[SCAN_ITEMS], s = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    v[k] = base + k < n ? in[base + k] : 0;
+    s += v[k];
+  }
+  int total;
+  int pre = block_exclusive_scan(s, &total);
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    if (base + k < n) out[base + k] = pre;
+    pre += v[k];
+  }
+  if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+}
+
+// phase 2: one block scans the tile totals (sequentially over chunks of SCAN_TILE)
+__global__ void k_scan_sums(int ntiles, int *__restrict__ tile_sums, int *__restrict__ grand_total,
+                            const RunState *rs, int gated)
+{
+  if (skip_build(rs, gated)) return;
+  int carry = 0;
+  for (int base = 0; base < ntiles; base += SCAN_TILE) {
+    int b = base + threadIdx.x * SCAN_ITEMS;
+    int v[SCAN_ITEMS], s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+      v[k] = b + k < ntiles ? tile_sums[b + k] : 0;
+      s += v[k];
+    }
+    int total;
+    int pre = block_exclusive_scan(s, &total) + carry;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+      if (b + k < ntiles) tile_sums[b + k] = pre;
+      pre += v[k];
+    }
+    carry += total;
+  }
+  if (threadIdx.x == 0) *grand_total = carry;
+}
+
+// phase 3: add tile offsets; zero the counts for the next build
+__global__ void k_scan_add(int n, int *__restrict__ out, const int *__restrict__ tile_sums, int *__restrict__ counts,
+                           const RunState *rs, int gated)
+{
+  if (skip_build(rs, gated)) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  out[i] += tile_sums[i / SCAN_TILE];
+  counts[i] = 0;
+}
+
+__global__ void k_cell_fill(int N, const int *__restrict__ cell_of, const int *__restrict__ rank,
+                            const int *__restrict__ cell_start, int *__restrict__ cell_atoms, const RunState *rs,
+                            int gated)
+{
+  if (skip_build(rs, gated)) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  cell_atoms[cell_start[cell_of[i]] + rank[i]] = i;
+}
+
+// Stencil range along one axis: 3 neighbouring cells, or every cell when the axis
+// has fewer than 3 (then -1, 0, +1 would visit a cell twice).
+__device__ __forceinline__ void axis_range(int c, int nc, int *lo, int *n)
+{
+  if (nc >= 3) { *lo = c - 1; *n = 3; }
+  else { *lo = 0; *n = nc; }
+}
+
+// One thread per atom i: scan the stencil, keep j with |d_ij| < r_list, then sort
+// the column by j so the list order depends only on the set of neighbours.
+__global__ void k_build(int N, const int4 *__restrict__ q, CellGrid g, Geom geo, const int *__restrict__ cell_start,
+                        const int *__restrict__ cell_atoms, int *__restrict__ nbr, int *__restrict__ cnt, int cap,
+                        int4 *__restrict__ qref, RunState *rs, int gated)
+{
+  if (skip_build(rs, gated)) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  int4 pi = q[i];
+  qref[i] = pi;
+  int c[3] = {cell_coord((uint32_t)pi.x, g.nc[0]), cell_coord((uint32_t)pi.y, g.nc[1]),
+              cell_coord((uint32_t)pi.z, g.nc[2])};
+  int lo[3], nr[3];
+  for (int a = 0; a < 3; ++a) axis_range(c[a], g.nc[a], &lo[a], &nr[a]);
+  int n = 0;
+  for (int oz = 0; oz < nr[2]; ++oz) {
+    int cz = lo[2] + oz;
+    cz += (cz < 0) ? g.nc[2] : 0;
+    cz -= (cz >= g.nc[2]) ? g.nc[2] : 0;
+    for (int oy = 0; oy < nr[1]; ++oy) {
+      int cy = lo[1] + oy;
+      cy += (cy < 0) ? g.nc[1] : 0;
+      cy -= (cy >= g.nc[1]) ? g.nc[1] : 0;
+      for (int ox = 0; ox < nr[0]; ++ox) {
+        int cx = lo[0] + ox;
+        cx += (cx < 0) ? g.nc[0] : 0;
+        cx -= (cx >= g.nc[0]) ? g.nc[0] : 0;
+        int cell = (cz * g.nc[1] + cy) * g.nc[0] + cx;
+        int b = cell_start[cell], e = cell_start[cell + 1];
+        for (int t = b; t < e; ++t) {
+          int j = cell_atoms[t];
+          if (j == i) continue;
+          int4 pj = q[j];
+          float dx = (float)qdiff(pj.x, pi.x) * geo.q_to_f[0];
+          float dy = (float)qdiff(pj.y, pi.y) * geo.q_to_f[1];
+          float dz = (float)qdiff(pj.z, pi.z) * geo.q_to_f[2];
+          float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          if (r2 < g.rl2) {
+            if (n < cap) nbr[(size_t)n * N + i] = j;
+            ++n;
+          }
+        }
+      }
+    }
+  }
+  cnt[i] = n;
+  if (n > cap) {
+    atomicOr(&rs->status, ST_NLIST_OVERFLOW);
+    n = cap;
+  }
+  atomicMax(&rs->maxcount, cnt[i]);
+  // insertion sort of the column (short: ~4-20 entries)
+  for (int s = 1; s < n; ++s) {
+    int v = nbr[(size_t)s * N + i];
+    int t = s - 1;
+    while (t >= 0) {
+      int u = nbr[(size_t)t * N + i];
+      if (u <= v) break;
+      nbr[(size_t)(t + 1) * N + i] = u;
+      --t;
+    }
+    nbr[(size_t)(t + 1) * N + i] = v;
+  }
+}
+
+// rev[s][i] = slot of i in the (sorted) list of j = nbr[s][i], found by binary search.
+__global__ void k_reverse(int N, const int *__restrict__ nbr, const int *__restrict__ cnt, int *__restrict__ rev,
+                          RunState *rs, int gated)
+{
+  if (skip_build(rs, gated)) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  int n = cnt[i];
+  for (int s = 0; s < n; ++s) {
+    int j = nbr[(size_t)s * N + i];
+    int lo = 0, hi = cnt[j] - 1, found = -1;
+    while (lo <= hi) {
+      int mid = (lo + hi) >> 1;
+      int v = nbr[(size_t)mid * N + j];
+      if (v == i) { found = mid; break; }
+      if (v < i) lo = mid + 1; else hi = mid - 1;
+    }
+    if (found < 0) atomicOr(&rs->status, ST_REV_MISSING);
+    rev[(size_t)s * N + i] = found < 0 ? 0 : found;
+  }
+}
+
+// close a build: count it, clear the request
+__global__ void k_build_done(RunState *rs, int gated)
+{
+  if (skip_build(rs, gated)) return;
+  rs->nrebuild += 1;
+  rs->rebuild = 0;
+}
+
+}  // namespace tsf
+
+namespace tsf {
+
+// Enqueue one list build on st.  Buffers: cell_count[ncell] (zero on entry, zero
+// on exit), cell_start[ncell+1], tile_sums[ceil(ncell/SCAN_TILE)], cell_atoms[N],
+// cell_of[N], rank[N]; list nbr/rev [cap][N], cnt[N]; qref[N].
+cudaError_t launch_build(cudaStream_t st, int N, const int4 *q, const CellGrid &g, const Geom &geo, int *cell_count,
+                         int *cell_start, int *tile_sums, int *cell_atoms, int *cell_of, int *rank, int *nbr,
+                         int *rev, int *cnt, int cap, int4 *qref, RunState *rs, int gated)
+{
+  if (N == 0) return cudaSuccess;
+  const int T = 256;
+  const int BN = (N + T - 1) / T;
+  const int ntiles = (g.ncell + SCAN_TILE - 1) / SCAN_TILE;
+  k_cell_count<<<BN, T, 0, st>>>(N, q, g, cell_of, rank, cell_count, rs, gated);
+  k_scan_tiles<<<ntiles, SCAN_THREADS, 0, st>>>(g.ncell, cell_count, cell_start, tile_sums, rs, gated);
+  k_scan_sums<<<1, SCAN_THREADS, 0, st>>>(ntiles, tile_sums, cell_start + g.ncell, rs, gated);
+  k_scan_add<<<(g.ncell + T - 1) / T, T, 0, st>>>(g.ncell, cell_start, tile_sums, cell_count, rs, gated);
+  k_cell_fill<<<BN, T, 0, st>>>(N, cell_of, rank, cell_start, cell_atoms, rs, gated);
+  k_build<<<BN, 128, 0, st>>>(N, q, g, geo, cell_start, cell_atoms, nbr, cnt, cap, qref, rs, gated);
+  k_reverse<<<BN, 128, 0, st>>>(N, nbr, cnt, rev, rs, gated);
+  k_build_done<<<1, 1, 0, st>>>(rs, gated);
+  return cudaGetLastError();
+}
+
+int scan_tiles_for(int ncell) { return (ncell + SCAN_TILE - 1) / SCAN_TILE; }
+
+}  // namespace tsf

@@ -1,0 +1,1047 @@
+// Host runtime and C ABI of libtersoff.so (declared in include/tersoff.h):
+// contexts, parameter tables, neighbour lists, single evaluations and the
+// velocity-Verlet MD driver.  Every step of the computation runs in the kernels
+// of neighbor.cu, force.cu and integrate.cu; this file validates arguments,
+// owns device buffers, enqueues launches and reads back status words.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "tersoff.h"
+#include "internal.cuh"
+#include "runtime.h"
+
+namespace tsf {
+
+// launchers defined in the kernel translation units
+cudaError_t launch_build(cudaStream_t, int, const int4 *, const CellGrid &, const Geom &, int *, int *, int *, int *,
+                         int *, int *, int *, int *, int *, int, int4 *, RunState *, int);
+int scan_tiles_for(int ncell);
+int force_slots_for(int need);
+cudaError_t launch_force(cudaStream_t, bool, int, int, int, int, const dbl4 *, const int4 *, const int *,
+                         const int *, const Geom &, const void *, const void *, int, void *, void *,
+                         unsigned long long *, RunState *);
+cudaError_t launch_vv(cudaStream_t, bool, bool, int, int, dbl4 *, dbl4 *, int4 *, const int4 *, const void *,
+                      const void *, const unsigned long long *, const int *, const int *, const double *,
+                      const double *, double, const Geom &, float, RunState *);
+cudaError_t launch_gather_out(cudaStream_t, bool, int, const void *, const void *, const unsigned long long *,
+                              const int *, const int *, double *, RunState *);
+cudaError_t launch_ingest(cudaStream_t, int, const double *, const int *, int, const Geom &, dbl4 *, int4 *,
+                          RunState *);
+cudaError_t launch_ingest_vel(cudaStream_t, int, const double *, dbl4 *);
+cudaError_t launch_extract(cudaStream_t, int, const dbl4 *, const dbl4 *, double *, double *);
+cudaError_t launch_step_end(cudaStream_t, RunState *, double *, long long);
+cudaError_t launch_final(cudaStream_t, RunState *, double *, long long);
+cudaError_t launch_force_done(cudaStream_t, RunState *);
+
+// ---------------------------------------------------------------------------
+// device buffers
+
+template <class T>
+void dfree(T *&p)
+{
+  if (p) cudaFree((void *)p);
+  p = nullptr;
+}
+
+// (re)allocate p to hold at least `bytes`; contents are not kept
+template <class T>
+bool dreserve(T *&p, size_t &have, size_t bytes)
+{
+  if (bytes <= have && p) return true;
+  dfree(p);
+  have = 0;
+  if (bytes == 0) bytes = 16;
+  void *q = nullptr;
+  if (cudaMalloc(&q, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  p = (T *)q;
+  have = bytes;
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// geometry
+
+Geom make_geom(const double box[3])
+{
+  Geom g;
+  for (int a = 0; a < 3; ++a) {
+    g.L[a] = box[a];
+    g.invL[a] = 1.0 / box[a];
+    g.to_q[a] = 4294967296.0 / box[a];
+    g.q_to_d[a] = box[a] / 4294967296.0;
+    g.q_to_f[a] = (float)(box[a] / 4294967296.0);
+  }
+  return g;
+}
+
+int make_grid(const double box[3], double rl, CellGrid *g)
+{
+  long long ncell = 1;
+  for (int a = 0; a < 3; ++a) {
+    int n = (int)std::floor(box[a] / (rl * (1.0 + 1e-6)));
+    if (n < 1) n = 1;
+    if (n > 1024) n = 1024;
+    g->nc[a] = n;
+    ncell *= n;
+  }
+  if (ncell > (1LL << 30)) return TERSOFF_ERR_ARG;
+  g->ncell = (int)ncell;
+  g->allpairs = 0;
+  g->rl2 = (float)(rl * rl * (1.0 + 1e-5));
+  return TERSOFF_OK;
+}
+
+}  // namespace tsf
+
+using namespace tsf;
+
+// ---------------------------------------------------------------------------
+// context
+
+struct tersoff_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  AtomState cstate;        // scratch state of tersoff_compute
+  ListState clist;         // internal list of tersoff_compute when none is given
+  RunState *crs = nullptr; // run state of tersoff_compute
+  void *stage = nullptr;   // host-pointer staging (AoS positions/forces, types)
+  size_t stage_bytes = 0;
+};
+
+struct tersoff_params {
+  int nt = 0;
+  std::vector<double> entries;
+  double masses[MAX_TYPES] = {0, 0, 0, 0};
+  double rcmax = 0;
+  void *pair_f = nullptr, *trip_f = nullptr, *pair_d = nullptr, *trip_d = nullptr;
+  double *d_mass = nullptr;
+};
+
+struct tersoff_nlist {
+  tersoff_ctx *ctx = nullptr;
+  AtomState atoms;    // positions the list was built from
+  ListState list;
+  RunState *rs = nullptr;
+};
+
+struct tersoff_md {
+  tersoff_ctx *ctx = nullptr;
+  const tersoff_params *params = nullptr;
+  AtomState atoms;
+  ListState list;
+  RunState *rs = nullptr;
+  double *d_kick = nullptr;
+  double *d_trace = nullptr;
+  size_t trace_cap = 0;
+  double dt = 0, skin = 0;
+  bool mixed = false;
+  bool open = false;            // velocities are at the half step (a closing kick is pending)
+  bool pe_valid = false;        // rs->epot_last holds the potential energy of the current positions
+  long long steps_done = 0;     // host count of completed steps
+  long long steps_target = 0;   // host count of enqueued steps
+  int slots = 8;
+  // phase profiling: event pairs per phase, reused across reads
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<std::pair<int, std::pair<size_t, size_t>>> ev_marks;  // (phase, (start idx, end idx))
+  long long launches[4] = {0, 0, 0, 0};
+};
+
+namespace tsf {
+
+int set_err(tersoff_ctx *ctx, int code, const char *fmt, ...)
+{
+  if (ctx) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    ctx->err = buf;
+  }
+  return code;
+}
+
+int cuda_err(tersoff_ctx *ctx, cudaError_t e, const char *what)
+{
+  return set_err(ctx, TERSOFF_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call)                                                        \
+  do {                                                                  \
+    cudaError_t e_ = (call);                                            \
+    if (e_ != cudaSuccess) return cuda_err(ctx, e_, #call);             \
+  } while (0)
+
+#define CKR(call)                                                       \
+  do {                                                                  \
+    int r_ = (call);                                                    \
+    if (r_ != TERSOFF_OK) return r_;                                    \
+  } while (0)
+
+int status_to_code(tersoff_ctx *ctx, int st, const RunState &h)
+{
+  if (st & ST_BAD_TYPE) return set_err(ctx, TERSOFF_ERR_ARG, "atom type out of range");
+  if (st & ST_NONFINITE) return set_err(ctx, TERSOFF_ERR_NONFINITE, "non-finite force or energy");
+  if (st & ST_REV_MISSING) return set_err(ctx, TERSOFF_ERR_NLIST_OVERFLOW, "neighbour list not symmetric");
+  if (st & ST_NLIST_OVERFLOW)
+    return set_err(ctx, TERSOFF_ERR_NLIST_OVERFLOW, "neighbour list overflow (%d entries)", h.maxcount);
+  if (st & ST_NC_OVERFLOW)
+    return set_err(ctx, TERSOFF_ERR_NLIST_OVERFLOW, "too many in-cutoff neighbours (%d)", h.maxnc);
+  return set_err(ctx, TERSOFF_ERR_CUDA, "device status %d", st);
+}
+
+int read_rs(tersoff_ctx *ctx, RunState *rs, RunState *h)
+{
+  CK(cudaMemcpyAsync(h, rs, sizeof(RunState), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return TERSOFF_OK;
+}
+
+int new_rs(tersoff_ctx *ctx, RunState **rs)
+{
+  void *p = nullptr;
+  if (cudaMalloc(&p, sizeof(RunState)) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(ctx, TERSOFF_ERR_NOMEM, "cannot allocate run state");
+  }
+  CK(cudaMemsetAsync(p, 0, sizeof(RunState), ctx->stream));
+  *rs = (RunState *)p;
+  return TERSOFF_OK;
+}
+
+void free_atoms(AtomState &A)
+{
+  dfree(A.x); dfree(A.v); dfree(A.q);
+  dfree(A.contrib); dfree(A.selfF); dfree(A.mask);
+  A = AtomState();
+}
+
+void free_list(ListState &L)
+{
+  dfree(L.nbr); dfree(L.rev); dfree(L.cnt); dfree(L.qref);
+  dfree(L.cell_count); dfree(L.cell_start); dfree(L.tile_sums);
+  dfree(L.cell_atoms); dfree(L.cell_of); dfree(L.rank);
+  L = ListState();
+}
+
+int ensure_atoms(tersoff_ctx *ctx, AtomState &A, int64_t N, bool need_v)
+{
+  size_t n = (size_t)std::max<int64_t>(N, 1);
+  if (!dreserve(A.x, A.x_b, n * sizeof(dbl4)) || !dreserve(A.q, A.q_b, n * sizeof(int4)) ||
+      (need_v && !dreserve(A.v, A.v_b, n * sizeof(dbl4))))
+    return set_err(ctx, TERSOFF_ERR_NOMEM, "cannot allocate atom arrays for N=%lld", (long long)N);
+  A.N = N;
+  return TERSOFF_OK;
+}
+
+int ensure_scatter(tersoff_ctx *ctx, AtomState &A, int64_t N, int cap, bool mixed)
+{
+  size_t v4 = mixed ? sizeof(float4) : sizeof(dbl4);
+  size_t n = (size_t)std::max<int64_t>(N, 1);
+  if (!dreserve(A.contrib, A.contrib_b, n * (size_t)cap * v4) || !dreserve(A.selfF, A.selfF_b, n * v4) ||
+      !dreserve(A.mask, A.mask_b, n * sizeof(unsigned long long)))
+    return set_err(ctx, TERSOFF_ERR_NOMEM, "cannot allocate force scatter buffers (N=%lld, cap=%d)", (long long)N,
+                   cap);
+  return TERSOFF_OK;
+}
+
+int ensure_list(tersoff_ctx *ctx, ListState &L, int64_t N, int cap, int ncell)
+{
+  size_t n = (size_t)std::max<int64_t>(N, 1);
+  bool ok = dreserve(L.nbr, L.nbr_b, n * cap * sizeof(int)) &&
+            dreserve(L.rev, L.rev_b, n * cap * sizeof(int)) &&
+            dreserve(L.cnt, L.cnt_b, n * sizeof(int)) &&
+            dreserve(L.qref, L.qref_b, n * sizeof(int4)) &&
+            dreserve(L.cell_atoms, L.cell_atoms_b, n * sizeof(int)) &&
+            dreserve(L.cell_of, L.cell_of_b, n * sizeof(int)) &&
+            dreserve(L.rank, L.rank_b, n * sizeof(int)) &&
+            dreserve(L.cell_start, L.cell_start_b, ((size_t)ncell + 1) * sizeof(int)) &&
+            dreserve(L.tile_sums, L.tile_sums_b, (size_t)scan_tiles_for(ncell) * sizeof(int) + 16);
+  if (ok && (size_t)ncell * sizeof(int) > L.cell_count_b) {
+    ok = dreserve(L.cell_count, L.cell_count_b, (size_t)ncell * sizeof(int));
+    if (ok) CK(cudaMemsetAsync(L.cell_count, 0, L.cell_count_b, ctx->stream));
+  }
+  if (!ok) return set_err(ctx, TERSOFF_ERR_NOMEM, "cannot allocate neighbour list (N=%lld, cap=%d)", (long long)N, cap);
+  L.N = N;
+  L.cap = cap;
+  return TERSOFF_OK;
+}
+
+int check_box(tersoff_ctx *ctx, const double box[3], double rl)
+{
+  for (int a = 0; a < 3; ++a) {
+    if (!(box[a] > 0) || !std::isfinite(box[a])) return set_err(ctx, TERSOFF_ERR_ARG, "box side %d not positive", a);
+    if (box[a] < 2.0 * rl)
+      return set_err(ctx, TERSOFF_ERR_BOX_TOO_SMALL, "box side %d = %g < 2*(cutoff+skin) = %g", a, box[a], 2 * rl);
+  }
+  return TERSOFF_OK;
+}
+
+// Host-visible list build from A.q: grows the capacity on overflow and sizes it to
+// the longest list plus headroom.
+int build_list_sync(tersoff_ctx *ctx, const AtomState &A, ListState &L, RunState *rs, const double box[3],
+                    double cutoff, double skin)
+{
+  const double rl = cutoff + skin;
+  CKR(check_box(ctx, box, rl));
+  CellGrid g;
+  if (make_grid(box, rl, &g) != TERSOFF_OK) return set_err(ctx, TERSOFF_ERR_ARG, "cell grid too large");
+  L.grid = g;
+  L.geo = make_geom(box);
+  L.cutoff = cutoff;
+  L.skin = skin;
+  int cap = L.cap > 0 ? L.cap : MAX_CAP;
+  for (int attempt = 0; attempt < 3; ++attempt) {
+    CKR(ensure_list(ctx, L, A.N, cap, g.ncell));
+    CK(cudaMemsetAsync(&rs->maxcount, 0, sizeof(int), ctx->stream));
+    CK(launch_build(ctx->stream, (int)A.N, A.q, L.grid, L.geo, L.cell_count, L.cell_start, L.tile_sums,
+                    L.cell_atoms, L.cell_of, L.rank, L.nbr, L.rev, L.cnt, cap, L.qref, rs, 0));
+    RunState h;
+    CKR(read_rs(ctx, rs, &h));
+    L.maxcount = h.maxcount;
+    if (h.status == 0) {
+      // shrink an oversized first allocation (contrib buffers scale with the capacity)
+      int want = std::min(MAX_CAP, h.maxcount + std::max(4, h.maxcount / 4));
+      want = (want + 3) & ~3;
+      if (want < cap && cap == MAX_CAP && attempt == 0) {
+        cap = want;
+        free_list(L);
+        L.grid = g; L.geo = make_geom(box); L.cutoff = cutoff; L.skin = skin;
+        continue;
+      }
+      return TERSOFF_OK;
+    }
+    if (h.status != ST_NLIST_OVERFLOW) return status_to_code(ctx, h.status, h);
+    if (h.maxcount > MAX_CAP)
+      return set_err(ctx, TERSOFF_ERR_NLIST_OVERFLOW, "%d neighbours within cutoff+skin exceed the limit %d",
+                     h.maxcount, MAX_CAP);
+    cap = std::min(MAX_CAP, ((h.maxcount + std::max(4, h.maxcount / 4)) + 3) & ~3);
+    CK(cudaMemsetAsync(&rs->status, 0, sizeof(int), ctx->stream));
+  }
+  return set_err(ctx, TERSOFF_ERR_NLIST_OVERFLOW, "neighbour list build did not converge");
+}
+
+// Copy AoS positions (+ types) into the device state; host or device pointers.
+int ingest(tersoff_ctx *ctx, AtomState &A, const double *pos, const int32_t *types, int64_t N, int nt,
+           const double box[3], bool dev, RunState *rs)
+{
+  A.geo = make_geom(box);
+  if (N == 0) return TERSOFF_OK;
+  const double *dpos = pos;
+  const int *dtyp = types;
+  if (!dev) {
+    size_t need = (size_t)N * (3 * sizeof(double) + sizeof(int));
+    if (!dreserve(ctx->stage, ctx->stage_bytes, need)) return set_err(ctx, TERSOFF_ERR_NOMEM, "staging buffer");
+    double *sp = (double *)ctx->stage;
+    int *st = (int *)(sp + 3 * N);
+    CK(cudaMemcpyAsync(sp, pos, (size_t)N * 3 * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(st, types, (size_t)N * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    dpos = sp;
+    dtyp = st;
+  }
+  CK(launch_ingest(ctx->stream, (int)N, dpos, dtyp, nt, A.geo, A.x, A.q, rs));
+  return TERSOFF_OK;
+}
+
+int check_common(tersoff_ctx *ctx, const double *pos, int64_t N, const double box[3])
+{
+  if (!ctx) return TERSOFF_ERR_ARG;
+  if (N < 0 || N > (int64_t)INT32_MAX / 16) return set_err(ctx, TERSOFF_ERR_ARG, "N=%lld out of range", (long long)N);
+  if (N > 0 && !pos) return set_err(ctx, TERSOFF_ERR_ARG, "null positions");
+  if (!box) return set_err(ctx, TERSOFF_ERR_ARG, "null box");
+  return TERSOFF_OK;
+}
+
+}  // namespace tsf
+
+// ===========================================================================
+// C ABI
+
+extern "C" {
+
+const char *tersoff_version(void) { return "tersoff-gb300 0.1 (sm_103a)"; }
+
+int tersoff_ctx_create(int device, void *stream, tersoff_ctx **out)
+{
+  if (!out) return TERSOFF_ERR_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return TERSOFF_ERR_CUDA;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return TERSOFF_ERR_CUDA;
+  tersoff_ctx *ctx = new (std::nothrow) tersoff_ctx();
+  if (!ctx) return TERSOFF_ERR_NOMEM;
+  ctx->device = device;
+  if (stream) {
+    ctx->stream = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete ctx;
+      return TERSOFF_ERR_CUDA;
+    }
+    ctx->own_stream = true;
+  }
+  if (new_rs(ctx, &ctx->crs) != TERSOFF_OK) {
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return TERSOFF_ERR_NOMEM;
+  }
+  *out = ctx;
+  return TERSOFF_OK;
+}
+
+void tersoff_ctx_destroy(tersoff_ctx *ctx)
+{
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  free_atoms(ctx->cstate);
+  free_list(ctx->clist);
+  dfree(ctx->crs);
+  dfree(ctx->stage);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+const char *tersoff_last_error(const tersoff_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+// ---------------------------------------------------------------------------
+
+int tersoff_params_create(tersoff_ctx *ctx, int ntypes, const double *entries, const double *masses_amu,
+                          tersoff_params **out)
+{
+  if (!ctx || !out) return TERSOFF_ERR_ARG;
+  *out = nullptr;
+  if (ntypes < 1 || ntypes > MAX_TYPES) return set_err(ctx, TERSOFF_ERR_ARG, "ntypes=%d not in [1,%d]", ntypes, MAX_TYPES);
+  if (!entries || !masses_amu) return set_err(ctx, TERSOFF_ERR_ARG, "null parameter table or masses");
+  const int nt = ntypes, nrow = nt * nt * nt;
+  auto row = [&](int a, int b, int c) { return entries + (size_t)((a * nt + b) * nt + c) * NFIELDS; };
+  for (int r = 0; r < nrow; ++r)
+    for (int f = 0; f < NFIELDS; ++f)
+      if (!std::isfinite(entries[(size_t)r * NFIELDS + f])) return set_err(ctx, TERSOFF_ERR_ARG, "non-finite table entry");
+  for (int a = 0; a < nt; ++a) {
+    if (!(masses_amu[a] > 0)) return set_err(ctx, TERSOFF_ERR_ARG, "mass of type %d not positive", a);
+    for (int b = 0; b < nt; ++b) {
+      const double *p = row(a, b, b);
+      if (!(p[F_DD] > 0) || !(p[F_R] > p[F_DD]))
+        return set_err(ctx, TERSOFF_ERR_ARG, "row (%d,%d,%d): need R > D > 0", a, b, b);
+      if (!(p[F_N] > 0) || !(p[F_BETA] >= 0))
+        return set_err(ctx, TERSOFF_ERR_ARG, "row (%d,%d,%d): need n > 0, beta >= 0", a, b, b);
+      const double *q = row(b, a, a);
+      if (p[F_R] != q[F_R] || p[F_DD] != q[F_DD])
+        return set_err(ctx, TERSOFF_ERR_ARG, "cutoff of pair (%d,%d) differs from (%d,%d)", a, b, b, a);
+      for (int c = 0; c < nt; ++c) {
+        const double *t = row(a, b, c), *u = row(a, c, c);
+        if (t[F_R] != u[F_R] || t[F_DD] != u[F_DD])
+          return set_err(ctx, TERSOFF_ERR_ARG, "row (%d,%d,%d): cutoff must equal that of row (%d,%d,%d)", a, b, c, a,
+                         c, c);
+        if (t[F_M] != 1.0 && t[F_M] != 3.0) return set_err(ctx, TERSOFF_ERR_ARG, "row (%d,%d,%d): m must be 1 or 3", a, b, c);
+        if (!(t[F_D] != 0)) return set_err(ctx, TERSOFF_ERR_ARG, "row (%d,%d,%d): d must be nonzero", a, b, c);
+      }
+    }
+  }
+  tersoff_params *P = new (std::nothrow) tersoff_params();
+  if (!P) return TERSOFF_ERR_NOMEM;
+  P->nt = nt;
+  P->entries.assign(entries, entries + (size_t)nrow * NFIELDS);
+  for (int a = 0; a < nt; ++a) P->masses[a] = masses_amu[a];
+  std::vector<PairP<float>> pf(nt * nt);
+  std::vector<PairP<double>> pd(nt * nt);
+  std::vector<TripP<float>> tf(nrow);
+  std::vector<TripP<double>> td(nrow);
+  const double PI = 3.14159265358979323846;
+  for (int a = 0; a < nt; ++a)
+    for (int b = 0; b < nt; ++b) {
+      const double *p = row(a, b, b);
+      PairP<double> d;
+      d.A = p[F_A]; d.lam1 = p[F_LAM1]; d.B = p[F_B]; d.lam2 = p[F_LAM2];
+      d.beta = p[F_BETA]; d.n = p[F_N]; d.neg_inv2n = -1.0 / (2.0 * p[F_N]);
+      d.Rc = p[F_R]; d.Dc = p[F_DD];
+      d.r_in = p[F_R] - p[F_DD]; d.r_out = p[F_R] + p[F_DD]; d.rc2 = d.r_out * d.r_out;
+      d.inv2D = 1.0 / (2.0 * p[F_DD]); d.dfc_scale = -PI / (4.0 * p[F_DD]);
+      P->rcmax = std::max(P->rcmax, d.r_out);
+      pd[a * nt + b] = d;
+      PairP<float> f;
+      f.A = (float)d.A; f.lam1 = (float)d.lam1; f.B = (float)d.B; f.lam2 = (float)d.lam2;
+      f.beta = (float)d.beta; f.n = (float)d.n; f.neg_inv2n = (float)d.neg_inv2n;
+      f.Rc = (float)d.Rc; f.Dc = (float)d.Dc; f.r_in = (float)d.r_in; f.r_out = (float)d.r_out;
+      // float cutoff test must not admit a pair the float64 test rejects: use the float below r_out^2
+      f.rc2 = (float)d.rc2;
+      if ((double)f.rc2 > d.rc2) f.rc2 = std::nextafter(f.rc2, 0.0f);
+      f.inv2D = (float)d.inv2D; f.dfc_scale = (float)d.dfc_scale;
+      pf[a * nt + b] = f;
+      for (int c = 0; c < nt; ++c) {
+        const double *t = row(a, b, c);
+        TripP<double> e;
+        e.gamma = t[F_GAMMA]; e.lam3 = t[F_LAM3];
+        const double c2 = t[F_C] * t[F_C], d2 = t[F_D] * t[F_D];
+        e.K = t[F_GAMMA] * c2 / d2; e.G2 = 2.0 * t[F_GAMMA] * c2; e.d2 = d2; e.h = t[F_H];
+        e.m3 = t[F_M] == 3.0 ? 1.0 : 0.0; e.pad = 0;
+        td[(a * nt + b) * nt + c] = e;
+        TripP<float> g;
+        g.gamma = (float)e.gamma; g.lam3 = (float)e.lam3; g.K = (float)e.K; g.G2 = (float)e.G2;
+        g.d2 = (float)e.d2; g.h = (float)e.h; g.m3 = (float)e.m3; g.pad = 0;
+        tf[(a * nt + b) * nt + c] = g;
+      }
+    }
+  bool ok = cudaMalloc(&P->pair_f, pf.size() * sizeof(pf[0])) == cudaSuccess &&
+            cudaMalloc(&P->pair_d, pd.size() * sizeof(pd[0])) == cudaSuccess &&
+            cudaMalloc(&P->trip_f, tf.size() * sizeof(tf[0])) == cudaSuccess &&
+            cudaMalloc(&P->trip_d, td.size() * sizeof(td[0])) == cudaSuccess &&
+            cudaMalloc((void **)&P->d_mass, MAX_TYPES * sizeof(double)) == cudaSuccess;
+  if (ok)
+    ok = cudaMemcpy(P->pair_f, pf.data(), pf.size() * sizeof(pf[0]), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(P->pair_d, pd.data(), pd.size() * sizeof(pd[0]), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(P->trip_f, tf.data(), tf.size() * sizeof(tf[0]), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(P->trip_d, td.data(), td.size() * sizeof(td[0]), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(P->d_mass, P->masses, MAX_TYPES * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    tersoff_params_destroy(P);
+    return set_err(ctx, TERSOFF_ERR_NOMEM, "cannot upload parameter table");
+  }
+  *out = P;
+  return TERSOFF_OK;
+}
+
+void tersoff_params_destroy(tersoff_params *P)
+{
+  if (!P) return;
+  dfree(P->pair_f); dfree(P->pair_d); dfree(P->trip_f); dfree(P->trip_d); dfree(P->d_mass);
+  delete P;
+}
+
+double tersoff_params_cutoff(const tersoff_params *P) { return P ? P->rcmax : 0.0; }
+
+// ---------------------------------------------------------------------------
+
+int tersoff_neighbor_build(tersoff_ctx *ctx, const double *pos, int64_t N, const double box[3], double cutoff,
+                           double skin, int flags, tersoff_nlist **inout)
+{
+  CKR(check_common(ctx, pos, N, box));
+  if (!inout) return set_err(ctx, TERSOFF_ERR_ARG, "null list handle");
+  if (!(cutoff > 0) || !(skin >= 0)) return set_err(ctx, TERSOFF_ERR_ARG, "need cutoff > 0, skin >= 0");
+  cudaSetDevice(ctx->device);
+  tersoff_nlist *nl = *inout;
+  bool created = false;
+  if (!nl) {
+    nl = new (std::nothrow) tersoff_nlist();
+    if (!nl) return TERSOFF_ERR_NOMEM;
+    nl->ctx = ctx;
+    if (new_rs(ctx, &nl->rs) != TERSOFF_OK) {
+      delete nl;
+      return TERSOFF_ERR_NOMEM;
+    }
+    created = true;
+  }
+  int rc = TERSOFF_OK;
+  CK(cudaMemsetAsync(nl->rs, 0, sizeof(RunState), ctx->stream));
+  rc = ensure_atoms(ctx, nl->atoms, N, false);
+  if (rc == TERSOFF_OK) rc = check_box(ctx, box, cutoff + skin);
+  if (rc == TERSOFF_OK) {
+    // types are irrelevant to the list; pass zeros through the ingest path
+    std::vector<int32_t> zeros;
+    const int32_t *types = nullptr;
+    void *dz = nullptr;
+    if (flags & TERSOFF_DEVICE_PTRS) {
+      if (N > 0 && cudaMalloc(&dz, (size_t)N * sizeof(int)) != cudaSuccess) rc = set_err(ctx, TERSOFF_ERR_NOMEM, "types");
+      else if (N > 0) cudaMemsetAsync(dz, 0, (size_t)N * sizeof(int), ctx->stream);
+      types = (const int32_t *)dz;
+    } else {
+      zeros.assign((size_t)N, 0);
+      types = zeros.data();
+    }
+    if (rc == TERSOFF_OK) rc = ingest(ctx, nl->atoms, pos, types, N, 1, box, flags & TERSOFF_DEVICE_PTRS, nl->rs);
+    if (rc == TERSOFF_OK) rc = build_list_sync(ctx, nl->atoms, nl->list, nl->rs, box, cutoff, skin);
+    if (dz) {
+      cudaStreamSynchronize(ctx->stream);
+      cudaFree(dz);
+    }
+  }
+  if (rc != TERSOFF_OK) {
+    if (created) tersoff_nlist_destroy(nl);
+    return rc;
+  }
+  *inout = nl;
+  return TERSOFF_OK;
+}
+
+void tersoff_nlist_destroy(tersoff_nlist *nl)
+{
+  if (!nl) return;
+  if (nl->ctx) cudaStreamSynchronize(nl->ctx->stream);
+  free_atoms(nl->atoms);
+  free_list(nl->list);
+  dfree(nl->rs);
+  delete nl;
+}
+
+int tersoff_nlist_get(tersoff_ctx *ctx, const tersoff_nlist *nl, int64_t *N, int32_t *stride, int32_t *counts,
+                      int32_t *idx)
+{
+  if (!ctx || !nl) return TERSOFF_ERR_ARG;
+  const ListState &L = nl->list;
+  if (N) *N = L.N;
+  if (stride) *stride = L.cap;
+  if (!idx && !counts) return TERSOFF_OK;
+  std::vector<int> tmp((size_t)L.N * L.cap);
+  std::vector<int> cnt((size_t)L.N);
+  if (L.N > 0) {
+    CK(cudaMemcpyAsync(cnt.data(), L.cnt, (size_t)L.N * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(tmp.data(), L.nbr, (size_t)L.N * L.cap * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int64_t i = 0; i < L.N; ++i) {
+    if (counts) counts[i] = cnt[i];
+    if (idx)
+      for (int s = 0; s < L.cap; ++s) idx[i * L.cap + s] = s < cnt[i] ? tmp[(size_t)s * L.N + i] : -1;
+  }
+  return TERSOFF_OK;
+}
+
+// ---------------------------------------------------------------------------
+
+int tersoff_compute(tersoff_ctx *ctx, const double *pos, const int32_t *types, int64_t N, const double box[3],
+                    const tersoff_params *P, const tersoff_nlist *nl, tersoff_precision prec, int flags,
+                    double *energy, double *forces, double *virial)
+{
+  CKR(check_common(ctx, pos, N, box));
+  if (!P) return set_err(ctx, TERSOFF_ERR_ARG, "null parameters");
+  if (N > 0 && !types) return set_err(ctx, TERSOFF_ERR_ARG, "null types");
+  if (prec != TERSOFF_FP64 && prec != TERSOFF_MIXED) return set_err(ctx, TERSOFF_ERR_ARG, "bad precision");
+  if (nl && nl->list.N != N) return set_err(ctx, TERSOFF_ERR_ARG, "list built for %lld atoms, not %lld", (long long)nl->list.N, (long long)N);
+  if (nl && nl->list.cutoff < P->rcmax) return set_err(ctx, TERSOFF_ERR_ARG, "list cutoff below the table's cutoff");
+  cudaSetDevice(ctx->device);
+  const bool mixed = prec == TERSOFF_MIXED;
+  const bool dev = flags & TERSOFF_DEVICE_PTRS;
+  AtomState &A = ctx->cstate;
+  RunState *rs = ctx->crs;
+  CK(cudaMemsetAsync(rs, 0, sizeof(RunState), ctx->stream));
+  CKR(ensure_atoms(ctx, A, N, false));
+  CKR(check_box(ctx, box, P->rcmax));
+  CKR(ingest(ctx, A, pos, types, N, P->nt, box, dev, rs));
+  const ListState *L = nl ? &nl->list : nullptr;
+  if (!L) {
+    CKR(build_list_sync(ctx, A, ctx->clist, rs, box, P->rcmax, 0.0));
+    L = &ctx->clist;
+  } else {
+    for (int a = 0; a < 3; ++a)
+      if (nl->list.geo.L[a] != box[a]) return set_err(ctx, TERSOFF_ERR_ARG, "list built for another box");
+  }
+  CKR(ensure_scatter(ctx, A, N, L->cap, mixed));
+  const int slots = force_slots_for(std::max(1, L->maxcount));
+  CK(launch_force(ctx->stream, mixed, slots, 1, virial != nullptr, (int)N, A.x, A.q, L->nbr, L->cnt, A.geo,
+                  mixed ? P->pair_f : P->pair_d, mixed ? P->trip_f : P->trip_d, P->nt, A.contrib, A.selfF, A.mask,
+                  rs));
+  double *dF = nullptr;
+  if (forces) {
+    if (dev) {
+      dF = forces;
+    } else {
+      size_t need = (size_t)std::max<int64_t>(N, 1) * 3 * sizeof(double);
+      if (!dreserve(ctx->stage, ctx->stage_bytes, std::max(need, (size_t)N * (3 * sizeof(double) + sizeof(int)))))
+        return set_err(ctx, TERSOFF_ERR_NOMEM, "staging buffer");
+      dF = (double *)ctx->stage;
+    }
+    CK(launch_gather_out(ctx->stream, mixed, (int)N, A.contrib, A.selfF, A.mask, L->nbr, L->rev, dF, rs));
+  }
+  RunState h;
+  CKR(read_rs(ctx, rs, &h));
+  if (h.status != 0) return status_to_code(ctx, h.status, h);
+  if (!std::isfinite(h.epot)) return set_err(ctx, TERSOFF_ERR_NONFINITE, "non-finite energy");
+  if (energy) *energy = h.epot;
+  if (virial)
+    for (int c = 0; c < 6; ++c) virial[c] = h.virial[c];
+  if (forces && !dev && N > 0) {
+    CK(cudaMemcpyAsync(forces, dF, (size_t)N * 3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  return TERSOFF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// MD
+
+static cudaEvent_t md_event(tersoff_md *md)
+{
+  if (md->ev_used == md->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    md->ev_pool.push_back(e);
+  }
+  return md->ev_pool[md->ev_used++];
+}
+
+// bracket one phase with events when profiling; returns the start index
+static size_t md_mark_begin(tersoff_md *md)
+{
+  if (!md->prof) return 0;
+  size_t i = md->ev_used;
+  cudaEvent_t e = md_event(md);
+  if (e) cudaEventRecord(e, md->ctx->stream);
+  return i;
+}
+
+static void md_mark_end(tersoff_md *md, int phase, size_t begin, int nlaunch)
+{
+  md->launches[phase] += nlaunch;
+  if (!md->prof) return;
+  size_t i = md->ev_used;
+  cudaEvent_t e = md_event(md);
+  if (e) {
+    cudaEventRecord(e, md->ctx->stream);
+    md->ev_marks.push_back({phase, {begin, i}});
+  }
+}
+
+static int md_force(tersoff_md *md, int eflag)
+{
+  tersoff_ctx *ctx = md->ctx;
+  const tersoff_params *P = md->params;
+  CK(launch_force(ctx->stream, md->mixed, md->slots, eflag, 0, (int)md->atoms.N, md->atoms.x, md->atoms.q,
+                  md->list.nbr, md->list.cnt, md->atoms.geo, md->mixed ? P->pair_f : P->pair_d,
+                  md->mixed ? P->trip_f : P->trip_d, P->nt, md->atoms.contrib, md->atoms.selfF, md->atoms.mask,
+                  md->rs));
+  return TERSOFF_OK;
+}
+
+static int md_vv(tersoff_md *md, int mode, bool ke)
+{
+  tersoff_ctx *ctx = md->ctx;
+  const float lim = (float)(0.25 * md->skin * md->skin);
+  CK(launch_vv(ctx->stream, md->mixed, ke, (int)md->atoms.N, mode, md->atoms.x, md->atoms.v, md->atoms.q,
+               md->list.qref, md->atoms.contrib, md->atoms.selfF, md->atoms.mask, md->list.nbr, md->list.rev,
+               md->d_kick, md->params->d_mass, md->dt, md->atoms.geo, lim, md->rs));
+  return TERSOFF_OK;
+}
+
+static int md_build_gated(tersoff_md *md)
+{
+  tersoff_ctx *ctx = md->ctx;
+  ListState &L = md->list;
+  CK(launch_build(ctx->stream, (int)md->atoms.N, md->atoms.q, L.grid, L.geo, L.cell_count, L.cell_start, L.tile_sums,
+                  L.cell_atoms, L.cell_of, L.rank, L.nbr, L.rev, L.cnt, L.cap, L.qref, md->rs, 1));
+  return TERSOFF_OK;
+}
+
+// enqueue steps k0..k1 (1-based within the current call's trace numbering)
+static int md_enqueue(tersoff_md *md, long long k0, long long k1, double *d_trace, bool first_open_done)
+{
+  tersoff_ctx *ctx = md->ctx;
+  const bool tr = d_trace != nullptr;
+  for (long long k = k0; k <= k1; ++k) {
+    const int mode = (k == k0 && !first_open_done) ? (md->open ? (1 | 2) : 2) : (1 | 2);
+    size_t b = md_mark_begin(md);
+    CKR(md_vv(md, mode, tr));
+    md_mark_end(md, 0, b, 1);
+    md->open = true;
+    b = md_mark_begin(md);
+    CKR(md_build_gated(md));
+    md_mark_end(md, 1, b, 8);
+    b = md_mark_begin(md);
+    CKR(md_force(md, tr ? 1 : 0));
+    md_mark_end(md, 2, b, 1);
+    b = md_mark_begin(md);
+    CK(launch_step_end(ctx->stream, md->rs, d_trace, k));
+    md_mark_end(md, 3, b, 1);
+  }
+  return TERSOFF_OK;
+}
+
+// Recover from a device status raised inside enqueued steps: the failing step k
+// stopped after its drift (list overflow: in the build; slot overflow: in the
+// force kernel).  Fix the cause, redo the step from there, then enqueue the rest.
+static int md_recover(tersoff_md *md, const RunState &h, long long call_base, long long n_call, double *d_trace)
+{
+  tersoff_ctx *ctx = md->ctx;
+  const long long kfail = h.step - call_base + 1;   // 1-based step of this call that failed
+  if (h.status & ST_NLIST_OVERFLOW) {
+    if (h.maxcount > MAX_CAP)
+      return set_err(ctx, TERSOFF_ERR_NLIST_OVERFLOW, "%d neighbours within cutoff+skin exceed the limit %d",
+                     h.maxcount, MAX_CAP);
+    int cap = std::min(MAX_CAP, ((h.maxcount + std::max(4, h.maxcount / 4)) + 3) & ~3);
+    CKR(ensure_list(ctx, md->list, md->atoms.N, cap, md->list.grid.ncell));
+    CKR(ensure_scatter(ctx, md->atoms, md->atoms.N, cap, md->mixed));
+    const int one = 1;
+    CK(cudaMemsetAsync(&md->rs->status, 0, sizeof(int), ctx->stream));
+    CK(cudaMemcpyAsync(&md->rs->rebuild, &one, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    CKR(md_build_gated(md));
+  } else if (h.status & ST_NC_OVERFLOW) {
+    md->slots = force_slots_for(h.maxnc);
+    CK(cudaMemsetAsync(&md->rs->status, 0, sizeof(int), ctx->stream));
+  } else {
+    return status_to_code(ctx, h.status, h);
+  }
+  CK(cudaMemsetAsync(&md->rs->epot, 0, sizeof(double), ctx->stream));
+  CKR(md_force(md, d_trace ? 1 : 0));
+  CK(launch_step_end(ctx->stream, md->rs, d_trace, kfail));
+  if (kfail < n_call) CKR(md_enqueue(md, kfail + 1, n_call, d_trace, true));
+  return TERSOFF_OK;
+}
+
+// Close pending half kick (optional), wait, check status and recover if needed.
+static int md_finish(tersoff_md *md, long long call_base, long long n_call, double *d_trace, bool close)
+{
+  tersoff_ctx *ctx = md->ctx;
+  for (int attempt = 0; attempt < 8; ++attempt) {
+    if (close && md->open) {
+      CKR(md_vv(md, 1, d_trace != nullptr));
+      CK(launch_final(ctx->stream, md->rs, d_trace, n_call));
+    }
+    RunState h;
+    CKR(read_rs(ctx, md->rs, &h));
+    if (h.status == 0) {
+      if (close) md->open = false;
+      md->steps_done = h.step;
+      md->steps_target = h.step;
+      return TERSOFF_OK;
+    }
+    CKR(md_recover(md, h, call_base, n_call, d_trace));
+  }
+  return set_err(ctx, TERSOFF_ERR_NLIST_OVERFLOW, "MD recovery did not converge");
+}
+
+int tersoff_md_create(tersoff_ctx *ctx, const double *pos, const double *vel, const int32_t *types, int64_t N,
+                      const double box[3], const tersoff_params *P, double dt_ps, double skin, tersoff_precision prec,
+                      int flags, tersoff_md **out)
+{
+  CKR(check_common(ctx, pos, N, box));
+  if (!out || !P || (N > 0 && (!vel || !types))) return set_err(ctx, TERSOFF_ERR_ARG, "null argument");
+  if (!(dt_ps > 0) || !(skin >= 0)) return set_err(ctx, TERSOFF_ERR_ARG, "need dt > 0 and skin >= 0");
+  if (prec != TERSOFF_FP64 && prec != TERSOFF_MIXED) return set_err(ctx, TERSOFF_ERR_ARG, "bad precision");
+  *out = nullptr;
+  cudaSetDevice(ctx->device);
+  tersoff_md *md = new (std::nothrow) tersoff_md();
+  if (!md) return TERSOFF_ERR_NOMEM;
+  md->ctx = ctx;
+  md->params = P;
+  md->dt = dt_ps;
+  md->skin = skin;
+  md->mixed = prec == TERSOFF_MIXED;
+  auto fail = [&](int rc) {
+    tersoff_md_destroy(md);
+    return rc;
+  };
+  int rc = new_rs(ctx, &md->rs);
+  if (rc != TERSOFF_OK) return fail(rc);
+  if ((rc = ensure_atoms(ctx, md->atoms, N, true)) != TERSOFF_OK) return fail(rc);
+  if ((rc = check_box(ctx, box, P->rcmax + skin)) != TERSOFF_OK) return fail(rc);
+  if ((rc = ingest(ctx, md->atoms, pos, types, N, P->nt, box, flags & TERSOFF_DEVICE_PTRS, md->rs)) != TERSOFF_OK)
+    return fail(rc);
+  if (N > 0) {
+    const double *dvel = vel;
+    void *tmp = nullptr;
+    if (!(flags & TERSOFF_DEVICE_PTRS)) {
+      if (cudaMalloc(&tmp, (size_t)N * 3 * sizeof(double)) != cudaSuccess) return fail(set_err(ctx, TERSOFF_ERR_NOMEM, "vel"));
+      cudaMemcpyAsync(tmp, vel, (size_t)N * 3 * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+      dvel = (const double *)tmp;
+    }
+    cudaError_t e = launch_ingest_vel(ctx->stream, (int)N, dvel, md->atoms.v);
+    cudaStreamSynchronize(ctx->stream);
+    if (tmp) cudaFree(tmp);
+    if (e != cudaSuccess) return fail(cuda_err(ctx, e, "ingest velocities"));
+  }
+  double kick[MAX_TYPES] = {0, 0, 0, 0};
+  for (int a = 0; a < P->nt; ++a) kick[a] = 0.5 * dt_ps * ACCEL / P->masses[a];
+  if (cudaMalloc((void **)&md->d_kick, sizeof kick) != cudaSuccess) return fail(set_err(ctx, TERSOFF_ERR_NOMEM, "kick"));
+  cudaMemcpy(md->d_kick, kick, sizeof kick, cudaMemcpyHostToDevice);
+  if ((rc = build_list_sync(ctx, md->atoms, md->list, md->rs, box, P->rcmax, skin)) != TERSOFF_OK) return fail(rc);
+  if ((rc = ensure_scatter(ctx, md->atoms, N, md->list.cap, md->mixed)) != TERSOFF_OK) return fail(rc);
+  md->slots = force_slots_for(std::max(1, md->list.maxcount));
+  if ((rc = md_force(md, 1)) != TERSOFF_OK) return fail(rc);
+  if (launch_force_done(ctx->stream, md->rs) != cudaSuccess) return fail(set_err(ctx, TERSOFF_ERR_CUDA, "force_done"));
+  RunState h;
+  if ((rc = read_rs(ctx, md->rs, &h)) != TERSOFF_OK) return fail(rc);
+  if (h.status != 0) return fail(status_to_code(ctx, h.status, h));
+  // size the force kernel's slots to the observed in-cutoff count plus headroom
+  md->slots = force_slots_for(std::min(std::max(1, md->list.maxcount), h.maxnc + 2));
+  md->steps_done = md->steps_target = 0;
+  md->pe_valid = true;
+  CK(cudaMemsetAsync(&md->rs->step, 0, sizeof(long long), ctx->stream));
+  *out = md;
+  return TERSOFF_OK;
+}
+
+int tersoff_md_step_async(tersoff_md *md, int64_t nsteps)
+{
+  if (!md || nsteps < 0) return TERSOFF_ERR_ARG;
+  tersoff_ctx *ctx = md->ctx;
+  cudaSetDevice(ctx->device);
+  if (nsteps == 0) return TERSOFF_OK;
+  const long long base = md->steps_target;
+  CKR(md_enqueue(md, base + 1, base + nsteps, nullptr, false));
+  md->steps_target += nsteps;
+  md->pe_valid = false;
+  return TERSOFF_OK;
+}
+
+int tersoff_md_sync(tersoff_md *md)
+{
+  if (!md) return TERSOFF_ERR_ARG;
+  cudaSetDevice(md->ctx->device);
+  // async steps are numbered from 1 at the first step ever; recovery re-enqueues
+  // with the same numbering (no trace)
+  return md_finish(md, 0, md->steps_target, nullptr, true);
+}
+
+int tersoff_md_step(tersoff_md *md, int64_t nsteps, double *trace)
+{
+  if (!md || nsteps < 0) return TERSOFF_ERR_ARG;
+  tersoff_ctx *ctx = md->ctx;
+  cudaSetDevice(ctx->device);
+  CKR(tersoff_md_sync(md));
+  double *d_trace = nullptr;
+  if (trace) {
+    size_t need = (size_t)(nsteps + 1) * 2 * sizeof(double);
+    if (!dreserve(md->d_trace, md->trace_cap, need)) return set_err(ctx, TERSOFF_ERR_NOMEM, "trace");
+    d_trace = md->d_trace;
+  }
+  if (trace && !md->pe_valid) {
+    // steps run without energy accumulation left no potential energy for the
+    // current positions: evaluate it (the forces come out bitwise the same)
+    CK(cudaMemsetAsync(&md->rs->epot, 0, sizeof(double), ctx->stream));
+    CKR(md_force(md, 1));
+    CK(launch_force_done(ctx->stream, md->rs));
+    md->pe_valid = true;
+  }
+  const long long base = md->steps_done;
+  if (nsteps > 0) CKR(md_enqueue(md, 1, nsteps, d_trace, false));
+  md->steps_target = base + nsteps;
+  if (nsteps == 0) {
+    if (!trace) return TERSOFF_OK;
+    // no step: report the current state
+    RunState h;
+    CKR(md_vv(md, 0, true));
+    CKR(read_rs(ctx, md->rs, &h));
+    trace[0] = h.epot_last;
+    trace[1] = 0.5 * h.ekin2 / ACCEL;
+    CK(cudaMemsetAsync(&md->rs->ekin2, 0, sizeof(double), ctx->stream));
+    return TERSOFF_OK;
+  }
+  CKR(md_finish(md, base, nsteps, d_trace, true));
+  md->pe_valid = trace != nullptr;
+  if (trace) {
+    CK(cudaMemcpyAsync(trace, d_trace, (size_t)(nsteps + 1) * 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  return TERSOFF_OK;
+}
+
+int tersoff_md_get(tersoff_md *md, double *pos, double *vel, double *forces, int flags)
+{
+  if (!md) return TERSOFF_ERR_ARG;
+  tersoff_ctx *ctx = md->ctx;
+  cudaSetDevice(ctx->device);
+  CKR(tersoff_md_sync(md));
+  const int64_t N = md->atoms.N;
+  if (N == 0) return TERSOFF_OK;
+  const bool dev = flags & TERSOFF_DEVICE_PTRS;
+  const size_t bytes = (size_t)N * 3 * sizeof(double);
+  double *dp = nullptr, *dv = nullptr, *df = nullptr;
+  void *tmp = nullptr;
+  if (dev) {
+    dp = pos; dv = vel; df = forces;
+  } else {
+    if (cudaMalloc(&tmp, 3 * bytes) != cudaSuccess) return set_err(ctx, TERSOFF_ERR_NOMEM, "staging");
+    dp = pos ? (double *)tmp : nullptr;
+    dv = vel ? (double *)tmp + 3 * N : nullptr;
+    df = forces ? (double *)tmp + 6 * N : nullptr;
+  }
+  int rc = TERSOFF_OK;
+  if (launch_extract(ctx->stream, (int)N, md->atoms.x, md->atoms.v, dp, dv) != cudaSuccess) rc = TERSOFF_ERR_CUDA;
+  if (rc == TERSOFF_OK && df &&
+      launch_gather_out(ctx->stream, md->mixed, (int)N, md->atoms.contrib, md->atoms.selfF, md->atoms.mask,
+                        md->list.nbr, md->list.rev, df, md->rs) != cudaSuccess)
+    rc = TERSOFF_ERR_CUDA;
+  if (rc == TERSOFF_OK && !dev) {
+    if (pos) cudaMemcpyAsync(pos, dp, bytes, cudaMemcpyDeviceToHost, ctx->stream);
+    if (vel) cudaMemcpyAsync(vel, dv, bytes, cudaMemcpyDeviceToHost, ctx->stream);
+    if (forces) cudaMemcpyAsync(forces, df, bytes, cudaMemcpyDeviceToHost, ctx->stream);
+  }
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) rc = set_err(ctx, TERSOFF_ERR_CUDA, "md_get sync");
+  if (tmp) cudaFree(tmp);
+  return rc;
+}
+
+int tersoff_md_stats(tersoff_md *md, int64_t *steps, int64_t *rebuilds, int32_t *stride)
+{
+  if (!md) return TERSOFF_ERR_ARG;
+  RunState h;
+  CKR(read_rs(md->ctx, md->rs, &h));
+  if (steps) *steps = h.step;
+  if (rebuilds) *rebuilds = h.nrebuild;
+  if (stride) *stride = md->list.cap;
+  return TERSOFF_OK;
+}
+
+int tersoff_md_profile(tersoff_md *md, int enable)
+{
+  if (!md) return TERSOFF_ERR_ARG;
+  tersoff_ctx *ctx = md->ctx;
+  CK(cudaStreamSynchronize(ctx->stream));
+  md->prof = enable != 0;
+  md->ev_used = 0;
+  md->ev_marks.clear();
+  for (int p = 0; p < 4; ++p) md->launches[p] = 0;
+  return TERSOFF_OK;
+}
+
+int tersoff_md_profile_read(tersoff_md *md, double ms[4], int64_t launches[4])
+{
+  if (!md) return TERSOFF_ERR_ARG;
+  tersoff_ctx *ctx = md->ctx;
+  CK(cudaStreamSynchronize(ctx->stream));
+  double acc[4] = {0, 0, 0, 0};
+  for (auto &m : md->ev_marks) {
+    float t = 0;
+    CK(cudaEventElapsedTime(&t, md->ev_pool[m.second.first], md->ev_pool[m.second.second]));
+    acc[m.first] += t;
+  }
+  for (int p = 0; p < 4; ++p) {
+    if (ms) ms[p] = acc[p];
+    if (launches) launches[p] = md->launches[p];
+  }
+  return TERSOFF_OK;
+}
+
+void tersoff_md_destroy(tersoff_md *md)
+{
+  if (!md) return;
+  if (md->ctx) cudaStreamSynchronize(md->ctx->stream);
+  for (auto e : md->ev_pool) cudaEventDestroy(e);
+  free_atoms(md->atoms);
+  free_list(md->list);
+  dfree(md->rs);
+  dfree(md->d_kick);
+  dfree(md->d_trace);
+  delete md;
+}
+
+int tersoff_md_run(tersoff_ctx *ctx, double *pos, double *vel, const int32_t *types, int64_t N, const double box[3],
+                   const tersoff_params *P, double dt_ps, int64_t nsteps, double skin, tersoff_precision prec,
+                   int flags, double *energy_trace)
+{
+  tersoff_md *md = nullptr;
+  CKR(tersoff_md_create(ctx, pos, vel, types, N, box, P, dt_ps, skin, prec, flags, &md));
+  int rc = tersoff_md_step(md, nsteps, energy_trace);
+  if (rc == TERSOFF_OK) rc = tersoff_md_get(md, pos, vel, nullptr, flags);
+  tersoff_md_destroy(md);
+  return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,292 @@
+"""ctypes binding of libtersoff.so (include/tersoff.h).
+
+The functions named ``tersoff_*`` mirror the C entry points one to one and only
+marshal arguments; every step of the computation runs in the library's CUDA
+kernels.  The small classes below (Context, Params, NeighborList, MD) own the
+opaque handles and turn status codes into exceptions.
+
+Arrays may be numpy arrays (host pointers) or CUDA torch tensors (device
+pointers, TERSOFF_DEVICE_PTRS): the binding reads ``.ctypes.data`` or
+``.data_ptr()`` and passes the pointer through.  There is no fallback: if the
+library is missing, importing this module raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtersoff.so")
+
+OK = 0
+ERR_ARG = -1
+ERR_NOMEM = -2
+ERR_CUDA = -3
+ERR_NLIST_OVERFLOW = -4
+ERR_NONFINITE = -5
+ERR_TIMEOUT = -6
+ERR_BOX_TOO_SMALL = -7
+ERR_BUSY = -8
+ERR_NOT_FOUND = -9
+
+FP64 = 0
+MIXED = 1
+
+HOST_PTRS = 0
+DEVICE_PTRS = 1
+DETERMINISTIC = 2
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libtersoff.so not built ({LIB_PATH}); run __graft_entry__.build() or "
+                      "python paper_1710_00882_gb300/build.py")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_I64 = ctypes.c_int64
+_D = ctypes.c_double
+_PP = ctypes.POINTER(ctypes.c_void_p)
+
+
+def _sig(name, res, *args):
+    f = getattr(_lib, name)
+    f.restype = res
+    f.argtypes = list(args)
+    return f
+
+
+tersoff_version = _sig("tersoff_version", ctypes.c_char_p)
+tersoff_ctx_create = _sig("tersoff_ctx_create", _I, _I, _P, _PP)
+tersoff_ctx_destroy = _sig("tersoff_ctx_destroy", None, _P)
+tersoff_last_error = _sig("tersoff_last_error", ctypes.c_char_p, _P)
+tersoff_params_create = _sig("tersoff_params_create", _I, _P, _I, _P, _P, _PP)
+tersoff_params_destroy = _sig("tersoff_params_destroy", None, _P)
+tersoff_params_cutoff = _sig("tersoff_params_cutoff", _D, _P)
+tersoff_neighbor_build = _sig("tersoff_neighbor_build", _I, _P, _P, _I64, _P, _D, _D, _I, _PP)
+tersoff_nlist_destroy = _sig("tersoff_nlist_destroy", None, _P)
+tersoff_nlist_get = _sig("tersoff_nlist_get", _I, _P, _P, _P, _P, _P, _P)
+tersoff_compute = _sig("tersoff_compute", _I, _P, _P, _P, _I64, _P, _P, _P, _I, _I, _P, _P, _P)
+tersoff_md_create = _sig("tersoff_md_create", _I, _P, _P, _P, _P, _I64, _P, _P, _D, _D, _I, _I, _PP)
+tersoff_md_step = _sig("tersoff_md_step", _I, _P, _I64, _P)
+tersoff_md_step_async = _sig("tersoff_md_step_async", _I, _P, _I64)
+tersoff_md_sync = _sig("tersoff_md_sync", _I, _P)
+tersoff_md_get = _sig("tersoff_md_get", _I, _P, _P, _P, _P, _I)
+tersoff_md_stats = _sig("tersoff_md_stats", _I, _P, _P, _P, _P)
+tersoff_md_destroy = _sig("tersoff_md_destroy", None, _P)
+tersoff_md_profile = _sig("tersoff_md_profile", _I, _P, _I)
+tersoff_md_profile_read = _sig("tersoff_md_profile_read", _I, _P, _P, _P)
+tersoff_md_run = _sig("tersoff_md_run", _I, _P, _P, _P, _P, _I64, _P, _P, _D, _I64, _D, _I, _I, _P)
+
+
+class TersoffError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"tersoff error {code}: {msg}")
+        self.code = code
+
+
+# ---- argument marshalling -----------------------------------------------------
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def ptr(a):
+    """Raw pointer of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if _is_torch(a):
+        return ctypes.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _dev_flag(*arrays):
+    dev = [_is_torch(a) and a.is_cuda for a in arrays if a is not None]
+    if dev and all(dev):
+        return DEVICE_PTRS
+    if any(dev):
+        raise ValueError("mix of device and host arrays")
+    return HOST_PTRS
+
+
+def _f64(a, shape):
+    if _is_torch(a):
+        import torch
+        assert a.dtype == torch.float64 and a.is_contiguous() and tuple(a.shape) == shape, (a.dtype, a.shape, shape)
+        return a
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a.reshape(shape)
+
+
+def _i32(a, n):
+    if _is_torch(a):
+        import torch
+        assert a.dtype == torch.int32 and a.is_contiguous() and a.numel() == n
+        return a
+    return np.ascontiguousarray(a, dtype=np.int32).reshape(n)
+
+
+def _box(box):
+    return np.ascontiguousarray(box, dtype=np.float64).reshape(3)
+
+
+# ---- handle classes -------------------------------------------------------------
+
+class Context:
+    def __init__(self, device=0, stream=None):
+        h = ctypes.c_void_p()
+        s = None if stream is None else ctypes.c_void_p(int(stream))
+        rc = tersoff_ctx_create(int(device), s, ctypes.byref(h))
+        if rc != OK:
+            raise TersoffError(rc, "tersoff_ctx_create failed (no CUDA device?)")
+        self.h = h
+
+    def check(self, rc):
+        if rc != OK:
+            raise TersoffError(rc, tersoff_last_error(self.h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            tersoff_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+
+class Params:
+    def __init__(self, ctx, table, masses):
+        table = np.ascontiguousarray(table, dtype=np.float64).reshape(-1, 14)
+        nt = round(table.shape[0] ** (1 / 3))
+        assert nt ** 3 == table.shape[0]
+        masses = np.ascontiguousarray(masses, dtype=np.float64)
+        h = ctypes.c_void_p()
+        ctx.check(tersoff_params_create(ctx.h, nt, ptr(table), ptr(masses), ctypes.byref(h)))
+        self.h, self.ctx, self.ntypes = h, ctx, nt
+
+    @property
+    def cutoff(self):
+        return tersoff_params_cutoff(self.h)
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            tersoff_params_destroy(self.h)
+            self.h = None
+
+
+class NeighborList:
+    def __init__(self, ctx, pos, box, cutoff, skin):
+        n = int(pos.shape[0])
+        pos = _f64(pos, (n, 3))
+        h = ctypes.c_void_p()
+        ctx.check(tersoff_neighbor_build(ctx.h, ptr(pos), n, ptr(_box(box)), float(cutoff), float(skin),
+                                         _dev_flag(pos), ctypes.byref(h)))
+        self.h, self.ctx, self.n = h, ctx, n
+
+    def rebuild(self, pos, box, cutoff, skin):
+        pos = _f64(pos, (self.n, 3))
+        self.ctx.check(tersoff_neighbor_build(self.ctx.h, ptr(pos), self.n, ptr(_box(box)), float(cutoff), float(skin),
+                                              _dev_flag(pos), ctypes.byref(self.h)))
+
+    def get(self):
+        """(counts[N], idx[N, stride]) with -1 past each count."""
+        n = ctypes.c_int64()
+        stride = ctypes.c_int32()
+        self.ctx.check(tersoff_nlist_get(self.ctx.h, self.h, ctypes.byref(n), ctypes.byref(stride), None, None))
+        counts = np.zeros(n.value, dtype=np.int32)
+        idx = np.zeros((n.value, stride.value), dtype=np.int32)
+        self.ctx.check(tersoff_nlist_get(self.ctx.h, self.h, None, None, ptr(counts), ptr(idx)))
+        return counts, idx
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            tersoff_nlist_destroy(self.h)
+            self.h = None
+
+
+def compute(ctx, params, pos, types, box, prec=FP64, nlist=None, forces=None, virial=True):
+    """Energy (eV), forces [N,3] (eV/A) and virial (6) of one configuration.
+
+    pos/types may be host numpy arrays or CUDA torch tensors (then ``forces``, if
+    given, must be a CUDA float64 tensor [N,3]; it is written in place)."""
+    n = int(pos.shape[0])
+    pos = _f64(pos, (n, 3))
+    types = _i32(types, n)
+    flags = _dev_flag(pos, types, forces)
+    if forces is None:
+        if flags == DEVICE_PTRS:
+            import torch
+            forces = torch.empty((n, 3), dtype=torch.float64, device=pos.device)
+        else:
+            forces = np.zeros((n, 3))
+    e = ctypes.c_double()
+    w = np.zeros(6)
+    ctx.check(tersoff_compute(ctx.h, ptr(pos), ptr(types), n, ptr(_box(box)), params.h,
+                              nlist.h if nlist is not None else None, int(prec), flags, ctypes.byref(e),
+                              ptr(forces), ptr(w) if virial else None))
+    return e.value, forces, (w if virial else None)
+
+
+class MD:
+    """Device-resident velocity-Verlet state (tersoff_md_*)."""
+
+    def __init__(self, ctx, params, pos, vel, types, box, dt, skin, prec=MIXED):
+        n = int(pos.shape[0])
+        pos = _f64(pos, (n, 3))
+        vel = _f64(vel, (n, 3))
+        types = _i32(types, n)
+        h = ctypes.c_void_p()
+        ctx.check(tersoff_md_create(ctx.h, ptr(pos), ptr(vel), ptr(types), n, ptr(_box(box)), params.h, float(dt),
+                                    float(skin), int(prec), _dev_flag(pos, vel, types), ctypes.byref(h)))
+        self.h, self.ctx, self.n, self.params = h, ctx, n, params
+
+    def step(self, nsteps, trace=False):
+        tr = np.zeros((nsteps + 1, 2)) if trace else None
+        self.ctx.check(tersoff_md_step(self.h, int(nsteps), ptr(tr)))
+        return tr
+
+    def step_async(self, nsteps):
+        self.ctx.check(tersoff_md_step_async(self.h, int(nsteps)))
+
+    def sync(self):
+        self.ctx.check(tersoff_md_sync(self.h))
+
+    def get(self, forces=False):
+        p = np.zeros((self.n, 3))
+        v = np.zeros((self.n, 3))
+        f = np.zeros((self.n, 3)) if forces else None
+        self.ctx.check(tersoff_md_get(self.h, ptr(p), ptr(v), ptr(f), HOST_PTRS))
+        return (p, v, f) if forces else (p, v)
+
+    def stats(self):
+        s, r, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        self.ctx.check(tersoff_md_stats(self.h, ctypes.byref(s), ctypes.byref(r), ctypes.byref(c)))
+        return dict(steps=s.value, rebuilds=r.value, stride=c.value)
+
+    def profile(self, enable=True):
+        self.ctx.check(tersoff_md_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self):
+        """(ms[4], launches[4]) for phases (integrator, list build, force, bookkeeping)."""
+        ms = np.zeros(4)
+        n = np.zeros(4, dtype=np.int64)
+        self.ctx.check(tersoff_md_profile_read(self.h, ptr(ms), ptr(n)))
+        return ms, n
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            tersoff_md_destroy(self.h)
+            self.h = None
+
+
+def md_run(ctx, params, pos, vel, types, box, dt, nsteps, skin, prec=MIXED, trace=True):
+    """One call: returns (pos, vel, trace) after nsteps (host arrays)."""
+    n = int(pos.shape[0])
+    pos = np.array(pos, dtype=np.float64).reshape(n, 3)
+    vel = np.array(vel, dtype=np.float64).reshape(n, 3)
+    types = _i32(types, n)
+    tr = np.zeros((nsteps + 1, 2)) if trace else None
+    ctx.check(tersoff_md_run(ctx.h, ptr(pos), ptr(vel), ptr(types), n, ptr(_box(box)), params.h, float(dt),
+                             int(nsteps), float(skin), int(prec), HOST_PTRS, ptr(tr)))
+    return pos, vel, tr

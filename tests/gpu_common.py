@@ -1,0 +1,36 @@
+"""Shared fixtures of the GPU tests: one library context per session, the
+product's and the oracle's parameter tables built independently."""
+import numpy as np
+import pytest
+
+from oracle import oracle, params as oparams
+from paper_1710_00882_gb300 import params as pparams
+from paper_1710_00882_gb300 import workloads as wl
+
+# tolerances against the FP64 oracle
+FP64_E_REL, FP64_F_ABS = 1e-12, 1e-10
+MIX_E_REL, MIX_F_ABS = 1e-6, 1e-4
+
+
+def oracle_table(species, **kw):
+    if species == ("Si",):
+        return oparams.si_table(**kw), oparams.masses(["Si"])
+    if species == ("Si", "C"):
+        return oparams.sic_table(**kw), oparams.masses(["Si", "C"])
+    raise ValueError(species)
+
+
+def product_params(ctx, species, **kw):
+    from paper_1710_00882_gb300 import tersoff as T
+    tab, m = pparams.for_species(species, **kw)
+    return T.Params(ctx, tab, m)
+
+
+def assert_parity(E, F, W, Eo, Fo, Wo, e_rel, f_abs, w_abs_per_atom, what=""):
+    """Energy relative, force max-abs and virial absolute (per atom, summed) bounds."""
+    assert abs(E - Eo) <= e_rel * abs(Eo), f"{what} energy {E!r} vs {Eo!r} rel {abs(E - Eo) / abs(Eo):.3e}"
+    err = np.abs(F - Fo).max() if len(F) else 0.0
+    assert err <= f_abs, f"{what} force max-abs err {err:.3e}"
+    if W is not None and Wo is not None:
+        werr = np.abs(np.asarray(W) - np.asarray(Wo)).max()
+        assert werr <= w_abs_per_atom * max(1, len(F)), f"{what} virial err {werr:.3e}: {W} vs {Wo}"

@@ -1,0 +1,181 @@
+"""Velocity-Verlet MD on the GPU against the FP64 oracle and against itself.
+
+MD is chaotic, so trajectories are compared only over a short window (50 steps,
+rel 1e-9 in FP64); over longer runs the oracle re-evaluates the GPU's own
+snapshot positions, and NVE energy conservation, drift, reversibility and
+bitwise resume are checked on the GPU alone."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle
+from paper_1710_00882_gb300 import workloads as wl
+
+from gpu_common import FP64_E_REL, FP64_F_ABS, MIX_E_REL, MIX_F_ABS, assert_parity, oracle_table, product_params
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def T():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1710_00882_gb300 import tersoff
+    return tersoff
+
+
+@pytest.fixture(scope="module")
+def ctx(T):
+    return T.Context(0)
+
+
+def test_fp64_trajectory_matches_oracle(T, ctx):
+    s = wl.si_32k()
+    P = product_params(ctx, s.species)
+    tab, m = oracle_table(s.species)
+    n = 50
+    md = T.MD(ctx, P, s.pos, s.vel, s.types, s.box, dt=1e-3, skin=0.3, prec=T.FP64)
+    tr = md.step(n, trace=True)
+    p, v = md.get()
+    po, vo, tro = oracle.md_run(s.pos, s.vel, s.types, s.box, tab, m, 1e-3, n)
+    assert np.abs(p - po).max() < 1e-9 * 50
+    assert np.abs(v - vo).max() < 1e-9 * 20
+    assert np.allclose(tr, tro, rtol=1e-9, atol=1e-9)
+
+
+def test_mixed_trajectory_close_to_oracle(T, ctx):
+    s = wl.si_box(8, 8, 8, seed=21, T=1000.0)
+    P = product_params(ctx, s.species)
+    tab, m = oracle_table(s.species)
+    n = 10
+    md = T.MD(ctx, P, s.pos, s.vel, s.types, s.box, dt=1e-3, skin=0.3, prec=T.MIXED)
+    tr = md.step(n, trace=True)
+    p, v = md.get()
+    po, vo, tro = oracle.md_run(s.pos, s.vel, s.types, s.box, tab, m, 1e-3, n)
+    assert np.abs(p - po).max() < 1e-7
+    assert np.allclose(tr[:, 0], tro[:, 0], rtol=MIX_E_REL)
+
+
+@pytest.mark.parametrize("prec_name", ["FP64", "MIXED"])
+def test_snapshots_reevaluated_by_oracle(T, ctx, prec_name):
+    """1000 NVE steps of the 32,000-atom box; at steps 0, 100, ..., 1000 the oracle
+    evaluates the GPU's positions: energy and forces within the precision's tolerance."""
+    prec = getattr(T, prec_name)
+    er, fa = (FP64_E_REL, FP64_F_ABS) if prec == T.FP64 else (MIX_E_REL, MIX_F_ABS)
+    s = wl.si_32k()
+    P = product_params(ctx, s.species)
+    tab, m = oracle_table(s.species)
+    md = T.MD(ctx, P, s.pos, s.vel, s.types, s.box, dt=1e-3, skin=0.3, prec=prec)
+    for k in range(11):
+        tr = md.step(0 if k == 0 else 100, trace=True)
+        p, v, f = md.get(forces=True)
+        Eo, Fo, _ = oracle.energy_forces(p, s.types, s.box, tab)
+        assert_parity(tr[-1, 0], f, None, Eo, Fo, None, er, fa, 0, f"step {100 * k}")
+        assert tr[-1, 1] == pytest.approx(oracle.kinetic(v, s.types, m), rel=1e-12)
+    st = md.stats()
+    assert st["steps"] == 1000 and st["rebuilds"] >= 2
+
+
+def test_energy_conservation_fp64(T, ctx):
+    s = wl.si_32k()
+    P = product_params(ctx, s.species)
+    md = T.MD(ctx, P, s.pos, s.vel, s.types, s.box, dt=1e-3, skin=0.3, prec=T.FP64)
+    tr = md.step(1000, trace=True)
+    et = tr.sum(axis=1)
+    assert np.abs(et - et[0]).max() / s.n < 2e-4
+
+
+def drift_stats(tr, n, dt):
+    et = tr.sum(axis=1) / n
+    t = np.arange(len(et)) * dt
+    slope = np.polyfit(t, et, 1)[0]
+    return abs(slope), np.abs(et - et[0]).max()
+
+
+@pytest.mark.slow
+def test_mixed_drift_within_twice_fp64(T, ctx):
+    """10,000 NVE steps on 32,000 atoms: mixed-precision energy drift (fitted slope and
+    max excursion per atom) within 2x the FP64 path's, with a 1e-6 eV/atom floor."""
+    s = wl.si_32k()
+    P = product_params(ctx, s.species)
+    res = {}
+    for prec in (T.FP64, T.MIXED):
+        md = T.MD(ctx, P, s.pos, s.vel, s.types, s.box, dt=1e-3, skin=0.3, prec=prec)
+        tr = md.step(10000, trace=True)
+        res[prec] = drift_stats(tr, s.n, 1e-3)
+    (s64, m64), (smx, mmx) = res[T.FP64], res[T.MIXED]
+    print(f"drift slope eV/atom/ps fp64 {s64:.3e} mixed {smx:.3e}; max dev fp64 {m64:.3e} mixed {mmx:.3e}")
+    assert smx <= 2 * max(s64, 1e-6 / 10.0)
+    assert mmx <= 2 * max(m64, 1e-6)
+
+
+@pytest.mark.parametrize("prec_name", ["FP64", "MIXED"])
+def test_resume_is_bitwise(T, ctx, prec_name):
+    prec = getattr(T, prec_name)
+    s = wl.sic_box(6, seed=22, T=1500.0)
+    P = product_params(ctx, s.species)
+    a = T.MD(ctx, P, s.pos, s.vel, s.types, s.box, dt=0.5e-3, skin=0.3, prec=prec)
+    a.step(200)
+    pa, va = a.get()
+    b = T.MD(ctx, P, s.pos, s.vel, s.types, s.box, dt=0.5e-3, skin=0.3, prec=prec)
+    b.step(100)
+    pb, vb = b.get()
+    c = T.MD(ctx, P, pb, vb, s.types, s.box, dt=0.5e-3, skin=0.3, prec=prec)
+    c.step(100)
+    pc, vc = c.get()
+    assert np.array_equal(pa, pc) and np.array_equal(va, vc)
+
+
+def test_async_steps_equal_sync_steps(T, ctx):
+    s = wl.si_box(6, 6, 6, seed=23, T=1000.0)
+    P = product_params(ctx, s.species)
+    a = T.MD(ctx, P, s.pos, s.vel, s.types, s.box, dt=1e-3, skin=0.3, prec=T.MIXED)
+    for _ in range(10):
+        a.step_async(7)
+    a.sync()
+    b = T.MD(ctx, P, s.pos, s.vel, s.types, s.box, dt=1e-3, skin=0.3, prec=T.MIXED)
+    b.step(70)
+    pa, va = a.get()
+    pb, vb = b.get()
+    assert np.array_equal(pa, pb) and np.array_equal(va, vb)
+
+
+def test_time_reversible_fp64(T, ctx):
+    s = wl.si_box(6, 6, 6, seed=24, T=1000.0)
+    P = product_params(ctx, s.species)
+    md = T.MD(ctx, P, s.pos, s.vel, s.types, s.box, dt=1e-3, skin=0.3, prec=T.FP64)
+    md.step(200)
+    p, v = md.get()
+    back = T.MD(ctx, P, p, -v, s.types, s.box, dt=1e-3, skin=0.3, prec=T.FP64)
+    back.step(200)
+    p2, v2 = back.get()
+    assert np.abs(p2 - s.pos).max() < 1e-8
+    assert np.abs(v2 + s.vel).max() < 1e-7
+
+
+def test_md_run_one_call(T, ctx):
+    s = wl.si_box(5, 5, 5, seed=25, T=800.0)
+    P = product_params(ctx, s.species)
+    p, v, tr = T.md_run(ctx, P, s.pos, s.vel, s.types, s.box, 1e-3, 30, 0.3, prec=T.FP64)
+    md = T.MD(ctx, P, s.pos, s.vel, s.types, s.box, dt=1e-3, skin=0.3, prec=T.FP64)
+    tr2 = md.step(30, trace=True)
+    p2, v2 = md.get()
+    assert np.array_equal(p, p2) and np.array_equal(v, v2)
+    assert np.allclose(tr, tr2, rtol=1e-13)
+
+
+def test_list_grows_during_run(T, ctx):
+    """A cold crystal that melts under a huge initial temperature: the neighbour lists
+    grow past the capacity chosen at creation; the run recovers on the device state
+    and still matches the oracle's energy on its final positions."""
+    s = wl.si_box(4, 4, 4, seed=26, T=30000.0, sigma=0.0)
+    P = product_params(ctx, s.species)
+    tab, m = oracle_table(s.species)
+    md = T.MD(ctx, P, s.pos, s.vel, s.types, s.box, dt=0.5e-3, skin=1.0, prec=T.FP64)
+    stride0 = md.stats()["stride"]
+    tr = md.step(400, trace=True)
+    p, v, f = md.get(forces=True)
+    Eo, Fo, _ = oracle.energy_forces(p, s.types, s.box, tab)
+    assert_parity(tr[-1, 0], f, None, Eo, Fo, None, FP64_E_REL, FP64_F_ABS, 0, "melt")
+    assert md.stats()["stride"] >= stride0

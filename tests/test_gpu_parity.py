@@ -1,0 +1,209 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances: FP64 energy rel <= 1e-12, force max-abs <= 1e-10 eV/A; mixed
+energy rel <= 1e-6, force max-abs <= 1e-4 eV/A (the accuracy targets the
+workloads are specified with).  Virial: 1e-10 (FP64) / 1e-5 (mixed) eV per atom.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle
+from paper_1710_00882_gb300 import workloads as wl
+
+from gpu_common import (FP64_E_REL, FP64_F_ABS, MIX_E_REL, MIX_F_ABS, assert_parity, oracle_table,
+                        product_params)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def T():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1710_00882_gb300 import tersoff
+    return tersoff
+
+
+@pytest.fixture(scope="module")
+def ctx(T):
+    return T.Context(0)
+
+
+def run_pair(T, ctx, s, species=None, prec=None, **kw):
+    species = species or s.species
+    P = product_params(ctx, species, **kw)
+    tab, _ = oracle_table(species, **kw)
+    Eo, Fo, Wo = oracle.energy_forces(s.pos, s.types, s.box, tab)
+    out = {}
+    for p in ([prec] if prec is not None else [T.FP64, T.MIXED]):
+        E, F, W = T.compute(ctx, P, s.pos, s.types, s.box, prec=p)
+        out[p] = (E, F, W)
+    return out, (Eo, Fo, Wo)
+
+
+def check(T, out, ref, what):
+    Eo, Fo, Wo = ref
+    if T.FP64 in out:
+        E, F, W = out[T.FP64]
+        assert_parity(E, F, W, Eo, Fo, Wo, FP64_E_REL, FP64_F_ABS, 1e-10, what + " fp64")
+    if T.MIXED in out:
+        E, F, W = out[T.MIXED]
+        assert_parity(E, F, W, Eo, Fo, Wo, MIX_E_REL, MIX_F_ABS, 1e-5, what + " mixed")
+
+
+def test_si_512_config(T, ctx):
+    """512-atom Si diamond, uniform +-0.05 A displacements: the single-evaluation workload."""
+    s = wl.si_512()
+    out, ref = run_pair(T, ctx, s)
+    check(T, out, ref, "si512")
+
+
+def test_sic_ragged_with_vacancies(T, ctx):
+    """3C-SiC 4^3 cells with vacancies (N = 487, not a multiple of any block), 1500 K
+    displacements: skin-dominated lists, two types, Si-Si pairs in the taper."""
+    s = wl.sic_box(4, seed=41, T=1500.0, sigma=0.08)
+    assert s.n % 32 != 0
+    out, ref = run_pair(T, ctx, s)
+    check(T, out, ref, "sic")
+
+
+@pytest.mark.parametrize("lam3,m", [(1.3, 1), (1.1, 3)])
+def test_lambda3_variants(T, ctx, lam3, m):
+    s = wl.sic_box(3, seed=42, T=2000.0, sigma=0.1)
+    out, ref = run_pair(T, ctx, s, lambda3=lam3, m=m)
+    check(T, out, ref, f"lam3={lam3},m={m}")
+
+
+def test_compressed_many_neighbours(T, ctx):
+    """Si compressed to a = 4.1 A with displacements: the second shell (2.90 A) sits in
+    the f_C taper, ~16 in-cutoff neighbours per atom, exercises the wider slot kernels."""
+    rng = np.random.default_rng(5)
+    s = wl.diamond(3, 3, 3, 4.1)
+    s.pos = s.pos + rng.normal(0, 0.12, size=s.pos.shape)
+    out, ref = run_pair(T, ctx, s)
+    check(T, out, ref, "compressed")
+
+
+def test_two_cells_per_side(T, ctx):
+    """Smallest legal boxes: 2 cells per side (box < 3 * r_list)."""
+    s = wl.sic_box(2, seed=43, T=1000.0)
+    out, ref = run_pair(T, ctx, s)
+    check(T, out, ref, "sic2")
+    s = wl.si_box(2, 2, 2, seed=44, T=1000.0)
+    out, ref = run_pair(T, ctx, s)
+    check(T, out, ref, "si2")
+
+
+def test_positions_outside_box(T, ctx):
+    s = wl.si_box(3, 3, 3, seed=45, T=1000.0)
+    rng = np.random.default_rng(0)
+    s.pos = s.pos + s.box * rng.integers(-3, 4, size=s.pos.shape)
+    out, ref = run_pair(T, ctx, s)
+    check(T, out, ref, "unwrapped")
+
+
+def test_edge_cases(T, ctx):
+    P = product_params(ctx, ("Si",))
+    box = np.array([20.0, 20.0, 20.0])
+    # empty system
+    E, F, W = T.compute(ctx, P, np.zeros((0, 3)), np.zeros(0, np.int32), box)
+    assert E == 0.0 and F.shape == (0, 3) and np.all(W == 0)
+    # isolated atom, dimer (zeta = 0 path), trimer
+    for pos in ([[1.0, 2.0, 3.0]], [[5.0, 5.0, 5.0], [7.35, 5.0, 5.0]],
+                [[5.0, 5.0, 5.0], [7.3, 5.0, 5.0], [4.2, 7.2, 5.0]]):
+        pos = np.array(pos)
+        types = np.zeros(len(pos), np.int32)
+        Eo, Fo, Wo = oracle.energy_forces(pos, types, box, oracle_table(("Si",))[0])
+        for prec, (er, fa) in ((T.FP64, (FP64_E_REL, FP64_F_ABS)), (T.MIXED, (MIX_E_REL, MIX_F_ABS))):
+            E, F, W = T.compute(ctx, P, pos, types, box, prec=prec)
+            if Eo == 0.0:
+                assert E == 0.0 and np.all(F == 0)
+            else:
+                assert_parity(E, F, W, Eo, Fo, Wo, er, fa, 1e-4)
+
+
+def test_errors_are_reported(T, ctx):
+    P = product_params(ctx, ("Si",))
+    s = wl.si_box(2, 2, 2, seed=46, T=300.0)
+    with pytest.raises(T.TersoffError) as e:
+        T.compute(ctx, P, s.pos, np.full(s.n, 3, np.int32), s.box)
+    assert e.value.code == T.ERR_ARG
+    with pytest.raises(T.TersoffError) as e:
+        T.compute(ctx, P, s.pos[:10], s.types[:10], np.array([5.0, 20.0, 20.0]))
+    assert e.value.code == T.ERR_BOX_TOO_SMALL
+    bad = s.pos.copy()
+    bad[3, 1] = np.nan
+    with pytest.raises(T.TersoffError) as e:
+        T.compute(ctx, P, bad, s.types, s.box)
+    assert e.value.code == T.ERR_NONFINITE
+    # the context stays usable after errors
+    E, F, W = T.compute(ctx, P, s.pos, s.types, s.box)
+    assert np.isfinite(E)
+
+
+def test_deterministic(T, ctx):
+    s = wl.sic_box(5, seed=47, T=1500.0)
+    P = product_params(ctx, s.species)
+    for prec in (T.FP64, T.MIXED):
+        E1, F1, W1 = T.compute(ctx, P, s.pos, s.types, s.box, prec=prec)
+        E2, F2, W2 = T.compute(ctx, P, s.pos, s.types, s.box, prec=prec)
+        assert np.array_equal(F1, F2)
+
+
+def test_device_pointers(T, ctx):
+    import torch
+    s = wl.si_box(4, 4, 4, seed=48, T=1000.0)
+    P = product_params(ctx, s.species)
+    pos = torch.tensor(s.pos, device="cuda")
+    types = torch.tensor(s.types, device="cuda")
+    E, F, W = T.compute(ctx, P, pos, types, s.box, prec=T.FP64)
+    Eh, Fh, Wh = T.compute(ctx, P, s.pos, s.types, s.box, prec=T.FP64)
+    assert E == Eh and np.array_equal(F.cpu().numpy(), Fh)
+
+
+def test_given_neighbor_list_with_skin(T, ctx):
+    """A list built with skin 0.3 A stays valid for displacements below skin/2."""
+    s = wl.si_box(5, 5, 5, seed=49, T=1000.0)
+    P = product_params(ctx, s.species)
+    nl = T.NeighborList(ctx, s.pos, s.box, P.cutoff, 0.3)
+    rng = np.random.default_rng(1)
+    moved = s.pos + rng.uniform(-0.08, 0.08, size=s.pos.shape)
+    tab, _ = oracle_table(s.species)
+    Eo, Fo, Wo = oracle.energy_forces(moved, s.types, s.box, tab)
+    E, F, W = T.compute(ctx, P, moved, s.types, s.box, prec=T.FP64, nlist=nl)
+    assert_parity(E, F, W, Eo, Fo, Wo, FP64_E_REL, FP64_F_ABS, 1e-10, "given list")
+
+
+@pytest.mark.parametrize("seed,box_cells,skin", [(1, 2, 0.3), (2, 3, 0.0), (3, 5, 0.5), (4, 2, 1.2)])
+def test_neighbor_list_equals_brute_force(T, ctx, seed, box_cells, skin):
+    s = wl.sic_box(box_cells, seed=seed, T=2000.0)
+    rc = 3.0
+    nl = T.NeighborList(ctx, s.pos, s.box, rc, skin)
+    counts, idx = nl.get()
+    off, oidx = oracle.neighbors(s.pos, s.box, rc + skin, method="brute")
+    # the GPU list may also hold pairs within a relative 1e-5 above r_list
+    for i in range(s.n):
+        got = set(idx[i, :counts[i]].tolist())
+        want = set(oidx[off[i]:off[i + 1]].tolist())
+        assert want <= got
+        for j in got - want:
+            dj = np.linalg.norm((s.pos[j] - s.pos[i] + s.box / 2) % s.box - s.box / 2)
+            assert dj < (rc + skin) * (1 + 1e-5)
+        assert list(idx[i, :counts[i]]) == sorted(got)
+
+
+@pytest.mark.slow
+def test_full_size_si_512k(T, ctx):
+    """The 512,000-atom Si box at its full size, in the launch configuration the bench times:
+    every force and the energy against the oracle."""
+    s = wl.si_512k()
+    out, ref = run_pair(T, ctx, s)
+    check(T, out, ref, "si512k")
+
+
+@pytest.mark.slow
+def test_full_size_sic_950k(T, ctx):
+    """The 3C-SiC box at full size (950,000 atoms), mixed and FP64, against the oracle."""
+    s = wl.sic_1m()
+    out, ref = run_pair(T, ctx, s)
+    check(T, out, ref, "sic950k")
