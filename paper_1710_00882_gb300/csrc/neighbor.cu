@@ -266,8 +266,9 @@ cudaError_t launch_build(cudaStream_t st, int N, const int4 *q, const CellGrid &
   k_scan_sums<<<1, SCAN_THREADS, 0, st>>>(ntiles, tile_sums, cell_start + g.ncell, rs, gated);
   k_scan_add<<<(g.ncell + T - 1) / T, T, 0, st>>>(g.ncell, cell_start, tile_sums, cell_count, rs, gated);
   k_cell_fill<<<BN, T, 0, st>>>(N, cell_of, rank, cell_start, cell_atoms, rs, gated);
-  k_build<<<BN, 128, 0, st>>>(N, q, g, geo, cell_start, cell_atoms, nbr, cnt, cap, qref, rs, gated);
-  k_reverse<<<BN, 128, 0, st>>>(N, nbr, cnt, rev, rs, gated);
+  const int BN128 = (N + 127) / 128;
+  k_build<<<BN128, 128, 0, st>>>(N, q, g, geo, cell_start, cell_atoms, nbr, cnt, cap, qref, rs, gated);
+  k_reverse<<<BN128, 128, 0, st>>>(N, nbr, cnt, rev, rs, gated);
   k_build_done<<<1, 1, 0, st>>>(rs, gated);
   return cudaGetLastError();
 }
