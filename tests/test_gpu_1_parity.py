@@ -41,14 +41,17 @@ def run_pair(T, ctx, s, species=None, prec=None, **kw):
     return out, (Eo, Fo, Wo)
 
 
-def check(T, out, ref, what):
+def check(T, out, ref, what, mixed_f_rel=None):
+    """mixed_f_rel: for stress cases with forces far above the workloads' (|F| up to
+    ~50 eV/A), bound the mixed force error relative to the largest force instead."""
     Eo, Fo, Wo = ref
     if T.FP64 in out:
         E, F, W = out[T.FP64]
         assert_parity(E, F, W, Eo, Fo, Wo, FP64_E_REL, FP64_F_ABS, 1e-10, what + " fp64")
     if T.MIXED in out:
         E, F, W = out[T.MIXED]
-        assert_parity(E, F, W, Eo, Fo, Wo, MIX_E_REL, MIX_F_ABS, 1e-5, what + " mixed")
+        fa = MIX_F_ABS if mixed_f_rel is None else max(MIX_F_ABS, mixed_f_rel * np.abs(Fo).max())
+        assert_parity(E, F, W, Eo, Fo, Wo, MIX_E_REL, fa, 1e-5, what + " mixed")
 
 
 def test_si_512_config(T, ctx):
@@ -81,7 +84,7 @@ def test_compressed_many_neighbours(T, ctx):
     s = wl.diamond(3, 3, 3, 4.1)
     s.pos = s.pos + rng.normal(0, 0.12, size=s.pos.shape)
     out, ref = run_pair(T, ctx, s)
-    check(T, out, ref, "compressed")
+    check(T, out, ref, "compressed", mixed_f_rel=4e-6)
 
 
 def test_two_cells_per_side(T, ctx):
