@@ -1,25 +1,39 @@
-// Tersoff energy/force kernel: Algorithm 1 of the paper, one thread per atom i.
+// Tersoff energy/force kernels: Algorithm 1 of the paper, one thread per atom i.
 //
-// Per atom the thread
-//   1. walks i's Verlet list and packs the in-cutoff neighbours (Sec. 3: skin
-//      atoms are tested once and never enter the K loops) into per-thread
-//      shared-memory slots: unit vector, r, 1/r, f_C(r), f_C'(r), type;
-//   2. first K loop (pass A): zeta_ij for every packed j (Eq. 3), then the pair
-//      term V(i,j,zeta_ij) (Eqs. 1-2), its r-derivative and dV/dzeta;
-//   3. second K loop (pass B): dzeta(i,j,k)/dx_j and /dx_k scaled by dV/dzeta
-//      (the restructuring of Sec. 2: zeta is complete before any derivative is
-//      scaled, so each derivative is formed once).
-// All force contributions that i's terms make to neighbour j are summed per j in
-// the thread and written once, to slot s of i's list (contrib[s][i]); the
-// force on i itself follows from translation invariance (minus their sum).  No
-// atomics: a reverse gather (gather.cu / integrate.cu) adds, for each atom m,
-// the contributions written in m's slot of each neighbour's list, in list order,
-// so the result is bitwise reproducible.  This replaces the serialised
-// conflicting updates of the paper's "I" vectorisation (Sec. 3).
+// Per atom i the thread
+//   0. walks i's Verlet list once and marks the in-cutoff entries (Sec. 3: skin
+//      atoms are tested once and never enter the K loops);
+//   1. packs the in-cutoff neighbours into slots: unit vector, r, 1/r, f_C(r),
+//      f_C'(r), type, list slot;
+//   2. first K loop: zeta_ij for every slot j (Eq. 3); then the pair term
+//      V(i,j,zeta_ij) (Eqs. 1-2), its r-derivative and dV/dzeta;
+//   3. second K loop: the derivatives of zeta(i,j,k) scaled by dV/dzeta (the
+//      restructuring of Sec. 2: zeta is complete before any derivative is formed).
+//
+// Fast kernel (k_force_reg): slots live in registers (compile-time slot count 4
+// or 8, loops fully unrolled).  Both K loops run over unordered neighbour pairs
+// {j,k}: cos(theta), g and g' are shared by zeta(i,j,k) and zeta(i,k,j) whenever
+// the angular constants of rows (i,j,k) and (i,k,j) agree (Tersoff's tables take
+// them from atom i), so each is evaluated once per pair instead of twice.  Atoms
+// with more in-cutoff neighbours than slots are queued, per block and in order,
+// for the general kernel.
+//
+// General kernel (k_force_gen): slots in per-thread shared memory (8..64), loops
+// over ordered (j,k) as in Algorithm 1; handles any table and any neighbour count.
+//
+// Scatter: all force contributions of i's terms on neighbour j are summed per j in
+// the thread and written once, to slot s of i's list (contrib[s][i]); the force of
+// i's terms on i itself is minus their sum (translation invariance).  No atomics:
+// the reverse gather (integrate.cu) adds them per atom in list order, so forces are
+// bitwise reproducible.  Energy and virial go to per-block partial sums that a
+// single block reduces in a fixed order.
 //
 // Precision: R = double (FP64 mode) or float (mixed mode).  In mixed mode the
-// relative vector d_ij is the exact int32 difference of 32-bit fixed-point
-// coordinates, converted once to float.
+// relative vector d_ij is formed from the exact int32 difference of 32-bit
+// fixed-point coordinates; the conversion to float splits the integer and the
+// scale so that d_ij is within ~1 ulp, and exp(-lambda r) forms lambda r with an
+// FMA-exact product, because the pair term's r-derivative is a difference of two
+// terms ~10x larger than itself.
 #include "internal.cuh"
 
 namespace tsf {
@@ -28,21 +42,75 @@ template <class R> struct V4t;
 template <> struct V4t<float> { using type = float4; };
 template <> struct V4t<double> { using type = dbl4; };
 
-__device__ __forceinline__ float t_exp(float x) { return expf(x); }
-__device__ __forceinline__ double t_exp(double x) { return exp(x); }
-__device__ __forceinline__ float t_exp2(float x) { return exp2f(x); }
-__device__ __forceinline__ double t_exp2(double x) { return exp2(x); }
-__device__ __forceinline__ float t_log2(float x) { return log2f(x); }
-__device__ __forceinline__ double t_log2(double x) { return log2(x); }
-__device__ __forceinline__ float t_rsqrt(float x) { return rsqrtf(x); }
-__device__ __forceinline__ double t_rsqrt(double x) { return rsqrt(x); }
-__device__ __forceinline__ float t_rcp(float x) { return __frcp_rn(x); }
-__device__ __forceinline__ double t_rcp(double x) { return 1.0 / x; }
-__device__ __forceinline__ void t_sincospi(float x, float *s, float *c) { sincospif(x, s, c); }
-__device__ __forceinline__ void t_sincospi(double x, double *s, double *c) { sincospi(x, s, c); }
+constexpr int FAST_THREADS = 128;
+constexpr float L2E_F = 1.44269502f;                   // log2(e) rounded to float
+constexpr float L2E_F_LO = 1.925963033500011e-08f;     // log2(e) - L2E_F
+
+// ---- math of the two precisions ------------------------------------------
+
+struct MathF {
+  using R = float;
+  static __device__ __forceinline__ float rcp(float x)
+  {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+  }
+  static __device__ __forceinline__ float rsqrt(float x)
+  {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+  }
+  static __device__ __forceinline__ float lg2(float x)
+  {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+  }
+  static __device__ __forceinline__ float ex2(float x)
+  {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+  }
+  // e^{-x} for x = xh + xl (|xl| << |xh|): e^{-x} = 2^{-x log2 e}; the product
+  // xh * log2(e) is split exactly with an FMA and the small remainder applied to
+  // first order, so the result carries the error of one ex2 only.
+  static __device__ __forceinline__ float expneg2(float xh, float xl)
+  {
+    const float yh = xh * L2E_F;
+    const float yl = fmaf(xh, L2E_F, -yh) + fmaf(xh, L2E_F_LO, xl * L2E_F);
+    return ex2(-yh) * fmaf(-yl, 0.69314718f, 1.0f);
+  }
+  // e^{-(lh + ll) r}, lambda given as float hi + lo
+  static __device__ __forceinline__ float expneg(float lh, float ll, float r)
+  {
+    const float p = lh * r;
+    const float pe = fmaf(lh, r, -p) + ll * r;
+    return expneg2(p, pe);
+  }
+  static __device__ __forceinline__ float expv(float x) { return expneg2(-x, 0.0f); }
+  static __device__ __forceinline__ void sincospi(float t, float *s, float *c) { sincospif(t, s, c); }
+};
+
+struct MathD {
+  using R = double;
+  static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+  static __device__ __forceinline__ double rsqrt(double x) { return ::rsqrt(x); }
+  static __device__ __forceinline__ double lg2(double x) { return ::log2(x); }
+  static __device__ __forceinline__ double ex2(double x) { return ::exp2(x); }
+  static __device__ __forceinline__ double expneg(double lh, double, double r) { return ::exp(-lh * r); }
+  static __device__ __forceinline__ double expv(double x) { return ::exp(x); }
+  static __device__ __forceinline__ void sincospi(double t, double *s, double *c) { ::sincospi(t, s, c); }
+};
+
+template <class R> struct MathOf;
+template <> struct MathOf<float> { using M = MathF; };
+template <> struct MathOf<double> { using M = MathD; };
 
 // f_C and f_C' for r < R + D
-template <class R>
+template <class M, class R>
 __device__ __forceinline__ void cutoff_fn(R r, const PairP<R> &P, R &fc, R &dfc)
 {
   if (r <= P.r_in) {
@@ -50,22 +118,36 @@ __device__ __forceinline__ void cutoff_fn(R r, const PairP<R> &P, R &fc, R &dfc)
     dfc = R(0);
   } else {
     R s, c;
-    t_sincospi((r - P.Rc) * P.inv2D, &s, &c);
+    M::sincospi((r - P.Rc) * P.inv2D, &s, &c);
     fc = R(0.5) - R(0.5) * s;
     dfc = P.dfc_scale * c;
   }
 }
 
-constexpr int NRF = 11;   // real fields per slot
-enum { S_UX = 0, S_UY, S_UZ, S_R, S_IR, S_FC, S_DFC, S_DZ, S_FX, S_FY, S_FZ };
+// bond order b(zeta) (Eq. 2) and db/dzeta
+template <class M, class R>
+__device__ __forceinline__ void bond_order(R zeta, const PairP<R> &P, R &b, R &db)
+{
+  b = R(1);
+  db = R(0);
+  if (zeta > R(0)) {
+    const R xb = M::ex2(P.n * M::lg2(P.beta * zeta));
+    b = M::ex2(P.neg_inv2n * M::lg2(R(1) + xb));
+    db = R(-0.5) * b * xb * M::rcp((R(1) + xb) * zeta);
+  }
+}
 
-template <class R, int MAXNC>
-struct ForceCfg {
-  static constexpr int slot_bytes = NRF * (int)sizeof(R) + 4;
-  static constexpr int raw = 98304 / (MAXNC * slot_bytes);
-  static constexpr int threads = raw >= 128 ? 128 : raw >= 64 ? 64 : 32;
-  static constexpr size_t smem_slots = (size_t)threads * MAXNC * slot_bytes;
-};
+// minimum-image relative vector of a fixed-point pair, accurate to ~1 ulp:
+// the int32 difference is split into a 24-bit head and an 8-bit tail (both exact in
+// float) and the scale into float head + tail.
+__device__ __forceinline__ float qd_fine(int dq, float sh, float sl)
+{
+  const float h = (float)(dq & ~0xff);
+  const float l = (float)(dq & 0xff);
+  const float p = h * sh;
+  const float pe = fmaf(h, sh, -p);
+  return p + fmaf(h, sl, fmaf(l, sh, pe));
+}
 
 template <class R> __device__ __forceinline__ R warp_sum(R v)
 {
@@ -74,15 +156,320 @@ template <class R> __device__ __forceinline__ R warp_sum(R v)
   return v;
 }
 
-template <class R, int MAXNC, bool EFLAG, bool VFLAG>
-__global__ void __launch_bounds__(ForceCfg<R, MAXNC>::threads)
-k_force(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const int *__restrict__ nbr,
-        const int *__restrict__ cnt, Geom geo, const PairP<R> *__restrict__ gpairs,
-        const TripP<R> *__restrict__ gtrips, int nt, typename V4t<R>::type *__restrict__ contrib,
-        typename V4t<R>::type *__restrict__ selfF, unsigned long long *__restrict__ mask, RunState *rs)
+// Per-block partial of (E, W[6]) in a fixed order: float/double per-thread values,
+// warp sums in R, warps combined in float64 in warp order.
+template <class R, int T>
+__device__ __forceinline__ void block_partial(const R (&v)[7], bool eflag, bool vflag, double *out)
 {
+  __shared__ double sw[T / 32][7];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int c = 0; c < 7; ++c) {
+    if ((c == 0 && !eflag) || (c > 0 && !vflag)) continue;
+    R s = warp_sum(v[c]);
+    if (lane == 0) sw[w][c] = (double)s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int c = 0; c < 7; ++c) {
+      double a = 0.0;
+      for (int k = 0; k < T / 32; ++k) a += ((c == 0 && !eflag) || (c > 0 && !vflag)) ? 0.0 : sw[k][c];
+      out[c] = a;
+    }
+    out[7] = 0.0;
+  }
+}
+
+// ============================================================================
+// fast kernel: register slots, unordered neighbour pairs
+
+template <class R, int MAXNC, bool ONE, bool EFLAG, bool VFLAG>
+__global__ void __launch_bounds__(FAST_THREADS)
+k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const int *__restrict__ nbr,
+            const int *__restrict__ cnt, Geom geo, const PairP<R> *__restrict__ gpairs,
+            const TripP<R> *__restrict__ gtrips, int nt, typename V4t<R>::type *__restrict__ contrib,
+            typename V4t<R>::type *__restrict__ selfF, unsigned long long *__restrict__ mask,
+            int *__restrict__ work, int *__restrict__ nwork, double *__restrict__ partial, RunState *rs)
+{
+  using M = typename MathOf<R>::M;
   using V4 = typename V4t<R>::type;
-  constexpr int T = ForceCfg<R, MAXNC>::threads;
+  constexpr bool MIXED = sizeof(R) == 4;
+  constexpr int T = FAST_THREADS;
+  __shared__ PairP<R> pairs[ONE ? 1 : MAX_TYPES * MAX_TYPES];
+  __shared__ TripP<R> trips[ONE ? 1 : MAX_TYPES * MAX_TYPES * MAX_TYPES];
+  __shared__ int warp_over[T / 32];
+
+  if (rs->status != 0) return;   // uniform across the grid
+  if (threadIdx.x < (ONE ? 1 : nt * nt)) pairs[threadIdx.x] = gpairs[threadIdx.x];
+  if (threadIdx.x < (ONE ? 1 : nt * nt * nt)) trips[threadIdx.x] = gtrips[threadIdx.x];
+  __syncthreads();
+
+  const int t = threadIdx.x;
+  const int i = blockIdx.x * T + t;
+  const bool active = i < N;
+
+  int ti = 0;
+  int4 qi = make_int4(0, 0, 0, 0);
+  dbl4 xi = make_dbl4(0, 0, 0, 0);
+  unsigned long long mb = 0ull;
+  if (active) {
+    if (MIXED) {
+      qi = q[i];
+      ti = qi.w;
+    } else {
+      xi = x[i];
+      ti = (int)__double_as_longlong(xi.w);
+    }
+    // pass 0: in-cutoff test of every list entry
+    const int n = cnt[i];
+    for (int s = 0; s < n; ++s) {
+      const int j = nbr[(size_t)s * N + i];
+      R r2;
+      int tj;
+      if (MIXED) {
+        const int4 qj = q[j];
+        tj = qj.w;
+        const float dx = (float)qdiff(qj.x, qi.x) * geo.q_to_f[0];
+        const float dy = (float)qdiff(qj.y, qi.y) * geo.q_to_f[1];
+        const float dz = (float)qdiff(qj.z, qi.z) * geo.q_to_f[2];
+        r2 = dx * dx + dy * dy + dz * dz;
+      } else {
+        const dbl4 xj = x[j];
+        tj = (int)__double_as_longlong(xj.w);
+        double dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
+        dx -= geo.L[0] * rint(dx * geo.invL[0]);
+        dy -= geo.L[1] * rint(dy * geo.invL[1]);
+        dz -= geo.L[2] * rint(dz * geo.invL[2]);
+        r2 = dx * dx + dy * dy + dz * dz;
+      }
+      if (r2 < pairs[ONE ? 0 : ti * nt + tj].rc2) mb |= 1ull << s;
+    }
+  }
+  const int nc_all = __popcll(mb);
+  const bool over = nc_all > MAXNC;
+  // queue atoms with too many neighbours, per block and in thread order
+  {
+    const unsigned bal = __ballot_sync(0xffffffffu, over);
+    if ((t & 31) == 0) warp_over[t >> 5] = __popc(bal);
+    __syncthreads();
+    if (over) {
+      int base = 0;
+      for (int w = 0; w < (t >> 5); ++w) base += warp_over[w];
+      const int k = base + __popc(bal & ((1u << (t & 31)) - 1u));
+      work[(size_t)blockIdx.x * T + k] = i;
+    }
+    if (t == 0) {
+      int s = 0;
+      for (int w = 0; w < T / 32; ++w) s += warp_over[w];
+      nwork[blockIdx.x] = s;
+    }
+  }
+  const int nc = over ? 0 : nc_all;
+  {
+    int m = nc_all;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((t & 31) == 0 && m > 0) atomicMax(&rs->maxnc, m);
+  }
+
+  // ---- slots ---------------------------------------------------------------
+  R ux[MAXNC], uy[MAXNC], uz[MAXNC], rr[MAXNC], ir[MAXNC], fc[MAXNC], dfc[MAXNC];
+  int meta[MAXNC];
+  {
+    unsigned long long rem = over ? 0ull : mb;
+#pragma unroll
+    for (int s = 0; s < MAXNC; ++s) {
+      ux[s] = uy[s] = uz[s] = R(0);
+      rr[s] = ir[s] = R(1);
+      fc[s] = dfc[s] = R(0);
+      meta[s] = 0;
+      if (s < nc) {
+        const int e = __ffsll((long long)rem) - 1;
+        rem &= rem - 1;
+        const int j = nbr[(size_t)e * N + i];
+        R dx, dy, dz;
+        int tj;
+        if (MIXED) {
+          const int4 qj = q[j];
+          tj = qj.w;
+          dx = (R)qd_fine(qdiff(qj.x, qi.x), geo.q_to_f[0], geo.q_to_f_lo[0]);
+          dy = (R)qd_fine(qdiff(qj.y, qi.y), geo.q_to_f[1], geo.q_to_f_lo[1]);
+          dz = (R)qd_fine(qdiff(qj.z, qi.z), geo.q_to_f[2], geo.q_to_f_lo[2]);
+        } else {
+          const dbl4 xj = x[j];
+          tj = (int)__double_as_longlong(xj.w);
+          double ddx = xj.x - xi.x, ddy = xj.y - xi.y, ddz = xj.z - xi.z;
+          ddx -= geo.L[0] * rint(ddx * geo.invL[0]);
+          ddy -= geo.L[1] * rint(ddy * geo.invL[1]);
+          ddz -= geo.L[2] * rint(ddz * geo.invL[2]);
+          dx = (R)ddx; dy = (R)ddy; dz = (R)ddz;
+        }
+        const R r2 = dx * dx + dy * dy + dz * dz;
+        const R inv = M::rsqrt(r2);
+        const R r = r2 * inv;
+        ux[s] = dx * inv;
+        uy[s] = dy * inv;
+        uz[s] = dz * inv;
+        rr[s] = r;
+        ir[s] = inv;
+        cutoff_fn<M>(r, pairs[ONE ? 0 : ti * nt + tj], fc[s], dfc[s]);
+        meta[s] = e | (tj << 8);
+      }
+    }
+  }
+
+  // ---- first K loop: zeta over unordered pairs --------------------------------
+  R zeta[MAXNC];
+#pragma unroll
+  for (int s = 0; s < MAXNC; ++s) zeta[s] = R(0);
+#pragma unroll
+  for (int a = 0; a < MAXNC; ++a) {
+#pragma unroll
+    for (int b = a + 1; b < MAXNC; ++b) {
+      if (b < nc) {
+        const TripP<R> &Tp = trips[ONE ? 0 : (ti * nt + (meta[a] >> 8)) * nt + (meta[b] >> 8)];
+        const R cost = ux[a] * ux[b] + uy[a] * uy[b] + uz[a] * uz[b];
+        const R u = Tp.h - cost;
+        const R u2 = u * u;
+        const R g = Tp.gamma + Tp.K * u2 * M::rcp(Tp.d2 + u2);
+        R eab = R(1), eba = R(1);
+        if (Tp.lam3 != R(0)) {
+          R arg = Tp.lam3 * (rr[a] - rr[b]);
+          if (Tp.m3 != R(0)) arg = arg * arg * arg;
+          eab = M::expv(arg);
+          eba = M::expv(-arg);
+        }
+        zeta[a] += fc[b] * g * eab;
+        zeta[b] += fc[a] * g * eba;
+      }
+    }
+  }
+
+  // ---- pair terms -------------------------------------------------------------
+  R dz[MAXNC], Fx[MAXNC], Fy[MAXNC], Fz[MAXNC];
+  R e_i = R(0);
+#pragma unroll
+  for (int a = 0; a < MAXNC; ++a) {
+    dz[a] = Fx[a] = Fy[a] = Fz[a] = R(0);
+    if (a < nc) {
+      const PairP<R> &P = pairs[ONE ? 0 : ti * nt + (meta[a] >> 8)];
+      const R fR = P.A * M::expneg(P.lam1, P.lam1_lo, rr[a]);
+      const R fA = -P.B * M::expneg(P.lam2, P.lam2_lo, rr[a]);
+      R bij, dbij;
+      bond_order<M>(zeta[a], P, bij, dbij);
+      const R pr = fR + bij * fA;
+      e_i += R(0.5) * fc[a] * pr;
+      const R dvdr = R(0.5) * (dfc[a] * pr + fc[a] * (-P.lam1 * fR - bij * P.lam2 * fA));
+      dz[a] = R(0.5) * fc[a] * fA * dbij;
+      Fx[a] = -dvdr * ux[a];
+      Fy[a] = -dvdr * uy[a];
+      Fz[a] = -dvdr * uz[a];
+    }
+  }
+
+  // ---- second K loop: zeta derivatives over unordered pairs -------------------
+  // With P = dV/dzeta_ij fc_k e_jk, Q = dV/dzeta_ik fc_j e_kj, S = (P + Q) g'
+  // (e_jk the lambda3 factor, arg' its exponent's derivative):
+  //   F_j -= S/r_j u_k + (dV/dzeta_ik fc'_j g e_kj - S/r_j cos + (P - Q) g arg') u_j
+  //   F_k -= S/r_k u_j + (dV/dzeta_ij fc'_k g e_jk - S/r_k cos - (P - Q) g arg') u_k
+#pragma unroll
+  for (int a = 0; a < MAXNC; ++a) {
+#pragma unroll
+    for (int b = a + 1; b < MAXNC; ++b) {
+      if (b < nc) {
+        const TripP<R> &Tp = trips[ONE ? 0 : (ti * nt + (meta[a] >> 8)) * nt + (meta[b] >> 8)];
+        const R cost = ux[a] * ux[b] + uy[a] * uy[b] + uz[a] * uz[b];
+        const R u = Tp.h - cost;
+        const R u2 = u * u;
+        const R inv = M::rcp(Tp.d2 + u2);
+        const R g = Tp.gamma + Tp.K * u2 * inv;
+        const R dg = -Tp.G2 * u * inv * inv;
+        R eab = R(1), eba = R(1), darg = R(0);
+        if (Tp.lam3 != R(0)) {
+          const R tt = Tp.lam3 * (rr[a] - rr[b]);
+          R arg = tt;
+          darg = Tp.lam3;
+          if (Tp.m3 != R(0)) {
+            arg = tt * tt * tt;
+            darg = R(3) * Tp.lam3 * tt * tt;
+          }
+          eab = M::expv(arg);
+          eba = M::expv(-arg);
+        }
+        const R Pv = dz[a] * fc[b] * eab;
+        const R Qv = dz[b] * fc[a] * eba;
+        const R S = (Pv + Qv) * dg;
+        const R PQd = (Pv - Qv) * g * darg;
+        const R cj = S * ir[a];
+        const R ck = S * ir[b];
+        const R ca = dz[b] * dfc[a] * g * eba - cj * cost + PQd;
+        const R cb = dz[a] * dfc[b] * g * eab - ck * cost - PQd;
+        Fx[a] -= cj * ux[b] + ca * ux[a];
+        Fy[a] -= cj * uy[b] + ca * uy[a];
+        Fz[a] -= cj * uz[b] + ca * uz[a];
+        Fx[b] -= ck * ux[a] + cb * ux[b];
+        Fy[b] -= ck * uy[a] + cb * uy[b];
+        Fz[b] -= ck * uz[a] + cb * uz[b];
+      }
+    }
+  }
+
+  // ---- outputs ------------------------------------------------------------------
+  R red[7] = {e_i, R(0), R(0), R(0), R(0), R(0), R(0)};
+  if (active && !over) {
+    R fix = R(0), fiy = R(0), fiz = R(0);
+#pragma unroll
+    for (int a = 0; a < MAXNC; ++a) {
+      if (a < nc) {
+        fix -= Fx[a];
+        fiy -= Fy[a];
+        fiz -= Fz[a];
+        V4 c;
+        c.x = Fx[a]; c.y = Fy[a]; c.z = Fz[a]; c.w = R(0);
+        contrib[(size_t)(meta[a] & 0xff) * N + i] = c;
+        if (VFLAG) {
+          const R dx = rr[a] * ux[a], dy = rr[a] * uy[a], dzz = rr[a] * uz[a];
+          red[1] += dx * Fx[a]; red[2] += dy * Fy[a]; red[3] += dzz * Fz[a];
+          red[4] += dx * Fy[a]; red[5] += dx * Fz[a]; red[6] += dy * Fz[a];
+        }
+      }
+    }
+    V4 c;
+    c.x = fix; c.y = fiy; c.z = fiz; c.w = R(0);
+    selfF[i] = c;
+    mask[i] = mb;
+  }
+  if (EFLAG || VFLAG) block_partial<R, T>(red, EFLAG, VFLAG, partial + (size_t)blockIdx.x * 8);
+}
+
+// ============================================================================
+// general kernel: per-thread shared-memory slots, ordered (j,k) loops
+
+constexpr int NRF = 11;   // real fields per slot
+enum { S_UX = 0, S_UY, S_UZ, S_R, S_IR, S_FC, S_DFC, S_DZ, S_FX, S_FY, S_FZ };
+
+template <class R, int MAXNC>
+struct GenCfg {
+  static constexpr int slot_bytes = NRF * (int)sizeof(R) + 4;
+  static constexpr int raw = 98304 / (MAXNC * slot_bytes);
+  static constexpr int threads = raw >= 128 ? 128 : raw >= 64 ? 64 : 32;
+  static constexpr size_t smem_slots = (size_t)threads * MAXNC * slot_bytes;
+};
+
+// Evaluates atoms either all (work == nullptr: atom = global thread index) or the
+// overflow atoms queued by the fast kernel (work/nwork: per fast block, in order;
+// block b of this kernel takes fast blocks b, b + gridDim.x, ...).
+template <class R, int MAXNC, bool EFLAG, bool VFLAG>
+__global__ void __launch_bounds__(GenCfg<R, MAXNC>::threads)
+k_force_gen(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const int *__restrict__ nbr,
+            const int *__restrict__ cnt, Geom geo, const PairP<R> *__restrict__ gpairs,
+            const TripP<R> *__restrict__ gtrips, int nt, typename V4t<R>::type *__restrict__ contrib,
+            typename V4t<R>::type *__restrict__ selfF, unsigned long long *__restrict__ mask,
+            const int *__restrict__ work, const int *__restrict__ nwork, int nfast, double *__restrict__ partial,
+            RunState *rs)
+{
+  using M = typename MathOf<R>::M;
+  using V4 = typename V4t<R>::type;
+  constexpr int T = GenCfg<R, MAXNC>::threads;
   constexpr bool MIXED = sizeof(R) == 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   PairP<R> *pairs = reinterpret_cast<PairP<R> *>(smem_raw);
@@ -97,227 +484,242 @@ k_force(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const int
   __syncthreads();
 
   const int t = threadIdx.x;
-  const int i = blockIdx.x * T + t;
-  const bool active = i < N;
 #define SLOT(f, s) sr[((f) * MAXNC + (s)) * T + t]
 #define META(s) smeta[(s) * T + t]
-
-  int ti = 0, nc = 0;
-  unsigned long long mbits = 0ull;
+  R red[7] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
   bool overflow = false;
-  int4 qi = make_int4(0, 0, 0, 0);
-  dbl4 xi = make_dbl4(0, 0, 0, 0);
-  if (active) {
-    if (MIXED) {
-      qi = q[i];
-      ti = qi.w;
-    } else {
-      xi = x[i];
-      ti = (int)__double_as_longlong(xi.w);
+  int maxnc = 0;
+
+  // the atoms of this thread
+  const int nouter = work ? (nfast + (int)gridDim.x - 1) / (int)gridDim.x : 1;
+  for (int ob = 0; ob < nouter; ++ob) {
+    const int fb = blockIdx.x + ob * gridDim.x;
+    int cntb = 1;
+    if (work) {
+      if (fb >= nfast) break;
+      cntb = nwork[fb];
     }
-    const int n = cnt[i];
-    for (int s = 0; s < n; ++s) {
-      const int j = nbr[(size_t)s * N + i];
-      R dx, dy, dz;
-      int tj;
+    for (int k = t; k < (work ? cntb : T); k += T) {
+      const int i = work ? work[(size_t)fb * FAST_THREADS + k] : (int)blockIdx.x * T + t;
+      if (i >= N) continue;
+      int ti;
+      int4 qi = make_int4(0, 0, 0, 0);
+      dbl4 xi = make_dbl4(0, 0, 0, 0);
       if (MIXED) {
-        int4 qj = q[j];
-        tj = qj.w;
-        dx = (R)(float)qdiff(qj.x, qi.x) * (R)geo.q_to_f[0];
-        dy = (R)(float)qdiff(qj.y, qi.y) * (R)geo.q_to_f[1];
-        dz = (R)(float)qdiff(qj.z, qi.z) * (R)geo.q_to_f[2];
+        qi = q[i];
+        ti = qi.w;
       } else {
-        dbl4 xj = x[j];
-        tj = (int)__double_as_longlong(xj.w);
-        double ddx = xj.x - xi.x, ddy = xj.y - xi.y, ddz = xj.z - xi.z;
-        ddx -= geo.L[0] * rint(ddx * geo.invL[0]);
-        ddy -= geo.L[1] * rint(ddy * geo.invL[1]);
-        ddz -= geo.L[2] * rint(ddz * geo.invL[2]);
-        dx = (R)ddx; dy = (R)ddy; dz = (R)ddz;
+        xi = x[i];
+        ti = (int)__double_as_longlong(xi.w);
       }
-      const R r2 = dx * dx + dy * dy + dz * dz;
-      const PairP<R> &P = pairs[ti * nt + tj];
-      if (r2 < P.rc2) {
-        if (nc < MAXNC) {
-          const R ir = t_rsqrt(r2);
-          const R r = r2 * ir;
-          R fc, dfc;
-          cutoff_fn(r, P, fc, dfc);
-          SLOT(S_UX, nc) = dx * ir;
-          SLOT(S_UY, nc) = dy * ir;
-          SLOT(S_UZ, nc) = dz * ir;
-          SLOT(S_R, nc) = r;
-          SLOT(S_IR, nc) = ir;
-          SLOT(S_FC, nc) = fc;
-          SLOT(S_DFC, nc) = dfc;
-          META(nc) = s | (tj << 8);
+      int nc = 0;
+      unsigned long long mbits = 0ull;
+      const int n = cnt[i];
+      for (int s = 0; s < n; ++s) {
+        const int j = nbr[(size_t)s * N + i];
+        R dx, dy, dz;
+        int tj;
+        if (MIXED) {
+          const int4 qj = q[j];
+          tj = qj.w;
+          dx = (R)(float)qdiff(qj.x, qi.x) * (R)geo.q_to_f[0];
+          dy = (R)(float)qdiff(qj.y, qi.y) * (R)geo.q_to_f[1];
+          dz = (R)(float)qdiff(qj.z, qi.z) * (R)geo.q_to_f[2];
         } else {
-          overflow = true;
+          const dbl4 xj = x[j];
+          tj = (int)__double_as_longlong(xj.w);
+          double ddx = xj.x - xi.x, ddy = xj.y - xi.y, ddz = xj.z - xi.z;
+          ddx -= geo.L[0] * rint(ddx * geo.invL[0]);
+          ddy -= geo.L[1] * rint(ddy * geo.invL[1]);
+          ddz -= geo.L[2] * rint(ddz * geo.invL[2]);
+          dx = (R)ddx; dy = (R)ddy; dz = (R)ddz;
         }
-        ++nc;
-        mbits |= 1ull << s;
-      }
-    }
-    if (overflow) {
-      atomicOr(&rs->status, ST_NC_OVERFLOW);
-      atomicMax(&rs->maxnc, nc);
-      nc = 0;
-    }
-  }
-
-  // ---- pass A: zeta_ij, pair term, dV/dzeta --------------------------------
-  R e_i = R(0);
-  for (int a = 0; a < nc; ++a) {
-    const int tj = META(a) >> 8;
-    const R uax = SLOT(S_UX, a), uay = SLOT(S_UY, a), uaz = SLOT(S_UZ, a), ra = SLOT(S_R, a);
-    const TripP<R> *Tj = trips + (ti * nt + tj) * nt;
-    R zeta = R(0);
-    for (int b = 0; b < nc; ++b) {
-      if (b == a) continue;
-      const TripP<R> &Tp = Tj[META(b) >> 8];
-      const R cost = uax * SLOT(S_UX, b) + uay * SLOT(S_UY, b) + uaz * SLOT(S_UZ, b);
-      const R u = Tp.h - cost;
-      const R u2 = u * u;
-      const R g = Tp.gamma + Tp.K * u2 * t_rcp(Tp.d2 + u2);
-      R ex = R(1);
-      if (Tp.lam3 != R(0)) {
-        R arg = Tp.lam3 * (ra - SLOT(S_R, b));
-        if (Tp.m3 != R(0)) arg = arg * arg * arg;
-        ex = t_exp(arg);
-      }
-      zeta += SLOT(S_FC, b) * g * ex;
-    }
-    const PairP<R> &P = pairs[ti * nt + tj];
-    const R fc = SLOT(S_FC, a), dfc = SLOT(S_DFC, a);
-    const R fR = P.A * t_exp(-P.lam1 * ra);
-    const R fA = -P.B * t_exp(-P.lam2 * ra);
-    R bij = R(1), dbij = R(0);
-    if (zeta > R(0)) {
-      const R xb = t_exp2(P.n * t_log2(P.beta * zeta));
-      bij = t_exp2(P.neg_inv2n * t_log2(R(1) + xb));
-      dbij = R(-0.5) * bij * xb * t_rcp((R(1) + xb) * zeta);
-    }
-    const R pr = fR + bij * fA;
-    e_i += R(0.5) * fc * pr;
-    const R dvdr = R(0.5) * (dfc * pr + fc * (-P.lam1 * fR - bij * P.lam2 * fA));
-    SLOT(S_DZ, a) = R(0.5) * fc * fA * dbij;
-    SLOT(S_FX, a) = -dvdr * uax;
-    SLOT(S_FY, a) = -dvdr * uay;
-    SLOT(S_FZ, a) = -dvdr * uaz;
-  }
-
-  // ---- pass B: zeta derivatives scaled by dV/dzeta ------------------------
-  for (int a = 0; a < nc; ++a) {
-    const R dzv = SLOT(S_DZ, a);
-    if (dzv == R(0)) continue;
-    const int tj = META(a) >> 8;
-    const R uax = SLOT(S_UX, a), uay = SLOT(S_UY, a), uaz = SLOT(S_UZ, a), ra = SLOT(S_R, a), ira = SLOT(S_IR, a);
-    const TripP<R> *Tj = trips + (ti * nt + tj) * nt;
-    R fjx = R(0), fjy = R(0), fjz = R(0);
-    for (int b = 0; b < nc; ++b) {
-      if (b == a) continue;
-      const TripP<R> &Tp = Tj[META(b) >> 8];
-      const R ubx = SLOT(S_UX, b), uby = SLOT(S_UY, b), ubz = SLOT(S_UZ, b), irb = SLOT(S_IR, b);
-      const R cost = uax * ubx + uay * uby + uaz * ubz;
-      const R u = Tp.h - cost;
-      const R u2 = u * u;
-      const R inv = t_rcp(Tp.d2 + u2);
-      const R g = Tp.gamma + Tp.K * u2 * inv;
-      const R dg = -Tp.G2 * u * inv * inv;
-      R ex = R(1), darg = R(0);
-      if (Tp.lam3 != R(0)) {
-        R tt = Tp.lam3 * (ra - SLOT(S_R, b));
-        R arg = tt;
-        darg = Tp.lam3;
-        if (Tp.m3 != R(0)) {
-          arg = tt * tt * tt;
-          darg = R(3) * Tp.lam3 * tt * tt;
+        const R r2 = dx * dx + dy * dy + dz * dz;
+        const PairP<R> &P = pairs[ti * nt + tj];
+        if (r2 < P.rc2) {
+          if (nc < MAXNC) {
+            if (MIXED) {
+              const int4 qj = q[j];
+              dx = (R)qd_fine(qdiff(qj.x, qi.x), geo.q_to_f[0], geo.q_to_f_lo[0]);
+              dy = (R)qd_fine(qdiff(qj.y, qi.y), geo.q_to_f[1], geo.q_to_f_lo[1]);
+              dz = (R)qd_fine(qdiff(qj.z, qi.z), geo.q_to_f[2], geo.q_to_f_lo[2]);
+            }
+            const R rf2 = dx * dx + dy * dy + dz * dz;
+            const R inv = M::rsqrt(rf2);
+            const R r = rf2 * inv;
+            R fcv, dfcv;
+            cutoff_fn<M>(r, P, fcv, dfcv);
+            SLOT(S_UX, nc) = dx * inv;
+            SLOT(S_UY, nc) = dy * inv;
+            SLOT(S_UZ, nc) = dz * inv;
+            SLOT(S_R, nc) = r;
+            SLOT(S_IR, nc) = inv;
+            SLOT(S_FC, nc) = fcv;
+            SLOT(S_DFC, nc) = dfcv;
+            META(nc) = s | (tj << 8);
+          }
+          ++nc;
+          mbits |= 1ull << s;
         }
-        ex = t_exp(arg);
       }
-      const R fcb = SLOT(S_FC, b), dfcb = SLOT(S_DFC, b);
-      const R a1 = fcb * ex * dg;          // coefficient of dcos/dx
-      const R a2 = fcb * ex * g * darg;    // coefficient of dr_ij/dx_j and -dr_ik/dx_k
-      const R a3 = dfcb * g * ex;          // coefficient of dr_ik/dx_k from f_C(r_ik)
-      // dzeta/dx_j = a1 (u_b - cos u_a)/r_a + a2 u_a
-      const R cj = a1 * ira;
-      const R dzjx = cj * (ubx - cost * uax) + a2 * uax;
-      const R dzjy = cj * (uby - cost * uay) + a2 * uay;
-      const R dzjz = cj * (ubz - cost * uaz) + a2 * uaz;
-      // dzeta/dx_k = a3 u_b + a1 (u_a - cos u_b)/r_b - a2 u_b
-      const R ck = a1 * irb;
-      const R dzkx = (a3 - a2) * ubx + ck * (uax - cost * ubx);
-      const R dzky = (a3 - a2) * uby + ck * (uay - cost * uby);
-      const R dzkz = (a3 - a2) * ubz + ck * (uaz - cost * ubz);
-      fjx -= dzv * dzjx;
-      fjy -= dzv * dzjy;
-      fjz -= dzv * dzjz;
-      SLOT(S_FX, b) -= dzv * dzkx;
-      SLOT(S_FY, b) -= dzv * dzky;
-      SLOT(S_FZ, b) -= dzv * dzkz;
-    }
-    SLOT(S_FX, a) += fjx;
-    SLOT(S_FY, a) += fjy;
-    SLOT(S_FZ, a) += fjz;
-  }
+      maxnc = max(maxnc, nc);
+      if (nc > MAXNC) {
+        overflow = true;
+        continue;
+      }
 
-  // ---- outputs --------------------------------------------------------------
-  R fix = R(0), fiy = R(0), fiz = R(0);
-  R w0 = R(0), w1 = R(0), w2 = R(0), w3 = R(0), w4 = R(0), w5 = R(0);
-  for (int a = 0; a < nc; ++a) {
-    const R fx = SLOT(S_FX, a), fy = SLOT(S_FY, a), fz = SLOT(S_FZ, a);
-    fix -= fx;
-    fiy -= fy;
-    fiz -= fz;
-    V4 c;
-    c.x = fx; c.y = fy; c.z = fz; c.w = R(0);
-    contrib[(size_t)(META(a) & 0xff) * N + i] = c;
-    if (VFLAG) {
-      const R r = SLOT(S_R, a);
-      const R dx = r * SLOT(S_UX, a), dy = r * SLOT(S_UY, a), dz = r * SLOT(S_UZ, a);
-      w0 += dx * fx; w1 += dy * fy; w2 += dz * fz;
-      w3 += dx * fy; w4 += dx * fz; w5 += dy * fz;
+      // first K loop and pair terms
+      for (int a = 0; a < nc; ++a) {
+        const int tj = META(a) >> 8;
+        const R uax = SLOT(S_UX, a), uay = SLOT(S_UY, a), uaz = SLOT(S_UZ, a), ra = SLOT(S_R, a);
+        const TripP<R> *Tj = trips + (ti * nt + tj) * nt;
+        R zeta = R(0);
+        for (int b = 0; b < nc; ++b) {
+          if (b == a) continue;
+          const TripP<R> &Tp = Tj[META(b) >> 8];
+          const R cost = uax * SLOT(S_UX, b) + uay * SLOT(S_UY, b) + uaz * SLOT(S_UZ, b);
+          const R u = Tp.h - cost;
+          const R u2 = u * u;
+          const R g = Tp.gamma + Tp.K * u2 * M::rcp(Tp.d2 + u2);
+          R ex = R(1);
+          if (Tp.lam3 != R(0)) {
+            R arg = Tp.lam3 * (ra - SLOT(S_R, b));
+            if (Tp.m3 != R(0)) arg = arg * arg * arg;
+            ex = M::expv(arg);
+          }
+          zeta += SLOT(S_FC, b) * g * ex;
+        }
+        const PairP<R> &P = pairs[ti * nt + tj];
+        const R fcv = SLOT(S_FC, a), dfcv = SLOT(S_DFC, a);
+        const R fR = P.A * M::expneg(P.lam1, P.lam1_lo, ra);
+        const R fA = -P.B * M::expneg(P.lam2, P.lam2_lo, ra);
+        R bij, dbij;
+        bond_order<M>(zeta, P, bij, dbij);
+        const R pr = fR + bij * fA;
+        red[0] += R(0.5) * fcv * pr;
+        const R dvdr = R(0.5) * (dfcv * pr + fcv * (-P.lam1 * fR - bij * P.lam2 * fA));
+        SLOT(S_DZ, a) = R(0.5) * fcv * fA * dbij;
+        SLOT(S_FX, a) = -dvdr * uax;
+        SLOT(S_FY, a) = -dvdr * uay;
+        SLOT(S_FZ, a) = -dvdr * uaz;
+      }
+
+      // second K loop
+      for (int a = 0; a < nc; ++a) {
+        const R dzv = SLOT(S_DZ, a);
+        if (dzv == R(0)) continue;
+        const int tj = META(a) >> 8;
+        const R uax = SLOT(S_UX, a), uay = SLOT(S_UY, a), uaz = SLOT(S_UZ, a), ra = SLOT(S_R, a),
+                ira = SLOT(S_IR, a);
+        const TripP<R> *Tj = trips + (ti * nt + tj) * nt;
+        R fjx = R(0), fjy = R(0), fjz = R(0);
+        for (int b = 0; b < nc; ++b) {
+          if (b == a) continue;
+          const TripP<R> &Tp = Tj[META(b) >> 8];
+          const R ubx = SLOT(S_UX, b), uby = SLOT(S_UY, b), ubz = SLOT(S_UZ, b), irb = SLOT(S_IR, b);
+          const R cost = uax * ubx + uay * uby + uaz * ubz;
+          const R u = Tp.h - cost;
+          const R u2 = u * u;
+          const R inv = M::rcp(Tp.d2 + u2);
+          const R g = Tp.gamma + Tp.K * u2 * inv;
+          const R dg = -Tp.G2 * u * inv * inv;
+          R ex = R(1), darg = R(0);
+          if (Tp.lam3 != R(0)) {
+            const R tt = Tp.lam3 * (ra - SLOT(S_R, b));
+            R arg = tt;
+            darg = Tp.lam3;
+            if (Tp.m3 != R(0)) {
+              arg = tt * tt * tt;
+              darg = R(3) * Tp.lam3 * tt * tt;
+            }
+            ex = M::expv(arg);
+          }
+          const R fcb = SLOT(S_FC, b), dfcb = SLOT(S_DFC, b);
+          const R a1 = fcb * ex * dg;
+          const R a2 = fcb * ex * g * darg;
+          const R a3 = dfcb * g * ex;
+          const R cj = a1 * ira;
+          const R dzjx = cj * (ubx - cost * uax) + a2 * uax;
+          const R dzjy = cj * (uby - cost * uay) + a2 * uay;
+          const R dzjz = cj * (ubz - cost * uaz) + a2 * uaz;
+          const R ck = a1 * irb;
+          const R dzkx = (a3 - a2) * ubx + ck * (uax - cost * ubx);
+          const R dzky = (a3 - a2) * uby + ck * (uay - cost * uby);
+          const R dzkz = (a3 - a2) * ubz + ck * (uaz - cost * ubz);
+          fjx -= dzv * dzjx;
+          fjy -= dzv * dzjy;
+          fjz -= dzv * dzjz;
+          SLOT(S_FX, b) -= dzv * dzkx;
+          SLOT(S_FY, b) -= dzv * dzky;
+          SLOT(S_FZ, b) -= dzv * dzkz;
+        }
+        SLOT(S_FX, a) += fjx;
+        SLOT(S_FY, a) += fjy;
+        SLOT(S_FZ, a) += fjz;
+      }
+
+      R fix = R(0), fiy = R(0), fiz = R(0);
+      for (int a = 0; a < nc; ++a) {
+        const R fx = SLOT(S_FX, a), fy = SLOT(S_FY, a), fz = SLOT(S_FZ, a);
+        fix -= fx;
+        fiy -= fy;
+        fiz -= fz;
+        V4 c;
+        c.x = fx; c.y = fy; c.z = fz; c.w = R(0);
+        contrib[(size_t)(META(a) & 0xff) * N + i] = c;
+        if (VFLAG) {
+          const R r = SLOT(S_R, a);
+          const R dx = r * SLOT(S_UX, a), dy = r * SLOT(S_UY, a), dz = r * SLOT(S_UZ, a);
+          red[1] += dx * fx; red[2] += dy * fy; red[3] += dz * fz;
+          red[4] += dx * fy; red[5] += dx * fz; red[6] += dy * fz;
+        }
+      }
+      V4 c;
+      c.x = fix; c.y = fiy; c.z = fiz; c.w = R(0);
+      selfF[i] = c;
+      mask[i] = mbits;
     }
   }
-  if (active) {
-    V4 c;
-    c.x = fix; c.y = fiy; c.z = fiz; c.w = R(0);
-    selfF[i] = c;
-    mask[i] = mbits;
-  }
-  if (EFLAG) {
-    // float32 sums over the 32 atoms of a warp, then float64 across warps
-    R e = warp_sum(e_i);
-    if ((t & 31) == 0) atomicAdd(&rs->epot, (double)e);
-  }
-  if (VFLAG) {
-    R w[6] = {w0, w1, w2, w3, w4, w5};
-#pragma unroll
-    for (int c = 0; c < 6; ++c) {
-      R v = warp_sum(w[c]);
-      if ((t & 31) == 0) atomicAdd(&rs->virial[c], (double)v);
-    }
-  }
-  {
-    int m = nc;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((t & 31) == 0) atomicMax(&rs->maxnc, m);
-  }
+  if (overflow) atomicOr(&rs->status, ST_NC_OVERFLOW);
+  if (maxnc > 0) atomicMax(&rs->maxnc, maxnc);
+  if (EFLAG || VFLAG) block_partial<R, T>(red, EFLAG, VFLAG, partial + (size_t)blockIdx.x * 8);
 #undef SLOT
 #undef META
 }
 
-// ---- host-side launch ------------------------------------------------------
-template <class R, int MAXNC, bool EFLAG, bool VFLAG>
-static cudaError_t launch_force_t(cudaStream_t st, int N, const dbl4 *x, const int4 *q, const int *nbr,
-                                  const int *cnt, const Geom &geo, const void *pairs, const void *trips, int nt,
-                                  void *contrib, void *selfF, unsigned long long *mask, RunState *rs)
+// Sum n partial rows of (E, W[6]) in a fixed order into rs->epot / rs->virial.
+__global__ void k_reduce_partials(const double *__restrict__ partial, int n, RunState *rs)
 {
-  using C = ForceCfg<R, MAXNC>;
+  __shared__ double sh[256][7];
+  if (rs->status != 0) return;
+  double a[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int k = threadIdx.x; k < n; k += 256)
+    for (int c = 0; c < 7; ++c) a[c] += partial[(size_t)k * 8 + c];
+  for (int c = 0; c < 7; ++c) sh[threadIdx.x][c] = a[c];
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int c = 0; c < 7; ++c) sh[threadIdx.x][c] += sh[threadIdx.x + w][c];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    rs->epot += sh[0][0];
+    for (int c = 0; c < 6; ++c) rs->virial[c] += sh[0][1 + c];
+  }
+}
+
+// ---- host-side launch ------------------------------------------------------
+
+template <class R, int MAXNC, bool EFLAG, bool VFLAG>
+static cudaError_t launch_gen_t(cudaStream_t st, int N, const dbl4 *x, const int4 *q, const int *nbr, const int *cnt,
+                                const Geom &geo, const void *pairs, const void *trips, int nt, void *contrib,
+                                void *selfF, unsigned long long *mask, const int *work, const int *nwork, int nfast,
+                                int gen_blocks, double *partial, RunState *rs)
+{
+  using C = GenCfg<R, MAXNC>;
   const size_t smem = sizeof(PairP<R>) * MAX_TYPES * MAX_TYPES + sizeof(TripP<R>) * MAX_TYPES * MAX_TYPES * MAX_TYPES +
                       C::smem_slots;
-  auto kern = k_force<R, MAXNC, EFLAG, VFLAG>;
+  auto kern = k_force_gen<R, MAXNC, EFLAG, VFLAG>;
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -325,27 +727,83 @@ static cudaError_t launch_force_t(cudaStream_t st, int N, const dbl4 *x, const i
     attr_set = true;
   }
   if (N == 0) return cudaSuccess;
-  const int blocks = (N + C::threads - 1) / C::threads;
+  const int blocks = work ? gen_blocks : (N + C::threads - 1) / C::threads;
   kern<<<blocks, C::threads, smem, st>>>(N, x, q, nbr, cnt, geo, (const PairP<R> *)pairs, (const TripP<R> *)trips,
                                          nt, (typename V4t<R>::type *)contrib, (typename V4t<R>::type *)selfF, mask,
-                                         rs);
+                                         work, nwork, nfast, partial, rs);
   return cudaGetLastError();
 }
 
 template <class R, int MAXNC>
-static cudaError_t launch_force_nc(cudaStream_t st, int eflag, int vflag, int N, const dbl4 *x, const int4 *q,
-                                   const int *nbr, const int *cnt, const Geom &geo, const void *pairs,
-                                   const void *trips, int nt, void *contrib, void *selfF, unsigned long long *mask,
-                                   RunState *rs)
+static cudaError_t launch_gen(cudaStream_t st, int eflag, int vflag, int N, const dbl4 *x, const int4 *q,
+                              const int *nbr, const int *cnt, const Geom &geo, const void *pairs, const void *trips,
+                              int nt, void *contrib, void *selfF, unsigned long long *mask, const int *work,
+                              const int *nwork, int nfast, int gen_blocks, double *partial, RunState *rs)
 {
   if (vflag)
-    return launch_force_t<R, MAXNC, true, true>(st, N, x, q, nbr, cnt, geo, pairs, trips, nt, contrib, selfF, mask, rs);
+    return launch_gen_t<R, MAXNC, true, true>(st, N, x, q, nbr, cnt, geo, pairs, trips, nt, contrib, selfF, mask, work,
+                                              nwork, nfast, gen_blocks, partial, rs);
   if (eflag)
-    return launch_force_t<R, MAXNC, true, false>(st, N, x, q, nbr, cnt, geo, pairs, trips, nt, contrib, selfF, mask, rs);
-  return launch_force_t<R, MAXNC, false, false>(st, N, x, q, nbr, cnt, geo, pairs, trips, nt, contrib, selfF, mask, rs);
+    return launch_gen_t<R, MAXNC, true, false>(st, N, x, q, nbr, cnt, geo, pairs, trips, nt, contrib, selfF, mask,
+                                               work, nwork, nfast, gen_blocks, partial, rs);
+  return launch_gen_t<R, MAXNC, false, false>(st, N, x, q, nbr, cnt, geo, pairs, trips, nt, contrib, selfF, mask,
+                                              work, nwork, nfast, gen_blocks, partial, rs);
 }
 
-// Smallest compiled slot count >= need (8, 16, 32 or 64).
+template <class R>
+static int gen_threads(int slots)
+{
+  switch (slots) {
+    case 8: return GenCfg<R, 8>::threads;
+    case 16: return GenCfg<R, 16>::threads;
+    case 32: return GenCfg<R, 32>::threads;
+    default: return GenCfg<R, 64>::threads;
+  }
+}
+
+template <class R>
+static cudaError_t launch_gen_any(cudaStream_t st, int slots, int eflag, int vflag, int N, const dbl4 *x,
+                                  const int4 *q, const int *nbr, const int *cnt, const Geom &geo, const void *pairs,
+                                  const void *trips, int nt, void *contrib, void *selfF, unsigned long long *mask,
+                                  const int *work, const int *nwork, int nfast, int gen_blocks, double *partial,
+                                  RunState *rs)
+{
+#define TSF_GEN(NC)                                                                                                \
+  case NC:                                                                                                         \
+    return launch_gen<R, NC>(st, eflag, vflag, N, x, q, nbr, cnt, geo, pairs, trips, nt, contrib, selfF, mask, work, \
+                             nwork, nfast, gen_blocks, partial, rs);
+  switch (slots) {
+    TSF_GEN(8)
+    TSF_GEN(16)
+    TSF_GEN(32)
+    TSF_GEN(64)
+  }
+#undef TSF_GEN
+  return cudaErrorInvalidValue;
+}
+
+template <class R, int MAXNC, bool ONE>
+static cudaError_t launch_reg(cudaStream_t st, int eflag, int vflag, int N, const dbl4 *x, const int4 *q,
+                              const int *nbr, const int *cnt, const Geom &geo, const void *pairs, const void *trips,
+                              int nt, void *contrib, void *selfF, unsigned long long *mask, int *work, int *nwork,
+                              double *partial, RunState *rs)
+{
+  const int blocks = (N + FAST_THREADS - 1) / FAST_THREADS;
+  using P = const PairP<R> *;
+  using Tt = const TripP<R> *;
+  using V = typename V4t<R>::type *;
+  if (vflag)
+    k_force_reg<R, MAXNC, ONE, true, true><<<blocks, FAST_THREADS, 0, st>>>(
+        N, x, q, nbr, cnt, geo, (P)pairs, (Tt)trips, nt, (V)contrib, (V)selfF, mask, work, nwork, partial, rs);
+  else if (eflag)
+    k_force_reg<R, MAXNC, ONE, true, false><<<blocks, FAST_THREADS, 0, st>>>(
+        N, x, q, nbr, cnt, geo, (P)pairs, (Tt)trips, nt, (V)contrib, (V)selfF, mask, work, nwork, partial, rs);
+  else
+    k_force_reg<R, MAXNC, ONE, false, false><<<blocks, FAST_THREADS, 0, st>>>(
+        N, x, q, nbr, cnt, geo, (P)pairs, (Tt)trips, nt, (V)contrib, (V)selfF, mask, work, nwork, partial, rs);
+  return cudaGetLastError();
+}
+
 int force_slots_for(int need)
 {
   if (need <= 8) return 8;
@@ -354,25 +812,58 @@ int force_slots_for(int need)
   return 64;
 }
 
-cudaError_t launch_force(cudaStream_t st, bool mixed, int maxnc, int eflag, int vflag, int N, const dbl4 *x,
-                         const int4 *q, const int *nbr, const int *cnt, const Geom &geo, const void *pairs,
-                         const void *trips, int nt, void *contrib, void *selfF, unsigned long long *mask,
-                         RunState *rs)
+int force_gen_blocks() { return 2 * 152; }
+
+// Rows of 8 doubles the partial-sum buffer needs for N atoms (any launch shape).
+int force_partial_rows(int N) { return (N + 31) / 32 + force_gen_blocks(); }
+
+// One force evaluation.  fast_slots 4 or 8 runs the register kernel plus the
+// general kernel (gen_slots wide) over its overflow queue; fast_slots 0 runs the
+// general kernel over all atoms.  Buffers: partial force_partial_rows(N) x 8
+// doubles; work N ints; nwork ceil(N/128) ints.  With eflag/vflag the energy and
+// virial are added to rs->epot / rs->virial.
+cudaError_t launch_force(cudaStream_t st, bool mixed, int fast_slots, bool one_type, int gen_slots, int eflag,
+                         int vflag, int N, const dbl4 *x, const int4 *q, const int *nbr, const int *cnt,
+                         const Geom &geo, const void *pairs, const void *trips, int nt, void *contrib, void *selfF,
+                         unsigned long long *mask, int *work, int *nwork, double *partial, RunState *rs)
 {
-#define TSF_CASE(NC)                                                                                          \
-  case NC:                                                                                                    \
-    return mixed ? launch_force_nc<float, NC>(st, eflag, vflag, N, x, q, nbr, cnt, geo, pairs, trips, nt, contrib, \
-                                              selfF, mask, rs)                                                \
-                 : launch_force_nc<double, NC>(st, eflag, vflag, N, x, q, nbr, cnt, geo, pairs, trips, nt,     \
-                                               contrib, selfF, mask, rs);
-  switch (force_slots_for(maxnc)) {
-    TSF_CASE(8)
-    TSF_CASE(16)
-    TSF_CASE(32)
-    TSF_CASE(64)
+  if (N == 0) return cudaSuccess;
+  const int nfast = (N + FAST_THREADS - 1) / FAST_THREADS;
+  cudaError_t e = cudaSuccess;
+  int rows = 0;
+  if (fast_slots > 0) {
+#define TSF_REG(R, NC)                                                                                              \
+  e = one_type ? launch_reg<R, NC, true>(st, eflag, vflag, N, x, q, nbr, cnt, geo, pairs, trips, nt, contrib, selfF, \
+                                         mask, work, nwork, partial, rs)                                            \
+               : launch_reg<R, NC, false>(st, eflag, vflag, N, x, q, nbr, cnt, geo, pairs, trips, nt, contrib,      \
+                                          selfF, mask, work, nwork, partial, rs);
+    if (mixed) {
+      if (fast_slots <= 4) { TSF_REG(float, 4) } else { TSF_REG(float, 8) }
+    } else {
+      if (fast_slots <= 4) { TSF_REG(double, 4) } else { TSF_REG(double, 8) }
+    }
+#undef TSF_REG
+    if (e != cudaSuccess) return e;
+    double *gp = partial + (size_t)nfast * 8;
+    e = mixed ? launch_gen_any<float>(st, gen_slots, eflag, vflag, N, x, q, nbr, cnt, geo, pairs, trips, nt, contrib,
+                                      selfF, mask, work, nwork, nfast, force_gen_blocks(), gp, rs)
+              : launch_gen_any<double>(st, gen_slots, eflag, vflag, N, x, q, nbr, cnt, geo, pairs, trips, nt, contrib,
+                                       selfF, mask, work, nwork, nfast, force_gen_blocks(), gp, rs);
+    rows = nfast + force_gen_blocks();
+  } else {
+    e = mixed ? launch_gen_any<float>(st, gen_slots, eflag, vflag, N, x, q, nbr, cnt, geo, pairs, trips, nt, contrib,
+                                      selfF, mask, nullptr, nullptr, 0, 0, partial, rs)
+              : launch_gen_any<double>(st, gen_slots, eflag, vflag, N, x, q, nbr, cnt, geo, pairs, trips, nt, contrib,
+                                       selfF, mask, nullptr, nullptr, 0, 0, partial, rs);
+    const int T = mixed ? gen_threads<float>(gen_slots) : gen_threads<double>(gen_slots);
+    rows = (N + T - 1) / T;
   }
-#undef TSF_CASE
-  return cudaErrorInvalidValue;
+  if (e != cudaSuccess) return e;
+  if (eflag || vflag) {
+    k_reduce_partials<<<1, 256, 0, st>>>(partial, rows, rs);
+    e = cudaGetLastError();
+  }
+  return e;
 }
 
 }  // namespace tsf

@@ -16,27 +16,72 @@ template <class R> struct V4g;
 template <> struct V4g<float> { using type = float4; };
 template <> struct V4g<double> { using type = dbl4; };
 
+// Knuth's TwoSum: s + e == a + b exactly (float32 round-to-nearest).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+template <class R> struct GatherAcc;
+
+// float32 contributions: compensated (TwoSum) accumulation, a head and tail
+// float per component; the force is head + tail rounded once to float64.  Its
+// error is that of a float64 sum of the same float32 terms, on the float32 pipe.
+template <> struct GatherAcc<float> {
+  float h[3], l[3];
+  __device__ __forceinline__ void init(const float4 &c)
+  {
+    h[0] = c.x; h[1] = c.y; h[2] = c.z;
+    l[0] = l[1] = l[2] = 0.0f;
+  }
+  __device__ __forceinline__ void add(const float4 &c)
+  {
+    float e;
+    two_sum(h[0], c.x, h[0], e); l[0] += e;
+    two_sum(h[1], c.y, h[1], e); l[1] += e;
+    two_sum(h[2], c.z, h[2], e); l[2] += e;
+  }
+  __device__ __forceinline__ void out(double &fx, double &fy, double &fz) const
+  {
+    fx = (double)h[0] + (double)l[0];
+    fy = (double)h[1] + (double)l[1];
+    fz = (double)h[2] + (double)l[2];
+  }
+};
+
+template <> struct GatherAcc<double> {
+  double f[3];
+  __device__ __forceinline__ void init(const dbl4 &c) { f[0] = c.x; f[1] = c.y; f[2] = c.z; }
+  __device__ __forceinline__ void add(const dbl4 &c) { f[0] += c.x; f[1] += c.y; f[2] += c.z; }
+  __device__ __forceinline__ void out(double &fx, double &fy, double &fz) const { fx = f[0]; fy = f[1]; fz = f[2]; }
+};
+
 template <class R>
 __device__ __forceinline__ void gather_force(int m, int N, const typename V4g<R>::type *__restrict__ contrib,
                                              const typename V4g<R>::type *__restrict__ selfF,
                                              const unsigned long long *__restrict__ mask, const int *__restrict__ nbr,
                                              const int *__restrict__ rev, double &fx, double &fy, double &fz)
 {
-  const auto s0 = selfF[m];
-  fx = (double)s0.x;
-  fy = (double)s0.y;
-  fz = (double)s0.z;
+  GatherAcc<R> acc;
+  acc.init(selfF[m]);
   unsigned long long mb = mask[m];
   while (mb) {
     const int s = __ffsll((long long)mb) - 1;
     mb &= mb - 1;
     const int j = nbr[(size_t)s * N + m];
     const int s2 = rev[(size_t)s * N + m];
-    const auto c = contrib[(size_t)s2 * N + j];
-    fx += (double)c.x;
-    fy += (double)c.y;
-    fz += (double)c.z;
+    acc.add(contrib[(size_t)s2 * N + j]);
   }
+  acc.out(fx, fy, fz);
+}
+
+// round(x * to_q) mod 2^32 with one rounding: adding 1.5 * 2^52 inside the FMA puts
+// the nearest integer in the low mantissa bits (valid for |x * to_q| < 2^51).
+__device__ __forceinline__ int fixed_q(double x, double to_q)
+{
+  return __double2loint(fma(x, to_q, 6755399441055744.0));
 }
 
 __device__ __forceinline__ double warp_sum_d(double v)
@@ -64,12 +109,12 @@ __global__ void k_ingest(int N, const double *__restrict__ pos, const int *__res
   int qq[3];
   for (int a = 0; a < 3; ++a) {
     double v = pos[3 * (size_t)i + a];
-    if (!isfinite(v) || fabs(v * geo.invL[a]) > 1e6) {
+    if (!isfinite(v) || fabs(v * geo.invL[a]) > 1e5) {
       atomicOr(&rs->status, ST_NONFINITE);
       v = 0.0;
     }
     p[a] = v;
-    qq[a] = (int)(unsigned)(unsigned long long)__double2ll_rn(v * geo.to_q[a]);
+    qq[a] = fixed_q(v, geo.to_q[a]);
   }
   x[i] = make_dbl4(p[0], p[1], p[2], __longlong_as_double((long long)t));
   q[i] = make_int4(qq[0], qq[1], qq[2], t);
@@ -113,8 +158,10 @@ __global__ void k_vv(int N, int mode, dbl4 *__restrict__ x, dbl4 *__restrict__ v
                      const int4 *__restrict__ qref, const typename V4g<R>::type *__restrict__ contrib,
                      const typename V4g<R>::type *__restrict__ selfF, const unsigned long long *__restrict__ mask,
                      const int *__restrict__ nbr, const int *__restrict__ rev, const double *__restrict__ kick,
-                     const double *__restrict__ mass, double dt, Geom geo, float disp2_lim, RunState *rs)
+                     const double *__restrict__ mass, double dt, Geom geo, float disp2_lim, double *__restrict__ kepart,
+                     RunState *rs)
 {
+  __shared__ double sw[8];
   if (rs->status != 0) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   bool active = i < N;
@@ -142,9 +189,9 @@ __global__ void k_vv(int N, int mode, dbl4 *__restrict__ x, dbl4 *__restrict__ v
       xi.y = fma(dt, vi.y, xi.y);
       xi.z = fma(dt, vi.z, xi.z);
       x[i] = xi;
-      qi.x = (int)(unsigned)(unsigned long long)__double2ll_rn(xi.x * geo.to_q[0]);
-      qi.y = (int)(unsigned)(unsigned long long)__double2ll_rn(xi.y * geo.to_q[1]);
-      qi.z = (int)(unsigned)(unsigned long long)__double2ll_rn(xi.z * geo.to_q[2]);
+      qi.x = fixed_q(xi.x, geo.to_q[0]);
+      qi.y = fixed_q(xi.y, geo.to_q[1]);
+      qi.z = fixed_q(xi.z, geo.to_q[2]);
       q[i] = qi;
       const int4 qr = qref[i];
       const float dx = (float)qdiff(qi.x, qr.x) * geo.q_to_f[0];
@@ -156,9 +203,31 @@ __global__ void k_vv(int N, int mode, dbl4 *__restrict__ x, dbl4 *__restrict__ v
   }
   if (__any_sync(0xffffffffu, moved) && (threadIdx.x & 31) == 0) atomicOr(&rs->rebuild, 1);
   if (KE) {
+    // per-block partial in a fixed order; k_ke_reduce adds the blocks in order
     double s = warp_sum_d(ke);
-    if ((threadIdx.x & 31) == 0) atomicAdd(&rs->ekin2, s);
+    if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double a = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += sw[w];
+      kepart[blockIdx.x] = a;
+    }
   }
+}
+
+__global__ void k_ke_reduce(const double *__restrict__ kepart, int n, RunState *rs)
+{
+  __shared__ double sh[256];
+  if (rs->status != 0) return;
+  double a = 0.0;
+  for (int k = threadIdx.x; k < n; k += 256) a += kepart[k];
+  sh[threadIdx.x] = a;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) rs->ekin2 += sh[0];
 }
 
 // AoS copies out of the device state
@@ -217,27 +286,31 @@ __global__ void k_force_done(RunState *rs)
 cudaError_t launch_vv(cudaStream_t st, bool mixed, bool ke, int N, int mode, dbl4 *x, dbl4 *v, int4 *q,
                       const int4 *qref, const void *contrib, const void *selfF, const unsigned long long *mask,
                       const int *nbr, const int *rev, const double *kick, const double *mass, double dt,
-                      const Geom &geo, float disp2_lim, RunState *rs)
+                      const Geom &geo, float disp2_lim, double *kepart, RunState *rs)
 {
   if (N == 0) return cudaSuccess;
   const int T = 256, B = (N + T - 1) / T;
   if (mixed) {
     if (ke)
       k_vv<float, true><<<B, T, 0, st>>>(N, mode, x, v, q, qref, (const float4 *)contrib, (const float4 *)selfF,
-                                         mask, nbr, rev, kick, mass, dt, geo, disp2_lim, rs);
+                                         mask, nbr, rev, kick, mass, dt, geo, disp2_lim, kepart, rs);
     else
       k_vv<float, false><<<B, T, 0, st>>>(N, mode, x, v, q, qref, (const float4 *)contrib, (const float4 *)selfF,
-                                          mask, nbr, rev, kick, mass, dt, geo, disp2_lim, rs);
+                                          mask, nbr, rev, kick, mass, dt, geo, disp2_lim, kepart, rs);
   } else {
     if (ke)
       k_vv<double, true><<<B, T, 0, st>>>(N, mode, x, v, q, qref, (const dbl4 *)contrib, (const dbl4 *)selfF,
-                                          mask, nbr, rev, kick, mass, dt, geo, disp2_lim, rs);
+                                          mask, nbr, rev, kick, mass, dt, geo, disp2_lim, kepart, rs);
     else
       k_vv<double, false><<<B, T, 0, st>>>(N, mode, x, v, q, qref, (const dbl4 *)contrib,
-                                           (const dbl4 *)selfF, mask, nbr, rev, kick, mass, dt, geo, disp2_lim, rs);
+                                           (const dbl4 *)selfF, mask, nbr, rev, kick, mass, dt, geo, disp2_lim,
+                                           kepart, rs);
   }
+  if (ke) k_ke_reduce<<<1, 256, 0, st>>>(kepart, B, rs);
   return cudaGetLastError();
 }
+
+int vv_blocks(int N) { return (N + 255) / 256; }
 
 cudaError_t launch_gather_out(cudaStream_t st, bool mixed, int N, const void *contrib, const void *selfF,
                               const unsigned long long *mask, const int *nbr, const int *rev, double *out,

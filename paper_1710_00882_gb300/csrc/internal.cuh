@@ -31,6 +31,7 @@ enum : int {
 template <class R>
 struct PairP {
   R A, lam1, B, lam2;     // f_R = A e^{-lam1 r}, f_A = -B e^{-lam2 r}
+  R lam1_lo, lam2_lo;     // float32 tables: lam - (float)lam, so that lam r is formed to ~1 ulp
   R beta, n, neg_inv2n;   // b = (1 + (beta zeta)^n)^(-1/(2n))
   R Rc, Dc;               // cutoff centre and half width
   R r_in, r_out, rc2;     // R - D, R + D, (R + D)^2
@@ -53,6 +54,7 @@ struct Geom {
   double to_q[3];     // 2^32 / L
   double q_to_d[3];   // L / 2^32
   float q_to_f[3];    // L / 2^32 rounded to float
+  float q_to_f_lo[3]; // L / 2^32 - q_to_f (the rounding error of q_to_f)
 };
 
 // Device-resident run bookkeeping (one per MD state / computation).
@@ -67,6 +69,9 @@ struct RunState {
   double ekin2;          // sum m v^2 accumulator (integrator), amu A^2/ps^2
   double virial[6];
   double epot_last;      // potential energy of the last completed step
+  int nfast_blocks;      // blocks of the last force launch (partials to reduce)
+  int ngen_blocks;       // blocks of the overflow kernel
+  int nvv_blocks;        // blocks of the last integrator launch with kinetic energy
   double *trace;         // device trace [..][2] or null
   long long trace_k;     // next trace row
 };

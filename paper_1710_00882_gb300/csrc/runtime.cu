@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -23,12 +24,14 @@ cudaError_t launch_build(cudaStream_t, int, const int4 *, const CellGrid &, cons
                          int *, int *, int *, int *, int *, int, int4 *, RunState *, int);
 int scan_tiles_for(int ncell);
 int force_slots_for(int need);
-cudaError_t launch_force(cudaStream_t, bool, int, int, int, int, const dbl4 *, const int4 *, const int *,
+int force_partial_rows(int N);
+int vv_blocks(int N);
+cudaError_t launch_force(cudaStream_t, bool, int, bool, int, int, int, int, const dbl4 *, const int4 *, const int *,
                          const int *, const Geom &, const void *, const void *, int, void *, void *,
-                         unsigned long long *, RunState *);
+                         unsigned long long *, int *, int *, double *, RunState *);
 cudaError_t launch_vv(cudaStream_t, bool, bool, int, int, dbl4 *, dbl4 *, int4 *, const int4 *, const void *,
                       const void *, const unsigned long long *, const int *, const int *, const double *,
-                      const double *, double, const Geom &, float, RunState *);
+                      const double *, double, const Geom &, float, double *, RunState *);
 cudaError_t launch_gather_out(cudaStream_t, bool, int, const void *, const void *, const unsigned long long *,
                               const int *, const int *, double *, RunState *);
 cudaError_t launch_ingest(cudaStream_t, int, const double *, const int *, int, const Geom &, dbl4 *, int4 *,
@@ -79,6 +82,7 @@ Geom make_geom(const double box[3])
     g.to_q[a] = 4294967296.0 / box[a];
     g.q_to_d[a] = box[a] / 4294967296.0;
     g.q_to_f[a] = (float)(box[a] / 4294967296.0);
+    g.q_to_f_lo[a] = (float)(box[a] / 4294967296.0 - (double)g.q_to_f[a]);
   }
   return g;
 }
@@ -117,6 +121,7 @@ struct tersoff_ctx {
   RunState *crs = nullptr; // run state of tersoff_compute
   void *stage = nullptr;   // host-pointer staging (AoS positions/forces, types)
   size_t stage_bytes = 0;
+  bool general_only = false;  // TERSOFF_FORCE_KERNEL=general: skip the register force kernel
 };
 
 struct tersoff_params {
@@ -126,6 +131,7 @@ struct tersoff_params {
   double rcmax = 0;
   void *pair_f = nullptr, *trip_f = nullptr, *pair_d = nullptr, *trip_d = nullptr;
   double *d_mass = nullptr;
+  bool sym_angular = false;   // rows (i,j,k) and (i,k,j) share their angular constants
 };
 
 struct tersoff_nlist {
@@ -150,7 +156,8 @@ struct tersoff_md {
   bool pe_valid = false;        // rs->epot_last holds the potential energy of the current positions
   long long steps_done = 0;     // host count of completed steps
   long long steps_target = 0;   // host count of enqueued steps
-  int slots = 8;
+  int fast_slots = 8;   // register force kernel slots (4 or 8; 0 = general kernel only)
+  int gen_slots = 8;    // general force kernel slots
   // phase profiling: event pairs per phase, reused across reads
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -226,6 +233,7 @@ void free_atoms(AtomState &A)
 {
   dfree(A.x); dfree(A.v); dfree(A.q);
   dfree(A.contrib); dfree(A.selfF); dfree(A.mask);
+  dfree(A.work); dfree(A.nwork); dfree(A.partial); dfree(A.kepart);
   A = AtomState();
 }
 
@@ -251,8 +259,12 @@ int ensure_scatter(tersoff_ctx *ctx, AtomState &A, int64_t N, int cap, bool mixe
 {
   size_t v4 = mixed ? sizeof(float4) : sizeof(dbl4);
   size_t n = (size_t)std::max<int64_t>(N, 1);
+  const size_t nfast = (n + 127) / 128;
   if (!dreserve(A.contrib, A.contrib_b, n * (size_t)cap * v4) || !dreserve(A.selfF, A.selfF_b, n * v4) ||
-      !dreserve(A.mask, A.mask_b, n * sizeof(unsigned long long)))
+      !dreserve(A.mask, A.mask_b, n * sizeof(unsigned long long)) ||
+      !dreserve(A.work, A.work_b, nfast * 128 * sizeof(int)) || !dreserve(A.nwork, A.nwork_b, nfast * sizeof(int)) ||
+      !dreserve(A.partial, A.partial_b, (size_t)force_partial_rows((int)n) * 8 * sizeof(double)) ||
+      !dreserve(A.kepart, A.kepart_b, (size_t)vv_blocks((int)n) * sizeof(double)))
     return set_err(ctx, TERSOFF_ERR_NOMEM, "cannot allocate force scatter buffers (N=%lld, cap=%d)", (long long)N,
                    cap);
   return TERSOFF_OK;
@@ -387,6 +399,10 @@ int tersoff_ctx_create(int device, void *stream, tersoff_ctx **out)
   tersoff_ctx *ctx = new (std::nothrow) tersoff_ctx();
   if (!ctx) return TERSOFF_ERR_NOMEM;
   ctx->device = device;
+  {
+    const char *fk = getenv("TERSOFF_FORCE_KERNEL");
+    ctx->general_only = fk && strcmp(fk, "general") == 0;
+  }
   if (stream) {
     ctx->stream = (cudaStream_t)stream;
   } else {
@@ -459,6 +475,16 @@ int tersoff_params_create(tersoff_ctx *ctx, int ntypes, const double *entries, c
   if (!P) return TERSOFF_ERR_NOMEM;
   P->nt = nt;
   P->entries.assign(entries, entries + (size_t)nrow * NFIELDS);
+  // the register force kernel evaluates g(theta) once per unordered neighbour pair:
+  // allowed when rows (i,j,k) and (i,k,j) carry the same angular constants
+  P->sym_angular = true;
+  for (int a = 0; a < nt; ++a)
+    for (int b = 0; b < nt; ++b)
+      for (int c = 0; c < nt; ++c) {
+        const double *t1 = row(a, b, c), *t2 = row(a, c, b);
+        for (int f : {F_M, F_GAMMA, F_LAM3, F_C, F_D, F_H})
+          if (t1[f] != t2[f]) P->sym_angular = false;
+      }
   for (int a = 0; a < nt; ++a) P->masses[a] = masses_amu[a];
   std::vector<PairP<float>> pf(nt * nt);
   std::vector<PairP<double>> pd(nt * nt);
@@ -470,6 +496,7 @@ int tersoff_params_create(tersoff_ctx *ctx, int ntypes, const double *entries, c
       const double *p = row(a, b, b);
       PairP<double> d;
       d.A = p[F_A]; d.lam1 = p[F_LAM1]; d.B = p[F_B]; d.lam2 = p[F_LAM2];
+      d.lam1_lo = 0.0; d.lam2_lo = 0.0;
       d.beta = p[F_BETA]; d.n = p[F_N]; d.neg_inv2n = -1.0 / (2.0 * p[F_N]);
       d.Rc = p[F_R]; d.Dc = p[F_DD];
       d.r_in = p[F_R] - p[F_DD]; d.r_out = p[F_R] + p[F_DD]; d.rc2 = d.r_out * d.r_out;
@@ -478,6 +505,8 @@ int tersoff_params_create(tersoff_ctx *ctx, int ntypes, const double *entries, c
       pd[a * nt + b] = d;
       PairP<float> f;
       f.A = (float)d.A; f.lam1 = (float)d.lam1; f.B = (float)d.B; f.lam2 = (float)d.lam2;
+      f.lam1_lo = (float)(d.lam1 - (double)f.lam1);
+      f.lam2_lo = (float)(d.lam2 - (double)f.lam2);
       f.beta = (float)d.beta; f.n = (float)d.n; f.neg_inv2n = (float)d.neg_inv2n;
       f.Rc = (float)d.Rc; f.Dc = (float)d.Dc; f.r_in = (float)d.r_in; f.r_out = (float)d.r_out;
       // float cutoff test must not admit a pair the float64 test rejects: use the float below r_out^2
@@ -644,10 +673,11 @@ int tersoff_compute(tersoff_ctx *ctx, const double *pos, const int32_t *types, i
       if (nl->list.geo.L[a] != box[a]) return set_err(ctx, TERSOFF_ERR_ARG, "list built for another box");
   }
   CKR(ensure_scatter(ctx, A, N, L->cap, mixed));
-  const int slots = force_slots_for(std::max(1, L->maxcount));
-  CK(launch_force(ctx->stream, mixed, slots, 1, virial != nullptr, (int)N, A.x, A.q, L->nbr, L->cnt, A.geo,
-                  mixed ? P->pair_f : P->pair_d, mixed ? P->trip_f : P->trip_d, P->nt, A.contrib, A.selfF, A.mask,
-                  rs));
+  const int gen_slots = force_slots_for(std::max(1, L->maxcount));
+  const int fast_slots = (P->sym_angular && !ctx->general_only) ? (L->maxcount <= 4 ? 4 : 8) : 0;
+  CK(launch_force(ctx->stream, mixed, fast_slots, P->nt == 1, gen_slots, 1, virial != nullptr, (int)N, A.x, A.q,
+                  L->nbr, L->cnt, A.geo, mixed ? P->pair_f : P->pair_d, mixed ? P->trip_f : P->trip_d, P->nt,
+                  A.contrib, A.selfF, A.mask, A.work, A.nwork, A.partial, rs));
   double *dF = nullptr;
   if (forces) {
     if (dev) {
@@ -713,10 +743,10 @@ static int md_force(tersoff_md *md, int eflag)
 {
   tersoff_ctx *ctx = md->ctx;
   const tersoff_params *P = md->params;
-  CK(launch_force(ctx->stream, md->mixed, md->slots, eflag, 0, (int)md->atoms.N, md->atoms.x, md->atoms.q,
-                  md->list.nbr, md->list.cnt, md->atoms.geo, md->mixed ? P->pair_f : P->pair_d,
-                  md->mixed ? P->trip_f : P->trip_d, P->nt, md->atoms.contrib, md->atoms.selfF, md->atoms.mask,
-                  md->rs));
+  CK(launch_force(ctx->stream, md->mixed, md->fast_slots, P->nt == 1, md->gen_slots, eflag, 0, (int)md->atoms.N,
+                  md->atoms.x, md->atoms.q, md->list.nbr, md->list.cnt, md->atoms.geo,
+                  md->mixed ? P->pair_f : P->pair_d, md->mixed ? P->trip_f : P->trip_d, P->nt, md->atoms.contrib,
+                  md->atoms.selfF, md->atoms.mask, md->atoms.work, md->atoms.nwork, md->atoms.partial, md->rs));
   return TERSOFF_OK;
 }
 
@@ -726,7 +756,7 @@ static int md_vv(tersoff_md *md, int mode, bool ke)
   const float lim = (float)(0.25 * md->skin * md->skin);
   CK(launch_vv(ctx->stream, md->mixed, ke, (int)md->atoms.N, mode, md->atoms.x, md->atoms.v, md->atoms.q,
                md->list.qref, md->atoms.contrib, md->atoms.selfF, md->atoms.mask, md->list.nbr, md->list.rev,
-               md->d_kick, md->params->d_mass, md->dt, md->atoms.geo, lim, md->rs));
+               md->d_kick, md->params->d_mass, md->dt, md->atoms.geo, lim, md->atoms.kepart, md->rs));
   return TERSOFF_OK;
 }
 
@@ -782,7 +812,7 @@ static int md_recover(tersoff_md *md, const RunState &h, long long call_base, lo
     CK(cudaMemcpyAsync(&md->rs->rebuild, &one, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
     CKR(md_build_gated(md));
   } else if (h.status & ST_NC_OVERFLOW) {
-    md->slots = force_slots_for(h.maxnc);
+    md->gen_slots = force_slots_for(h.maxnc);
     CK(cudaMemsetAsync(&md->rs->status, 0, sizeof(int), ctx->stream));
   } else {
     return status_to_code(ctx, h.status, h);
@@ -862,14 +892,16 @@ int tersoff_md_create(tersoff_ctx *ctx, const double *pos, const double *vel, co
   cudaMemcpy(md->d_kick, kick, sizeof kick, cudaMemcpyHostToDevice);
   if ((rc = build_list_sync(ctx, md->atoms, md->list, md->rs, box, P->rcmax, skin)) != TERSOFF_OK) return fail(rc);
   if ((rc = ensure_scatter(ctx, md->atoms, N, md->list.cap, md->mixed)) != TERSOFF_OK) return fail(rc);
-  md->slots = force_slots_for(std::max(1, md->list.maxcount));
+  md->gen_slots = force_slots_for(std::max(1, md->list.maxcount));
+  md->fast_slots = (P->sym_angular && !ctx->general_only) ? 8 : 0;
   if ((rc = md_force(md, 1)) != TERSOFF_OK) return fail(rc);
   if (launch_force_done(ctx->stream, md->rs) != cudaSuccess) return fail(set_err(ctx, TERSOFF_ERR_CUDA, "force_done"));
   RunState h;
   if ((rc = read_rs(ctx, md->rs, &h)) != TERSOFF_OK) return fail(rc);
   if (h.status != 0) return fail(status_to_code(ctx, h.status, h));
-  // size the force kernel's slots to the observed in-cutoff count plus headroom
-  md->slots = force_slots_for(std::min(std::max(1, md->list.maxcount), h.maxnc + 2));
+  // register kernel with 4 slots when no atom has more than 4 in-cutoff neighbours
+  // (diamond-like solids), else 8; atoms beyond that go to the general kernel
+  if (md->fast_slots > 0 && h.maxnc <= 4) md->fast_slots = 4;
   md->steps_done = md->steps_target = 0;
   md->pe_valid = true;
   CK(cudaMemsetAsync(&md->rs->step, 0, sizeof(long long), ctx->stream));

@@ -17,7 +17,12 @@ struct AtomState {
   void *contrib = nullptr;          // [cap][N] float4/dbl4 force contributions (force kernel -> gather)
   void *selfF = nullptr;            // [N] force of each atom's own terms on itself
   unsigned long long *mask = nullptr;  // [N] in-cutoff list slots
-  size_t x_b = 0, v_b = 0, q_b = 0, contrib_b = 0, selfF_b = 0, mask_b = 0;
+  int *work = nullptr;              // [ceil(N/128)*128] overflow atoms of the register force kernel
+  int *nwork = nullptr;             // [ceil(N/128)] overflow count per block
+  double *partial = nullptr;        // per-block (E, W[6]) partial sums
+  double *kepart = nullptr;         // per-block kinetic-energy partial sums
+  size_t x_b = 0, v_b = 0, q_b = 0, contrib_b = 0, selfF_b = 0, mask_b = 0, work_b = 0, nwork_b = 0, partial_b = 0,
+         kepart_b = 0;
 };
 
 // Device arrays of one neighbour list and its cell grid.

@@ -33,4 +33,5 @@ def assert_parity(E, F, W, Eo, Fo, Wo, e_rel, f_abs, w_abs_per_atom, what=""):
     assert err <= f_abs, f"{what} force max-abs err {err:.3e}"
     if W is not None and Wo is not None:
         werr = np.abs(np.asarray(W) - np.asarray(Wo)).max()
-        assert werr <= w_abs_per_atom * max(1, len(F)), f"{what} virial err {werr:.3e}: {W} vs {Wo}"
+        wtol = max(w_abs_per_atom * max(1, len(F)), e_rel * np.abs(Wo).max())
+        assert werr <= wtol, f"{what} virial err {werr:.3e}: {W} vs {Wo}"
