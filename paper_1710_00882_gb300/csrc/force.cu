@@ -83,11 +83,11 @@ struct MathF {
     const float yl = fmaf(xh, L2E_F, -yh) + fmaf(xh, L2E_F_LO, xl * L2E_F);
     return ex2(-yh) * fmaf(-yl, 0.69314718f, 1.0f);
   }
-  // e^{-(lh + ll) r}, lambda given as float hi + lo
-  static __device__ __forceinline__ float expneg(float lh, float ll, float r)
+  // e^{-(lh + ll)(rh + rl)}: lambda and r both given as float head + tail
+  static __device__ __forceinline__ float expneg(float lh, float ll, float rh, float rl)
   {
-    const float p = lh * r;
-    const float pe = fmaf(lh, r, -p) + ll * r;
+    const float p = lh * rh;
+    const float pe = fmaf(lh, rh, -p) + fmaf(ll, rh, lh * rl);
     return expneg2(p, pe);
   }
   static __device__ __forceinline__ float expv(float x) { return expneg2(-x, 0.0f); }
@@ -100,7 +100,7 @@ struct MathD {
   static __device__ __forceinline__ double rsqrt(double x) { return ::rsqrt(x); }
   static __device__ __forceinline__ double lg2(double x) { return ::log2(x); }
   static __device__ __forceinline__ double ex2(double x) { return ::exp2(x); }
-  static __device__ __forceinline__ double expneg(double lh, double, double r) { return ::exp(-lh * r); }
+  static __device__ __forceinline__ double expneg(double lh, double, double r, double) { return ::exp(-lh * r); }
   static __device__ __forceinline__ double expv(double x) { return ::exp(x); }
   static __device__ __forceinline__ void sincospi(double t, double *s, double *c) { ::sincospi(t, s, c); }
 };
@@ -109,16 +109,16 @@ template <class R> struct MathOf;
 template <> struct MathOf<float> { using M = MathF; };
 template <> struct MathOf<double> { using M = MathD; };
 
-// f_C and f_C' for r < R + D
+// f_C and f_C' for r = rh + rl < R + D
 template <class M, class R>
-__device__ __forceinline__ void cutoff_fn(R r, const PairP<R> &P, R &fc, R &dfc)
+__device__ __forceinline__ void cutoff_fn(R rh, R rl, const PairP<R> &P, R &fc, R &dfc)
 {
-  if (r <= P.r_in) {
+  if (rh <= P.r_in) {
     fc = R(1);
     dfc = R(0);
   } else {
     R s, c;
-    M::sincospi((r - P.Rc) * P.inv2D, &s, &c);
+    M::sincospi(((rh - P.Rc) + rl) * P.inv2D, &s, &c);
     fc = R(0.5) - R(0.5) * s;
     dfc = P.dfc_scale * c;
   }
@@ -140,13 +140,38 @@ __device__ __forceinline__ void bond_order(R zeta, const PairP<R> &P, R &b, R &d
 // minimum-image relative vector of a fixed-point pair, accurate to ~1 ulp:
 // the int32 difference is split into a 24-bit head and an 8-bit tail (both exact in
 // float) and the scale into float head + tail.
-__device__ __forceinline__ float qd_fine(int dq, float sh, float sl)
+__device__ __forceinline__ void qd_fine(int dq, float sh, float sl, float &dh, float &dl)
 {
   const float h = (float)(dq & ~0xff);
   const float l = (float)(dq & 0xff);
   const float p = h * sh;
-  const float pe = fmaf(h, sh, -p);
-  return p + fmaf(h, sl, fmaf(l, sh, pe));
+  const float t = fmaf(h, sl, fmaf(l, sh, fmaf(h, sh, -p)));
+  dh = p + t;
+  dl = t - (dh - p);   // |p| >= |t|: exact tail
+}
+
+// r = |d| as head + tail from d given as head + tail per component: squares split
+// exactly with FMAs, summed with TwoSum, square root refined by one Newton step.
+// Returns rh (the rounded distance), rl (its tail) and 1/rh.
+__device__ __forceinline__ void norm_fine(const float (&dh)[3], const float (&dl)[3], float &rh, float &rl,
+                                          float &irh)
+{
+  float sq[3], er[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    sq[a] = dh[a] * dh[a];
+    er[a] = fmaf(dh[a], dh[a], -sq[a]) + 2.0f * dh[a] * dl[a];
+  }
+  const float s1 = sq[0] + sq[1];
+  const float bb1 = s1 - sq[0];
+  const float e1 = (sq[0] - (s1 - bb1)) + (sq[1] - bb1);
+  const float s2 = s1 + sq[2];
+  const float bb2 = s2 - s1;
+  const float e2 = (s1 - (s2 - bb2)) + (sq[2] - bb2);
+  const float r2l = e1 + e2 + er[0] + er[1] + er[2];
+  irh = MathF::rsqrt(s2);
+  rh = s2 * irh;
+  rl = (fmaf(-rh, rh, s2) + r2l) * 0.5f * irh;
 }
 
 template <class R> __device__ __forceinline__ R warp_sum(R v)
@@ -272,7 +297,7 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
   }
 
   // ---- slots ---------------------------------------------------------------
-  R ux[MAXNC], uy[MAXNC], uz[MAXNC], rr[MAXNC], ir[MAXNC], fc[MAXNC], dfc[MAXNC];
+  R ux[MAXNC], uy[MAXNC], uz[MAXNC], rr[MAXNC], rl[MAXNC], ir[MAXNC], fc[MAXNC], dfc[MAXNC];
   int meta[MAXNC];
   {
     unsigned long long rem = over ? 0ull : mb;
@@ -280,20 +305,25 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
     for (int s = 0; s < MAXNC; ++s) {
       ux[s] = uy[s] = uz[s] = R(0);
       rr[s] = ir[s] = R(1);
-      fc[s] = dfc[s] = R(0);
+      rl[s] = fc[s] = dfc[s] = R(0);
       meta[s] = 0;
       if (s < nc) {
         const int e = __ffsll((long long)rem) - 1;
         rem &= rem - 1;
         const int j = nbr[(size_t)e * N + i];
-        R dx, dy, dz;
+        R dx, dy, dz, r, rlo, inv;
         int tj;
         if (MIXED) {
           const int4 qj = q[j];
           tj = qj.w;
-          dx = (R)qd_fine(qdiff(qj.x, qi.x), geo.q_to_f[0], geo.q_to_f_lo[0]);
-          dy = (R)qd_fine(qdiff(qj.y, qi.y), geo.q_to_f[1], geo.q_to_f_lo[1]);
-          dz = (R)qd_fine(qdiff(qj.z, qi.z), geo.q_to_f[2], geo.q_to_f_lo[2]);
+          float dh[3], dl[3];
+          qd_fine(qdiff(qj.x, qi.x), geo.q_to_f[0], geo.q_to_f_lo[0], dh[0], dl[0]);
+          qd_fine(qdiff(qj.y, qi.y), geo.q_to_f[1], geo.q_to_f_lo[1], dh[1], dl[1]);
+          qd_fine(qdiff(qj.z, qi.z), geo.q_to_f[2], geo.q_to_f_lo[2], dh[2], dl[2]);
+          float rh_, rl_, irh_;
+          norm_fine(dh, dl, rh_, rl_, irh_);
+          dx = (R)dh[0]; dy = (R)dh[1]; dz = (R)dh[2];
+          r = (R)rh_; rlo = (R)rl_; inv = (R)irh_;
         } else {
           const dbl4 xj = x[j];
           tj = (int)__double_as_longlong(xj.w);
@@ -302,16 +332,18 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
           ddy -= geo.L[1] * rint(ddy * geo.invL[1]);
           ddz -= geo.L[2] * rint(ddz * geo.invL[2]);
           dx = (R)ddx; dy = (R)ddy; dz = (R)ddz;
+          const R r2 = dx * dx + dy * dy + dz * dz;
+          inv = M::rsqrt(r2);
+          r = r2 * inv;
+          rlo = R(0);
         }
-        const R r2 = dx * dx + dy * dy + dz * dz;
-        const R inv = M::rsqrt(r2);
-        const R r = r2 * inv;
         ux[s] = dx * inv;
         uy[s] = dy * inv;
         uz[s] = dz * inv;
         rr[s] = r;
+        rl[s] = rlo;
         ir[s] = inv;
-        cutoff_fn<M>(r, pairs[ONE ? 0 : ti * nt + tj], fc[s], dfc[s]);
+        cutoff_fn<M>(r, rlo, pairs[ONE ? 0 : ti * nt + tj], fc[s], dfc[s]);
         meta[s] = e | (tj << 8);
       }
     }
@@ -352,8 +384,8 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
     dz[a] = Fx[a] = Fy[a] = Fz[a] = R(0);
     if (a < nc) {
       const PairP<R> &P = pairs[ONE ? 0 : ti * nt + (meta[a] >> 8)];
-      const R fR = P.A * M::expneg(P.lam1, P.lam1_lo, rr[a]);
-      const R fA = -P.B * M::expneg(P.lam2, P.lam2_lo, rr[a]);
+      const R fR = P.A * M::expneg(P.lam1, P.lam1_lo, rr[a], rl[a]);
+      const R fA = -P.B * M::expneg(P.lam2, P.lam2_lo, rr[a], rl[a]);
       R bij, dbij;
       bond_order<M>(zeta[a], P, bij, dbij);
       const R pr = fR + bij * fA;
@@ -444,8 +476,8 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
 // ============================================================================
 // general kernel: per-thread shared-memory slots, ordered (j,k) loops
 
-constexpr int NRF = 11;   // real fields per slot
-enum { S_UX = 0, S_UY, S_UZ, S_R, S_IR, S_FC, S_DFC, S_DZ, S_FX, S_FY, S_FZ };
+constexpr int NRF = 12;   // real fields per slot
+enum { S_UX = 0, S_UY, S_UZ, S_R, S_IR, S_FC, S_DFC, S_DZ, S_FX, S_FY, S_FZ, S_RL };
 
 template <class R, int MAXNC>
 struct GenCfg {
@@ -538,21 +570,30 @@ k_force_gen(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
         const PairP<R> &P = pairs[ti * nt + tj];
         if (r2 < P.rc2) {
           if (nc < MAXNC) {
+            R r, rlo, inv;
             if (MIXED) {
               const int4 qj = q[j];
-              dx = (R)qd_fine(qdiff(qj.x, qi.x), geo.q_to_f[0], geo.q_to_f_lo[0]);
-              dy = (R)qd_fine(qdiff(qj.y, qi.y), geo.q_to_f[1], geo.q_to_f_lo[1]);
-              dz = (R)qd_fine(qdiff(qj.z, qi.z), geo.q_to_f[2], geo.q_to_f_lo[2]);
+              float dh[3], dl[3];
+              qd_fine(qdiff(qj.x, qi.x), geo.q_to_f[0], geo.q_to_f_lo[0], dh[0], dl[0]);
+              qd_fine(qdiff(qj.y, qi.y), geo.q_to_f[1], geo.q_to_f_lo[1], dh[1], dl[1]);
+              qd_fine(qdiff(qj.z, qi.z), geo.q_to_f[2], geo.q_to_f_lo[2], dh[2], dl[2]);
+              float rh_, rl_, irh_;
+              norm_fine(dh, dl, rh_, rl_, irh_);
+              dx = (R)dh[0]; dy = (R)dh[1]; dz = (R)dh[2];
+              r = (R)rh_; rlo = (R)rl_; inv = (R)irh_;
+            } else {
+              const R rf2 = dx * dx + dy * dy + dz * dz;
+              inv = M::rsqrt(rf2);
+              r = rf2 * inv;
+              rlo = R(0);
             }
-            const R rf2 = dx * dx + dy * dy + dz * dz;
-            const R inv = M::rsqrt(rf2);
-            const R r = rf2 * inv;
             R fcv, dfcv;
-            cutoff_fn<M>(r, P, fcv, dfcv);
+            cutoff_fn<M>(r, rlo, P, fcv, dfcv);
             SLOT(S_UX, nc) = dx * inv;
             SLOT(S_UY, nc) = dy * inv;
             SLOT(S_UZ, nc) = dz * inv;
             SLOT(S_R, nc) = r;
+            SLOT(S_RL, nc) = rlo;
             SLOT(S_IR, nc) = inv;
             SLOT(S_FC, nc) = fcv;
             SLOT(S_DFC, nc) = dfcv;
@@ -591,8 +632,8 @@ k_force_gen(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
         }
         const PairP<R> &P = pairs[ti * nt + tj];
         const R fcv = SLOT(S_FC, a), dfcv = SLOT(S_DFC, a);
-        const R fR = P.A * M::expneg(P.lam1, P.lam1_lo, ra);
-        const R fA = -P.B * M::expneg(P.lam2, P.lam2_lo, ra);
+        const R fR = P.A * M::expneg(P.lam1, P.lam1_lo, ra, SLOT(S_RL, a));
+        const R fA = -P.B * M::expneg(P.lam2, P.lam2_lo, ra, SLOT(S_RL, a));
         R bij, dbij;
         bond_order<M>(zeta, P, bij, dbij);
         const R pr = fR + bij * fA;
