@@ -163,6 +163,7 @@ __global__ void k_vv(int N, int mode, dbl4 *__restrict__ x, dbl4 *__restrict__ v
 {
   __shared__ double sw[8];
   if (rs->status != 0) return;
+  if (mode < 0) mode = rs->open ? (VV_FINISH | VV_START) : VV_START;   // uniform across the grid
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   bool active = i < N;
   double ke = 0.0;
@@ -250,10 +251,17 @@ __global__ void k_extract(int N, const dbl4 *__restrict__ x, const dbl4 *__restr
   }
 }
 
-// End of an MD step: record (PE_k, KE_{k-1}) in the trace, roll the accumulators.
-__global__ void k_step_end(RunState *rs, double *trace, long long k)
+// End of an MD step: record (PE_k, KE_{k-1}) in the trace (row k = rs->trace_k),
+// roll the accumulators, count the step; inside a graph, decide whether the step
+// loop goes on.
+__global__ void k_step_end(RunState *rs, cudaGraphConditionalHandle loop, int use_cond)
 {
-  if (rs->status != 0) return;
+  if (rs->status != 0) {
+    if (use_cond) cudaGraphSetConditional(loop, 0);
+    return;
+  }
+  const long long k = rs->trace_k;
+  double *trace = rs->trace;
   if (trace) {
     if (k == 1) trace[0] = rs->epot_last;
     trace[2 * k] = rs->epot;
@@ -264,14 +272,40 @@ __global__ void k_step_end(RunState *rs, double *trace, long long k)
   rs->ekin2 = 0.0;
   for (int c = 0; c < 6; ++c) rs->virial[c] = 0.0;
   rs->step += 1;
+  rs->trace_k = k + 1;
+  rs->open = 1;
+  rs->steps_left -= 1;
+  if (use_cond) cudaGraphSetConditional(loop, rs->steps_left > 0 ? 1u : 0u);
 }
 
-// after the closing half kick: KE of the last step
-__global__ void k_final(RunState *rs, double *trace, long long n)
+// before the step loop of a graph launch
+__global__ void k_loop_begin(RunState *rs, cudaGraphConditionalHandle loop)
+{
+  cudaGraphSetConditional(loop, (rs->status == 0 && rs->steps_left > 0) ? 1u : 0u);
+}
+
+// after the integrator of a step: rebuild the list in this step?
+__global__ void k_decide(RunState *rs, cudaGraphConditionalHandle build)
+{
+  cudaGraphSetConditional(build, (rs->status == 0 && rs->rebuild != 0) ? 1u : 0u);
+}
+
+// host-chosen controls of the next launch
+__global__ void k_set_control(RunState *rs, long long steps, double *trace, long long trace_k, int open)
+{
+  rs->steps_left = steps;
+  rs->trace = trace;
+  rs->trace_k = trace_k;
+  rs->open = open;
+}
+
+// after the closing half kick: KE of the last step (row trace_k - 1)
+__global__ void k_final(RunState *rs)
 {
   if (rs->status != 0) return;
-  if (trace) trace[2 * n + 1] = 0.5 * rs->ekin2 / ACCEL;
+  if (rs->trace) rs->trace[2 * (rs->trace_k - 1) + 1] = 0.5 * rs->ekin2 / ACCEL;
   rs->ekin2 = 0.0;
+  rs->open = 0;
 }
 
 // after a standalone force evaluation: keep its energy as the current PE
@@ -352,15 +386,34 @@ cudaError_t launch_extract(cudaStream_t st, int N, const dbl4 *x, const dbl4 *v,
   return cudaGetLastError();
 }
 
-cudaError_t launch_step_end(cudaStream_t st, RunState *rs, double *trace, long long k)
+cudaError_t launch_step_end(cudaStream_t st, RunState *rs, cudaGraphConditionalHandle loop, int use_cond)
 {
-  k_step_end<<<1, 1, 0, st>>>(rs, trace, k);
+  k_step_end<<<1, 1, 0, st>>>(rs, loop, use_cond);
   return cudaGetLastError();
 }
 
-cudaError_t launch_final(cudaStream_t st, RunState *rs, double *trace, long long n)
+cudaError_t launch_loop_begin(cudaStream_t st, RunState *rs, cudaGraphConditionalHandle loop)
 {
-  k_final<<<1, 1, 0, st>>>(rs, trace, n);
+  k_loop_begin<<<1, 1, 0, st>>>(rs, loop);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_decide(cudaStream_t st, RunState *rs, cudaGraphConditionalHandle build)
+{
+  k_decide<<<1, 1, 0, st>>>(rs, build);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_control(cudaStream_t st, RunState *rs, long long steps, double *trace, long long trace_k,
+                               int open)
+{
+  k_set_control<<<1, 1, 0, st>>>(rs, steps, trace, trace_k, open);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_final(cudaStream_t st, RunState *rs)
+{
+  k_final<<<1, 1, 0, st>>>(rs);
   return cudaGetLastError();
 }
 

@@ -73,7 +73,9 @@ struct RunState {
   int ngen_blocks;       // blocks of the overflow kernel
   int nvv_blocks;        // blocks of the last integrator launch with kinetic energy
   double *trace;         // device trace [..][2] or null
-  long long trace_k;     // next trace row
+  long long trace_k;     // trace row of the step in progress (1-based within a call)
+  long long steps_left;  // steps still to run in the current graph launch
+  int open;              // velocities at the half step (a closing kick is pending)
 };
 
 // minimum-image difference of two fixed-point coordinates, in units of L / 2^32

@@ -38,8 +38,11 @@ cudaError_t launch_ingest(cudaStream_t, int, const double *, const int *, int, c
                           RunState *);
 cudaError_t launch_ingest_vel(cudaStream_t, int, const double *, dbl4 *);
 cudaError_t launch_extract(cudaStream_t, int, const dbl4 *, const dbl4 *, double *, double *);
-cudaError_t launch_step_end(cudaStream_t, RunState *, double *, long long);
-cudaError_t launch_final(cudaStream_t, RunState *, double *, long long);
+cudaError_t launch_step_end(cudaStream_t, RunState *, cudaGraphConditionalHandle, int);
+cudaError_t launch_loop_begin(cudaStream_t, RunState *, cudaGraphConditionalHandle);
+cudaError_t launch_decide(cudaStream_t, RunState *, cudaGraphConditionalHandle);
+cudaError_t launch_set_control(cudaStream_t, RunState *, long long, double *, long long, int);
+cudaError_t launch_final(cudaStream_t, RunState *);
 cudaError_t launch_force_done(cudaStream_t, RunState *);
 
 // ---------------------------------------------------------------------------
@@ -141,8 +144,18 @@ struct tersoff_nlist {
   RunState *rs = nullptr;
 };
 
+struct MdGraph {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool valid = false;
+};
+
 struct tersoff_md {
   tersoff_ctx *ctx = nullptr;
+  cudaStream_t cap_stream = nullptr;   // stream used only to capture the step graphs
+  MdGraph graph[2];                    // step loop without / with energy trace
+  bool use_graphs = true;
+  bool pending = false;                // async steps launched and not yet checked
   const tersoff_params *params = nullptr;
   AtomState atoms;
   ListState list;
@@ -739,99 +752,194 @@ static void md_mark_end(tersoff_md *md, int phase, size_t begin, int nlaunch)
   }
 }
 
-static int md_force(tersoff_md *md, int eflag)
+static int md_force(tersoff_md *md, cudaStream_t st, int eflag)
 {
   tersoff_ctx *ctx = md->ctx;
   const tersoff_params *P = md->params;
-  CK(launch_force(ctx->stream, md->mixed, md->fast_slots, P->nt == 1, md->gen_slots, eflag, 0, (int)md->atoms.N,
-                  md->atoms.x, md->atoms.q, md->list.nbr, md->list.cnt, md->atoms.geo,
-                  md->mixed ? P->pair_f : P->pair_d, md->mixed ? P->trip_f : P->trip_d, P->nt, md->atoms.contrib,
-                  md->atoms.selfF, md->atoms.mask, md->atoms.work, md->atoms.nwork, md->atoms.partial, md->rs));
+  CK(launch_force(st, md->mixed, md->fast_slots, P->nt == 1, md->gen_slots, eflag, 0, (int)md->atoms.N, md->atoms.x,
+                  md->atoms.q, md->list.nbr, md->list.cnt, md->atoms.geo, md->mixed ? P->pair_f : P->pair_d,
+                  md->mixed ? P->trip_f : P->trip_d, P->nt, md->atoms.contrib, md->atoms.selfF, md->atoms.mask,
+                  md->atoms.work, md->atoms.nwork, md->atoms.partial, md->rs));
   return TERSOFF_OK;
 }
 
-static int md_vv(tersoff_md *md, int mode, bool ke)
+// mode: VV_FINISH (1), VV_START (2), both (3), 0 (kinetic energy only) or -1 (from rs->open)
+static int md_vv(tersoff_md *md, cudaStream_t st, int mode, bool ke)
 {
   tersoff_ctx *ctx = md->ctx;
   const float lim = (float)(0.25 * md->skin * md->skin);
-  CK(launch_vv(ctx->stream, md->mixed, ke, (int)md->atoms.N, mode, md->atoms.x, md->atoms.v, md->atoms.q,
-               md->list.qref, md->atoms.contrib, md->atoms.selfF, md->atoms.mask, md->list.nbr, md->list.rev,
-               md->d_kick, md->params->d_mass, md->dt, md->atoms.geo, lim, md->atoms.kepart, md->rs));
+  CK(launch_vv(st, md->mixed, ke, (int)md->atoms.N, mode, md->atoms.x, md->atoms.v, md->atoms.q, md->list.qref,
+               md->atoms.contrib, md->atoms.selfF, md->atoms.mask, md->list.nbr, md->list.rev, md->d_kick,
+               md->params->d_mass, md->dt, md->atoms.geo, lim, md->atoms.kepart, md->rs));
   return TERSOFF_OK;
 }
 
-static int md_build_gated(tersoff_md *md)
+static int md_build(tersoff_md *md, cudaStream_t st, int gated)
 {
   tersoff_ctx *ctx = md->ctx;
   ListState &L = md->list;
-  CK(launch_build(ctx->stream, (int)md->atoms.N, md->atoms.q, L.grid, L.geo, L.cell_count, L.cell_start, L.tile_sums,
-                  L.cell_atoms, L.cell_of, L.rank, L.nbr, L.rev, L.cnt, L.cap, L.qref, md->rs, 1));
+  CK(launch_build(st, (int)md->atoms.N, md->atoms.q, L.grid, L.geo, L.cell_count, L.cell_start, L.tile_sums,
+                  L.cell_atoms, L.cell_of, L.rank, L.nbr, L.rev, L.cnt, L.cap, L.qref, md->rs, gated));
   return TERSOFF_OK;
 }
 
-// enqueue steps k0..k1 (1-based within the current call's trace numbering)
-static int md_enqueue(tersoff_md *md, long long k0, long long k1, double *d_trace, bool first_open_done)
+static void md_graphs_free(tersoff_md *md)
+{
+  for (auto &G : md->graph) {
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+    if (G.g) cudaGraphDestroy(G.g);
+    G = MdGraph();
+  }
+}
+
+// Graph of the step loop (which = 1: with energy trace):
+//   loop_begin -> WHILE(steps_left > 0) { vv -> decide -> IF(rebuild) { list build } -> force -> step_end }
+// step_end decrements steps_left and sets the loop condition, so one launch runs any
+// number of steps, and a step without a rebuild launches no build kernel.
+static int md_graph_build(tersoff_md *md, int which)
 {
   tersoff_ctx *ctx = md->ctx;
+  const bool tr = which == 1;
+  MdGraph &G = md->graph[which];
+  cudaStream_t st = md->cap_stream;
+  const cudaStreamCaptureMode mode = cudaStreamCaptureModeRelaxed;
+  cudaGraph_t g = nullptr;
+  CK(cudaGraphCreate(&g, 0));
+  G.g = g;
+  cudaGraphConditionalHandle hloop, hbuild;
+  CK(cudaGraphConditionalHandleCreate(&hloop, g, 0, cudaGraphCondAssignDefault));
+  CK(cudaStreamBeginCaptureToGraph(st, g, nullptr, nullptr, 0, mode));
+  CK(launch_loop_begin(st, md->rs, hloop));
+  cudaStreamCaptureStatus cs;
+  const cudaGraphNode_t *deps = nullptr;
+  const cudaGraphEdgeData *edges = nullptr;
+  size_t nd = 0;
+  CK(cudaStreamGetCaptureInfo(st, &cs, nullptr, nullptr, &deps, &edges, &nd));
+  cudaGraphNodeParams wp = {};
+  wp.type = cudaGraphNodeTypeConditional;
+  wp.conditional.handle = hloop;
+  wp.conditional.type = cudaGraphCondTypeWhile;
+  wp.conditional.size = 1;
+  cudaGraphNode_t wnode;
+  CK(cudaGraphAddNode(&wnode, g, deps, edges, nd, &wp));
+  CK(cudaStreamUpdateCaptureDependencies(st, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+  CK(cudaStreamEndCapture(st, &g));
+  cudaGraph_t body = wp.conditional.phGraph_out[0];
+
+  CK(cudaGraphConditionalHandleCreate(&hbuild, body, 0, cudaGraphCondAssignDefault));
+  CK(cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, mode));
+  CKR(md_vv(md, st, -1, tr));
+  CK(launch_decide(st, md->rs, hbuild));
+  CK(cudaStreamGetCaptureInfo(st, &cs, nullptr, nullptr, &deps, &edges, &nd));
+  cudaGraphNodeParams ip = {};
+  ip.type = cudaGraphNodeTypeConditional;
+  ip.conditional.handle = hbuild;
+  ip.conditional.type = cudaGraphCondTypeIf;
+  ip.conditional.size = 1;
+  cudaGraphNode_t inode;
+  CK(cudaGraphAddNode(&inode, body, deps, edges, nd, &ip));
+  CK(cudaStreamUpdateCaptureDependencies(st, &inode, nullptr, 1, cudaStreamSetCaptureDependencies));
+  CKR(md_force(md, st, tr ? 1 : 0));
+  CK(launch_step_end(st, md->rs, hloop, 1));
+  cudaGraph_t bodyc = body;
+  CK(cudaStreamEndCapture(st, &bodyc));
+
+  cudaGraph_t ifbody = ip.conditional.phGraph_out[0];
+  CK(cudaStreamBeginCaptureToGraph(st, ifbody, nullptr, nullptr, 0, mode));
+  CKR(md_build(md, st, 0));
+  cudaGraph_t ifc = ifbody;
+  CK(cudaStreamEndCapture(st, &ifc));
+
+  CK(cudaGraphInstantiate(&G.exec, g, 0));
+  G.valid = true;
+  return TERSOFF_OK;
+}
+
+// Enqueue n steps on the context stream: one graph launch, or, when profiling,
+// kernel by kernel with events around each phase.  trace rows start at k0.
+static int md_launch_steps(tersoff_md *md, long long n, double *d_trace, long long k0)
+{
+  tersoff_ctx *ctx = md->ctx;
+  cudaStream_t st = ctx->stream;
+  if (n <= 0) return TERSOFF_OK;
   const bool tr = d_trace != nullptr;
-  for (long long k = k0; k <= k1; ++k) {
-    const int mode = (k == k0 && !first_open_done) ? (md->open ? (1 | 2) : 2) : (1 | 2);
+  CK(launch_set_control(st, md->rs, n, d_trace, k0, md->open ? 1 : 0));
+  if (!md->prof && md->use_graphs) {
+    MdGraph &G = md->graph[tr ? 1 : 0];
+    if (!G.valid) {
+      int rc = md_graph_build(md, tr ? 1 : 0);
+      if (rc != TERSOFF_OK) {
+        // fall back to kernel-by-kernel launches for this state
+        cudaGetLastError();
+        md_graphs_free(md);
+        md->use_graphs = false;
+      }
+    }
+    if (md->use_graphs) {
+      CK(cudaGraphLaunch(G.exec, st));
+      md->launches[0] += n;
+      md->open = true;
+      return TERSOFF_OK;
+    }
+  }
+  for (long long k = 0; k < n; ++k) {
     size_t b = md_mark_begin(md);
-    CKR(md_vv(md, mode, tr));
+    CKR(md_vv(md, st, -1, tr));
     md_mark_end(md, 0, b, 1);
-    md->open = true;
     b = md_mark_begin(md);
-    CKR(md_build_gated(md));
+    CKR(md_build(md, st, 1));
     md_mark_end(md, 1, b, 8);
     b = md_mark_begin(md);
-    CKR(md_force(md, tr ? 1 : 0));
-    md_mark_end(md, 2, b, 1);
+    CKR(md_force(md, st, tr ? 1 : 0));
+    md_mark_end(md, 2, b, 2 + (tr ? 1 : 0));
     b = md_mark_begin(md);
-    CK(launch_step_end(ctx->stream, md->rs, d_trace, k));
+    CK(launch_step_end(st, md->rs, 0, 0));
     md_mark_end(md, 3, b, 1);
   }
+  md->open = true;
   return TERSOFF_OK;
 }
 
-// Recover from a device status raised inside enqueued steps: the failing step k
-// stopped after its drift (list overflow: in the build; slot overflow: in the
-// force kernel).  Fix the cause, redo the step from there, then enqueue the rest.
-static int md_recover(tersoff_md *md, const RunState &h, long long call_base, long long n_call, double *d_trace)
+// Recover from a device status raised inside launched steps.  The failing step
+// stopped after its drift (list overflow: in the build; slot overflow: in the force
+// kernel): fix the cause, finish that step, then launch the rest.
+static int md_recover(tersoff_md *md, const RunState &h, double *d_trace)
 {
   tersoff_ctx *ctx = md->ctx;
-  const long long kfail = h.step - call_base + 1;   // 1-based step of this call that failed
+  cudaStream_t st = ctx->stream;
   if (h.status & ST_NLIST_OVERFLOW) {
     if (h.maxcount > MAX_CAP)
       return set_err(ctx, TERSOFF_ERR_NLIST_OVERFLOW, "%d neighbours within cutoff+skin exceed the limit %d",
                      h.maxcount, MAX_CAP);
     int cap = std::min(MAX_CAP, ((h.maxcount + std::max(4, h.maxcount / 4)) + 3) & ~3);
+    md_graphs_free(md);
     CKR(ensure_list(ctx, md->list, md->atoms.N, cap, md->list.grid.ncell));
     CKR(ensure_scatter(ctx, md->atoms, md->atoms.N, cap, md->mixed));
-    const int one = 1;
-    CK(cudaMemsetAsync(&md->rs->status, 0, sizeof(int), ctx->stream));
-    CK(cudaMemcpyAsync(&md->rs->rebuild, &one, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
-    CKR(md_build_gated(md));
+    CK(cudaMemsetAsync(&md->rs->status, 0, sizeof(int), st));
+    CKR(md_build(md, st, 0));
   } else if (h.status & ST_NC_OVERFLOW) {
+    md_graphs_free(md);
     md->gen_slots = force_slots_for(h.maxnc);
-    CK(cudaMemsetAsync(&md->rs->status, 0, sizeof(int), ctx->stream));
+    CK(cudaMemsetAsync(&md->rs->status, 0, sizeof(int), st));
   } else {
     return status_to_code(ctx, h.status, h);
   }
-  CK(cudaMemsetAsync(&md->rs->epot, 0, sizeof(double), ctx->stream));
-  CKR(md_force(md, d_trace ? 1 : 0));
-  CK(launch_step_end(ctx->stream, md->rs, d_trace, kfail));
-  if (kfail < n_call) CKR(md_enqueue(md, kfail + 1, n_call, d_trace, true));
+  CK(cudaMemsetAsync(&md->rs->epot, 0, sizeof(double), st));
+  CKR(md_force(md, st, d_trace ? 1 : 0));
+  CK(launch_step_end(st, md->rs, 0, 0));
+  const long long rest = h.steps_left - 1;
+  if (rest > 0) CKR(md_launch_steps(md, rest, d_trace, h.trace_k + 1));
   return TERSOFF_OK;
 }
 
-// Close pending half kick (optional), wait, check status and recover if needed.
-static int md_finish(tersoff_md *md, long long call_base, long long n_call, double *d_trace, bool close)
+// Close the pending half kick (optional), wait, check status and recover if needed.
+static int md_finish(tersoff_md *md, double *d_trace, bool close)
 {
   tersoff_ctx *ctx = md->ctx;
   for (int attempt = 0; attempt < 8; ++attempt) {
     if (close && md->open) {
-      CKR(md_vv(md, 1, d_trace != nullptr));
-      CK(launch_final(ctx->stream, md->rs, d_trace, n_call));
+      CKR(md_vv(md, ctx->stream, 1, d_trace != nullptr));
+      CK(launch_final(ctx->stream, md->rs));
     }
     RunState h;
     CKR(read_rs(ctx, md->rs, &h));
@@ -841,7 +949,7 @@ static int md_finish(tersoff_md *md, long long call_base, long long n_call, doub
       md->steps_target = h.step;
       return TERSOFF_OK;
     }
-    CKR(md_recover(md, h, call_base, n_call, d_trace));
+    CKR(md_recover(md, h, d_trace));
   }
   return set_err(ctx, TERSOFF_ERR_NLIST_OVERFLOW, "MD recovery did not converge");
 }
@@ -894,7 +1002,7 @@ int tersoff_md_create(tersoff_ctx *ctx, const double *pos, const double *vel, co
   if ((rc = ensure_scatter(ctx, md->atoms, N, md->list.cap, md->mixed)) != TERSOFF_OK) return fail(rc);
   md->gen_slots = force_slots_for(std::max(1, md->list.maxcount));
   md->fast_slots = (P->sym_angular && !ctx->general_only) ? 8 : 0;
-  if ((rc = md_force(md, 1)) != TERSOFF_OK) return fail(rc);
+  if ((rc = md_force(md, ctx->stream, 1)) != TERSOFF_OK) return fail(rc);
   if (launch_force_done(ctx->stream, md->rs) != cudaSuccess) return fail(set_err(ctx, TERSOFF_ERR_CUDA, "force_done"));
   RunState h;
   if ((rc = read_rs(ctx, md->rs, &h)) != TERSOFF_OK) return fail(rc);
@@ -904,6 +1012,12 @@ int tersoff_md_create(tersoff_ctx *ctx, const double *pos, const double *vel, co
   if (md->fast_slots > 0 && h.maxnc <= 4) md->fast_slots = 4;
   md->steps_done = md->steps_target = 0;
   md->pe_valid = true;
+  {
+    const char *g = getenv("TERSOFF_GRAPHS");
+    md->use_graphs = !(g && strcmp(g, "0") == 0);
+  }
+  if (cudaStreamCreateWithFlags(&md->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(set_err(ctx, TERSOFF_ERR_CUDA, "capture stream"));
   CK(cudaMemsetAsync(&md->rs->step, 0, sizeof(long long), ctx->stream));
   *out = md;
   return TERSOFF_OK;
@@ -915,9 +1029,13 @@ int tersoff_md_step_async(tersoff_md *md, int64_t nsteps)
   tersoff_ctx *ctx = md->ctx;
   cudaSetDevice(ctx->device);
   if (nsteps == 0) return TERSOFF_OK;
-  const long long base = md->steps_target;
-  CKR(md_enqueue(md, base + 1, base + nsteps, nullptr, false));
+  if (md->pending) {
+    // steps already in flight: let them finish (and recover) before chaining more
+    CKR(md_finish(md, nullptr, false));
+  }
+  CKR(md_launch_steps(md, nsteps, nullptr, 1));
   md->steps_target += nsteps;
+  md->pending = true;
   md->pe_valid = false;
   return TERSOFF_OK;
 }
@@ -926,9 +1044,8 @@ int tersoff_md_sync(tersoff_md *md)
 {
   if (!md) return TERSOFF_ERR_ARG;
   cudaSetDevice(md->ctx->device);
-  // async steps are numbered from 1 at the first step ever; recovery re-enqueues
-  // with the same numbering (no trace)
-  return md_finish(md, 0, md->steps_target, nullptr, true);
+  md->pending = false;
+  return md_finish(md, nullptr, true);
 }
 
 int tersoff_md_step(tersoff_md *md, int64_t nsteps, double *trace)
@@ -947,25 +1064,24 @@ int tersoff_md_step(tersoff_md *md, int64_t nsteps, double *trace)
     // steps run without energy accumulation left no potential energy for the
     // current positions: evaluate it (the forces come out bitwise the same)
     CK(cudaMemsetAsync(&md->rs->epot, 0, sizeof(double), ctx->stream));
-    CKR(md_force(md, 1));
+    CKR(md_force(md, ctx->stream, 1));
     CK(launch_force_done(ctx->stream, md->rs));
     md->pe_valid = true;
   }
-  const long long base = md->steps_done;
-  if (nsteps > 0) CKR(md_enqueue(md, 1, nsteps, d_trace, false));
-  md->steps_target = base + nsteps;
   if (nsteps == 0) {
     if (!trace) return TERSOFF_OK;
     // no step: report the current state
     RunState h;
-    CKR(md_vv(md, 0, true));
+    CKR(md_vv(md, ctx->stream, 0, true));
     CKR(read_rs(ctx, md->rs, &h));
     trace[0] = h.epot_last;
     trace[1] = 0.5 * h.ekin2 / ACCEL;
     CK(cudaMemsetAsync(&md->rs->ekin2, 0, sizeof(double), ctx->stream));
     return TERSOFF_OK;
   }
-  CKR(md_finish(md, base, nsteps, d_trace, true));
+  CKR(md_launch_steps(md, nsteps, d_trace, 1));
+  md->steps_target += nsteps;
+  CKR(md_finish(md, d_trace, true));
   md->pe_valid = trace != nullptr;
   if (trace) {
     CK(cudaMemcpyAsync(trace, d_trace, (size_t)(nsteps + 1) * 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
@@ -1055,6 +1171,8 @@ void tersoff_md_destroy(tersoff_md *md)
 {
   if (!md) return;
   if (md->ctx) cudaStreamSynchronize(md->ctx->stream);
+  md_graphs_free(md);
+  if (md->cap_stream) cudaStreamDestroy(md->cap_stream);
   for (auto e : md->ev_pool) cudaEventDestroy(e);
   free_atoms(md->atoms);
   free_list(md->list);
