@@ -109,7 +109,12 @@ template <class R> struct MathOf;
 template <> struct MathOf<float> { using M = MathF; };
 template <> struct MathOf<double> { using M = MathD; };
 
-// f_C and f_C' for r = rh + rl < R + D
+// f_C and f_C' for r = rh + rl < R + D.  In the taper
+//   f_C = 1/2 - 1/2 sin(pi (r - R)/(2D)) = sin^2(pi w),  w = (R + D - r)/(4D),
+//   f_C' = -pi/(4D) cos(pi (r - R)/(2D)) = -pi/(4D) sin(2 pi w),
+// identities that avoid the cancellation of 1/2 - 1/2 sin near the outer cutoff,
+// where f_C is small and zeta, hence dV/dzeta, is most sensitive to it.  R + D - r
+// is formed from head+tail values so it keeps its relative accuracy there.
 template <class M, class R>
 __device__ __forceinline__ void cutoff_fn(R rh, R rl, const PairP<R> &P, R &fc, R &dfc)
 {
@@ -117,10 +122,11 @@ __device__ __forceinline__ void cutoff_fn(R rh, R rl, const PairP<R> &P, R &fc, 
     fc = R(1);
     dfc = R(0);
   } else {
+    const R w = ((P.r_out - rh) + (P.r_out_lo - rl)) * P.inv4D;
     R s, c;
-    M::sincospi(((rh - P.Rc) + rl) * P.inv2D, &s, &c);
-    fc = R(0.5) - R(0.5) * s;
-    dfc = P.dfc_scale * c;
+    M::sincospi(w, &s, &c);
+    fc = s * s;
+    dfc = P.dfc_scale * R(2) * s * c;
   }
 }
 

@@ -290,9 +290,14 @@ __global__ void k_decide(RunState *rs, cudaGraphConditionalHandle build)
   cudaGraphSetConditional(build, (rs->status == 0 && rs->rebuild != 0) ? 1u : 0u);
 }
 
-// host-chosen controls of the next launch
+// host-chosen controls of the next launch.  After a failure the launched steps do
+// not run; their count is added to the steps left so that recovery resumes them all.
 __global__ void k_set_control(RunState *rs, long long steps, double *trace, long long trace_k, int open)
 {
+  if (rs->status != 0) {
+    rs->steps_left += steps;
+    return;
+  }
   rs->steps_left = steps;
   rs->trace = trace;
   rs->trace_k = trace_k;

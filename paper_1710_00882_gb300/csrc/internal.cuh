@@ -35,7 +35,8 @@ struct PairP {
   R beta, n, neg_inv2n;   // b = (1 + (beta zeta)^n)^(-1/(2n))
   R Rc, Dc;               // cutoff centre and half width
   R r_in, r_out, rc2;     // R - D, R + D, (R + D)^2
-  R inv2D, dfc_scale;     // 1/(2D), -pi/(4D)
+  R r_out_lo;             // float32 tables: (R + D) - (float)(R + D)
+  R inv4D, dfc_scale;     // 1/(4D), -pi/(4D)
 };
 
 // Angular part of the table (row (ti,tj,tk)).

@@ -513,7 +513,7 @@ int tersoff_params_create(tersoff_ctx *ctx, int ntypes, const double *entries, c
       d.beta = p[F_BETA]; d.n = p[F_N]; d.neg_inv2n = -1.0 / (2.0 * p[F_N]);
       d.Rc = p[F_R]; d.Dc = p[F_DD];
       d.r_in = p[F_R] - p[F_DD]; d.r_out = p[F_R] + p[F_DD]; d.rc2 = d.r_out * d.r_out;
-      d.inv2D = 1.0 / (2.0 * p[F_DD]); d.dfc_scale = -PI / (4.0 * p[F_DD]);
+      d.inv4D = 1.0 / (4.0 * p[F_DD]); d.dfc_scale = -PI / (4.0 * p[F_DD]); d.r_out_lo = 0.0;
       P->rcmax = std::max(P->rcmax, d.r_out);
       pd[a * nt + b] = d;
       PairP<float> f;
@@ -525,7 +525,8 @@ int tersoff_params_create(tersoff_ctx *ctx, int ntypes, const double *entries, c
       // float cutoff test must not admit a pair the float64 test rejects: use the float below r_out^2
       f.rc2 = (float)d.rc2;
       if ((double)f.rc2 > d.rc2) f.rc2 = std::nextafter(f.rc2, 0.0f);
-      f.inv2D = (float)d.inv2D; f.dfc_scale = (float)d.dfc_scale;
+      f.inv4D = (float)d.inv4D; f.dfc_scale = (float)d.dfc_scale;
+      f.r_out_lo = (float)(d.r_out - (double)f.r_out);
       pf[a * nt + b] = f;
       for (int c = 0; c < nt; ++c) {
         const double *t = row(a, b, c);
@@ -1029,10 +1030,6 @@ int tersoff_md_step_async(tersoff_md *md, int64_t nsteps)
   tersoff_ctx *ctx = md->ctx;
   cudaSetDevice(ctx->device);
   if (nsteps == 0) return TERSOFF_OK;
-  if (md->pending) {
-    // steps already in flight: let them finish (and recover) before chaining more
-    CKR(md_finish(md, nullptr, false));
-  }
   CKR(md_launch_steps(md, nsteps, nullptr, 1));
   md->steps_target += nsteps;
   md->pending = true;
