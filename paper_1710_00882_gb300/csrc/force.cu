@@ -242,6 +242,7 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
   int4 qi = make_int4(0, 0, 0, 0);
   dbl4 xi = make_dbl4(0, 0, 0, 0);
   unsigned long long mb = 0ull;
+  int n = 0;
   if (active) {
     if (MIXED) {
       qi = q[i];
@@ -250,33 +251,113 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
       xi = x[i];
       ti = (int)__double_as_longlong(xi.w);
     }
-    // pass 0: in-cutoff test of every list entry
-    const int n = cnt[i];
+    n = cnt[i];
+  }
+  // Direct path: the whole list fits the slots, so slot s is list entry s (entries
+  // outside the cutoff get f_C = f_C' = 0 and contribute nothing) and every load is
+  // issued in one unrolled burst.  Otherwise the list is packed: a first pass marks
+  // in-cutoff entries, the second loads them into consecutive slots.
+  const bool direct = active && n <= MAXNC;
+
+  R ux[MAXNC], uy[MAXNC], uz[MAXNC], rr[MAXNC], rl[MAXNC], ir[MAXNC], fc[MAXNC], dfc[MAXNC];
+  int meta[MAXNC];
+#pragma unroll
+  for (int s = 0; s < MAXNC; ++s) {
+    ux[s] = uy[s] = uz[s] = R(0);
+    rr[s] = ir[s] = R(1);
+    rl[s] = fc[s] = dfc[s] = R(0);
+    meta[s] = 0;
+  }
+
+  // geometry of slot s from list entry e (neighbour j): unit vector, r, 1/r, f_C, f_C'
+  auto fill_slot = [&](int s, int e, int j, const int4 &qj, const dbl4 &xj, int tj) {
+    R dx, dy, dz, r, rlo, inv;
+    if (MIXED) {
+      float dh[3], dl[3];
+      qd_fine(qdiff(qj.x, qi.x), geo.q_to_f[0], geo.q_to_f_lo[0], dh[0], dl[0]);
+      qd_fine(qdiff(qj.y, qi.y), geo.q_to_f[1], geo.q_to_f_lo[1], dh[1], dl[1]);
+      qd_fine(qdiff(qj.z, qi.z), geo.q_to_f[2], geo.q_to_f_lo[2], dh[2], dl[2]);
+      float rh_, rl_, irh_;
+      norm_fine(dh, dl, rh_, rl_, irh_);
+      dx = (R)dh[0]; dy = (R)dh[1]; dz = (R)dh[2];
+      r = (R)rh_; rlo = (R)rl_; inv = (R)irh_;
+    } else {
+      double ddx = xj.x - xi.x, ddy = xj.y - xi.y, ddz = xj.z - xi.z;
+      ddx -= geo.L[0] * rint(ddx * geo.invL[0]);
+      ddy -= geo.L[1] * rint(ddy * geo.invL[1]);
+      ddz -= geo.L[2] * rint(ddz * geo.invL[2]);
+      dx = (R)ddx; dy = (R)ddy; dz = (R)ddz;
+      const R r2 = dx * dx + dy * dy + dz * dz;
+      inv = M::rsqrt(r2);
+      r = r2 * inv;
+      rlo = R(0);
+    }
+    ux[s] = dx * inv;
+    uy[s] = dy * inv;
+    uz[s] = dz * inv;
+    rr[s] = r;
+    rl[s] = rlo;
+    ir[s] = inv;
+    cutoff_fn<M>(r, rlo, pairs[ONE ? 0 : ti * nt + tj], fc[s], dfc[s]);
+    meta[s] = e | (tj << 8);
+  };
+
+  // cheap in-cutoff test of entry (i, j)
+  auto in_cutoff = [&](const int4 &qj, const dbl4 &xj, int tj) -> bool {
+    R r2;
+    if (MIXED) {
+      const float dx = (float)qdiff(qj.x, qi.x) * geo.q_to_f[0];
+      const float dy = (float)qdiff(qj.y, qi.y) * geo.q_to_f[1];
+      const float dz = (float)qdiff(qj.z, qi.z) * geo.q_to_f[2];
+      r2 = dx * dx + dy * dy + dz * dz;
+    } else {
+      double dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
+      dx -= geo.L[0] * rint(dx * geo.invL[0]);
+      dy -= geo.L[1] * rint(dy * geo.invL[1]);
+      dz -= geo.L[2] * rint(dz * geo.invL[2]);
+      r2 = dx * dx + dy * dy + dz * dz;
+    }
+    return r2 < pairs[ONE ? 0 : ti * nt + tj].rc2;
+  };
+
+  int nc_all = 0;
+  if (direct) {
+    int jj[MAXNC];
+#pragma unroll
+    for (int s = 0; s < MAXNC; ++s) jj[s] = s < n ? nbr[(size_t)s * N + i] : i;
+    int4 qq[MAXNC];
+    dbl4 xx[MAXNC];
+#pragma unroll
+    for (int s = 0; s < MAXNC; ++s) {
+      if (MIXED) qq[s] = q[jj[s]];
+      else xx[s] = x[jj[s]];
+    }
+#pragma unroll
+    for (int s = 0; s < MAXNC; ++s) {
+      if (s < n) {
+        const int tj = MIXED ? qq[s].w : (int)__double_as_longlong(xx[s].w);
+        if (in_cutoff(qq[s], xx[s], tj)) {
+          mb |= 1ull << s;
+          fill_slot(s, s, jj[s], qq[s], xx[s], tj);
+        } else {
+          meta[s] = s | (tj << 8);
+        }
+      }
+    }
+    nc_all = __popcll(mb);
+  } else if (active) {
     for (int s = 0; s < n; ++s) {
       const int j = nbr[(size_t)s * N + i];
-      R r2;
+      int4 qj = make_int4(0, 0, 0, 0);
+      dbl4 xj = make_dbl4(0, 0, 0, 0);
       int tj;
-      if (MIXED) {
-        const int4 qj = q[j];
-        tj = qj.w;
-        const float dx = (float)qdiff(qj.x, qi.x) * geo.q_to_f[0];
-        const float dy = (float)qdiff(qj.y, qi.y) * geo.q_to_f[1];
-        const float dz = (float)qdiff(qj.z, qi.z) * geo.q_to_f[2];
-        r2 = dx * dx + dy * dy + dz * dz;
-      } else {
-        const dbl4 xj = x[j];
-        tj = (int)__double_as_longlong(xj.w);
-        double dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
-        dx -= geo.L[0] * rint(dx * geo.invL[0]);
-        dy -= geo.L[1] * rint(dy * geo.invL[1]);
-        dz -= geo.L[2] * rint(dz * geo.invL[2]);
-        r2 = dx * dx + dy * dy + dz * dz;
-      }
-      if (r2 < pairs[ONE ? 0 : ti * nt + tj].rc2) mb |= 1ull << s;
+      if (MIXED) { qj = q[j]; tj = qj.w; }
+      else { xj = x[j]; tj = (int)__double_as_longlong(xj.w); }
+      if (in_cutoff(qj, xj, tj)) mb |= 1ull << s;
     }
+    nc_all = __popcll(mb);
   }
-  const int nc_all = __popcll(mb);
-  const bool over = nc_all > MAXNC;
+  const bool over = !direct && nc_all > MAXNC;
   // queue atoms with too many neighbours, per block and in thread order
   {
     const unsigned bal = __ballot_sync(0xffffffffu, over);
@@ -292,65 +373,31 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
       int s = 0;
       for (int w = 0; w < T / 32; ++w) s += warp_over[w];
       nwork[blockIdx.x] = s;
+      if (s > 0) atomicAdd(&rs->over_total, s);
     }
   }
-  const int nc = over ? 0 : nc_all;
   {
     int m = nc_all;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((t & 31) == 0 && m > 0) atomicMax(&rs->maxnc, m);
   }
-
-  // ---- slots ---------------------------------------------------------------
-  R ux[MAXNC], uy[MAXNC], uz[MAXNC], rr[MAXNC], rl[MAXNC], ir[MAXNC], fc[MAXNC], dfc[MAXNC];
-  int meta[MAXNC];
-  {
-    unsigned long long rem = over ? 0ull : mb;
+  // slots in use: the whole list on the direct path, the packed in-cutoff entries else
+  const int nc = direct ? n : (over ? 0 : nc_all);
+  if (!direct && !over && active) {
+    unsigned long long rem = mb;
 #pragma unroll
     for (int s = 0; s < MAXNC; ++s) {
-      ux[s] = uy[s] = uz[s] = R(0);
-      rr[s] = ir[s] = R(1);
-      rl[s] = fc[s] = dfc[s] = R(0);
-      meta[s] = 0;
       if (s < nc) {
         const int e = __ffsll((long long)rem) - 1;
         rem &= rem - 1;
         const int j = nbr[(size_t)e * N + i];
-        R dx, dy, dz, r, rlo, inv;
+        int4 qj = make_int4(0, 0, 0, 0);
+        dbl4 xj = make_dbl4(0, 0, 0, 0);
         int tj;
-        if (MIXED) {
-          const int4 qj = q[j];
-          tj = qj.w;
-          float dh[3], dl[3];
-          qd_fine(qdiff(qj.x, qi.x), geo.q_to_f[0], geo.q_to_f_lo[0], dh[0], dl[0]);
-          qd_fine(qdiff(qj.y, qi.y), geo.q_to_f[1], geo.q_to_f_lo[1], dh[1], dl[1]);
-          qd_fine(qdiff(qj.z, qi.z), geo.q_to_f[2], geo.q_to_f_lo[2], dh[2], dl[2]);
-          float rh_, rl_, irh_;
-          norm_fine(dh, dl, rh_, rl_, irh_);
-          dx = (R)dh[0]; dy = (R)dh[1]; dz = (R)dh[2];
-          r = (R)rh_; rlo = (R)rl_; inv = (R)irh_;
-        } else {
-          const dbl4 xj = x[j];
-          tj = (int)__double_as_longlong(xj.w);
-          double ddx = xj.x - xi.x, ddy = xj.y - xi.y, ddz = xj.z - xi.z;
-          ddx -= geo.L[0] * rint(ddx * geo.invL[0]);
-          ddy -= geo.L[1] * rint(ddy * geo.invL[1]);
-          ddz -= geo.L[2] * rint(ddz * geo.invL[2]);
-          dx = (R)ddx; dy = (R)ddy; dz = (R)ddz;
-          const R r2 = dx * dx + dy * dy + dz * dz;
-          inv = M::rsqrt(r2);
-          r = r2 * inv;
-          rlo = R(0);
-        }
-        ux[s] = dx * inv;
-        uy[s] = dy * inv;
-        uz[s] = dz * inv;
-        rr[s] = r;
-        rl[s] = rlo;
-        ir[s] = inv;
-        cutoff_fn<M>(r, rlo, pairs[ONE ? 0 : ti * nt + tj], fc[s], dfc[s]);
-        meta[s] = e | (tj << 8);
+        if (MIXED) { qj = q[j]; tj = qj.w; }
+        else { xj = x[j]; tj = (int)__double_as_longlong(xj.w); }
+        fill_slot(s, e, j, qj, xj, tj);
       }
     }
   }
@@ -457,7 +504,7 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
     R fix = R(0), fiy = R(0), fiz = R(0);
 #pragma unroll
     for (int a = 0; a < MAXNC; ++a) {
-      if (a < nc) {
+      if (a < nc && ((mb >> (meta[a] & 0xff)) & 1ull)) {
         fix -= Fx[a];
         fiy -= Fy[a];
         fiz -= Fz[a];
@@ -517,6 +564,11 @@ k_force_gen(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
   int *smeta = reinterpret_cast<int *>(sr + (size_t)NRF * MAXNC * T);
 
   if (rs->status != 0) return;   // uniform across the grid
+  if (work && rs->over_total == 0) {
+    // no atom was queued: leave zero partial sums and stop
+    if ((EFLAG || VFLAG) && threadIdx.x < 8) partial[(size_t)blockIdx.x * 8 + threadIdx.x] = 0.0;
+    return;
+  }
   for (int k = threadIdx.x; k < nt * nt; k += T) pairs[k] = gpairs[k];
   for (int k = threadIdx.x; k < nt * nt * nt; k += T) trips[k] = gtrips[k];
   __syncthreads();
@@ -734,24 +786,33 @@ k_force_gen(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
 #undef META
 }
 
-// Sum n partial rows of (E, W[6]) in a fixed order into rs->epot / rs->virial.
-__global__ void k_reduce_partials(const double *__restrict__ partial, int n, RunState *rs)
+// Sum n partial rows of (E, W[6]) in a fixed order into rs->epot / rs->virial:
+// thread k adds rows k, k + 1024, ...; then a fixed tree over the threads.
+__global__ void __launch_bounds__(1024) k_reduce_partials(const double *__restrict__ partial, int n, RunState *rs)
 {
-  __shared__ double sh[256][7];
+  __shared__ double sh[32][7];
   if (rs->status != 0) return;
   double a[7] = {0, 0, 0, 0, 0, 0, 0};
-  for (int k = threadIdx.x; k < n; k += 256)
+  for (int k = threadIdx.x; k < n; k += 1024)
     for (int c = 0; c < 7; ++c) a[c] += partial[(size_t)k * 8 + c];
-  for (int c = 0; c < 7; ++c) sh[threadIdx.x][c] = a[c];
-  __syncthreads();
-  for (int w = 128; w > 0; w >>= 1) {
-    if (threadIdx.x < w)
-      for (int c = 0; c < 7; ++c) sh[threadIdx.x][c] += sh[threadIdx.x + w][c];
-    __syncthreads();
+  for (int c = 0; c < 7; ++c) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a[c] += __shfl_xor_sync(0xffffffffu, a[c], o);
   }
-  if (threadIdx.x == 0) {
-    rs->epot += sh[0][0];
-    for (int c = 0; c < 6; ++c) rs->virial[c] += sh[0][1 + c];
+  if ((threadIdx.x & 31) == 0)
+    for (int c = 0; c < 7; ++c) sh[threadIdx.x >> 5][c] = a[c];
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    for (int c = 0; c < 7; ++c) {
+      double v = sh[threadIdx.x][c];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      a[c] = v;
+    }
+    if (threadIdx.x == 0) {
+      rs->epot += a[0];
+      for (int c = 0; c < 6; ++c) rs->virial[c] += a[1 + c];
+    }
   }
 }
 
@@ -907,7 +968,7 @@ cudaError_t launch_force(cudaStream_t st, bool mixed, int fast_slots, bool one_t
   }
   if (e != cudaSuccess) return e;
   if (eflag || vflag) {
-    k_reduce_partials<<<1, 256, 0, st>>>(partial, rows, rs);
+    k_reduce_partials<<<1, 1024, 0, st>>>(partial, rows, rs);
     e = cudaGetLastError();
   }
   return e;

@@ -272,6 +272,7 @@ __global__ void k_step_end(RunState *rs, cudaGraphConditionalHandle loop, int us
   rs->ekin2 = 0.0;
   for (int c = 0; c < 6; ++c) rs->virial[c] = 0.0;
   rs->step += 1;
+  rs->over_total = 0;
   rs->trace_k = k + 1;
   rs->open = 1;
   rs->steps_left -= 1;
@@ -319,6 +320,7 @@ __global__ void k_force_done(RunState *rs)
   if (rs->status != 0) return;
   rs->epot_last = rs->epot;
   rs->epot = 0.0;
+  rs->over_total = 0;
   for (int c = 0; c < 6; ++c) rs->virial[c] = 0.0;
 }
 

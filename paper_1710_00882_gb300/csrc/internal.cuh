@@ -77,6 +77,7 @@ struct RunState {
   long long trace_k;     // trace row of the step in progress (1-based within a call)
   long long steps_left;  // steps still to run in the current graph launch
   int open;              // velocities at the half step (a closing kick is pending)
+  int over_total;        // atoms the register force kernel queued for the general kernel
 };
 
 // minimum-image difference of two fixed-point coordinates, in units of L / 2^32

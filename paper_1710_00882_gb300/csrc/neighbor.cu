@@ -150,73 +150,125 @@ __device__ __forceinline__ void axis_range(int c, int nc, int *lo, int *n)
   else { *lo = 0; *n = nc; }
 }
 
-// Entries of one atom's list kept sorted while they arrive (local memory, L1).
-constexpr int BUILD_LOCAL = 64;   // == MAX_CAP
+// One stage pair (K, J) of a bitonic sorting network over v[W], then the next;
+// all indices are compile-time so v[] stays in registers.
+template <int W, int K, int J>
+__device__ __forceinline__ void bitonic(int (&v)[W])
+{
+#pragma unroll
+  for (int a = 0; a < W; ++a) {
+    const int b = a ^ J;
+    if (b > a) {
+      const int x = v[a], y = v[b];
+      const int lo = min(x, y), hi = max(x, y);
+      const bool up = (a & K) == 0;
+      v[a] = up ? lo : hi;
+      v[b] = up ? hi : lo;
+    }
+  }
+  if constexpr (J > 1) bitonic<W, K, J / 2>(v);
+  else if constexpr (K < W) bitonic<W, 2 * K, K>(v);
+}
 
-// One thread per atom i: scan the stencil cells, keep j with |d_ij| < r_list, and
-// insert each into a sorted local buffer so that the list order depends only on the
-// set of neighbours.  The candidate loop runs over all stencil atoms as one flat
-// sequence (advance the cell when its atoms are done), so threads of a warp stay in
-// step however their cells are filled.
+// Sort the first n (<= W) entries of atom i's column in registers (padding with INT_MAX).
+template <int W>
+__device__ __forceinline__ void sort_column(int *__restrict__ nbr, int N, int i, int n)
+{
+  int v[W];
+#pragma unroll
+  for (int s = 0; s < W; ++s) v[s] = (s < n) ? nbr[(size_t)s * N + i] : 0x7fffffff;
+  bitonic<W, 2, 1>(v);
+#pragma unroll
+  for (int s = 0; s < W; ++s)
+    if (s < n) nbr[(size_t)s * N + i] = v[s];
+}
+
+// One thread per atom, atoms taken in cell order (threads of a warp share most of
+// their 27 stencil cells, so candidate loads hit L1): scan the stencil, keep j with
+// |d_ij| < r_list, then sort the column by j so that the list order depends only on
+// the set of neighbours.
 __global__ void __launch_bounds__(128) k_build(int N, const int4 *__restrict__ q, CellGrid g, Geom geo,
                                                const int *__restrict__ cell_start, const int *__restrict__ cell_atoms,
                                                int *__restrict__ nbr, int *__restrict__ cnt, int cap,
                                                int4 *__restrict__ qref, RunState *rs, int gated)
 {
+  __shared__ int sbuf[32][128];
   if (skip_build(rs, gated)) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N) return;
+  const int i = cell_atoms[t];
   const int4 pi = q[i];
   qref[i] = pi;
   int c[3] = {cell_coord((uint32_t)pi.x, g.nc[0]), cell_coord((uint32_t)pi.y, g.nc[1]),
               cell_coord((uint32_t)pi.z, g.nc[2])};
   int lo[3], nr[3];
   for (int a = 0; a < 3; ++a) axis_range(c[a], g.nc[a], &lo[a], &nr[a]);
-  const int ncells = nr[0] * nr[1] * nr[2];
-  int buf[BUILD_LOCAL];
   int n = 0;
-  int cidx = -1, t = 0, e = 0;
-  for (;;) {
-    if (t >= e) {
-      // next stencil cell
-      if (++cidx >= ncells) break;
-      const int ox = cidx % nr[0], oy = (cidx / nr[0]) % nr[1], oz = cidx / (nr[0] * nr[1]);
-      int cx = lo[0] + ox, cy = lo[1] + oy, cz = lo[2] + oz;
-      cx += (cx < 0) ? g.nc[0] : 0;
-      cx -= (cx >= g.nc[0]) ? g.nc[0] : 0;
+  for (int oz = 0; oz < nr[2]; ++oz) {
+    int cz = lo[2] + oz;
+    cz += (cz < 0) ? g.nc[2] : 0;
+    cz -= (cz >= g.nc[2]) ? g.nc[2] : 0;
+    for (int oy = 0; oy < nr[1]; ++oy) {
+      int cy = lo[1] + oy;
       cy += (cy < 0) ? g.nc[1] : 0;
       cy -= (cy >= g.nc[1]) ? g.nc[1] : 0;
-      cz += (cz < 0) ? g.nc[2] : 0;
-      cz -= (cz >= g.nc[2]) ? g.nc[2] : 0;
-      const int cell = (cz * g.nc[1] + cy) * g.nc[0] + cx;
-      t = cell_start[cell];
-      e = cell_start[cell + 1];
-      continue;
-    }
-    const int j = cell_atoms[t++];
-    if (j == i) continue;
-    const int4 pj = q[j];
-    const float dx = (float)qdiff(pj.x, pi.x) * geo.q_to_f[0];
-    const float dy = (float)qdiff(pj.y, pi.y) * geo.q_to_f[1];
-    const float dz = (float)qdiff(pj.z, pi.z) * geo.q_to_f[2];
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    if (r2 < g.rl2) {
-      if (n < BUILD_LOCAL) {
-        int k = n;
-        while (k > 0 && buf[k - 1] > j) {
-          buf[k] = buf[k - 1];
-          --k;
+      const int row = (cz * g.nc[1] + cy) * g.nc[0];
+      for (int ox = 0; ox < nr[0]; ++ox) {
+        int cx = lo[0] + ox;
+        cx += (cx < 0) ? g.nc[0] : 0;
+        cx -= (cx >= g.nc[0]) ? g.nc[0] : 0;
+        const int b = cell_start[row + cx], e = cell_start[row + cx + 1];
+        for (int u = b; u < e; ++u) {
+          const int j = cell_atoms[u];
+          if (j == i) continue;
+          const int4 pj = q[j];
+          const float dx = (float)qdiff(pj.x, pi.x) * geo.q_to_f[0];
+          const float dy = (float)qdiff(pj.y, pi.y) * geo.q_to_f[1];
+          const float dz = (float)qdiff(pj.z, pi.z) * geo.q_to_f[2];
+          const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          if (r2 < g.rl2) {
+            if (n < cap) nbr[(size_t)n * N + i] = j;
+            ++n;
+          }
         }
-        buf[k] = j;
       }
-      ++n;
     }
   }
   cnt[i] = n;
-  if (n > cap) atomicOr(&rs->status, ST_NLIST_OVERFLOW);
-  atomicMax(&rs->maxcount, n);
-  const int m = n < cap ? n : cap;
-  for (int k = 0; k < m; ++k) nbr[(size_t)k * N + i] = buf[k];
+  if (n > cap) {
+    atomicOr(&rs->status, ST_NLIST_OVERFLOW);
+    n = cap;
+  }
+  atomicMax(&rs->maxcount, cnt[i]);
+  if (n <= 8) {
+    sort_column<8>(nbr, N, i, n);
+  } else if (n <= 16) {
+    sort_column<16>(nbr, N, i, n);
+  } else if (n <= 32) {
+    // insertion sort in this thread's shared-memory column (stride 128: no bank conflicts)
+    for (int s1 = 0; s1 < n; ++s1) {
+      const int v = nbr[(size_t)s1 * N + i];
+      int k = s1 - 1;
+      while (k >= 0 && sbuf[k][threadIdx.x] > v) {
+        sbuf[k + 1][threadIdx.x] = sbuf[k][threadIdx.x];
+        --k;
+      }
+      sbuf[k + 1][threadIdx.x] = v;
+    }
+    for (int s1 = 0; s1 < n; ++s1) nbr[(size_t)s1 * N + i] = sbuf[s1][threadIdx.x];
+  } else {
+    for (int s1 = 1; s1 < n; ++s1) {
+      const int v = nbr[(size_t)s1 * N + i];
+      int k = s1 - 1;
+      while (k >= 0) {
+        const int w = nbr[(size_t)k * N + i];
+        if (w <= v) break;
+        nbr[(size_t)(k + 1) * N + i] = w;
+        --k;
+      }
+      nbr[(size_t)(k + 1) * N + i] = v;
+    }
+  }
 }
 
 // rev[s][i] = slot of i in the (sorted) list of j = nbr[s][i], found by binary search.
