@@ -125,6 +125,8 @@ struct tersoff_ctx {
   void *stage = nullptr;   // host-pointer staging (AoS positions/forces, types)
   size_t stage_bytes = 0;
   bool general_only = false;  // TERSOFF_FORCE_KERNEL=general: skip the register force kernel
+  int refs = 1;               // the caller's handle plus one per live list / MD state
+  bool destroyed = false;     // tersoff_ctx_destroy called; freed when refs reaches 0
 };
 
 struct tersoff_params {
@@ -434,9 +436,8 @@ int tersoff_ctx_create(int device, void *stream, tersoff_ctx **out)
   return TERSOFF_OK;
 }
 
-void tersoff_ctx_destroy(tersoff_ctx *ctx)
+static void ctx_free(tersoff_ctx *ctx)
 {
-  if (!ctx) return;
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   free_atoms(ctx->cstate);
@@ -445,6 +446,19 @@ void tersoff_ctx_destroy(tersoff_ctx *ctx)
   dfree(ctx->stage);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
+}
+
+// Lists and MD states keep their context alive: destroying handles in any order is safe.
+static void ctx_release(tersoff_ctx *ctx)
+{
+  if (ctx && --ctx->refs == 0) ctx_free(ctx);
+}
+
+void tersoff_ctx_destroy(tersoff_ctx *ctx)
+{
+  if (!ctx || ctx->destroyed) return;
+  ctx->destroyed = true;
+  ctx_release(ctx);
 }
 
 const char *tersoff_last_error(const tersoff_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
@@ -586,8 +600,9 @@ int tersoff_neighbor_build(tersoff_ctx *ctx, const double *pos, int64_t N, const
     nl = new (std::nothrow) tersoff_nlist();
     if (!nl) return TERSOFF_ERR_NOMEM;
     nl->ctx = ctx;
+    ctx->refs += 1;
     if (new_rs(ctx, &nl->rs) != TERSOFF_OK) {
-      delete nl;
+      tersoff_nlist_destroy(nl);
       return TERSOFF_ERR_NOMEM;
     }
     created = true;
@@ -631,6 +646,7 @@ void tersoff_nlist_destroy(tersoff_nlist *nl)
   free_atoms(nl->atoms);
   free_list(nl->list);
   dfree(nl->rs);
+  ctx_release(nl->ctx);
   delete nl;
 }
 
@@ -968,6 +984,7 @@ int tersoff_md_create(tersoff_ctx *ctx, const double *pos, const double *vel, co
   tersoff_md *md = new (std::nothrow) tersoff_md();
   if (!md) return TERSOFF_ERR_NOMEM;
   md->ctx = ctx;
+  ctx->refs += 1;
   md->params = P;
   md->dt = dt_ps;
   md->skin = skin;
@@ -1176,6 +1193,7 @@ void tersoff_md_destroy(tersoff_md *md)
   dfree(md->rs);
   dfree(md->d_kick);
   dfree(md->d_trace);
+  ctx_release(md->ctx);
   delete md;
 }
 
