@@ -282,12 +282,10 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
       dx = (R)dh[0]; dy = (R)dh[1]; dz = (R)dh[2];
       r = (R)rh_; rlo = (R)rl_; inv = (R)irh_;
     } else {
-      double ddx = xj.x - xi.x, ddy = xj.y - xi.y, ddz = xj.z - xi.z;
-      ddx -= geo.L[0] * rint(ddx * geo.invL[0]);
-      ddy -= geo.L[1] * rint(ddy * geo.invL[1]);
-      ddz -= geo.L[2] * rint(ddz * geo.invL[2]);
-      dx = (R)ddx; dy = (R)ddy; dz = (R)ddz;
-      const R r2 = dx * dx + dy * dy + dz * dz;
+      dx = (R)min_image(__dsub_rn(xj.x, xi.x), geo.L[0], geo.invL[0]);
+      dy = (R)min_image(__dsub_rn(xj.y, xi.y), geo.L[1], geo.invL[1]);
+      dz = (R)min_image(__dsub_rn(xj.z, xi.z), geo.L[2], geo.invL[2]);
+      const R r2 = r2_decide(dx, dy, dz);
       inv = M::rsqrt(r2);
       r = r2 * inv;
       rlo = R(0);
@@ -306,16 +304,12 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
   auto in_cutoff = [&](const int4 &qj, const dbl4 &xj, int tj) -> bool {
     R r2;
     if (MIXED) {
-      const float dx = (float)qdiff(qj.x, qi.x) * geo.q_to_f[0];
-      const float dy = (float)qdiff(qj.y, qi.y) * geo.q_to_f[1];
-      const float dz = (float)qdiff(qj.z, qi.z) * geo.q_to_f[2];
-      r2 = dx * dx + dy * dy + dz * dz;
+      r2 = r2_decide(q_scaled(qdiff(qj.x, qi.x), geo.q_to_f[0]), q_scaled(qdiff(qj.y, qi.y), geo.q_to_f[1]),
+                     q_scaled(qdiff(qj.z, qi.z), geo.q_to_f[2]));
     } else {
-      double dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
-      dx -= geo.L[0] * rint(dx * geo.invL[0]);
-      dy -= geo.L[1] * rint(dy * geo.invL[1]);
-      dz -= geo.L[2] * rint(dz * geo.invL[2]);
-      r2 = dx * dx + dy * dy + dz * dz;
+      r2 = r2_decide(min_image(__dsub_rn(xj.x, xi.x), geo.L[0], geo.invL[0]),
+                     min_image(__dsub_rn(xj.y, xi.y), geo.L[1], geo.invL[1]),
+                     min_image(__dsub_rn(xj.z, xi.z), geo.L[2], geo.invL[2]));
     }
     return r2 < pairs[ONE ? 0 : ti * nt + tj].rc2;
   };
@@ -612,19 +606,17 @@ k_force_gen(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
         if (MIXED) {
           const int4 qj = q[j];
           tj = qj.w;
-          dx = (R)(float)qdiff(qj.x, qi.x) * (R)geo.q_to_f[0];
-          dy = (R)(float)qdiff(qj.y, qi.y) * (R)geo.q_to_f[1];
-          dz = (R)(float)qdiff(qj.z, qi.z) * (R)geo.q_to_f[2];
+          dx = (R)q_scaled(qdiff(qj.x, qi.x), geo.q_to_f[0]);
+          dy = (R)q_scaled(qdiff(qj.y, qi.y), geo.q_to_f[1]);
+          dz = (R)q_scaled(qdiff(qj.z, qi.z), geo.q_to_f[2]);
         } else {
           const dbl4 xj = x[j];
           tj = (int)__double_as_longlong(xj.w);
-          double ddx = xj.x - xi.x, ddy = xj.y - xi.y, ddz = xj.z - xi.z;
-          ddx -= geo.L[0] * rint(ddx * geo.invL[0]);
-          ddy -= geo.L[1] * rint(ddy * geo.invL[1]);
-          ddz -= geo.L[2] * rint(ddz * geo.invL[2]);
-          dx = (R)ddx; dy = (R)ddy; dz = (R)ddz;
+          dx = (R)min_image(__dsub_rn(xj.x, xi.x), geo.L[0], geo.invL[0]);
+          dy = (R)min_image(__dsub_rn(xj.y, xi.y), geo.L[1], geo.invL[1]);
+          dz = (R)min_image(__dsub_rn(xj.z, xi.z), geo.L[2], geo.invL[2]);
         }
-        const R r2 = dx * dx + dy * dy + dz * dz;
+        const R r2 = r2_decide(dx, dy, dz);
         const PairP<R> &P = pairs[ti * nt + tj];
         if (r2 < P.rc2) {
           if (nc < MAXNC) {
@@ -640,7 +632,7 @@ k_force_gen(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
               dx = (R)dh[0]; dy = (R)dh[1]; dz = (R)dh[2];
               r = (R)rh_; rlo = (R)rl_; inv = (R)irh_;
             } else {
-              const R rf2 = dx * dx + dy * dy + dz * dz;
+              const R rf2 = r2_decide(dx, dy, dz);
               inv = M::rsqrt(rf2);
               r = rf2 * inv;
               rlo = R(0);

@@ -86,6 +86,26 @@ __host__ __device__ __forceinline__ int qdiff(int qj, int qi)
   return (int)((unsigned)qj - (unsigned)qi);
 }
 
+// Squared length used for every neighbour / cutoff decision.  Written with explicit
+// round-to-nearest operations so that the compiler cannot contract or reassociate
+// it differently in different places: the decision for (i, j) and (j, i) must be
+// bitwise the same wherever it is taken.
+__device__ __forceinline__ float r2_decide(float dx, float dy, float dz)
+{
+  return __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
+}
+__device__ __forceinline__ double r2_decide(double dx, double dy, double dz)
+{
+  return __fma_rn(dx, dx, __fma_rn(dy, dy, __dmul_rn(dz, dz)));
+}
+// minimum image in float64, one rounding per operation in a fixed order
+__device__ __forceinline__ double min_image(double d, double L, double invL)
+{
+  return __fma_rn(-L, rint(__dmul_rn(d, invL)), d);
+}
+// fixed-point difference scaled to Angstrom, one rounding
+__device__ __forceinline__ float q_scaled(int dq, float s) { return __fmul_rn((float)dq, s); }
+
 constexpr int ST_BAD_TYPE = 32;
 constexpr double ACCEL = 1.602176634e-19 / 1.66053906660e-27 * 1e-4;   // (eV/A)/amu in A/ps^2
 

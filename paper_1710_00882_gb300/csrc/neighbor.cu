@@ -222,10 +222,10 @@ __global__ void __launch_bounds__(128) k_build(int N, const int4 *__restrict__ q
           const int j = cell_atoms[u];
           if (j == i) continue;
           const int4 pj = q[j];
-          const float dx = (float)qdiff(pj.x, pi.x) * geo.q_to_f[0];
-          const float dy = (float)qdiff(pj.y, pi.y) * geo.q_to_f[1];
-          const float dz = (float)qdiff(pj.z, pi.z) * geo.q_to_f[2];
-          const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          const float dx = q_scaled(qdiff(pj.x, pi.x), geo.q_to_f[0]);
+          const float dy = q_scaled(qdiff(pj.y, pi.y), geo.q_to_f[1]);
+          const float dz = q_scaled(qdiff(pj.z, pi.z), geo.q_to_f[2]);
+          const float r2 = r2_decide(dx, dy, dz);
           if (r2 < g.rl2) {
             if (n < cap) nbr[(size_t)n * N + i] = j;
             ++n;
