@@ -34,6 +34,8 @@
 // scale so that d_ij is within ~1 ulp, and exp(-lambda r) forms lambda r with an
 // FMA-exact product, because the pair term's r-derivative is a difference of two
 // terms ~10x larger than itself.
+#include <cstdlib>
+
 #include "internal.cuh"
 
 namespace tsf {
@@ -43,6 +45,7 @@ template <> struct V4t<float> { using type = float4; };
 template <> struct V4t<double> { using type = dbl4; };
 
 constexpr int FAST_THREADS = 128;
+static int g_allow_direct = getenv("TERSOFF_NO_DIRECT") ? 0 : 1;
 constexpr float L2E_F = 1.44269502f;                   // log2(e) rounded to float
 constexpr float L2E_F_LO = 1.925963033500011e-08f;     // log2(e) - L2E_F
 
@@ -79,15 +82,16 @@ struct MathF {
   // first order, so the result carries the error of one ex2 only.
   static __device__ __forceinline__ float expneg2(float xh, float xl)
   {
-    const float yh = xh * L2E_F;
-    const float yl = fmaf(xh, L2E_F, -yh) + fmaf(xh, L2E_F_LO, xl * L2E_F);
-    return ex2(-yh) * fmaf(-yl, 0.69314718f, 1.0f);
+    // explicit round-to-nearest operations: a contracted product would break the split
+    const float yh = __fmul_rn(xh, L2E_F);
+    const float yl = __fadd_rn(__fmaf_rn(xh, L2E_F, -yh), __fmaf_rn(xh, L2E_F_LO, __fmul_rn(xl, L2E_F)));
+    return __fmul_rn(ex2(-yh), __fmaf_rn(-yl, 0.69314718f, 1.0f));
   }
   // e^{-(lh + ll)(rh + rl)}: lambda and r both given as float head + tail
   static __device__ __forceinline__ float expneg(float lh, float ll, float rh, float rl)
   {
-    const float p = lh * rh;
-    const float pe = fmaf(lh, rh, -p) + fmaf(ll, rh, lh * rl);
+    const float p = __fmul_rn(lh, rh);
+    const float pe = __fadd_rn(__fmaf_rn(lh, rh, -p), __fmaf_rn(ll, rh, __fmul_rn(lh, rl)));
     return expneg2(p, pe);
   }
   static __device__ __forceinline__ float expv(float x) { return expneg2(-x, 0.0f); }
@@ -146,14 +150,16 @@ __device__ __forceinline__ void bond_order(R zeta, const PairP<R> &P, R &b, R &d
 // minimum-image relative vector of a fixed-point pair, accurate to ~1 ulp:
 // the int32 difference is split into a 24-bit head and an 8-bit tail (both exact in
 // float) and the scale into float head + tail.
+// (Error-free transformations: every operation is an explicit round-to-nearest
+// intrinsic, which the compiler never contracts or reassociates.)
 __device__ __forceinline__ void qd_fine(int dq, float sh, float sl, float &dh, float &dl)
 {
   const float h = (float)(dq & ~0xff);
   const float l = (float)(dq & 0xff);
-  const float p = h * sh;
-  const float t = fmaf(h, sl, fmaf(l, sh, fmaf(h, sh, -p)));
-  dh = p + t;
-  dl = t - (dh - p);   // |p| >= |t|: exact tail
+  const float p = __fmul_rn(h, sh);
+  const float t = __fmaf_rn(h, sl, __fmaf_rn(l, sh, __fmaf_rn(h, sh, -p)));
+  dh = __fadd_rn(p, t);
+  dl = __fsub_rn(t, __fsub_rn(dh, p));   // |p| >= |t|: exact tail
 }
 
 // r = |d| as head + tail from d given as head + tail per component: squares split
@@ -165,19 +171,19 @@ __device__ __forceinline__ void norm_fine(const float (&dh)[3], const float (&dl
   float sq[3], er[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    sq[a] = dh[a] * dh[a];
-    er[a] = fmaf(dh[a], dh[a], -sq[a]) + 2.0f * dh[a] * dl[a];
+    sq[a] = __fmul_rn(dh[a], dh[a]);
+    er[a] = __fmaf_rn(__fmul_rn(2.0f, dh[a]), dl[a], __fmaf_rn(dh[a], dh[a], -sq[a]));
   }
-  const float s1 = sq[0] + sq[1];
-  const float bb1 = s1 - sq[0];
-  const float e1 = (sq[0] - (s1 - bb1)) + (sq[1] - bb1);
-  const float s2 = s1 + sq[2];
-  const float bb2 = s2 - s1;
-  const float e2 = (s1 - (s2 - bb2)) + (sq[2] - bb2);
-  const float r2l = e1 + e2 + er[0] + er[1] + er[2];
+  const float s1 = __fadd_rn(sq[0], sq[1]);
+  const float bb1 = __fsub_rn(s1, sq[0]);
+  const float e1 = __fadd_rn(__fsub_rn(sq[0], __fsub_rn(s1, bb1)), __fsub_rn(sq[1], bb1));
+  const float s2 = __fadd_rn(s1, sq[2]);
+  const float bb2 = __fsub_rn(s2, s1);
+  const float e2 = __fadd_rn(__fsub_rn(s1, __fsub_rn(s2, bb2)), __fsub_rn(sq[2], bb2));
+  const float r2l = __fadd_rn(__fadd_rn(e1, e2), __fadd_rn(er[0], __fadd_rn(er[1], er[2])));
   irh = MathF::rsqrt(s2);
-  rh = s2 * irh;
-  rl = (fmaf(-rh, rh, s2) + r2l) * 0.5f * irh;
+  rh = __fmul_rn(s2, irh);
+  rl = __fmul_rn(__fmul_rn(__fadd_rn(__fmaf_rn(-rh, rh, s2), r2l), 0.5f), irh);
 }
 
 template <class R> __device__ __forceinline__ R warp_sum(R v)
@@ -219,7 +225,8 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
             const int *__restrict__ cnt, Geom geo, const PairP<R> *__restrict__ gpairs,
             const TripP<R> *__restrict__ gtrips, int nt, typename V4t<R>::type *__restrict__ contrib,
             typename V4t<R>::type *__restrict__ selfF, unsigned long long *__restrict__ mask,
-            int *__restrict__ work, int *__restrict__ nwork, double *__restrict__ partial, RunState *rs)
+            int *__restrict__ work, int *__restrict__ nwork, double *__restrict__ partial, RunState *rs,
+            int allow_direct)
 {
   using M = typename MathOf<R>::M;
   using V4 = typename V4t<R>::type;
@@ -257,7 +264,7 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
   // outside the cutoff get f_C = f_C' = 0 and contribute nothing) and every load is
   // issued in one unrolled burst.  Otherwise the list is packed: a first pass marks
   // in-cutoff entries, the second loads them into consecutive slots.
-  const bool direct = active && n <= MAXNC;
+  const bool direct = active && n <= MAXNC && allow_direct;
 
   R ux[MAXNC], uy[MAXNC], uz[MAXNC], rr[MAXNC], rl[MAXNC], ir[MAXNC], fc[MAXNC], dfc[MAXNC];
   int meta[MAXNC];
@@ -894,13 +901,16 @@ static cudaError_t launch_reg(cudaStream_t st, int eflag, int vflag, int N, cons
   using V = typename V4t<R>::type *;
   if (vflag)
     k_force_reg<R, MAXNC, ONE, true, true><<<blocks, FAST_THREADS, 0, st>>>(
-        N, x, q, nbr, cnt, geo, (P)pairs, (Tt)trips, nt, (V)contrib, (V)selfF, mask, work, nwork, partial, rs);
+        N, x, q, nbr, cnt, geo, (P)pairs, (Tt)trips, nt, (V)contrib, (V)selfF, mask, work, nwork, partial, rs,
+        g_allow_direct);
   else if (eflag)
     k_force_reg<R, MAXNC, ONE, true, false><<<blocks, FAST_THREADS, 0, st>>>(
-        N, x, q, nbr, cnt, geo, (P)pairs, (Tt)trips, nt, (V)contrib, (V)selfF, mask, work, nwork, partial, rs);
+        N, x, q, nbr, cnt, geo, (P)pairs, (Tt)trips, nt, (V)contrib, (V)selfF, mask, work, nwork, partial, rs,
+        g_allow_direct);
   else
     k_force_reg<R, MAXNC, ONE, false, false><<<blocks, FAST_THREADS, 0, st>>>(
-        N, x, q, nbr, cnt, geo, (P)pairs, (Tt)trips, nt, (V)contrib, (V)selfF, mask, work, nwork, partial, rs);
+        N, x, q, nbr, cnt, geo, (P)pairs, (Tt)trips, nt, (V)contrib, (V)selfF, mask, work, nwork, partial, rs,
+        g_allow_direct);
   return cudaGetLastError();
 }
 

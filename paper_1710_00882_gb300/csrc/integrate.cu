@@ -16,12 +16,13 @@ template <class R> struct V4g;
 template <> struct V4g<float> { using type = float4; };
 template <> struct V4g<double> { using type = dbl4; };
 
-// Knuth's TwoSum: s + e == a + b exactly (float32 round-to-nearest).
+// Knuth's TwoSum: s + e == a + b exactly (float32 round-to-nearest; explicit
+// intrinsics so that no step is contracted or reassociated).
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
 {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
 template <class R> struct GatherAcc;
@@ -39,9 +40,9 @@ template <> struct GatherAcc<float> {
   __device__ __forceinline__ void add(const float4 &c)
   {
     float e;
-    two_sum(h[0], c.x, h[0], e); l[0] += e;
-    two_sum(h[1], c.y, h[1], e); l[1] += e;
-    two_sum(h[2], c.z, h[2], e); l[2] += e;
+    two_sum(h[0], c.x, h[0], e); l[0] = __fadd_rn(l[0], e);
+    two_sum(h[1], c.y, h[1], e); l[1] = __fadd_rn(l[1], e);
+    two_sum(h[2], c.z, h[2], e); l[2] = __fadd_rn(l[2], e);
   }
   __device__ __forceinline__ void out(double &fx, double &fy, double &fz) const
   {
