@@ -222,7 +222,7 @@ __device__ __forceinline__ void block_partial(const R (&v)[7], bool eflag, bool 
 template <class R, int MAXNC, bool ONE, bool EFLAG, bool VFLAG>
 __global__ void __launch_bounds__(FAST_THREADS)
 k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const int *__restrict__ nbr,
-            const int *__restrict__ cnt, Geom geo, const PairP<R> *__restrict__ gpairs,
+            const int *__restrict__ cnt, const SysTab *__restrict__ sys, const PairP<R> *__restrict__ gpairs,
             const TripP<R> *__restrict__ gtrips, int nt, typename V4t<R>::type *__restrict__ contrib,
             typename V4t<R>::type *__restrict__ selfF, unsigned long long *__restrict__ mask,
             int *__restrict__ work, int *__restrict__ nwork, double *__restrict__ partial, RunState *rs,
@@ -250,14 +250,18 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
   dbl4 xi = make_dbl4(0, 0, 0, 0);
   unsigned long long mb = 0ull;
   int n = 0;
+  const Geom *gp = &sys[0].geo;   // geometry of atom i's system (all its neighbours share it)
   if (active) {
+    int w;
     if (MIXED) {
       qi = q[i];
-      ti = qi.w;
+      w = qi.w;
     } else {
       xi = x[i];
-      ti = (int)__double_as_longlong(xi.w);
+      w = (int)__double_as_longlong(xi.w);
     }
+    ti = type_of(w);
+    gp = &sys[sys_of(w)].geo;
     n = cnt[i];
   }
   // Direct path: the whole list fits the slots, so slot s is list entry s (entries
@@ -281,17 +285,17 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
     R dx, dy, dz, r, rlo, inv;
     if (MIXED) {
       float dh[3], dl[3];
-      qd_fine(qdiff(qj.x, qi.x), geo.q_to_f[0], geo.q_to_f_lo[0], dh[0], dl[0]);
-      qd_fine(qdiff(qj.y, qi.y), geo.q_to_f[1], geo.q_to_f_lo[1], dh[1], dl[1]);
-      qd_fine(qdiff(qj.z, qi.z), geo.q_to_f[2], geo.q_to_f_lo[2], dh[2], dl[2]);
+      qd_fine(qdiff(qj.x, qi.x), gp->q_to_f[0], gp->q_to_f_lo[0], dh[0], dl[0]);
+      qd_fine(qdiff(qj.y, qi.y), gp->q_to_f[1], gp->q_to_f_lo[1], dh[1], dl[1]);
+      qd_fine(qdiff(qj.z, qi.z), gp->q_to_f[2], gp->q_to_f_lo[2], dh[2], dl[2]);
       float rh_, rl_, irh_;
       norm_fine(dh, dl, rh_, rl_, irh_);
       dx = (R)dh[0]; dy = (R)dh[1]; dz = (R)dh[2];
       r = (R)rh_; rlo = (R)rl_; inv = (R)irh_;
     } else {
-      dx = (R)min_image(__dsub_rn(xj.x, xi.x), geo.L[0], geo.invL[0]);
-      dy = (R)min_image(__dsub_rn(xj.y, xi.y), geo.L[1], geo.invL[1]);
-      dz = (R)min_image(__dsub_rn(xj.z, xi.z), geo.L[2], geo.invL[2]);
+      dx = (R)min_image(__dsub_rn(xj.x, xi.x), gp->L[0], gp->invL[0]);
+      dy = (R)min_image(__dsub_rn(xj.y, xi.y), gp->L[1], gp->invL[1]);
+      dz = (R)min_image(__dsub_rn(xj.z, xi.z), gp->L[2], gp->invL[2]);
       const R r2 = r2_decide(dx, dy, dz);
       inv = M::rsqrt(r2);
       r = r2 * inv;
@@ -311,12 +315,12 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
   auto in_cutoff = [&](const int4 &qj, const dbl4 &xj, int tj) -> bool {
     R r2;
     if (MIXED) {
-      r2 = r2_decide(q_scaled(qdiff(qj.x, qi.x), geo.q_to_f[0]), q_scaled(qdiff(qj.y, qi.y), geo.q_to_f[1]),
-                     q_scaled(qdiff(qj.z, qi.z), geo.q_to_f[2]));
+      r2 = r2_decide(q_scaled(qdiff(qj.x, qi.x), gp->q_to_f[0]), q_scaled(qdiff(qj.y, qi.y), gp->q_to_f[1]),
+                     q_scaled(qdiff(qj.z, qi.z), gp->q_to_f[2]));
     } else {
-      r2 = r2_decide(min_image(__dsub_rn(xj.x, xi.x), geo.L[0], geo.invL[0]),
-                     min_image(__dsub_rn(xj.y, xi.y), geo.L[1], geo.invL[1]),
-                     min_image(__dsub_rn(xj.z, xi.z), geo.L[2], geo.invL[2]));
+      r2 = r2_decide(min_image(__dsub_rn(xj.x, xi.x), gp->L[0], gp->invL[0]),
+                     min_image(__dsub_rn(xj.y, xi.y), gp->L[1], gp->invL[1]),
+                     min_image(__dsub_rn(xj.z, xi.z), gp->L[2], gp->invL[2]));
     }
     return r2 < pairs[ONE ? 0 : ti * nt + tj].rc2;
   };
@@ -336,7 +340,7 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
 #pragma unroll
     for (int s = 0; s < MAXNC; ++s) {
       if (s < n) {
-        const int tj = MIXED ? qq[s].w : (int)__double_as_longlong(xx[s].w);
+        const int tj = type_of(MIXED ? qq[s].w : (int)__double_as_longlong(xx[s].w));
         if (in_cutoff(qq[s], xx[s], tj)) {
           mb |= 1ull << s;
           fill_slot(s, s, jj[s], qq[s], xx[s], tj);
@@ -352,8 +356,8 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
       int4 qj = make_int4(0, 0, 0, 0);
       dbl4 xj = make_dbl4(0, 0, 0, 0);
       int tj;
-      if (MIXED) { qj = q[j]; tj = qj.w; }
-      else { xj = x[j]; tj = (int)__double_as_longlong(xj.w); }
+      if (MIXED) { qj = q[j]; tj = type_of(qj.w); }
+      else { xj = x[j]; tj = type_of((int)__double_as_longlong(xj.w)); }
       if (in_cutoff(qj, xj, tj)) mb |= 1ull << s;
     }
     nc_all = __popcll(mb);
@@ -396,8 +400,8 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
         int4 qj = make_int4(0, 0, 0, 0);
         dbl4 xj = make_dbl4(0, 0, 0, 0);
         int tj;
-        if (MIXED) { qj = q[j]; tj = qj.w; }
-        else { xj = x[j]; tj = (int)__double_as_longlong(xj.w); }
+        if (MIXED) { qj = q[j]; tj = type_of(qj.w); }
+        else { xj = x[j]; tj = type_of((int)__double_as_longlong(xj.w)); }
         fill_slot(s, e, j, qj, xj, tj);
       }
     }
@@ -547,7 +551,7 @@ struct GenCfg {
 template <class R, int MAXNC, bool EFLAG, bool VFLAG>
 __global__ void __launch_bounds__(GenCfg<R, MAXNC>::threads)
 k_force_gen(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const int *__restrict__ nbr,
-            const int *__restrict__ cnt, Geom geo, const PairP<R> *__restrict__ gpairs,
+            const int *__restrict__ cnt, const SysTab *__restrict__ sys, const PairP<R> *__restrict__ gpairs,
             const TripP<R> *__restrict__ gtrips, int nt, typename V4t<R>::type *__restrict__ contrib,
             typename V4t<R>::type *__restrict__ selfF, unsigned long long *__restrict__ mask,
             const int *__restrict__ work, const int *__restrict__ nwork, int nfast, double *__restrict__ partial,
@@ -593,16 +597,18 @@ k_force_gen(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
     for (int k = t; k < (work ? cntb : T); k += T) {
       const int i = work ? work[(size_t)fb * FAST_THREADS + k] : (int)blockIdx.x * T + t;
       if (i >= N) continue;
-      int ti;
+      int ti, w;
       int4 qi = make_int4(0, 0, 0, 0);
       dbl4 xi = make_dbl4(0, 0, 0, 0);
       if (MIXED) {
         qi = q[i];
-        ti = qi.w;
+        w = qi.w;
       } else {
         xi = x[i];
-        ti = (int)__double_as_longlong(xi.w);
+        w = (int)__double_as_longlong(xi.w);
       }
+      ti = type_of(w);
+      const Geom *gp = &sys[sys_of(w)].geo;
       int nc = 0;
       unsigned long long mbits = 0ull;
       const int n = cnt[i];
@@ -612,16 +618,16 @@ k_force_gen(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
         int tj;
         if (MIXED) {
           const int4 qj = q[j];
-          tj = qj.w;
-          dx = (R)q_scaled(qdiff(qj.x, qi.x), geo.q_to_f[0]);
-          dy = (R)q_scaled(qdiff(qj.y, qi.y), geo.q_to_f[1]);
-          dz = (R)q_scaled(qdiff(qj.z, qi.z), geo.q_to_f[2]);
+          tj = type_of(qj.w);
+          dx = (R)q_scaled(qdiff(qj.x, qi.x), gp->q_to_f[0]);
+          dy = (R)q_scaled(qdiff(qj.y, qi.y), gp->q_to_f[1]);
+          dz = (R)q_scaled(qdiff(qj.z, qi.z), gp->q_to_f[2]);
         } else {
           const dbl4 xj = x[j];
-          tj = (int)__double_as_longlong(xj.w);
-          dx = (R)min_image(__dsub_rn(xj.x, xi.x), geo.L[0], geo.invL[0]);
-          dy = (R)min_image(__dsub_rn(xj.y, xi.y), geo.L[1], geo.invL[1]);
-          dz = (R)min_image(__dsub_rn(xj.z, xi.z), geo.L[2], geo.invL[2]);
+          tj = type_of((int)__double_as_longlong(xj.w));
+          dx = (R)min_image(__dsub_rn(xj.x, xi.x), gp->L[0], gp->invL[0]);
+          dy = (R)min_image(__dsub_rn(xj.y, xi.y), gp->L[1], gp->invL[1]);
+          dz = (R)min_image(__dsub_rn(xj.z, xi.z), gp->L[2], gp->invL[2]);
         }
         const R r2 = r2_decide(dx, dy, dz);
         const PairP<R> &P = pairs[ti * nt + tj];
@@ -631,9 +637,9 @@ k_force_gen(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
             if (MIXED) {
               const int4 qj = q[j];
               float dh[3], dl[3];
-              qd_fine(qdiff(qj.x, qi.x), geo.q_to_f[0], geo.q_to_f_lo[0], dh[0], dl[0]);
-              qd_fine(qdiff(qj.y, qi.y), geo.q_to_f[1], geo.q_to_f_lo[1], dh[1], dl[1]);
-              qd_fine(qdiff(qj.z, qi.z), geo.q_to_f[2], geo.q_to_f_lo[2], dh[2], dl[2]);
+              qd_fine(qdiff(qj.x, qi.x), gp->q_to_f[0], gp->q_to_f_lo[0], dh[0], dl[0]);
+              qd_fine(qdiff(qj.y, qi.y), gp->q_to_f[1], gp->q_to_f_lo[1], dh[1], dl[1]);
+              qd_fine(qdiff(qj.z, qi.z), gp->q_to_f[2], gp->q_to_f_lo[2], dh[2], dl[2]);
               float rh_, rl_, irh_;
               norm_fine(dh, dl, rh_, rl_, irh_);
               dx = (R)dh[0]; dy = (R)dh[1]; dz = (R)dh[2];
@@ -819,7 +825,7 @@ __global__ void __launch_bounds__(1024) k_reduce_partials(const double *__restri
 
 template <class R, int MAXNC, bool EFLAG, bool VFLAG>
 static cudaError_t launch_gen_t(cudaStream_t st, int N, const dbl4 *x, const int4 *q, const int *nbr, const int *cnt,
-                                const Geom &geo, const void *pairs, const void *trips, int nt, void *contrib,
+                                const SysTab *sys, const void *pairs, const void *trips, int nt, void *contrib,
                                 void *selfF, unsigned long long *mask, const int *work, const int *nwork, int nfast,
                                 int gen_blocks, double *partial, RunState *rs)
 {
@@ -835,7 +841,7 @@ static cudaError_t launch_gen_t(cudaStream_t st, int N, const dbl4 *x, const int
   }
   if (N == 0) return cudaSuccess;
   const int blocks = work ? gen_blocks : (N + C::threads - 1) / C::threads;
-  kern<<<blocks, C::threads, smem, st>>>(N, x, q, nbr, cnt, geo, (const PairP<R> *)pairs, (const TripP<R> *)trips,
+  kern<<<blocks, C::threads, smem, st>>>(N, x, q, nbr, cnt, sys, (const PairP<R> *)pairs, (const TripP<R> *)trips,
                                          nt, (typename V4t<R>::type *)contrib, (typename V4t<R>::type *)selfF, mask,
                                          work, nwork, nfast, partial, rs);
   return cudaGetLastError();
@@ -843,17 +849,17 @@ static cudaError_t launch_gen_t(cudaStream_t st, int N, const dbl4 *x, const int
 
 template <class R, int MAXNC>
 static cudaError_t launch_gen(cudaStream_t st, int eflag, int vflag, int N, const dbl4 *x, const int4 *q,
-                              const int *nbr, const int *cnt, const Geom &geo, const void *pairs, const void *trips,
+                              const int *nbr, const int *cnt, const SysTab *sys, const void *pairs, const void *trips,
                               int nt, void *contrib, void *selfF, unsigned long long *mask, const int *work,
                               const int *nwork, int nfast, int gen_blocks, double *partial, RunState *rs)
 {
   if (vflag)
-    return launch_gen_t<R, MAXNC, true, true>(st, N, x, q, nbr, cnt, geo, pairs, trips, nt, contrib, selfF, mask, work,
+    return launch_gen_t<R, MAXNC, true, true>(st, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib, selfF, mask, work,
                                               nwork, nfast, gen_blocks, partial, rs);
   if (eflag)
-    return launch_gen_t<R, MAXNC, true, false>(st, N, x, q, nbr, cnt, geo, pairs, trips, nt, contrib, selfF, mask,
+    return launch_gen_t<R, MAXNC, true, false>(st, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib, selfF, mask,
                                                work, nwork, nfast, gen_blocks, partial, rs);
-  return launch_gen_t<R, MAXNC, false, false>(st, N, x, q, nbr, cnt, geo, pairs, trips, nt, contrib, selfF, mask,
+  return launch_gen_t<R, MAXNC, false, false>(st, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib, selfF, mask,
                                               work, nwork, nfast, gen_blocks, partial, rs);
 }
 
@@ -870,14 +876,14 @@ static int gen_threads(int slots)
 
 template <class R>
 static cudaError_t launch_gen_any(cudaStream_t st, int slots, int eflag, int vflag, int N, const dbl4 *x,
-                                  const int4 *q, const int *nbr, const int *cnt, const Geom &geo, const void *pairs,
+                                  const int4 *q, const int *nbr, const int *cnt, const SysTab *sys, const void *pairs,
                                   const void *trips, int nt, void *contrib, void *selfF, unsigned long long *mask,
                                   const int *work, const int *nwork, int nfast, int gen_blocks, double *partial,
                                   RunState *rs)
 {
 #define TSF_GEN(NC)                                                                                                \
   case NC:                                                                                                         \
-    return launch_gen<R, NC>(st, eflag, vflag, N, x, q, nbr, cnt, geo, pairs, trips, nt, contrib, selfF, mask, work, \
+    return launch_gen<R, NC>(st, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib, selfF, mask, work, \
                              nwork, nfast, gen_blocks, partial, rs);
   switch (slots) {
     TSF_GEN(8)
@@ -891,7 +897,7 @@ static cudaError_t launch_gen_any(cudaStream_t st, int slots, int eflag, int vfl
 
 template <class R, int MAXNC, bool ONE>
 static cudaError_t launch_reg(cudaStream_t st, int eflag, int vflag, int N, const dbl4 *x, const int4 *q,
-                              const int *nbr, const int *cnt, const Geom &geo, const void *pairs, const void *trips,
+                              const int *nbr, const int *cnt, const SysTab *sys, const void *pairs, const void *trips,
                               int nt, void *contrib, void *selfF, unsigned long long *mask, int *work, int *nwork,
                               double *partial, RunState *rs)
 {
@@ -901,15 +907,15 @@ static cudaError_t launch_reg(cudaStream_t st, int eflag, int vflag, int N, cons
   using V = typename V4t<R>::type *;
   if (vflag)
     k_force_reg<R, MAXNC, ONE, true, true><<<blocks, FAST_THREADS, 0, st>>>(
-        N, x, q, nbr, cnt, geo, (P)pairs, (Tt)trips, nt, (V)contrib, (V)selfF, mask, work, nwork, partial, rs,
+        N, x, q, nbr, cnt, sys, (P)pairs, (Tt)trips, nt, (V)contrib, (V)selfF, mask, work, nwork, partial, rs,
         g_allow_direct);
   else if (eflag)
     k_force_reg<R, MAXNC, ONE, true, false><<<blocks, FAST_THREADS, 0, st>>>(
-        N, x, q, nbr, cnt, geo, (P)pairs, (Tt)trips, nt, (V)contrib, (V)selfF, mask, work, nwork, partial, rs,
+        N, x, q, nbr, cnt, sys, (P)pairs, (Tt)trips, nt, (V)contrib, (V)selfF, mask, work, nwork, partial, rs,
         g_allow_direct);
   else
     k_force_reg<R, MAXNC, ONE, false, false><<<blocks, FAST_THREADS, 0, st>>>(
-        N, x, q, nbr, cnt, geo, (P)pairs, (Tt)trips, nt, (V)contrib, (V)selfF, mask, work, nwork, partial, rs,
+        N, x, q, nbr, cnt, sys, (P)pairs, (Tt)trips, nt, (V)contrib, (V)selfF, mask, work, nwork, partial, rs,
         g_allow_direct);
   return cudaGetLastError();
 }
@@ -934,7 +940,7 @@ int force_partial_rows(int N) { return (N + 31) / 32 + force_gen_blocks(); }
 // virial are added to rs->epot / rs->virial.
 cudaError_t launch_force(cudaStream_t st, bool mixed, int fast_slots, bool one_type, int gen_slots, int eflag,
                          int vflag, int N, const dbl4 *x, const int4 *q, const int *nbr, const int *cnt,
-                         const Geom &geo, const void *pairs, const void *trips, int nt, void *contrib, void *selfF,
+                         const SysTab *sys, const void *pairs, const void *trips, int nt, void *contrib, void *selfF,
                          unsigned long long *mask, int *work, int *nwork, double *partial, RunState *rs)
 {
   if (N == 0) return cudaSuccess;
@@ -943,9 +949,9 @@ cudaError_t launch_force(cudaStream_t st, bool mixed, int fast_slots, bool one_t
   int rows = 0;
   if (fast_slots > 0) {
 #define TSF_REG(R, NC)                                                                                              \
-  e = one_type ? launch_reg<R, NC, true>(st, eflag, vflag, N, x, q, nbr, cnt, geo, pairs, trips, nt, contrib, selfF, \
+  e = one_type ? launch_reg<R, NC, true>(st, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib, selfF, \
                                          mask, work, nwork, partial, rs)                                            \
-               : launch_reg<R, NC, false>(st, eflag, vflag, N, x, q, nbr, cnt, geo, pairs, trips, nt, contrib,      \
+               : launch_reg<R, NC, false>(st, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib,      \
                                           selfF, mask, work, nwork, partial, rs);
     if (mixed) {
       if (fast_slots <= 4) { TSF_REG(float, 4) } else { TSF_REG(float, 8) }
@@ -955,15 +961,15 @@ cudaError_t launch_force(cudaStream_t st, bool mixed, int fast_slots, bool one_t
 #undef TSF_REG
     if (e != cudaSuccess) return e;
     double *gp = partial + (size_t)nfast * 8;
-    e = mixed ? launch_gen_any<float>(st, gen_slots, eflag, vflag, N, x, q, nbr, cnt, geo, pairs, trips, nt, contrib,
+    e = mixed ? launch_gen_any<float>(st, gen_slots, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib,
                                       selfF, mask, work, nwork, nfast, force_gen_blocks(), gp, rs)
-              : launch_gen_any<double>(st, gen_slots, eflag, vflag, N, x, q, nbr, cnt, geo, pairs, trips, nt, contrib,
+              : launch_gen_any<double>(st, gen_slots, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib,
                                        selfF, mask, work, nwork, nfast, force_gen_blocks(), gp, rs);
     rows = nfast + force_gen_blocks();
   } else {
-    e = mixed ? launch_gen_any<float>(st, gen_slots, eflag, vflag, N, x, q, nbr, cnt, geo, pairs, trips, nt, contrib,
+    e = mixed ? launch_gen_any<float>(st, gen_slots, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib,
                                       selfF, mask, nullptr, nullptr, 0, 0, partial, rs)
-              : launch_gen_any<double>(st, gen_slots, eflag, vflag, N, x, q, nbr, cnt, geo, pairs, trips, nt, contrib,
+              : launch_gen_any<double>(st, gen_slots, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib,
                                        selfF, mask, nullptr, nullptr, 0, 0, partial, rs);
     const int T = mixed ? gen_threads<float>(gen_slots) : gen_threads<double>(gen_slots);
     rows = (N + T - 1) / T;

@@ -96,11 +96,12 @@ __device__ __forceinline__ double warp_sum_d(double v)
 // (type in w).  Positions are kept as given (not wrapped): every distance is a
 // minimum image, and an MD state copied out and back in reproduces the same
 // float64 values.  The fixed-point copy wraps by construction (mod 2^32).
-__global__ void k_ingest(int N, const double *__restrict__ pos, const int *__restrict__ types, int nt, Geom geo,
-                         dbl4 *__restrict__ x, int4 *__restrict__ q, RunState *rs)
+__global__ void k_ingest(int N, const double *__restrict__ pos, const int *__restrict__ types, int nt, int sid,
+                         const SysTab *__restrict__ sys, dbl4 *__restrict__ x, int4 *__restrict__ q, RunState *rs)
 {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
+  const Geom &geo = sys[sid].geo;
   int t = types[i];
   if (t < 0 || t >= nt) {
     atomicOr(&rs->status, ST_BAD_TYPE);
@@ -117,8 +118,9 @@ __global__ void k_ingest(int N, const double *__restrict__ pos, const int *__res
     p[a] = v;
     qq[a] = fixed_q(v, geo.to_q[a]);
   }
-  x[i] = make_dbl4(p[0], p[1], p[2], __longlong_as_double((long long)t));
-  q[i] = make_int4(qq[0], qq[1], qq[2], t);
+  const int w = make_w(t, sid);
+  x[i] = make_dbl4(p[0], p[1], p[2], __longlong_as_double((long long)w));
+  q[i] = make_int4(qq[0], qq[1], qq[2], w);
 }
 
 // AoS float64 velocities -> dbl4
@@ -158,31 +160,40 @@ template <class R, bool KE>
 __global__ void k_vv(int N, int mode, dbl4 *__restrict__ x, dbl4 *__restrict__ v, int4 *__restrict__ q,
                      const int4 *__restrict__ qref, const typename V4g<R>::type *__restrict__ contrib,
                      const typename V4g<R>::type *__restrict__ selfF, const unsigned long long *__restrict__ mask,
-                     const int *__restrict__ nbr, const int *__restrict__ rev, const double *__restrict__ kick,
-                     const double *__restrict__ mass, double dt, Geom geo, float disp2_lim, double *__restrict__ kepart,
-                     RunState *rs)
+                     const int *__restrict__ nbr, const int *__restrict__ rev, const SysTab *__restrict__ sys,
+                     const SysCtl *__restrict__ ctl, const double *__restrict__ mass, float disp2_lim,
+                     double *__restrict__ kepart, RunState *rs)
 {
   __shared__ double sw[8];
   if (rs->status != 0) return;
-  if (mode < 0) mode = rs->open ? (VV_FINISH | VV_START) : VV_START;   // uniform across the grid
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   bool active = i < N;
   double ke = 0.0;
   bool moved = false;
   if (active) {
     int4 qi = q[i];
-    const int t = qi.w;
-    const double c = kick[t];
+    const int t = type_of(qi.w);
+    const int sid = sys_of(qi.w);
+    const SysTab &T = sys[sid];
+    const Geom &geo = T.geo;
+    const double c = T.kick[t];
+    const double dt = T.dt;
+    int mode_i = mode;
+    if (mode_i < 0) {
+      // per-system step control: running, closing (last half kick pending) or done
+      const SysCtl C = ctl[sid];
+      mode_i = C.steps_left > 0 ? (C.open ? (VV_FINISH | VV_START) : VV_START) : (C.open ? VV_FINISH : 0);
+    }
     double fx, fy, fz;
     gather_force<R>(i, N, contrib, selfF, mask, nbr, rev, fx, fy, fz);
     dbl4 vi = v[i];
-    if (mode & VV_FINISH) {
+    if (mode_i & VV_FINISH) {
       vi.x = fma(c, fx, vi.x);
       vi.y = fma(c, fy, vi.y);
       vi.z = fma(c, fz, vi.z);
     }
     if (KE) ke = mass[t] * (vi.x * vi.x + vi.y * vi.y + vi.z * vi.z);
-    if (mode & VV_START) {
+    if (mode_i & VV_START) {
       vi.x = fma(c, fx, vi.x);
       vi.y = fma(c, fy, vi.y);
       vi.z = fma(c, fz, vi.z);
@@ -255,7 +266,7 @@ __global__ void k_extract(int N, const dbl4 *__restrict__ x, const dbl4 *__restr
 // End of an MD step: record (PE_k, KE_{k-1}) in the trace (row k = rs->trace_k),
 // roll the accumulators, count the step; inside a graph, decide whether the step
 // loop goes on.
-__global__ void k_step_end(RunState *rs, cudaGraphConditionalHandle loop, int use_cond)
+__global__ void k_step_end(RunState *rs, SysCtl *ctl, int nsys, cudaGraphConditionalHandle loop, int use_cond)
 {
   if (rs->status != 0) {
     if (use_cond) cudaGraphSetConditional(loop, 0);
@@ -275,8 +286,17 @@ __global__ void k_step_end(RunState *rs, cudaGraphConditionalHandle loop, int us
   rs->step += 1;
   rs->over_total = 0;
   rs->trace_k = k + 1;
-  rs->open = 1;
   rs->steps_left -= 1;
+  // per system: a running system counts its step; a closing one is now done
+  for (int s = 0; s < nsys; ++s) {
+    SysCtl &C = ctl[s];
+    if (C.steps_left > 0) {
+      C.steps_left -= 1;
+      C.open = 1;
+    } else if (C.open) {
+      C.open = 0;
+    }
+  }
   if (use_cond) cudaGraphSetConditional(loop, rs->steps_left > 0 ? 1u : 0u);
 }
 
@@ -292,27 +312,30 @@ __global__ void k_decide(RunState *rs, cudaGraphConditionalHandle build)
   cudaGraphSetConditional(build, (rs->status == 0 && rs->rebuild != 0) ? 1u : 0u);
 }
 
-// host-chosen controls of the next launch.  After a failure the launched steps do
-// not run; their count is added to the steps left so that recovery resumes them all.
-__global__ void k_set_control(RunState *rs, long long steps, double *trace, long long trace_k, int open)
+// Host-chosen controls of the next launch of a single system (system 0).  After a
+// failure the launched steps do not run; their count is added to the steps left
+// so that recovery resumes them all.
+__global__ void k_set_control(RunState *rs, SysCtl *ctl, long long steps, double *trace, long long trace_k, int open)
 {
   if (rs->status != 0) {
     rs->steps_left += steps;
+    ctl[0].steps_left += steps;
     return;
   }
   rs->steps_left = steps;
+  ctl[0].steps_left = steps;
+  ctl[0].open = open;
   rs->trace = trace;
   rs->trace_k = trace_k;
-  rs->open = open;
 }
 
-// after the closing half kick: KE of the last step (row trace_k - 1)
-__global__ void k_final(RunState *rs)
+// after the closing half kick of a single system: KE of the last step (row trace_k - 1)
+__global__ void k_final(RunState *rs, SysCtl *ctl)
 {
   if (rs->status != 0) return;
   if (rs->trace) rs->trace[2 * (rs->trace_k - 1) + 1] = 0.5 * rs->ekin2 / ACCEL;
   rs->ekin2 = 0.0;
-  rs->open = 0;
+  ctl[0].open = 0;
 }
 
 // after a standalone force evaluation: keep its energy as the current PE
@@ -327,26 +350,25 @@ __global__ void k_force_done(RunState *rs)
 
 cudaError_t launch_vv(cudaStream_t st, bool mixed, bool ke, int N, int mode, dbl4 *x, dbl4 *v, int4 *q,
                       const int4 *qref, const void *contrib, const void *selfF, const unsigned long long *mask,
-                      const int *nbr, const int *rev, const double *kick, const double *mass, double dt,
-                      const Geom &geo, float disp2_lim, double *kepart, RunState *rs)
+                      const int *nbr, const int *rev, const SysTab *sys, const SysCtl *ctl, const double *mass,
+                      float disp2_lim, double *kepart, RunState *rs)
 {
   if (N == 0) return cudaSuccess;
   const int T = 256, B = (N + T - 1) / T;
   if (mixed) {
     if (ke)
       k_vv<float, true><<<B, T, 0, st>>>(N, mode, x, v, q, qref, (const float4 *)contrib, (const float4 *)selfF,
-                                         mask, nbr, rev, kick, mass, dt, geo, disp2_lim, kepart, rs);
+                                         mask, nbr, rev, sys, ctl, mass, disp2_lim, kepart, rs);
     else
       k_vv<float, false><<<B, T, 0, st>>>(N, mode, x, v, q, qref, (const float4 *)contrib, (const float4 *)selfF,
-                                          mask, nbr, rev, kick, mass, dt, geo, disp2_lim, kepart, rs);
+                                          mask, nbr, rev, sys, ctl, mass, disp2_lim, kepart, rs);
   } else {
     if (ke)
       k_vv<double, true><<<B, T, 0, st>>>(N, mode, x, v, q, qref, (const dbl4 *)contrib, (const dbl4 *)selfF,
-                                          mask, nbr, rev, kick, mass, dt, geo, disp2_lim, kepart, rs);
+                                          mask, nbr, rev, sys, ctl, mass, disp2_lim, kepart, rs);
     else
-      k_vv<double, false><<<B, T, 0, st>>>(N, mode, x, v, q, qref, (const dbl4 *)contrib,
-                                           (const dbl4 *)selfF, mask, nbr, rev, kick, mass, dt, geo, disp2_lim,
-                                           kepart, rs);
+      k_vv<double, false><<<B, T, 0, st>>>(N, mode, x, v, q, qref, (const dbl4 *)contrib, (const dbl4 *)selfF,
+                                           mask, nbr, rev, sys, ctl, mass, disp2_lim, kepart, rs);
   }
   if (ke) k_ke_reduce<<<1, 256, 0, st>>>(kepart, B, rs);
   return cudaGetLastError();
@@ -372,11 +394,11 @@ cudaError_t launch_gather_out(cudaStream_t st, bool mixed, int N, const void *co
 
 namespace tsf {
 
-cudaError_t launch_ingest(cudaStream_t st, int N, const double *pos, const int *types, int nt, const Geom &geo,
-                          dbl4 *x, int4 *q, RunState *rs)
+cudaError_t launch_ingest(cudaStream_t st, int N, const double *pos, const int *types, int nt, int sid,
+                          const SysTab *sys, dbl4 *x, int4 *q, RunState *rs)
 {
   if (N == 0) return cudaSuccess;
-  k_ingest<<<(N + 255) / 256, 256, 0, st>>>(N, pos, types, nt, geo, x, q, rs);
+  k_ingest<<<(N + 255) / 256, 256, 0, st>>>(N, pos, types, nt, sid, sys, x, q, rs);
   return cudaGetLastError();
 }
 
@@ -394,9 +416,10 @@ cudaError_t launch_extract(cudaStream_t st, int N, const dbl4 *x, const dbl4 *v,
   return cudaGetLastError();
 }
 
-cudaError_t launch_step_end(cudaStream_t st, RunState *rs, cudaGraphConditionalHandle loop, int use_cond)
+cudaError_t launch_step_end(cudaStream_t st, RunState *rs, SysCtl *ctl, int nsys, cudaGraphConditionalHandle loop,
+                            int use_cond)
 {
-  k_step_end<<<1, 1, 0, st>>>(rs, loop, use_cond);
+  k_step_end<<<1, 1, 0, st>>>(rs, ctl, nsys, loop, use_cond);
   return cudaGetLastError();
 }
 
@@ -412,16 +435,16 @@ cudaError_t launch_decide(cudaStream_t st, RunState *rs, cudaGraphConditionalHan
   return cudaGetLastError();
 }
 
-cudaError_t launch_set_control(cudaStream_t st, RunState *rs, long long steps, double *trace, long long trace_k,
-                               int open)
+cudaError_t launch_set_control(cudaStream_t st, RunState *rs, SysCtl *ctl, long long steps, double *trace,
+                               long long trace_k, int open)
 {
-  k_set_control<<<1, 1, 0, st>>>(rs, steps, trace, trace_k, open);
+  k_set_control<<<1, 1, 0, st>>>(rs, ctl, steps, trace, trace_k, open);
   return cudaGetLastError();
 }
 
-cudaError_t launch_final(cudaStream_t st, RunState *rs)
+cudaError_t launch_final(cudaStream_t st, RunState *rs, SysCtl *ctl)
 {
-  k_final<<<1, 1, 0, st>>>(rs);
+  k_final<<<1, 1, 0, st>>>(rs, ctl);
   return cudaGetLastError();
 }
 

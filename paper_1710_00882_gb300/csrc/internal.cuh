@@ -76,7 +76,6 @@ struct RunState {
   double *trace;         // device trace [..][2] or null
   long long trace_k;     // trace row of the step in progress (1-based within a call)
   long long steps_left;  // steps still to run in the current graph launch
-  int open;              // velocities at the half step (a closing kick is pending)
   int over_total;        // atoms the register force kernel queued for the general kernel
 };
 
@@ -108,6 +107,31 @@ __device__ __forceinline__ float q_scaled(int dq, float s) { return __fmul_rn((f
 
 constexpr int ST_BAD_TYPE = 32;
 constexpr double ACCEL = 1.602176634e-19 / 1.66053906660e-27 * 1e-4;   // (eV/A)/amu in A/ps^2
+
+// Atom record word w (fixed-point q.w; bits of the float64 position's w): the
+// type in the low 3 bits, the system index above them (packed multi-system layouts).
+constexpr int TYPE_BITS = 3;
+__host__ __device__ __forceinline__ int type_of(int w) { return w & ((1 << TYPE_BITS) - 1); }
+__host__ __device__ __forceinline__ int sys_of(int w) { return (int)((unsigned)w >> TYPE_BITS); }
+__host__ __device__ __forceinline__ int make_w(int type, int sys) { return type | (sys << TYPE_BITS); }
+
+// Constant description of one system of a (possibly packed) layout.
+struct SysTab {
+  Geom geo;                 // its box
+  int nc[3];                // its cell grid
+  int cell_off;             // its first cell in the global cell numbering
+  int atom_off;             // its first atom
+  int natoms;
+  double dt;                // ps
+  double kick[MAX_TYPES];   // dt/2 * ACCEL / m per type
+};
+
+// Run control of one system (device-updated every step).
+struct SysCtl {
+  long long steps_left;     // steps this system still runs
+  int open;                 // velocities at the half step: a closing kick is pending
+  int pad;
+};
 
 struct CellGrid {
   int nc[3];

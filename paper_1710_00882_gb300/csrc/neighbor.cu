@@ -25,17 +25,21 @@ __device__ __forceinline__ int cell_coord(uint32_t qa, int nc)
   return (int)(((unsigned long long)qa * (unsigned long long)nc) >> 32);
 }
 
-__global__ void k_cell_count(int N, const int4 *__restrict__ q, CellGrid g, int *__restrict__ cell_of,
-                             int *__restrict__ rank, int *__restrict__ cell_count, const RunState *rs, int gated)
+// Each atom's cell in its own system's grid, numbered globally (system cell offset
+// + local cell), and its rank inside the cell.
+__global__ void k_cell_count(int N, const int4 *__restrict__ q, const SysTab *__restrict__ sys,
+                             int *__restrict__ cell_of, int *__restrict__ rank, int *__restrict__ cell_count,
+                             const RunState *rs, int gated)
 {
   if (skip_build(rs, gated)) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   int4 p = q[i];
-  int cx = cell_coord((uint32_t)p.x, g.nc[0]);
-  int cy = cell_coord((uint32_t)p.y, g.nc[1]);
-  int cz = cell_coord((uint32_t)p.z, g.nc[2]);
-  int c = (cz * g.nc[1] + cy) * g.nc[0] + cx;
+  const SysTab &T = sys[sys_of(p.w)];
+  int cx = cell_coord((uint32_t)p.x, T.nc[0]);
+  int cy = cell_coord((uint32_t)p.y, T.nc[1]);
+  int cz = cell_coord((uint32_t)p.z, T.nc[2]);
+  int c = T.cell_off + (cz * T.nc[1] + cy) * T.nc[0] + cx;
   cell_of[i] = c;
   rank[i] = atomicAdd(&cell_count[c], 1);
 }
@@ -187,10 +191,11 @@ __device__ __forceinline__ void sort_column(int *__restrict__ nbr, int N, int i,
 // their 27 stencil cells, so candidate loads hit L1): scan the stencil, keep j with
 // |d_ij| < r_list, then sort the column by j so that the list order depends only on
 // the set of neighbours.
-__global__ void __launch_bounds__(128) k_build(int N, const int4 *__restrict__ q, CellGrid g, Geom geo,
-                                               const int *__restrict__ cell_start, const int *__restrict__ cell_atoms,
-                                               int *__restrict__ nbr, int *__restrict__ cnt, int cap,
-                                               int4 *__restrict__ qref, RunState *rs, int gated)
+__global__ void __launch_bounds__(128) k_build(int N, const int4 *__restrict__ q, const SysTab *__restrict__ sys,
+                                               float rl2, const int *__restrict__ cell_start,
+                                               const int *__restrict__ cell_atoms, int *__restrict__ nbr,
+                                               int *__restrict__ cnt, int cap, int4 *__restrict__ qref, RunState *rs,
+                                               int gated)
 {
   __shared__ int sbuf[32][128];
   if (skip_build(rs, gated)) return;
@@ -199,6 +204,12 @@ __global__ void __launch_bounds__(128) k_build(int N, const int4 *__restrict__ q
   const int i = cell_atoms[t];
   const int4 pi = q[i];
   qref[i] = pi;
+  const SysTab &T = sys[sys_of(pi.w)];
+  const Geom &geo = T.geo;
+  CellGrid g;
+  g.nc[0] = T.nc[0]; g.nc[1] = T.nc[1]; g.nc[2] = T.nc[2];
+  g.rl2 = rl2;
+  const int coff = T.cell_off;
   int c[3] = {cell_coord((uint32_t)pi.x, g.nc[0]), cell_coord((uint32_t)pi.y, g.nc[1]),
               cell_coord((uint32_t)pi.z, g.nc[2])};
   int lo[3], nr[3];
@@ -212,7 +223,7 @@ __global__ void __launch_bounds__(128) k_build(int N, const int4 *__restrict__ q
       int cy = lo[1] + oy;
       cy += (cy < 0) ? g.nc[1] : 0;
       cy -= (cy >= g.nc[1]) ? g.nc[1] : 0;
-      const int row = (cz * g.nc[1] + cy) * g.nc[0];
+      const int row = coff + (cz * g.nc[1] + cy) * g.nc[0];
       for (int ox = 0; ox < nr[0]; ++ox) {
         int cx = lo[0] + ox;
         cx += (cx < 0) ? g.nc[0] : 0;
@@ -308,21 +319,21 @@ namespace tsf {
 // Enqueue one list build on st.  Buffers: cell_count[ncell] (zero on entry, zero
 // on exit), cell_start[ncell+1], tile_sums[ceil(ncell/SCAN_TILE)], cell_atoms[N],
 // cell_of[N], rank[N]; list nbr/rev [cap][N], cnt[N]; qref[N].
-cudaError_t launch_build(cudaStream_t st, int N, const int4 *q, const CellGrid &g, const Geom &geo, int *cell_count,
-                         int *cell_start, int *tile_sums, int *cell_atoms, int *cell_of, int *rank, int *nbr,
-                         int *rev, int *cnt, int cap, int4 *qref, RunState *rs, int gated)
+cudaError_t launch_build(cudaStream_t st, int N, const int4 *q, const SysTab *sys, int ncell, float rl2,
+                         int *cell_count, int *cell_start, int *tile_sums, int *cell_atoms, int *cell_of, int *rank,
+                         int *nbr, int *rev, int *cnt, int cap, int4 *qref, RunState *rs, int gated)
 {
   if (N == 0) return cudaSuccess;
   const int T = 256;
   const int BN = (N + T - 1) / T;
-  const int ntiles = (g.ncell + SCAN_TILE - 1) / SCAN_TILE;
-  k_cell_count<<<BN, T, 0, st>>>(N, q, g, cell_of, rank, cell_count, rs, gated);
-  k_scan_tiles<<<ntiles, SCAN_THREADS, 0, st>>>(g.ncell, cell_count, cell_start, tile_sums, rs, gated);
-  k_scan_sums<<<1, SCAN_THREADS, 0, st>>>(ntiles, tile_sums, cell_start + g.ncell, rs, gated);
-  k_scan_add<<<(g.ncell + T - 1) / T, T, 0, st>>>(g.ncell, cell_start, tile_sums, cell_count, rs, gated);
+  const int ntiles = (ncell + SCAN_TILE - 1) / SCAN_TILE;
+  k_cell_count<<<BN, T, 0, st>>>(N, q, sys, cell_of, rank, cell_count, rs, gated);
+  k_scan_tiles<<<ntiles, SCAN_THREADS, 0, st>>>(ncell, cell_count, cell_start, tile_sums, rs, gated);
+  k_scan_sums<<<1, SCAN_THREADS, 0, st>>>(ntiles, tile_sums, cell_start + ncell, rs, gated);
+  k_scan_add<<<(ncell + T - 1) / T, T, 0, st>>>(ncell, cell_start, tile_sums, cell_count, rs, gated);
   k_cell_fill<<<BN, T, 0, st>>>(N, cell_of, rank, cell_start, cell_atoms, rs, gated);
   const int BN128 = (N + 127) / 128;
-  k_build<<<BN128, 128, 0, st>>>(N, q, g, geo, cell_start, cell_atoms, nbr, cnt, cap, qref, rs, gated);
+  k_build<<<BN128, 128, 0, st>>>(N, q, sys, rl2, cell_start, cell_atoms, nbr, cnt, cap, qref, rs, gated);
   k_reverse<<<BN128, 128, 0, st>>>(N, nbr, cnt, rev, rs, gated);
   k_build_done<<<1, 1, 0, st>>>(rs, gated);
   return cudaGetLastError();

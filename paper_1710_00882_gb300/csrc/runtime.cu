@@ -20,29 +20,29 @@
 namespace tsf {
 
 // launchers defined in the kernel translation units
-cudaError_t launch_build(cudaStream_t, int, const int4 *, const CellGrid &, const Geom &, int *, int *, int *, int *,
+cudaError_t launch_build(cudaStream_t, int, const int4 *, const SysTab *, int, float, int *, int *, int *, int *,
                          int *, int *, int *, int *, int *, int, int4 *, RunState *, int);
 int scan_tiles_for(int ncell);
 int force_slots_for(int need);
 int force_partial_rows(int N);
 int vv_blocks(int N);
 cudaError_t launch_force(cudaStream_t, bool, int, bool, int, int, int, int, const dbl4 *, const int4 *, const int *,
-                         const int *, const Geom &, const void *, const void *, int, void *, void *,
+                         const int *, const SysTab *, const void *, const void *, int, void *, void *,
                          unsigned long long *, int *, int *, double *, RunState *);
 cudaError_t launch_vv(cudaStream_t, bool, bool, int, int, dbl4 *, dbl4 *, int4 *, const int4 *, const void *,
-                      const void *, const unsigned long long *, const int *, const int *, const double *,
-                      const double *, double, const Geom &, float, double *, RunState *);
+                      const void *, const unsigned long long *, const int *, const int *, const SysTab *,
+                      const SysCtl *, const double *, float, double *, RunState *);
 cudaError_t launch_gather_out(cudaStream_t, bool, int, const void *, const void *, const unsigned long long *,
                               const int *, const int *, double *, RunState *);
-cudaError_t launch_ingest(cudaStream_t, int, const double *, const int *, int, const Geom &, dbl4 *, int4 *,
+cudaError_t launch_ingest(cudaStream_t, int, const double *, const int *, int, int, const SysTab *, dbl4 *, int4 *,
                           RunState *);
 cudaError_t launch_ingest_vel(cudaStream_t, int, const double *, dbl4 *);
 cudaError_t launch_extract(cudaStream_t, int, const dbl4 *, const dbl4 *, double *, double *);
-cudaError_t launch_step_end(cudaStream_t, RunState *, cudaGraphConditionalHandle, int);
+cudaError_t launch_step_end(cudaStream_t, RunState *, SysCtl *, int, cudaGraphConditionalHandle, int);
 cudaError_t launch_loop_begin(cudaStream_t, RunState *, cudaGraphConditionalHandle);
 cudaError_t launch_decide(cudaStream_t, RunState *, cudaGraphConditionalHandle);
-cudaError_t launch_set_control(cudaStream_t, RunState *, long long, double *, long long, int);
-cudaError_t launch_final(cudaStream_t, RunState *);
+cudaError_t launch_set_control(cudaStream_t, RunState *, SysCtl *, long long, double *, long long, int);
+cudaError_t launch_final(cudaStream_t, RunState *, SysCtl *);
 cudaError_t launch_force_done(cudaStream_t, RunState *);
 
 // ---------------------------------------------------------------------------
@@ -107,6 +107,32 @@ int make_grid(const double box[3], double rl, CellGrid *g)
   return TERSOFF_OK;
 }
 
+// one-entry system table: allocate device storage
+bool sys_alloc(SysDev &S, int cap)
+{
+  if (S.tab && S.cap >= cap) return true;
+  if (S.tab) cudaFree(S.tab);
+  if (S.ctl) cudaFree(S.ctl);
+  S.tab = nullptr;
+  S.ctl = nullptr;
+  S.cap = 0;
+  if (cudaMalloc((void **)&S.tab, sizeof(SysTab) * cap) != cudaSuccess ||
+      cudaMalloc((void **)&S.ctl, sizeof(SysCtl) * cap) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  cudaMemset(S.ctl, 0, sizeof(SysCtl) * cap);
+  S.cap = cap;
+  return true;
+}
+
+void sys_free(SysDev &S)
+{
+  if (S.tab) cudaFree(S.tab);
+  if (S.ctl) cudaFree(S.ctl);
+  S = SysDev();
+}
+
 }  // namespace tsf
 
 using namespace tsf;
@@ -120,6 +146,7 @@ struct tersoff_ctx {
   bool own_stream = false;
   std::string err;
   AtomState cstate;        // scratch state of tersoff_compute
+  SysDev csys;             // its system table
   ListState clist;         // internal list of tersoff_compute when none is given
   RunState *crs = nullptr; // run state of tersoff_compute
   void *stage = nullptr;   // host-pointer staging (AoS positions/forces, types)
@@ -141,6 +168,7 @@ struct tersoff_params {
 
 struct tersoff_nlist {
   tersoff_ctx *ctx = nullptr;
+  SysDev sys;
   AtomState atoms;    // positions the list was built from
   ListState list;
   RunState *rs = nullptr;
@@ -161,6 +189,7 @@ struct tersoff_md {
   const tersoff_params *params = nullptr;
   AtomState atoms;
   ListState list;
+  SysDev sys;
   RunState *rs = nullptr;
   double *d_kick = nullptr;
   double *d_trace = nullptr;
@@ -320,7 +349,7 @@ int check_box(tersoff_ctx *ctx, const double box[3], double rl)
 // Host-visible list build from A.q: grows the capacity on overflow and sizes it to
 // the longest list plus headroom.
 int build_list_sync(tersoff_ctx *ctx, const AtomState &A, ListState &L, RunState *rs, const double box[3],
-                    double cutoff, double skin)
+                    double cutoff, double skin, SysDev &S)
 {
   const double rl = cutoff + skin;
   CKR(check_box(ctx, box, rl));
@@ -330,11 +359,18 @@ int build_list_sync(tersoff_ctx *ctx, const AtomState &A, ListState &L, RunState
   L.geo = make_geom(box);
   L.cutoff = cutoff;
   L.skin = skin;
+  // system 0 of the table: geometry and cell grid
+  S.host.geo = L.geo;
+  for (int a = 0; a < 3; ++a) S.host.nc[a] = g.nc[a];
+  S.host.cell_off = 0;
+  S.host.atom_off = 0;
+  S.host.natoms = (int)A.N;
+  CK(cudaMemcpyAsync(S.tab, &S.host, sizeof(SysTab), cudaMemcpyHostToDevice, ctx->stream));
   int cap = L.cap > 0 ? L.cap : MAX_CAP;
   for (int attempt = 0; attempt < 3; ++attempt) {
     CKR(ensure_list(ctx, L, A.N, cap, g.ncell));
     CK(cudaMemsetAsync(&rs->maxcount, 0, sizeof(int), ctx->stream));
-    CK(launch_build(ctx->stream, (int)A.N, A.q, L.grid, L.geo, L.cell_count, L.cell_start, L.tile_sums,
+    CK(launch_build(ctx->stream, (int)A.N, A.q, S.tab, g.ncell, g.rl2, L.cell_count, L.cell_start, L.tile_sums,
                     L.cell_atoms, L.cell_of, L.rank, L.nbr, L.rev, L.cnt, cap, L.qref, rs, 0));
     RunState h;
     CKR(read_rs(ctx, rs, &h));
@@ -363,9 +399,14 @@ int build_list_sync(tersoff_ctx *ctx, const AtomState &A, ListState &L, RunState
 
 // Copy AoS positions (+ types) into the device state; host or device pointers.
 int ingest(tersoff_ctx *ctx, AtomState &A, const double *pos, const int32_t *types, int64_t N, int nt,
-           const double box[3], bool dev, RunState *rs)
+           const double box[3], bool dev, RunState *rs, SysDev &S)
 {
   A.geo = make_geom(box);
+  if (!sys_alloc(S, 1)) return set_err(ctx, TERSOFF_ERR_NOMEM, "system table");
+  S.host.geo = A.geo;
+  S.host.atom_off = 0;
+  S.host.natoms = (int)N;
+  CK(cudaMemcpyAsync(S.tab, &S.host, sizeof(SysTab), cudaMemcpyHostToDevice, ctx->stream));
   if (N == 0) return TERSOFF_OK;
   const double *dpos = pos;
   const int *dtyp = types;
@@ -379,7 +420,7 @@ int ingest(tersoff_ctx *ctx, AtomState &A, const double *pos, const int32_t *typ
     dpos = sp;
     dtyp = st;
   }
-  CK(launch_ingest(ctx->stream, (int)N, dpos, dtyp, nt, A.geo, A.x, A.q, rs));
+  CK(launch_ingest(ctx->stream, (int)N, dpos, dtyp, nt, 0, S.tab, A.x, A.q, rs));
   return TERSOFF_OK;
 }
 
@@ -441,6 +482,7 @@ static void ctx_free(tersoff_ctx *ctx)
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   free_atoms(ctx->cstate);
+  sys_free(ctx->csys);
   free_list(ctx->clist);
   dfree(ctx->crs);
   dfree(ctx->stage);
@@ -624,8 +666,9 @@ int tersoff_neighbor_build(tersoff_ctx *ctx, const double *pos, int64_t N, const
       zeros.assign((size_t)N, 0);
       types = zeros.data();
     }
-    if (rc == TERSOFF_OK) rc = ingest(ctx, nl->atoms, pos, types, N, 1, box, flags & TERSOFF_DEVICE_PTRS, nl->rs);
-    if (rc == TERSOFF_OK) rc = build_list_sync(ctx, nl->atoms, nl->list, nl->rs, box, cutoff, skin);
+    if (rc == TERSOFF_OK)
+      rc = ingest(ctx, nl->atoms, pos, types, N, 1, box, flags & TERSOFF_DEVICE_PTRS, nl->rs, nl->sys);
+    if (rc == TERSOFF_OK) rc = build_list_sync(ctx, nl->atoms, nl->list, nl->rs, box, cutoff, skin, nl->sys);
     if (dz) {
       cudaStreamSynchronize(ctx->stream);
       cudaFree(dz);
@@ -644,6 +687,7 @@ void tersoff_nlist_destroy(tersoff_nlist *nl)
   if (!nl) return;
   if (nl->ctx) cudaStreamSynchronize(nl->ctx->stream);
   free_atoms(nl->atoms);
+  sys_free(nl->sys);
   free_list(nl->list);
   dfree(nl->rs);
   ctx_release(nl->ctx);
@@ -693,10 +737,10 @@ int tersoff_compute(tersoff_ctx *ctx, const double *pos, const int32_t *types, i
   CK(cudaMemsetAsync(rs, 0, sizeof(RunState), ctx->stream));
   CKR(ensure_atoms(ctx, A, N, false));
   CKR(check_box(ctx, box, P->rcmax));
-  CKR(ingest(ctx, A, pos, types, N, P->nt, box, dev, rs));
+  CKR(ingest(ctx, A, pos, types, N, P->nt, box, dev, rs, ctx->csys));
   const ListState *L = nl ? &nl->list : nullptr;
   if (!L) {
-    CKR(build_list_sync(ctx, A, ctx->clist, rs, box, P->rcmax, 0.0));
+    CKR(build_list_sync(ctx, A, ctx->clist, rs, box, P->rcmax, 0.0, ctx->csys));
     L = &ctx->clist;
   } else {
     for (int a = 0; a < 3; ++a)
@@ -706,7 +750,7 @@ int tersoff_compute(tersoff_ctx *ctx, const double *pos, const int32_t *types, i
   const int gen_slots = force_slots_for(std::max(1, L->maxcount));
   const int fast_slots = (P->sym_angular && !ctx->general_only) ? (L->maxcount <= 4 ? 4 : 8) : 0;
   CK(launch_force(ctx->stream, mixed, fast_slots, P->nt == 1, gen_slots, 1, virial != nullptr, (int)N, A.x, A.q,
-                  L->nbr, L->cnt, A.geo, mixed ? P->pair_f : P->pair_d, mixed ? P->trip_f : P->trip_d, P->nt,
+                  L->nbr, L->cnt, ctx->csys.tab, mixed ? P->pair_f : P->pair_d, mixed ? P->trip_f : P->trip_d, P->nt,
                   A.contrib, A.selfF, A.mask, A.work, A.nwork, A.partial, rs));
   double *dF = nullptr;
   if (forces) {
@@ -774,7 +818,7 @@ static int md_force(tersoff_md *md, cudaStream_t st, int eflag)
   tersoff_ctx *ctx = md->ctx;
   const tersoff_params *P = md->params;
   CK(launch_force(st, md->mixed, md->fast_slots, P->nt == 1, md->gen_slots, eflag, 0, (int)md->atoms.N, md->atoms.x,
-                  md->atoms.q, md->list.nbr, md->list.cnt, md->atoms.geo, md->mixed ? P->pair_f : P->pair_d,
+                  md->atoms.q, md->list.nbr, md->list.cnt, md->sys.tab, md->mixed ? P->pair_f : P->pair_d,
                   md->mixed ? P->trip_f : P->trip_d, P->nt, md->atoms.contrib, md->atoms.selfF, md->atoms.mask,
                   md->atoms.work, md->atoms.nwork, md->atoms.partial, md->rs));
   return TERSOFF_OK;
@@ -786,8 +830,8 @@ static int md_vv(tersoff_md *md, cudaStream_t st, int mode, bool ke)
   tersoff_ctx *ctx = md->ctx;
   const float lim = (float)(0.25 * md->skin * md->skin);
   CK(launch_vv(st, md->mixed, ke, (int)md->atoms.N, mode, md->atoms.x, md->atoms.v, md->atoms.q, md->list.qref,
-               md->atoms.contrib, md->atoms.selfF, md->atoms.mask, md->list.nbr, md->list.rev, md->d_kick,
-               md->params->d_mass, md->dt, md->atoms.geo, lim, md->atoms.kepart, md->rs));
+               md->atoms.contrib, md->atoms.selfF, md->atoms.mask, md->list.nbr, md->list.rev, md->sys.tab,
+               md->sys.ctl, md->params->d_mass, lim, md->atoms.kepart, md->rs));
   return TERSOFF_OK;
 }
 
@@ -795,7 +839,8 @@ static int md_build(tersoff_md *md, cudaStream_t st, int gated)
 {
   tersoff_ctx *ctx = md->ctx;
   ListState &L = md->list;
-  CK(launch_build(st, (int)md->atoms.N, md->atoms.q, L.grid, L.geo, L.cell_count, L.cell_start, L.tile_sums,
+  CK(launch_build(st, (int)md->atoms.N, md->atoms.q, md->sys.tab, L.grid.ncell, L.grid.rl2, L.cell_count,
+                  L.cell_start, L.tile_sums,
                   L.cell_atoms, L.cell_of, L.rank, L.nbr, L.rev, L.cnt, L.cap, L.qref, md->rs, gated));
   return TERSOFF_OK;
 }
@@ -857,7 +902,7 @@ static int md_graph_build(tersoff_md *md, int which)
   CK(cudaGraphAddNode(&inode, body, deps, edges, nd, &ip));
   CK(cudaStreamUpdateCaptureDependencies(st, &inode, nullptr, 1, cudaStreamSetCaptureDependencies));
   CKR(md_force(md, st, tr ? 1 : 0));
-  CK(launch_step_end(st, md->rs, hloop, 1));
+  CK(launch_step_end(st, md->rs, md->sys.ctl, 1, hloop, 1));
   cudaGraph_t bodyc = body;
   CK(cudaStreamEndCapture(st, &bodyc));
 
@@ -880,7 +925,7 @@ static int md_launch_steps(tersoff_md *md, long long n, double *d_trace, long lo
   cudaStream_t st = ctx->stream;
   if (n <= 0) return TERSOFF_OK;
   const bool tr = d_trace != nullptr;
-  CK(launch_set_control(st, md->rs, n, d_trace, k0, md->open ? 1 : 0));
+  CK(launch_set_control(st, md->rs, md->sys.ctl, n, d_trace, k0, md->open ? 1 : 0));
   if (!md->prof && md->use_graphs) {
     MdGraph &G = md->graph[tr ? 1 : 0];
     if (!G.valid) {
@@ -910,7 +955,7 @@ static int md_launch_steps(tersoff_md *md, long long n, double *d_trace, long lo
     CKR(md_force(md, st, tr ? 1 : 0));
     md_mark_end(md, 2, b, 2 + (tr ? 1 : 0));
     b = md_mark_begin(md);
-    CK(launch_step_end(st, md->rs, 0, 0));
+    CK(launch_step_end(st, md->rs, md->sys.ctl, 1, 0, 0));
     md_mark_end(md, 3, b, 1);
   }
   md->open = true;
@@ -943,7 +988,7 @@ static int md_recover(tersoff_md *md, const RunState &h, double *d_trace)
   }
   CK(cudaMemsetAsync(&md->rs->epot, 0, sizeof(double), st));
   CKR(md_force(md, st, d_trace ? 1 : 0));
-  CK(launch_step_end(st, md->rs, 0, 0));
+  CK(launch_step_end(st, md->rs, md->sys.ctl, 1, 0, 0));
   const long long rest = h.steps_left - 1;
   if (rest > 0) CKR(md_launch_steps(md, rest, d_trace, h.trace_k + 1));
   return TERSOFF_OK;
@@ -956,7 +1001,7 @@ static int md_finish(tersoff_md *md, double *d_trace, bool close)
   for (int attempt = 0; attempt < 8; ++attempt) {
     if (close && md->open) {
       CKR(md_vv(md, ctx->stream, 1, d_trace != nullptr));
-      CK(launch_final(ctx->stream, md->rs));
+      CK(launch_final(ctx->stream, md->rs, md->sys.ctl));
     }
     RunState h;
     CKR(read_rs(ctx, md->rs, &h));
@@ -997,7 +1042,8 @@ int tersoff_md_create(tersoff_ctx *ctx, const double *pos, const double *vel, co
   if (rc != TERSOFF_OK) return fail(rc);
   if ((rc = ensure_atoms(ctx, md->atoms, N, true)) != TERSOFF_OK) return fail(rc);
   if ((rc = check_box(ctx, box, P->rcmax + skin)) != TERSOFF_OK) return fail(rc);
-  if ((rc = ingest(ctx, md->atoms, pos, types, N, P->nt, box, flags & TERSOFF_DEVICE_PTRS, md->rs)) != TERSOFF_OK)
+  if ((rc = ingest(ctx, md->atoms, pos, types, N, P->nt, box, flags & TERSOFF_DEVICE_PTRS, md->rs, md->sys)) !=
+      TERSOFF_OK)
     return fail(rc);
   if (N > 0) {
     const double *dvel = vel;
@@ -1016,7 +1062,10 @@ int tersoff_md_create(tersoff_ctx *ctx, const double *pos, const double *vel, co
   for (int a = 0; a < P->nt; ++a) kick[a] = 0.5 * dt_ps * ACCEL / P->masses[a];
   if (cudaMalloc((void **)&md->d_kick, sizeof kick) != cudaSuccess) return fail(set_err(ctx, TERSOFF_ERR_NOMEM, "kick"));
   cudaMemcpy(md->d_kick, kick, sizeof kick, cudaMemcpyHostToDevice);
-  if ((rc = build_list_sync(ctx, md->atoms, md->list, md->rs, box, P->rcmax, skin)) != TERSOFF_OK) return fail(rc);
+  md->sys.host.dt = dt_ps;
+  for (int a = 0; a < MAX_TYPES; ++a) md->sys.host.kick[a] = a < P->nt ? 0.5 * dt_ps * ACCEL / P->masses[a] : 0.0;
+  if ((rc = build_list_sync(ctx, md->atoms, md->list, md->rs, box, P->rcmax, skin, md->sys)) != TERSOFF_OK)
+    return fail(rc);
   if ((rc = ensure_scatter(ctx, md->atoms, N, md->list.cap, md->mixed)) != TERSOFF_OK) return fail(rc);
   md->gen_slots = force_slots_for(std::max(1, md->list.maxcount));
   md->fast_slots = (P->sym_angular && !ctx->general_only) ? 8 : 0;
@@ -1189,6 +1238,7 @@ void tersoff_md_destroy(tersoff_md *md)
   if (md->cap_stream) cudaStreamDestroy(md->cap_stream);
   for (auto e : md->ev_pool) cudaEventDestroy(e);
   free_atoms(md->atoms);
+  sys_free(md->sys);
   free_list(md->list);
   dfree(md->rs);
   dfree(md->d_kick);

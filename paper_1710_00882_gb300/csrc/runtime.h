@@ -41,4 +41,13 @@ struct ListState {
          cell_atoms_b = 0, cell_of_b = 0, rank_b = 0;
 };
 
+// One system's device-side table and run control (the single-system paths use
+// system 0 of a one-entry table; packed layouts use many).
+struct SysDev {
+  SysTab host{};            // host copy of the table entries
+  SysTab *tab = nullptr;    // device [cap]
+  SysCtl *ctl = nullptr;    // device [cap]
+  int cap = 0;
+};
+
 }  // namespace tsf
