@@ -275,9 +275,70 @@ def run_gpu(args, ws, rank, local):
     }
     if e2e:
         line["e2e"] = e2e
+    if args.serving_jobs > 0:
+        md_mix = md_64 = None
+        line["serving"] = serving_bench(ctx, args.serving_jobs)
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args, s, quick=True)
     return line
+
+
+def serving_bench(ctx, njobs, budget_gb=4.0, max_slots=512, chunk=25):
+    """Continuous-batching server on the 4096-job stream (Si or SiC 50/50, 64-16,384
+    atoms log-uniform, 50-500 steps, mixed precision): closed loop (all jobs queued at
+    once) for the batch throughput, then Poisson arrivals at 0.5, 0.7 and 0.9 of that
+    job rate.  Latency is submission -> result on the library's clock; throughput is
+    the jobs' atom-steps over the time from the first submission to the last result."""
+    from paper_1710_00882_gb300 import params as pp
+    from paper_1710_00882_gb300 import tersoff as T
+    from paper_1710_00882_gb300 import workloads as wl
+
+    t_gen = time.perf_counter()
+    jobs = wl.serving_stream(njobs, seed=5)
+    t_gen = time.perf_counter() - t_gen
+    tab, masses = pp.for_species(("Si", "C"))
+    P = T.Params(ctx, tab, masses)
+    work = sum(j.system.n * j.steps for j in jobs)
+
+    def run(arrivals):
+        srv = T.Server(ctx, P, prec=T.MIXED, skin=SKIN, budget_bytes=int(budget_gb * 2**30), max_slots=max_slots,
+                       chunk_steps=chunk)
+        ids = []
+        t0 = time.perf_counter()
+        for j, ta in zip(jobs, arrivals):
+            d = t0 + ta - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            s = j.system
+            ids.append(srv.submit(s.pos, s.vel, s.types, s.box, j.dt, j.steps))
+        lat = []
+        for jid in ids:
+            assert srv.wait(jid, timeout=600.0)
+            lat.append(srv.result(jid)[3][2])
+        t1 = time.perf_counter()
+        st = srv.stats()
+        srv.close()
+        lat = np.array(lat)
+        return {"atom_steps_per_s": work / (t1 - t0), "seconds": t1 - t0,
+                "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
+                "chunks": st["chunks"], "repacks": st["repacks"], "busy_s": st["busy_s"],
+                "capacity_atoms": st["capacity_atoms"]}
+
+    closed = run(np.zeros(len(jobs)))
+    rate_closed = len(jobs) / closed["seconds"]
+    out = {"workload": f"{len(jobs)} jobs: Si or SiC 50/50, 64-16,384 atoms log-uniform, 5% vacancies, "
+                       "T ~ U(300, 2000) K, 50-500 steps, dt 1 fs (Si) / 0.5 fs (SiC), seed 5",
+           "precision": "mixed", "atom_steps": work, "server": {"budget_gb": budget_gb, "max_slots": max_slots,
+                                                                   "chunk_steps": chunk, "skin": SKIN},
+           "closed_loop": closed, "closed_loop_jobs_per_s": rate_closed, "poisson": {},
+           "stream_generation_s": t_gen}
+    rng = np.random.default_rng(55)
+    for f in (0.5, 0.7, 0.9):
+        lam = f * rate_closed
+        arr = np.cumsum(rng.exponential(1.0 / lam, size=len(jobs)))
+        arr -= arr[0]
+        out["poisson"][f"{f:.1f}"] = dict(run(arr), rate_jobs_per_s=lam)
+    return out
 
 
 def cpu_baseline(args, s=None, quick=True, steps=None):
@@ -324,6 +385,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--serving-jobs", type=int, default=4096, help="jobs of the serving stream (0: skip serving)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     ws, rank, local = dist_setup()

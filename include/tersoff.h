@@ -174,6 +174,67 @@ int tersoff_md_run(tersoff_ctx *ctx, double *pos, double *vel, const int32_t *ty
                    const double box[3], const tersoff_params *params, double dt_ps, int64_t nsteps, double skin,
                    tersoff_precision prec, int flags, double *energy_trace);
 
+/* ---- serving: continuous batching of MD jobs ---------------------------------
+ * A server runs many independent NVE jobs (periodic boxes of any size, each with
+ * its own dt and step count) on one GPU.  Admitted jobs live in one packed
+ * device layout (atoms, neighbour lists and cells of all jobs in contiguous
+ * per-job ranges); every kernel of a step covers all of them in one launch, and
+ * chunks of steps run as one CUDA graph launch.  A scheduler thread owned by the
+ * server retires finished jobs and admits queued ones at chunk boundaries, as
+ * slots and the device-memory budget allow (continuous batching): requests that
+ * arrive while others run join the next chunk.  A job's trajectory does not
+ * depend on the other jobs in the batch (same arithmetic, same order): its result
+ * is bitwise the same alone and in any mix.
+ *
+ * params: shared by all jobs (job types index into it).  prec: precision of all
+ * jobs.  skin: Verlet skin (A).  device_mem_budget: bytes the packed layout may
+ * use; it fixes the largest number of resident atoms.  max_slots: largest number
+ * of resident jobs (1..4096).  chunk_steps: steps between scheduling points.
+ * The server uses the context's device with its own stream and thread and holds a
+ * reference to the context.  The paper evaluates one system per process; the
+ * packed layout applies the same per-atom work (Algorithm 1, Eqs. 1-3) to many
+ * systems at once. */
+typedef struct {
+  int64_t n_atoms;
+  const double *pos;     /* [n][3] A (host) */
+  const double *vel;     /* [n][3] A/ps (host) */
+  const int32_t *types;  /* [n] (host) */
+  double box[3];         /* A */
+  double dt_ps;
+  int64_t nsteps;
+} tersoff_job;
+
+typedef struct {
+  int64_t submitted, admitted, completed, failed, queued, running;
+  int64_t atom_steps;    /* atom-steps of completed work */
+  int64_t chunks, repacks;
+  double busy_s;         /* wall time with jobs resident */
+  int64_t capacity_atoms;
+} tersoff_server_stats;
+
+int tersoff_server_create(tersoff_ctx *ctx, const tersoff_params *params, tersoff_precision prec, double skin,
+                          size_t device_mem_budget, int max_slots, int chunk_steps, tersoff_server **out);
+/* Copies the job's inputs and queues it.  TERSOFF_ERR_NOMEM: the job can never
+ * fit the budget; TERSOFF_ERR_ARG: bad job; TERSOFF_ERR_BOX_TOO_SMALL. */
+int tersoff_server_submit(tersoff_server *s, const tersoff_job *job, uint64_t *job_id);
+/* *done = 1 when the job finished (or failed). */
+int tersoff_server_poll(tersoff_server *s, uint64_t job_id, int *done);
+/* Blocks until the job finished; TERSOFF_ERR_TIMEOUT after timeout_s seconds. */
+int tersoff_server_wait(tersoff_server *s, uint64_t job_id, double timeout_s);
+/* Results of a finished job (any pointer may be NULL): final positions and
+ * velocities [n][3], energy[2] = (potential, kinetic) eV, times[3] = seconds from
+ * submission to admission, from admission to completion, and in total.  Releases
+ * the job. */
+int tersoff_server_result(tersoff_server *s, uint64_t job_id, double *pos, double *vel, double energy[2],
+                          double times[3]);
+int tersoff_server_get_stats(tersoff_server *s, tersoff_server_stats *out);
+/* Why the last rejected submission or the last failed batch failed (valid until
+ * the next call on this server). */
+const char *tersoff_server_last_error(tersoff_server *s);
+/* Stops the scheduler after the chunk of steps in flight; unfinished and queued
+ * jobs are dropped. */
+void tersoff_server_destroy(tersoff_server *s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -226,7 +226,7 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
             const TripP<R> *__restrict__ gtrips, int nt, typename V4t<R>::type *__restrict__ contrib,
             typename V4t<R>::type *__restrict__ selfF, unsigned long long *__restrict__ mask,
             int *__restrict__ work, int *__restrict__ nwork, double *__restrict__ partial, RunState *rs,
-            int allow_direct)
+            int allow_direct, double *__restrict__ eatom)
 {
   using M = typename MathOf<R>::M;
   using V4 = typename V4t<R>::type;
@@ -527,6 +527,7 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
     c.x = fix; c.y = fiy; c.z = fiz; c.w = R(0);
     selfF[i] = c;
     mask[i] = mb;
+    if (eatom) eatom[i] = (double)e_i;
   }
   if (EFLAG || VFLAG) block_partial<R, T>(red, EFLAG, VFLAG, partial + (size_t)blockIdx.x * 8);
 }
@@ -555,7 +556,7 @@ k_force_gen(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
             const TripP<R> *__restrict__ gtrips, int nt, typename V4t<R>::type *__restrict__ contrib,
             typename V4t<R>::type *__restrict__ selfF, unsigned long long *__restrict__ mask,
             const int *__restrict__ work, const int *__restrict__ nwork, int nfast, double *__restrict__ partial,
-            RunState *rs)
+            RunState *rs, double *__restrict__ eatom)
 {
   using M = typename MathOf<R>::M;
   using V4 = typename V4t<R>::type;
@@ -673,6 +674,7 @@ k_force_gen(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
       }
 
       // first K loop and pair terms
+      R e_atom = R(0);
       for (int a = 0; a < nc; ++a) {
         const int tj = META(a) >> 8;
         const R uax = SLOT(S_UX, a), uay = SLOT(S_UY, a), uaz = SLOT(S_UZ, a), ra = SLOT(S_R, a);
@@ -701,6 +703,7 @@ k_force_gen(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
         bond_order<M>(zeta, P, bij, dbij);
         const R pr = fR + bij * fA;
         red[0] += R(0.5) * fcv * pr;
+        e_atom += R(0.5) * fcv * pr;
         const R dvdr = R(0.5) * (dfcv * pr + fcv * (-P.lam1 * fR - bij * P.lam2 * fA));
         SLOT(S_DZ, a) = R(0.5) * fcv * fA * dbij;
         SLOT(S_FX, a) = -dvdr * uax;
@@ -782,6 +785,7 @@ k_force_gen(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
       c.x = fix; c.y = fiy; c.z = fiz; c.w = R(0);
       selfF[i] = c;
       mask[i] = mbits;
+      if (eatom) eatom[i] = (double)e_atom;
     }
   }
   if (overflow) atomicOr(&rs->status, ST_NC_OVERFLOW);
@@ -827,7 +831,7 @@ template <class R, int MAXNC, bool EFLAG, bool VFLAG>
 static cudaError_t launch_gen_t(cudaStream_t st, int N, const dbl4 *x, const int4 *q, const int *nbr, const int *cnt,
                                 const SysTab *sys, const void *pairs, const void *trips, int nt, void *contrib,
                                 void *selfF, unsigned long long *mask, const int *work, const int *nwork, int nfast,
-                                int gen_blocks, double *partial, RunState *rs)
+                                int gen_blocks, double *partial, RunState *rs, double *eatom)
 {
   using C = GenCfg<R, MAXNC>;
   const size_t smem = sizeof(PairP<R>) * MAX_TYPES * MAX_TYPES + sizeof(TripP<R>) * MAX_TYPES * MAX_TYPES * MAX_TYPES +
@@ -843,7 +847,7 @@ static cudaError_t launch_gen_t(cudaStream_t st, int N, const dbl4 *x, const int
   const int blocks = work ? gen_blocks : (N + C::threads - 1) / C::threads;
   kern<<<blocks, C::threads, smem, st>>>(N, x, q, nbr, cnt, sys, (const PairP<R> *)pairs, (const TripP<R> *)trips,
                                          nt, (typename V4t<R>::type *)contrib, (typename V4t<R>::type *)selfF, mask,
-                                         work, nwork, nfast, partial, rs);
+                                         work, nwork, nfast, partial, rs, eatom);
   return cudaGetLastError();
 }
 
@@ -851,16 +855,17 @@ template <class R, int MAXNC>
 static cudaError_t launch_gen(cudaStream_t st, int eflag, int vflag, int N, const dbl4 *x, const int4 *q,
                               const int *nbr, const int *cnt, const SysTab *sys, const void *pairs, const void *trips,
                               int nt, void *contrib, void *selfF, unsigned long long *mask, const int *work,
-                              const int *nwork, int nfast, int gen_blocks, double *partial, RunState *rs)
+                              const int *nwork, int nfast, int gen_blocks, double *partial, RunState *rs,
+                              double *eatom)
 {
   if (vflag)
     return launch_gen_t<R, MAXNC, true, true>(st, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib, selfF, mask, work,
-                                              nwork, nfast, gen_blocks, partial, rs);
+                                              nwork, nfast, gen_blocks, partial, rs, eatom);
   if (eflag)
     return launch_gen_t<R, MAXNC, true, false>(st, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib, selfF, mask,
-                                               work, nwork, nfast, gen_blocks, partial, rs);
+                                               work, nwork, nfast, gen_blocks, partial, rs, eatom);
   return launch_gen_t<R, MAXNC, false, false>(st, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib, selfF, mask,
-                                              work, nwork, nfast, gen_blocks, partial, rs);
+                                              work, nwork, nfast, gen_blocks, partial, rs, eatom);
 }
 
 template <class R>
@@ -879,12 +884,12 @@ static cudaError_t launch_gen_any(cudaStream_t st, int slots, int eflag, int vfl
                                   const int4 *q, const int *nbr, const int *cnt, const SysTab *sys, const void *pairs,
                                   const void *trips, int nt, void *contrib, void *selfF, unsigned long long *mask,
                                   const int *work, const int *nwork, int nfast, int gen_blocks, double *partial,
-                                  RunState *rs)
+                                  RunState *rs, double *eatom)
 {
 #define TSF_GEN(NC)                                                                                                \
   case NC:                                                                                                         \
     return launch_gen<R, NC>(st, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib, selfF, mask, work, \
-                             nwork, nfast, gen_blocks, partial, rs);
+                             nwork, nfast, gen_blocks, partial, rs, eatom);
   switch (slots) {
     TSF_GEN(8)
     TSF_GEN(16)
@@ -899,7 +904,7 @@ template <class R, int MAXNC, bool ONE>
 static cudaError_t launch_reg(cudaStream_t st, int eflag, int vflag, int N, const dbl4 *x, const int4 *q,
                               const int *nbr, const int *cnt, const SysTab *sys, const void *pairs, const void *trips,
                               int nt, void *contrib, void *selfF, unsigned long long *mask, int *work, int *nwork,
-                              double *partial, RunState *rs)
+                              double *partial, RunState *rs, double *eatom)
 {
   const int blocks = (N + FAST_THREADS - 1) / FAST_THREADS;
   using P = const PairP<R> *;
@@ -908,15 +913,15 @@ static cudaError_t launch_reg(cudaStream_t st, int eflag, int vflag, int N, cons
   if (vflag)
     k_force_reg<R, MAXNC, ONE, true, true><<<blocks, FAST_THREADS, 0, st>>>(
         N, x, q, nbr, cnt, sys, (P)pairs, (Tt)trips, nt, (V)contrib, (V)selfF, mask, work, nwork, partial, rs,
-        g_allow_direct);
+        g_allow_direct, eatom);
   else if (eflag)
     k_force_reg<R, MAXNC, ONE, true, false><<<blocks, FAST_THREADS, 0, st>>>(
         N, x, q, nbr, cnt, sys, (P)pairs, (Tt)trips, nt, (V)contrib, (V)selfF, mask, work, nwork, partial, rs,
-        g_allow_direct);
+        g_allow_direct, eatom);
   else
     k_force_reg<R, MAXNC, ONE, false, false><<<blocks, FAST_THREADS, 0, st>>>(
         N, x, q, nbr, cnt, sys, (P)pairs, (Tt)trips, nt, (V)contrib, (V)selfF, mask, work, nwork, partial, rs,
-        g_allow_direct);
+        g_allow_direct, eatom);
   return cudaGetLastError();
 }
 
@@ -941,7 +946,8 @@ int force_partial_rows(int N) { return (N + 31) / 32 + force_gen_blocks(); }
 cudaError_t launch_force(cudaStream_t st, bool mixed, int fast_slots, bool one_type, int gen_slots, int eflag,
                          int vflag, int N, const dbl4 *x, const int4 *q, const int *nbr, const int *cnt,
                          const SysTab *sys, const void *pairs, const void *trips, int nt, void *contrib, void *selfF,
-                         unsigned long long *mask, int *work, int *nwork, double *partial, RunState *rs)
+                         unsigned long long *mask, int *work, int *nwork, double *partial, RunState *rs,
+                         double *eatom)
 {
   if (N == 0) return cudaSuccess;
   const int nfast = (N + FAST_THREADS - 1) / FAST_THREADS;
@@ -950,9 +956,9 @@ cudaError_t launch_force(cudaStream_t st, bool mixed, int fast_slots, bool one_t
   if (fast_slots > 0) {
 #define TSF_REG(R, NC)                                                                                              \
   e = one_type ? launch_reg<R, NC, true>(st, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib, selfF, \
-                                         mask, work, nwork, partial, rs)                                            \
+                                         mask, work, nwork, partial, rs, eatom)                                     \
                : launch_reg<R, NC, false>(st, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib,      \
-                                          selfF, mask, work, nwork, partial, rs);
+                                          selfF, mask, work, nwork, partial, rs, eatom);
     if (mixed) {
       if (fast_slots <= 4) { TSF_REG(float, 4) } else { TSF_REG(float, 8) }
     } else {
@@ -962,15 +968,15 @@ cudaError_t launch_force(cudaStream_t st, bool mixed, int fast_slots, bool one_t
     if (e != cudaSuccess) return e;
     double *gp = partial + (size_t)nfast * 8;
     e = mixed ? launch_gen_any<float>(st, gen_slots, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib,
-                                      selfF, mask, work, nwork, nfast, force_gen_blocks(), gp, rs)
+                                      selfF, mask, work, nwork, nfast, force_gen_blocks(), gp, rs, eatom)
               : launch_gen_any<double>(st, gen_slots, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib,
-                                       selfF, mask, work, nwork, nfast, force_gen_blocks(), gp, rs);
+                                       selfF, mask, work, nwork, nfast, force_gen_blocks(), gp, rs, eatom);
     rows = nfast + force_gen_blocks();
   } else {
     e = mixed ? launch_gen_any<float>(st, gen_slots, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib,
-                                      selfF, mask, nullptr, nullptr, 0, 0, partial, rs)
+                                      selfF, mask, nullptr, nullptr, 0, 0, partial, rs, eatom)
               : launch_gen_any<double>(st, gen_slots, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib,
-                                       selfF, mask, nullptr, nullptr, 0, 0, partial, rs);
+                                       selfF, mask, nullptr, nullptr, 0, 0, partial, rs, eatom);
     const int T = mixed ? gen_threads<float>(gen_slots) : gen_threads<double>(gen_slots);
     rows = (N + T - 1) / T;
   }

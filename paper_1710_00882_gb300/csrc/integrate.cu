@@ -265,13 +265,25 @@ __global__ void k_extract(int N, const dbl4 *__restrict__ x, const dbl4 *__restr
 
 // End of an MD step: record (PE_k, KE_{k-1}) in the trace (row k = rs->trace_k),
 // roll the accumulators, count the step; inside a graph, decide whether the step
-// loop goes on.
+// loop goes on.  One block: thread 0 rolls the run state, all threads update the
+// per-system step control.
 __global__ void k_step_end(RunState *rs, SysCtl *ctl, int nsys, cudaGraphConditionalHandle loop, int use_cond)
 {
   if (rs->status != 0) {
-    if (use_cond) cudaGraphSetConditional(loop, 0);
+    if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(loop, 0);
     return;
   }
+  // per system: a running system counts its step; a closing one is now done
+  for (int s = threadIdx.x; s < nsys; s += blockDim.x) {
+    SysCtl &C = ctl[s];
+    if (C.steps_left > 0) {
+      C.steps_left -= 1;
+      C.open = 1;
+    } else if (C.open) {
+      C.open = 0;
+    }
+  }
+  if (threadIdx.x != 0) return;
   const long long k = rs->trace_k;
   double *trace = rs->trace;
   if (trace) {
@@ -287,16 +299,6 @@ __global__ void k_step_end(RunState *rs, SysCtl *ctl, int nsys, cudaGraphConditi
   rs->over_total = 0;
   rs->trace_k = k + 1;
   rs->steps_left -= 1;
-  // per system: a running system counts its step; a closing one is now done
-  for (int s = 0; s < nsys; ++s) {
-    SysCtl &C = ctl[s];
-    if (C.steps_left > 0) {
-      C.steps_left -= 1;
-      C.open = 1;
-    } else if (C.open) {
-      C.open = 0;
-    }
-  }
   if (use_cond) cudaGraphSetConditional(loop, rs->steps_left > 0 ? 1u : 0u);
 }
 
@@ -419,7 +421,7 @@ cudaError_t launch_extract(cudaStream_t st, int N, const dbl4 *x, const dbl4 *v,
 cudaError_t launch_step_end(cudaStream_t st, RunState *rs, SysCtl *ctl, int nsys, cudaGraphConditionalHandle loop,
                             int use_cond)
 {
-  k_step_end<<<1, 1, 0, st>>>(rs, ctl, nsys, loop, use_cond);
+  k_step_end<<<1, nsys > 1 ? 256 : 32, 0, st>>>(rs, ctl, nsys, loop, use_cond);
   return cudaGetLastError();
 }
 

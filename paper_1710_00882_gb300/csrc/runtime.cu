@@ -19,59 +19,8 @@
 
 namespace tsf {
 
-// launchers defined in the kernel translation units
-cudaError_t launch_build(cudaStream_t, int, const int4 *, const SysTab *, int, float, int *, int *, int *, int *,
-                         int *, int *, int *, int *, int *, int, int4 *, RunState *, int);
-int scan_tiles_for(int ncell);
-int force_slots_for(int need);
-int force_partial_rows(int N);
-int vv_blocks(int N);
-cudaError_t launch_force(cudaStream_t, bool, int, bool, int, int, int, int, const dbl4 *, const int4 *, const int *,
-                         const int *, const SysTab *, const void *, const void *, int, void *, void *,
-                         unsigned long long *, int *, int *, double *, RunState *);
-cudaError_t launch_vv(cudaStream_t, bool, bool, int, int, dbl4 *, dbl4 *, int4 *, const int4 *, const void *,
-                      const void *, const unsigned long long *, const int *, const int *, const SysTab *,
-                      const SysCtl *, const double *, float, double *, RunState *);
-cudaError_t launch_gather_out(cudaStream_t, bool, int, const void *, const void *, const unsigned long long *,
-                              const int *, const int *, double *, RunState *);
-cudaError_t launch_ingest(cudaStream_t, int, const double *, const int *, int, int, const SysTab *, dbl4 *, int4 *,
-                          RunState *);
-cudaError_t launch_ingest_vel(cudaStream_t, int, const double *, dbl4 *);
-cudaError_t launch_extract(cudaStream_t, int, const dbl4 *, const dbl4 *, double *, double *);
-cudaError_t launch_step_end(cudaStream_t, RunState *, SysCtl *, int, cudaGraphConditionalHandle, int);
-cudaError_t launch_loop_begin(cudaStream_t, RunState *, cudaGraphConditionalHandle);
-cudaError_t launch_decide(cudaStream_t, RunState *, cudaGraphConditionalHandle);
-cudaError_t launch_set_control(cudaStream_t, RunState *, SysCtl *, long long, double *, long long, int);
-cudaError_t launch_final(cudaStream_t, RunState *, SysCtl *);
-cudaError_t launch_force_done(cudaStream_t, RunState *);
-
 // ---------------------------------------------------------------------------
 // device buffers
-
-template <class T>
-void dfree(T *&p)
-{
-  if (p) cudaFree((void *)p);
-  p = nullptr;
-}
-
-// (re)allocate p to hold at least `bytes`; contents are not kept
-template <class T>
-bool dreserve(T *&p, size_t &have, size_t bytes)
-{
-  if (bytes <= have && p) return true;
-  dfree(p);
-  have = 0;
-  if (bytes == 0) bytes = 16;
-  void *q = nullptr;
-  if (cudaMalloc(&q, bytes) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  p = (T *)q;
-  have = bytes;
-  return true;
-}
 
 // ---------------------------------------------------------------------------
 // geometry
@@ -139,32 +88,6 @@ using namespace tsf;
 
 // ---------------------------------------------------------------------------
 // context
-
-struct tersoff_ctx {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  std::string err;
-  AtomState cstate;        // scratch state of tersoff_compute
-  SysDev csys;             // its system table
-  ListState clist;         // internal list of tersoff_compute when none is given
-  RunState *crs = nullptr; // run state of tersoff_compute
-  void *stage = nullptr;   // host-pointer staging (AoS positions/forces, types)
-  size_t stage_bytes = 0;
-  bool general_only = false;  // TERSOFF_FORCE_KERNEL=general: skip the register force kernel
-  int refs = 1;               // the caller's handle plus one per live list / MD state
-  bool destroyed = false;     // tersoff_ctx_destroy called; freed when refs reaches 0
-};
-
-struct tersoff_params {
-  int nt = 0;
-  std::vector<double> entries;
-  double masses[MAX_TYPES] = {0, 0, 0, 0};
-  double rcmax = 0;
-  void *pair_f = nullptr, *trip_f = nullptr, *pair_d = nullptr, *trip_d = nullptr;
-  double *d_mass = nullptr;
-  bool sym_angular = false;   // rows (i,j,k) and (i,k,j) share their angular constants
-};
 
 struct tersoff_nlist {
   tersoff_ctx *ctx = nullptr;
@@ -433,6 +356,25 @@ int check_common(tersoff_ctx *ctx, const double *pos, int64_t N, const double bo
   return TERSOFF_OK;
 }
 
+static void ctx_free(tersoff_ctx *ctx)
+{
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  free_atoms(ctx->cstate);
+  sys_free(ctx->csys);
+  free_list(ctx->clist);
+  dfree(ctx->crs);
+  dfree(ctx->stage);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+// Lists and MD states keep their context alive: destroying handles in any order is safe.
+void ctx_release(tersoff_ctx *ctx)
+{
+  if (ctx && --ctx->refs == 0) ctx_free(ctx);
+}
+
 }  // namespace tsf
 
 // ===========================================================================
@@ -475,25 +417,6 @@ int tersoff_ctx_create(int device, void *stream, tersoff_ctx **out)
   }
   *out = ctx;
   return TERSOFF_OK;
-}
-
-static void ctx_free(tersoff_ctx *ctx)
-{
-  cudaSetDevice(ctx->device);
-  cudaStreamSynchronize(ctx->stream);
-  free_atoms(ctx->cstate);
-  sys_free(ctx->csys);
-  free_list(ctx->clist);
-  dfree(ctx->crs);
-  dfree(ctx->stage);
-  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
-  delete ctx;
-}
-
-// Lists and MD states keep their context alive: destroying handles in any order is safe.
-static void ctx_release(tersoff_ctx *ctx)
-{
-  if (ctx && --ctx->refs == 0) ctx_free(ctx);
 }
 
 void tersoff_ctx_destroy(tersoff_ctx *ctx)
@@ -751,7 +674,7 @@ int tersoff_compute(tersoff_ctx *ctx, const double *pos, const int32_t *types, i
   const int fast_slots = (P->sym_angular && !ctx->general_only) ? (L->maxcount <= 4 ? 4 : 8) : 0;
   CK(launch_force(ctx->stream, mixed, fast_slots, P->nt == 1, gen_slots, 1, virial != nullptr, (int)N, A.x, A.q,
                   L->nbr, L->cnt, ctx->csys.tab, mixed ? P->pair_f : P->pair_d, mixed ? P->trip_f : P->trip_d, P->nt,
-                  A.contrib, A.selfF, A.mask, A.work, A.nwork, A.partial, rs));
+                  A.contrib, A.selfF, A.mask, A.work, A.nwork, A.partial, rs, nullptr));
   double *dF = nullptr;
   if (forces) {
     if (dev) {
@@ -820,7 +743,7 @@ static int md_force(tersoff_md *md, cudaStream_t st, int eflag)
   CK(launch_force(st, md->mixed, md->fast_slots, P->nt == 1, md->gen_slots, eflag, 0, (int)md->atoms.N, md->atoms.x,
                   md->atoms.q, md->list.nbr, md->list.cnt, md->sys.tab, md->mixed ? P->pair_f : P->pair_d,
                   md->mixed ? P->trip_f : P->trip_d, P->nt, md->atoms.contrib, md->atoms.selfF, md->atoms.mask,
-                  md->atoms.work, md->atoms.nwork, md->atoms.partial, md->rs));
+                  md->atoms.work, md->atoms.nwork, md->atoms.partial, md->rs, nullptr));
   return TERSOFF_OK;
 }
 

@@ -3,6 +3,10 @@
 #include <cstddef>
 #include <cstdint>
 
+#include <string>
+#include <vector>
+
+#include "tersoff.h"
 #include "internal.cuh"
 
 namespace tsf {
@@ -50,4 +54,111 @@ struct SysDev {
   int cap = 0;
 };
 
+}  // namespace tsf
+
+namespace tsf {
+
+// launchers defined in the kernel translation units
+cudaError_t launch_build(cudaStream_t, int, const int4 *, const SysTab *, int, float, int *, int *, int *, int *,
+                         int *, int *, int *, int *, int *, int, int4 *, RunState *, int);
+int scan_tiles_for(int ncell);
+int force_slots_for(int need);
+int force_partial_rows(int N);
+int vv_blocks(int N);
+cudaError_t launch_force(cudaStream_t, bool, int, bool, int, int, int, int, const dbl4 *, const int4 *, const int *,
+                         const int *, const SysTab *, const void *, const void *, int, void *, void *,
+                         unsigned long long *, int *, int *, double *, RunState *, double *);
+cudaError_t launch_vv(cudaStream_t, bool, bool, int, int, dbl4 *, dbl4 *, int4 *, const int4 *, const void *,
+                      const void *, const unsigned long long *, const int *, const int *, const SysTab *,
+                      const SysCtl *, const double *, float, double *, RunState *);
+cudaError_t launch_gather_out(cudaStream_t, bool, int, const void *, const void *, const unsigned long long *,
+                              const int *, const int *, double *, RunState *);
+cudaError_t launch_ingest(cudaStream_t, int, const double *, const int *, int, int, const SysTab *, dbl4 *, int4 *,
+                          RunState *);
+cudaError_t launch_ingest_vel(cudaStream_t, int, const double *, dbl4 *);
+cudaError_t launch_extract(cudaStream_t, int, const dbl4 *, const dbl4 *, double *, double *);
+cudaError_t launch_step_end(cudaStream_t, RunState *, SysCtl *, int, cudaGraphConditionalHandle, int);
+cudaError_t launch_loop_begin(cudaStream_t, RunState *, cudaGraphConditionalHandle);
+cudaError_t launch_decide(cudaStream_t, RunState *, cudaGraphConditionalHandle);
+cudaError_t launch_set_control(cudaStream_t, RunState *, SysCtl *, long long, double *, long long, int);
+cudaError_t launch_final(cudaStream_t, RunState *, SysCtl *);
+cudaError_t launch_force_done(cudaStream_t, RunState *);
+
+
+template <class T>
+inline void dfree(T *&p)
+{
+  if (p) cudaFree((void *)p);
+  p = nullptr;
+}
+
+// (re)allocate p to hold at least `bytes`; contents are not kept
+template <class T>
+inline bool dreserve(T *&p, size_t &have, size_t bytes)
+{
+  if (bytes <= have && p) return true;
+  dfree(p);
+  have = 0;
+  if (bytes == 0) bytes = 16;
+  void *q = nullptr;
+  if (cudaMalloc(&q, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  p = (T *)q;
+  have = bytes;
+  return true;
+}
+
+
+Geom make_geom(const double box[3]);
+int make_grid(const double box[3], double rl, CellGrid *g);
+bool sys_alloc(SysDev &S, int cap);
+void sys_free(SysDev &S);
+void free_atoms(AtomState &A);
+void free_list(ListState &L);
+
+}  // namespace tsf
+
+using tsf::AtomState;
+using tsf::ListState;
+using tsf::SysDev;
+
+struct tersoff_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  tsf::AtomState cstate;        // scratch state of tersoff_compute
+  tsf::SysDev csys;             // its system table
+  tsf::ListState clist;         // internal list of tersoff_compute when none is given
+  tsf::RunState *crs = nullptr; // run state of tersoff_compute
+  void *stage = nullptr;   // host-pointer staging (AoS positions/forces, types)
+  size_t stage_bytes = 0;
+  bool general_only = false;  // TERSOFF_FORCE_KERNEL=general: skip the register force kernel
+  int refs = 1;               // the caller's handle plus one per live list / MD state
+  bool destroyed = false;     // tersoff_ctx_destroy called; freed when refs reaches 0
+};
+
+struct tersoff_params {
+  int nt = 0;
+  std::vector<double> entries;
+  double masses[tsf::MAX_TYPES] = {0, 0, 0, 0};
+  double rcmax = 0;
+  void *pair_f = nullptr, *trip_f = nullptr, *pair_d = nullptr, *trip_d = nullptr;
+  double *d_mass = nullptr;
+  bool sym_angular = false;   // rows (i,j,k) and (i,k,j) share their angular constants
+};
+
+
+namespace tsf {
+int set_err(tersoff_ctx *ctx, int code, const char *fmt, ...);
+int cuda_err(tersoff_ctx *ctx, cudaError_t e, const char *what);
+int status_to_code(tersoff_ctx *ctx, int st, const RunState &h);
+int new_rs(tersoff_ctx *ctx, RunState **rs);
+int ensure_atoms(tersoff_ctx *ctx, AtomState &A, int64_t N, bool need_v);
+int ensure_scatter(tersoff_ctx *ctx, AtomState &A, int64_t N, int cap, bool mixed);
+int ensure_list(tersoff_ctx *ctx, ListState &L, int64_t N, int cap, int ncell);
+int check_box(tersoff_ctx *ctx, const double box[3], double rl);
+void ctx_release(tersoff_ctx *ctx);   // drops one reference; frees the context at zero
 }  // namespace tsf

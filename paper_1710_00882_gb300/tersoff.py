@@ -2,7 +2,7 @@
 
 The functions named ``tersoff_*`` mirror the C entry points one to one and only
 marshal arguments; every step of the computation runs in the library's CUDA
-kernels.  The small classes below (Context, Params, NeighborList, MD) own the
+kernels.  The small classes below (Context, Params, NeighborList, MD, Server) own the
 opaque handles and turn status codes into exceptions.
 
 Arrays may be numpy arrays (host pointers) or CUDA torch tensors (device
@@ -77,6 +77,28 @@ tersoff_md_destroy = _sig("tersoff_md_destroy", None, _P)
 tersoff_md_profile = _sig("tersoff_md_profile", _I, _P, _I)
 tersoff_md_profile_read = _sig("tersoff_md_profile_read", _I, _P, _P, _P)
 tersoff_md_run = _sig("tersoff_md_run", _I, _P, _P, _P, _P, _I64, _P, _P, _D, _I64, _D, _I, _I, _P)
+
+
+class tersoff_job(ctypes.Structure):
+    _fields_ = [("n_atoms", ctypes.c_int64), ("pos", _P), ("vel", _P), ("types", _P), ("box", ctypes.c_double * 3),
+                ("dt_ps", ctypes.c_double), ("nsteps", ctypes.c_int64)]
+
+
+class tersoff_server_stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in ("submitted", "admitted", "completed", "failed", "queued", "running",
+                                              "atom_steps", "chunks", "repacks")] + \
+               [("busy_s", ctypes.c_double), ("capacity_atoms", ctypes.c_int64)]
+
+
+_U64 = ctypes.c_uint64
+tersoff_server_create = _sig("tersoff_server_create", _I, _P, _P, _I, _D, ctypes.c_size_t, _I, _I, _PP)
+tersoff_server_submit = _sig("tersoff_server_submit", _I, _P, ctypes.POINTER(tersoff_job), ctypes.POINTER(_U64))
+tersoff_server_poll = _sig("tersoff_server_poll", _I, _P, _U64, ctypes.POINTER(_I))
+tersoff_server_wait = _sig("tersoff_server_wait", _I, _P, _U64, _D)
+tersoff_server_result = _sig("tersoff_server_result", _I, _P, _U64, _P, _P, _P, _P)
+tersoff_server_get_stats = _sig("tersoff_server_get_stats", _I, _P, ctypes.POINTER(tersoff_server_stats))
+tersoff_server_last_error = _sig("tersoff_server_last_error", ctypes.c_char_p, _P)
+tersoff_server_destroy = _sig("tersoff_server_destroy", None, _P)
 
 
 class TersoffError(RuntimeError):
@@ -290,3 +312,66 @@ def md_run(ctx, params, pos, vel, types, box, dt, nsteps, skin, prec=MIXED, trac
     ctx.check(tersoff_md_run(ctx.h, ptr(pos), ptr(vel), ptr(types), n, ptr(_box(box)), params.h, float(dt),
                              int(nsteps), float(skin), int(prec), HOST_PTRS, ptr(tr)))
     return pos, vel, tr
+
+
+class Server:
+    """Continuous-batching MD server (tersoff_server_*): jobs of independent
+    systems run together on one device, admitted between chunks of steps."""
+
+    def __init__(self, ctx, params, prec=MIXED, skin=0.5, budget_bytes=1 << 30, max_slots=64, chunk_steps=50):
+        h = ctypes.c_void_p()
+        ctx.check(tersoff_server_create(ctx.h, params.h, int(prec), float(skin), int(budget_bytes), int(max_slots),
+                                        int(chunk_steps), ctypes.byref(h)))
+        self.h, self.ctx, self.params = h, ctx, params
+        self._n = {}
+
+    def check(self, rc):
+        if rc != OK:
+            raise TersoffError(rc, tersoff_server_last_error(self.h).decode())
+        return rc
+
+    def submit(self, pos, vel, types, box, dt, nsteps):
+        n = int(np.shape(pos)[0])
+        pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(n, 3)
+        vel = np.ascontiguousarray(vel, dtype=np.float64).reshape(n, 3)
+        types = np.ascontiguousarray(types, dtype=np.int32).reshape(n)
+        job = tersoff_job(n, pos.ctypes.data, vel.ctypes.data, types.ctypes.data,
+                          (ctypes.c_double * 3)(*[float(b) for b in _box(box)]), float(dt), int(nsteps))
+        jid = _U64()
+        self.check(tersoff_server_submit(self.h, ctypes.byref(job), ctypes.byref(jid)))
+        self._n[jid.value] = n
+        return jid.value
+
+    def poll(self, jid):
+        d = _I()
+        self.check(tersoff_server_poll(self.h, jid, ctypes.byref(d)))
+        return bool(d.value)
+
+    def wait(self, jid, timeout=60.0):
+        """True when the job finished, False on timeout; raises if the job failed."""
+        rc = tersoff_server_wait(self.h, jid, float(timeout))
+        if rc == ERR_TIMEOUT:
+            return False
+        self.check(rc)
+        return True
+
+    def result(self, jid):
+        """(pos, vel, (epot, ekin), (queued_s, run_s, total_s)); releases the job."""
+        n = self._n[jid]
+        p, v, e, t = np.zeros((n, 3)), np.zeros((n, 3)), np.zeros(2), np.zeros(3)
+        self.check(tersoff_server_result(self.h, jid, ptr(p), ptr(v), ptr(e), ptr(t)))
+        del self._n[jid]
+        return p, v, (e[0], e[1]), tuple(t)
+
+    def stats(self):
+        st = tersoff_server_stats()
+        self.check(tersoff_server_get_stats(self.h, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in st._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            tersoff_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()

@@ -152,14 +152,16 @@ def sic_1m(seed=4):
 
 # ---- serving stream ----------------------------------------------------------
 
-def cells_for_atoms(target):
-    """n_x <= n_y <= n_z with 8 n_x n_y n_z closest to target (ties: most cubic)."""
+def cells_for_atoms(target, min_cells=1):
+    """n_x <= n_y <= n_z, each >= min_cells, with 8 n_x n_y n_z closest to target
+    (ties: most cubic)."""
     best = None
-    top = int(np.ceil((target / 8.0) ** (1.0 / 1.0))) + 1
-    for nx in range(1, int(np.ceil((target / 8.0) ** (1 / 3))) + 2):
-        for ny in range(nx, int(np.ceil(np.sqrt(target / 8.0 / nx))) + 2):
-            nz_f = target / (8.0 * nx * ny)
-            for nz in (int(np.floor(nz_f)), int(np.ceil(nz_f))):
+    cells = target / 8.0
+    top = max(int(np.ceil(cells)), min_cells) + 1
+    for nx in range(min_cells, max(int(np.ceil(cells ** (1 / 3))), min_cells) + 2):
+        for ny in range(nx, max(int(np.ceil(np.sqrt(cells / nx))), nx) + 2):
+            nz_f = cells / (nx * ny)
+            for nz in (int(np.floor(nz_f)), int(np.ceil(nz_f)), ny):
                 if nz < ny or nz > top:
                     continue
                 err = abs(8 * nx * ny * nz - target)
@@ -188,7 +190,7 @@ def serving_stream(njobs=4096, seed=5, rate=None, min_atoms=64, max_atoms=16384,
     for _ in range(njobs):
         sic = bool(rng.integers(0, 2))
         target = float(np.exp(rng.uniform(np.log(min_atoms), np.log(max_atoms))))
-        nx, ny, nz = (max(c, min_cells) for c in cells_for_atoms(target))
+        nx, ny, nz = cells_for_atoms(target, min_cells)
         T = float(rng.uniform(300.0, 2000.0))
         steps = int(rng.integers(50, 501))
         if sic:

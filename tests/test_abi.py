@@ -82,3 +82,36 @@ def test_product_table_layout():
     assert np.isclose(t[0, 1, 0, 10], 2.85) and np.isclose(t[0, 1, 1, 11], (np.sqrt(6.3) - np.sqrt(4.86)) / 2)
     # pair cutoffs symmetric (the C ABI requires it)
     assert t[0, 1, 1, 10] == t[1, 0, 0, 10] and t[0, 1, 1, 11] == t[1, 0, 0, 11]
+
+
+def test_server_null_arguments_rejected_without_gpu(lib):
+    from paper_1710_00882_gb300 import tersoff as t
+    assert t.tersoff_server_create(None, None, 0, 0.3, 1 << 20, 4, 10, None) == t.ERR_ARG
+    assert t.tersoff_server_submit(None, None, None) == t.ERR_ARG
+    assert t.tersoff_server_poll(None, 1, None) == t.ERR_ARG
+    assert t.tersoff_server_wait(None, 1, 0.0) == t.ERR_ARG
+    assert t.tersoff_server_result(None, 1, None, None, None, None) == t.ERR_ARG
+    assert t.tersoff_server_get_stats(None, None) == t.ERR_ARG
+    assert t.tersoff_server_last_error(None) == b"null server"
+    t.tersoff_server_destroy(None)
+
+
+def test_server_struct_layout_matches_header(tmp_path):
+    """The binding's ctypes structures have the C compiler's sizes and offsets."""
+    from paper_1710_00882_gb300 import tersoff as t
+    src = tmp_path / "layout.c"
+    fields_job = [f for f, _ in t.tersoff_job._fields_]
+    fields_st = [f for f, _ in t.tersoff_server_stats._fields_]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "tersoff.h"', "int main(void) {",
+             'printf("%zu\\n", sizeof(tersoff_job));']
+    lines += [f'printf("%zu\\n", offsetof(tersoff_job, {f}));' for f in fields_job]
+    lines += ['printf("%zu\\n", sizeof(tersoff_server_stats));']
+    lines += [f'printf("%zu\\n", offsetof(tersoff_server_stats, {f}));' for f in fields_st]
+    lines += ["return 0; }"]
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = [ctypes.sizeof(t.tersoff_job)] + [getattr(t.tersoff_job, f).offset for f in fields_job]
+    want += [ctypes.sizeof(t.tersoff_server_stats)] + [getattr(t.tersoff_server_stats, f).offset for f in fields_st]
+    assert got == want
