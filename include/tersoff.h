@@ -174,6 +174,47 @@ int tersoff_md_run(tersoff_ctx *ctx, double *pos, double *vel, const int32_t *ty
                    const double box[3], const tersoff_params *params, double dt_ps, int64_t nsteps, double skin,
                    tersoff_precision prec, int flags, double *energy_trace);
 
+/* ---- evaluation without device allocation --------------------------------------
+ * The paper has no counterpart to this entry point; it serves callers that must
+ * not allocate device memory while they run: a program whose framework allocator
+ * has already reserved the device's memory (a cudaMalloc would fail or make it
+ * give memory back), or a latency-critical loop where cudaMalloc/cudaFree would
+ * synchronize the device.  It computes what tersoff_compute computes (energy,
+ * forces and virial of one configuration, Algorithm 1, Eqs. 1-3, list built
+ * internally with skin 0) and calls no cudaMalloc, cudaFree or other allocating
+ * routine: every working buffer lives in one fixed device array of
+ * TERSOFF_NOALLOC_SCRATCH_BYTES (about 22 MB) compiled into the library, which
+ * every device that loads it holds until the process exits.
+ *
+ * Limits: N <= TERSOFF_NOALLOC_MAX_ATOMS, at most TERSOFF_NOALLOC_MAX_NEIGHBORS
+ * atoms within the cutoff of any atom, cell grids coarsened to at most
+ * TERSOFF_NOALLOC_MAX_CELLS cells.  A larger N returns TERSOFF_ERR_NOMEM before
+ * any GPU work; a longer neighbour list returns TERSOFF_ERR_NLIST_OVERFLOW.
+ *
+ * params: created beforehand (tersoff_params_create allocates; do it at set-up)
+ * on the device that is current at this call.  pos [N][3] float64 and types [N]
+ * int32: DEVICE pointers.  box: host, 3 sides (A), each >= 2 * cutoff.
+ * stream: cudaStream_t of the call (NULL: the default stream).
+ * energy_virial: DEVICE [7] float64 (E in eV, then virial xx, yy, zz, xy, xz, yz
+ * as in tersoff_compute) or NULL.  forces: DEVICE [N][3] float64 eV/A or NULL.
+ * errbuf/errlen: optional host buffer for a message on failure.
+ * The call returns after the stream has finished its work (it reads the device
+ * status word).
+ *
+ * The first call on a device looks up the array's device address with that
+ * device current and keeps it; make that first call before any stream capture.
+ * All calls on a device share the array and find the last call's contents in it;
+ * each call clears what must start at zero.  Calls whose GPU work may overlap
+ * (several host threads, or streams not ordered with each other) race on the
+ * array: serialize them. */
+#define TERSOFF_NOALLOC_MAX_ATOMS 16384
+#define TERSOFF_NOALLOC_MAX_NEIGHBORS 32
+#define TERSOFF_NOALLOC_MAX_CELLS 32768
+#define TERSOFF_NOALLOC_SCRATCH_BYTES 23323136
+int tersoff_compute_noalloc(const tersoff_params *params, const double *pos, const int32_t *types, int64_t N,
+                            const double box[3], tersoff_precision prec, void *stream, double *energy_virial,
+                            double *forces, char *errbuf, size_t errlen);
+
 /* ---- serving: continuous batching of MD jobs ---------------------------------
  * A server runs many independent NVE jobs (periodic boxes of any size, each with
  * its own dt and step count) on one GPU.  Admitted jobs live in one packed

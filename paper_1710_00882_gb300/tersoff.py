@@ -32,6 +32,8 @@ ERR_NOT_FOUND = -9
 FP64 = 0
 MIXED = 1
 
+NOALLOC_MAX_ATOMS = 16384   # TERSOFF_NOALLOC_MAX_ATOMS
+
 HOST_PTRS = 0
 DEVICE_PTRS = 1
 DETERMINISTIC = 2
@@ -77,6 +79,8 @@ tersoff_md_destroy = _sig("tersoff_md_destroy", None, _P)
 tersoff_md_profile = _sig("tersoff_md_profile", _I, _P, _I)
 tersoff_md_profile_read = _sig("tersoff_md_profile_read", _I, _P, _P, _P)
 tersoff_md_run = _sig("tersoff_md_run", _I, _P, _P, _P, _P, _I64, _P, _P, _D, _I64, _D, _I, _I, _P)
+tersoff_compute_noalloc = _sig("tersoff_compute_noalloc", _I, _P, _P, _P, _I64, _P, _I, _P, _P, _P, ctypes.c_char_p,
+                               ctypes.c_size_t)
 
 
 class tersoff_job(ctypes.Structure):
