@@ -24,8 +24,9 @@
 // Scatter: all force contributions of i's terms on neighbour j are summed per j in
 // the thread and written once, to slot s of i's list (contrib[s][i]); the force of
 // i's terms on i itself is minus their sum (translation invariance).  No atomics:
-// the reverse gather (integrate.cu) adds them per atom in list order, so forces are
-// bitwise reproducible.  Energy and virial go to per-block partial sums that a
+// the gather (integrate.cu) reads, for each atom m and in-cutoff slot s of its list,
+// the contribution at the flat index rev[s][m] (m's slot in its neighbour's list)
+// and adds them in list order, so forces are bitwise reproducible.  Energy and virial go to per-block partial sums that a
 // single block reduces in a fixed order.
 //
 // Precision: R = double (FP64 mode) or float (mixed mode).  In mixed mode the
@@ -34,8 +35,6 @@
 // scale so that d_ij is within ~1 ulp, and exp(-lambda r) forms lambda r with an
 // FMA-exact product, because the pair term's r-derivative is a difference of two
 // terms ~10x larger than itself.
-#include <cstdlib>
-
 #include "internal.cuh"
 
 namespace tsf {
@@ -45,7 +44,6 @@ template <> struct V4t<float> { using type = float4; };
 template <> struct V4t<double> { using type = dbl4; };
 
 constexpr int FAST_THREADS = 128;
-static int g_allow_direct = getenv("TERSOFF_NO_DIRECT") ? 0 : 1;
 constexpr float L2E_F = 1.44269502f;                   // log2(e) rounded to float
 constexpr float L2E_F_LO = 1.925963033500011e-08f;     // log2(e) - L2E_F
 
@@ -226,7 +224,7 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
             const TripP<R> *__restrict__ gtrips, int nt, typename V4t<R>::type *__restrict__ contrib,
             typename V4t<R>::type *__restrict__ selfF, unsigned long long *__restrict__ mask,
             int *__restrict__ work, int *__restrict__ nwork, double *__restrict__ partial, RunState *rs,
-            int allow_direct, double *__restrict__ eatom)
+            double *__restrict__ eatom)
 {
   using M = typename MathOf<R>::M;
   using V4 = typename V4t<R>::type;
@@ -268,7 +266,7 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
   // outside the cutoff get f_C = f_C' = 0 and contribute nothing) and every load is
   // issued in one unrolled burst.  Otherwise the list is packed: a first pass marks
   // in-cutoff entries, the second loads them into consecutive slots.
-  const bool direct = active && n <= MAXNC && allow_direct;
+  const bool direct = active && n <= MAXNC;
 
   R ux[MAXNC], uy[MAXNC], uz[MAXNC], rr[MAXNC], rl[MAXNC], ir[MAXNC], fc[MAXNC], dfc[MAXNC];
   int meta[MAXNC];
@@ -913,15 +911,15 @@ static cudaError_t launch_reg(cudaStream_t st, int eflag, int vflag, int N, cons
   if (vflag)
     k_force_reg<R, MAXNC, ONE, true, true><<<blocks, FAST_THREADS, 0, st>>>(
         N, x, q, nbr, cnt, sys, (P)pairs, (Tt)trips, nt, (V)contrib, (V)selfF, mask, work, nwork, partial, rs,
-        g_allow_direct, eatom);
+        eatom);
   else if (eflag)
     k_force_reg<R, MAXNC, ONE, true, false><<<blocks, FAST_THREADS, 0, st>>>(
         N, x, q, nbr, cnt, sys, (P)pairs, (Tt)trips, nt, (V)contrib, (V)selfF, mask, work, nwork, partial, rs,
-        g_allow_direct, eatom);
+        eatom);
   else
     k_force_reg<R, MAXNC, ONE, false, false><<<blocks, FAST_THREADS, 0, st>>>(
         N, x, q, nbr, cnt, sys, (P)pairs, (Tt)trips, nt, (V)contrib, (V)selfF, mask, work, nwork, partial, rs,
-        g_allow_direct, eatom);
+        eatom);
   return cudaGetLastError();
 }
 

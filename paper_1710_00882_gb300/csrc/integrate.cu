@@ -4,10 +4,11 @@
 // contributions of i's terms on each in-cutoff neighbour in slot s of i's list
 // (contrib[s][i]), the force on i itself (selfF[i]) and the set of in-cutoff
 // slots (mask[i]).  The force on atom m is selfF[m] plus, for each in-cutoff slot
-// s of m's list with neighbour j, contrib[rev[s][m]][j]: the slot of m in j's
-// list.  In-cutoff is symmetric (the minimum-image r^2 is bitwise symmetric and
+// s of m's list, the contribution of its neighbour j's terms on m, stored at the
+// slot of m in j's list: flat index rev[s][m] (written by the list build).
+// In-cutoff is symmetric (the minimum-image r^2 is bitwise symmetric and
 // r_C(i,j) = r_C(j,i)), so exactly the slots the force kernel wrote are read.
-// The sum is taken in float64 in list order: deterministic.
+// The sum runs in list order: deterministic.
 #include "internal.cuh"
 
 namespace tsf {
@@ -62,18 +63,31 @@ template <> struct GatherAcc<double> {
 template <class R>
 __device__ __forceinline__ void gather_force(int m, int N, const typename V4g<R>::type *__restrict__ contrib,
                                              const typename V4g<R>::type *__restrict__ selfF,
-                                             const unsigned long long *__restrict__ mask, const int *__restrict__ nbr,
-                                             const int *__restrict__ rev, double &fx, double &fy, double &fz)
+                                             const unsigned long long *__restrict__ mask, const int *__restrict__ rev,
+                                             double &fx, double &fy, double &fz)
 {
+  using V = typename V4g<R>::type;
+  constexpr int U = 4;   // slots whose loads are issued together
   GatherAcc<R> acc;
   acc.init(selfF[m]);
   unsigned long long mb = mask[m];
   while (mb) {
-    const int s = __ffsll((long long)mb) - 1;
-    mb &= mb - 1;
-    const int j = nbr[(size_t)s * N + m];
-    const int s2 = rev[(size_t)s * N + m];
-    acc.add(contrib[(size_t)s2 * N + j]);
+    int sl[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      sl[u] = mb ? __ffsll((long long)mb) - 1 : -1;
+      mb &= mb - 1;
+    }
+    unsigned g[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) g[u] = sl[u] >= 0 ? (unsigned)rev[(size_t)sl[u] * N + m] : 0u;
+    V c[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (sl[u] >= 0) c[u] = contrib[g[u]];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (sl[u] >= 0) acc.add(c[u]);
   }
   acc.out(fx, fy, fz);
 }
@@ -135,14 +149,14 @@ __global__ void k_ingest_vel(int N, const double *__restrict__ vel, dbl4 *__rest
 template <class R>
 __global__ void k_gather_out(int N, const typename V4g<R>::type *__restrict__ contrib,
                              const typename V4g<R>::type *__restrict__ selfF,
-                             const unsigned long long *__restrict__ mask, const int *__restrict__ nbr,
-                             const int *__restrict__ rev, double *__restrict__ out, RunState *rs)
+                             const unsigned long long *__restrict__ mask, const int *__restrict__ rev,
+                             double *__restrict__ out, RunState *rs)
 {
   if (rs->status != 0) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   double fx, fy, fz;
-  gather_force<R>(i, N, contrib, selfF, mask, nbr, rev, fx, fy, fz);
+  gather_force<R>(i, N, contrib, selfF, mask, rev, fx, fy, fz);
   if (!isfinite(fx) || !isfinite(fy) || !isfinite(fz)) atomicOr(&rs->status, ST_NONFINITE);
   out[3 * (size_t)i] = fx;
   out[3 * (size_t)i + 1] = fy;
@@ -160,7 +174,7 @@ template <class R, bool KE>
 __global__ void k_vv(int N, int mode, dbl4 *__restrict__ x, dbl4 *__restrict__ v, int4 *__restrict__ q,
                      const int4 *__restrict__ qref, const typename V4g<R>::type *__restrict__ contrib,
                      const typename V4g<R>::type *__restrict__ selfF, const unsigned long long *__restrict__ mask,
-                     const int *__restrict__ nbr, const int *__restrict__ rev, const SysTab *__restrict__ sys,
+                     const int *__restrict__ rev, const SysTab *__restrict__ sys,
                      const SysCtl *__restrict__ ctl, const double *__restrict__ mass, float disp2_lim,
                      double *__restrict__ kepart, RunState *rs)
 {
@@ -185,7 +199,7 @@ __global__ void k_vv(int N, int mode, dbl4 *__restrict__ x, dbl4 *__restrict__ v
       mode_i = C.steps_left > 0 ? (C.open ? (VV_FINISH | VV_START) : VV_START) : (C.open ? VV_FINISH : 0);
     }
     double fx, fy, fz;
-    gather_force<R>(i, N, contrib, selfF, mask, nbr, rev, fx, fy, fz);
+    gather_force<R>(i, N, contrib, selfF, mask, rev, fx, fy, fz);
     dbl4 vi = v[i];
     if (mode_i & VV_FINISH) {
       vi.x = fma(c, fx, vi.x);
@@ -352,25 +366,25 @@ __global__ void k_force_done(RunState *rs)
 
 cudaError_t launch_vv(cudaStream_t st, bool mixed, bool ke, int N, int mode, dbl4 *x, dbl4 *v, int4 *q,
                       const int4 *qref, const void *contrib, const void *selfF, const unsigned long long *mask,
-                      const int *nbr, const int *rev, const SysTab *sys, const SysCtl *ctl, const double *mass,
-                      float disp2_lim, double *kepart, RunState *rs)
+                      const int *rev, const SysTab *sys, const SysCtl *ctl, const double *mass, float disp2_lim,
+                      double *kepart, RunState *rs)
 {
   if (N == 0) return cudaSuccess;
   const int T = 256, B = (N + T - 1) / T;
   if (mixed) {
     if (ke)
       k_vv<float, true><<<B, T, 0, st>>>(N, mode, x, v, q, qref, (const float4 *)contrib, (const float4 *)selfF,
-                                         mask, nbr, rev, sys, ctl, mass, disp2_lim, kepart, rs);
+                                         mask, rev, sys, ctl, mass, disp2_lim, kepart, rs);
     else
       k_vv<float, false><<<B, T, 0, st>>>(N, mode, x, v, q, qref, (const float4 *)contrib, (const float4 *)selfF,
-                                          mask, nbr, rev, sys, ctl, mass, disp2_lim, kepart, rs);
+                                          mask, rev, sys, ctl, mass, disp2_lim, kepart, rs);
   } else {
     if (ke)
       k_vv<double, true><<<B, T, 0, st>>>(N, mode, x, v, q, qref, (const dbl4 *)contrib, (const dbl4 *)selfF,
-                                          mask, nbr, rev, sys, ctl, mass, disp2_lim, kepart, rs);
+                                          mask, rev, sys, ctl, mass, disp2_lim, kepart, rs);
     else
       k_vv<double, false><<<B, T, 0, st>>>(N, mode, x, v, q, qref, (const dbl4 *)contrib, (const dbl4 *)selfF,
-                                           mask, nbr, rev, sys, ctl, mass, disp2_lim, kepart, rs);
+                                           mask, rev, sys, ctl, mass, disp2_lim, kepart, rs);
   }
   if (ke) k_ke_reduce<<<1, 256, 0, st>>>(kepart, B, rs);
   return cudaGetLastError();
@@ -379,16 +393,14 @@ cudaError_t launch_vv(cudaStream_t st, bool mixed, bool ke, int N, int mode, dbl
 int vv_blocks(int N) { return (N + 255) / 256; }
 
 cudaError_t launch_gather_out(cudaStream_t st, bool mixed, int N, const void *contrib, const void *selfF,
-                              const unsigned long long *mask, const int *nbr, const int *rev, double *out,
-                              RunState *rs)
+                              const unsigned long long *mask, const int *rev, double *out, RunState *rs)
 {
   if (N == 0) return cudaSuccess;
   const int T = 256, B = (N + T - 1) / T;
   if (mixed)
-    k_gather_out<float><<<B, T, 0, st>>>(N, (const float4 *)contrib, (const float4 *)selfF, mask, nbr, rev, out, rs);
+    k_gather_out<float><<<B, T, 0, st>>>(N, (const float4 *)contrib, (const float4 *)selfF, mask, rev, out, rs);
   else
-    k_gather_out<double><<<B, T, 0, st>>>(N, (const dbl4 *)contrib, (const dbl4 *)selfF, mask, nbr, rev, out,
-                                          rs);
+    k_gather_out<double><<<B, T, 0, st>>>(N, (const dbl4 *)contrib, (const dbl4 *)selfF, mask, rev, out, rs);
   return cudaGetLastError();
 }
 

@@ -136,16 +136,7 @@ struct SysCtl {
 struct CellGrid {
   int nc[3];
   int ncell;
-  int allpairs;   // 1: fewer than 3 cells in some dimension, scan all atoms
   float rl2;      // (cutoff + skin)^2 with a small safety margin
-};
-
-// Per-state list / scatter buffers.
-struct ListBuf {
-  int *nbr;        // [cap][N] list entries (atom index j), slot-major
-  int *rev;        // [cap][N] slot of i in j's list
-  int *cnt;        // [N]
-  int cap;
 };
 
 }  // namespace tsf

@@ -10,7 +10,7 @@
 //   k_scan_*      -> exclusive scan of the cell counts (three-phase block scan)
 //   k_cell_fill   -> atoms in cell order
 //   k_build       -> per atom: 27-cell stencil, keep r < r_list, sort by j
-//   k_reverse     -> for each entry (i,s) the slot of i in j's list
+//   k_reverse     -> for each entry (i,s) the flat index of i's slot in j's list
 #include "internal.cuh"
 
 namespace tsf {
@@ -136,14 +136,17 @@ __global__ void k_scan_add(int n, int *__restrict__ out, const int *__restrict__
   counts[i] = 0;
 }
 
-__global__ void k_cell_fill(int N, const int *__restrict__ cell_of, const int *__restrict__ rank,
-                            const int *__restrict__ cell_start, int *__restrict__ cell_atoms, const RunState *rs,
-                            int gated)
+// atoms in cell order, each with its fixed-point position: the stencil scan of
+// k_build then reads candidates as contiguous runs
+__global__ void k_cell_fill(int N, const int4 *__restrict__ q, const int *__restrict__ cell_of,
+                            const int *__restrict__ rank, const int *__restrict__ cell_start,
+                            int4 *__restrict__ cell_atoms, const RunState *rs, int gated)
 {
   if (skip_build(rs, gated)) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
-  cell_atoms[cell_start[cell_of[i]] + rank[i]] = i;
+  const int4 p = q[i];
+  cell_atoms[cell_start[cell_of[i]] + rank[i]] = make_int4(p.x, p.y, p.z, i);
 }
 
 // Stencil range along one axis: 3 neighbouring cells, or every cell when the axis
@@ -193,7 +196,7 @@ __device__ __forceinline__ void sort_column(int *__restrict__ nbr, int N, int i,
 // the set of neighbours.
 __global__ void __launch_bounds__(128) k_build(int N, const int4 *__restrict__ q, const SysTab *__restrict__ sys,
                                                float rl2, const int *__restrict__ cell_start,
-                                               const int *__restrict__ cell_atoms, int *__restrict__ nbr,
+                                               const int4 *__restrict__ cell_atoms, int *__restrict__ nbr,
                                                int *__restrict__ cnt, int cap, int4 *__restrict__ qref, RunState *rs,
                                                int gated)
 {
@@ -201,45 +204,52 @@ __global__ void __launch_bounds__(128) k_build(int N, const int4 *__restrict__ q
   if (skip_build(rs, gated)) return;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= N) return;
-  const int i = cell_atoms[t];
+  const int i = cell_atoms[t].w;
   const int4 pi = q[i];
   qref[i] = pi;
   const SysTab &T = sys[sys_of(pi.w)];
-  const Geom &geo = T.geo;
-  CellGrid g;
-  g.nc[0] = T.nc[0]; g.nc[1] = T.nc[1]; g.nc[2] = T.nc[2];
-  g.rl2 = rl2;
+  const float s0 = T.geo.q_to_f[0], s1 = T.geo.q_to_f[1], s2 = T.geo.q_to_f[2];
+  const int nc0 = T.nc[0], nc1 = T.nc[1], nc2 = T.nc[2];
   const int coff = T.cell_off;
-  int c[3] = {cell_coord((uint32_t)pi.x, g.nc[0]), cell_coord((uint32_t)pi.y, g.nc[1]),
-              cell_coord((uint32_t)pi.z, g.nc[2])};
+  int c[3] = {cell_coord((uint32_t)pi.x, nc0), cell_coord((uint32_t)pi.y, nc1), cell_coord((uint32_t)pi.z, nc2)};
   int lo[3], nr[3];
-  for (int a = 0; a < 3; ++a) axis_range(c[a], g.nc[a], &lo[a], &nr[a]);
+  axis_range(c[0], nc0, &lo[0], &nr[0]);
+  axis_range(c[1], nc1, &lo[1], &nr[1]);
+  axis_range(c[2], nc2, &lo[2], &nr[2]);
+  // the x cells of one stencil row are one run of cell_atoms, or two where the row wraps
+  const int xa = lo[0] < 0 ? lo[0] + nc0 : lo[0];
+  const int xe = xa + nr[0];
+  const int xa2 = xe > nc0 ? 0 : xa, xe1 = xe > nc0 ? nc0 : xe, xe2 = xe > nc0 ? xe - nc0 : 0;
   int n = 0;
   for (int oz = 0; oz < nr[2]; ++oz) {
     int cz = lo[2] + oz;
-    cz += (cz < 0) ? g.nc[2] : 0;
-    cz -= (cz >= g.nc[2]) ? g.nc[2] : 0;
+    cz += (cz < 0) ? nc2 : 0;
+    cz -= (cz >= nc2) ? nc2 : 0;
     for (int oy = 0; oy < nr[1]; ++oy) {
       int cy = lo[1] + oy;
-      cy += (cy < 0) ? g.nc[1] : 0;
-      cy -= (cy >= g.nc[1]) ? g.nc[1] : 0;
-      const int row = coff + (cz * g.nc[1] + cy) * g.nc[0];
-      for (int ox = 0; ox < nr[0]; ++ox) {
-        int cx = lo[0] + ox;
-        cx += (cx < 0) ? g.nc[0] : 0;
-        cx -= (cx >= g.nc[0]) ? g.nc[0] : 0;
-        const int b = cell_start[row + cx], e = cell_start[row + cx + 1];
-        for (int u = b; u < e; ++u) {
-          const int j = cell_atoms[u];
-          if (j == i) continue;
-          const int4 pj = q[j];
-          const float dx = q_scaled(qdiff(pj.x, pi.x), geo.q_to_f[0]);
-          const float dy = q_scaled(qdiff(pj.y, pi.y), geo.q_to_f[1]);
-          const float dz = q_scaled(qdiff(pj.z, pi.z), geo.q_to_f[2]);
-          const float r2 = r2_decide(dx, dy, dz);
-          if (r2 < g.rl2) {
-            if (n < cap) nbr[(size_t)n * N + i] = j;
-            ++n;
+      cy += (cy < 0) ? nc1 : 0;
+      cy -= (cy >= nc1) ? nc1 : 0;
+      const int row = coff + (cz * nc1 + cy) * nc0;
+      for (int part = 0; part < 2; ++part) {
+        if (part == 1 && xe2 == 0) break;
+        const int b = part == 0 ? cell_start[row + xa] : cell_start[row + xa2];
+        const int e = part == 0 ? cell_start[row + xe1] : cell_start[row + xe2];
+        // four candidates per round: their loads are issued together
+        for (int u = b; u < e; u += 4) {
+          int4 pj[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) pj[k] = u + k < e ? cell_atoms[u + k] : make_int4(0, 0, 0, -1);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int j = pj[k].w;
+            const float dx = q_scaled(qdiff(pj[k].x, pi.x), s0);
+            const float dy = q_scaled(qdiff(pj[k].y, pi.y), s1);
+            const float dz = q_scaled(qdiff(pj[k].z, pi.z), s2);
+            const float r2 = r2_decide(dx, dy, dz);
+            if (j >= 0 && j != i && r2 < rl2) {
+              if (n < cap) nbr[(size_t)n * N + i] = j;
+              ++n;
+            }
           }
         }
       }
@@ -282,7 +292,9 @@ __global__ void __launch_bounds__(128) k_build(int N, const int4 *__restrict__ q
   }
 }
 
-// rev[s][i] = slot of i in the (sorted) list of j = nbr[s][i], found by binary search.
+// rev[s][i] = where the force gather finds the contribution of the terms of i's
+// neighbour j = nbr[s][i] on i: the flat index s2 * N + j of i's slot s2 in j's
+// (sorted) list, found by binary search (a 32-bit unsigned value: cap * N < 2^32).
 __global__ void k_reverse(int N, const int *__restrict__ nbr, const int *__restrict__ cnt, int *__restrict__ rev,
                           RunState *rs, int gated)
 {
@@ -300,7 +312,7 @@ __global__ void k_reverse(int N, const int *__restrict__ nbr, const int *__restr
       if (v < i) lo = mid + 1; else hi = mid - 1;
     }
     if (found < 0) atomicOr(&rs->status, ST_REV_MISSING);
-    rev[(size_t)s * N + i] = found < 0 ? 0 : found;
+    rev[(size_t)s * N + i] = (int)((unsigned)(found < 0 ? 0 : found) * (unsigned)N + (unsigned)j);
   }
 }
 
@@ -317,10 +329,10 @@ __global__ void k_build_done(RunState *rs, int gated)
 namespace tsf {
 
 // Enqueue one list build on st.  Buffers: cell_count[ncell] (zero on entry, zero
-// on exit), cell_start[ncell+1], tile_sums[ceil(ncell/SCAN_TILE)], cell_atoms[N],
+// on exit), cell_start[ncell+1], tile_sums[ceil(ncell/SCAN_TILE)], cell_atoms[N] (int4),
 // cell_of[N], rank[N]; list nbr/rev [cap][N], cnt[N]; qref[N].
 cudaError_t launch_build(cudaStream_t st, int N, const int4 *q, const SysTab *sys, int ncell, float rl2,
-                         int *cell_count, int *cell_start, int *tile_sums, int *cell_atoms, int *cell_of, int *rank,
+                         int *cell_count, int *cell_start, int *tile_sums, int4 *cell_atoms, int *cell_of, int *rank,
                          int *nbr, int *rev, int *cnt, int cap, int4 *qref, RunState *rs, int gated)
 {
   if (N == 0) return cudaSuccess;
@@ -331,7 +343,7 @@ cudaError_t launch_build(cudaStream_t st, int N, const int4 *q, const SysTab *sy
   k_scan_tiles<<<ntiles, SCAN_THREADS, 0, st>>>(ncell, cell_count, cell_start, tile_sums, rs, gated);
   k_scan_sums<<<1, SCAN_THREADS, 0, st>>>(ntiles, tile_sums, cell_start + ncell, rs, gated);
   k_scan_add<<<(ncell + T - 1) / T, T, 0, st>>>(ncell, cell_start, tile_sums, cell_count, rs, gated);
-  k_cell_fill<<<BN, T, 0, st>>>(N, cell_of, rank, cell_start, cell_atoms, rs, gated);
+  k_cell_fill<<<BN, T, 0, st>>>(N, q, cell_of, rank, cell_start, cell_atoms, rs, gated);
   const int BN128 = (N + 127) / 128;
   k_build<<<BN128, 128, 0, st>>>(N, q, sys, rl2, cell_start, cell_atoms, nbr, cnt, cap, qref, rs, gated);
   k_reverse<<<BN128, 128, 0, st>>>(N, nbr, cnt, rev, rs, gated);

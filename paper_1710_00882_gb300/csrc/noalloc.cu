@@ -50,7 +50,7 @@ struct Layout {
   static constexpr size_t rev = nbr + up256(kMaxAtoms * kCap * sizeof(int));
   static constexpr size_t cnt = rev + up256(kMaxAtoms * kCap * sizeof(int));
   static constexpr size_t cell_atoms = cnt + up256(kMaxAtoms * sizeof(int));
-  static constexpr size_t cell_of = cell_atoms + up256(kMaxAtoms * sizeof(int));
+  static constexpr size_t cell_of = cell_atoms + up256(kMaxAtoms * sizeof(int4));
   static constexpr size_t rank = cell_of + up256(kMaxAtoms * sizeof(int));
   static constexpr size_t cell_count = rank + up256(kMaxAtoms * sizeof(int));
   static constexpr size_t cell_start = cell_count + up256(kMaxCells * sizeof(int));
@@ -156,7 +156,8 @@ extern "C" int tersoff_compute_noalloc(const tersoff_params *P, const double *po
   int4 *q = (int4 *)(base + Layout::q);
   int4 *qref = (int4 *)(base + Layout::qref);
   int *nbr = (int *)(base + Layout::nbr), *rev = (int *)(base + Layout::rev), *cnt = (int *)(base + Layout::cnt);
-  int *cell_atoms = (int *)(base + Layout::cell_atoms), *cell_of = (int *)(base + Layout::cell_of);
+  int4 *cell_atoms = (int4 *)(base + Layout::cell_atoms);
+  int *cell_of = (int *)(base + Layout::cell_of);
   int *rank = (int *)(base + Layout::rank), *cell_count = (int *)(base + Layout::cell_count);
   int *cell_start = (int *)(base + Layout::cell_start), *tile_sums = (int *)(base + Layout::tile_sums);
   void *contrib = base + Layout::contrib, *selfF = base + Layout::selfF;
@@ -186,7 +187,7 @@ extern "C" int tersoff_compute_noalloc(const tersoff_params *P, const double *po
   NK(launch_force(st, mixed, fast_slots, P->nt == 1, force_slots_for(kCap), 1, 1, (int)N, x, q, nbr, cnt, sys,
                   mixed ? P->pair_f : P->pair_d, mixed ? P->trip_f : P->trip_d, P->nt, contrib, selfF, mask, work,
                   nwork, partial, rs, nullptr));
-  if (forces) NK(launch_gather_out(st, mixed, (int)N, contrib, selfF, mask, nbr, rev, forces, rs));
+  if (forces) NK(launch_gather_out(st, mixed, (int)N, contrib, selfF, mask, rev, forces, rs));
   if (energy_virial) {
     NK(cudaMemcpyAsync(energy_virial, &rs->epot, sizeof(double), cudaMemcpyDeviceToDevice, st));
     NK(cudaMemcpyAsync(energy_virial + 1, rs->virial, 6 * sizeof(double), cudaMemcpyDeviceToDevice, st));

@@ -51,7 +51,6 @@ int make_grid(const double box[3], double rl, CellGrid *g)
   }
   if (ncell > (1LL << 30)) return TERSOFF_ERR_ARG;
   g->ncell = (int)ncell;
-  g->allpairs = 0;
   g->rl2 = (float)(rl * rl * (1.0 + 1e-5));
   return TERSOFF_OK;
 }
@@ -114,7 +113,6 @@ struct tersoff_md {
   ListState list;
   SysDev sys;
   RunState *rs = nullptr;
-  double *d_kick = nullptr;
   double *d_trace = nullptr;
   size_t trace_cap = 0;
   double dt = 0, skin = 0;
@@ -240,11 +238,14 @@ int ensure_scatter(tersoff_ctx *ctx, AtomState &A, int64_t N, int cap, bool mixe
 int ensure_list(tersoff_ctx *ctx, ListState &L, int64_t N, int cap, int ncell)
 {
   size_t n = (size_t)std::max<int64_t>(N, 1);
+  // list slots are addressed by 32-bit flat indices (slot * N + atom)
+  if (n * (size_t)cap > 0xffffffffull)
+    return set_err(ctx, TERSOFF_ERR_NOMEM, "N=%lld x %d list slots exceeds 2^32 entries", (long long)N, cap);
   bool ok = dreserve(L.nbr, L.nbr_b, n * cap * sizeof(int)) &&
             dreserve(L.rev, L.rev_b, n * cap * sizeof(int)) &&
             dreserve(L.cnt, L.cnt_b, n * sizeof(int)) &&
             dreserve(L.qref, L.qref_b, n * sizeof(int4)) &&
-            dreserve(L.cell_atoms, L.cell_atoms_b, n * sizeof(int)) &&
+            dreserve(L.cell_atoms, L.cell_atoms_b, n * sizeof(int4)) &&
             dreserve(L.cell_of, L.cell_of_b, n * sizeof(int)) &&
             dreserve(L.rank, L.rank_b, n * sizeof(int)) &&
             dreserve(L.cell_start, L.cell_start_b, ((size_t)ncell + 1) * sizeof(int)) &&
@@ -685,7 +686,7 @@ int tersoff_compute(tersoff_ctx *ctx, const double *pos, const int32_t *types, i
         return set_err(ctx, TERSOFF_ERR_NOMEM, "staging buffer");
       dF = (double *)ctx->stage;
     }
-    CK(launch_gather_out(ctx->stream, mixed, (int)N, A.contrib, A.selfF, A.mask, L->nbr, L->rev, dF, rs));
+    CK(launch_gather_out(ctx->stream, mixed, (int)N, A.contrib, A.selfF, A.mask, L->rev, dF, rs));
   }
   RunState h;
   CKR(read_rs(ctx, rs, &h));
@@ -753,7 +754,7 @@ static int md_vv(tersoff_md *md, cudaStream_t st, int mode, bool ke)
   tersoff_ctx *ctx = md->ctx;
   const float lim = (float)(0.25 * md->skin * md->skin);
   CK(launch_vv(st, md->mixed, ke, (int)md->atoms.N, mode, md->atoms.x, md->atoms.v, md->atoms.q, md->list.qref,
-               md->atoms.contrib, md->atoms.selfF, md->atoms.mask, md->list.nbr, md->list.rev, md->sys.tab,
+               md->atoms.contrib, md->atoms.selfF, md->atoms.mask, md->list.rev, md->sys.tab,
                md->sys.ctl, md->params->d_mass, lim, md->atoms.kepart, md->rs));
   return TERSOFF_OK;
 }
@@ -981,10 +982,6 @@ int tersoff_md_create(tersoff_ctx *ctx, const double *pos, const double *vel, co
     if (tmp) cudaFree(tmp);
     if (e != cudaSuccess) return fail(cuda_err(ctx, e, "ingest velocities"));
   }
-  double kick[MAX_TYPES] = {0, 0, 0, 0};
-  for (int a = 0; a < P->nt; ++a) kick[a] = 0.5 * dt_ps * ACCEL / P->masses[a];
-  if (cudaMalloc((void **)&md->d_kick, sizeof kick) != cudaSuccess) return fail(set_err(ctx, TERSOFF_ERR_NOMEM, "kick"));
-  cudaMemcpy(md->d_kick, kick, sizeof kick, cudaMemcpyHostToDevice);
   md->sys.host.dt = dt_ps;
   for (int a = 0; a < MAX_TYPES; ++a) md->sys.host.kick[a] = a < P->nt ? 0.5 * dt_ps * ACCEL / P->masses[a] : 0.0;
   if ((rc = build_list_sync(ctx, md->atoms, md->list, md->rs, box, P->rcmax, skin, md->sys)) != TERSOFF_OK)
@@ -1100,7 +1097,7 @@ int tersoff_md_get(tersoff_md *md, double *pos, double *vel, double *forces, int
   if (launch_extract(ctx->stream, (int)N, md->atoms.x, md->atoms.v, dp, dv) != cudaSuccess) rc = TERSOFF_ERR_CUDA;
   if (rc == TERSOFF_OK && df &&
       launch_gather_out(ctx->stream, md->mixed, (int)N, md->atoms.contrib, md->atoms.selfF, md->atoms.mask,
-                        md->list.nbr, md->list.rev, df, md->rs) != cudaSuccess)
+                        md->list.rev, df, md->rs) != cudaSuccess)
     rc = TERSOFF_ERR_CUDA;
   if (rc == TERSOFF_OK && !dev) {
     if (pos) cudaMemcpyAsync(pos, dp, bytes, cudaMemcpyDeviceToHost, ctx->stream);
@@ -1164,7 +1161,6 @@ void tersoff_md_destroy(tersoff_md *md)
   sys_free(md->sys);
   free_list(md->list);
   dfree(md->rs);
-  dfree(md->d_kick);
   dfree(md->d_trace);
   ctx_release(md->ctx);
   delete md;

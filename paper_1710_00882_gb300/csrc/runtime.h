@@ -39,8 +39,8 @@ struct ListState {
   double cutoff = 0, skin = 0;
   int *nbr = nullptr, *rev = nullptr, *cnt = nullptr;
   int4 *qref = nullptr;
-  int *cell_count = nullptr, *cell_start = nullptr, *tile_sums = nullptr, *cell_atoms = nullptr, *cell_of = nullptr,
-      *rank = nullptr;
+  int *cell_count = nullptr, *cell_start = nullptr, *tile_sums = nullptr, *cell_of = nullptr, *rank = nullptr;
+  int4 *cell_atoms = nullptr;   // atoms in cell order: fixed-point position and index
   size_t nbr_b = 0, rev_b = 0, cnt_b = 0, qref_b = 0, cell_count_b = 0, cell_start_b = 0, tile_sums_b = 0,
          cell_atoms_b = 0, cell_of_b = 0, rank_b = 0;
 };
@@ -59,7 +59,7 @@ struct SysDev {
 namespace tsf {
 
 // launchers defined in the kernel translation units
-cudaError_t launch_build(cudaStream_t, int, const int4 *, const SysTab *, int, float, int *, int *, int *, int *,
+cudaError_t launch_build(cudaStream_t, int, const int4 *, const SysTab *, int, float, int *, int *, int *, int4 *,
                          int *, int *, int *, int *, int *, int, int4 *, RunState *, int);
 int scan_tiles_for(int ncell);
 int force_slots_for(int need);
@@ -69,10 +69,10 @@ cudaError_t launch_force(cudaStream_t, bool, int, bool, int, int, int, int, cons
                          const int *, const SysTab *, const void *, const void *, int, void *, void *,
                          unsigned long long *, int *, int *, double *, RunState *, double *);
 cudaError_t launch_vv(cudaStream_t, bool, bool, int, int, dbl4 *, dbl4 *, int4 *, const int4 *, const void *,
-                      const void *, const unsigned long long *, const int *, const int *, const SysTab *,
-                      const SysCtl *, const double *, float, double *, RunState *);
+                      const void *, const unsigned long long *, const int *, const SysTab *, const SysCtl *,
+                      const double *, float, double *, RunState *);
 cudaError_t launch_gather_out(cudaStream_t, bool, int, const void *, const void *, const unsigned long long *,
-                              const int *, const int *, double *, RunState *);
+                              const int *, double *, RunState *);
 cudaError_t launch_ingest(cudaStream_t, int, const double *, const int *, int, int, const SysTab *, dbl4 *, int4 *,
                           RunState *);
 cudaError_t launch_ingest_vel(cudaStream_t, int, const double *, dbl4 *);

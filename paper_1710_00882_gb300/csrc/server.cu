@@ -215,7 +215,7 @@ int srv_vv(tersoff_server *s, cudaStream_t st)
   AtomState &X = cur_atoms(s);
   const float lim = (float)(0.25 * s->skin * s->skin);
   SK(launch_vv(st, s->mixed, false, (int)s->natoms, -1, X.x, X.v, X.q, s->L.qref, s->SC.contrib, s->SC.selfF,
-               s->SC.mask, s->L.nbr, s->L.rev, s->S.tab, s->S.ctl, s->P->d_mass, lim, s->SC.kepart, s->rs));
+               s->SC.mask, s->L.rev, s->S.tab, s->S.ctl, s->P->d_mass, lim, s->SC.kepart, s->rs));
   return TERSOFF_OK;
 }
 
