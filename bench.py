@@ -34,12 +34,21 @@ WORKLOAD = "Si diamond 40x40x40 = 512,000 atoms, sigma 0.05 A, 1000 K, Si(C), sk
 SKIN = 0.3
 DT = 1e-3
 
-# Algorithmic float32 operation counts of the force kernel (flops; FMA = 2), per
-# Verlet-list entry tested, per in-cutoff pair and per ordered triplet; counted from
-# force.cu (filter + pass A + pass B + outputs), transcendentals counted as 1 each.
-C_ENTRY = 12
-C_PAIR = 96
-C_TRIPLET = 74
+# Float32 operations of the mixed-precision force kernel as written in force.cu
+# (FMA = 2, add/sub/mul = 1, each rcp/rsqrt/lg2/ex2/sin/cos = 1; integer, load and
+# compare work not counted):
+#   per Verlet-list entry tested (fixed-point difference scaled, r^2):          8
+#   per in-cutoff pair: relative vector to ~1 ulp (30), |d| head+tail (41), unit
+#     vector (3), f_R and f_A with split exponents (38), b and db/dzeta (14),
+#     pair energy / dV/dr / dV/dzeta / force (19), self-force sum (3):        148
+#   per in-cutoff pair inside the f_C taper (R - D < r): w, sin, cos, f_C, f_C': 10
+#   per ordered triplet: each unordered pair {j,k} evaluates cos, g (12) and
+#     both zeta terms (6) in the first K loop and cos, g, g' and the force
+#     terms on j and k (62) in the second, shared by (i,j,k) and (i,k,j):     40
+C_ENTRY = 8
+C_PAIR = 148
+C_TAPER = 10
+C_TRIPLET = 40
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x 2 x max SM clock
 FP64_PEAK_TFLOPS = 1.25                              # GB300 nominal FP64
 
@@ -78,9 +87,10 @@ def allreduce_max(ws, x):
     return float(t.item())
 
 
-def workload_counts(s, rc):
-    """Verlet-list entries (r < rc + skin), in-cutoff ordered pairs P and ordered
-    triplets T of the starting configuration, counted with a periodic k-d tree."""
+def workload_counts(s, rc, r_in):
+    """Verlet-list entries (r < rc + skin), in-cutoff ordered pairs P, ordered pairs
+    inside the cutoff taper (r_in < r < rc) and ordered triplets T of the starting
+    configuration, counted with a periodic k-d tree (single-type cutoffs)."""
     from scipy.spatial import cKDTree
     pos = np.mod(s.pos, s.box)
     tree = cKDTree(pos, boxsize=s.box)
@@ -88,8 +98,9 @@ def workload_counts(s, rc):
     pairs = tree.query_pairs(rc, output_type="ndarray")
     deg = np.bincount(pairs.ravel(), minlength=s.n)
     P = int(deg.sum())
+    P_taper = P - tree.query_pairs(r_in, output_type="ndarray").shape[0] * 2
     T = int(np.sum(deg * (deg - 1)))
-    return n_list, P, T
+    return n_list, P, P_taper, T
 
 
 class ClockSampler:
@@ -155,7 +166,8 @@ def run_gpu(args, ws, rank, local):
     s = wl.si_512k(seed=3 + rank)
     tab, masses = pp.for_species(s.species)
     P = T.Params(ctx, tab, masses)
-    n_list, npair, ntrip = workload_counts(s, P.cutoff)
+    si = pp.SILICON
+    n_list, npair, ntaper, ntrip = workload_counts(s, P.cutoff, si.R1)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
 
     def timed(prec, steps, warmup):
@@ -206,7 +218,7 @@ def run_gpu(args, ws, rank, local):
     value64 = ws * s.n * len(ms_64) / (tot_64 / 1e3)
 
     # roofline of the dominant kernel (the force kernel), achieved from algorithmic flops
-    flops = C_ENTRY * n_list + C_PAIR * npair + C_TRIPLET * ntrip
+    flops = C_ENTRY * n_list + C_PAIR * npair + C_TAPER * ntaper + C_TRIPLET * ntrip
     # force phase per step (register kernel + overflow kernel) from the profiled pass
     f_ms = prof_mix[0][2] / st_mix["prof_steps"]
     f64_ms = prof_64[0][2] / st_64["prof_steps"]
@@ -268,7 +280,10 @@ def run_gpu(args, ws, rank, local):
                      "traffic": traffic, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
                      "algorithmic_flops_per_launch": flops, "force_phase_ms": f_ms,
                      "timing": "CUDA events around the force launches of a profiled pass of the same workload",
-                     "counts": {"list_entries": n_list, "pairs": npair, "triplets": ntrip}},
+                     "counts": {"list_entries": n_list, "pairs": npair, "taper_pairs": ntaper,
+                                "triplets": ntrip},
+                     "flops_per_unit": {"list_entry": C_ENTRY, "pair": C_PAIR, "taper_pair": C_TAPER,
+                                        "ordered_triplet": C_TRIPLET}},
         "gpu_launches": launches,
         "rebuilds_in_timed_steps": {"mixed": st_mix["rebuilds"], "fp64": st_64["rebuilds"]},
         "clocks": clk,
