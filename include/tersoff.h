@@ -161,12 +161,12 @@ int tersoff_md_stats(tersoff_md *md, int64_t *steps, int64_t *rebuilds, int32_t 
  * bracketed phase by phase with CUDA events on the context's stream.
  * tersoff_md_profile(md, 1) starts (and resets) recording, (md, 0) stops it.
  * tersoff_md_profile_read waits for the stream and returns, summed over the
- * recorded steps, ms[4] = {integrator (force gather, kicks, drift), neighbour-
+ * recorded steps, ms[5] = {integrator (force gather, kicks, drift), neighbour-
  * list build (launched every step, skipped on the device when no atom moved
- * skin/2), force kernel, step bookkeeping} and launches[4] = kernel launches of
- * each phase. */
+ * skin/2), register force kernel, overflow force kernel and energy/virial
+ * reduction, step bookkeeping} and launches[5] = kernel launches of each phase. */
 int tersoff_md_profile(tersoff_md *md, int enable);
-int tersoff_md_profile_read(tersoff_md *md, double ms[4], int64_t launches[4]);
+int tersoff_md_profile_read(tersoff_md *md, double ms[5], int64_t launches[5]);
 void tersoff_md_destroy(tersoff_md *md);
 
 /* one call: create, step nsteps, copy pos/vel back in place, destroy */
@@ -210,7 +210,7 @@ int tersoff_md_run(tersoff_ctx *ctx, double *pos, double *vel, const int32_t *ty
 #define TERSOFF_NOALLOC_MAX_ATOMS 16384
 #define TERSOFF_NOALLOC_MAX_NEIGHBORS 32
 #define TERSOFF_NOALLOC_MAX_CELLS 32768
-#define TERSOFF_NOALLOC_SCRATCH_BYTES 23519744
+#define TERSOFF_NOALLOC_SCRATCH_BYTES 23539200
 int tersoff_compute_noalloc(const tersoff_params *params, const double *pos, const int32_t *types, int64_t N,
                             const double box[3], tersoff_precision prec, void *stream, double *energy_virial,
                             double *forces, char *errbuf, size_t errlen);
@@ -251,6 +251,9 @@ typedef struct {
   int64_t chunks, repacks;
   double busy_s;         /* wall time with jobs resident */
   int64_t capacity_atoms;
+  /* scheduler wall time by activity (s): retiring finished jobs, repacking the
+   * layout on admission, capturing graphs, running chunks of steps */
+  double retire_s, repack_s, graph_s, run_s;
 } tersoff_server_stats;
 
 int tersoff_server_create(tersoff_ctx *ctx, const tersoff_params *params, tersoff_precision prec, double skin,

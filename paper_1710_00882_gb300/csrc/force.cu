@@ -218,7 +218,7 @@ __device__ __forceinline__ void block_partial(const R (&v)[7], bool eflag, bool 
 // fast kernel: register slots, unordered neighbour pairs
 
 template <class R, int MAXNC, bool ONE, bool EFLAG, bool VFLAG>
-__global__ void __launch_bounds__(FAST_THREADS)
+__global__ void __launch_bounds__(FAST_THREADS, (sizeof(R) == 4 && MAXNC == 4) ? 7 : 1)
 k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const int *__restrict__ nbr,
             const int *__restrict__ cnt, const SysTab *__restrict__ sys, const PairP<R> *__restrict__ gpairs,
             const TripP<R> *__restrict__ gtrips, int nt, typename V4t<R>::type *__restrict__ contrib,
@@ -531,6 +531,45 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
 }
 
 // ============================================================================
+// off[k] = sum of in[0..k) for k <= n (n <= GEN_SUB), computed by the T threads of a
+// block: each thread sums a run of entries, then the runs are offset in order.
+constexpr int GEN_SUB = 256;
+template <int T>
+__device__ __forceinline__ void block_exclusive_offsets(const int *__restrict__ in, int n, int *off)
+{
+  constexpr int PER = (GEN_SUB + T - 1) / T;
+  __shared__ int runs[T + 1];
+  const int t = threadIdx.x;
+  int v[PER], sum = 0;
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const int idx = t * PER + k;
+    v[k] = idx < n ? in[idx] : 0;
+    sum += v[k];
+  }
+  runs[t] = sum;
+  __syncthreads();
+  if (t == 0) {
+    int acc = 0;
+    for (int k = 0; k < T; ++k) {
+      const int x = runs[k];
+      runs[k] = acc;
+      acc += x;
+    }
+    runs[T] = acc;
+  }
+  __syncthreads();
+  int acc = runs[t];
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const int idx = t * PER + k;
+    if (idx < n) off[idx] = acc;
+    acc += v[k];
+  }
+  if (t == 0) off[n] = runs[T];
+  __syncthreads();
+}
+
 // general kernel: per-thread shared-memory slots, ordered (j,k) loops
 
 constexpr int NRF = 12;   // real fields per slot
@@ -546,7 +585,7 @@ struct GenCfg {
 
 // Evaluates atoms either all (work == nullptr: atom = global thread index) or the
 // overflow atoms queued by the fast kernel (work/nwork: per fast block, in order;
-// block b of this kernel takes fast blocks b, b + gridDim.x, ...).
+// block b of this kernel takes a contiguous run of fast blocks as one flat queue).
 template <class R, int MAXNC, bool EFLAG, bool VFLAG>
 __global__ void __launch_bounds__(GenCfg<R, MAXNC>::threads)
 k_force_gen(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const int *__restrict__ nbr,
@@ -584,206 +623,221 @@ k_force_gen(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
   bool overflow = false;
   int maxnc = 0;
 
-  // the atoms of this thread
-  const int nouter = work ? (nfast + (int)gridDim.x - 1) / (int)gridDim.x : 1;
-  for (int ob = 0; ob < nouter; ++ob) {
-    const int fb = blockIdx.x + ob * gridDim.x;
-    int cntb = 1;
-    if (work) {
-      if (fb >= nfast) break;
-      cntb = nwork[fb];
+  // one atom: in-cutoff slots, first K loop and pair terms, second K loop, outputs
+  auto process = [&](const int i) {
+    int ti, w;
+    int4 qi = make_int4(0, 0, 0, 0);
+    dbl4 xi = make_dbl4(0, 0, 0, 0);
+    if (MIXED) {
+      qi = q[i];
+      w = qi.w;
+    } else {
+      xi = x[i];
+      w = (int)__double_as_longlong(xi.w);
     }
-    for (int k = t; k < (work ? cntb : T); k += T) {
-      const int i = work ? work[(size_t)fb * FAST_THREADS + k] : (int)blockIdx.x * T + t;
-      if (i >= N) continue;
-      int ti, w;
-      int4 qi = make_int4(0, 0, 0, 0);
-      dbl4 xi = make_dbl4(0, 0, 0, 0);
+    ti = type_of(w);
+    const Geom *gp = &sys[sys_of(w)].geo;
+    int nc = 0;
+    unsigned long long mbits = 0ull;
+    const int n = cnt[i];
+    for (int s = 0; s < n; ++s) {
+      const int j = nbr[(size_t)s * N + i];
+      R dx, dy, dz;
+      int tj;
       if (MIXED) {
-        qi = q[i];
-        w = qi.w;
+        const int4 qj = q[j];
+        tj = type_of(qj.w);
+        dx = (R)q_scaled(qdiff(qj.x, qi.x), gp->q_to_f[0]);
+        dy = (R)q_scaled(qdiff(qj.y, qi.y), gp->q_to_f[1]);
+        dz = (R)q_scaled(qdiff(qj.z, qi.z), gp->q_to_f[2]);
       } else {
-        xi = x[i];
-        w = (int)__double_as_longlong(xi.w);
+        const dbl4 xj = x[j];
+        tj = type_of((int)__double_as_longlong(xj.w));
+        dx = (R)min_image(__dsub_rn(xj.x, xi.x), gp->L[0], gp->invL[0]);
+        dy = (R)min_image(__dsub_rn(xj.y, xi.y), gp->L[1], gp->invL[1]);
+        dz = (R)min_image(__dsub_rn(xj.z, xi.z), gp->L[2], gp->invL[2]);
       }
-      ti = type_of(w);
-      const Geom *gp = &sys[sys_of(w)].geo;
-      int nc = 0;
-      unsigned long long mbits = 0ull;
-      const int n = cnt[i];
-      for (int s = 0; s < n; ++s) {
-        const int j = nbr[(size_t)s * N + i];
-        R dx, dy, dz;
-        int tj;
-        if (MIXED) {
-          const int4 qj = q[j];
-          tj = type_of(qj.w);
-          dx = (R)q_scaled(qdiff(qj.x, qi.x), gp->q_to_f[0]);
-          dy = (R)q_scaled(qdiff(qj.y, qi.y), gp->q_to_f[1]);
-          dz = (R)q_scaled(qdiff(qj.z, qi.z), gp->q_to_f[2]);
-        } else {
-          const dbl4 xj = x[j];
-          tj = type_of((int)__double_as_longlong(xj.w));
-          dx = (R)min_image(__dsub_rn(xj.x, xi.x), gp->L[0], gp->invL[0]);
-          dy = (R)min_image(__dsub_rn(xj.y, xi.y), gp->L[1], gp->invL[1]);
-          dz = (R)min_image(__dsub_rn(xj.z, xi.z), gp->L[2], gp->invL[2]);
-        }
-        const R r2 = r2_decide(dx, dy, dz);
-        const PairP<R> &P = pairs[ti * nt + tj];
-        if (r2 < P.rc2) {
-          if (nc < MAXNC) {
-            R r, rlo, inv;
-            if (MIXED) {
-              const int4 qj = q[j];
-              float dh[3], dl[3];
-              qd_fine(qdiff(qj.x, qi.x), gp->q_to_f[0], gp->q_to_f_lo[0], dh[0], dl[0]);
-              qd_fine(qdiff(qj.y, qi.y), gp->q_to_f[1], gp->q_to_f_lo[1], dh[1], dl[1]);
-              qd_fine(qdiff(qj.z, qi.z), gp->q_to_f[2], gp->q_to_f_lo[2], dh[2], dl[2]);
-              float rh_, rl_, irh_;
-              norm_fine(dh, dl, rh_, rl_, irh_);
-              dx = (R)dh[0]; dy = (R)dh[1]; dz = (R)dh[2];
-              r = (R)rh_; rlo = (R)rl_; inv = (R)irh_;
-            } else {
-              const R rf2 = r2_decide(dx, dy, dz);
-              inv = M::rsqrt(rf2);
-              r = rf2 * inv;
-              rlo = R(0);
-            }
-            R fcv, dfcv;
-            cutoff_fn<M>(r, rlo, P, fcv, dfcv);
-            SLOT(S_UX, nc) = dx * inv;
-            SLOT(S_UY, nc) = dy * inv;
-            SLOT(S_UZ, nc) = dz * inv;
-            SLOT(S_R, nc) = r;
-            SLOT(S_RL, nc) = rlo;
-            SLOT(S_IR, nc) = inv;
-            SLOT(S_FC, nc) = fcv;
-            SLOT(S_DFC, nc) = dfcv;
-            META(nc) = s | (tj << 8);
+      const R r2 = r2_decide(dx, dy, dz);
+      const PairP<R> &P = pairs[ti * nt + tj];
+      if (r2 < P.rc2) {
+        if (nc < MAXNC) {
+          R r, rlo, inv;
+          if (MIXED) {
+            const int4 qj = q[j];
+            float dh[3], dl[3];
+            qd_fine(qdiff(qj.x, qi.x), gp->q_to_f[0], gp->q_to_f_lo[0], dh[0], dl[0]);
+            qd_fine(qdiff(qj.y, qi.y), gp->q_to_f[1], gp->q_to_f_lo[1], dh[1], dl[1]);
+            qd_fine(qdiff(qj.z, qi.z), gp->q_to_f[2], gp->q_to_f_lo[2], dh[2], dl[2]);
+            float rh_, rl_, irh_;
+            norm_fine(dh, dl, rh_, rl_, irh_);
+            dx = (R)dh[0]; dy = (R)dh[1]; dz = (R)dh[2];
+            r = (R)rh_; rlo = (R)rl_; inv = (R)irh_;
+          } else {
+            const R rf2 = r2_decide(dx, dy, dz);
+            inv = M::rsqrt(rf2);
+            r = rf2 * inv;
+            rlo = R(0);
           }
-          ++nc;
-          mbits |= 1ull << s;
+          R fcv, dfcv;
+          cutoff_fn<M>(r, rlo, P, fcv, dfcv);
+          SLOT(S_UX, nc) = dx * inv;
+          SLOT(S_UY, nc) = dy * inv;
+          SLOT(S_UZ, nc) = dz * inv;
+          SLOT(S_R, nc) = r;
+          SLOT(S_RL, nc) = rlo;
+          SLOT(S_IR, nc) = inv;
+          SLOT(S_FC, nc) = fcv;
+          SLOT(S_DFC, nc) = dfcv;
+          META(nc) = s | (tj << 8);
         }
+        ++nc;
+        mbits |= 1ull << s;
       }
-      maxnc = max(maxnc, nc);
-      if (nc > MAXNC) {
-        overflow = true;
-        continue;
-      }
+    }
+    maxnc = max(maxnc, nc);
+    if (nc > MAXNC) {
+      overflow = true;
+      return;
+    }
 
-      // first K loop and pair terms
-      R e_atom = R(0);
-      for (int a = 0; a < nc; ++a) {
-        const int tj = META(a) >> 8;
-        const R uax = SLOT(S_UX, a), uay = SLOT(S_UY, a), uaz = SLOT(S_UZ, a), ra = SLOT(S_R, a);
-        const TripP<R> *Tj = trips + (ti * nt + tj) * nt;
-        R zeta = R(0);
-        for (int b = 0; b < nc; ++b) {
-          if (b == a) continue;
-          const TripP<R> &Tp = Tj[META(b) >> 8];
-          const R cost = uax * SLOT(S_UX, b) + uay * SLOT(S_UY, b) + uaz * SLOT(S_UZ, b);
-          const R u = Tp.h - cost;
-          const R u2 = u * u;
-          const R g = Tp.gamma + Tp.K * u2 * M::rcp(Tp.d2 + u2);
-          R ex = R(1);
-          if (Tp.lam3 != R(0)) {
-            R arg = Tp.lam3 * (ra - SLOT(S_R, b));
-            if (Tp.m3 != R(0)) arg = arg * arg * arg;
-            ex = M::expv(arg);
+    // first K loop and pair terms
+    R e_atom = R(0);
+    for (int a = 0; a < nc; ++a) {
+      const int tj = META(a) >> 8;
+      const R uax = SLOT(S_UX, a), uay = SLOT(S_UY, a), uaz = SLOT(S_UZ, a), ra = SLOT(S_R, a);
+      const TripP<R> *Tj = trips + (ti * nt + tj) * nt;
+      R zeta = R(0);
+      for (int b = 0; b < nc; ++b) {
+        if (b == a) continue;
+        const TripP<R> &Tp = Tj[META(b) >> 8];
+        const R cost = uax * SLOT(S_UX, b) + uay * SLOT(S_UY, b) + uaz * SLOT(S_UZ, b);
+        const R u = Tp.h - cost;
+        const R u2 = u * u;
+        const R g = Tp.gamma + Tp.K * u2 * M::rcp(Tp.d2 + u2);
+        R ex = R(1);
+        if (Tp.lam3 != R(0)) {
+          R arg = Tp.lam3 * (ra - SLOT(S_R, b));
+          if (Tp.m3 != R(0)) arg = arg * arg * arg;
+          ex = M::expv(arg);
+        }
+        zeta += SLOT(S_FC, b) * g * ex;
+      }
+      const PairP<R> &P = pairs[ti * nt + tj];
+      const R fcv = SLOT(S_FC, a), dfcv = SLOT(S_DFC, a);
+      const R fR = P.A * M::expneg(P.lam1, P.lam1_lo, ra, SLOT(S_RL, a));
+      const R fA = -P.B * M::expneg(P.lam2, P.lam2_lo, ra, SLOT(S_RL, a));
+      R bij, dbij;
+      bond_order<M>(zeta, P, bij, dbij);
+      const R pr = fR + bij * fA;
+      red[0] += R(0.5) * fcv * pr;
+      e_atom += R(0.5) * fcv * pr;
+      const R dvdr = R(0.5) * (dfcv * pr + fcv * (-P.lam1 * fR - bij * P.lam2 * fA));
+      SLOT(S_DZ, a) = R(0.5) * fcv * fA * dbij;
+      SLOT(S_FX, a) = -dvdr * uax;
+      SLOT(S_FY, a) = -dvdr * uay;
+      SLOT(S_FZ, a) = -dvdr * uaz;
+    }
+
+    // second K loop
+    for (int a = 0; a < nc; ++a) {
+      const R dzv = SLOT(S_DZ, a);
+      if (dzv == R(0)) continue;
+      const int tj = META(a) >> 8;
+      const R uax = SLOT(S_UX, a), uay = SLOT(S_UY, a), uaz = SLOT(S_UZ, a), ra = SLOT(S_R, a),
+              ira = SLOT(S_IR, a);
+      const TripP<R> *Tj = trips + (ti * nt + tj) * nt;
+      R fjx = R(0), fjy = R(0), fjz = R(0);
+      for (int b = 0; b < nc; ++b) {
+        if (b == a) continue;
+        const TripP<R> &Tp = Tj[META(b) >> 8];
+        const R ubx = SLOT(S_UX, b), uby = SLOT(S_UY, b), ubz = SLOT(S_UZ, b), irb = SLOT(S_IR, b);
+        const R cost = uax * ubx + uay * uby + uaz * ubz;
+        const R u = Tp.h - cost;
+        const R u2 = u * u;
+        const R inv = M::rcp(Tp.d2 + u2);
+        const R g = Tp.gamma + Tp.K * u2 * inv;
+        const R dg = -Tp.G2 * u * inv * inv;
+        R ex = R(1), darg = R(0);
+        if (Tp.lam3 != R(0)) {
+          const R tt = Tp.lam3 * (ra - SLOT(S_R, b));
+          R arg = tt;
+          darg = Tp.lam3;
+          if (Tp.m3 != R(0)) {
+            arg = tt * tt * tt;
+            darg = R(3) * Tp.lam3 * tt * tt;
           }
-          zeta += SLOT(S_FC, b) * g * ex;
+          ex = M::expv(arg);
         }
-        const PairP<R> &P = pairs[ti * nt + tj];
-        const R fcv = SLOT(S_FC, a), dfcv = SLOT(S_DFC, a);
-        const R fR = P.A * M::expneg(P.lam1, P.lam1_lo, ra, SLOT(S_RL, a));
-        const R fA = -P.B * M::expneg(P.lam2, P.lam2_lo, ra, SLOT(S_RL, a));
-        R bij, dbij;
-        bond_order<M>(zeta, P, bij, dbij);
-        const R pr = fR + bij * fA;
-        red[0] += R(0.5) * fcv * pr;
-        e_atom += R(0.5) * fcv * pr;
-        const R dvdr = R(0.5) * (dfcv * pr + fcv * (-P.lam1 * fR - bij * P.lam2 * fA));
-        SLOT(S_DZ, a) = R(0.5) * fcv * fA * dbij;
-        SLOT(S_FX, a) = -dvdr * uax;
-        SLOT(S_FY, a) = -dvdr * uay;
-        SLOT(S_FZ, a) = -dvdr * uaz;
+        const R fcb = SLOT(S_FC, b), dfcb = SLOT(S_DFC, b);
+        const R a1 = fcb * ex * dg;
+        const R a2 = fcb * ex * g * darg;
+        const R a3 = dfcb * g * ex;
+        const R cj = a1 * ira;
+        const R dzjx = cj * (ubx - cost * uax) + a2 * uax;
+        const R dzjy = cj * (uby - cost * uay) + a2 * uay;
+        const R dzjz = cj * (ubz - cost * uaz) + a2 * uaz;
+        const R ck = a1 * irb;
+        const R dzkx = (a3 - a2) * ubx + ck * (uax - cost * ubx);
+        const R dzky = (a3 - a2) * uby + ck * (uay - cost * uby);
+        const R dzkz = (a3 - a2) * ubz + ck * (uaz - cost * ubz);
+        fjx -= dzv * dzjx;
+        fjy -= dzv * dzjy;
+        fjz -= dzv * dzjz;
+        SLOT(S_FX, b) -= dzv * dzkx;
+        SLOT(S_FY, b) -= dzv * dzky;
+        SLOT(S_FZ, b) -= dzv * dzkz;
       }
+      SLOT(S_FX, a) += fjx;
+      SLOT(S_FY, a) += fjy;
+      SLOT(S_FZ, a) += fjz;
+    }
 
-      // second K loop
-      for (int a = 0; a < nc; ++a) {
-        const R dzv = SLOT(S_DZ, a);
-        if (dzv == R(0)) continue;
-        const int tj = META(a) >> 8;
-        const R uax = SLOT(S_UX, a), uay = SLOT(S_UY, a), uaz = SLOT(S_UZ, a), ra = SLOT(S_R, a),
-                ira = SLOT(S_IR, a);
-        const TripP<R> *Tj = trips + (ti * nt + tj) * nt;
-        R fjx = R(0), fjy = R(0), fjz = R(0);
-        for (int b = 0; b < nc; ++b) {
-          if (b == a) continue;
-          const TripP<R> &Tp = Tj[META(b) >> 8];
-          const R ubx = SLOT(S_UX, b), uby = SLOT(S_UY, b), ubz = SLOT(S_UZ, b), irb = SLOT(S_IR, b);
-          const R cost = uax * ubx + uay * uby + uaz * ubz;
-          const R u = Tp.h - cost;
-          const R u2 = u * u;
-          const R inv = M::rcp(Tp.d2 + u2);
-          const R g = Tp.gamma + Tp.K * u2 * inv;
-          const R dg = -Tp.G2 * u * inv * inv;
-          R ex = R(1), darg = R(0);
-          if (Tp.lam3 != R(0)) {
-            const R tt = Tp.lam3 * (ra - SLOT(S_R, b));
-            R arg = tt;
-            darg = Tp.lam3;
-            if (Tp.m3 != R(0)) {
-              arg = tt * tt * tt;
-              darg = R(3) * Tp.lam3 * tt * tt;
-            }
-            ex = M::expv(arg);
-          }
-          const R fcb = SLOT(S_FC, b), dfcb = SLOT(S_DFC, b);
-          const R a1 = fcb * ex * dg;
-          const R a2 = fcb * ex * g * darg;
-          const R a3 = dfcb * g * ex;
-          const R cj = a1 * ira;
-          const R dzjx = cj * (ubx - cost * uax) + a2 * uax;
-          const R dzjy = cj * (uby - cost * uay) + a2 * uay;
-          const R dzjz = cj * (ubz - cost * uaz) + a2 * uaz;
-          const R ck = a1 * irb;
-          const R dzkx = (a3 - a2) * ubx + ck * (uax - cost * ubx);
-          const R dzky = (a3 - a2) * uby + ck * (uay - cost * uby);
-          const R dzkz = (a3 - a2) * ubz + ck * (uaz - cost * ubz);
-          fjx -= dzv * dzjx;
-          fjy -= dzv * dzjy;
-          fjz -= dzv * dzjz;
-          SLOT(S_FX, b) -= dzv * dzkx;
-          SLOT(S_FY, b) -= dzv * dzky;
-          SLOT(S_FZ, b) -= dzv * dzkz;
-        }
-        SLOT(S_FX, a) += fjx;
-        SLOT(S_FY, a) += fjy;
-        SLOT(S_FZ, a) += fjz;
-      }
-
-      R fix = R(0), fiy = R(0), fiz = R(0);
-      for (int a = 0; a < nc; ++a) {
-        const R fx = SLOT(S_FX, a), fy = SLOT(S_FY, a), fz = SLOT(S_FZ, a);
-        fix -= fx;
-        fiy -= fy;
-        fiz -= fz;
-        V4 c;
-        c.x = fx; c.y = fy; c.z = fz; c.w = R(0);
-        contrib[(size_t)(META(a) & 0xff) * N + i] = c;
-        if (VFLAG) {
-          const R r = SLOT(S_R, a);
-          const R dx = r * SLOT(S_UX, a), dy = r * SLOT(S_UY, a), dz = r * SLOT(S_UZ, a);
-          red[1] += dx * fx; red[2] += dy * fy; red[3] += dz * fz;
-          red[4] += dx * fy; red[5] += dx * fz; red[6] += dy * fz;
-        }
-      }
+    R fix = R(0), fiy = R(0), fiz = R(0);
+    for (int a = 0; a < nc; ++a) {
+      const R fx = SLOT(S_FX, a), fy = SLOT(S_FY, a), fz = SLOT(S_FZ, a);
+      fix -= fx;
+      fiy -= fy;
+      fiz -= fz;
       V4 c;
-      c.x = fix; c.y = fiy; c.z = fiz; c.w = R(0);
-      selfF[i] = c;
-      mask[i] = mbits;
-      if (eatom) eatom[i] = (double)e_atom;
+      c.x = fx; c.y = fy; c.z = fz; c.w = R(0);
+      contrib[(size_t)(META(a) & 0xff) * N + i] = c;
+      if (VFLAG) {
+        const R r = SLOT(S_R, a);
+        const R dx = r * SLOT(S_UX, a), dy = r * SLOT(S_UY, a), dz = r * SLOT(S_UZ, a);
+        red[1] += dx * fx; red[2] += dy * fy; red[3] += dz * fz;
+        red[4] += dx * fy; red[5] += dx * fz; red[6] += dy * fz;
+      }
+    }
+    V4 c;
+    c.x = fix; c.y = fiy; c.z = fiz; c.w = R(0);
+    selfF[i] = c;
+    mask[i] = mbits;
+    if (eatom) eatom[i] = (double)e_atom;
+  };
+
+  if (!work) {
+    const int i = (int)blockIdx.x * T + t;
+    if (i < N) process(i);
+  } else {
+    // Overflow queues of the register kernel: block b takes the contiguous run of
+    // fast blocks [b G, (b + 1) G), G = ceil(nfast / gridDim.x), as one flat queue in
+    // order (GEN_SUB fast blocks per pass) and its threads take entries t, t + T, ...
+    __shared__ int qoff[GEN_SUB + 1];
+    const int G = (nfast + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int fb0 = (int)blockIdx.x * G, fb1 = min(fb0 + G, nfast);
+    for (int sb = fb0; sb < fb1; sb += GEN_SUB) {
+      const int ns = min(GEN_SUB, fb1 - sb);
+      block_exclusive_offsets<T>(nwork + sb, ns, qoff);
+      const int total = qoff[ns];
+      for (int pidx = t; pidx < total; pidx += T) {
+        int lo = 0, hi = ns - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (qoff[mid] <= pidx) lo = mid; else hi = mid - 1;
+        }
+        process(work[(size_t)(sb + lo) * FAST_THREADS + (pidx - qoff[lo])]);
+      }
+      __syncthreads();
     }
   }
   if (overflow) atomicOr(&rs->status, ST_NC_OVERFLOW);
@@ -931,7 +985,7 @@ int force_slots_for(int need)
   return 64;
 }
 
-int force_gen_blocks() { return 2 * 152; }
+int force_gen_blocks() { return GEN_BLOCKS; }
 
 // Rows of 8 doubles the partial-sum buffer needs for N atoms (any launch shape).
 int force_partial_rows(int N) { return (N + 31) / 32 + force_gen_blocks(); }
@@ -940,30 +994,34 @@ int force_partial_rows(int N) { return (N + 31) / 32 + force_gen_blocks(); }
 // general kernel (gen_slots wide) over its overflow queue; fast_slots 0 runs the
 // general kernel over all atoms.  Buffers: partial force_partial_rows(N) x 8
 // doubles; work N ints; nwork ceil(N/128) ints.  With eflag/vflag the energy and
-// virial are added to rs->epot / rs->virial.
-cudaError_t launch_force(cudaStream_t st, bool mixed, int fast_slots, bool one_type, int gen_slots, int eflag,
-                         int vflag, int N, const dbl4 *x, const int4 *q, const int *nbr, const int *cnt,
-                         const SysTab *sys, const void *pairs, const void *trips, int nt, void *contrib, void *selfF,
-                         unsigned long long *mask, int *work, int *nwork, double *partial, RunState *rs,
-                         double *eatom)
+// virial are added to rs->epot / rs->virial.  part: 1 launches the register
+// kernel only, 2 the rest (general kernel and reduction), 3 both.
+cudaError_t launch_force_part(int part, cudaStream_t st, bool mixed, int fast_slots, bool one_type, int gen_slots,
+                              int eflag, int vflag, int N, const dbl4 *x, const int4 *q, const int *nbr,
+                              const int *cnt, const SysTab *sys, const void *pairs, const void *trips, int nt,
+                              void *contrib, void *selfF, unsigned long long *mask, int *work, int *nwork,
+                              double *partial, RunState *rs, double *eatom)
 {
   if (N == 0) return cudaSuccess;
   const int nfast = (N + FAST_THREADS - 1) / FAST_THREADS;
   cudaError_t e = cudaSuccess;
   int rows = 0;
   if (fast_slots > 0) {
+    if (part & 1) {
 #define TSF_REG(R, NC)                                                                                              \
   e = one_type ? launch_reg<R, NC, true>(st, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib, selfF, \
                                          mask, work, nwork, partial, rs, eatom)                                     \
                : launch_reg<R, NC, false>(st, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib,      \
                                           selfF, mask, work, nwork, partial, rs, eatom);
-    if (mixed) {
-      if (fast_slots <= 4) { TSF_REG(float, 4) } else { TSF_REG(float, 8) }
-    } else {
-      if (fast_slots <= 4) { TSF_REG(double, 4) } else { TSF_REG(double, 8) }
-    }
+      if (mixed) {
+        if (fast_slots <= 4) { TSF_REG(float, 4) } else { TSF_REG(float, 8) }
+      } else {
+        if (fast_slots <= 4) { TSF_REG(double, 4) } else { TSF_REG(double, 8) }
+      }
 #undef TSF_REG
-    if (e != cudaSuccess) return e;
+      if (e != cudaSuccess) return e;
+    }
+    if (!(part & 2)) return cudaSuccess;
     double *gp = partial + (size_t)nfast * 8;
     e = mixed ? launch_gen_any<float>(st, gen_slots, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib,
                                       selfF, mask, work, nwork, nfast, force_gen_blocks(), gp, rs, eatom)
@@ -971,6 +1029,7 @@ cudaError_t launch_force(cudaStream_t st, bool mixed, int fast_slots, bool one_t
                                        selfF, mask, work, nwork, nfast, force_gen_blocks(), gp, rs, eatom);
     rows = nfast + force_gen_blocks();
   } else {
+    if (!(part & 2)) return cudaSuccess;
     e = mixed ? launch_gen_any<float>(st, gen_slots, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib,
                                       selfF, mask, nullptr, nullptr, 0, 0, partial, rs, eatom)
               : launch_gen_any<double>(st, gen_slots, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib,
@@ -984,6 +1043,16 @@ cudaError_t launch_force(cudaStream_t st, bool mixed, int fast_slots, bool one_t
     e = cudaGetLastError();
   }
   return e;
+}
+
+cudaError_t launch_force(cudaStream_t st, bool mixed, int fast_slots, bool one_type, int gen_slots, int eflag,
+                         int vflag, int N, const dbl4 *x, const int4 *q, const int *nbr, const int *cnt,
+                         const SysTab *sys, const void *pairs, const void *trips, int nt, void *contrib, void *selfF,
+                         unsigned long long *mask, int *work, int *nwork, double *partial, RunState *rs,
+                         double *eatom)
+{
+  return launch_force_part(3, st, mixed, fast_slots, one_type, gen_slots, eflag, vflag, N, x, q, nbr, cnt, sys, pairs,
+                           trips, nt, contrib, selfF, mask, work, nwork, partial, rs, eatom);
 }
 
 }  // namespace tsf

@@ -92,13 +92,6 @@ __device__ __forceinline__ void gather_force(int m, int N, const typename V4g<R>
   acc.out(fx, fy, fz);
 }
 
-// round(x * to_q) mod 2^32 with one rounding: adding 1.5 * 2^52 inside the FMA puts
-// the nearest integer in the low mantissa bits (valid for |x * to_q| < 2^51).
-__device__ __forceinline__ int fixed_q(double x, double to_q)
-{
-  return __double2loint(fma(x, to_q, 6755399441055744.0));
-}
-
 __device__ __forceinline__ double warp_sum_d(double v)
 {
 #pragma unroll
@@ -174,9 +167,8 @@ template <class R, bool KE>
 __global__ void k_vv(int N, int mode, dbl4 *__restrict__ x, dbl4 *__restrict__ v, int4 *__restrict__ q,
                      const int4 *__restrict__ qref, const typename V4g<R>::type *__restrict__ contrib,
                      const typename V4g<R>::type *__restrict__ selfF, const unsigned long long *__restrict__ mask,
-                     const int *__restrict__ rev, const SysTab *__restrict__ sys,
-                     const SysCtl *__restrict__ ctl, const double *__restrict__ mass, float disp2_lim,
-                     double *__restrict__ kepart, RunState *rs)
+                     const int *__restrict__ rev, const SysTab *__restrict__ sys, SysCtl *__restrict__ ctl,
+                     const double *__restrict__ mass, float disp2_lim, double *__restrict__ kepart, RunState *rs)
 {
   __shared__ double sw[8];
   if (rs->status != 0) return;
@@ -225,6 +217,7 @@ __global__ void k_vv(int N, int mode, dbl4 *__restrict__ x, dbl4 *__restrict__ v
       const float dy = (float)qdiff(qi.y, qr.y) * geo.q_to_f[1];
       const float dz = (float)qdiff(qi.z, qr.z) * geo.q_to_f[2];
       moved = dx * dx + dy * dy + dz * dz > disp2_lim;
+      if (moved && ctl[sid].rebuild == 0) atomicOr(&ctl[sid].rebuild, 1);
     }
     v[i] = vi;
   }
@@ -296,6 +289,7 @@ __global__ void k_step_end(RunState *rs, SysCtl *ctl, int nsys, cudaGraphConditi
     } else if (C.open) {
       C.open = 0;
     }
+    C.rebuild = 0;
   }
   if (threadIdx.x != 0) return;
   const long long k = rs->trace_k;
@@ -366,7 +360,7 @@ __global__ void k_force_done(RunState *rs)
 
 cudaError_t launch_vv(cudaStream_t st, bool mixed, bool ke, int N, int mode, dbl4 *x, dbl4 *v, int4 *q,
                       const int4 *qref, const void *contrib, const void *selfF, const unsigned long long *mask,
-                      const int *rev, const SysTab *sys, const SysCtl *ctl, const double *mass, float disp2_lim,
+                      const int *rev, const SysTab *sys, SysCtl *ctl, const double *mass, float disp2_lim,
                       double *kepart, RunState *rs)
 {
   if (N == 0) return cudaSuccess;

@@ -102,8 +102,19 @@ __device__ __forceinline__ double min_image(double d, double L, double invL)
 {
   return __fma_rn(-L, rint(__dmul_rn(d, invL)), d);
 }
+// round(x * to_q) mod 2^32 with one rounding: adding 1.5 * 2^52 inside the FMA puts
+// the nearest integer in the low mantissa bits (valid for |x * to_q| < 2^51).
+__device__ __forceinline__ int fixed_q(double x, double to_q)
+{
+  return __double2loint(fma(x, to_q, 6755399441055744.0));
+}
+
 // fixed-point difference scaled to Angstrom, one rounding
 __device__ __forceinline__ float q_scaled(int dq, float s) { return __fmul_rn((float)dq, s); }
+
+// blocks of the general force kernel over the register kernel's overflow queues:
+// four per SM of a GB300 (its shared-memory slots fit four blocks per SM)
+constexpr int GEN_BLOCKS = 4 * 152;
 
 constexpr int ST_BAD_TYPE = 32;
 constexpr double ACCEL = 1.602176634e-19 / 1.66053906660e-27 * 1e-4;   // (eV/A)/amu in A/ps^2
@@ -130,7 +141,7 @@ struct SysTab {
 struct SysCtl {
   long long steps_left;     // steps this system still runs
   int open;                 // velocities at the half step: a closing kick is pending
-  int pad;
+  int rebuild;              // some atom of this system moved skin/2 since its last list build
 };
 
 struct CellGrid {

@@ -195,7 +195,8 @@ __device__ __forceinline__ void sort_column(int *__restrict__ nbr, int N, int i,
 // |d_ij| < r_list, then sort the column by j so that the list order depends only on
 // the set of neighbours.
 __global__ void __launch_bounds__(128) k_build(int N, const int4 *__restrict__ q, const SysTab *__restrict__ sys,
-                                               float rl2, const int *__restrict__ cell_start,
+                                               const SysCtl *__restrict__ ctl, float rl2,
+                                               const int *__restrict__ cell_start,
                                                const int4 *__restrict__ cell_atoms, int *__restrict__ nbr,
                                                int *__restrict__ cnt, int cap, int4 *__restrict__ qref, RunState *rs,
                                                int gated)
@@ -206,6 +207,8 @@ __global__ void __launch_bounds__(128) k_build(int N, const int4 *__restrict__ q
   if (t >= N) return;
   const int i = cell_atoms[t].w;
   const int4 pi = q[i];
+  // per-system builds: a system none of whose atoms moved skin/2 keeps its lists
+  if (ctl && ctl[sys_of(pi.w)].rebuild == 0) return;
   qref[i] = pi;
   const SysTab &T = sys[sys_of(pi.w)];
   const float s0 = T.geo.q_to_f[0], s1 = T.geo.q_to_f[1], s2 = T.geo.q_to_f[2];
@@ -295,25 +298,26 @@ __global__ void __launch_bounds__(128) k_build(int N, const int4 *__restrict__ q
 // rev[s][i] = where the force gather finds the contribution of the terms of i's
 // neighbour j = nbr[s][i] on i: the flat index s2 * N + j of i's slot s2 in j's
 // (sorted) list, found by binary search (a 32-bit unsigned value: cap * N < 2^32).
-__global__ void k_reverse(int N, const int *__restrict__ nbr, const int *__restrict__ cnt, int *__restrict__ rev,
-                          RunState *rs, int gated)
+// One thread per list entry (grid y = slot), so the searches run side by side.
+__global__ void k_reverse(int N, const int4 *__restrict__ q, const SysCtl *__restrict__ ctl,
+                          const int *__restrict__ nbr, const int *__restrict__ cnt, int *__restrict__ rev, RunState *rs,
+                          int gated)
 {
   if (skip_build(rs, gated)) return;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  int n = cnt[i];
-  for (int s = 0; s < n; ++s) {
-    int j = nbr[(size_t)s * N + i];
-    int lo = 0, hi = cnt[j] - 1, found = -1;
-    while (lo <= hi) {
-      int mid = (lo + hi) >> 1;
-      int v = nbr[(size_t)mid * N + j];
-      if (v == i) { found = mid; break; }
-      if (v < i) lo = mid + 1; else hi = mid - 1;
-    }
-    if (found < 0) atomicOr(&rs->status, ST_REV_MISSING);
-    rev[(size_t)s * N + i] = (int)((unsigned)(found < 0 ? 0 : found) * (unsigned)N + (unsigned)j);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = blockIdx.y;
+  if (i >= N || s >= cnt[i]) return;
+  if (ctl && ctl[sys_of(q[i].w)].rebuild == 0) return;
+  const int j = nbr[(size_t)s * N + i];
+  int lo = 0, hi = cnt[j] - 1, found = -1;
+  while (lo <= hi) {
+    const int mid = (lo + hi) >> 1;
+    const int v = nbr[(size_t)mid * N + j];
+    if (v == i) { found = mid; break; }
+    if (v < i) lo = mid + 1; else hi = mid - 1;
   }
+  if (found < 0) atomicOr(&rs->status, ST_REV_MISSING);
+  rev[(size_t)s * N + i] = (int)((unsigned)(found < 0 ? 0 : found) * (unsigned)N + (unsigned)j);
 }
 
 // close a build: count it, clear the request
@@ -328,10 +332,12 @@ __global__ void k_build_done(RunState *rs, int gated)
 
 namespace tsf {
 
-// Enqueue one list build on st.  Buffers: cell_count[ncell] (zero on entry, zero
+// Enqueue one list build on st (ctl non-null: only the systems whose rebuild flag is
+// set get new lists; null: every atom).  Buffers: cell_count[ncell] (zero on entry, zero
 // on exit), cell_start[ncell+1], tile_sums[ceil(ncell/SCAN_TILE)], cell_atoms[N] (int4),
 // cell_of[N], rank[N]; list nbr/rev [cap][N], cnt[N]; qref[N].
-cudaError_t launch_build(cudaStream_t st, int N, const int4 *q, const SysTab *sys, int ncell, float rl2,
+cudaError_t launch_build(cudaStream_t st, int N, const int4 *q, const SysTab *sys, const SysCtl *ctl, int ncell,
+                         float rl2,
                          int *cell_count, int *cell_start, int *tile_sums, int4 *cell_atoms, int *cell_of, int *rank,
                          int *nbr, int *rev, int *cnt, int cap, int4 *qref, RunState *rs, int gated)
 {
@@ -345,8 +351,8 @@ cudaError_t launch_build(cudaStream_t st, int N, const int4 *q, const SysTab *sy
   k_scan_add<<<(ncell + T - 1) / T, T, 0, st>>>(ncell, cell_start, tile_sums, cell_count, rs, gated);
   k_cell_fill<<<BN, T, 0, st>>>(N, q, cell_of, rank, cell_start, cell_atoms, rs, gated);
   const int BN128 = (N + 127) / 128;
-  k_build<<<BN128, 128, 0, st>>>(N, q, sys, rl2, cell_start, cell_atoms, nbr, cnt, cap, qref, rs, gated);
-  k_reverse<<<BN128, 128, 0, st>>>(N, nbr, cnt, rev, rs, gated);
+  k_build<<<BN128, 128, 0, st>>>(N, q, sys, ctl, rl2, cell_start, cell_atoms, nbr, cnt, cap, qref, rs, gated);
+  k_reverse<<<dim3(BN128, cap), 128, 0, st>>>(N, q, ctl, nbr, cnt, rev, rs, gated);
   k_build_done<<<1, 1, 0, st>>>(rs, gated);
   return cudaGetLastError();
 }

@@ -61,8 +61,8 @@ struct Layout {
   static constexpr size_t work = mask + up256(kMaxAtoms * sizeof(unsigned long long));
   static constexpr size_t nwork = work + up256(kMaxAtoms * sizeof(int));
   static constexpr size_t partial = nwork + up256((kMaxAtoms / 128 + 1) * sizeof(int));
-  // force_partial_rows(N) = ceil(N / 32) + 304 rows of 8 float64
-  static constexpr size_t partial_rows = (kMaxAtoms + 31) / 32 + 304;
+  // force_partial_rows(N) = ceil(N / 32) + GEN_BLOCKS rows of 8 float64
+  static constexpr size_t partial_rows = (kMaxAtoms + 31) / 32 + GEN_BLOCKS;
   static constexpr size_t total = partial + up256(partial_rows * 8 * sizeof(double));
 };
 
@@ -181,7 +181,7 @@ extern "C" int tersoff_compute_noalloc(const tersoff_params *P, const double *po
   T.natoms = (int)N;
   NK(cudaMemcpyAsync(sys, &T, sizeof(SysTab), cudaMemcpyHostToDevice, st));
   NK(launch_ingest(st, (int)N, pos, types, P->nt, 0, sys, x, q, rs));
-  NK(launch_build(st, (int)N, q, sys, g.ncell, g.rl2, cell_count, cell_start, tile_sums, cell_atoms, cell_of, rank,
+  NK(launch_build(st, (int)N, q, sys, nullptr, g.ncell, g.rl2, cell_count, cell_start, tile_sums, cell_atoms, cell_of, rank,
                   nbr, rev, cnt, kCap, qref, rs, 0));
   const int fast_slots = P->sym_angular ? 8 : 0;
   NK(launch_force(st, mixed, fast_slots, P->nt == 1, force_slots_for(kCap), 1, 1, (int)N, x, q, nbr, cnt, sys,

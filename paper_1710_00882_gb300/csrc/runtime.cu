@@ -102,6 +102,10 @@ struct MdGraph {
   bool valid = false;
 };
 
+// profiled phases: integrator, list build, register force kernel, overflow force
+// kernel + reductions, step bookkeeping
+constexpr int TSF_PHASES = 5;
+
 struct tersoff_md {
   tersoff_ctx *ctx = nullptr;
   cudaStream_t cap_stream = nullptr;   // stream used only to capture the step graphs
@@ -128,7 +132,7 @@ struct tersoff_md {
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
   std::vector<std::pair<int, std::pair<size_t, size_t>>> ev_marks;  // (phase, (start idx, end idx))
-  long long launches[4] = {0, 0, 0, 0};
+  long long launches[TSF_PHASES] = {0, 0, 0, 0, 0};
 };
 
 namespace tsf {
@@ -294,7 +298,7 @@ int build_list_sync(tersoff_ctx *ctx, const AtomState &A, ListState &L, RunState
   for (int attempt = 0; attempt < 3; ++attempt) {
     CKR(ensure_list(ctx, L, A.N, cap, g.ncell));
     CK(cudaMemsetAsync(&rs->maxcount, 0, sizeof(int), ctx->stream));
-    CK(launch_build(ctx->stream, (int)A.N, A.q, S.tab, g.ncell, g.rl2, L.cell_count, L.cell_start, L.tile_sums,
+    CK(launch_build(ctx->stream, (int)A.N, A.q, S.tab, nullptr, g.ncell, g.rl2, L.cell_count, L.cell_start, L.tile_sums,
                     L.cell_atoms, L.cell_of, L.rank, L.nbr, L.rev, L.cnt, cap, L.qref, rs, 0));
     RunState h;
     CKR(read_rs(ctx, rs, &h));
@@ -737,11 +741,11 @@ static void md_mark_end(tersoff_md *md, int phase, size_t begin, int nlaunch)
   }
 }
 
-static int md_force(tersoff_md *md, cudaStream_t st, int eflag)
+static int md_force(tersoff_md *md, cudaStream_t st, int eflag, int part = 3)
 {
   tersoff_ctx *ctx = md->ctx;
   const tersoff_params *P = md->params;
-  CK(launch_force(st, md->mixed, md->fast_slots, P->nt == 1, md->gen_slots, eflag, 0, (int)md->atoms.N, md->atoms.x,
+  CK(launch_force_part(part, st, md->mixed, md->fast_slots, P->nt == 1, md->gen_slots, eflag, 0, (int)md->atoms.N, md->atoms.x,
                   md->atoms.q, md->list.nbr, md->list.cnt, md->sys.tab, md->mixed ? P->pair_f : P->pair_d,
                   md->mixed ? P->trip_f : P->trip_d, P->nt, md->atoms.contrib, md->atoms.selfF, md->atoms.mask,
                   md->atoms.work, md->atoms.nwork, md->atoms.partial, md->rs, nullptr));
@@ -759,13 +763,15 @@ static int md_vv(tersoff_md *md, cudaStream_t st, int mode, bool ke)
   return TERSOFF_OK;
 }
 
-static int md_build(tersoff_md *md, cudaStream_t st, int gated)
+// gated: skipped on the device unless some atom moved skin/2; full: every atom gets
+// a new list (recovery), else only systems whose rebuild flag is set
+static int md_build(tersoff_md *md, cudaStream_t st, int gated, bool full = false)
 {
   tersoff_ctx *ctx = md->ctx;
   ListState &L = md->list;
-  CK(launch_build(st, (int)md->atoms.N, md->atoms.q, md->sys.tab, L.grid.ncell, L.grid.rl2, L.cell_count,
-                  L.cell_start, L.tile_sums,
-                  L.cell_atoms, L.cell_of, L.rank, L.nbr, L.rev, L.cnt, L.cap, L.qref, md->rs, gated));
+  CK(launch_build(st, (int)md->atoms.N, md->atoms.q, md->sys.tab, full ? nullptr : md->sys.ctl, L.grid.ncell,
+                  L.grid.rl2, L.cell_count, L.cell_start, L.tile_sums, L.cell_atoms, L.cell_of, L.rank, L.nbr, L.rev,
+                  L.cnt, L.cap, L.qref, md->rs, gated));
   return TERSOFF_OK;
 }
 
@@ -876,11 +882,14 @@ static int md_launch_steps(tersoff_md *md, long long n, double *d_trace, long lo
     CKR(md_build(md, st, 1));
     md_mark_end(md, 1, b, 8);
     b = md_mark_begin(md);
-    CKR(md_force(md, st, tr ? 1 : 0));
-    md_mark_end(md, 2, b, 2 + (tr ? 1 : 0));
+    CKR(md_force(md, st, tr ? 1 : 0, 1));
+    md_mark_end(md, 2, b, md->fast_slots > 0 ? 1 : 0);
+    b = md_mark_begin(md);
+    CKR(md_force(md, st, tr ? 1 : 0, 2));
+    md_mark_end(md, 3, b, 1 + (tr ? 1 : 0));
     b = md_mark_begin(md);
     CK(launch_step_end(st, md->rs, md->sys.ctl, 1, 0, 0));
-    md_mark_end(md, 3, b, 1);
+    md_mark_end(md, 4, b, 1);
   }
   md->open = true;
   return TERSOFF_OK;
@@ -902,7 +911,7 @@ static int md_recover(tersoff_md *md, const RunState &h, double *d_trace)
     CKR(ensure_list(ctx, md->list, md->atoms.N, cap, md->list.grid.ncell));
     CKR(ensure_scatter(ctx, md->atoms, md->atoms.N, cap, md->mixed));
     CK(cudaMemsetAsync(&md->rs->status, 0, sizeof(int), st));
-    CKR(md_build(md, st, 0));
+    CKR(md_build(md, st, 0, true));
   } else if (h.status & ST_NC_OVERFLOW) {
     md_graphs_free(md);
     md->gen_slots = force_slots_for(h.maxnc);
@@ -997,6 +1006,10 @@ int tersoff_md_create(tersoff_ctx *ctx, const double *pos, const double *vel, co
   // register kernel with 4 slots when no atom has more than 4 in-cutoff neighbours
   // (diamond-like solids), else 8; atoms beyond that go to the general kernel
   if (md->fast_slots > 0 && h.maxnc <= 4) md->fast_slots = 4;
+  // the general kernel needs slots for in-cutoff neighbours only (not the whole
+  // list): size it from the largest count seen plus headroom; a later overflow
+  // widens it (recovery in md_finish)
+  md->gen_slots = force_slots_for(std::max(8, h.maxnc + 2));
   md->steps_done = md->steps_target = 0;
   md->pe_valid = true;
   {
@@ -1128,22 +1141,22 @@ int tersoff_md_profile(tersoff_md *md, int enable)
   md->prof = enable != 0;
   md->ev_used = 0;
   md->ev_marks.clear();
-  for (int p = 0; p < 4; ++p) md->launches[p] = 0;
+  for (int p = 0; p < TSF_PHASES; ++p) md->launches[p] = 0;
   return TERSOFF_OK;
 }
 
-int tersoff_md_profile_read(tersoff_md *md, double ms[4], int64_t launches[4])
+int tersoff_md_profile_read(tersoff_md *md, double ms[5], int64_t launches[5])
 {
   if (!md) return TERSOFF_ERR_ARG;
   tersoff_ctx *ctx = md->ctx;
   CK(cudaStreamSynchronize(ctx->stream));
-  double acc[4] = {0, 0, 0, 0};
+  double acc[TSF_PHASES] = {0, 0, 0, 0, 0};
   for (auto &m : md->ev_marks) {
     float t = 0;
     CK(cudaEventElapsedTime(&t, md->ev_pool[m.second.first], md->ev_pool[m.second.second]));
     acc[m.first] += t;
   }
-  for (int p = 0; p < 4; ++p) {
+  for (int p = 0; p < TSF_PHASES; ++p) {
     if (ms) ms[p] = acc[p];
     if (launches) launches[p] = md->launches[p];
   }

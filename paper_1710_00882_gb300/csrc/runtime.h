@@ -59,8 +59,8 @@ struct SysDev {
 namespace tsf {
 
 // launchers defined in the kernel translation units
-cudaError_t launch_build(cudaStream_t, int, const int4 *, const SysTab *, int, float, int *, int *, int *, int4 *,
-                         int *, int *, int *, int *, int *, int, int4 *, RunState *, int);
+cudaError_t launch_build(cudaStream_t, int, const int4 *, const SysTab *, const SysCtl *, int, float, int *, int *,
+                         int *, int4 *, int *, int *, int *, int *, int *, int, int4 *, RunState *, int);
 int scan_tiles_for(int ncell);
 int force_slots_for(int need);
 int force_partial_rows(int N);
@@ -68,8 +68,11 @@ int vv_blocks(int N);
 cudaError_t launch_force(cudaStream_t, bool, int, bool, int, int, int, int, const dbl4 *, const int4 *, const int *,
                          const int *, const SysTab *, const void *, const void *, int, void *, void *,
                          unsigned long long *, int *, int *, double *, RunState *, double *);
+cudaError_t launch_force_part(int, cudaStream_t, bool, int, bool, int, int, int, int, const dbl4 *, const int4 *,
+                              const int *, const int *, const SysTab *, const void *, const void *, int, void *, void *,
+                              unsigned long long *, int *, int *, double *, RunState *, double *);
 cudaError_t launch_vv(cudaStream_t, bool, bool, int, int, dbl4 *, dbl4 *, int4 *, const int4 *, const void *,
-                      const void *, const unsigned long long *, const int *, const SysTab *, const SysCtl *,
+                      const void *, const unsigned long long *, const int *, const SysTab *, SysCtl *,
                       const double *, float, double *, RunState *);
 cudaError_t launch_gather_out(cudaStream_t, bool, int, const void *, const void *, const unsigned long long *,
                               const int *, double *, RunState *);

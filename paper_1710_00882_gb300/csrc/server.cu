@@ -16,6 +16,7 @@
 #include <cmath>
 #include <condition_variable>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <deque>
@@ -31,19 +32,90 @@
 
 namespace tsf {
 
-// Rewrite the system index in every atom word from the table's atom ranges.
-__global__ void k_resid(int N, int4 *__restrict__ q, dbl4 *__restrict__ x, const SysTab *__restrict__ sys, int nsys)
+// index k of the range containing t among n ranges starting at off[0..n) (off ascending)
+__device__ __forceinline__ int range_of(const int *__restrict__ off, int n, int t)
 {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  int lo = 0, hi = nsys - 1;
+  int lo = 0, hi = n - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (sys[mid].atom_off <= i) lo = mid; else hi = mid - 1;
+    if (off[mid] <= t) lo = mid; else hi = mid - 1;
   }
-  const int w = make_w(type_of(q[i].w), lo);
-  q[i].w = w;
-  x[i].w = __longlong_as_double((long long)w);
+  return lo;
+}
+
+// Survivors of a repack: atom d of the new layout (systems 0..nsurv-1 come first)
+// is atom src_off[k] + (d - atom_off[k]) of the old layout; its word gets the new
+// system index.
+__global__ void k_move(int n, const dbl4 *__restrict__ sx, const dbl4 *__restrict__ sv, const int4 *__restrict__ sq,
+                       dbl4 *__restrict__ dx, dbl4 *__restrict__ dv, int4 *__restrict__ dq,
+                       const int *__restrict__ dst_off, const int *__restrict__ src_off, int nsurv)
+{
+  const int d = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= n) return;
+  const int k = range_of(dst_off, nsurv, d);
+  const int src = src_off[k] + (d - dst_off[k]);
+  dbl4 x = sx[src];
+  int4 q = sq[src];
+  const int w = make_w(type_of(q.w), k);
+  q.w = w;
+  x.w = __longlong_as_double((long long)w);
+  dx[d] = x;
+  dq[d] = q;
+  dv[d] = sv[src];
+}
+
+// New jobs of a repack, staged back to back (pos [n][3], vel [n][3], types [n]):
+// staged atom t belongs to new job k (staging offsets st_off), system sys0 + k.
+__global__ void k_ingest_batch(int n, const double *__restrict__ pos, const double *__restrict__ vel,
+                               const int *__restrict__ types, const int *__restrict__ st_off, int nnew, int sys0,
+                               const SysTab *__restrict__ sys, int nt, dbl4 *__restrict__ x, dbl4 *__restrict__ v,
+                               int4 *__restrict__ q, RunState *rs)
+{
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int k = range_of(st_off, nnew, t);
+  const int sid = sys0 + k;
+  const SysTab &T = sys[sid];
+  const int d = T.atom_off + (t - st_off[k]);
+  int ty = types[t];
+  if (ty < 0 || ty >= nt) {
+    atomicOr(&rs->status, ST_BAD_TYPE);
+    ty = 0;
+  }
+  double p[3];
+  int qq[3];
+  for (int a = 0; a < 3; ++a) {
+    double c = pos[3 * (size_t)t + a];
+    if (!isfinite(c) || fabs(c * T.geo.invL[a]) > 1e5) {
+      atomicOr(&rs->status, ST_NONFINITE);
+      c = 0.0;
+    }
+    p[a] = c;
+    qq[a] = fixed_q(c, T.geo.to_q[a]);
+  }
+  const int w = make_w(ty, sid);
+  x[d] = make_dbl4(p[0], p[1], p[2], __longlong_as_double((long long)w));
+  q[d] = make_int4(qq[0], qq[1], qq[2], w);
+  v[d] = make_dbl4(vel[3 * (size_t)t], vel[3 * (size_t)t + 1], vel[3 * (size_t)t + 2], 0.0);
+}
+
+// Finished jobs: staged atom t belongs to retiring job k (offsets r_off), system
+// r_sys[k]; positions and velocities go out back to back as AoS float64.
+__global__ void k_extract_batch(int n, const dbl4 *__restrict__ x, const dbl4 *__restrict__ v,
+                                const int *__restrict__ r_off, const int *__restrict__ r_sys, int nret,
+                                const SysTab *__restrict__ sys, double *__restrict__ pos, double *__restrict__ vel)
+{
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int k = range_of(r_off, nret, t);
+  const int d = sys[r_sys[k]].atom_off + (t - r_off[k]);
+  const dbl4 a = x[d], b = v[d];
+  pos[3 * (size_t)t] = a.x;
+  pos[3 * (size_t)t + 1] = a.y;
+  pos[3 * (size_t)t + 2] = a.z;
+  vel[3 * (size_t)t] = b.x;
+  vel[3 * (size_t)t + 1] = b.y;
+  vel[3 * (size_t)t + 2] = b.z;
 }
 
 // Per-system potential and kinetic energy: one block per system, fixed-order sums.
@@ -133,8 +205,11 @@ struct tersoff_server {
   SysDev S;
   RunState *rs = nullptr;
   double *eatom = nullptr, *sysE = nullptr;
-  double *stage = nullptr;
+  double *stage = nullptr;      // device staging (new jobs in, finished jobs out)
   size_t stage_b = 0;
+  char *hstage = nullptr;       // pinned host staging
+  size_t hstage_b = 0;
+  int *dtabs = nullptr;         // device index tables of a repack / retire (4 x (max_slots + 1) ints)
   std::vector<SysTab> tab;
   std::vector<Job *> batch;      // resident jobs in layout order (owned by `jobs`; touched by the worker only)
   int64_t natoms = 0;
@@ -143,6 +218,7 @@ struct tersoff_server {
   cudaGraph_t g = nullptr;
   cudaGraphExec_t exec = nullptr;
   bool graph_ok = false;
+  bool use_graphs = true;   // TERSOFF_GRAPHS=0: chunks kernel by kernel (profiling)
   bool broken = false;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
@@ -151,7 +227,10 @@ struct tersoff_server {
   uint64_t next_id = 1;
   bool stop = false;
   std::thread worker;
-  tersoff_server_stats stats{};
+  tersoff_server_stats stats{};   // published under mu
+  // worker-side counters, published into stats under mu once per loop
+  int64_t w_chunks = 0, w_repacks = 0;
+  double w_retire = 0, w_repack = 0, w_graph = 0, w_run = 0;
   std::string msg;              // last error reported to the caller (under mu)
 };
 
@@ -188,8 +267,21 @@ size_t bytes_per_atom(bool mixed, int listcap)
          + v4 + 8 + 8 + 4 + 16 + 12 + 8 + 16;      // selfF, mask, work, cnt, qref, cells, eatom, slack
 }
 
-// staging bytes of one new job (positions, velocities, types), 256-byte aligned
-size_t stage_bytes(int64_t n) { return ((size_t)n * (6 * sizeof(double) + sizeof(int32_t)) + 255) / 256 * 256; }
+// pinned host staging of at least `bytes` (contents not kept)
+bool host_reserve(tersoff_server *s, size_t bytes)
+{
+  if (bytes <= s->hstage_b && s->hstage) return true;
+  if (s->hstage) cudaFreeHost(s->hstage);
+  s->hstage = nullptr;
+  s->hstage_b = 0;
+  bytes = std::max<size_t>(bytes + bytes / 4, 1 << 20);
+  if (cudaHostAlloc((void **)&s->hstage, bytes, cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  s->hstage_b = bytes;
+  return true;
+}
 
 int read_state(tersoff_server *s, RunState *h)
 {
@@ -219,13 +311,14 @@ int srv_vv(tersoff_server *s, cudaStream_t st)
   return TERSOFF_OK;
 }
 
-int srv_build(tersoff_server *s, cudaStream_t st, int gated)
+// full: every atom gets a new list; else only systems whose rebuild flag is set
+int srv_build(tersoff_server *s, cudaStream_t st, bool full)
 {
   AtomState &X = cur_atoms(s);
   ListState &L = s->L;
-  SK(launch_build(st, (int)s->natoms, X.q, s->S.tab, s->ncell, (float)(s->rl * s->rl * (1.0 + 1e-5)), L.cell_count,
-                  L.cell_start, L.tile_sums, L.cell_atoms, L.cell_of, L.rank, L.nbr, L.rev, L.cnt, L.cap, L.qref,
-                  s->rs, gated));
+  SK(launch_build(st, (int)s->natoms, X.q, s->S.tab, full ? nullptr : s->S.ctl, s->ncell,
+                  (float)(s->rl * s->rl * (1.0 + 1e-5)), L.cell_count, L.cell_start, L.tile_sums, L.cell_atoms,
+                  L.cell_of, L.rank, L.nbr, L.rev, L.cnt, L.cap, L.qref, s->rs, 0));
   return TERSOFF_OK;
 }
 
@@ -285,7 +378,7 @@ int graph_build(tersoff_server *s)
   SK(cudaStreamEndCapture(st, &bodyc));
   cudaGraph_t ifbody = ip.conditional.phGraph_out[0];
   SK(cudaStreamBeginCaptureToGraph(st, ifbody, nullptr, nullptr, 0, mode));
-  SKR(srv_build(s, st, 0));
+  SKR(srv_build(s, st, false));
   cudaGraph_t ifc = ifbody;
   SK(cudaStreamEndCapture(st, &ifc));
   SK(cudaGraphInstantiate(&s->exec, g, 0));
@@ -293,18 +386,20 @@ int graph_build(tersoff_server *s)
   return TERSOFF_OK;
 }
 
-// Full list build of the current layout, growing the list capacity within the
-// budget on overflow.
-int build_sync(tersoff_server *s)
+// Full list build and force evaluation of the current layout, growing the list
+// capacity on overflow.
+int build_and_force(tersoff_server *s)
 {
   for (int attempt = 0; attempt < 3; ++attempt) {
     SK(cudaMemsetAsync(&s->rs->maxcount, 0, sizeof(int), s->st));
-    SKR(srv_build(s, s->st, 0));
+    SKR(srv_build(s, s->st, true));
+    SKR(srv_force(s, s->st));
     RunState h;
     SKR(read_state(s, &h));
     if (h.status == 0) return TERSOFF_OK;
     if (h.status != ST_NLIST_OVERFLOW || h.maxcount > MAX_CAP)
-      return srv_err(s, TERSOFF_ERR_NLIST_OVERFLOW, "list build failed (status %d, %d entries)", h.status, h.maxcount);
+      return srv_err(s, TERSOFF_ERR_NLIST_OVERFLOW, "list build or force failed (status %d, %d entries)", h.status,
+                     h.maxcount);
     const int cap = std::min(MAX_CAP, ((h.maxcount + std::max(4, h.maxcount / 4)) + 3) & ~3);
     graph_free(s);
     if (ensure_list(&s->priv, s->L, s->cap_atoms, cap, std::max(1, s->ncell)) != TERSOFF_OK ||
@@ -316,18 +411,24 @@ int build_sync(tersoff_server *s)
   return srv_err(s, TERSOFF_ERR_NLIST_OVERFLOW, "list build did not converge");
 }
 
-// Rebuild the packed layout from the jobs in `order` (survivors first, then new).
+// Rebuild the packed layout from the jobs in `order` (survivors first, then new):
+// survivors move with one kernel, new jobs are staged back to back and ingested
+// with one copy and one kernel.
 int repack(tersoff_server *s, const std::vector<Job *> &order, const std::vector<bool> &is_new)
 {
   const tersoff_params *P = s->P;
-  std::vector<SysTab> tab(order.size());
-  std::vector<SysCtl> ctl(order.size());
-  std::vector<int64_t> old_off(order.size(), -1);
-  std::map<const Job *, int64_t> prev;
+  const int S = (int)order.size();
+  std::vector<SysTab> tab(S);
+  std::vector<SysCtl> ctl(S);
+  std::map<const Job *, int> prev;
   for (size_t k = 0; k < s->batch.size(); ++k) prev[s->batch[k]] = s->tab[k].atom_off;
-  int64_t off = 0;
-  int coff = 0;
-  for (size_t k = 0; k < order.size(); ++k) {
+  // index tables: [0, S) new atom offsets, [S+1, ...) survivor source offsets, then
+  // staging offsets of the new jobs
+  std::vector<int> itab(3 * (size_t)(S + 1), 0);
+  int *dst_off = itab.data(), *src_off = itab.data() + (S + 1), *st_off = itab.data() + 2 * (S + 1);
+  int64_t off = 0, staged = 0;
+  int coff = 0, nsurv = 0, nnew = 0;
+  for (int k = 0; k < S; ++k) {
     Job &J = *order[k];
     SysTab &T = tab[k];
     T.geo = make_geom(J.box);
@@ -341,138 +442,182 @@ int repack(tersoff_server *s, const std::vector<Job *> &order, const std::vector
     for (int a = 0; a < MAX_TYPES; ++a) T.kick[a] = a < P->nt ? 0.5 * J.dt * ACCEL / P->masses[a] : 0.0;
     ctl[k] = is_new[k] ? SysCtl{J.nsteps, 0, 0} : J.ctl;
     J.ctl = ctl[k];
-    if (!is_new[k]) old_off[k] = prev[order[k]];
+    dst_off[k] = (int)off;
+    if (!is_new[k]) {
+      if (nnew > 0) return srv_err(s, TERSOFF_ERR_ARG, "survivors must precede new jobs");
+      src_off[k] = prev[order[k]];
+      ++nsurv;
+    } else {
+      st_off[nnew++] = (int)staged;
+      staged += J.n;
+    }
     off += J.n;
     coff += gr.ncell;
   }
+  const int64_t surv_atoms = nsurv < S ? dst_off[nsurv] : off;
   s->natoms = off;
   s->ncell = coff;
-  if (!sys_alloc(s->S, std::max(1, (int)order.size()))) return srv_err(s, TERSOFF_ERR_NOMEM, "system tables");
+  if (!sys_alloc(s->S, std::max(1, S))) return srv_err(s, TERSOFF_ERR_NOMEM, "system tables");
   if (ensure_list(&s->priv, s->L, s->cap_atoms, s->listcap, std::max(1, coff)) != TERSOFF_OK)
     return srv_err(s, TERSOFF_ERR_NOMEM, "cell arrays for %d cells", coff);
-  SK(cudaMemcpyAsync(s->S.tab, tab.data(), sizeof(SysTab) * tab.size(), cudaMemcpyHostToDevice, s->st));
-  SK(cudaMemcpyAsync(s->S.ctl, ctl.data(), sizeof(SysCtl) * ctl.size(), cudaMemcpyHostToDevice, s->st));
+  // pinned staging: tables, then the new jobs' positions, velocities and types
+  const size_t tbytes = sizeof(SysTab) * S + sizeof(SysCtl) * S + sizeof(int) * itab.size();
+  const size_t tpad = (tbytes + 255) / 256 * 256;
+  const size_t nbytes = (size_t)staged * (6 * sizeof(double) + sizeof(int32_t));
+  if (!host_reserve(s, tpad + nbytes)) return srv_err(s, TERSOFF_ERR_NOMEM, "pinned staging");
+  if (nbytes && !dreserve(s->stage, s->stage_b, nbytes)) return srv_err(s, TERSOFF_ERR_NOMEM, "staging");
+  char *h = s->hstage;
+  memcpy(h, tab.data(), sizeof(SysTab) * S);
+  memcpy(h + sizeof(SysTab) * S, ctl.data(), sizeof(SysCtl) * S);
+  memcpy(h + sizeof(SysTab) * S + sizeof(SysCtl) * S, itab.data(), sizeof(int) * itab.size());
+  double *hpos = (double *)(h + tpad);
+  double *hvel = hpos + 3 * staged;
+  int32_t *hty = (int32_t *)(hvel + 3 * staged);
+  for (int k = nsurv, m = 0; k < S; ++k, ++m) {
+    const Job &J = *order[k];
+    memcpy(hpos + 3 * (size_t)st_off[m], J.pos.data(), sizeof(double) * 3 * J.n);
+    memcpy(hvel + 3 * (size_t)st_off[m], J.vel.data(), sizeof(double) * 3 * J.n);
+    memcpy(hty + st_off[m], J.types.data(), sizeof(int32_t) * J.n);
+  }
+  SK(cudaMemcpyAsync(s->S.tab, h, sizeof(SysTab) * S, cudaMemcpyHostToDevice, s->st));
+  SK(cudaMemcpyAsync(s->S.ctl, h + sizeof(SysTab) * S, sizeof(SysCtl) * S, cudaMemcpyHostToDevice, s->st));
+  SK(cudaMemcpyAsync(s->dtabs, h + sizeof(SysTab) * S + sizeof(SysCtl) * S, sizeof(int) * itab.size(),
+                     cudaMemcpyHostToDevice, s->st));
   AtomState &src = s->A[s->cur];
   AtomState &dst = s->A[1 - s->cur];
-  // survivors: copy their ranges; new jobs: stage and ingest
-  size_t need = 0;
-  for (size_t k = 0; k < order.size(); ++k)
-    if (is_new[k]) need += stage_bytes(order[k]->n);
-  if (need && !dreserve(s->stage, s->stage_b, need)) return srv_err(s, TERSOFF_ERR_NOMEM, "staging");
-  char *sp = (char *)s->stage;
-  for (size_t k = 0; k < order.size(); ++k) {
-    Job &J = *order[k];
-    const int64_t o = tab[k].atom_off;
-    if (!is_new[k]) {
-      const int64_t p = old_off[k];
-      SK(cudaMemcpyAsync(dst.x + o, src.x + p, sizeof(dbl4) * J.n, cudaMemcpyDeviceToDevice, s->st));
-      SK(cudaMemcpyAsync(dst.v + o, src.v + p, sizeof(dbl4) * J.n, cudaMemcpyDeviceToDevice, s->st));
-      SK(cudaMemcpyAsync(dst.q + o, src.q + p, sizeof(int4) * J.n, cudaMemcpyDeviceToDevice, s->st));
-    } else {
-      double *dpos = (double *)sp;
-      double *dvel = dpos + 3 * J.n;
-      int32_t *dty = (int32_t *)(dvel + 3 * J.n);
-      sp += stage_bytes(J.n);
-      SK(cudaMemcpyAsync(dpos, J.pos.data(), sizeof(double) * 3 * J.n, cudaMemcpyHostToDevice, s->st));
-      SK(cudaMemcpyAsync(dvel, J.vel.data(), sizeof(double) * 3 * J.n, cudaMemcpyHostToDevice, s->st));
-      SK(cudaMemcpyAsync(dty, J.types.data(), sizeof(int32_t) * J.n, cudaMemcpyHostToDevice, s->st));
-      SK(launch_ingest(s->st, (int)J.n, dpos, dty, P->nt, (int)k, s->S.tab, dst.x + o, dst.q + o, s->rs));
-      SK(launch_ingest_vel(s->st, (int)J.n, dvel, dst.v + o));
-    }
+  const int *d_dst = s->dtabs, *d_src = s->dtabs + (S + 1), *d_st = s->dtabs + 2 * (S + 1);
+  if (surv_atoms > 0) {
+    k_move<<<(int)((surv_atoms + 255) / 256), 256, 0, s->st>>>((int)surv_atoms, src.x, src.v, src.q, dst.x, dst.v,
+                                                                dst.q, d_dst, d_src, nsurv);
+    SK(cudaGetLastError());
   }
-  if (s->natoms > 0) {
-    k_resid<<<(int)((s->natoms + 255) / 256), 256, 0, s->st>>>((int)s->natoms, dst.q, dst.x, s->S.tab,
-                                                              (int)order.size());
+  if (staged > 0) {
+    double *dpos = s->stage, *dvel = dpos + 3 * staged;
+    int *dty = (int *)(dvel + 3 * staged);
+    SK(cudaMemcpyAsync(dpos, hpos, nbytes, cudaMemcpyHostToDevice, s->st));
+    k_ingest_batch<<<(int)((staged + 255) / 256), 256, 0, s->st>>>((int)staged, dpos, dvel, dty, d_st, nnew, nsurv,
+                                                                   s->S.tab, P->nt, dst.x, dst.v, dst.q, s->rs);
     SK(cudaGetLastError());
   }
   s->cur = 1 - s->cur;
   s->tab = tab;
   s->batch = order;
   graph_free(s);
-  SKR(build_sync(s));
-  SKR(srv_force(s, s->st));
-  RunState h;
-  SKR(read_state(s, &h));
-  if (h.status != 0) return srv_err(s, TERSOFF_ERR_CUDA, "force after repack: status %d", h.status);
-  s->stats.repacks += 1;
+  SKR(build_and_force(s));
+  s->w_repacks += 1;
+  return TERSOFF_OK;
+}
+
+// n steps: one graph launch, or kernel by kernel without graphs
+int launch_steps(tersoff_server *s, long long n)
+{
+  k_set_loop<<<1, 1, 0, s->st>>>(s->rs, n);
+  SK(cudaGetLastError());
+  if (s->use_graphs) {
+    if (!s->graph_ok) {
+      const double t0 = now_s();
+      SKR(graph_build(s));
+      s->w_graph += now_s() - t0;
+    }
+    SK(cudaGraphLaunch(s->exec, s->st));
+    return TERSOFF_OK;
+  }
+  for (long long k = 0; k < n; ++k) {
+    SKR(srv_vv(s, s->st));
+    AtomState &X = cur_atoms(s);
+    ListState &L = s->L;
+    SK(launch_build(s->st, (int)s->natoms, X.q, s->S.tab, s->S.ctl, s->ncell, (float)(s->rl * s->rl * (1.0 + 1e-5)),
+                    L.cell_count, L.cell_start, L.tile_sums, L.cell_atoms, L.cell_of, L.rank, L.nbr, L.rev, L.cnt,
+                    L.cap, L.qref, s->rs, 1));
+    SKR(srv_force(s, s->st));
+    SK(launch_step_end(s->st, s->rs, s->S.ctl, (int)s->batch.size(), 0, 0));
+  }
   return TERSOFF_OK;
 }
 
 // One chunk of steps for the whole batch (recovering from list or slot overflow).
 int run_chunk(tersoff_server *s)
 {
-  if (!s->graph_ok) SKR(graph_build(s));
-  k_set_loop<<<1, 1, 0, s->st>>>(s->rs, s->chunk);
-  SK(cudaGetLastError());
-  SK(cudaGraphLaunch(s->exec, s->st));
+  SKR(launch_steps(s, s->chunk));
   for (int attempt = 0; attempt < 8; ++attempt) {
     RunState h;
     SKR(read_state(s, &h));
     if (h.status == 0) break;
+    // finish the failed step (its integrator part ran), then the rest of the chunk
     if (h.status & ST_NLIST_OVERFLOW) {
       SK(cudaMemsetAsync(&s->rs->status, 0, sizeof(int), s->st));
-      SKR(build_sync(s));
+      SKR(build_and_force(s));
     } else if (h.status & ST_NC_OVERFLOW) {
       if (h.maxnc > MAX_CAP) return srv_err(s, TERSOFF_ERR_NLIST_OVERFLOW, "%d in-cutoff neighbours", h.maxnc);
       s->gen_slots = force_slots_for(h.maxnc);
       graph_free(s);
       SK(cudaMemsetAsync(&s->rs->status, 0, sizeof(int), s->st));
+      SKR(srv_force(s, s->st));
     } else {
       return srv_err(s, h.status & ST_NONFINITE ? TERSOFF_ERR_NONFINITE : TERSOFF_ERR_CUDA, "device status %d",
                      h.status);
     }
-    // finish the failed step (its integrator part ran), then the rest of the chunk
-    SK(cudaMemsetAsync(&s->rs->epot, 0, sizeof(double), s->st));
-    SKR(srv_force(s, s->st));
     SK(launch_step_end(s->st, s->rs, s->S.ctl, (int)s->batch.size(), 0, 0));
     const long long rest = h.steps_left - 1;
-    if (rest > 0) {
-      if (!s->graph_ok) SKR(graph_build(s));
-      k_set_loop<<<1, 1, 0, s->st>>>(s->rs, rest);
-      SK(cudaGetLastError());
-      SK(cudaGraphLaunch(s->exec, s->st));
-    }
+    if (rest > 0) SKR(launch_steps(s, rest));
   }
-  s->stats.chunks += 1;
+  s->w_chunks += 1;
   return TERSOFF_OK;
 }
 
-// Copy results of jobs whose run is over (steps done, closing kick applied).
+// Copy results of jobs whose run is over (steps done, closing kick applied): one
+// energy kernel, one extraction kernel and one copy for all of them.
 int retire(tersoff_server *s, std::vector<Job *> &done)
 {
-  const size_t S = s->batch.size();
+  const int S = (int)s->batch.size();
   if (!S) return TERSOFF_OK;
   std::vector<SysCtl> ctl(S);
   SK(cudaMemcpyAsync(ctl.data(), s->S.ctl, sizeof(SysCtl) * S, cudaMemcpyDeviceToHost, s->st));
   SK(cudaStreamSynchronize(s->st));
-  bool any = false;
-  for (size_t k = 0; k < S; ++k) {
+  std::vector<int> rtab;   // [nret + 1] staging offsets, then [nret] systems
+  std::vector<int> rsys;
+  int64_t staged = 0;
+  for (int k = 0; k < S; ++k) {
     Job &J = *s->batch[k];
     J.ctl = ctl[k];
-    if (ctl[k].steps_left == 0 && ctl[k].open == 0) any = true;
+    if (ctl[k].steps_left == 0 && ctl[k].open == 0) {
+      rtab.push_back((int)staged);
+      rsys.push_back(k);
+      staged += J.n;
+    }
   }
-  if (!any) return TERSOFF_OK;
+  const int nret = (int)rsys.size();
+  if (!nret) return TERSOFF_OK;
+  rtab.push_back((int)staged);
+  rtab.insert(rtab.end(), rsys.begin(), rsys.end());
+  const size_t ebytes = sizeof(double) * 2 * S;
+  const size_t tbytes = (sizeof(int) * rtab.size() + 255) / 256 * 256;
+  const size_t nbytes = (size_t)staged * 6 * sizeof(double);
+  if (!host_reserve(s, ebytes + tbytes + nbytes) || !dreserve(s->stage, s->stage_b, nbytes))
+    return srv_err(s, TERSOFF_ERR_NOMEM, "staging");
+  char *h = s->hstage;
+  double *hE = (double *)h;
+  int *ht = (int *)(h + ebytes);
+  double *hpos = (double *)(h + ebytes + tbytes);
+  memcpy(ht, rtab.data(), sizeof(int) * rtab.size());
   AtomState &X = cur_atoms(s);
-  k_sys_energy<<<(int)S, 256, 0, s->st>>>(s->eatom, X.v, X.q, s->P->d_mass, s->S.tab, s->sysE);
+  k_sys_energy<<<S, 256, 0, s->st>>>(s->eatom, X.v, X.q, s->P->d_mass, s->S.tab, s->sysE);
   SK(cudaGetLastError());
-  std::vector<double> E(2 * S);
-  SK(cudaMemcpyAsync(E.data(), s->sysE, sizeof(double) * 2 * S, cudaMemcpyDeviceToHost, s->st));
-  for (size_t k = 0; k < S; ++k) {
-    Job &J = *s->batch[k];
-    if (!(J.ctl.steps_left == 0 && J.ctl.open == 0)) continue;
-    const int64_t o = s->tab[k].atom_off;
-    if (!dreserve(s->stage, s->stage_b, sizeof(double) * 6 * (size_t)J.n + 64))
-      return srv_err(s, TERSOFF_ERR_NOMEM, "staging");
-    double *dp = (double *)s->stage;
-    double *dv = dp + 3 * J.n;
-    SK(launch_extract(s->st, (int)J.n, X.x + o, X.v + o, dp, dv));
-    J.rpos.resize(3 * J.n);
-    J.rvel.resize(3 * J.n);
-    SK(cudaMemcpyAsync(J.rpos.data(), dp, sizeof(double) * 3 * J.n, cudaMemcpyDeviceToHost, s->st));
-    SK(cudaMemcpyAsync(J.rvel.data(), dv, sizeof(double) * 3 * J.n, cudaMemcpyDeviceToHost, s->st));
-    SK(cudaStreamSynchronize(s->st));
-    J.epot = E[2 * k];
-    J.ekin = E[2 * k + 1];
+  SK(cudaMemcpyAsync(s->dtabs, ht, sizeof(int) * rtab.size(), cudaMemcpyHostToDevice, s->st));
+  double *dpos = s->stage, *dvel = dpos + 3 * staged;
+  k_extract_batch<<<(int)((staged + 255) / 256), 256, 0, s->st>>>((int)staged, X.x, X.v, s->dtabs,
+                                                                   s->dtabs + nret + 1, nret, s->S.tab, dpos, dvel);
+  SK(cudaGetLastError());
+  SK(cudaMemcpyAsync(hE, s->sysE, ebytes, cudaMemcpyDeviceToHost, s->st));
+  SK(cudaMemcpyAsync(hpos, dpos, nbytes, cudaMemcpyDeviceToHost, s->st));
+  SK(cudaStreamSynchronize(s->st));
+  const double *hvel = hpos + 3 * staged;
+  for (int m = 0; m < nret; ++m) {
+    Job &J = *s->batch[rsys[m]];
+    J.rpos.assign(hpos + 3 * (size_t)rtab[m], hpos + 3 * (size_t)rtab[m] + 3 * J.n);
+    J.rvel.assign(hvel + 3 * (size_t)rtab[m], hvel + 3 * (size_t)rtab[m] + 3 * J.n);
+    J.epot = hE[2 * rsys[m]];
+    J.ekin = hE[2 * rsys[m] + 1];
     done.push_back(&J);
   }
   return TERSOFF_OK;
@@ -524,7 +669,9 @@ void worker_loop(tersoff_server *s)
     }
     // retire finished jobs
     std::vector<Job *> done;
+    double t0 = now_s();
     int rc = retire(s, done);
+    s->w_retire += now_s() - t0;
     if (rc != TERSOFF_OK) {
       fail_all(s, rc);
       continue;
@@ -535,6 +682,12 @@ void worker_loop(tersoff_server *s)
     {
       std::lock_guard<std::mutex> lk(s->mu);
       const double t = now_s();
+      s->stats.chunks = s->w_chunks;
+      s->stats.repacks = s->w_repacks;
+      s->stats.retire_s = s->w_retire;
+      s->stats.repack_s = s->w_repack;
+      s->stats.graph_s = s->w_graph;
+      s->stats.run_s = s->w_run;
       for (Job *jp : done) {
         jp->state = 2;
         jp->t_done = t;
@@ -572,10 +725,15 @@ void worker_loop(tersoff_server *s)
         s->tab.clear();
         s->natoms = 0;
         graph_free(s);
-      } else if ((rc = repack(s, order, is_new)) != TERSOFF_OK) {
-        s->batch = order;
-        fail_all(s, rc);
-        continue;
+      } else {
+        t0 = now_s();
+        rc = repack(s, order, is_new);
+        s->w_repack += now_s() - t0;
+        if (rc != TERSOFF_OK) {
+          s->batch = order;
+          fail_all(s, rc);
+          continue;
+        }
       }
     }
     // nothing left to integrate (all resident jobs finished): retire without stepping
@@ -586,14 +744,22 @@ void worker_loop(tersoff_server *s)
     }
     if (s->batch.empty()) {
       if (busy_since > 0) {
+        std::lock_guard<std::mutex> lk(s->mu);
         s->stats.busy_s += now_s() - busy_since;
         busy_since = 0;
       }
       continue;
     }
     if (busy_since == 0) busy_since = now_s();
-    if (active && (rc = run_chunk(s)) != TERSOFF_OK) fail_all(s, rc);
+    if (active) {
+      t0 = now_s();
+      const double g0 = s->w_graph;
+      rc = run_chunk(s);
+      s->w_run += now_s() - t0 - (s->w_graph - g0);
+      if (rc != TERSOFF_OK) fail_all(s, rc);
+    }
   }
+  std::lock_guard<std::mutex> lk(s->mu);
   if (busy_since > 0) s->stats.busy_s += now_s() - busy_since;
 }
 
@@ -622,7 +788,8 @@ int tersoff_server_create(tersoff_ctx *ctx, const tersoff_params *P, tersoff_pre
   s->chunk = chunk_steps;
   s->listcap = 32;
   s->fast_slots = (P->sym_angular && !ctx->general_only) ? 8 : 0;
-  s->gen_slots = 32;
+  s->gen_slots = 16;
+  s->use_graphs = !(getenv("TERSOFF_GRAPHS") && strcmp(getenv("TERSOFF_GRAPHS"), "0") == 0);
   s->cap_atoms = (int64_t)(budget / bytes_per_atom(s->mixed, s->listcap));
   auto fail = [&](int rc) {
     tersoff_server_destroy(s);
@@ -642,7 +809,8 @@ int tersoff_server_create(tersoff_ctx *ctx, const tersoff_params *P, tersoff_pre
       ensure_scatter(pc, s->SC, cap, s->listcap, s->mixed) != TERSOFF_OK ||
       ensure_list(pc, s->L, cap, s->listcap, 1) != TERSOFF_OK || !sys_alloc(s->S, max_slots) ||
       cudaMalloc((void **)&s->eatom, sizeof(double) * cap) != cudaSuccess ||
-      cudaMalloc((void **)&s->sysE, sizeof(double) * 2 * max_slots) != cudaSuccess) {
+      cudaMalloc((void **)&s->sysE, sizeof(double) * 2 * max_slots) != cudaSuccess ||
+      cudaMalloc((void **)&s->dtabs, sizeof(int) * 3 * (size_t)(max_slots + 1)) != cudaSuccess) {
     cudaGetLastError();
     return fail(set_err(ctx, TERSOFF_ERR_NOMEM, "cannot allocate the packed layout for %lld atoms", (long long)cap));
   }
@@ -785,6 +953,8 @@ void tersoff_server_destroy(tersoff_server *s)
   dfree(s->eatom);
   dfree(s->sysE);
   dfree(s->stage);
+  dfree(s->dtabs);
+  if (s->hstage) cudaFreeHost(s->hstage);
   if (s->st) cudaStreamDestroy(s->st);
   if (s->cap_st) cudaStreamDestroy(s->cap_st);
   tersoff_ctx *ctx = s->ctx;

@@ -91,7 +91,8 @@ class tersoff_job(ctypes.Structure):
 class tersoff_server_stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in ("submitted", "admitted", "completed", "failed", "queued", "running",
                                               "atom_steps", "chunks", "repacks")] + \
-               [("busy_s", ctypes.c_double), ("capacity_atoms", ctypes.c_int64)]
+               [("busy_s", ctypes.c_double), ("capacity_atoms", ctypes.c_int64)] + \
+               [(k, ctypes.c_double) for k in ("retire_s", "repack_s", "graph_s", "run_s")]
 
 
 _U64 = ctypes.c_uint64
@@ -294,9 +295,10 @@ class MD:
         self.ctx.check(tersoff_md_profile(self.h, 1 if enable else 0))
 
     def profile_read(self):
-        """(ms[4], launches[4]) for phases (integrator, list build, force, bookkeeping)."""
-        ms = np.zeros(4)
-        n = np.zeros(4, dtype=np.int64)
+        """(ms[5], launches[5]) for phases (integrator, list build, register force kernel,
+        overflow force kernel + reductions, bookkeeping)."""
+        ms = np.zeros(5)
+        n = np.zeros(5, dtype=np.int64)
         self.ctx.check(tersoff_md_profile_read(self.h, ptr(ms), ptr(n)))
         return ms, n
 
