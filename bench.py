@@ -89,6 +89,26 @@ def allreduce_max(ws, x):
     return float(t.item())
 
 
+def force_traffic():
+    """DRAM bytes (read + write) per launch of the mixed force kernel from the committed
+    ncu summary, or None when the kernel source changed since that capture."""
+    import hashlib
+    import re
+    path = os.path.join(ROOT, "profiles", "force_kernel_si512k_mixed.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    m_t = re.search(r"read \+ write\): (\d+) bytes", txt)
+    m_h = re.search(r"source_sha256 = ([0-9a-f]{16})", txt)
+    if not (m_t and m_h):
+        return None
+    h = hashlib.sha256()
+    for f in ("force.cu", "internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1710_00882_gb300", "csrc", f), "rb").read())
+    return int(m_t.group(1)) if h.hexdigest()[:16] == m_h.group(1) else None
+
+
 def workload_counts(s, rc, r_in):
     """Verlet-list entries (r < rc + skin), in-cutoff ordered pairs P, ordered pairs
     inside the cutoff taper (r_in < r < rc) and ordered triplets T of the starting
@@ -172,12 +192,14 @@ def run_gpu(args, ws, rank, local):
     n_list, npair, ntaper, ntrip = workload_counts(s, P.cutoff, si.R1)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
 
-    def timed(prec, steps, warmup):
+    def timed(prec, steps, warmup, sysm=None, params=None, dt=DT):
         """K steps as one graph launch (the way the library runs MD) bracketed by CUDA
         events after an L2 flush; then the timed steps of the headline, one graph launch
         each with L2 flushed before it; then a profiled pass (kernel by kernel, events
         around each phase) for the per-kernel times the roofline uses."""
-        md = T.MD(ctx, P, s.pos, s.vel, s.types, s.box, dt=DT, skin=SKIN, prec=prec)
+        sysm = s if sysm is None else sysm
+        md = T.MD(ctx, P if params is None else params, sysm.pos, sysm.vel, sysm.types, sysm.box, dt=dt, skin=SKIN,
+                  prec=prec)
         md.step_async(warmup)
         md.sync()
         st0 = md.stats()
@@ -228,6 +250,27 @@ def run_gpu(args, ws, rank, local):
     k_mix, k_64 = args.steps, max(3, args.steps // 4)
     one_mix, fl_mix, prof_mix, st_mix, md_mix = timed(T.MIXED, k_mix, args.warmup)
     one_64, fl_64, prof_64, st_64, md_64 = timed(T.FP64, k_64, args.warmup)
+    md_mix = md_64 = None
+    # 3C-SiC 50^3 cells with 5% vacancies (950,000 atoms), mixed, dt 0.5 fs
+    sic = None
+    if not args.no_sic:
+        sc = wl.sic_1m(seed=4 + rank)
+        tab2, m2 = pp.for_species(sc.species)
+        P2 = T.Params(ctx, tab2, m2)
+        k_sic = max(3, args.steps // 2)
+        one_s, fl_s, prof_s, st_s, md_s = timed(T.MIXED, k_sic, args.warmup, sc, P2, 0.5e-3)
+        md_s = None
+        fl_tot_s = allreduce_max(ws, sum(fl_s))
+        one_s = allreduce_max(ws, one_s)
+        sic = {"workload": f"3C-SiC a = 4.36, 50^3 cells, 5% vacancies = {sc.n} atoms, 1500 K, Tersoff 1989 "
+                           "Si-C, skin 0.3 A, dt 0.5 fs, mixed",
+               "value": ws * sc.n * len(fl_s) / (fl_tot_s / 1e3), "unit": "atom-steps/s",
+               "ms_per_step": fl_tot_s / len(fl_s), "steps": len(fl_s),
+               "one_launch": {"value": ws * sc.n * k_sic / (one_s / 1e3), "ms_per_step": one_s / k_sic},
+               "rebuilds_in_timed_steps": st_s["rebuilds_flushed"],
+               "phases_ms_per_step_profiled": {k: prof_s[0][n] / st_s["prof_steps"] for n, k in
+                                               enumerate(("integrator", "list_build", "force_register_kernel",
+                                                          "force_overflow_and_reduce", "bookkeeping"))}}
     clk = clocks.stop()
 
     # headline: one launch per step with L2 flushed before each step
@@ -262,13 +305,7 @@ def run_gpu(args, ws, rank, local):
                "d2h_bytes_per_step": (pos.nbytes + vel.nbytes) / n_e2e,
                "call": "tersoff_md_run(host pos/vel/types, 100 steps, mixed)", "seconds": t1 - t0}
 
-    traffic = None
-    tr_path = os.path.join(ROOT, "profiles", "force_kernel_traffic.json")
-    if os.path.exists(tr_path):
-        try:
-            traffic = json.load(open(tr_path)).get("mixed_si512k_bytes_per_launch")
-        except (OSError, ValueError):
-            traffic = None
+    traffic = force_traffic()
 
     # kernels per timed step on the graph path: set_control + loop_begin per launch,
     # then integrator, decide, force (register + overflow), step_end; 8 more on rebuilds
@@ -318,8 +355,9 @@ def run_gpu(args, ws, rank, local):
     }
     if e2e:
         line["e2e"] = e2e
+    if sic:
+        line["sic_1m"] = sic
     if args.serving_jobs > 0:
-        md_mix = md_64 = None
         line["serving"] = serving_bench(ctx, args.serving_jobs)
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args, s, quick=True)
@@ -429,6 +467,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-sic", action="store_true", help="skip the 950k-atom SiC line")
     ap.add_argument("--serving-jobs", type=int, default=4096, help="jobs of the serving stream (0: skip serving)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)

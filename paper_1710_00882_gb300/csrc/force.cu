@@ -349,14 +349,24 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
     }
     nc_all = __popcll(mb);
   } else if (active) {
-    for (int s = 0; s < n; ++s) {
-      const int j = nbr[(size_t)s * N + i];
-      int4 qj = make_int4(0, 0, 0, 0);
-      dbl4 xj = make_dbl4(0, 0, 0, 0);
-      int tj;
-      if (MIXED) { qj = q[j]; tj = type_of(qj.w); }
-      else { xj = x[j]; tj = type_of((int)__double_as_longlong(xj.w)); }
-      if (in_cutoff(qj, xj, tj)) mb |= 1ull << s;
+    // PU list entries per round: their loads are issued together
+    constexpr int PU = MIXED ? 4 : 2;
+    for (int s0 = 0; s0 < n; s0 += PU) {
+      int jj[PU];
+#pragma unroll
+      for (int k = 0; k < PU; ++k) jj[k] = s0 + k < n ? nbr[(size_t)(s0 + k) * N + i] : i;
+      int4 qq[PU];
+      dbl4 xx[PU];
+#pragma unroll
+      for (int k = 0; k < PU; ++k) {
+        if (MIXED) qq[k] = q[jj[k]];
+        else xx[k] = x[jj[k]];
+      }
+#pragma unroll
+      for (int k = 0; k < PU; ++k) {
+        const int tj = type_of(MIXED ? qq[k].w : (int)__double_as_longlong(xx[k].w));
+        if (s0 + k < n && in_cutoff(qq[k], xx[k], tj)) mb |= 1ull << (s0 + k);
+      }
     }
     nc_all = __popcll(mb);
   }

@@ -298,26 +298,53 @@ __global__ void __launch_bounds__(128) k_build(int N, const int4 *__restrict__ q
 // rev[s][i] = where the force gather finds the contribution of the terms of i's
 // neighbour j = nbr[s][i] on i: the flat index s2 * N + j of i's slot s2 in j's
 // (sorted) list, found by binary search (a 32-bit unsigned value: cap * N < 2^32).
-// One thread per list entry (grid y = slot), so the searches run side by side.
+// One thread per atom; the searches of up to RS slots run interleaved, level by
+// level, so their loads are in flight together.
+constexpr int RS = 8;
 __global__ void k_reverse(int N, const int4 *__restrict__ q, const SysCtl *__restrict__ ctl,
                           const int *__restrict__ nbr, const int *__restrict__ cnt, int *__restrict__ rev, RunState *rs,
                           int gated)
 {
   if (skip_build(rs, gated)) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int s = blockIdx.y;
-  if (i >= N || s >= cnt[i]) return;
+  if (i >= N) return;
   if (ctl && ctl[sys_of(q[i].w)].rebuild == 0) return;
-  const int j = nbr[(size_t)s * N + i];
-  int lo = 0, hi = cnt[j] - 1, found = -1;
-  while (lo <= hi) {
-    const int mid = (lo + hi) >> 1;
-    const int v = nbr[(size_t)mid * N + j];
-    if (v == i) { found = mid; break; }
-    if (v < i) lo = mid + 1; else hi = mid - 1;
+  const int n = cnt[i];
+  bool missing = false;
+  for (int s0 = 0; s0 < n; s0 += RS) {
+    int j[RS], lo[RS], hi[RS], found[RS];
+#pragma unroll
+    for (int k = 0; k < RS; ++k) j[k] = s0 + k < n ? nbr[(size_t)(s0 + k) * N + i] : -1;
+#pragma unroll
+    for (int k = 0; k < RS; ++k) {
+      lo[k] = 0;
+      hi[k] = j[k] >= 0 ? cnt[j[k]] - 1 : -1;
+      found[k] = -1;
+    }
+    bool more = true;
+    while (more) {
+      more = false;
+#pragma unroll
+      for (int k = 0; k < RS; ++k) {
+        if (found[k] < 0 && lo[k] <= hi[k]) {
+          const int mid = (lo[k] + hi[k]) >> 1;
+          const int v = nbr[(size_t)mid * N + j[k]];
+          if (v == i) found[k] = mid;
+          else if (v < i) lo[k] = mid + 1;
+          else hi[k] = mid - 1;
+          more = true;
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < RS; ++k) {
+      if (j[k] < 0) continue;
+      if (found[k] < 0) missing = true;
+      rev[(size_t)(s0 + k) * N + i] =
+          (int)((unsigned)(found[k] < 0 ? 0 : found[k]) * (unsigned)N + (unsigned)j[k]);
+    }
   }
-  if (found < 0) atomicOr(&rs->status, ST_REV_MISSING);
-  rev[(size_t)s * N + i] = (int)((unsigned)(found < 0 ? 0 : found) * (unsigned)N + (unsigned)j);
+  if (missing) atomicOr(&rs->status, ST_REV_MISSING);
 }
 
 // close a build: count it, clear the request
@@ -352,7 +379,7 @@ cudaError_t launch_build(cudaStream_t st, int N, const int4 *q, const SysTab *sy
   k_cell_fill<<<BN, T, 0, st>>>(N, q, cell_of, rank, cell_start, cell_atoms, rs, gated);
   const int BN128 = (N + 127) / 128;
   k_build<<<BN128, 128, 0, st>>>(N, q, sys, ctl, rl2, cell_start, cell_atoms, nbr, cnt, cap, qref, rs, gated);
-  k_reverse<<<dim3(BN128, cap), 128, 0, st>>>(N, q, ctl, nbr, cnt, rev, rs, gated);
+  k_reverse<<<BN128, 128, 0, st>>>(N, q, ctl, nbr, cnt, rev, rs, gated);
   k_build_done<<<1, 1, 0, st>>>(rs, gated);
   return cudaGetLastError();
 }
