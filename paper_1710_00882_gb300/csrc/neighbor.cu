@@ -9,7 +9,8 @@
 //   k_cell_count  -> cell of each atom, rank inside its cell (atomic)
 //   k_scan_*      -> exclusive scan of the cell counts (three-phase block scan)
 //   k_cell_fill   -> atoms in cell order
-//   k_build       -> per atom: 27-cell stencil, keep r < r_list, sort by j
+//   k_build       -> per atom: half stencil, each pair within r_list appended to both lists
+//   k_sort_lists  -> each list sorted by j; overflow check
 //   k_reverse     -> for each entry (i,s) the flat index of i's slot in j's list
 #include "internal.cuh"
 
@@ -28,13 +29,15 @@ __device__ __forceinline__ int cell_coord(uint32_t qa, int nc)
 // Each atom's cell in its own system's grid, numbered globally (system cell offset
 // + local cell), and its rank inside the cell.
 __global__ void k_cell_count(int N, const int4 *__restrict__ q, const SysTab *__restrict__ sys,
-                             int *__restrict__ cell_of, int *__restrict__ rank, int *__restrict__ cell_count,
-                             const RunState *rs, int gated)
+                             const SysCtl *__restrict__ ctl, int *__restrict__ cell_of, int *__restrict__ rank,
+                             int *__restrict__ cell_count, int *__restrict__ cnt, const RunState *rs, int gated)
 {
   if (skip_build(rs, gated)) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   int4 p = q[i];
+  // list counts of the atoms that get new lists start at zero (pairs are appended)
+  if (!ctl || ctl[sys_of(p.w)].rebuild) cnt[i] = 0;
   const SysTab &T = sys[sys_of(p.w)];
   int cx = cell_coord((uint32_t)p.x, T.nc[0]);
   int cy = cell_coord((uint32_t)p.y, T.nc[1]);
@@ -190,10 +193,24 @@ __device__ __forceinline__ void sort_column(int *__restrict__ nbr, int N, int i,
     if (s < n) nbr[(size_t)s * N + i] = v[s];
 }
 
+// Append pair (i, j) to both lists (slot from an atomic count; order fixed later by
+// the sort).
+__device__ __forceinline__ void add_pair(int i, int j, int N, int cap, int *__restrict__ nbr, int *__restrict__ cnt)
+{
+  const int si = atomicAdd(&cnt[i], 1);
+  if (si < cap) nbr[(size_t)si * N + i] = j;
+  const int sj = atomicAdd(&cnt[j], 1);
+  if (sj < cap) nbr[(size_t)sj * N + j] = i;
+}
+
 // One thread per atom, atoms taken in cell order (threads of a warp share most of
-// their 27 stencil cells, so candidate loads hit L1): scan the stencil, keep j with
-// |d_ij| < r_list, then sort the column by j so that the list order depends only on
-// the set of neighbours.
+// their stencil cells, so candidate loads hit L1).  Each pair within r_list is found
+// once and appended to both lists: atom i scans its own cell (j > i) and the 13
+// "forward" neighbour cells (dz = +1; dz = 0, dy = +1; dz = dy = 0, dx = +1), which
+// with every axis >= 3 cells hold each neighbouring cell pair exactly once.  A
+// system with an axis of fewer than 3 cells scans its whole (deduplicated) stencil
+// and keeps j > i.  Candidates of one stencil row are one run of cell_atoms (two
+// where the row wraps).
 __global__ void __launch_bounds__(128) k_build(int N, const int4 *__restrict__ q, const SysTab *__restrict__ sys,
                                                const SysCtl *__restrict__ ctl, float rl2,
                                                const int *__restrict__ cell_start,
@@ -201,7 +218,6 @@ __global__ void __launch_bounds__(128) k_build(int N, const int4 *__restrict__ q
                                                int *__restrict__ cnt, int cap, int4 *__restrict__ qref, RunState *rs,
                                                int gated)
 {
-  __shared__ int sbuf[32][128];
   if (skip_build(rs, gated)) return;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= N) return;
@@ -214,56 +230,108 @@ __global__ void __launch_bounds__(128) k_build(int N, const int4 *__restrict__ q
   const float s0 = T.geo.q_to_f[0], s1 = T.geo.q_to_f[1], s2 = T.geo.q_to_f[2];
   const int nc0 = T.nc[0], nc1 = T.nc[1], nc2 = T.nc[2];
   const int coff = T.cell_off;
-  int c[3] = {cell_coord((uint32_t)pi.x, nc0), cell_coord((uint32_t)pi.y, nc1), cell_coord((uint32_t)pi.z, nc2)};
-  int lo[3], nr[3];
-  axis_range(c[0], nc0, &lo[0], &nr[0]);
-  axis_range(c[1], nc1, &lo[1], &nr[1]);
-  axis_range(c[2], nc2, &lo[2], &nr[2]);
-  // the x cells of one stencil row are one run of cell_atoms, or two where the row wraps
-  const int xa = lo[0] < 0 ? lo[0] + nc0 : lo[0];
-  const int xe = xa + nr[0];
-  const int xa2 = xe > nc0 ? 0 : xa, xe1 = xe > nc0 ? nc0 : xe, xe2 = xe > nc0 ? xe - nc0 : 0;
-  int n = 0;
-  for (int oz = 0; oz < nr[2]; ++oz) {
-    int cz = lo[2] + oz;
-    cz += (cz < 0) ? nc2 : 0;
-    cz -= (cz >= nc2) ? nc2 : 0;
-    for (int oy = 0; oy < nr[1]; ++oy) {
-      int cy = lo[1] + oy;
-      cy += (cy < 0) ? nc1 : 0;
-      cy -= (cy >= nc1) ? nc1 : 0;
-      const int row = coff + (cz * nc1 + cy) * nc0;
-      for (int part = 0; part < 2; ++part) {
-        if (part == 1 && xe2 == 0) break;
-        const int b = part == 0 ? cell_start[row + xa] : cell_start[row + xa2];
-        const int e = part == 0 ? cell_start[row + xe1] : cell_start[row + xe2];
-        // four candidates per round: their loads are issued together
-        for (int u = b; u < e; u += 4) {
-          int4 pj[4];
+  const int cx = cell_coord((uint32_t)pi.x, nc0), cy = cell_coord((uint32_t)pi.y, nc1),
+            cz = cell_coord((uint32_t)pi.z, nc2);
+  const bool half = nc0 >= 3 && nc1 >= 3 && nc2 >= 3;
+
+  // scan candidates [b, e) of cell_atoms (four per round: their loads go together)
+  auto scan = [&](int b, int e) {
+    for (int u = b; u < e; u += 4) {
+      int4 pj[4];
 #pragma unroll
-          for (int k = 0; k < 4; ++k) pj[k] = u + k < e ? cell_atoms[u + k] : make_int4(0, 0, 0, -1);
+      for (int k = 0; k < 4; ++k) pj[k] = u + k < e ? cell_atoms[u + k] : make_int4(0, 0, 0, -1);
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const int j = pj[k].w;
-            const float dx = q_scaled(qdiff(pj[k].x, pi.x), s0);
-            const float dy = q_scaled(qdiff(pj[k].y, pi.y), s1);
-            const float dz = q_scaled(qdiff(pj[k].z, pi.z), s2);
-            const float r2 = r2_decide(dx, dy, dz);
-            if (j >= 0 && j != i && r2 < rl2) {
-              if (n < cap) nbr[(size_t)n * N + i] = j;
-              ++n;
-            }
-          }
-        }
+      for (int k = 0; k < 4; ++k) {
+        const int j = pj[k].w;
+        const float dx = q_scaled(qdiff(pj[k].x, pi.x), s0);
+        const float dy = q_scaled(qdiff(pj[k].y, pi.y), s1);
+        const float dz = q_scaled(qdiff(pj[k].z, pi.z), s2);
+        const float r2 = r2_decide(dx, dy, dz);
+        if (j > i && r2 < rl2) add_pair(i, j, N, cap, nbr, cnt);
       }
     }
+  };
+  // cells x0 .. x0 + nx - 1 (mod nc0) of row (y, z): one or two runs
+  auto scan_row = [&](int y, int z, int x0, int nx) {
+    y += (y < 0) ? nc1 : 0;
+    y -= (y >= nc1) ? nc1 : 0;
+    z += (z < 0) ? nc2 : 0;
+    z -= (z >= nc2) ? nc2 : 0;
+    x0 += (x0 < 0) ? nc0 : 0;
+    x0 -= (x0 >= nc0) ? nc0 : 0;
+    const int row = coff + (z * nc1 + y) * nc0;
+    const int xe = x0 + nx;
+    scan(cell_start[row + x0], cell_start[row + min(xe, nc0)]);
+    if (xe > nc0) scan(cell_start[row], cell_start[row + xe - nc0]);
+  };
+
+  if (half) {
+    // own cell and its +x neighbour; keep j > i only in the own cell
+    const int row = coff + (cz * nc1 + cy) * nc0;
+    {
+      const int b = cell_start[row + cx], e = cell_start[row + cx + 1];
+      scan(b, e);
+    }
+    // forward cells: j may be smaller or larger than i, so test j != i by cell instead
+    auto scan_any = [&](int b, int e) {
+      for (int u = b; u < e; u += 4) {
+        int4 pj[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) pj[k] = u + k < e ? cell_atoms[u + k] : make_int4(0, 0, 0, -1);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int j = pj[k].w;
+          const float dx = q_scaled(qdiff(pj[k].x, pi.x), s0);
+          const float dy = q_scaled(qdiff(pj[k].y, pi.y), s1);
+          const float dz = q_scaled(qdiff(pj[k].z, pi.z), s2);
+          const float r2 = r2_decide(dx, dy, dz);
+          if (j >= 0 && r2 < rl2) add_pair(i, j, N, cap, nbr, cnt);
+        }
+      }
+    };
+    auto row_any = [&](int y, int z, int x0, int nx) {
+      y += (y < 0) ? nc1 : 0;
+      y -= (y >= nc1) ? nc1 : 0;
+      z += (z < 0) ? nc2 : 0;
+      z -= (z >= nc2) ? nc2 : 0;
+      x0 += (x0 < 0) ? nc0 : 0;
+      x0 -= (x0 >= nc0) ? nc0 : 0;
+      const int r = coff + (z * nc1 + y) * nc0;
+      const int xe = x0 + nx;
+      scan_any(cell_start[r + x0], cell_start[r + min(xe, nc0)]);
+      if (xe > nc0) scan_any(cell_start[r], cell_start[r + xe - nc0]);
+    };
+    row_any(cy, cz, cx + 1, 1);
+    row_any(cy + 1, cz, cx - 1, 3);
+    row_any(cy - 1, cz + 1, cx - 1, 3);
+    row_any(cy, cz + 1, cx - 1, 3);
+    row_any(cy + 1, cz + 1, cx - 1, 3);
+  } else {
+    // whole stencil, every cell once
+    const int ny = nc1 >= 3 ? 3 : nc1, nz = nc2 >= 3 ? 3 : nc2, nx = nc0 >= 3 ? 3 : nc0;
+    const int y0 = nc1 >= 3 ? cy - 1 : 0, z0 = nc2 >= 3 ? cz - 1 : 0, x0 = nc0 >= 3 ? cx - 1 : 0;
+    for (int oz = 0; oz < nz; ++oz)
+      for (int oy = 0; oy < ny; ++oy) scan_row(y0 + oy, z0 + oz, x0, nx);
   }
-  cnt[i] = n;
+}
+
+// Sort each rebuilt list by neighbour index, so that the list order depends only on
+// the set of neighbours; flag lists longer than the capacity.
+__global__ void __launch_bounds__(128) k_sort_lists(int N, const int4 *__restrict__ q, const SysCtl *__restrict__ ctl,
+                                                    int *__restrict__ nbr, const int *__restrict__ cnt, int cap,
+                                                    RunState *rs, int gated)
+{
+  __shared__ int sbuf[32][128];
+  if (skip_build(rs, gated)) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  if (ctl && ctl[sys_of(q[i].w)].rebuild == 0) return;
+  int n = cnt[i];
+  atomicMax(&rs->maxcount, n);
   if (n > cap) {
     atomicOr(&rs->status, ST_NLIST_OVERFLOW);
-    n = cap;
+    return;
   }
-  atomicMax(&rs->maxcount, cnt[i]);
   if (n <= 8) {
     sort_column<8>(nbr, N, i, n);
   } else if (n <= 16) {
@@ -372,13 +440,14 @@ cudaError_t launch_build(cudaStream_t st, int N, const int4 *q, const SysTab *sy
   const int T = 256;
   const int BN = (N + T - 1) / T;
   const int ntiles = (ncell + SCAN_TILE - 1) / SCAN_TILE;
-  k_cell_count<<<BN, T, 0, st>>>(N, q, sys, cell_of, rank, cell_count, rs, gated);
+  k_cell_count<<<BN, T, 0, st>>>(N, q, sys, ctl, cell_of, rank, cell_count, cnt, rs, gated);
   k_scan_tiles<<<ntiles, SCAN_THREADS, 0, st>>>(ncell, cell_count, cell_start, tile_sums, rs, gated);
   k_scan_sums<<<1, SCAN_THREADS, 0, st>>>(ntiles, tile_sums, cell_start + ncell, rs, gated);
   k_scan_add<<<(ncell + T - 1) / T, T, 0, st>>>(ncell, cell_start, tile_sums, cell_count, rs, gated);
   k_cell_fill<<<BN, T, 0, st>>>(N, q, cell_of, rank, cell_start, cell_atoms, rs, gated);
   const int BN128 = (N + 127) / 128;
   k_build<<<BN128, 128, 0, st>>>(N, q, sys, ctl, rl2, cell_start, cell_atoms, nbr, cnt, cap, qref, rs, gated);
+  k_sort_lists<<<BN128, 128, 0, st>>>(N, q, ctl, nbr, cnt, cap, rs, gated);
   k_reverse<<<BN128, 128, 0, st>>>(N, q, ctl, nbr, cnt, rev, rs, gated);
   k_build_done<<<1, 1, 0, st>>>(rs, gated);
   return cudaGetLastError();
