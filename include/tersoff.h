@@ -210,7 +210,7 @@ int tersoff_md_run(tersoff_ctx *ctx, double *pos, double *vel, const int32_t *ty
 #define TERSOFF_NOALLOC_MAX_ATOMS 16384
 #define TERSOFF_NOALLOC_MAX_NEIGHBORS 32
 #define TERSOFF_NOALLOC_MAX_CELLS 32768
-#define TERSOFF_NOALLOC_SCRATCH_BYTES 23539200
+#define TERSOFF_NOALLOC_SCRATCH_BYTES 23540480
 int tersoff_compute_noalloc(const tersoff_params *params, const double *pos, const int32_t *types, int64_t N,
                             const double box[3], tersoff_precision prec, void *stream, double *energy_virial,
                             double *forces, char *errbuf, size_t errlen);

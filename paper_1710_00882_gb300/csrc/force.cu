@@ -224,7 +224,8 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
             const TripP<R> *__restrict__ gtrips, int nt, typename V4t<R>::type *__restrict__ contrib,
             typename V4t<R>::type *__restrict__ selfF, unsigned long long *__restrict__ mask,
             int *__restrict__ work, int *__restrict__ nwork, double *__restrict__ partial, RunState *rs,
-            double *__restrict__ eatom)
+            double *__restrict__ eatom, const int *__restrict__ order, int begin, int count, int block_base,
+            int stats)
 {
   using M = typename MathOf<R>::M;
   using V4 = typename V4t<R>::type;
@@ -240,8 +241,10 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
   __syncthreads();
 
   const int t = threadIdx.x;
-  const int i = blockIdx.x * T + t;
-  const bool active = i < N;
+  const int tg = blockIdx.x * T + t;
+  const bool active = tg < count;
+  const int i = active ? (order ? order[begin + tg] : begin + tg) : 0;
+  const int fb = block_base + (int)blockIdx.x;   // this block's queue and partial-sum row
 
   int ti = 0;
   int4 qi = make_int4(0, 0, 0, 0);
@@ -380,20 +383,31 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
       int base = 0;
       for (int w = 0; w < (t >> 5); ++w) base += warp_over[w];
       const int k = base + __popc(bal & ((1u << (t & 31)) - 1u));
-      work[(size_t)blockIdx.x * T + k] = i;
+      work[(size_t)fb * T + k] = i;
     }
     if (t == 0) {
       int s = 0;
       for (int w = 0; w < T / 32; ++w) s += warp_over[w];
-      nwork[blockIdx.x] = s;
+      nwork[fb] = s;
       if (s > 0) atomicAdd(&rs->over_total, s);
     }
   }
-  {
-    int m = nc_all;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((t & 31) == 0 && m > 0) atomicMax(&rs->maxnc, m);
+  if (stats) {
+    // largest in-cutoff counts, overall and per type (they choose the slot counts of
+    // later launches): warp maxima, then one atomic per block and statistic
+    __shared__ unsigned smax[T / 32][MAX_TYPES + 1];
+    const unsigned m = __reduce_max_sync(0xffffffffu, (unsigned)nc_all);
+    if ((t & 31) == 0) smax[t >> 5][MAX_TYPES] = m;
+    for (int ty = 0; ty < (ONE ? 1 : nt); ++ty) {
+      const unsigned mt = __reduce_max_sync(0xffffffffu, (unsigned)((active && (ONE || ti == ty)) ? nc_all : 0));
+      if ((t & 31) == 0) smax[t >> 5][ty] = mt;
+    }
+    __syncthreads();
+    if (t <= MAX_TYPES && (t == MAX_TYPES || t < (ONE ? 1 : nt))) {
+      unsigned bm = 0;
+      for (int w = 0; w < T / 32; ++w) bm = max(bm, smax[w][t]);
+      if (bm > 0) atomicMax(t == MAX_TYPES ? &rs->maxnc : &rs->maxnc_t[t], (int)bm);
+    }
   }
   // slots in use: the whole list on the direct path, the packed in-cutoff entries else
   const int nc = direct ? n : (over ? 0 : nc_all);
@@ -537,7 +551,7 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
     mask[i] = mb;
     if (eatom) eatom[i] = (double)e_i;
   }
-  if (EFLAG || VFLAG) block_partial<R, T>(red, EFLAG, VFLAG, partial + (size_t)blockIdx.x * 8);
+  if (EFLAG || VFLAG) block_partial<R, T>(red, EFLAG, VFLAG, partial + (size_t)fb * 8);
 }
 
 // ============================================================================
@@ -966,24 +980,25 @@ template <class R, int MAXNC, bool ONE>
 static cudaError_t launch_reg(cudaStream_t st, int eflag, int vflag, int N, const dbl4 *x, const int4 *q,
                               const int *nbr, const int *cnt, const SysTab *sys, const void *pairs, const void *trips,
                               int nt, void *contrib, void *selfF, unsigned long long *mask, int *work, int *nwork,
-                              double *partial, RunState *rs, double *eatom)
+                              double *partial, RunState *rs, double *eatom, const ForceRoute &rt, int stats)
 {
-  const int blocks = (N + FAST_THREADS - 1) / FAST_THREADS;
+  const int blocks = (rt.count + FAST_THREADS - 1) / FAST_THREADS;
+  if (blocks == 0) return cudaSuccess;
   using P = const PairP<R> *;
   using Tt = const TripP<R> *;
   using V = typename V4t<R>::type *;
   if (vflag)
     k_force_reg<R, MAXNC, ONE, true, true><<<blocks, FAST_THREADS, 0, st>>>(
         N, x, q, nbr, cnt, sys, (P)pairs, (Tt)trips, nt, (V)contrib, (V)selfF, mask, work, nwork, partial, rs,
-        eatom);
+        eatom, rt.order, rt.begin, rt.count, rt.block_base, stats);
   else if (eflag)
     k_force_reg<R, MAXNC, ONE, true, false><<<blocks, FAST_THREADS, 0, st>>>(
         N, x, q, nbr, cnt, sys, (P)pairs, (Tt)trips, nt, (V)contrib, (V)selfF, mask, work, nwork, partial, rs,
-        eatom);
+        eatom, rt.order, rt.begin, rt.count, rt.block_base, stats);
   else
     k_force_reg<R, MAXNC, ONE, false, false><<<blocks, FAST_THREADS, 0, st>>>(
         N, x, q, nbr, cnt, sys, (P)pairs, (Tt)trips, nt, (V)contrib, (V)selfF, mask, work, nwork, partial, rs,
-        eatom);
+        eatom, rt.order, rt.begin, rt.count, rt.block_base, stats);
   return cudaGetLastError();
 }
 
@@ -998,35 +1013,47 @@ int force_slots_for(int need)
 int force_gen_blocks() { return GEN_BLOCKS; }
 
 // Rows of 8 doubles the partial-sum buffer needs for N atoms (any launch shape).
-int force_partial_rows(int N) { return (N + 31) / 32 + force_gen_blocks(); }
+int force_partial_rows(int N) { return (N + 31) / 32 + 2 + force_gen_blocks(); }
+
+// Overflow-queue blocks for N atoms split into up to two register-kernel launches.
+int force_queue_blocks(int N) { return (N + 127) / 128 + 2; }
 
 // One force evaluation.  fast_slots 4 or 8 runs the register kernel plus the
 // general kernel (gen_slots wide) over its overflow queue; fast_slots 0 runs the
-// general kernel over all atoms.  Buffers: partial force_partial_rows(N) x 8
-// doubles; work N ints; nwork ceil(N/128) ints.  With eflag/vflag the energy and
-// virial are added to rs->epot / rs->virial.  part: 1 launches the register
-// kernel only, 2 the rest (general kernel and reduction), 3 both.
+// general kernel over all atoms.  routes (may be null: every atom in index order with
+// fast_slots) splits the register kernel into launches over atom subsets, each with
+// its own slot count.  Buffers: partial force_partial_rows(N) x 8 doubles; work
+// force_queue_blocks(N) x 128 ints; nwork force_queue_blocks(N) ints.  With
+// eflag/vflag the energy and virial are added to rs->epot / rs->virial.  part: 1
+// launches the register kernel(s) only, 2 the rest (general kernel and reduction),
+// 3 both.  stats: record the largest in-cutoff counts (rs->maxnc, rs->maxnc_t).
 cudaError_t launch_force_part(int part, cudaStream_t st, bool mixed, int fast_slots, bool one_type, int gen_slots,
                               int eflag, int vflag, int N, const dbl4 *x, const int4 *q, const int *nbr,
                               const int *cnt, const SysTab *sys, const void *pairs, const void *trips, int nt,
                               void *contrib, void *selfF, unsigned long long *mask, int *work, int *nwork,
-                              double *partial, RunState *rs, double *eatom)
+                              double *partial, RunState *rs, double *eatom, const ForceRoutes *routes, int stats)
 {
   if (N == 0) return cudaSuccess;
-  const int nfast = (N + FAST_THREADS - 1) / FAST_THREADS;
   cudaError_t e = cudaSuccess;
   int rows = 0;
   if (fast_slots > 0) {
-    if (part & 1) {
-#define TSF_REG(R, NC)                                                                                              \
-  e = one_type ? launch_reg<R, NC, true>(st, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib, selfF, \
-                                         mask, work, nwork, partial, rs, eatom)                                     \
-               : launch_reg<R, NC, false>(st, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib,      \
-                                          selfF, mask, work, nwork, partial, rs, eatom);
+    ForceRoutes one{1, {{nullptr, 0, N, fast_slots, 0}, {nullptr, 0, 0, 0, 0}}};
+    const ForceRoutes &R = routes ? *routes : one;
+    int nfast = 0;
+    for (int k = 0; k < R.n; ++k) {
+      ForceRoute rt = R.r[k];
+      rt.block_base = nfast;
+      nfast += (rt.count + FAST_THREADS - 1) / FAST_THREADS;
+      if (!(part & 1)) continue;
+#define TSF_REG(RT, NC)                                                                                             \
+  e = one_type ? launch_reg<RT, NC, true>(st, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib, selfF, \
+                                          mask, work, nwork, partial, rs, eatom, rt, stats)                         \
+               : launch_reg<RT, NC, false>(st, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib,     \
+                                           selfF, mask, work, nwork, partial, rs, eatom, rt, stats);
       if (mixed) {
-        if (fast_slots <= 4) { TSF_REG(float, 4) } else { TSF_REG(float, 8) }
+        if (rt.slots <= 4) { TSF_REG(float, 4) } else { TSF_REG(float, 8) }
       } else {
-        if (fast_slots <= 4) { TSF_REG(double, 4) } else { TSF_REG(double, 8) }
+        if (rt.slots <= 4) { TSF_REG(double, 4) } else { TSF_REG(double, 8) }
       }
 #undef TSF_REG
       if (e != cudaSuccess) return e;
@@ -1062,7 +1089,7 @@ cudaError_t launch_force(cudaStream_t st, bool mixed, int fast_slots, bool one_t
                          double *eatom)
 {
   return launch_force_part(3, st, mixed, fast_slots, one_type, gen_slots, eflag, vflag, N, x, q, nbr, cnt, sys, pairs,
-                           trips, nt, contrib, selfF, mask, work, nwork, partial, rs, eatom);
+                           trips, nt, contrib, selfF, mask, work, nwork, partial, rs, eatom, nullptr, 1);
 }
 
 }  // namespace tsf

@@ -77,6 +77,19 @@ struct RunState {
   long long trace_k;     // trace row of the step in progress (1-based within a call)
   long long steps_left;  // steps still to run in the current graph launch
   int over_total;        // atoms the register force kernel queued for the general kernel
+  int maxnc_t[MAX_TYPES];  // max in-cutoff count seen by the register force kernel, per atom type
+};
+
+// Atoms of a register-force-kernel launch: order[begin .. begin + count) (or atoms
+// begin .. begin + count - 1 when order is null), slots per atom; block indices of
+// the overflow queues and partial sums start at block_base.
+struct ForceRoute {
+  const int *order;
+  int begin, count, slots, block_base;
+};
+struct ForceRoutes {
+  int n;                 // 1 or 2 launches
+  ForceRoute r[2];
 };
 
 // minimum-image difference of two fixed-point coordinates, in units of L / 2^32

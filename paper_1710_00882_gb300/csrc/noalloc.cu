@@ -59,10 +59,12 @@ struct Layout {
   static constexpr size_t selfF = contrib + up256(kMaxAtoms * kCap * sizeof(dbl4));
   static constexpr size_t mask = selfF + up256(kMaxAtoms * sizeof(dbl4));
   static constexpr size_t work = mask + up256(kMaxAtoms * sizeof(unsigned long long));
-  static constexpr size_t nwork = work + up256(kMaxAtoms * sizeof(int));
-  static constexpr size_t partial = nwork + up256((kMaxAtoms / 128 + 1) * sizeof(int));
-  // force_partial_rows(N) = ceil(N / 32) + GEN_BLOCKS rows of 8 float64
-  static constexpr size_t partial_rows = (kMaxAtoms + 31) / 32 + GEN_BLOCKS;
+  // overflow queues: force_queue_blocks(N) = ceil(N / 128) + 2 blocks of 128 entries
+  static constexpr size_t queue_blocks = (kMaxAtoms + 127) / 128 + 2;
+  static constexpr size_t nwork = work + up256(queue_blocks * 128 * sizeof(int));
+  static constexpr size_t partial = nwork + up256(queue_blocks * sizeof(int));
+  // force_partial_rows(N) = ceil(N / 32) + 2 + GEN_BLOCKS rows of 8 float64
+  static constexpr size_t partial_rows = (kMaxAtoms + 31) / 32 + 2 + GEN_BLOCKS;
   static constexpr size_t total = partial + up256(partial_rows * 8 * sizeof(double));
 };
 

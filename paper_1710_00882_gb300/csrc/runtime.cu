@@ -127,6 +127,9 @@ struct tersoff_md {
   long long steps_target = 0;   // host count of enqueued steps
   int fast_slots = 8;   // register force kernel slots (4 or 8; 0 = general kernel only)
   int gen_slots = 8;    // general force kernel slots
+  bool routed = false;  // register kernel split by atom type into a 4-slot and an 8-slot launch
+  ForceRoutes routes{};
+  int *d_order = nullptr;
   // phase profiling: event pairs per phase, reused across reads
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -228,7 +231,7 @@ int ensure_scatter(tersoff_ctx *ctx, AtomState &A, int64_t N, int cap, bool mixe
 {
   size_t v4 = mixed ? sizeof(float4) : sizeof(dbl4);
   size_t n = (size_t)std::max<int64_t>(N, 1);
-  const size_t nfast = (n + 127) / 128;
+  const size_t nfast = (size_t)force_queue_blocks((int)n);
   if (!dreserve(A.contrib, A.contrib_b, n * (size_t)cap * v4) || !dreserve(A.selfF, A.selfF_b, n * v4) ||
       !dreserve(A.mask, A.mask_b, n * sizeof(unsigned long long)) ||
       !dreserve(A.work, A.work_b, nfast * 128 * sizeof(int)) || !dreserve(A.nwork, A.nwork_b, nfast * sizeof(int)) ||
@@ -741,14 +744,15 @@ static void md_mark_end(tersoff_md *md, int phase, size_t begin, int nlaunch)
   }
 }
 
-static int md_force(tersoff_md *md, cudaStream_t st, int eflag, int part = 3)
+// stats: record the largest in-cutoff counts (set-up and recovery; off in steps)
+static int md_force(tersoff_md *md, cudaStream_t st, int eflag, int part = 3, int stats = 0)
 {
   tersoff_ctx *ctx = md->ctx;
   const tersoff_params *P = md->params;
   CK(launch_force_part(part, st, md->mixed, md->fast_slots, P->nt == 1, md->gen_slots, eflag, 0, (int)md->atoms.N, md->atoms.x,
                   md->atoms.q, md->list.nbr, md->list.cnt, md->sys.tab, md->mixed ? P->pair_f : P->pair_d,
                   md->mixed ? P->trip_f : P->trip_d, P->nt, md->atoms.contrib, md->atoms.selfF, md->atoms.mask,
-                  md->atoms.work, md->atoms.nwork, md->atoms.partial, md->rs, nullptr));
+                  md->atoms.work, md->atoms.nwork, md->atoms.partial, md->rs, nullptr, md->routed ? &md->routes : nullptr, stats));
   return TERSOFF_OK;
 }
 
@@ -920,7 +924,7 @@ static int md_recover(tersoff_md *md, const RunState &h, double *d_trace)
     return status_to_code(ctx, h.status, h);
   }
   CK(cudaMemsetAsync(&md->rs->epot, 0, sizeof(double), st));
-  CKR(md_force(md, st, d_trace ? 1 : 0));
+  CKR(md_force(md, st, d_trace ? 1 : 0, 3, 1));
   CK(launch_step_end(st, md->rs, md->sys.ctl, 1, 0, 0));
   const long long rest = h.steps_left - 1;
   if (rest > 0) CKR(md_launch_steps(md, rest, d_trace, h.trace_k + 1));
@@ -998,7 +1002,7 @@ int tersoff_md_create(tersoff_ctx *ctx, const double *pos, const double *vel, co
   if ((rc = ensure_scatter(ctx, md->atoms, N, md->list.cap, md->mixed)) != TERSOFF_OK) return fail(rc);
   md->gen_slots = force_slots_for(std::max(1, md->list.maxcount));
   md->fast_slots = (P->sym_angular && !ctx->general_only) ? 8 : 0;
-  if ((rc = md_force(md, ctx->stream, 1)) != TERSOFF_OK) return fail(rc);
+  if ((rc = md_force(md, ctx->stream, 1, 3, 1)) != TERSOFF_OK) return fail(rc);
   if (launch_force_done(ctx->stream, md->rs) != cudaSuccess) return fail(set_err(ctx, TERSOFF_ERR_CUDA, "force_done"));
   RunState h;
   if ((rc = read_rs(ctx, md->rs, &h)) != TERSOFF_OK) return fail(rc);
@@ -1006,6 +1010,35 @@ int tersoff_md_create(tersoff_ctx *ctx, const double *pos, const double *vel, co
   // register kernel with 4 slots when no atom has more than 4 in-cutoff neighbours
   // (diamond-like solids), else 8; atoms beyond that go to the general kernel
   if (md->fast_slots > 0 && h.maxnc <= 4) md->fast_slots = 4;
+  // several types with different neighbour counts (C atoms in SiC have 4, Si atoms up
+  // to 8): one register-kernel launch per slot count over the atoms of those types, so
+  // that the atoms of a warp share their loop trip counts
+  if (md->fast_slots > 0 && P->nt > 1) {
+    int slots_t[MAX_TYPES];
+    bool differ = false;
+    for (int t = 0; t < P->nt; ++t) {
+      slots_t[t] = h.maxnc_t[t] <= 4 ? 4 : 8;
+      differ = differ || slots_t[t] != slots_t[0];
+    }
+    if (differ) {
+      std::vector<int4> hq((size_t)N);
+      if (cudaMemcpy(hq.data(), md->atoms.q, sizeof(int4) * N, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(set_err(ctx, TERSOFF_ERR_CUDA, "types for routing"));
+      std::vector<int> order;
+      order.reserve((size_t)N);
+      for (int pass = 4; pass <= 8; pass += 4)
+        for (int64_t i = 0; i < N; ++i)
+          if (slots_t[type_of(hq[i].w)] == pass) order.push_back((int)i);
+      const int n4 = (int)std::count_if(hq.begin(), hq.end(), [&](const int4 &a) { return slots_t[type_of(a.w)] == 4; });
+      if (cudaMalloc((void **)&md->d_order, sizeof(int) * N) != cudaSuccess ||
+          cudaMemcpy(md->d_order, order.data(), sizeof(int) * N, cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(set_err(ctx, TERSOFF_ERR_NOMEM, "routing order"));
+      md->routes.n = 2;
+      md->routes.r[0] = ForceRoute{md->d_order, 0, n4, 4, 0};
+      md->routes.r[1] = ForceRoute{md->d_order, n4, (int)N - n4, 8, 0};
+      md->routed = true;
+    }
+  }
   // the general kernel needs slots for in-cutoff neighbours only (not the whole
   // list): size it from the largest count seen plus headroom; a later overflow
   // widens it (recovery in md_finish)
@@ -1175,6 +1208,7 @@ void tersoff_md_destroy(tersoff_md *md)
   free_list(md->list);
   dfree(md->rs);
   dfree(md->d_trace);
+  dfree(md->d_order);
   ctx_release(md->ctx);
   delete md;
 }

@@ -70,7 +70,9 @@ cudaError_t launch_force(cudaStream_t, bool, int, bool, int, int, int, int, cons
                          unsigned long long *, int *, int *, double *, RunState *, double *);
 cudaError_t launch_force_part(int, cudaStream_t, bool, int, bool, int, int, int, int, const dbl4 *, const int4 *,
                               const int *, const int *, const SysTab *, const void *, const void *, int, void *, void *,
-                              unsigned long long *, int *, int *, double *, RunState *, double *);
+                              unsigned long long *, int *, int *, double *, RunState *, double *,
+                              const ForceRoutes *routes = nullptr, int stats = 1);
+int force_queue_blocks(int N);
 cudaError_t launch_vv(cudaStream_t, bool, bool, int, int, dbl4 *, dbl4 *, int4 *, const int4 *, const void *,
                       const void *, const unsigned long long *, const int *, const SysTab *, SysCtl *,
                       const double *, float, double *, RunState *);

@@ -296,9 +296,10 @@ int srv_force(tersoff_server *s, cudaStream_t st)
 {
   const tersoff_params *P = s->P;
   AtomState &X = cur_atoms(s);
-  SK(launch_force(st, s->mixed, s->fast_slots, P->nt == 1, s->gen_slots, 0, 0, (int)s->natoms, X.x, X.q, s->L.nbr,
-                  s->L.cnt, s->S.tab, s->mixed ? P->pair_f : P->pair_d, s->mixed ? P->trip_f : P->trip_d, P->nt,
-                  s->SC.contrib, s->SC.selfF, s->SC.mask, s->SC.work, s->SC.nwork, s->SC.partial, s->rs, s->eatom));
+  SK(launch_force_part(3, st, s->mixed, s->fast_slots, P->nt == 1, s->gen_slots, 0, 0, (int)s->natoms, X.x, X.q,
+                       s->L.nbr, s->L.cnt, s->S.tab, s->mixed ? P->pair_f : P->pair_d,
+                       s->mixed ? P->trip_f : P->trip_d, P->nt, s->SC.contrib, s->SC.selfF, s->SC.mask, s->SC.work,
+                       s->SC.nwork, s->SC.partial, s->rs, s->eatom, nullptr, 0));
   return TERSOFF_OK;
 }
 

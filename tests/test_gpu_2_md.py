@@ -179,3 +179,23 @@ def test_list_grows_during_run(T, ctx):
     Eo, Fo, _ = oracle.energy_forces(p, s.types, s.box, tab)
     assert_parity(tr[-1, 0], f, None, Eo, Fo, None, FP64_E_REL, FP64_F_ABS, 0, "melt")
     assert md.stats()["stride"] >= stride0
+
+
+@pytest.mark.parametrize("prec_name", ["FP64", "MIXED"])
+def test_sic_md_matches_oracle(T, ctx, prec_name):
+    """Two atom types whose neighbour counts differ (C: 4, Si: up to 8): the register
+    force kernel runs as one launch per slot count over the atoms of those types."""
+    prec = getattr(T, prec_name)
+    s = wl.sic_box(4, seed=23, T=1500.0)
+    P = product_params(ctx, s.species)
+    tab, m = oracle_table(s.species)
+    n = 12
+    md = T.MD(ctx, P, s.pos, s.vel, s.types, s.box, dt=0.5e-3, skin=0.3, prec=prec)
+    tr = md.step(n, trace=True)
+    p, v = md.get()
+    po, vo, tro = oracle.md_run(s.pos, s.vel, s.types, s.box, tab, m, 0.5e-3, n)
+    tol = 1e-9 if prec == T.FP64 else 1e-7
+    assert np.abs(p - po).max() < 50 * tol
+    assert np.abs(v - vo).max() < 20 * 50 * tol
+    e_rel = 1e-9 if prec == T.FP64 else MIX_E_REL
+    assert np.allclose(tr[:, 0], tro[:, 0], rtol=e_rel)
