@@ -307,9 +307,9 @@ def run_gpu(args, ws, rank, local):
 
     traffic = force_traffic()
 
-    # kernels per timed step on the graph path: set_control + loop_begin per launch,
-    # then integrator, decide, force (register + overflow), step_end; 8 more on rebuilds
-    launches = len(fl_mix) * (2 + 5) + 8 * st_mix["rebuilds_flushed"]
+    # kernels per timed step on the graph path: loop_start per launch, then integrator,
+    # decide, force (register + overflow), step_end; 9 more on rebuilds
+    launches = len(fl_mix) * (1 + 5) + 9 * st_mix["rebuilds_flushed"]
     line = {
         "metric": METRIC,
         "value": value,

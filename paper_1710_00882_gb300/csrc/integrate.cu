@@ -310,10 +310,26 @@ __global__ void k_step_end(RunState *rs, SysCtl *ctl, int nsys, cudaGraphConditi
   if (use_cond) cudaGraphSetConditional(loop, rs->steps_left > 0 ? 1u : 0u);
 }
 
-// before the step loop of a graph launch
-__global__ void k_loop_begin(RunState *rs, cudaGraphConditionalHandle loop)
+// First node of a step-loop graph: the launch's controls (as k_set_control, system
+// 0 when ctl is non-null) and the loop's first condition.  The host sets its
+// parameters before each launch.
+__global__ void k_loop_start(RunState *rs, SysCtl *ctl, long long steps, double *trace, long long trace_k, int open,
+                             cudaGraphConditionalHandle loop)
 {
-  cudaGraphSetConditional(loop, (rs->status == 0 && rs->steps_left > 0) ? 1u : 0u);
+  if (rs->status != 0) {
+    rs->steps_left += steps;
+    if (ctl) ctl[0].steps_left += steps;
+    cudaGraphSetConditional(loop, 0u);
+    return;
+  }
+  rs->steps_left = steps;
+  if (ctl) {
+    ctl[0].steps_left = steps;
+    ctl[0].open = open;
+  }
+  rs->trace = trace;
+  rs->trace_k = trace_k;
+  cudaGraphSetConditional(loop, steps > 0 ? 1u : 0u);
 }
 
 // after the integrator of a step: rebuild the list in this step?
@@ -431,10 +447,26 @@ cudaError_t launch_step_end(cudaStream_t st, RunState *rs, SysCtl *ctl, int nsys
   return cudaGetLastError();
 }
 
-cudaError_t launch_loop_begin(cudaStream_t st, RunState *rs, cudaGraphConditionalHandle loop)
+cudaError_t launch_loop_start(cudaStream_t st, RunState *rs, SysCtl *ctl, long long steps, double *trace,
+                              long long trace_k, int open, cudaGraphConditionalHandle loop)
 {
-  k_loop_begin<<<1, 1, 0, st>>>(rs, loop);
+  k_loop_start<<<1, 1, 0, st>>>(rs, ctl, steps, trace, trace_k, open, loop);
   return cudaGetLastError();
+}
+
+// New parameters of a captured k_loop_start node in an instantiated graph.
+cudaError_t set_loop_start(cudaGraphExec_t exec, cudaGraphNode_t node, RunState *rs, SysCtl *ctl, long long steps,
+                           double *trace, long long trace_k, int open, cudaGraphConditionalHandle loop)
+{
+  void *args[] = {&rs, &ctl, &steps, &trace, &trace_k, &open, &loop};
+  cudaKernelNodeParams p = {};
+  p.func = (void *)k_loop_start;
+  p.gridDim = dim3(1, 1, 1);
+  p.blockDim = dim3(1, 1, 1);
+  p.sharedMemBytes = 0;
+  p.kernelParams = args;
+  p.extra = nullptr;
+  return cudaGraphExecKernelNodeSetParams(exec, node, &p);
 }
 
 cudaError_t launch_decide(cudaStream_t st, RunState *rs, cudaGraphConditionalHandle build)

@@ -99,6 +99,8 @@ struct tersoff_nlist {
 struct MdGraph {
   cudaGraph_t g = nullptr;
   cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t start = nullptr;       // k_loop_start node (parameters set per launch)
+  cudaGraphConditionalHandle hloop = 0;
   bool valid = false;
 };
 
@@ -789,7 +791,9 @@ static void md_graphs_free(tersoff_md *md)
 }
 
 // Graph of the step loop (which = 1: with energy trace):
-//   loop_begin -> WHILE(steps_left > 0) { vv -> decide -> IF(rebuild) { list build } -> force -> step_end }
+//   loop_start -> WHILE(steps_left > 0) { vv -> decide -> IF(rebuild) { list build } -> force -> step_end }
+// loop_start takes the launch controls (steps, trace rows, open half kick), set per
+// launch in the instantiated graph, and sets the first loop condition.
 // step_end decrements steps_left and sets the loop condition, so one launch runs any
 // number of steps, and a step without a rebuild launches no build kernel.
 static int md_graph_build(tersoff_md *md, int which)
@@ -805,12 +809,15 @@ static int md_graph_build(tersoff_md *md, int which)
   cudaGraphConditionalHandle hloop, hbuild;
   CK(cudaGraphConditionalHandleCreate(&hloop, g, 0, cudaGraphCondAssignDefault));
   CK(cudaStreamBeginCaptureToGraph(st, g, nullptr, nullptr, 0, mode));
-  CK(launch_loop_begin(st, md->rs, hloop));
+  CK(launch_loop_start(st, md->rs, md->sys.ctl, 0, nullptr, 1, 0, hloop));
   cudaStreamCaptureStatus cs;
   const cudaGraphNode_t *deps = nullptr;
   const cudaGraphEdgeData *edges = nullptr;
   size_t nd = 0;
   CK(cudaStreamGetCaptureInfo(st, &cs, nullptr, nullptr, &deps, &edges, &nd));
+  if (nd != 1) return set_err(ctx, TERSOFF_ERR_CUDA, "unexpected graph capture state");
+  G.start = deps[0];
+  G.hloop = hloop;
   cudaGraphNodeParams wp = {};
   wp.type = cudaGraphNodeTypeConditional;
   wp.conditional.handle = hloop;
@@ -859,7 +866,6 @@ static int md_launch_steps(tersoff_md *md, long long n, double *d_trace, long lo
   cudaStream_t st = ctx->stream;
   if (n <= 0) return TERSOFF_OK;
   const bool tr = d_trace != nullptr;
-  CK(launch_set_control(st, md->rs, md->sys.ctl, n, d_trace, k0, md->open ? 1 : 0));
   if (!md->prof && md->use_graphs) {
     MdGraph &G = md->graph[tr ? 1 : 0];
     if (!G.valid) {
@@ -872,12 +878,15 @@ static int md_launch_steps(tersoff_md *md, long long n, double *d_trace, long lo
       }
     }
     if (md->use_graphs) {
+      // the launch's controls go into the graph's first node
+      CK(set_loop_start(G.exec, G.start, md->rs, md->sys.ctl, n, d_trace, k0, md->open ? 1 : 0, G.hloop));
       CK(cudaGraphLaunch(G.exec, st));
       md->launches[0] += n;
       md->open = true;
       return TERSOFF_OK;
     }
   }
+  CK(launch_set_control(st, md->rs, md->sys.ctl, n, d_trace, k0, md->open ? 1 : 0));
   for (long long k = 0; k < n; ++k) {
     size_t b = md_mark_begin(md);
     CKR(md_vv(md, st, -1, tr));

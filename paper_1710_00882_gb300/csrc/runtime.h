@@ -83,7 +83,10 @@ cudaError_t launch_ingest(cudaStream_t, int, const double *, const int *, int, i
 cudaError_t launch_ingest_vel(cudaStream_t, int, const double *, dbl4 *);
 cudaError_t launch_extract(cudaStream_t, int, const dbl4 *, const dbl4 *, double *, double *);
 cudaError_t launch_step_end(cudaStream_t, RunState *, SysCtl *, int, cudaGraphConditionalHandle, int);
-cudaError_t launch_loop_begin(cudaStream_t, RunState *, cudaGraphConditionalHandle);
+cudaError_t launch_loop_start(cudaStream_t, RunState *, SysCtl *, long long, double *, long long, int,
+                              cudaGraphConditionalHandle);
+cudaError_t set_loop_start(cudaGraphExec_t, cudaGraphNode_t, RunState *, SysCtl *, long long, double *, long long, int,
+                           cudaGraphConditionalHandle);
 cudaError_t launch_decide(cudaStream_t, RunState *, cudaGraphConditionalHandle);
 cudaError_t launch_set_control(cudaStream_t, RunState *, SysCtl *, long long, double *, long long, int);
 cudaError_t launch_final(cudaStream_t, RunState *, SysCtl *);

@@ -218,6 +218,8 @@ struct tersoff_server {
   cudaGraph_t g = nullptr;
   cudaGraphExec_t exec = nullptr;
   bool graph_ok = false;
+  cudaGraphNode_t start_node = nullptr;   // k_loop_start node (steps set per launch)
+  cudaGraphConditionalHandle hloop = 0;
   bool use_graphs = true;   // TERSOFF_GRAPHS=0: chunks kernel by kernel (profiling)
   bool broken = false;
   std::mutex mu;
@@ -332,7 +334,7 @@ void graph_free(tersoff_server *s)
   s->graph_ok = false;
 }
 
-// loop_begin -> WHILE { vv -> decide -> IF(rebuild) { build } -> force -> step_end }
+// loop_start (launch controls, first condition) -> WHILE { vv -> decide -> IF(rebuild) { build } -> force -> step_end }
 int graph_build(tersoff_server *s)
 {
   graph_free(s);
@@ -344,12 +346,15 @@ int graph_build(tersoff_server *s)
   cudaGraphConditionalHandle hloop, hbuild;
   SK(cudaGraphConditionalHandleCreate(&hloop, g, 0, cudaGraphCondAssignDefault));
   SK(cudaStreamBeginCaptureToGraph(st, g, nullptr, nullptr, 0, mode));
-  SK(launch_loop_begin(st, s->rs, hloop));
+  SK(launch_loop_start(st, s->rs, nullptr, 0, nullptr, 1, 0, hloop));
   cudaStreamCaptureStatus cs;
   const cudaGraphNode_t *deps = nullptr;
   const cudaGraphEdgeData *edges = nullptr;
   size_t nd = 0;
   SK(cudaStreamGetCaptureInfo(st, &cs, nullptr, nullptr, &deps, &edges, &nd));
+  if (nd != 1) return srv_err(s, TERSOFF_ERR_CUDA, "unexpected graph capture state");
+  s->start_node = deps[0];
+  s->hloop = hloop;
   cudaGraphNodeParams wp = {};
   wp.type = cudaGraphNodeTypeConditional;
   wp.conditional.handle = hloop;
@@ -512,17 +517,18 @@ int repack(tersoff_server *s, const std::vector<Job *> &order, const std::vector
 // n steps: one graph launch, or kernel by kernel without graphs
 int launch_steps(tersoff_server *s, long long n)
 {
-  k_set_loop<<<1, 1, 0, s->st>>>(s->rs, n);
-  SK(cudaGetLastError());
   if (s->use_graphs) {
     if (!s->graph_ok) {
       const double t0 = now_s();
       SKR(graph_build(s));
       s->w_graph += now_s() - t0;
     }
+    SK(set_loop_start(s->exec, s->start_node, s->rs, nullptr, n, nullptr, 1, 0, s->hloop));
     SK(cudaGraphLaunch(s->exec, s->st));
     return TERSOFF_OK;
   }
+  k_set_loop<<<1, 1, 0, s->st>>>(s->rs, n);
+  SK(cudaGetLastError());
   for (long long k = 0; k < n; ++k) {
     SKR(srv_vv(s, s->st));
     AtomState &X = cur_atoms(s);
