@@ -193,14 +193,21 @@ __device__ __forceinline__ void sort_column(int *__restrict__ nbr, int N, int i,
     if (s < n) nbr[(size_t)s * N + i] = v[s];
 }
 
-// Append pair (i, j) to both lists (slot from an atomic count; order fixed later by
-// the sort).
-__device__ __forceinline__ void add_pair(int i, int j, int N, int cap, int *__restrict__ nbr, int *__restrict__ cnt)
+// List counts during a build: the low 16 bits count the entries an atom found itself
+// ("forward", written from slot 0 up by its own thread), the high 16 bits the entries
+// other atoms appended to it ("backward", written from slot cap - 1 down, slot from
+// an atomic count).  The two ranges meet only when the list overflows.
+constexpr int BACK = 1 << 16;
+
+// Append the pair (i, j) found by i: j goes to i's forward range (no atomic), i to
+// j's backward range.
+__device__ __forceinline__ void add_pair(int i, int j, int N, int cap, int *__restrict__ nbr, int *__restrict__ cnt,
+                                         int &nf)
 {
-  const int si = atomicAdd(&cnt[i], 1);
-  if (si < cap) nbr[(size_t)si * N + i] = j;
-  const int sj = atomicAdd(&cnt[j], 1);
-  if (sj < cap) nbr[(size_t)sj * N + j] = i;
+  if (nf < cap) nbr[(size_t)nf * N + i] = j;
+  ++nf;
+  const int b = atomicAdd(&cnt[j], BACK) >> 16;
+  if (b < cap) nbr[(size_t)(cap - 1 - b) * N + j] = i;
 }
 
 // One thread per atom, atoms taken in cell order (threads of a warp share most of
@@ -233,6 +240,7 @@ __global__ void __launch_bounds__(128) k_build(int N, const int4 *__restrict__ q
   const int cx = cell_coord((uint32_t)pi.x, nc0), cy = cell_coord((uint32_t)pi.y, nc1),
             cz = cell_coord((uint32_t)pi.z, nc2);
   const bool half = nc0 >= 3 && nc1 >= 3 && nc2 >= 3;
+  int nf = 0;   // entries this thread found for i
 
   // scan candidates [b, e) of cell_atoms (four per round: their loads go together)
   auto scan = [&](int b, int e) {
@@ -247,7 +255,7 @@ __global__ void __launch_bounds__(128) k_build(int N, const int4 *__restrict__ q
         const float dy = q_scaled(qdiff(pj[k].y, pi.y), s1);
         const float dz = q_scaled(qdiff(pj[k].z, pi.z), s2);
         const float r2 = r2_decide(dx, dy, dz);
-        if (j > i && r2 < rl2) add_pair(i, j, N, cap, nbr, cnt);
+        if (j > i && r2 < rl2) add_pair(i, j, N, cap, nbr, cnt, nf);
       }
     }
   };
@@ -285,7 +293,7 @@ __global__ void __launch_bounds__(128) k_build(int N, const int4 *__restrict__ q
           const float dy = q_scaled(qdiff(pj[k].y, pi.y), s1);
           const float dz = q_scaled(qdiff(pj[k].z, pi.z), s2);
           const float r2 = r2_decide(dx, dy, dz);
-          if (j >= 0 && r2 < rl2) add_pair(i, j, N, cap, nbr, cnt);
+          if (j >= 0 && r2 < rl2) add_pair(i, j, N, cap, nbr, cnt, nf);
         }
       }
     };
@@ -313,12 +321,13 @@ __global__ void __launch_bounds__(128) k_build(int N, const int4 *__restrict__ q
     for (int oz = 0; oz < nz; ++oz)
       for (int oy = 0; oy < ny; ++oy) scan_row(y0 + oy, z0 + oz, x0, nx);
   }
+  atomicAdd(&cnt[i], min(nf, BACK - 1));
 }
 
 // Sort each rebuilt list by neighbour index, so that the list order depends only on
 // the set of neighbours; flag lists longer than the capacity.
 __global__ void __launch_bounds__(128) k_sort_lists(int N, const int4 *__restrict__ q, const SysCtl *__restrict__ ctl,
-                                                    int *__restrict__ nbr, const int *__restrict__ cnt, int cap,
+                                                    int *__restrict__ nbr, int *__restrict__ cnt, int cap,
                                                     RunState *rs, int gated)
 {
   __shared__ int sbuf[32][128];
@@ -326,20 +335,38 @@ __global__ void __launch_bounds__(128) k_sort_lists(int N, const int4 *__restric
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   if (ctl && ctl[sys_of(q[i].w)].rebuild == 0) return;
-  int n = cnt[i];
+  const int c = cnt[i];
+  const int nf = c & (BACK - 1), nb = c >> 16, n = nf + nb;
   atomicMax(&rs->maxcount, n);
   if (n > cap) {
     atomicOr(&rs->status, ST_NLIST_OVERFLOW);
     return;
   }
-  if (n <= 8) {
-    sort_column<8>(nbr, N, i, n);
-  } else if (n <= 16) {
-    sort_column<16>(nbr, N, i, n);
+  cnt[i] = n;
+  // entry s of the list: forward entries first, then the backward ones
+  auto entry = [&](int s) -> size_t { return (size_t)(s < nf ? s : cap - nb + (s - nf)) * N + i; };
+  if (n <= 16) {
+    int v[16];
+#pragma unroll
+    for (int s = 0; s < 16; ++s) v[s] = s < n ? nbr[entry(s)] : 0x7fffffff;
+    if (n <= 8) {
+      int w[8];
+#pragma unroll
+      for (int s = 0; s < 8; ++s) w[s] = v[s];
+      bitonic<8, 2, 1>(w);
+#pragma unroll
+      for (int s = 0; s < 8; ++s)
+        if (s < n) nbr[(size_t)s * N + i] = w[s];
+    } else {
+      bitonic<16, 2, 1>(v);
+#pragma unroll
+      for (int s = 0; s < 16; ++s)
+        if (s < n) nbr[(size_t)s * N + i] = v[s];
+    }
   } else if (n <= 32) {
     // insertion sort in this thread's shared-memory column (stride 128: no bank conflicts)
     for (int s1 = 0; s1 < n; ++s1) {
-      const int v = nbr[(size_t)s1 * N + i];
+      const int v = nbr[entry(s1)];
       int k = s1 - 1;
       while (k >= 0 && sbuf[k][threadIdx.x] > v) {
         sbuf[k + 1][threadIdx.x] = sbuf[k][threadIdx.x];
@@ -349,6 +376,9 @@ __global__ void __launch_bounds__(128) k_sort_lists(int N, const int4 *__restric
     }
     for (int s1 = 0; s1 < n; ++s1) nbr[(size_t)s1 * N + i] = sbuf[s1][threadIdx.x];
   } else {
+    // move the backward entries down behind the forward ones (cap - nb >= nf), then
+    // insertion sort in place
+    for (int k = 0; k < nb; ++k) nbr[(size_t)(nf + k) * N + i] = nbr[(size_t)(cap - nb + k) * N + i];
     for (int s1 = 1; s1 < n; ++s1) {
       const int v = nbr[(size_t)s1 * N + i];
       int k = s1 - 1;
