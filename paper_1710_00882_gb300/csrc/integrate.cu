@@ -157,6 +157,7 @@ __global__ void k_gather_out(int N, const typename V4g<R>::type *__restrict__ co
 }
 
 enum { VV_FINISH = 1, VV_START = 2 };
+constexpr int VV_THREADS = 128;   // integrator block size (more resident blocks per SM than 256)
 
 // Velocity Verlet around the force evaluation, float64.
 //   FINISH: v += dt/2 F/m          (second half kick of the previous step)
@@ -380,7 +381,7 @@ cudaError_t launch_vv(cudaStream_t st, bool mixed, bool ke, int N, int mode, dbl
                       double *kepart, RunState *rs)
 {
   if (N == 0) return cudaSuccess;
-  const int T = 256, B = (N + T - 1) / T;
+  const int T = VV_THREADS, B = (N + T - 1) / T;
   if (mixed) {
     if (ke)
       k_vv<float, true><<<B, T, 0, st>>>(N, mode, x, v, q, qref, (const float4 *)contrib, (const float4 *)selfF,
@@ -400,7 +401,7 @@ cudaError_t launch_vv(cudaStream_t st, bool mixed, bool ke, int N, int mode, dbl
   return cudaGetLastError();
 }
 
-int vv_blocks(int N) { return (N + 255) / 256; }
+int vv_blocks(int N) { return (N + VV_THREADS - 1) / VV_THREADS; }
 
 cudaError_t launch_gather_out(cudaStream_t st, bool mixed, int N, const void *contrib, const void *selfF,
                               const unsigned long long *mask, const int *rev, double *out, RunState *rs)
