@@ -199,3 +199,26 @@ def test_sic_md_matches_oracle(T, ctx, prec_name):
     assert np.abs(v - vo).max() < 20 * 50 * tol
     e_rel = 1e-9 if prec == T.FP64 else MIX_E_REL
     assert np.allclose(tr[:, 0], tro[:, 0], rtol=e_rel)
+
+
+def test_profiled_steps_equal_graph_steps(T, ctx):
+    """Kernel-by-kernel stepping with per-phase events (the profiled path) gives the
+    same trajectory as the graph path, and reports time in every phase it launched."""
+    s = wl.si_box(6, 6, 6, seed=29, T=1000.0)
+    P = product_params(ctx, s.species)
+    a = T.MD(ctx, P, s.pos, s.vel, s.types, s.box, dt=1e-3, skin=0.3, prec=T.MIXED)
+    b = T.MD(ctx, P, s.pos, s.vel, s.types, s.box, dt=1e-3, skin=0.3, prec=T.MIXED)
+    a.step(12)
+    b.profile(True)
+    b.step(12)
+    ms, n = b.profile_read()
+    b.profile(False)
+    pa, va = a.get()
+    pb, vb = b.get()
+    assert np.array_equal(pa, pb) and np.array_equal(va, vb)
+    assert ms.shape == (5,) and n.shape == (5,)
+    # integrator, list build (launched every step), register force kernel, overflow
+    # force kernel, bookkeeping
+    assert (n[[0, 1, 2, 3, 4]] > 0).all()
+    assert (ms[[0, 2, 4]] > 0).all()
+    assert a.stats()["steps"] == b.stats()["steps"] == 12
