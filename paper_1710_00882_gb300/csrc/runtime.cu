@@ -896,7 +896,7 @@ static int md_launch_steps(tersoff_md *md, long long n, double *d_trace, long lo
     md_mark_end(md, 1, b, 8);
     b = md_mark_begin(md);
     CKR(md_force(md, st, tr ? 1 : 0, 1));
-    md_mark_end(md, 2, b, md->fast_slots > 0 ? 1 : 0);
+    md_mark_end(md, 2, b, md->fast_slots > 0 ? (md->routed ? md->routes.n : 1) : 0);
     b = md_mark_begin(md);
     CKR(md_force(md, st, tr ? 1 : 0, 2));
     md_mark_end(md, 3, b, 1 + (tr ? 1 : 0));
