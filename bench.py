@@ -36,7 +36,7 @@ WORKLOAD = "Si diamond 40x40x40 = 512,000 atoms, sigma 0.05 A, 1000 K, Si(C), sk
 SKIN = 0.3
 DT = 1e-3
 
-# Float32 operations of the mixed-precision force kernel as written in force.cu
+# Float32 operations of the mixed-precision force kernel as written in force_kernels.cuh
 # (FMA = 2, add/sub/mul = 1, each rcp/rsqrt/lg2/ex2/sin/cos = 1; integer, load and
 # compare work not counted):
 #   per Verlet-list entry tested (fixed-point difference scaled, r^2):          8
@@ -51,6 +51,10 @@ C_ENTRY = 8
 C_PAIR = 148
 C_TAPER = 10
 C_TRIPLET = 40
+# Single mode forms the pair geometry without compensation: relative vector (3),
+# r^2 (5), rsqrt and r (2), and f_R, f_A from one ex2 each (8) in place of the
+# mixed kernel's 30 + 41 + 38; the rest is the same:                            57
+C_PAIR_SINGLE = 57
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x 2 x max SM clock
 FP64_PEAK_TFLOPS = 1.25                              # GB300 nominal FP64
 
@@ -104,7 +108,7 @@ def force_traffic():
     if not (m_t and m_h):
         return None
     h = hashlib.sha256()
-    for f in ("force.cu", "internal.cuh"):
+    for f in ("force_kernels.cuh", "force_mixed.cu", "internal.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1710_00882_gb300", "csrc", f), "rb").read())
     return int(m_t.group(1)) if h.hexdigest()[:16] == m_h.group(1) else None
 
@@ -250,7 +254,8 @@ def run_gpu(args, ws, rank, local):
     k_mix, k_64 = args.steps, max(3, args.steps // 4)
     one_mix, fl_mix, prof_mix, st_mix, md_mix = timed(T.MIXED, k_mix, args.warmup)
     one_64, fl_64, prof_64, st_64, md_64 = timed(T.FP64, k_64, args.warmup)
-    md_mix = md_64 = None
+    one_sg, fl_sg, prof_sg, st_sg, md_sg = timed(T.SINGLE, k_mix, args.warmup)
+    md_mix = md_64 = md_sg = None
     # 3C-SiC 50^3 cells with 5% vacancies (950,000 atoms), mixed, dt 0.5 fs
     sic = None
     if not args.no_sic:
@@ -276,9 +281,11 @@ def run_gpu(args, ws, rank, local):
     # headline: one launch per step with L2 flushed before each step
     tot_mix = allreduce_max(ws, sum(fl_mix))
     tot_64 = allreduce_max(ws, sum(fl_64))
+    tot_sg = allreduce_max(ws, sum(fl_sg))
     one_mix = allreduce_max(ws, one_mix)
     value = ws * s.n * len(fl_mix) / (tot_mix / 1e3)
     value64 = ws * s.n * len(fl_64) / (tot_64 / 1e3)
+    value_sg = ws * s.n * len(fl_sg) / (tot_sg / 1e3)
 
     # roofline of the dominant kernel (the force kernel), achieved from algorithmic flops
     flops = C_ENTRY * n_list + C_PAIR * npair + C_TAPER * ntaper + C_TRIPLET * ntrip
@@ -286,8 +293,11 @@ def run_gpu(args, ws, rank, local):
     # the register force kernel alone (one launch per step; events around it)
     f_ms = prof_mix[0][2] / prof_mix[1][2]
     f64_ms = prof_64[0][2] / prof_64[1][2]
+    fsg_ms = prof_sg[0][2] / prof_sg[1][2]
     achieved = flops / (f_ms / 1e3) / 1e12
     achieved64 = flops / (f64_ms / 1e3) / 1e12
+    flops_sg = C_ENTRY * n_list + C_PAIR_SINGLE * npair + C_TAPER * ntaper + C_TRIPLET * ntrip
+    achieved_sg = flops_sg / (fsg_ms / 1e3) / 1e12
 
     # end to end through the C ABI with host buffers: one tersoff_md_run call of 100 steps
     e2e = None
@@ -336,6 +346,14 @@ def run_gpu(args, ws, rank, local):
                  "mixed_over_fp64": value / value64,
                  "force_kernel_ms": f64_ms, "force_kernel_achieved_tflops": achieved64,
                  "peak_tflops": FP64_PEAK_TFLOPS, "frac_of_fp64_peak": achieved64 / FP64_PEAK_TFLOPS},
+        "single": {"value": value_sg, "unit": "atom-steps/s", "steps": len(fl_sg),
+                   "ms_per_step": tot_sg / len(fl_sg), "single_over_mixed": value_sg / value,
+                   "force_kernel_ms": fsg_ms, "force_kernel_achieved_tflops": achieved_sg,
+                   "frac_of_fp32_peak": achieved_sg / FP32_PEAK_TFLOPS, "algorithmic_flops_per_launch": flops_sg,
+                   "flops_per_unit": {"list_entry": C_ENTRY, "pair": C_PAIR_SINGLE, "taper_pair": C_TAPER,
+                                      "ordered_triplet": C_TRIPLET},
+                   "what": "float32 throughout the force evaluation (the paper's single mode), float64 "
+                           "integration; same workload and timing as the headline"},
         "phases_ms_per_step_profiled": {k: prof_mix[0][n] / st_mix["prof_steps"] for n, k in
                                         enumerate(("integrator", "list_build", "force_register_kernel",
                                                    "force_overflow_and_reduce", "bookkeeping"))},
@@ -350,7 +368,8 @@ def run_gpu(args, ws, rank, local):
                      "flops_per_unit": {"list_entry": C_ENTRY, "pair": C_PAIR, "taper_pair": C_TAPER,
                                         "ordered_triplet": C_TRIPLET}},
         "gpu_launches": launches,
-        "rebuilds_in_timed_steps": {"mixed": st_mix["rebuilds_flushed"], "fp64": st_64["rebuilds_flushed"]},
+        "rebuilds_in_timed_steps": {"mixed": st_mix["rebuilds_flushed"], "fp64": st_64["rebuilds_flushed"],
+                                    "single": st_sg["rebuilds_flushed"]},
         "clocks": clk,
     }
     if e2e:

@@ -62,15 +62,21 @@ extern "C" {
 #define TERSOFF_ERR_BUSY (-8)             /* server: no slot free and queue full */
 #define TERSOFF_ERR_NOT_FOUND (-9)        /* server: unknown job id */
 
-/* precision of the force evaluation (Sec. 4 of the paper names single, double
- * and mixed modes; it does not define "mixed").  TERSOFF_FP64: all arithmetic
- * in float64.  TERSOFF_MIXED: relative vectors formed exactly from 32-bit
- * fixed-point positions and rounded once to float32; f_C, g, exp, pow and all
- * per-term arithmetic in float32; each atom's contribution to a neighbour's
- * force (a float32 sum of at most 2 n_c terms) is added into float64 per-atom
- * force accumulators; energy and virial are summed over atoms in float64;
- * integration is float64. */
-typedef enum { TERSOFF_FP64 = 0, TERSOFF_MIXED = 1 } tersoff_precision;
+/* precision of the force evaluation (Sec. 4 of the paper compares single, double
+ * and mixed modes; it does not define "mixed").  Integration is float64 in all
+ * three.
+ * TERSOFF_FP64: all arithmetic in float64.
+ * TERSOFF_MIXED: relative vectors formed exactly from 32-bit fixed-point
+ *   positions and converted to float32 as head + tail; r and lambda*r kept to
+ *   ~1 ulp; f_C, g, exp, pow and all per-term arithmetic in float32; the float32
+ *   force contributions on each atom summed with compensation (TwoSum), so the sum
+ *   has float64 accuracy; energy and virial summed over atoms in float64.
+ * TERSOFF_SINGLE: the paper's single mode: float32 throughout the evaluation:
+ *   relative vectors rounded once to float32, r from a float32 rsqrt, exp from one
+ *   float32 exp2, float32 force sums per atom and float32 energy/virial sums per
+ *   block of 128 atoms (only the sum over blocks is float64).  Cheapest, and
+ *   the least accurate: see the tolerances the tests state. */
+typedef enum { TERSOFF_FP64 = 0, TERSOFF_MIXED = 1, TERSOFF_SINGLE = 2 } tersoff_precision;
 
 /* flags */
 #define TERSOFF_HOST_PTRS 0

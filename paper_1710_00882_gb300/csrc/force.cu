@@ -1,875 +1,9 @@
-// Tersoff energy/force kernels: Algorithm 1 of the paper, one thread per atom i.
-//
-// Per atom i the thread
-//   0. walks i's Verlet list once and marks the in-cutoff entries (Sec. 3: skin
-//      atoms are tested once and never enter the K loops);
-//   1. packs the in-cutoff neighbours into slots: unit vector, r, 1/r, f_C(r),
-//      f_C'(r), type, list slot;
-//   2. first K loop: zeta_ij for every slot j (Eq. 3); then the pair term
-//      V(i,j,zeta_ij) (Eqs. 1-2), its r-derivative and dV/dzeta;
-//   3. second K loop: the derivatives of zeta(i,j,k) scaled by dV/dzeta (the
-//      restructuring of Sec. 2: zeta is complete before any derivative is formed).
-//
-// Fast kernel (k_force_reg): slots live in registers (compile-time slot count 4
-// or 8, loops fully unrolled).  Both K loops run over unordered neighbour pairs
-// {j,k}: cos(theta), g and g' are shared by zeta(i,j,k) and zeta(i,k,j) whenever
-// the angular constants of rows (i,j,k) and (i,k,j) agree (Tersoff's tables take
-// them from atom i), so each is evaluated once per pair instead of twice.  Atoms
-// with more in-cutoff neighbours than slots are queued, per block and in order,
-// for the general kernel.
-//
-// General kernel (k_force_gen): slots in per-thread shared memory (8..64), loops
-// over ordered (j,k) as in Algorithm 1; handles any table and any neighbour count.
-//
-// Scatter: all force contributions of i's terms on neighbour j are summed per j in
-// the thread and written once, to slot s of i's list (contrib[s][i]); the force of
-// i's terms on i itself is minus their sum (translation invariance).  No atomics:
-// the gather (integrate.cu) reads, for each atom m and in-cutoff slot s of its list,
-// the contribution at the flat index rev[s][m] (m's slot in its neighbour's list)
-// and adds them in list order, so forces are bitwise reproducible.  Energy and virial go to per-block partial sums that a
-// single block reduces in a fixed order.
-//
-// Precision: R = double (FP64 mode) or float (mixed mode).  In mixed mode the
-// relative vector d_ij is formed from the exact int32 difference of 32-bit
-// fixed-point coordinates; the conversion to float splits the integer and the
-// scale so that d_ij is within ~1 ulp, and exp(-lambda r) forms lambda r with an
-// FMA-exact product, because the pair term's r-derivative is a difference of two
-// terms ~10x larger than itself.
+// Host-side dispatch of the Tersoff force evaluation (kernels in force_kernels.cuh,
+// one translation unit per precision) and the reduction of its energy/virial
+// partial sums.
 #include "internal.cuh"
 
 namespace tsf {
-
-template <class R> struct V4t;
-template <> struct V4t<float> { using type = float4; };
-template <> struct V4t<double> { using type = dbl4; };
-
-constexpr int FAST_THREADS = 128;
-constexpr float L2E_F = 1.44269502f;                   // log2(e) rounded to float
-constexpr float L2E_F_LO = 1.925963033500011e-08f;     // log2(e) - L2E_F
-
-// ---- math of the two precisions ------------------------------------------
-
-struct MathF {
-  using R = float;
-  static __device__ __forceinline__ float rcp(float x)
-  {
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-  }
-  static __device__ __forceinline__ float rsqrt(float x)
-  {
-    float y;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-  }
-  static __device__ __forceinline__ float lg2(float x)
-  {
-    float y;
-    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-  }
-  static __device__ __forceinline__ float ex2(float x)
-  {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-  }
-  // e^{-x} for x = xh + xl (|xl| << |xh|): e^{-x} = 2^{-x log2 e}; the product
-  // xh * log2(e) is split exactly with an FMA and the small remainder applied to
-  // first order, so the result carries the error of one ex2 only.
-  static __device__ __forceinline__ float expneg2(float xh, float xl)
-  {
-    // explicit round-to-nearest operations: a contracted product would break the split
-    const float yh = __fmul_rn(xh, L2E_F);
-    const float yl = __fadd_rn(__fmaf_rn(xh, L2E_F, -yh), __fmaf_rn(xh, L2E_F_LO, __fmul_rn(xl, L2E_F)));
-    return __fmul_rn(ex2(-yh), __fmaf_rn(-yl, 0.69314718f, 1.0f));
-  }
-  // e^{-(lh + ll)(rh + rl)}: lambda and r both given as float head + tail
-  static __device__ __forceinline__ float expneg(float lh, float ll, float rh, float rl)
-  {
-    const float p = __fmul_rn(lh, rh);
-    const float pe = __fadd_rn(__fmaf_rn(lh, rh, -p), __fmaf_rn(ll, rh, __fmul_rn(lh, rl)));
-    return expneg2(p, pe);
-  }
-  static __device__ __forceinline__ float expv(float x) { return expneg2(-x, 0.0f); }
-  static __device__ __forceinline__ void sincospi(float t, float *s, float *c) { sincospif(t, s, c); }
-};
-
-struct MathD {
-  using R = double;
-  static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
-  static __device__ __forceinline__ double rsqrt(double x) { return ::rsqrt(x); }
-  static __device__ __forceinline__ double lg2(double x) { return ::log2(x); }
-  static __device__ __forceinline__ double ex2(double x) { return ::exp2(x); }
-  static __device__ __forceinline__ double expneg(double lh, double, double r, double) { return ::exp(-lh * r); }
-  static __device__ __forceinline__ double expv(double x) { return ::exp(x); }
-  static __device__ __forceinline__ void sincospi(double t, double *s, double *c) { ::sincospi(t, s, c); }
-};
-
-template <class R> struct MathOf;
-template <> struct MathOf<float> { using M = MathF; };
-template <> struct MathOf<double> { using M = MathD; };
-
-// f_C and f_C' for r = rh + rl < R + D.  In the taper
-//   f_C = 1/2 - 1/2 sin(pi (r - R)/(2D)) = sin^2(pi w),  w = (R + D - r)/(4D),
-//   f_C' = -pi/(4D) cos(pi (r - R)/(2D)) = -pi/(4D) sin(2 pi w),
-// identities that avoid the cancellation of 1/2 - 1/2 sin near the outer cutoff,
-// where f_C is small and zeta, hence dV/dzeta, is most sensitive to it.  R + D - r
-// is formed from head+tail values so it keeps its relative accuracy there.
-template <class M, class R>
-__device__ __forceinline__ void cutoff_fn(R rh, R rl, const PairP<R> &P, R &fc, R &dfc)
-{
-  if (rh <= P.r_in) {
-    fc = R(1);
-    dfc = R(0);
-  } else {
-    const R w = ((P.r_out - rh) + (P.r_out_lo - rl)) * P.inv4D;
-    R s, c;
-    M::sincospi(w, &s, &c);
-    fc = s * s;
-    dfc = P.dfc_scale * R(2) * s * c;
-  }
-}
-
-// bond order b(zeta) (Eq. 2) and db/dzeta
-template <class M, class R>
-__device__ __forceinline__ void bond_order(R zeta, const PairP<R> &P, R &b, R &db)
-{
-  b = R(1);
-  db = R(0);
-  if (zeta > R(0)) {
-    const R xb = M::ex2(P.n * M::lg2(P.beta * zeta));
-    b = M::ex2(P.neg_inv2n * M::lg2(R(1) + xb));
-    db = R(-0.5) * b * xb * M::rcp((R(1) + xb) * zeta);
-  }
-}
-
-// minimum-image relative vector of a fixed-point pair, accurate to ~1 ulp:
-// the int32 difference is split into a 24-bit head and an 8-bit tail (both exact in
-// float) and the scale into float head + tail.
-// (Error-free transformations: every operation is an explicit round-to-nearest
-// intrinsic, which the compiler never contracts or reassociates.)
-__device__ __forceinline__ void qd_fine(int dq, float sh, float sl, float &dh, float &dl)
-{
-  const float h = (float)(dq & ~0xff);
-  const float l = (float)(dq & 0xff);
-  const float p = __fmul_rn(h, sh);
-  const float t = __fmaf_rn(h, sl, __fmaf_rn(l, sh, __fmaf_rn(h, sh, -p)));
-  dh = __fadd_rn(p, t);
-  dl = __fsub_rn(t, __fsub_rn(dh, p));   // |p| >= |t|: exact tail
-}
-
-// r = |d| as head + tail from d given as head + tail per component: squares split
-// exactly with FMAs, summed with TwoSum, square root refined by one Newton step.
-// Returns rh (the rounded distance), rl (its tail) and 1/rh.
-__device__ __forceinline__ void norm_fine(const float (&dh)[3], const float (&dl)[3], float &rh, float &rl,
-                                          float &irh)
-{
-  float sq[3], er[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    sq[a] = __fmul_rn(dh[a], dh[a]);
-    er[a] = __fmaf_rn(__fmul_rn(2.0f, dh[a]), dl[a], __fmaf_rn(dh[a], dh[a], -sq[a]));
-  }
-  const float s1 = __fadd_rn(sq[0], sq[1]);
-  const float bb1 = __fsub_rn(s1, sq[0]);
-  const float e1 = __fadd_rn(__fsub_rn(sq[0], __fsub_rn(s1, bb1)), __fsub_rn(sq[1], bb1));
-  const float s2 = __fadd_rn(s1, sq[2]);
-  const float bb2 = __fsub_rn(s2, s1);
-  const float e2 = __fadd_rn(__fsub_rn(s1, __fsub_rn(s2, bb2)), __fsub_rn(sq[2], bb2));
-  const float r2l = __fadd_rn(__fadd_rn(e1, e2), __fadd_rn(er[0], __fadd_rn(er[1], er[2])));
-  irh = MathF::rsqrt(s2);
-  rh = __fmul_rn(s2, irh);
-  rl = __fmul_rn(__fmul_rn(__fadd_rn(__fmaf_rn(-rh, rh, s2), r2l), 0.5f), irh);
-}
-
-template <class R> __device__ __forceinline__ R warp_sum(R v)
-{
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Per-block partial of (E, W[6]) in a fixed order: float/double per-thread values,
-// warp sums in R, warps combined in float64 in warp order.
-template <class R, int T>
-__device__ __forceinline__ void block_partial(const R (&v)[7], bool eflag, bool vflag, double *out)
-{
-  __shared__ double sw[T / 32][7];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int c = 0; c < 7; ++c) {
-    if ((c == 0 && !eflag) || (c > 0 && !vflag)) continue;
-    R s = warp_sum(v[c]);
-    if (lane == 0) sw[w][c] = (double)s;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int c = 0; c < 7; ++c) {
-      double a = 0.0;
-      for (int k = 0; k < T / 32; ++k) a += ((c == 0 && !eflag) || (c > 0 && !vflag)) ? 0.0 : sw[k][c];
-      out[c] = a;
-    }
-    out[7] = 0.0;
-  }
-}
-
-// ============================================================================
-// fast kernel: register slots, unordered neighbour pairs
-
-template <class R, int MAXNC, bool ONE, bool EFLAG, bool VFLAG>
-__global__ void __launch_bounds__(FAST_THREADS, (sizeof(R) == 4 && MAXNC == 4) ? 7 : 1)
-k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const int *__restrict__ nbr,
-            const int *__restrict__ cnt, const SysTab *__restrict__ sys, const PairP<R> *__restrict__ gpairs,
-            const TripP<R> *__restrict__ gtrips, int nt, typename V4t<R>::type *__restrict__ contrib,
-            typename V4t<R>::type *__restrict__ selfF, unsigned long long *__restrict__ mask,
-            int *__restrict__ work, int *__restrict__ nwork, double *__restrict__ partial, RunState *rs,
-            double *__restrict__ eatom, const int *__restrict__ order, int begin, int count, int block_base,
-            int stats)
-{
-  using M = typename MathOf<R>::M;
-  using V4 = typename V4t<R>::type;
-  constexpr bool MIXED = sizeof(R) == 4;
-  constexpr int T = FAST_THREADS;
-  __shared__ PairP<R> pairs[ONE ? 1 : MAX_TYPES * MAX_TYPES];
-  __shared__ TripP<R> trips[ONE ? 1 : MAX_TYPES * MAX_TYPES * MAX_TYPES];
-  __shared__ int warp_over[T / 32];
-
-  if (rs->status != 0) return;   // uniform across the grid
-  if (threadIdx.x < (ONE ? 1 : nt * nt)) pairs[threadIdx.x] = gpairs[threadIdx.x];
-  if (threadIdx.x < (ONE ? 1 : nt * nt * nt)) trips[threadIdx.x] = gtrips[threadIdx.x];
-  __syncthreads();
-
-  const int t = threadIdx.x;
-  const int tg = blockIdx.x * T + t;
-  const bool active = tg < count;
-  const int i = active ? (order ? order[begin + tg] : begin + tg) : 0;
-  const int fb = block_base + (int)blockIdx.x;   // this block's queue and partial-sum row
-
-  int ti = 0;
-  int4 qi = make_int4(0, 0, 0, 0);
-  dbl4 xi = make_dbl4(0, 0, 0, 0);
-  unsigned long long mb = 0ull;
-  int n = 0;
-  const Geom *gp = &sys[0].geo;   // geometry of atom i's system (all its neighbours share it)
-  if (active) {
-    int w;
-    if (MIXED) {
-      qi = q[i];
-      w = qi.w;
-    } else {
-      xi = x[i];
-      w = (int)__double_as_longlong(xi.w);
-    }
-    ti = type_of(w);
-    gp = &sys[sys_of(w)].geo;
-    n = cnt[i];
-  }
-  // Direct path: the whole list fits the slots, so slot s is list entry s (entries
-  // outside the cutoff get f_C = f_C' = 0 and contribute nothing) and every load is
-  // issued in one unrolled burst.  Otherwise the list is packed: a first pass marks
-  // in-cutoff entries, the second loads them into consecutive slots.
-  const bool direct = active && n <= MAXNC;
-
-  R ux[MAXNC], uy[MAXNC], uz[MAXNC], rr[MAXNC], rl[MAXNC], ir[MAXNC], fc[MAXNC], dfc[MAXNC];
-  int meta[MAXNC];
-#pragma unroll
-  for (int s = 0; s < MAXNC; ++s) {
-    ux[s] = uy[s] = uz[s] = R(0);
-    rr[s] = ir[s] = R(1);
-    rl[s] = fc[s] = dfc[s] = R(0);
-    meta[s] = 0;
-  }
-
-  // geometry of slot s from list entry e (neighbour j): unit vector, r, 1/r, f_C, f_C'
-  auto fill_slot = [&](int s, int e, int j, const int4 &qj, const dbl4 &xj, int tj) {
-    R dx, dy, dz, r, rlo, inv;
-    if (MIXED) {
-      float dh[3], dl[3];
-      qd_fine(qdiff(qj.x, qi.x), gp->q_to_f[0], gp->q_to_f_lo[0], dh[0], dl[0]);
-      qd_fine(qdiff(qj.y, qi.y), gp->q_to_f[1], gp->q_to_f_lo[1], dh[1], dl[1]);
-      qd_fine(qdiff(qj.z, qi.z), gp->q_to_f[2], gp->q_to_f_lo[2], dh[2], dl[2]);
-      float rh_, rl_, irh_;
-      norm_fine(dh, dl, rh_, rl_, irh_);
-      dx = (R)dh[0]; dy = (R)dh[1]; dz = (R)dh[2];
-      r = (R)rh_; rlo = (R)rl_; inv = (R)irh_;
-    } else {
-      dx = (R)min_image(__dsub_rn(xj.x, xi.x), gp->L[0], gp->invL[0]);
-      dy = (R)min_image(__dsub_rn(xj.y, xi.y), gp->L[1], gp->invL[1]);
-      dz = (R)min_image(__dsub_rn(xj.z, xi.z), gp->L[2], gp->invL[2]);
-      const R r2 = r2_decide(dx, dy, dz);
-      inv = M::rsqrt(r2);
-      r = r2 * inv;
-      rlo = R(0);
-    }
-    ux[s] = dx * inv;
-    uy[s] = dy * inv;
-    uz[s] = dz * inv;
-    rr[s] = r;
-    rl[s] = rlo;
-    ir[s] = inv;
-    cutoff_fn<M>(r, rlo, pairs[ONE ? 0 : ti * nt + tj], fc[s], dfc[s]);
-    meta[s] = e | (tj << 8);
-  };
-
-  // cheap in-cutoff test of entry (i, j)
-  auto in_cutoff = [&](const int4 &qj, const dbl4 &xj, int tj) -> bool {
-    R r2;
-    if (MIXED) {
-      r2 = r2_decide(q_scaled(qdiff(qj.x, qi.x), gp->q_to_f[0]), q_scaled(qdiff(qj.y, qi.y), gp->q_to_f[1]),
-                     q_scaled(qdiff(qj.z, qi.z), gp->q_to_f[2]));
-    } else {
-      r2 = r2_decide(min_image(__dsub_rn(xj.x, xi.x), gp->L[0], gp->invL[0]),
-                     min_image(__dsub_rn(xj.y, xi.y), gp->L[1], gp->invL[1]),
-                     min_image(__dsub_rn(xj.z, xi.z), gp->L[2], gp->invL[2]));
-    }
-    return r2 < pairs[ONE ? 0 : ti * nt + tj].rc2;
-  };
-
-  int nc_all = 0;
-  if (direct) {
-    int jj[MAXNC];
-#pragma unroll
-    for (int s = 0; s < MAXNC; ++s) jj[s] = s < n ? nbr[(size_t)s * N + i] : i;
-    int4 qq[MAXNC];
-    dbl4 xx[MAXNC];
-#pragma unroll
-    for (int s = 0; s < MAXNC; ++s) {
-      if (MIXED) qq[s] = q[jj[s]];
-      else xx[s] = x[jj[s]];
-    }
-#pragma unroll
-    for (int s = 0; s < MAXNC; ++s) {
-      if (s < n) {
-        const int tj = type_of(MIXED ? qq[s].w : (int)__double_as_longlong(xx[s].w));
-        if (in_cutoff(qq[s], xx[s], tj)) {
-          mb |= 1ull << s;
-          fill_slot(s, s, jj[s], qq[s], xx[s], tj);
-        } else {
-          meta[s] = s | (tj << 8);
-        }
-      }
-    }
-    nc_all = __popcll(mb);
-  } else if (active) {
-    // PU list entries per round: their loads are issued together
-    constexpr int PU = MIXED ? 4 : 2;
-    for (int s0 = 0; s0 < n; s0 += PU) {
-      int jj[PU];
-#pragma unroll
-      for (int k = 0; k < PU; ++k) jj[k] = s0 + k < n ? nbr[(size_t)(s0 + k) * N + i] : i;
-      int4 qq[PU];
-      dbl4 xx[PU];
-#pragma unroll
-      for (int k = 0; k < PU; ++k) {
-        if (MIXED) qq[k] = q[jj[k]];
-        else xx[k] = x[jj[k]];
-      }
-#pragma unroll
-      for (int k = 0; k < PU; ++k) {
-        const int tj = type_of(MIXED ? qq[k].w : (int)__double_as_longlong(xx[k].w));
-        if (s0 + k < n && in_cutoff(qq[k], xx[k], tj)) mb |= 1ull << (s0 + k);
-      }
-    }
-    nc_all = __popcll(mb);
-  }
-  const bool over = !direct && nc_all > MAXNC;
-  // queue atoms with too many neighbours, per block and in thread order
-  {
-    const unsigned bal = __ballot_sync(0xffffffffu, over);
-    if ((t & 31) == 0) warp_over[t >> 5] = __popc(bal);
-    __syncthreads();
-    if (over) {
-      int base = 0;
-      for (int w = 0; w < (t >> 5); ++w) base += warp_over[w];
-      const int k = base + __popc(bal & ((1u << (t & 31)) - 1u));
-      work[(size_t)fb * T + k] = i;
-    }
-    if (t == 0) {
-      int s = 0;
-      for (int w = 0; w < T / 32; ++w) s += warp_over[w];
-      nwork[fb] = s;
-      if (s > 0) atomicAdd(&rs->over_total, s);
-    }
-  }
-  if (stats) {
-    // largest in-cutoff counts, overall and per type (they choose the slot counts of
-    // later launches): warp maxima, then one atomic per block and statistic
-    __shared__ unsigned smax[T / 32][MAX_TYPES + 1];
-    const unsigned m = __reduce_max_sync(0xffffffffu, (unsigned)nc_all);
-    if ((t & 31) == 0) smax[t >> 5][MAX_TYPES] = m;
-    for (int ty = 0; ty < (ONE ? 1 : nt); ++ty) {
-      const unsigned mt = __reduce_max_sync(0xffffffffu, (unsigned)((active && (ONE || ti == ty)) ? nc_all : 0));
-      if ((t & 31) == 0) smax[t >> 5][ty] = mt;
-    }
-    __syncthreads();
-    if (t <= MAX_TYPES && (t == MAX_TYPES || t < (ONE ? 1 : nt))) {
-      unsigned bm = 0;
-      for (int w = 0; w < T / 32; ++w) bm = max(bm, smax[w][t]);
-      if (bm > 0) atomicMax(t == MAX_TYPES ? &rs->maxnc : &rs->maxnc_t[t], (int)bm);
-    }
-  }
-  // slots in use: the whole list on the direct path, the packed in-cutoff entries else
-  const int nc = direct ? n : (over ? 0 : nc_all);
-  if (!direct && !over && active) {
-    unsigned long long rem = mb;
-#pragma unroll
-    for (int s = 0; s < MAXNC; ++s) {
-      if (s < nc) {
-        const int e = __ffsll((long long)rem) - 1;
-        rem &= rem - 1;
-        const int j = nbr[(size_t)e * N + i];
-        int4 qj = make_int4(0, 0, 0, 0);
-        dbl4 xj = make_dbl4(0, 0, 0, 0);
-        int tj;
-        if (MIXED) { qj = q[j]; tj = type_of(qj.w); }
-        else { xj = x[j]; tj = type_of((int)__double_as_longlong(xj.w)); }
-        fill_slot(s, e, j, qj, xj, tj);
-      }
-    }
-  }
-
-  // ---- first K loop: zeta over unordered pairs --------------------------------
-  R zeta[MAXNC];
-#pragma unroll
-  for (int s = 0; s < MAXNC; ++s) zeta[s] = R(0);
-#pragma unroll
-  for (int a = 0; a < MAXNC; ++a) {
-#pragma unroll
-    for (int b = a + 1; b < MAXNC; ++b) {
-      if (b < nc) {
-        const TripP<R> &Tp = trips[ONE ? 0 : (ti * nt + (meta[a] >> 8)) * nt + (meta[b] >> 8)];
-        const R cost = ux[a] * ux[b] + uy[a] * uy[b] + uz[a] * uz[b];
-        const R u = Tp.h - cost;
-        const R u2 = u * u;
-        const R g = Tp.gamma + Tp.K * u2 * M::rcp(Tp.d2 + u2);
-        R eab = R(1), eba = R(1);
-        if (Tp.lam3 != R(0)) {
-          R arg = Tp.lam3 * (rr[a] - rr[b]);
-          if (Tp.m3 != R(0)) arg = arg * arg * arg;
-          eab = M::expv(arg);
-          eba = M::expv(-arg);
-        }
-        zeta[a] += fc[b] * g * eab;
-        zeta[b] += fc[a] * g * eba;
-      }
-    }
-  }
-
-  // ---- pair terms -------------------------------------------------------------
-  R dz[MAXNC], Fx[MAXNC], Fy[MAXNC], Fz[MAXNC];
-  R e_i = R(0);
-#pragma unroll
-  for (int a = 0; a < MAXNC; ++a) {
-    dz[a] = Fx[a] = Fy[a] = Fz[a] = R(0);
-    if (a < nc) {
-      const PairP<R> &P = pairs[ONE ? 0 : ti * nt + (meta[a] >> 8)];
-      const R fR = P.A * M::expneg(P.lam1, P.lam1_lo, rr[a], rl[a]);
-      const R fA = -P.B * M::expneg(P.lam2, P.lam2_lo, rr[a], rl[a]);
-      R bij, dbij;
-      bond_order<M>(zeta[a], P, bij, dbij);
-      const R pr = fR + bij * fA;
-      e_i += R(0.5) * fc[a] * pr;
-      const R dvdr = R(0.5) * (dfc[a] * pr + fc[a] * (-P.lam1 * fR - bij * P.lam2 * fA));
-      dz[a] = R(0.5) * fc[a] * fA * dbij;
-      Fx[a] = -dvdr * ux[a];
-      Fy[a] = -dvdr * uy[a];
-      Fz[a] = -dvdr * uz[a];
-    }
-  }
-
-  // ---- second K loop: zeta derivatives over unordered pairs -------------------
-  // With P = dV/dzeta_ij fc_k e_jk, Q = dV/dzeta_ik fc_j e_kj, S = (P + Q) g'
-  // (e_jk the lambda3 factor, arg' its exponent's derivative):
-  //   F_j -= S/r_j u_k + (dV/dzeta_ik fc'_j g e_kj - S/r_j cos + (P - Q) g arg') u_j
-  //   F_k -= S/r_k u_j + (dV/dzeta_ij fc'_k g e_jk - S/r_k cos - (P - Q) g arg') u_k
-#pragma unroll
-  for (int a = 0; a < MAXNC; ++a) {
-#pragma unroll
-    for (int b = a + 1; b < MAXNC; ++b) {
-      if (b < nc) {
-        const TripP<R> &Tp = trips[ONE ? 0 : (ti * nt + (meta[a] >> 8)) * nt + (meta[b] >> 8)];
-        const R cost = ux[a] * ux[b] + uy[a] * uy[b] + uz[a] * uz[b];
-        const R u = Tp.h - cost;
-        const R u2 = u * u;
-        const R inv = M::rcp(Tp.d2 + u2);
-        const R g = Tp.gamma + Tp.K * u2 * inv;
-        const R dg = -Tp.G2 * u * inv * inv;
-        R eab = R(1), eba = R(1), darg = R(0);
-        if (Tp.lam3 != R(0)) {
-          const R tt = Tp.lam3 * (rr[a] - rr[b]);
-          R arg = tt;
-          darg = Tp.lam3;
-          if (Tp.m3 != R(0)) {
-            arg = tt * tt * tt;
-            darg = R(3) * Tp.lam3 * tt * tt;
-          }
-          eab = M::expv(arg);
-          eba = M::expv(-arg);
-        }
-        const R Pv = dz[a] * fc[b] * eab;
-        const R Qv = dz[b] * fc[a] * eba;
-        const R S = (Pv + Qv) * dg;
-        const R PQd = (Pv - Qv) * g * darg;
-        const R cj = S * ir[a];
-        const R ck = S * ir[b];
-        const R ca = dz[b] * dfc[a] * g * eba - cj * cost + PQd;
-        const R cb = dz[a] * dfc[b] * g * eab - ck * cost - PQd;
-        Fx[a] -= cj * ux[b] + ca * ux[a];
-        Fy[a] -= cj * uy[b] + ca * uy[a];
-        Fz[a] -= cj * uz[b] + ca * uz[a];
-        Fx[b] -= ck * ux[a] + cb * ux[b];
-        Fy[b] -= ck * uy[a] + cb * uy[b];
-        Fz[b] -= ck * uz[a] + cb * uz[b];
-      }
-    }
-  }
-
-  // ---- outputs ------------------------------------------------------------------
-  R red[7] = {e_i, R(0), R(0), R(0), R(0), R(0), R(0)};
-  if (active && !over) {
-    R fix = R(0), fiy = R(0), fiz = R(0);
-#pragma unroll
-    for (int a = 0; a < MAXNC; ++a) {
-      if (a < nc && ((mb >> (meta[a] & 0xff)) & 1ull)) {
-        fix -= Fx[a];
-        fiy -= Fy[a];
-        fiz -= Fz[a];
-        V4 c;
-        c.x = Fx[a]; c.y = Fy[a]; c.z = Fz[a]; c.w = R(0);
-        contrib[(size_t)(meta[a] & 0xff) * N + i] = c;
-        if (VFLAG) {
-          const R dx = rr[a] * ux[a], dy = rr[a] * uy[a], dzz = rr[a] * uz[a];
-          red[1] += dx * Fx[a]; red[2] += dy * Fy[a]; red[3] += dzz * Fz[a];
-          red[4] += dx * Fy[a]; red[5] += dx * Fz[a]; red[6] += dy * Fz[a];
-        }
-      }
-    }
-    V4 c;
-    c.x = fix; c.y = fiy; c.z = fiz; c.w = R(0);
-    selfF[i] = c;
-    mask[i] = mb;
-    if (eatom) eatom[i] = (double)e_i;
-  }
-  if (EFLAG || VFLAG) block_partial<R, T>(red, EFLAG, VFLAG, partial + (size_t)fb * 8);
-}
-
-// ============================================================================
-// off[k] = sum of in[0..k) for k <= n (n <= GEN_SUB), computed by the T threads of a
-// block: each thread sums a run of entries, then the runs are offset in order.
-constexpr int GEN_SUB = 256;
-template <int T>
-__device__ __forceinline__ void block_exclusive_offsets(const int *__restrict__ in, int n, int *off)
-{
-  constexpr int PER = (GEN_SUB + T - 1) / T;
-  __shared__ int runs[T + 1];
-  const int t = threadIdx.x;
-  int v[PER], sum = 0;
-#pragma unroll
-  for (int k = 0; k < PER; ++k) {
-    const int idx = t * PER + k;
-    v[k] = idx < n ? in[idx] : 0;
-    sum += v[k];
-  }
-  runs[t] = sum;
-  __syncthreads();
-  if (t == 0) {
-    int acc = 0;
-    for (int k = 0; k < T; ++k) {
-      const int x = runs[k];
-      runs[k] = acc;
-      acc += x;
-    }
-    runs[T] = acc;
-  }
-  __syncthreads();
-  int acc = runs[t];
-#pragma unroll
-  for (int k = 0; k < PER; ++k) {
-    const int idx = t * PER + k;
-    if (idx < n) off[idx] = acc;
-    acc += v[k];
-  }
-  if (t == 0) off[n] = runs[T];
-  __syncthreads();
-}
-
-// general kernel: per-thread shared-memory slots, ordered (j,k) loops
-
-constexpr int NRF = 12;   // real fields per slot
-enum { S_UX = 0, S_UY, S_UZ, S_R, S_IR, S_FC, S_DFC, S_DZ, S_FX, S_FY, S_FZ, S_RL };
-
-template <class R, int MAXNC>
-struct GenCfg {
-  static constexpr int slot_bytes = NRF * (int)sizeof(R) + 4;
-  static constexpr int raw = 98304 / (MAXNC * slot_bytes);
-  static constexpr int threads = raw >= 128 ? 128 : raw >= 64 ? 64 : 32;
-  static constexpr size_t smem_slots = (size_t)threads * MAXNC * slot_bytes;
-};
-
-// Evaluates atoms either all (work == nullptr: atom = global thread index) or the
-// overflow atoms queued by the fast kernel (work/nwork: per fast block, in order;
-// block b of this kernel takes a contiguous run of fast blocks as one flat queue).
-template <class R, int MAXNC, bool EFLAG, bool VFLAG>
-__global__ void __launch_bounds__(GenCfg<R, MAXNC>::threads)
-k_force_gen(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const int *__restrict__ nbr,
-            const int *__restrict__ cnt, const SysTab *__restrict__ sys, const PairP<R> *__restrict__ gpairs,
-            const TripP<R> *__restrict__ gtrips, int nt, typename V4t<R>::type *__restrict__ contrib,
-            typename V4t<R>::type *__restrict__ selfF, unsigned long long *__restrict__ mask,
-            const int *__restrict__ work, const int *__restrict__ nwork, int nfast, double *__restrict__ partial,
-            RunState *rs, double *__restrict__ eatom)
-{
-  using M = typename MathOf<R>::M;
-  using V4 = typename V4t<R>::type;
-  constexpr int T = GenCfg<R, MAXNC>::threads;
-  constexpr bool MIXED = sizeof(R) == 4;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  PairP<R> *pairs = reinterpret_cast<PairP<R> *>(smem_raw);
-  TripP<R> *trips = reinterpret_cast<TripP<R> *>(smem_raw + sizeof(PairP<R>) * MAX_TYPES * MAX_TYPES);
-  R *sr = reinterpret_cast<R *>(smem_raw + sizeof(PairP<R>) * MAX_TYPES * MAX_TYPES +
-                                sizeof(TripP<R>) * MAX_TYPES * MAX_TYPES * MAX_TYPES);
-  int *smeta = reinterpret_cast<int *>(sr + (size_t)NRF * MAXNC * T);
-
-  if (rs->status != 0) return;   // uniform across the grid
-  if (work && rs->over_total == 0) {
-    // no atom was queued: leave zero partial sums and stop
-    if ((EFLAG || VFLAG) && threadIdx.x < 8) partial[(size_t)blockIdx.x * 8 + threadIdx.x] = 0.0;
-    return;
-  }
-  for (int k = threadIdx.x; k < nt * nt; k += T) pairs[k] = gpairs[k];
-  for (int k = threadIdx.x; k < nt * nt * nt; k += T) trips[k] = gtrips[k];
-  __syncthreads();
-
-  const int t = threadIdx.x;
-#define SLOT(f, s) sr[((f) * MAXNC + (s)) * T + t]
-#define META(s) smeta[(s) * T + t]
-  R red[7] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
-  bool overflow = false;
-  int maxnc = 0;
-
-  // one atom: in-cutoff slots, first K loop and pair terms, second K loop, outputs
-  auto process = [&](const int i) {
-    int ti, w;
-    int4 qi = make_int4(0, 0, 0, 0);
-    dbl4 xi = make_dbl4(0, 0, 0, 0);
-    if (MIXED) {
-      qi = q[i];
-      w = qi.w;
-    } else {
-      xi = x[i];
-      w = (int)__double_as_longlong(xi.w);
-    }
-    ti = type_of(w);
-    const Geom *gp = &sys[sys_of(w)].geo;
-    int nc = 0;
-    unsigned long long mbits = 0ull;
-    const int n = cnt[i];
-    for (int s = 0; s < n; ++s) {
-      const int j = nbr[(size_t)s * N + i];
-      R dx, dy, dz;
-      int tj;
-      if (MIXED) {
-        const int4 qj = q[j];
-        tj = type_of(qj.w);
-        dx = (R)q_scaled(qdiff(qj.x, qi.x), gp->q_to_f[0]);
-        dy = (R)q_scaled(qdiff(qj.y, qi.y), gp->q_to_f[1]);
-        dz = (R)q_scaled(qdiff(qj.z, qi.z), gp->q_to_f[2]);
-      } else {
-        const dbl4 xj = x[j];
-        tj = type_of((int)__double_as_longlong(xj.w));
-        dx = (R)min_image(__dsub_rn(xj.x, xi.x), gp->L[0], gp->invL[0]);
-        dy = (R)min_image(__dsub_rn(xj.y, xi.y), gp->L[1], gp->invL[1]);
-        dz = (R)min_image(__dsub_rn(xj.z, xi.z), gp->L[2], gp->invL[2]);
-      }
-      const R r2 = r2_decide(dx, dy, dz);
-      const PairP<R> &P = pairs[ti * nt + tj];
-      if (r2 < P.rc2) {
-        if (nc < MAXNC) {
-          R r, rlo, inv;
-          if (MIXED) {
-            const int4 qj = q[j];
-            float dh[3], dl[3];
-            qd_fine(qdiff(qj.x, qi.x), gp->q_to_f[0], gp->q_to_f_lo[0], dh[0], dl[0]);
-            qd_fine(qdiff(qj.y, qi.y), gp->q_to_f[1], gp->q_to_f_lo[1], dh[1], dl[1]);
-            qd_fine(qdiff(qj.z, qi.z), gp->q_to_f[2], gp->q_to_f_lo[2], dh[2], dl[2]);
-            float rh_, rl_, irh_;
-            norm_fine(dh, dl, rh_, rl_, irh_);
-            dx = (R)dh[0]; dy = (R)dh[1]; dz = (R)dh[2];
-            r = (R)rh_; rlo = (R)rl_; inv = (R)irh_;
-          } else {
-            const R rf2 = r2_decide(dx, dy, dz);
-            inv = M::rsqrt(rf2);
-            r = rf2 * inv;
-            rlo = R(0);
-          }
-          R fcv, dfcv;
-          cutoff_fn<M>(r, rlo, P, fcv, dfcv);
-          SLOT(S_UX, nc) = dx * inv;
-          SLOT(S_UY, nc) = dy * inv;
-          SLOT(S_UZ, nc) = dz * inv;
-          SLOT(S_R, nc) = r;
-          SLOT(S_RL, nc) = rlo;
-          SLOT(S_IR, nc) = inv;
-          SLOT(S_FC, nc) = fcv;
-          SLOT(S_DFC, nc) = dfcv;
-          META(nc) = s | (tj << 8);
-        }
-        ++nc;
-        mbits |= 1ull << s;
-      }
-    }
-    maxnc = max(maxnc, nc);
-    if (nc > MAXNC) {
-      overflow = true;
-      return;
-    }
-
-    // first K loop and pair terms
-    R e_atom = R(0);
-    for (int a = 0; a < nc; ++a) {
-      const int tj = META(a) >> 8;
-      const R uax = SLOT(S_UX, a), uay = SLOT(S_UY, a), uaz = SLOT(S_UZ, a), ra = SLOT(S_R, a);
-      const TripP<R> *Tj = trips + (ti * nt + tj) * nt;
-      R zeta = R(0);
-      for (int b = 0; b < nc; ++b) {
-        if (b == a) continue;
-        const TripP<R> &Tp = Tj[META(b) >> 8];
-        const R cost = uax * SLOT(S_UX, b) + uay * SLOT(S_UY, b) + uaz * SLOT(S_UZ, b);
-        const R u = Tp.h - cost;
-        const R u2 = u * u;
-        const R g = Tp.gamma + Tp.K * u2 * M::rcp(Tp.d2 + u2);
-        R ex = R(1);
-        if (Tp.lam3 != R(0)) {
-          R arg = Tp.lam3 * (ra - SLOT(S_R, b));
-          if (Tp.m3 != R(0)) arg = arg * arg * arg;
-          ex = M::expv(arg);
-        }
-        zeta += SLOT(S_FC, b) * g * ex;
-      }
-      const PairP<R> &P = pairs[ti * nt + tj];
-      const R fcv = SLOT(S_FC, a), dfcv = SLOT(S_DFC, a);
-      const R fR = P.A * M::expneg(P.lam1, P.lam1_lo, ra, SLOT(S_RL, a));
-      const R fA = -P.B * M::expneg(P.lam2, P.lam2_lo, ra, SLOT(S_RL, a));
-      R bij, dbij;
-      bond_order<M>(zeta, P, bij, dbij);
-      const R pr = fR + bij * fA;
-      red[0] += R(0.5) * fcv * pr;
-      e_atom += R(0.5) * fcv * pr;
-      const R dvdr = R(0.5) * (dfcv * pr + fcv * (-P.lam1 * fR - bij * P.lam2 * fA));
-      SLOT(S_DZ, a) = R(0.5) * fcv * fA * dbij;
-      SLOT(S_FX, a) = -dvdr * uax;
-      SLOT(S_FY, a) = -dvdr * uay;
-      SLOT(S_FZ, a) = -dvdr * uaz;
-    }
-
-    // second K loop
-    for (int a = 0; a < nc; ++a) {
-      const R dzv = SLOT(S_DZ, a);
-      if (dzv == R(0)) continue;
-      const int tj = META(a) >> 8;
-      const R uax = SLOT(S_UX, a), uay = SLOT(S_UY, a), uaz = SLOT(S_UZ, a), ra = SLOT(S_R, a),
-              ira = SLOT(S_IR, a);
-      const TripP<R> *Tj = trips + (ti * nt + tj) * nt;
-      R fjx = R(0), fjy = R(0), fjz = R(0);
-      for (int b = 0; b < nc; ++b) {
-        if (b == a) continue;
-        const TripP<R> &Tp = Tj[META(b) >> 8];
-        const R ubx = SLOT(S_UX, b), uby = SLOT(S_UY, b), ubz = SLOT(S_UZ, b), irb = SLOT(S_IR, b);
-        const R cost = uax * ubx + uay * uby + uaz * ubz;
-        const R u = Tp.h - cost;
-        const R u2 = u * u;
-        const R inv = M::rcp(Tp.d2 + u2);
-        const R g = Tp.gamma + Tp.K * u2 * inv;
-        const R dg = -Tp.G2 * u * inv * inv;
-        R ex = R(1), darg = R(0);
-        if (Tp.lam3 != R(0)) {
-          const R tt = Tp.lam3 * (ra - SLOT(S_R, b));
-          R arg = tt;
-          darg = Tp.lam3;
-          if (Tp.m3 != R(0)) {
-            arg = tt * tt * tt;
-            darg = R(3) * Tp.lam3 * tt * tt;
-          }
-          ex = M::expv(arg);
-        }
-        const R fcb = SLOT(S_FC, b), dfcb = SLOT(S_DFC, b);
-        const R a1 = fcb * ex * dg;
-        const R a2 = fcb * ex * g * darg;
-        const R a3 = dfcb * g * ex;
-        const R cj = a1 * ira;
-        const R dzjx = cj * (ubx - cost * uax) + a2 * uax;
-        const R dzjy = cj * (uby - cost * uay) + a2 * uay;
-        const R dzjz = cj * (ubz - cost * uaz) + a2 * uaz;
-        const R ck = a1 * irb;
-        const R dzkx = (a3 - a2) * ubx + ck * (uax - cost * ubx);
-        const R dzky = (a3 - a2) * uby + ck * (uay - cost * uby);
-        const R dzkz = (a3 - a2) * ubz + ck * (uaz - cost * ubz);
-        fjx -= dzv * dzjx;
-        fjy -= dzv * dzjy;
-        fjz -= dzv * dzjz;
-        SLOT(S_FX, b) -= dzv * dzkx;
-        SLOT(S_FY, b) -= dzv * dzky;
-        SLOT(S_FZ, b) -= dzv * dzkz;
-      }
-      SLOT(S_FX, a) += fjx;
-      SLOT(S_FY, a) += fjy;
-      SLOT(S_FZ, a) += fjz;
-    }
-
-    R fix = R(0), fiy = R(0), fiz = R(0);
-    for (int a = 0; a < nc; ++a) {
-      const R fx = SLOT(S_FX, a), fy = SLOT(S_FY, a), fz = SLOT(S_FZ, a);
-      fix -= fx;
-      fiy -= fy;
-      fiz -= fz;
-      V4 c;
-      c.x = fx; c.y = fy; c.z = fz; c.w = R(0);
-      contrib[(size_t)(META(a) & 0xff) * N + i] = c;
-      if (VFLAG) {
-        const R r = SLOT(S_R, a);
-        const R dx = r * SLOT(S_UX, a), dy = r * SLOT(S_UY, a), dz = r * SLOT(S_UZ, a);
-        red[1] += dx * fx; red[2] += dy * fy; red[3] += dz * fz;
-        red[4] += dx * fy; red[5] += dx * fz; red[6] += dy * fz;
-      }
-    }
-    V4 c;
-    c.x = fix; c.y = fiy; c.z = fiz; c.w = R(0);
-    selfF[i] = c;
-    mask[i] = mbits;
-    if (eatom) eatom[i] = (double)e_atom;
-  };
-
-  if (!work) {
-    const int i = (int)blockIdx.x * T + t;
-    if (i < N) process(i);
-  } else {
-    // Overflow queues of the register kernel: block b takes the contiguous run of
-    // fast blocks [b G, (b + 1) G), G = ceil(nfast / gridDim.x), as one flat queue in
-    // order (GEN_SUB fast blocks per pass) and its threads take entries t, t + T, ...
-    __shared__ int qoff[GEN_SUB + 1];
-    const int G = (nfast + (int)gridDim.x - 1) / (int)gridDim.x;
-    const int fb0 = (int)blockIdx.x * G, fb1 = min(fb0 + G, nfast);
-    for (int sb = fb0; sb < fb1; sb += GEN_SUB) {
-      const int ns = min(GEN_SUB, fb1 - sb);
-      block_exclusive_offsets<T>(nwork + sb, ns, qoff);
-      const int total = qoff[ns];
-      for (int pidx = t; pidx < total; pidx += T) {
-        int lo = 0, hi = ns - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (qoff[mid] <= pidx) lo = mid; else hi = mid - 1;
-        }
-        process(work[(size_t)(sb + lo) * FAST_THREADS + (pidx - qoff[lo])]);
-      }
-      __syncthreads();
-    }
-  }
-  if (overflow) atomicOr(&rs->status, ST_NC_OVERFLOW);
-  if (maxnc > 0) atomicMax(&rs->maxnc, maxnc);
-  if (EFLAG || VFLAG) block_partial<R, T>(red, EFLAG, VFLAG, partial + (size_t)blockIdx.x * 8);
-#undef SLOT
-#undef META
-}
 
 // Sum n partial rows of (E, W[6]) in a fixed order into rs->epot / rs->virial:
 // thread k adds rows k, k + 1024, ...; then a fixed tree over the threads.
@@ -901,106 +35,16 @@ __global__ void __launch_bounds__(1024) k_reduce_partials(const double *__restri
   }
 }
 
-// ---- host-side launch ------------------------------------------------------
-
-template <class R, int MAXNC, bool EFLAG, bool VFLAG>
-static cudaError_t launch_gen_t(cudaStream_t st, int N, const dbl4 *x, const int4 *q, const int *nbr, const int *cnt,
-                                const SysTab *sys, const void *pairs, const void *trips, int nt, void *contrib,
-                                void *selfF, unsigned long long *mask, const int *work, const int *nwork, int nfast,
-                                int gen_blocks, double *partial, RunState *rs, double *eatom)
-{
-  using C = GenCfg<R, MAXNC>;
-  const size_t smem = sizeof(PairP<R>) * MAX_TYPES * MAX_TYPES + sizeof(TripP<R>) * MAX_TYPES * MAX_TYPES * MAX_TYPES +
-                      C::smem_slots;
-  auto kern = k_force_gen<R, MAXNC, EFLAG, VFLAG>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  if (N == 0) return cudaSuccess;
-  const int blocks = work ? gen_blocks : (N + C::threads - 1) / C::threads;
-  kern<<<blocks, C::threads, smem, st>>>(N, x, q, nbr, cnt, sys, (const PairP<R> *)pairs, (const TripP<R> *)trips,
-                                         nt, (typename V4t<R>::type *)contrib, (typename V4t<R>::type *)selfF, mask,
-                                         work, nwork, nfast, partial, rs, eatom);
-  return cudaGetLastError();
-}
-
-template <class R, int MAXNC>
-static cudaError_t launch_gen(cudaStream_t st, int eflag, int vflag, int N, const dbl4 *x, const int4 *q,
-                              const int *nbr, const int *cnt, const SysTab *sys, const void *pairs, const void *trips,
-                              int nt, void *contrib, void *selfF, unsigned long long *mask, const int *work,
-                              const int *nwork, int nfast, int gen_blocks, double *partial, RunState *rs,
-                              double *eatom)
-{
-  if (vflag)
-    return launch_gen_t<R, MAXNC, true, true>(st, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib, selfF, mask, work,
-                                              nwork, nfast, gen_blocks, partial, rs, eatom);
-  if (eflag)
-    return launch_gen_t<R, MAXNC, true, false>(st, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib, selfF, mask,
-                                               work, nwork, nfast, gen_blocks, partial, rs, eatom);
-  return launch_gen_t<R, MAXNC, false, false>(st, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib, selfF, mask,
-                                              work, nwork, nfast, gen_blocks, partial, rs, eatom);
-}
-
-template <class R>
-static int gen_threads(int slots)
-{
-  switch (slots) {
-    case 8: return GenCfg<R, 8>::threads;
-    case 16: return GenCfg<R, 16>::threads;
-    case 32: return GenCfg<R, 32>::threads;
-    default: return GenCfg<R, 64>::threads;
-  }
-}
-
-template <class R>
-static cudaError_t launch_gen_any(cudaStream_t st, int slots, int eflag, int vflag, int N, const dbl4 *x,
-                                  const int4 *q, const int *nbr, const int *cnt, const SysTab *sys, const void *pairs,
-                                  const void *trips, int nt, void *contrib, void *selfF, unsigned long long *mask,
-                                  const int *work, const int *nwork, int nfast, int gen_blocks, double *partial,
-                                  RunState *rs, double *eatom)
-{
-#define TSF_GEN(NC)                                                                                                \
-  case NC:                                                                                                         \
-    return launch_gen<R, NC>(st, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib, selfF, mask, work, \
-                             nwork, nfast, gen_blocks, partial, rs, eatom);
-  switch (slots) {
-    TSF_GEN(8)
-    TSF_GEN(16)
-    TSF_GEN(32)
-    TSF_GEN(64)
-  }
-#undef TSF_GEN
-  return cudaErrorInvalidValue;
-}
-
-template <class R, int MAXNC, bool ONE>
-static cudaError_t launch_reg(cudaStream_t st, int eflag, int vflag, int N, const dbl4 *x, const int4 *q,
-                              const int *nbr, const int *cnt, const SysTab *sys, const void *pairs, const void *trips,
-                              int nt, void *contrib, void *selfF, unsigned long long *mask, int *work, int *nwork,
-                              double *partial, RunState *rs, double *eatom, const ForceRoute &rt, int stats)
-{
-  const int blocks = (rt.count + FAST_THREADS - 1) / FAST_THREADS;
-  if (blocks == 0) return cudaSuccess;
-  using P = const PairP<R> *;
-  using Tt = const TripP<R> *;
-  using V = typename V4t<R>::type *;
-  if (vflag)
-    k_force_reg<R, MAXNC, ONE, true, true><<<blocks, FAST_THREADS, 0, st>>>(
-        N, x, q, nbr, cnt, sys, (P)pairs, (Tt)trips, nt, (V)contrib, (V)selfF, mask, work, nwork, partial, rs,
-        eatom, rt.order, rt.begin, rt.count, rt.block_base, stats);
-  else if (eflag)
-    k_force_reg<R, MAXNC, ONE, true, false><<<blocks, FAST_THREADS, 0, st>>>(
-        N, x, q, nbr, cnt, sys, (P)pairs, (Tt)trips, nt, (V)contrib, (V)selfF, mask, work, nwork, partial, rs,
-        eatom, rt.order, rt.begin, rt.count, rt.block_base, stats);
-  else
-    k_force_reg<R, MAXNC, ONE, false, false><<<blocks, FAST_THREADS, 0, st>>>(
-        N, x, q, nbr, cnt, sys, (P)pairs, (Tt)trips, nt, (V)contrib, (V)selfF, mask, work, nwork, partial, rs,
-        eatom, rt.order, rt.begin, rt.count, rt.block_base, stats);
-  return cudaGetLastError();
-}
+#define TSF_FORCE_DECL(NAME)                                                                                        \
+  cudaError_t NAME(int part, cudaStream_t st, int fast_slots, bool one_type, int gen_slots, int eflag, int vflag,  \
+                   int N, const dbl4 *x, const int4 *q, const int *nbr, const int *cnt, const SysTab *sys,         \
+                   const void *pairs, const void *trips, int nt, void *contrib, void *selfF,                       \
+                   unsigned long long *mask, int *work, int *nwork, double *partial, RunState *rs, double *eatom,  \
+                   const ForceRoutes *routes, int stats, int *rows);
+TSF_FORCE_DECL(launch_force_fp64)
+TSF_FORCE_DECL(launch_force_mixed)
+TSF_FORCE_DECL(launch_force_single)
+#undef TSF_FORCE_DECL
 
 int force_slots_for(int need)
 {
@@ -1010,85 +54,46 @@ int force_slots_for(int need)
   return 64;
 }
 
-int force_gen_blocks() { return GEN_BLOCKS; }
-
 // Rows of 8 doubles the partial-sum buffer needs for N atoms (any launch shape).
-int force_partial_rows(int N) { return (N + 31) / 32 + 2 + force_gen_blocks(); }
+int force_partial_rows(int N) { return (N + 31) / 32 + 2 + GEN_BLOCKS; }
 
 // Overflow-queue blocks for N atoms split into up to two register-kernel launches.
-int force_queue_blocks(int N) { return (N + 127) / 128 + 2; }
+int force_queue_blocks(int N) { return (N + FAST_THREADS - 1) / FAST_THREADS + 2; }
 
-// One force evaluation.  fast_slots 4 or 8 runs the register kernel plus the
-// general kernel (gen_slots wide) over its overflow queue; fast_slots 0 runs the
-// general kernel over all atoms.  routes (may be null: every atom in index order with
+// One force evaluation in precision prec (PREC_FP64, PREC_MIXED or PREC_SINGLE).
+// fast_slots 4 or 8 runs the register kernel plus the general kernel (gen_slots
+// wide) over its overflow queue; fast_slots 0 runs the general kernel over all atoms.  routes (may be null: every atom in index order with
 // fast_slots) splits the register kernel into launches over atom subsets, each with
 // its own slot count.  Buffers: partial force_partial_rows(N) x 8 doubles; work
 // force_queue_blocks(N) x 128 ints; nwork force_queue_blocks(N) ints.  With
 // eflag/vflag the energy and virial are added to rs->epot / rs->virial.  part: 1
 // launches the register kernel(s) only, 2 the rest (general kernel and reduction),
 // 3 both.  stats: record the largest in-cutoff counts (rs->maxnc, rs->maxnc_t).
-cudaError_t launch_force_part(int part, cudaStream_t st, bool mixed, int fast_slots, bool one_type, int gen_slots,
+cudaError_t launch_force_part(int part, cudaStream_t st, int prec, int fast_slots, bool one_type, int gen_slots,
                               int eflag, int vflag, int N, const dbl4 *x, const int4 *q, const int *nbr,
                               const int *cnt, const SysTab *sys, const void *pairs, const void *trips, int nt,
                               void *contrib, void *selfF, unsigned long long *mask, int *work, int *nwork,
                               double *partial, RunState *rs, double *eatom, const ForceRoutes *routes, int stats)
 {
-  if (N == 0) return cudaSuccess;
-  cudaError_t e = cudaSuccess;
+  auto f = prec == PREC_FP64 ? launch_force_fp64 : prec == PREC_MIXED ? launch_force_mixed : launch_force_single;
   int rows = 0;
-  if (fast_slots > 0) {
-    ForceRoutes one{1, {{nullptr, 0, N, fast_slots, 0}, {nullptr, 0, 0, 0, 0}}};
-    const ForceRoutes &R = routes ? *routes : one;
-    int nfast = 0;
-    for (int k = 0; k < R.n; ++k) {
-      ForceRoute rt = R.r[k];
-      rt.block_base = nfast;
-      nfast += (rt.count + FAST_THREADS - 1) / FAST_THREADS;
-      if (!(part & 1)) continue;
-#define TSF_REG(RT, NC)                                                                                             \
-  e = one_type ? launch_reg<RT, NC, true>(st, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib, selfF, \
-                                          mask, work, nwork, partial, rs, eatom, rt, stats)                         \
-               : launch_reg<RT, NC, false>(st, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib,     \
-                                           selfF, mask, work, nwork, partial, rs, eatom, rt, stats);
-      if (mixed) {
-        if (rt.slots <= 4) { TSF_REG(float, 4) } else { TSF_REG(float, 8) }
-      } else {
-        if (rt.slots <= 4) { TSF_REG(double, 4) } else { TSF_REG(double, 8) }
-      }
-#undef TSF_REG
-      if (e != cudaSuccess) return e;
-    }
-    if (!(part & 2)) return cudaSuccess;
-    double *gp = partial + (size_t)nfast * 8;
-    e = mixed ? launch_gen_any<float>(st, gen_slots, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib,
-                                      selfF, mask, work, nwork, nfast, force_gen_blocks(), gp, rs, eatom)
-              : launch_gen_any<double>(st, gen_slots, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib,
-                                       selfF, mask, work, nwork, nfast, force_gen_blocks(), gp, rs, eatom);
-    rows = nfast + force_gen_blocks();
-  } else {
-    if (!(part & 2)) return cudaSuccess;
-    e = mixed ? launch_gen_any<float>(st, gen_slots, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib,
-                                      selfF, mask, nullptr, nullptr, 0, 0, partial, rs, eatom)
-              : launch_gen_any<double>(st, gen_slots, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib,
-                                       selfF, mask, nullptr, nullptr, 0, 0, partial, rs, eatom);
-    const int T = mixed ? gen_threads<float>(gen_slots) : gen_threads<double>(gen_slots);
-    rows = (N + T - 1) / T;
-  }
+  cudaError_t e = f(part, st, fast_slots, one_type, gen_slots, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt,
+                    contrib, selfF, mask, work, nwork, partial, rs, eatom, routes, stats, &rows);
   if (e != cudaSuccess) return e;
-  if (eflag || vflag) {
+  if ((eflag || vflag) && rows > 0 && (part & 2)) {
     k_reduce_partials<<<1, 1024, 0, st>>>(partial, rows, rs);
     e = cudaGetLastError();
   }
   return e;
 }
 
-cudaError_t launch_force(cudaStream_t st, bool mixed, int fast_slots, bool one_type, int gen_slots, int eflag,
+cudaError_t launch_force(cudaStream_t st, int prec, int fast_slots, bool one_type, int gen_slots, int eflag,
                          int vflag, int N, const dbl4 *x, const int4 *q, const int *nbr, const int *cnt,
                          const SysTab *sys, const void *pairs, const void *trips, int nt, void *contrib, void *selfF,
                          unsigned long long *mask, int *work, int *nwork, double *partial, RunState *rs,
                          double *eatom)
 {
-  return launch_force_part(3, st, mixed, fast_slots, one_type, gen_slots, eflag, vflag, N, x, q, nbr, cnt, sys, pairs,
+  return launch_force_part(3, st, prec, fast_slots, one_type, gen_slots, eflag, vflag, N, x, q, nbr, cnt, sys, pairs,
                            trips, nt, contrib, selfF, mask, work, nwork, partial, rs, eatom, nullptr, 1);
 }
 

@@ -13,10 +13,6 @@
 
 namespace tsf {
 
-template <class R> struct V4g;
-template <> struct V4g<float> { using type = float4; };
-template <> struct V4g<double> { using type = dbl4; };
-
 // Knuth's TwoSum: s + e == a + b exactly (float32 round-to-nearest; explicit
 // intrinsics so that no step is contracted or reassociated).
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
@@ -26,12 +22,13 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-template <class R> struct GatherAcc;
+// Force accumulators of the gather, one per precision; V is the contribution type.
 
-// float32 contributions: compensated (TwoSum) accumulation, a head and tail
-// float per component; the force is head + tail rounded once to float64.  Its
-// error is that of a float64 sum of the same float32 terms, on the float32 pipe.
-template <> struct GatherAcc<float> {
+// mixed mode: float32 contributions summed with TwoSum, a head and tail float per
+// component; the force is head + tail rounded once to float64.  Its error is that of
+// a float64 sum of the same float32 terms, on the float32 pipe.
+struct AccMixed {
+  using V = float4;
   float h[3], l[3];
   __device__ __forceinline__ void init(const float4 &c)
   {
@@ -53,22 +50,40 @@ template <> struct GatherAcc<float> {
   }
 };
 
-template <> struct GatherAcc<double> {
+// single mode: a plain float32 sum (the paper's all-float32 accumulation)
+struct AccSingle {
+  using V = float4;
+  float f[3];
+  __device__ __forceinline__ void init(const float4 &c) { f[0] = c.x; f[1] = c.y; f[2] = c.z; }
+  __device__ __forceinline__ void add(const float4 &c)
+  {
+    f[0] = __fadd_rn(f[0], c.x);
+    f[1] = __fadd_rn(f[1], c.y);
+    f[2] = __fadd_rn(f[2], c.z);
+  }
+  __device__ __forceinline__ void out(double &fx, double &fy, double &fz) const
+  {
+    fx = (double)f[0]; fy = (double)f[1]; fz = (double)f[2];
+  }
+};
+
+struct AccFP64 {
+  using V = dbl4;
   double f[3];
   __device__ __forceinline__ void init(const dbl4 &c) { f[0] = c.x; f[1] = c.y; f[2] = c.z; }
   __device__ __forceinline__ void add(const dbl4 &c) { f[0] += c.x; f[1] += c.y; f[2] += c.z; }
   __device__ __forceinline__ void out(double &fx, double &fy, double &fz) const { fx = f[0]; fy = f[1]; fz = f[2]; }
 };
 
-template <class R>
-__device__ __forceinline__ void gather_force(int m, int N, const typename V4g<R>::type *__restrict__ contrib,
-                                             const typename V4g<R>::type *__restrict__ selfF,
+template <class A>
+__device__ __forceinline__ void gather_force(int m, int N, const typename A::V *__restrict__ contrib,
+                                             const typename A::V *__restrict__ selfF,
                                              const unsigned long long *__restrict__ mask, const int *__restrict__ rev,
                                              double &fx, double &fy, double &fz)
 {
-  using V = typename V4g<R>::type;
+  using V = typename A::V;
   constexpr int U = 4;   // slots whose loads are issued together
-  GatherAcc<R> acc;
+  A acc;
   acc.init(selfF[m]);
   unsigned long long mb = mask[m];
   while (mb) {
@@ -139,9 +154,8 @@ __global__ void k_ingest_vel(int N, const double *__restrict__ vel, dbl4 *__rest
 }
 
 // reverse gather into AoS float64 forces; flags non-finite values
-template <class R>
-__global__ void k_gather_out(int N, const typename V4g<R>::type *__restrict__ contrib,
-                             const typename V4g<R>::type *__restrict__ selfF,
+template <class A>
+__global__ void k_gather_out(int N, const typename A::V *__restrict__ contrib, const typename A::V *__restrict__ selfF,
                              const unsigned long long *__restrict__ mask, const int *__restrict__ rev,
                              double *__restrict__ out, RunState *rs)
 {
@@ -149,7 +163,7 @@ __global__ void k_gather_out(int N, const typename V4g<R>::type *__restrict__ co
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   double fx, fy, fz;
-  gather_force<R>(i, N, contrib, selfF, mask, rev, fx, fy, fz);
+  gather_force<A>(i, N, contrib, selfF, mask, rev, fx, fy, fz);
   if (!isfinite(fx) || !isfinite(fy) || !isfinite(fz)) atomicOr(&rs->status, ST_NONFINITE);
   out[3 * (size_t)i] = fx;
   out[3 * (size_t)i + 1] = fy;
@@ -164,10 +178,10 @@ constexpr int VV_THREADS = 128;   // integrator block size (more resident blocks
 //   START:  v += dt/2 F/m; x += dt v; refresh fixed-point q; flag a rebuild when
 //           some atom moved more than skin/2 since the last build
 // KE: accumulate sum m v^2 of the full-step velocity (after FINISH, before START).
-template <class R, bool KE>
+template <class A, bool KE>
 __global__ void k_vv(int N, int mode, dbl4 *__restrict__ x, dbl4 *__restrict__ v, int4 *__restrict__ q,
-                     const int4 *__restrict__ qref, const typename V4g<R>::type *__restrict__ contrib,
-                     const typename V4g<R>::type *__restrict__ selfF, const unsigned long long *__restrict__ mask,
+                     const int4 *__restrict__ qref, const typename A::V *__restrict__ contrib,
+                     const typename A::V *__restrict__ selfF, const unsigned long long *__restrict__ mask,
                      const int *__restrict__ rev, const SysTab *__restrict__ sys, SysCtl *__restrict__ ctl,
                      const double *__restrict__ mass, float disp2_lim, double *__restrict__ kepart, RunState *rs)
 {
@@ -192,7 +206,7 @@ __global__ void k_vv(int N, int mode, dbl4 *__restrict__ x, dbl4 *__restrict__ v
       mode_i = C.steps_left > 0 ? (C.open ? (VV_FINISH | VV_START) : VV_START) : (C.open ? VV_FINISH : 0);
     }
     double fx, fy, fz;
-    gather_force<R>(i, N, contrib, selfF, mask, rev, fx, fy, fz);
+    gather_force<A>(i, N, contrib, selfF, mask, rev, fx, fy, fz);
     dbl4 vi = v[i];
     if (mode_i & VV_FINISH) {
       vi.x = fma(c, fx, vi.x);
@@ -375,43 +389,48 @@ __global__ void k_force_done(RunState *rs)
   for (int c = 0; c < 6; ++c) rs->virial[c] = 0.0;
 }
 
-cudaError_t launch_vv(cudaStream_t st, bool mixed, bool ke, int N, int mode, dbl4 *x, dbl4 *v, int4 *q,
+template <class A>
+static void launch_vv_a(cudaStream_t st, bool ke, int B, int N, int mode, dbl4 *x, dbl4 *v, int4 *q, const int4 *qref,
+                        const void *contrib, const void *selfF, const unsigned long long *mask, const int *rev,
+                        const SysTab *sys, SysCtl *ctl, const double *mass, float disp2_lim, double *kepart,
+                        RunState *rs)
+{
+  using V = const typename A::V *;
+  if (ke)
+    k_vv<A, true><<<B, VV_THREADS, 0, st>>>(N, mode, x, v, q, qref, (V)contrib, (V)selfF, mask, rev, sys, ctl, mass,
+                                            disp2_lim, kepart, rs);
+  else
+    k_vv<A, false><<<B, VV_THREADS, 0, st>>>(N, mode, x, v, q, qref, (V)contrib, (V)selfF, mask, rev, sys, ctl, mass,
+                                             disp2_lim, kepart, rs);
+}
+
+cudaError_t launch_vv(cudaStream_t st, int prec, bool ke, int N, int mode, dbl4 *x, dbl4 *v, int4 *q,
                       const int4 *qref, const void *contrib, const void *selfF, const unsigned long long *mask,
                       const int *rev, const SysTab *sys, SysCtl *ctl, const double *mass, float disp2_lim,
                       double *kepart, RunState *rs)
 {
   if (N == 0) return cudaSuccess;
-  const int T = VV_THREADS, B = (N + T - 1) / T;
-  if (mixed) {
-    if (ke)
-      k_vv<float, true><<<B, T, 0, st>>>(N, mode, x, v, q, qref, (const float4 *)contrib, (const float4 *)selfF,
-                                         mask, rev, sys, ctl, mass, disp2_lim, kepart, rs);
-    else
-      k_vv<float, false><<<B, T, 0, st>>>(N, mode, x, v, q, qref, (const float4 *)contrib, (const float4 *)selfF,
-                                          mask, rev, sys, ctl, mass, disp2_lim, kepart, rs);
-  } else {
-    if (ke)
-      k_vv<double, true><<<B, T, 0, st>>>(N, mode, x, v, q, qref, (const dbl4 *)contrib, (const dbl4 *)selfF,
-                                          mask, rev, sys, ctl, mass, disp2_lim, kepart, rs);
-    else
-      k_vv<double, false><<<B, T, 0, st>>>(N, mode, x, v, q, qref, (const dbl4 *)contrib, (const dbl4 *)selfF,
-                                           mask, rev, sys, ctl, mass, disp2_lim, kepart, rs);
-  }
+  const int B = (N + VV_THREADS - 1) / VV_THREADS;
+  auto f = prec == PREC_FP64 ? launch_vv_a<AccFP64> : prec == PREC_MIXED ? launch_vv_a<AccMixed>
+                                                                           : launch_vv_a<AccSingle>;
+  f(st, ke, B, N, mode, x, v, q, qref, contrib, selfF, mask, rev, sys, ctl, mass, disp2_lim, kepart, rs);
   if (ke) k_ke_reduce<<<1, 256, 0, st>>>(kepart, B, rs);
   return cudaGetLastError();
 }
 
 int vv_blocks(int N) { return (N + VV_THREADS - 1) / VV_THREADS; }
 
-cudaError_t launch_gather_out(cudaStream_t st, bool mixed, int N, const void *contrib, const void *selfF,
+cudaError_t launch_gather_out(cudaStream_t st, int prec, int N, const void *contrib, const void *selfF,
                               const unsigned long long *mask, const int *rev, double *out, RunState *rs)
 {
   if (N == 0) return cudaSuccess;
   const int T = 256, B = (N + T - 1) / T;
-  if (mixed)
-    k_gather_out<float><<<B, T, 0, st>>>(N, (const float4 *)contrib, (const float4 *)selfF, mask, rev, out, rs);
+  if (prec == PREC_FP64)
+    k_gather_out<AccFP64><<<B, T, 0, st>>>(N, (const dbl4 *)contrib, (const dbl4 *)selfF, mask, rev, out, rs);
+  else if (prec == PREC_MIXED)
+    k_gather_out<AccMixed><<<B, T, 0, st>>>(N, (const float4 *)contrib, (const float4 *)selfF, mask, rev, out, rs);
   else
-    k_gather_out<double><<<B, T, 0, st>>>(N, (const dbl4 *)contrib, (const dbl4 *)selfF, mask, rev, out, rs);
+    k_gather_out<AccSingle><<<B, T, 0, st>>>(N, (const float4 *)contrib, (const float4 *)selfF, mask, rev, out, rs);
   return cudaGetLastError();
 }
 

@@ -120,7 +120,8 @@ extern "C" int tersoff_compute_noalloc(const tersoff_params *P, const double *po
   if (errbuf && errlen) errbuf[0] = '\0';
   if (!P || !box || N < 0 || (N > 0 && (!pos || !types)))
     return fail(errbuf, errlen, TERSOFF_ERR_ARG, "null argument or N < 0");
-  if (prec != TERSOFF_FP64 && prec != TERSOFF_MIXED) return fail(errbuf, errlen, TERSOFF_ERR_ARG, "bad precision");
+  if (prec != TERSOFF_FP64 && prec != TERSOFF_MIXED && prec != TERSOFF_SINGLE)
+    return fail(errbuf, errlen, TERSOFF_ERR_ARG, "bad precision");
   if (N > kMaxAtoms)
     return fail(errbuf, errlen, TERSOFF_ERR_NOMEM,
                 "N = %lld atoms exceeds the fixed scratch limit of %d atoms of tersoff_compute_noalloc",
@@ -151,7 +152,7 @@ extern "C" int tersoff_compute_noalloc(const tersoff_params *P, const double *po
   int rc = scratch_address(dev, &base, errbuf, errlen);
   if (rc != TERSOFF_OK) return rc;
   cudaStream_t st = (cudaStream_t)stream;
-  const bool mixed = prec == TERSOFF_MIXED;
+  const bool f32 = prec != TERSOFF_FP64;
   RunState *rs = (RunState *)(base + Layout::rs);
   SysTab *sys = (SysTab *)(base + Layout::sys);
   dbl4 *x = (dbl4 *)(base + Layout::x);
@@ -186,10 +187,10 @@ extern "C" int tersoff_compute_noalloc(const tersoff_params *P, const double *po
   NK(launch_build(st, (int)N, q, sys, nullptr, g.ncell, g.rl2, cell_count, cell_start, tile_sums, cell_atoms, cell_of, rank,
                   nbr, rev, cnt, kCap, qref, rs, 0));
   const int fast_slots = P->sym_angular ? 8 : 0;
-  NK(launch_force(st, mixed, fast_slots, P->nt == 1, force_slots_for(kCap), 1, 1, (int)N, x, q, nbr, cnt, sys,
-                  mixed ? P->pair_f : P->pair_d, mixed ? P->trip_f : P->trip_d, P->nt, contrib, selfF, mask, work,
+  NK(launch_force(st, prec, fast_slots, P->nt == 1, force_slots_for(kCap), 1, 1, (int)N, x, q, nbr, cnt, sys,
+                  f32 ? P->pair_f : P->pair_d, f32 ? P->trip_f : P->trip_d, P->nt, contrib, selfF, mask, work,
                   nwork, partial, rs, nullptr));
-  if (forces) NK(launch_gather_out(st, mixed, (int)N, contrib, selfF, mask, rev, forces, rs));
+  if (forces) NK(launch_gather_out(st, prec, (int)N, contrib, selfF, mask, rev, forces, rs));
   if (energy_virial) {
     NK(cudaMemcpyAsync(energy_virial, &rs->epot, sizeof(double), cudaMemcpyDeviceToDevice, st));
     NK(cudaMemcpyAsync(energy_virial + 1, rs->virial, 6 * sizeof(double), cudaMemcpyDeviceToDevice, st));

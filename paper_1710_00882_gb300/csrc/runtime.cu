@@ -122,7 +122,8 @@ struct tersoff_md {
   double *d_trace = nullptr;
   size_t trace_cap = 0;
   double dt = 0, skin = 0;
-  bool mixed = false;
+  int prec = TERSOFF_FP64;
+  bool f32 = false;     // float32 force arithmetic (mixed or single precision)
   bool open = false;            // velocities are at the half step (a closing kick is pending)
   bool pe_valid = false;        // rs->epot_last holds the potential energy of the current positions
   long long steps_done = 0;     // host count of completed steps
@@ -229,9 +230,9 @@ int ensure_atoms(tersoff_ctx *ctx, AtomState &A, int64_t N, bool need_v)
   return TERSOFF_OK;
 }
 
-int ensure_scatter(tersoff_ctx *ctx, AtomState &A, int64_t N, int cap, bool mixed)
+int ensure_scatter(tersoff_ctx *ctx, AtomState &A, int64_t N, int cap, bool f32)
 {
-  size_t v4 = mixed ? sizeof(float4) : sizeof(dbl4);
+  size_t v4 = f32 ? sizeof(float4) : sizeof(dbl4);
   size_t n = (size_t)std::max<int64_t>(N, 1);
   const size_t nfast = (size_t)force_queue_blocks((int)n);
   if (!dreserve(A.contrib, A.contrib_b, n * (size_t)cap * v4) || !dreserve(A.selfF, A.selfF_b, n * v4) ||
@@ -659,11 +660,12 @@ int tersoff_compute(tersoff_ctx *ctx, const double *pos, const int32_t *types, i
   CKR(check_common(ctx, pos, N, box));
   if (!P) return set_err(ctx, TERSOFF_ERR_ARG, "null parameters");
   if (N > 0 && !types) return set_err(ctx, TERSOFF_ERR_ARG, "null types");
-  if (prec != TERSOFF_FP64 && prec != TERSOFF_MIXED) return set_err(ctx, TERSOFF_ERR_ARG, "bad precision");
+  if (prec != TERSOFF_FP64 && prec != TERSOFF_MIXED && prec != TERSOFF_SINGLE)
+    return set_err(ctx, TERSOFF_ERR_ARG, "bad precision");
   if (nl && nl->list.N != N) return set_err(ctx, TERSOFF_ERR_ARG, "list built for %lld atoms, not %lld", (long long)nl->list.N, (long long)N);
   if (nl && nl->list.cutoff < P->rcmax) return set_err(ctx, TERSOFF_ERR_ARG, "list cutoff below the table's cutoff");
   cudaSetDevice(ctx->device);
-  const bool mixed = prec == TERSOFF_MIXED;
+  const bool f32 = prec != TERSOFF_FP64;
   const bool dev = flags & TERSOFF_DEVICE_PTRS;
   AtomState &A = ctx->cstate;
   RunState *rs = ctx->crs;
@@ -679,11 +681,11 @@ int tersoff_compute(tersoff_ctx *ctx, const double *pos, const int32_t *types, i
     for (int a = 0; a < 3; ++a)
       if (nl->list.geo.L[a] != box[a]) return set_err(ctx, TERSOFF_ERR_ARG, "list built for another box");
   }
-  CKR(ensure_scatter(ctx, A, N, L->cap, mixed));
+  CKR(ensure_scatter(ctx, A, N, L->cap, f32));
   const int gen_slots = force_slots_for(std::max(1, L->maxcount));
   const int fast_slots = (P->sym_angular && !ctx->general_only) ? (L->maxcount <= 4 ? 4 : 8) : 0;
-  CK(launch_force(ctx->stream, mixed, fast_slots, P->nt == 1, gen_slots, 1, virial != nullptr, (int)N, A.x, A.q,
-                  L->nbr, L->cnt, ctx->csys.tab, mixed ? P->pair_f : P->pair_d, mixed ? P->trip_f : P->trip_d, P->nt,
+  CK(launch_force(ctx->stream, prec, fast_slots, P->nt == 1, gen_slots, 1, virial != nullptr, (int)N, A.x, A.q,
+                  L->nbr, L->cnt, ctx->csys.tab, f32 ? P->pair_f : P->pair_d, f32 ? P->trip_f : P->trip_d, P->nt,
                   A.contrib, A.selfF, A.mask, A.work, A.nwork, A.partial, rs, nullptr));
   double *dF = nullptr;
   if (forces) {
@@ -695,7 +697,7 @@ int tersoff_compute(tersoff_ctx *ctx, const double *pos, const int32_t *types, i
         return set_err(ctx, TERSOFF_ERR_NOMEM, "staging buffer");
       dF = (double *)ctx->stage;
     }
-    CK(launch_gather_out(ctx->stream, mixed, (int)N, A.contrib, A.selfF, A.mask, L->rev, dF, rs));
+    CK(launch_gather_out(ctx->stream, prec, (int)N, A.contrib, A.selfF, A.mask, L->rev, dF, rs));
   }
   RunState h;
   CKR(read_rs(ctx, rs, &h));
@@ -751,9 +753,9 @@ static int md_force(tersoff_md *md, cudaStream_t st, int eflag, int part = 3, in
 {
   tersoff_ctx *ctx = md->ctx;
   const tersoff_params *P = md->params;
-  CK(launch_force_part(part, st, md->mixed, md->fast_slots, P->nt == 1, md->gen_slots, eflag, 0, (int)md->atoms.N, md->atoms.x,
-                  md->atoms.q, md->list.nbr, md->list.cnt, md->sys.tab, md->mixed ? P->pair_f : P->pair_d,
-                  md->mixed ? P->trip_f : P->trip_d, P->nt, md->atoms.contrib, md->atoms.selfF, md->atoms.mask,
+  CK(launch_force_part(part, st, md->prec, md->fast_slots, P->nt == 1, md->gen_slots, eflag, 0, (int)md->atoms.N, md->atoms.x,
+                  md->atoms.q, md->list.nbr, md->list.cnt, md->sys.tab, md->f32 ? P->pair_f : P->pair_d,
+                  md->f32 ? P->trip_f : P->trip_d, P->nt, md->atoms.contrib, md->atoms.selfF, md->atoms.mask,
                   md->atoms.work, md->atoms.nwork, md->atoms.partial, md->rs, nullptr, md->routed ? &md->routes : nullptr, stats));
   return TERSOFF_OK;
 }
@@ -763,7 +765,7 @@ static int md_vv(tersoff_md *md, cudaStream_t st, int mode, bool ke)
 {
   tersoff_ctx *ctx = md->ctx;
   const float lim = (float)(0.25 * md->skin * md->skin);
-  CK(launch_vv(st, md->mixed, ke, (int)md->atoms.N, mode, md->atoms.x, md->atoms.v, md->atoms.q, md->list.qref,
+  CK(launch_vv(st, md->prec, ke, (int)md->atoms.N, mode, md->atoms.x, md->atoms.v, md->atoms.q, md->list.qref,
                md->atoms.contrib, md->atoms.selfF, md->atoms.mask, md->list.rev, md->sys.tab,
                md->sys.ctl, md->params->d_mass, lim, md->atoms.kepart, md->rs));
   return TERSOFF_OK;
@@ -922,7 +924,7 @@ static int md_recover(tersoff_md *md, const RunState &h, double *d_trace)
     int cap = std::min(MAX_CAP, ((h.maxcount + std::max(4, h.maxcount / 4)) + 3) & ~3);
     md_graphs_free(md);
     CKR(ensure_list(ctx, md->list, md->atoms.N, cap, md->list.grid.ncell));
-    CKR(ensure_scatter(ctx, md->atoms, md->atoms.N, cap, md->mixed));
+    CKR(ensure_scatter(ctx, md->atoms, md->atoms.N, cap, md->f32));
     CK(cudaMemsetAsync(&md->rs->status, 0, sizeof(int), st));
     CKR(md_build(md, st, 0, true));
   } else if (h.status & ST_NC_OVERFLOW) {
@@ -969,7 +971,8 @@ int tersoff_md_create(tersoff_ctx *ctx, const double *pos, const double *vel, co
   CKR(check_common(ctx, pos, N, box));
   if (!out || !P || (N > 0 && (!vel || !types))) return set_err(ctx, TERSOFF_ERR_ARG, "null argument");
   if (!(dt_ps > 0) || !(skin >= 0)) return set_err(ctx, TERSOFF_ERR_ARG, "need dt > 0 and skin >= 0");
-  if (prec != TERSOFF_FP64 && prec != TERSOFF_MIXED) return set_err(ctx, TERSOFF_ERR_ARG, "bad precision");
+  if (prec != TERSOFF_FP64 && prec != TERSOFF_MIXED && prec != TERSOFF_SINGLE)
+    return set_err(ctx, TERSOFF_ERR_ARG, "bad precision");
   *out = nullptr;
   cudaSetDevice(ctx->device);
   tersoff_md *md = new (std::nothrow) tersoff_md();
@@ -979,7 +982,8 @@ int tersoff_md_create(tersoff_ctx *ctx, const double *pos, const double *vel, co
   md->params = P;
   md->dt = dt_ps;
   md->skin = skin;
-  md->mixed = prec == TERSOFF_MIXED;
+  md->prec = prec;
+  md->f32 = prec != TERSOFF_FP64;
   auto fail = [&](int rc) {
     tersoff_md_destroy(md);
     return rc;
@@ -1008,7 +1012,7 @@ int tersoff_md_create(tersoff_ctx *ctx, const double *pos, const double *vel, co
   for (int a = 0; a < MAX_TYPES; ++a) md->sys.host.kick[a] = a < P->nt ? 0.5 * dt_ps * ACCEL / P->masses[a] : 0.0;
   if ((rc = build_list_sync(ctx, md->atoms, md->list, md->rs, box, P->rcmax, skin, md->sys)) != TERSOFF_OK)
     return fail(rc);
-  if ((rc = ensure_scatter(ctx, md->atoms, N, md->list.cap, md->mixed)) != TERSOFF_OK) return fail(rc);
+  if ((rc = ensure_scatter(ctx, md->atoms, N, md->list.cap, md->f32)) != TERSOFF_OK) return fail(rc);
   md->gen_slots = force_slots_for(std::max(1, md->list.maxcount));
   md->fast_slots = (P->sym_angular && !ctx->general_only) ? 8 : 0;
   if ((rc = md_force(md, ctx->stream, 1, 3, 1)) != TERSOFF_OK) return fail(rc);
@@ -1151,7 +1155,7 @@ int tersoff_md_get(tersoff_md *md, double *pos, double *vel, double *forces, int
   int rc = TERSOFF_OK;
   if (launch_extract(ctx->stream, (int)N, md->atoms.x, md->atoms.v, dp, dv) != cudaSuccess) rc = TERSOFF_ERR_CUDA;
   if (rc == TERSOFF_OK && df &&
-      launch_gather_out(ctx->stream, md->mixed, (int)N, md->atoms.contrib, md->atoms.selfF, md->atoms.mask,
+      launch_gather_out(ctx->stream, md->prec, (int)N, md->atoms.contrib, md->atoms.selfF, md->atoms.mask,
                         md->list.rev, df, md->rs) != cudaSuccess)
     rc = TERSOFF_ERR_CUDA;
   if (rc == TERSOFF_OK && !dev) {

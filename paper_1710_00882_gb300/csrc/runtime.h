@@ -65,18 +65,18 @@ int scan_tiles_for(int ncell);
 int force_slots_for(int need);
 int force_partial_rows(int N);
 int vv_blocks(int N);
-cudaError_t launch_force(cudaStream_t, bool, int, bool, int, int, int, int, const dbl4 *, const int4 *, const int *,
+cudaError_t launch_force(cudaStream_t, int, int, bool, int, int, int, int, const dbl4 *, const int4 *, const int *,
                          const int *, const SysTab *, const void *, const void *, int, void *, void *,
                          unsigned long long *, int *, int *, double *, RunState *, double *);
-cudaError_t launch_force_part(int, cudaStream_t, bool, int, bool, int, int, int, int, const dbl4 *, const int4 *,
+cudaError_t launch_force_part(int, cudaStream_t, int, int, bool, int, int, int, int, const dbl4 *, const int4 *,
                               const int *, const int *, const SysTab *, const void *, const void *, int, void *, void *,
                               unsigned long long *, int *, int *, double *, RunState *, double *,
                               const ForceRoutes *routes = nullptr, int stats = 1);
 int force_queue_blocks(int N);
-cudaError_t launch_vv(cudaStream_t, bool, bool, int, int, dbl4 *, dbl4 *, int4 *, const int4 *, const void *,
+cudaError_t launch_vv(cudaStream_t, int, bool, int, int, dbl4 *, dbl4 *, int4 *, const int4 *, const void *,
                       const void *, const unsigned long long *, const int *, const SysTab *, SysCtl *,
                       const double *, float, double *, RunState *);
-cudaError_t launch_gather_out(cudaStream_t, bool, int, const void *, const void *, const unsigned long long *,
+cudaError_t launch_gather_out(cudaStream_t, int, int, const void *, const void *, const unsigned long long *,
                               const int *, double *, RunState *);
 cudaError_t launch_ingest(cudaStream_t, int, const double *, const int *, int, int, const SysTab *, dbl4 *, int4 *,
                           RunState *);
@@ -165,7 +165,7 @@ int cuda_err(tersoff_ctx *ctx, cudaError_t e, const char *what);
 int status_to_code(tersoff_ctx *ctx, int st, const RunState &h);
 int new_rs(tersoff_ctx *ctx, RunState **rs);
 int ensure_atoms(tersoff_ctx *ctx, AtomState &A, int64_t N, bool need_v);
-int ensure_scatter(tersoff_ctx *ctx, AtomState &A, int64_t N, int cap, bool mixed);
+int ensure_scatter(tersoff_ctx *ctx, AtomState &A, int64_t N, int cap, bool f32);
 int ensure_list(tersoff_ctx *ctx, ListState &L, int64_t N, int cap, int ncell);
 int check_box(tersoff_ctx *ctx, const double box[3], double rl);
 void ctx_release(tersoff_ctx *ctx);   // drops one reference; frees the context at zero

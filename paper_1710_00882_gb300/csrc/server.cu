@@ -193,7 +193,8 @@ struct tersoff_server {
   tersoff_ctx *ctx = nullptr;   // the caller's context (device, reference held)
   tersoff_ctx priv;             // private context on the scheduler's stream: helpers and errors of the worker
   const tersoff_params *P = nullptr;
-  bool mixed = false;
+  int prec = TERSOFF_FP64;
+  bool f32 = false;             // float32 force arithmetic (mixed or single precision)
   double skin = 0, rl = 0;
   int max_slots = 0, chunk = 0, listcap = 32;
   int64_t cap_atoms = 0;
@@ -261,9 +262,9 @@ int srv_err(tersoff_server *s, int code, const char *fmt, ...)
   return code;
 }
 
-size_t bytes_per_atom(bool mixed, int listcap)
+size_t bytes_per_atom(bool f32, int listcap)
 {
-  const size_t v4 = mixed ? 16 : 32;
+  const size_t v4 = f32 ? 16 : 32;
   return 2 * (32 + 32 + 16)                        // two copies of x, v, q
          + (size_t)listcap * (v4 + 8)              // contrib + nbr/rev
          + v4 + 8 + 8 + 4 + 16 + 12 + 8 + 16;      // selfF, mask, work, cnt, qref, cells, eatom, slack
@@ -298,9 +299,9 @@ int srv_force(tersoff_server *s, cudaStream_t st)
 {
   const tersoff_params *P = s->P;
   AtomState &X = cur_atoms(s);
-  SK(launch_force_part(3, st, s->mixed, s->fast_slots, P->nt == 1, s->gen_slots, 0, 0, (int)s->natoms, X.x, X.q,
-                       s->L.nbr, s->L.cnt, s->S.tab, s->mixed ? P->pair_f : P->pair_d,
-                       s->mixed ? P->trip_f : P->trip_d, P->nt, s->SC.contrib, s->SC.selfF, s->SC.mask, s->SC.work,
+  SK(launch_force_part(3, st, s->prec, s->fast_slots, P->nt == 1, s->gen_slots, 0, 0, (int)s->natoms, X.x, X.q,
+                       s->L.nbr, s->L.cnt, s->S.tab, s->f32 ? P->pair_f : P->pair_d,
+                       s->f32 ? P->trip_f : P->trip_d, P->nt, s->SC.contrib, s->SC.selfF, s->SC.mask, s->SC.work,
                        s->SC.nwork, s->SC.partial, s->rs, s->eatom, nullptr, 0));
   return TERSOFF_OK;
 }
@@ -309,7 +310,7 @@ int srv_vv(tersoff_server *s, cudaStream_t st)
 {
   AtomState &X = cur_atoms(s);
   const float lim = (float)(0.25 * s->skin * s->skin);
-  SK(launch_vv(st, s->mixed, false, (int)s->natoms, -1, X.x, X.v, X.q, s->L.qref, s->SC.contrib, s->SC.selfF,
+  SK(launch_vv(st, s->prec, false, (int)s->natoms, -1, X.x, X.v, X.q, s->L.qref, s->SC.contrib, s->SC.selfF,
                s->SC.mask, s->L.rev, s->S.tab, s->S.ctl, s->P->d_mass, lim, s->SC.kepart, s->rs));
   return TERSOFF_OK;
 }
@@ -409,7 +410,7 @@ int build_and_force(tersoff_server *s)
     const int cap = std::min(MAX_CAP, ((h.maxcount + std::max(4, h.maxcount / 4)) + 3) & ~3);
     graph_free(s);
     if (ensure_list(&s->priv, s->L, s->cap_atoms, cap, std::max(1, s->ncell)) != TERSOFF_OK ||
-        ensure_scatter(&s->priv, s->SC, s->cap_atoms, cap, s->mixed) != TERSOFF_OK)
+        ensure_scatter(&s->priv, s->SC, s->cap_atoms, cap, s->f32) != TERSOFF_OK)
       return srv_err(s, TERSOFF_ERR_NOMEM, "cannot grow neighbour lists to %d entries", cap);
     s->listcap = cap;
     SK(cudaMemsetAsync(&s->rs->status, 0, sizeof(int), s->st));
@@ -780,7 +781,7 @@ int tersoff_server_create(tersoff_ctx *ctx, const tersoff_params *P, tersoff_pre
   if (!ctx || !P || !out) return TERSOFF_ERR_ARG;
   *out = nullptr;
   if (!(skin >= 0) || max_slots < 1 || max_slots > 4096 || chunk_steps < 1 ||
-      (prec != TERSOFF_FP64 && prec != TERSOFF_MIXED))
+      (prec != TERSOFF_FP64 && prec != TERSOFF_MIXED && prec != TERSOFF_SINGLE))
     return set_err(ctx, TERSOFF_ERR_ARG, "bad server arguments");
   cudaSetDevice(ctx->device);
   tersoff_server *s = new (std::nothrow) tersoff_server();
@@ -788,7 +789,8 @@ int tersoff_server_create(tersoff_ctx *ctx, const tersoff_params *P, tersoff_pre
   s->ctx = ctx;
   ctx->refs += 1;
   s->P = P;
-  s->mixed = prec == TERSOFF_MIXED;
+  s->prec = prec;
+  s->f32 = prec != TERSOFF_FP64;
   s->skin = skin;
   s->rl = P->rcmax + skin;
   s->max_slots = max_slots;
@@ -797,7 +799,7 @@ int tersoff_server_create(tersoff_ctx *ctx, const tersoff_params *P, tersoff_pre
   s->fast_slots = (P->sym_angular && !ctx->general_only) ? 8 : 0;
   s->gen_slots = 16;
   s->use_graphs = !(getenv("TERSOFF_GRAPHS") && strcmp(getenv("TERSOFF_GRAPHS"), "0") == 0);
-  s->cap_atoms = (int64_t)(budget / bytes_per_atom(s->mixed, s->listcap));
+  s->cap_atoms = (int64_t)(budget / bytes_per_atom(s->f32, s->listcap));
   auto fail = [&](int rc) {
     tersoff_server_destroy(s);
     return rc;
@@ -813,7 +815,7 @@ int tersoff_server_create(tersoff_ctx *ctx, const tersoff_params *P, tersoff_pre
   if (new_rs(pc, &s->rs) != TERSOFF_OK) return fail(TERSOFF_ERR_NOMEM);
   const int64_t cap = s->cap_atoms;
   if (ensure_atoms(pc, s->A[0], cap, true) != TERSOFF_OK || ensure_atoms(pc, s->A[1], cap, true) != TERSOFF_OK ||
-      ensure_scatter(pc, s->SC, cap, s->listcap, s->mixed) != TERSOFF_OK ||
+      ensure_scatter(pc, s->SC, cap, s->listcap, s->f32) != TERSOFF_OK ||
       ensure_list(pc, s->L, cap, s->listcap, 1) != TERSOFF_OK || !sys_alloc(s->S, max_slots) ||
       cudaMalloc((void **)&s->eatom, sizeof(double) * cap) != cudaSuccess ||
       cudaMalloc((void **)&s->sysE, sizeof(double) * 2 * max_slots) != cudaSuccess ||

@@ -31,6 +31,7 @@ ERR_NOT_FOUND = -9
 
 FP64 = 0
 MIXED = 1
+SINGLE = 2
 
 NOALLOC_MAX_ATOMS = 16384   # TERSOFF_NOALLOC_MAX_ATOMS
 

@@ -2,7 +2,9 @@
 
 Tolerances: FP64 energy rel <= 1e-12, force max-abs <= 1e-10 eV/A; mixed
 energy rel <= 1e-6, force max-abs <= 1e-4 eV/A (the accuracy targets the
-workloads are specified with).  Virial: 1e-10 (FP64) / 1e-5 (mixed) eV per atom.
+workloads are specified with); single (float32 throughout) energy rel <= 1e-5,
+force max-abs <= 1e-3 eV/A (derived in gpu_common).  Virial: 1e-10 (FP64) / 1e-5
+(mixed) / 1e-4 (single) eV per atom.
 """
 import numpy as np
 import pytest
@@ -10,8 +12,8 @@ import pytest
 from oracle import oracle
 from paper_1710_00882_gb300 import workloads as wl
 
-from gpu_common import (FP64_E_REL, FP64_F_ABS, MIX_E_REL, MIX_F_ABS, assert_parity, oracle_table,
-                        product_params)
+from gpu_common import (FP64_E_REL, FP64_F_ABS, MIX_E_REL, MIX_F_ABS, SGL_E_REL, SGL_F_ABS, assert_parity,
+                        oracle_table, product_params)
 
 pytestmark = pytest.mark.gpu
 
@@ -35,7 +37,7 @@ def run_pair(T, ctx, s, species=None, prec=None, **kw):
     tab, _ = oracle_table(species, **kw)
     Eo, Fo, Wo = oracle.energy_forces(s.pos, s.types, s.box, tab)
     out = {}
-    for p in ([prec] if prec is not None else [T.FP64, T.MIXED]):
+    for p in ([prec] if prec is not None else [T.FP64, T.MIXED, T.SINGLE]):
         E, F, W = T.compute(ctx, P, s.pos, s.types, s.box, prec=p)
         out[p] = (E, F, W)
     return out, (Eo, Fo, Wo)
@@ -43,7 +45,8 @@ def run_pair(T, ctx, s, species=None, prec=None, **kw):
 
 def check(T, out, ref, what, mixed_f_rel=None):
     """mixed_f_rel: for stress cases with forces far above the workloads' (|F| up to
-    ~50 eV/A), bound the mixed force error relative to the largest force instead."""
+    ~50 eV/A), bound the mixed force error relative to the largest force instead (10x
+    that for single mode)."""
     Eo, Fo, Wo = ref
     if T.FP64 in out:
         E, F, W = out[T.FP64]
@@ -52,6 +55,10 @@ def check(T, out, ref, what, mixed_f_rel=None):
         E, F, W = out[T.MIXED]
         fa = MIX_F_ABS if mixed_f_rel is None else max(MIX_F_ABS, mixed_f_rel * np.abs(Fo).max())
         assert_parity(E, F, W, Eo, Fo, Wo, MIX_E_REL, fa, 1e-5, what + " mixed")
+    if T.SINGLE in out:
+        E, F, W = out[T.SINGLE]
+        fa = SGL_F_ABS if mixed_f_rel is None else max(SGL_F_ABS, 10 * mixed_f_rel * np.abs(Fo).max())
+        assert_parity(E, F, W, Eo, Fo, Wo, SGL_E_REL, fa, 1e-4, what + " single")
 
 
 def test_si_512_config(T, ctx):
@@ -119,7 +126,8 @@ def test_edge_cases(T, ctx):
         Eo, Fo, Wo = oracle.energy_forces(pos, types, box, oracle_table(("Si",))[0])
         # a lone bond's energy f_R + f_A is ~5x smaller than its two terms, so the
         # float32 bound on it is looser than the workloads' 1e-6
-        for prec, (er, fa) in ((T.FP64, (FP64_E_REL, FP64_F_ABS)), (T.MIXED, (5e-6, MIX_F_ABS))):
+        for prec, (er, fa) in ((T.FP64, (FP64_E_REL, FP64_F_ABS)), (T.MIXED, (5e-6, MIX_F_ABS)),
+                               (T.SINGLE, (5e-5, SGL_F_ABS))):
             E, F, W = T.compute(ctx, P, pos, types, box, prec=prec)
             if Eo == 0.0:
                 assert E == 0.0 and np.all(F == 0)
@@ -149,7 +157,7 @@ def test_errors_are_reported(T, ctx):
 def test_deterministic(T, ctx):
     s = wl.sic_box(5, seed=47, T=1500.0)
     P = product_params(ctx, s.species)
-    for prec in (T.FP64, T.MIXED):
+    for prec in (T.FP64, T.MIXED, T.SINGLE):
         E1, F1, W1 = T.compute(ctx, P, s.pos, s.types, s.box, prec=prec)
         E2, F2, W2 = T.compute(ctx, P, s.pos, s.types, s.box, prec=prec)
         assert np.array_equal(F1, F2)
@@ -208,13 +216,13 @@ def test_full_size_si_512k(T, ctx):
 
 @pytest.mark.slow
 def test_full_size_sic_950k(T, ctx):
-    """The 3C-SiC box at full size (950,000 atoms), mixed and FP64, against the oracle."""
+    """The 3C-SiC box at full size (950,000 atoms), in all three precisions, against the oracle."""
     s = wl.sic_1m()
     out, ref = run_pair(T, ctx, s)
     check(T, out, ref, "sic950k")
 
 
-@pytest.mark.parametrize("prec_name", ["FP64", "MIXED"])
+@pytest.mark.parametrize("prec_name", ["FP64", "MIXED", "SINGLE"])
 def test_register_and_general_kernels_agree(T, prec_name, monkeypatch):
     """The register kernel (unordered neighbour pairs, overflow queue) and the general
     kernel (ordered pairs, shared-memory slots) on a SiC box where Si atoms exceed 8
@@ -230,5 +238,7 @@ def test_register_and_general_kernels_agree(T, prec_name, monkeypatch):
     E2, F2, W2 = T.compute(c2, P2, s.pos, s.types, s.box, prec=prec)
     if prec == T.FP64:
         assert abs(E1 - E2) <= 1e-13 * abs(E2) and np.abs(F1 - F2).max() < 1e-11
-    else:
+    elif prec == T.MIXED:
         assert abs(E1 - E2) <= 1e-6 * abs(E2) and np.abs(F1 - F2).max() < 1e-4
+    else:
+        assert abs(E1 - E2) <= 1e-5 * abs(E2) and np.abs(F1 - F2).max() < 1e-3

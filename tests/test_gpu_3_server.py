@@ -10,7 +10,7 @@ import pytest
 from oracle import oracle
 from paper_1710_00882_gb300 import workloads as wl
 
-from gpu_common import MIX_E_REL, oracle_table, product_params
+from gpu_common import MIX_E_REL, SGL_E_REL, oracle_table, product_params
 
 pytestmark = pytest.mark.gpu
 
@@ -58,7 +58,7 @@ def run_jobs(T, ctx, P, jobs, prec, chunk=7, budget=1 << 28, slots=16, stagger=F
     return out, st
 
 
-@pytest.mark.parametrize("prec_name", ["FP64", "MIXED"])
+@pytest.mark.parametrize("prec_name", ["FP64", "MIXED", "SINGLE"])
 def test_job_result_independent_of_batch(T, ctx, P, prec_name):
     prec = getattr(T, prec_name)
     jobs = jobs_mix()
@@ -85,17 +85,17 @@ def test_fp64_job_matches_oracle(T, ctx, P):
         assert abs(ekin - tro[-1, 1]) <= 1e-9 * abs(tro[-1, 1])
 
 
-@pytest.mark.parametrize("prec_name", ["FP64", "MIXED"])
+@pytest.mark.parametrize("prec_name", ["FP64", "MIXED", "SINGLE"])
 def test_job_matches_single_system_md(T, ctx, P, prec_name):
     prec = getattr(T, prec_name)
     jobs = jobs_mix()
     res, _ = run_jobs(T, ctx, P, jobs, prec)
-    tol = 1e-9 if prec == T.FP64 else 1e-6
+    tol = {T.FP64: 1e-9, T.MIXED: 1e-6, T.SINGLE: 1e-5}[prec]
     for (s, dt, n), (p, v, (epot, ekin), _) in zip(jobs, res):
         pr, vr, tr = T.md_run(ctx, P, s.pos, s.vel, s.types, s.box, dt, n, 0.3, prec=prec)
         assert np.abs(p - pr).max() < tol
         assert np.abs(v - vr).max() < 20 * tol
-        assert abs(epot - tr[-1, 0]) <= (1e-10 if prec == T.FP64 else MIX_E_REL) * abs(tr[-1, 0])
+        assert abs(epot - tr[-1, 0]) <= {T.FP64: 1e-10, T.MIXED: MIX_E_REL, T.SINGLE: SGL_E_REL}[prec] * abs(tr[-1, 0])
 
 
 def test_admission_limited_by_budget_and_slots(T, ctx, P):

@@ -13,7 +13,7 @@ import pytest
 
 from paper_1710_00882_gb300 import workloads as wl
 
-from gpu_common import FP64_E_REL, FP64_F_ABS, MIX_E_REL, MIX_F_ABS, product_params
+from gpu_common import FP64_E_REL, FP64_F_ABS, MIX_E_REL, MIX_F_ABS, SGL_E_REL, SGL_F_ABS, product_params
 
 pytestmark = pytest.mark.gpu
 
@@ -57,10 +57,11 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("prec_name", ["FP64", "MIXED"])
+@pytest.mark.parametrize("prec_name", ["FP64", "MIXED", "SINGLE"])
 def test_noalloc_matches_compute_twice(T, ctx, prec_name):
     prec = getattr(T, prec_name)
-    e_rel, f_abs = (FP64_E_REL, FP64_F_ABS) if prec == T.FP64 else (MIX_E_REL, MIX_F_ABS)
+    e_rel, f_abs = {T.FP64: (FP64_E_REL, FP64_F_ABS), T.MIXED: (MIX_E_REL, MIX_F_ABS),
+                    T.SINGLE: (SGL_E_REL, SGL_F_ABS)}[prec]
     # the cases run one after another, so each call finds the previous call's data in the array
     for name, make, species in CASES:
         s = make()
