@@ -124,6 +124,18 @@ double tersoff_params_cutoff(const tersoff_params *p);
  * normally tersoff_params_cutoff(); `skin` >= 0. */
 int tersoff_neighbor_build(tersoff_ctx *ctx, const double *pos, int64_t N, const double box[3], double cutoff,
                            double skin, int flags, tersoff_nlist **inout);
+/* The same list with one radius per type pair: j is listed for i when the
+ * minimum-image distance is < r_C(t_i, t_j) + skin, r_C = R + D of the table's
+ * row (t_i, t_j, t_j) (the larger of the rows (a,b,b) and (b,a,a), so that the lists
+ * stay symmetric).  This is the list tersoff_compute, the MD driver and the
+ * server build internally.  Its pairs within r_C are those of the one-radius
+ * list with cutoff = tersoff_params_cutoff(); pairs of types with a shorter r_C
+ * carry a shorter skin shell (in 3C-SiC the C-C second shell, 3.08 A, drops out of
+ * the C lists).  The list is valid for `params` (or tables whose r_C are no
+ * larger).  types: [N] in [0, ntypes). */
+int tersoff_neighbor_build_typed(tersoff_ctx *ctx, const double *pos, const int32_t *types, int64_t N,
+                                 const double box[3], const tersoff_params *params, double skin, int flags,
+                                 tersoff_nlist **inout);
 void tersoff_nlist_destroy(tersoff_nlist *nl);
 /* copy a built list to host arrays: counts[N] and idx[N * (*stride)] (row i
  * at idx + i*stride, first counts[i] entries valid).  Call with idx == NULL to

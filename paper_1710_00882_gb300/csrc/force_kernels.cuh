@@ -275,8 +275,9 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
 
   const int t = threadIdx.x;
   const int tg = blockIdx.x * T + t;
-  const bool active = tg < count;
-  const int i = active ? (order ? order[begin + tg] : begin + tg) : 0;
+  // (both reassigned by the count sort of the 8-slot kernels, below)
+  bool active = tg < count;
+  int i = active ? (order ? order[begin + tg] : begin + tg) : 0;
   const int fb = block_base + (int)blockIdx.x;   // this block's queue and partial-sum row
 
   int ti = 0;
@@ -302,7 +303,9 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
   // outside the cutoff get f_C = f_C' = 0 and contribute nothing) and every load is
   // issued in one unrolled burst.  Otherwise the list is packed: a first pass marks
   // in-cutoff entries, the second loads them into consecutive slots.
-  const bool direct = active && n <= MAXNC;
+  // (8-slot kernels always pack: their atoms change threads before the slots are filled)
+  constexpr bool SORT = MAXNC == 8;
+  const bool direct = !SORT && active && n <= MAXNC;
 
   R ux[MAXNC], uy[MAXNC], uz[MAXNC], rr[MAXNC], rl[MAXNC], ir[MAXNC], fc[MAXNC], dfc[MAXNC];
   int meta[MAXNC];
@@ -414,7 +417,7 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
     }
     nc_all = __popcll(mb);
   }
-  const bool over = !direct && nc_all > MAXNC;
+  bool over = !direct && nc_all > MAXNC;
   // queue atoms with too many neighbours, per block and in thread order
   {
     const unsigned bal = __ballot_sync(0xffffffffu, over);
@@ -448,6 +451,52 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
       unsigned bm = 0;
       for (int w = 0; w < T / 32; ++w) bm = max(bm, smax[w][t]);
       if (bm > 0) atomicMax(t == MAX_TYPES ? &rs->maxnc : &rs->maxnc_t[t], (int)bm);
+    }
+  }
+  if (SORT) {
+    // Count sort of the block's atoms (8-slot kernels): the unrolled pair loops below
+    // run, per warp, up to the largest in-cutoff count of its lanes, and counts of 4..8
+    // mixed in one warp make every warp run all 28 pairs.  The atoms this block
+    // evaluates are reassigned to threads in order of their count (stable: ties keep
+    // thread order), so each warp holds similar counts.  An atom's result does not
+    // depend on the thread that evaluates it.
+    constexpr int NK = MAXNC + 2;   // keys 0..MAXNC; MAXNC + 1: not evaluated here
+    __shared__ int s_cnt[T / 32][NK];
+    __shared__ int s_atom[T];
+    __shared__ unsigned long long s_mb[T];
+    const int lane = t & 31, w = t >> 5;
+    const int key = (active && !over) ? nc_all : MAXNC + 1;
+    int r = 0;
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+      const unsigned b = __ballot_sync(0xffffffffu, key == k);
+      if (lane == 0) s_cnt[w][k] = __popc(b);
+      if (key == k) r = __popc(b & ((1u << lane) - 1u));
+    }
+    __syncthreads();
+    for (int k = 0; k < key; ++k)
+      for (int v = 0; v < T / 32; ++v) r += s_cnt[v][k];
+    for (int v = 0; v < w; ++v) r += s_cnt[v][key];
+    s_atom[r] = key <= MAXNC ? i : -1;
+    s_mb[r] = mb;
+    __syncthreads();
+    const int inew = s_atom[t];
+    active = inew >= 0;
+    over = false;
+    i = active ? inew : 0;
+    mb = active ? s_mb[t] : 0ull;
+    nc_all = __popcll(mb);
+    if (active) {
+      int wn;
+      if (MIXED) {
+        qi = q[i];
+        wn = qi.w;
+      } else {
+        xi = x[i];
+        wn = (int)__double_as_longlong(xi.w);
+      }
+      ti = type_of(wn);
+      gp = &sys[sys_of(wn)].geo;
     }
   }
   // slots in use: the whole list on the direct path, the packed in-cutoff entries else

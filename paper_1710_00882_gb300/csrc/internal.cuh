@@ -161,10 +161,23 @@ struct SysCtl {
   int rebuild;              // some atom of this system moved skin/2 since its last list build
 };
 
+// Squared neighbour-list radius per type pair, (r_C(a,b) + skin)^2 with a small
+// safety margin, float32 and symmetric (rl2[a][b] == rl2[b][a]), so that the pairs
+// (i,j) and (j,i) are decided identically.
+struct PairRadii {
+  float rl2[MAX_TYPES * MAX_TYPES];
+};
+
+// Atom record of the cell-ordered copy used by the list build: fixed-point x, y, z
+// and, in w, the atom index in the low CELL_IDX_BITS bits with its type above them.
+constexpr int CELL_IDX_BITS = 30;
+constexpr int CELL_IDX_MASK = (1 << CELL_IDX_BITS) - 1;
+constexpr int64_t MAX_LIST_ATOMS = CELL_IDX_MASK;   // atoms per neighbour list
+
 struct CellGrid {
   int nc[3];
   int ncell;
-  float rl2;      // (cutoff + skin)^2 with a small safety margin
+  PairRadii radii;   // list radius per type pair
 };
 
 }  // namespace tsf

@@ -9,7 +9,8 @@
 //   k_cell_count  -> cell of each atom, rank inside its cell (atomic)
 //   k_scan_*      -> exclusive scan of the cell counts (three-phase block scan)
 //   k_cell_fill   -> atoms in cell order
-//   k_build       -> per atom: half stencil, each pair within r_list appended to both lists
+//   k_build       -> per atom: half stencil, each pair within its type pair's list
+//                    radius r_C(ti,tj) + skin appended to both lists
 //   k_sort_lists  -> each list sorted by j; overflow check
 //   k_reverse     -> for each entry (i,s) the flat index of i's slot in j's list
 #include "internal.cuh"
@@ -139,8 +140,8 @@ __global__ void k_scan_add(int n, int *__restrict__ out, const int *__restrict__
   counts[i] = 0;
 }
 
-// atoms in cell order, each with its fixed-point position: the stencil scan of
-// k_build then reads candidates as contiguous runs
+// atoms in cell order, each with its fixed-point position and its type: the stencil
+// scan of k_build then reads candidates as contiguous runs
 __global__ void k_cell_fill(int N, const int4 *__restrict__ q, const int *__restrict__ cell_of,
                             const int *__restrict__ rank, const int *__restrict__ cell_start,
                             int4 *__restrict__ cell_atoms, const RunState *rs, int gated)
@@ -149,7 +150,7 @@ __global__ void k_cell_fill(int N, const int4 *__restrict__ q, const int *__rest
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const int4 p = q[i];
-  cell_atoms[cell_start[cell_of[i]] + rank[i]] = make_int4(p.x, p.y, p.z, i);
+  cell_atoms[cell_start[cell_of[i]] + rank[i]] = make_int4(p.x, p.y, p.z, i | (type_of(p.w) << CELL_IDX_BITS));
 }
 
 // Stencil range along one axis: 3 neighbouring cells, or every cell when the axis
@@ -211,25 +212,31 @@ __device__ __forceinline__ void add_pair(int i, int j, int N, int cap, int *__re
 }
 
 // One thread per atom, atoms taken in cell order (threads of a warp share most of
-// their stencil cells, so candidate loads hit L1).  Each pair within r_list is found
-// once and appended to both lists: atom i scans its own cell (j > i) and the 13
+// their stencil cells, so candidate loads hit L1).  Each pair within its type pair's
+// list radius is found once and appended to both lists: atom i scans its own cell (j > i) and the 13
 // "forward" neighbour cells (dz = +1; dz = 0, dy = +1; dz = dy = 0, dx = +1), which
 // with every axis >= 3 cells hold each neighbouring cell pair exactly once.  A
 // system with an axis of fewer than 3 cells scans its whole (deduplicated) stencil
 // and keeps j > i.  Candidates of one stencil row are one run of cell_atoms (two
 // where the row wraps).
 __global__ void __launch_bounds__(128) k_build(int N, const int4 *__restrict__ q, const SysTab *__restrict__ sys,
-                                               const SysCtl *__restrict__ ctl, float rl2,
+                                               const SysCtl *__restrict__ ctl, PairRadii radii,
                                                const int *__restrict__ cell_start,
                                                const int4 *__restrict__ cell_atoms, int *__restrict__ nbr,
                                                int *__restrict__ cnt, int cap, int4 *__restrict__ qref, RunState *rs,
                                                int gated)
 {
+  __shared__ float s_rl2[MAX_TYPES * MAX_TYPES];
   if (skip_build(rs, gated)) return;
+#pragma unroll
+  for (int k = 0; k < MAX_TYPES * MAX_TYPES; ++k)
+    if (threadIdx.x == k) s_rl2[k] = radii.rl2[k];
+  __syncthreads();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= N) return;
-  const int i = cell_atoms[t].w;
+  const int i = cell_atoms[t].w & CELL_IDX_MASK;
   const int4 pi = q[i];
+  const float *lim = s_rl2 + type_of(pi.w) * MAX_TYPES;   // row of i's type
   // per-system builds: a system none of whose atoms moved skin/2 keeps its lists
   if (ctl && ctl[sys_of(pi.w)].rebuild == 0) return;
   qref[i] = pi;
@@ -247,15 +254,16 @@ __global__ void __launch_bounds__(128) k_build(int N, const int4 *__restrict__ q
     for (int u = b; u < e; u += 4) {
       int4 pj[4];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) pj[k] = u + k < e ? cell_atoms[u + k] : make_int4(0, 0, 0, -1);
+      for (int k = 0; k < 4; ++k) pj[k] = u + k < e ? cell_atoms[u + k] : make_int4(0, 0, 0, 0);
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        const int j = pj[k].w;
+        const int j = pj[k].w & CELL_IDX_MASK;
+        const int tj = (int)((unsigned)pj[k].w >> CELL_IDX_BITS);
         const float dx = q_scaled(qdiff(pj[k].x, pi.x), s0);
         const float dy = q_scaled(qdiff(pj[k].y, pi.y), s1);
         const float dz = q_scaled(qdiff(pj[k].z, pi.z), s2);
         const float r2 = r2_decide(dx, dy, dz);
-        if (j > i && r2 < rl2) add_pair(i, j, N, cap, nbr, cnt, nf);
+        if (u + k < e && j > i && r2 < lim[tj]) add_pair(i, j, N, cap, nbr, cnt, nf);
       }
     }
   };
@@ -285,15 +293,16 @@ __global__ void __launch_bounds__(128) k_build(int N, const int4 *__restrict__ q
       for (int u = b; u < e; u += 4) {
         int4 pj[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) pj[k] = u + k < e ? cell_atoms[u + k] : make_int4(0, 0, 0, -1);
+        for (int k = 0; k < 4; ++k) pj[k] = u + k < e ? cell_atoms[u + k] : make_int4(0, 0, 0, 0);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          const int j = pj[k].w;
+          const int j = pj[k].w & CELL_IDX_MASK;
+          const int tj = (int)((unsigned)pj[k].w >> CELL_IDX_BITS);
           const float dx = q_scaled(qdiff(pj[k].x, pi.x), s0);
           const float dy = q_scaled(qdiff(pj[k].y, pi.y), s1);
           const float dz = q_scaled(qdiff(pj[k].z, pi.z), s2);
           const float r2 = r2_decide(dx, dy, dz);
-          if (j >= 0 && r2 < rl2) add_pair(i, j, N, cap, nbr, cnt, nf);
+          if (u + k < e && r2 < lim[tj]) add_pair(i, j, N, cap, nbr, cnt, nf);
         }
       }
     };
@@ -458,11 +467,12 @@ __global__ void k_build_done(RunState *rs, int gated)
 namespace tsf {
 
 // Enqueue one list build on st (ctl non-null: only the systems whose rebuild flag is
-// set get new lists; null: every atom).  Buffers: cell_count[ncell] (zero on entry, zero
+// set get new lists; null: every atom).  N <= MAX_LIST_ATOMS; radii: list radius
+// per type pair.  Buffers: cell_count[ncell] (zero on entry, zero
 // on exit), cell_start[ncell+1], tile_sums[ceil(ncell/SCAN_TILE)], cell_atoms[N] (int4),
 // cell_of[N], rank[N]; list nbr/rev [cap][N], cnt[N]; qref[N].
 cudaError_t launch_build(cudaStream_t st, int N, const int4 *q, const SysTab *sys, const SysCtl *ctl, int ncell,
-                         float rl2,
+                         const PairRadii &radii,
                          int *cell_count, int *cell_start, int *tile_sums, int4 *cell_atoms, int *cell_of, int *rank,
                          int *nbr, int *rev, int *cnt, int cap, int4 *qref, RunState *rs, int gated)
 {
@@ -476,7 +486,7 @@ cudaError_t launch_build(cudaStream_t st, int N, const int4 *q, const SysTab *sy
   k_scan_add<<<(ncell + T - 1) / T, T, 0, st>>>(ncell, cell_start, tile_sums, cell_count, rs, gated);
   k_cell_fill<<<BN, T, 0, st>>>(N, q, cell_of, rank, cell_start, cell_atoms, rs, gated);
   const int BN128 = (N + 127) / 128;
-  k_build<<<BN128, 128, 0, st>>>(N, q, sys, ctl, rl2, cell_start, cell_atoms, nbr, cnt, cap, qref, rs, gated);
+  k_build<<<BN128, 128, 0, st>>>(N, q, sys, ctl, radii, cell_start, cell_atoms, nbr, cnt, cap, qref, rs, gated);
   k_sort_lists<<<BN128, 128, 0, st>>>(N, q, ctl, nbr, cnt, cap, rs, gated);
   k_reverse<<<BN128, 128, 0, st>>>(N, q, ctl, nbr, cnt, rev, rs, gated);
   k_build_done<<<1, 1, 0, st>>>(rs, gated);

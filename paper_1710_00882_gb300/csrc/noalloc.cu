@@ -134,7 +134,8 @@ extern "C" int tersoff_compute_noalloc(const tersoff_params *P, const double *po
   }
   // cell grid with cells at least the cutoff wide, coarsened to fit the fixed cell arrays
   CellGrid g;
-  if (make_grid(box, P->rcmax, &g) != TERSOFF_OK) g.rl2 = (float)(P->rcmax * P->rcmax * (1.0 + 1e-5));
+  make_grid(box, P->rcmax, &g);   // a grid over the cell limit is coarsened below
+  g.radii = pair_radii(P, 0.0);
   while ((long long)g.nc[0] * g.nc[1] * g.nc[2] > kMaxCells) {
     int a = 0;
     for (int b = 1; b < 3; ++b)
@@ -184,7 +185,7 @@ extern "C" int tersoff_compute_noalloc(const tersoff_params *P, const double *po
   T.natoms = (int)N;
   NK(cudaMemcpyAsync(sys, &T, sizeof(SysTab), cudaMemcpyHostToDevice, st));
   NK(launch_ingest(st, (int)N, pos, types, P->nt, 0, sys, x, q, rs));
-  NK(launch_build(st, (int)N, q, sys, nullptr, g.ncell, g.rl2, cell_count, cell_start, tile_sums, cell_atoms, cell_of, rank,
+  NK(launch_build(st, (int)N, q, sys, nullptr, g.ncell, g.radii, cell_count, cell_start, tile_sums, cell_atoms, cell_of, rank,
                   nbr, rev, cnt, kCap, qref, rs, 0));
   const int fast_slots = P->sym_angular ? 8 : 0;
   NK(launch_force(st, prec, fast_slots, P->nt == 1, force_slots_for(kCap), 1, 1, (int)N, x, q, nbr, cnt, sys,

@@ -51,8 +51,36 @@ int make_grid(const double box[3], double rl, CellGrid *g)
   }
   if (ncell > (1LL << 30)) return TERSOFF_ERR_ARG;
   g->ncell = (int)ncell;
-  g->rl2 = (float)(rl * rl * (1.0 + 1e-5));
+  g->radii = uniform_radii(rl);
   return TERSOFF_OK;
+}
+
+// Squared list radius with the build's relative safety margin, rounded to float32.
+static float list_rl2(double rl) { return (float)(rl * rl * (1.0 + 1e-5)); }
+
+PairRadii uniform_radii(double rl)
+{
+  PairRadii r;
+  for (int k = 0; k < MAX_TYPES * MAX_TYPES; ++k) r.rl2[k] = list_rl2(rl);
+  return r;
+}
+
+// List radius per type pair: r_C(a,b) + skin, r_C = R + D of row (a,b,b) (the larger
+// of rows (a,b,b) and (b,a,a), so that the table is symmetric whatever the rows
+// hold).  A pair outside its radius at a build cannot come within r_C(a,b) before
+// one of its atoms has moved skin/2, the rebuild criterion, as with one radius.
+// Types the table does not have get the largest radius.
+PairRadii pair_radii(const tersoff_params *P, double skin)
+{
+  PairRadii r = uniform_radii(P->rcmax + skin);
+  const int nt = P->nt;
+  auto rc = [&](int a, int b) {
+    const double *row = &P->entries[(size_t)((a * nt + b) * nt + b) * NFIELDS];
+    return row[F_R] + row[F_DD];
+  };
+  for (int a = 0; a < nt; ++a)
+    for (int b = 0; b < nt; ++b) r.rl2[a * MAX_TYPES + b] = list_rl2(std::max(rc(a, b), rc(b, a)) + skin);
+  return r;
 }
 
 // one-entry system table: allocate device storage
@@ -248,6 +276,9 @@ int ensure_scatter(tersoff_ctx *ctx, AtomState &A, int64_t N, int cap, bool f32)
 int ensure_list(tersoff_ctx *ctx, ListState &L, int64_t N, int cap, int ncell)
 {
   size_t n = (size_t)std::max<int64_t>(N, 1);
+  if (N > MAX_LIST_ATOMS)
+    return set_err(ctx, TERSOFF_ERR_NOMEM, "N=%lld exceeds %lld atoms per neighbour list", (long long)N,
+                   (long long)MAX_LIST_ATOMS);
   // list slots are addressed by 32-bit flat indices (slot * N + atom)
   if (n * (size_t)cap > 0xffffffffull)
     return set_err(ctx, TERSOFF_ERR_NOMEM, "N=%lld x %d list slots exceeds 2^32 entries", (long long)N, cap);
@@ -283,12 +314,13 @@ int check_box(tersoff_ctx *ctx, const double box[3], double rl)
 // Host-visible list build from A.q: grows the capacity on overflow and sizes it to
 // the longest list plus headroom.
 int build_list_sync(tersoff_ctx *ctx, const AtomState &A, ListState &L, RunState *rs, const double box[3],
-                    double cutoff, double skin, SysDev &S)
+                    double cutoff, double skin, SysDev &S, const tersoff_params *P)
 {
   const double rl = cutoff + skin;
   CKR(check_box(ctx, box, rl));
   CellGrid g;
   if (make_grid(box, rl, &g) != TERSOFF_OK) return set_err(ctx, TERSOFF_ERR_ARG, "cell grid too large");
+  if (P) g.radii = pair_radii(P, skin);
   L.grid = g;
   L.geo = make_geom(box);
   L.cutoff = cutoff;
@@ -304,7 +336,7 @@ int build_list_sync(tersoff_ctx *ctx, const AtomState &A, ListState &L, RunState
   for (int attempt = 0; attempt < 3; ++attempt) {
     CKR(ensure_list(ctx, L, A.N, cap, g.ncell));
     CK(cudaMemsetAsync(&rs->maxcount, 0, sizeof(int), ctx->stream));
-    CK(launch_build(ctx->stream, (int)A.N, A.q, S.tab, nullptr, g.ncell, g.rl2, L.cell_count, L.cell_start, L.tile_sums,
+    CK(launch_build(ctx->stream, (int)A.N, A.q, S.tab, nullptr, g.ncell, g.radii, L.cell_count, L.cell_start, L.tile_sums,
                     L.cell_atoms, L.cell_of, L.rank, L.nbr, L.rev, L.cnt, cap, L.qref, rs, 0));
     RunState h;
     CKR(read_rs(ctx, rs, &h));
@@ -563,8 +595,11 @@ double tersoff_params_cutoff(const tersoff_params *P) { return P ? P->rcmax : 0.
 
 // ---------------------------------------------------------------------------
 
-int tersoff_neighbor_build(tersoff_ctx *ctx, const double *pos, int64_t N, const double box[3], double cutoff,
-                           double skin, int flags, tersoff_nlist **inout)
+// Shared body of the two list builders: P null builds every pair within
+// cutoff + skin (types ignored); P non-null builds per type pair within
+// r_C(ti,tj) + skin of P's table (types required).
+static int nlist_build(tersoff_ctx *ctx, const double *pos, const int32_t *types_in, int64_t N, const double box[3],
+                       double cutoff, double skin, const tersoff_params *P, int flags, tersoff_nlist **inout)
 {
   CKR(check_common(ctx, pos, N, box));
   if (!inout) return set_err(ctx, TERSOFF_ERR_ARG, "null list handle");
@@ -588,21 +623,21 @@ int tersoff_neighbor_build(tersoff_ctx *ctx, const double *pos, int64_t N, const
   rc = ensure_atoms(ctx, nl->atoms, N, false);
   if (rc == TERSOFF_OK) rc = check_box(ctx, box, cutoff + skin);
   if (rc == TERSOFF_OK) {
-    // types are irrelevant to the list; pass zeros through the ingest path
+    // without a table the types are irrelevant to the list: pass zeros through the ingest path
     std::vector<int32_t> zeros;
-    const int32_t *types = nullptr;
+    const int32_t *types = types_in;
     void *dz = nullptr;
-    if (flags & TERSOFF_DEVICE_PTRS) {
+    if (!P && (flags & TERSOFF_DEVICE_PTRS)) {
       if (N > 0 && cudaMalloc(&dz, (size_t)N * sizeof(int)) != cudaSuccess) rc = set_err(ctx, TERSOFF_ERR_NOMEM, "types");
       else if (N > 0) cudaMemsetAsync(dz, 0, (size_t)N * sizeof(int), ctx->stream);
       types = (const int32_t *)dz;
-    } else {
+    } else if (!P) {
       zeros.assign((size_t)N, 0);
       types = zeros.data();
     }
     if (rc == TERSOFF_OK)
-      rc = ingest(ctx, nl->atoms, pos, types, N, 1, box, flags & TERSOFF_DEVICE_PTRS, nl->rs, nl->sys);
-    if (rc == TERSOFF_OK) rc = build_list_sync(ctx, nl->atoms, nl->list, nl->rs, box, cutoff, skin, nl->sys);
+      rc = ingest(ctx, nl->atoms, pos, types, N, P ? P->nt : 1, box, flags & TERSOFF_DEVICE_PTRS, nl->rs, nl->sys);
+    if (rc == TERSOFF_OK) rc = build_list_sync(ctx, nl->atoms, nl->list, nl->rs, box, cutoff, skin, nl->sys, P);
     if (dz) {
       cudaStreamSynchronize(ctx->stream);
       cudaFree(dz);
@@ -614,6 +649,22 @@ int tersoff_neighbor_build(tersoff_ctx *ctx, const double *pos, int64_t N, const
   }
   *inout = nl;
   return TERSOFF_OK;
+}
+
+int tersoff_neighbor_build(tersoff_ctx *ctx, const double *pos, int64_t N, const double box[3], double cutoff,
+                           double skin, int flags, tersoff_nlist **inout)
+{
+  return nlist_build(ctx, pos, nullptr, N, box, cutoff, skin, nullptr, flags, inout);
+}
+
+int tersoff_neighbor_build_typed(tersoff_ctx *ctx, const double *pos, const int32_t *types, int64_t N,
+                                 const double box[3], const tersoff_params *params, double skin, int flags,
+                                 tersoff_nlist **inout)
+{
+  if (!ctx) return TERSOFF_ERR_ARG;
+  if (!params) return set_err(ctx, TERSOFF_ERR_ARG, "null parameters");
+  if (N > 0 && !types) return set_err(ctx, TERSOFF_ERR_ARG, "null types");
+  return nlist_build(ctx, pos, types, N, box, params->rcmax, skin, params, flags, inout);
 }
 
 void tersoff_nlist_destroy(tersoff_nlist *nl)
@@ -675,7 +726,7 @@ int tersoff_compute(tersoff_ctx *ctx, const double *pos, const int32_t *types, i
   CKR(ingest(ctx, A, pos, types, N, P->nt, box, dev, rs, ctx->csys));
   const ListState *L = nl ? &nl->list : nullptr;
   if (!L) {
-    CKR(build_list_sync(ctx, A, ctx->clist, rs, box, P->rcmax, 0.0, ctx->csys));
+    CKR(build_list_sync(ctx, A, ctx->clist, rs, box, P->rcmax, 0.0, ctx->csys, P));
     L = &ctx->clist;
   } else {
     for (int a = 0; a < 3; ++a)
@@ -778,7 +829,7 @@ static int md_build(tersoff_md *md, cudaStream_t st, int gated, bool full = fals
   tersoff_ctx *ctx = md->ctx;
   ListState &L = md->list;
   CK(launch_build(st, (int)md->atoms.N, md->atoms.q, md->sys.tab, full ? nullptr : md->sys.ctl, L.grid.ncell,
-                  L.grid.rl2, L.cell_count, L.cell_start, L.tile_sums, L.cell_atoms, L.cell_of, L.rank, L.nbr, L.rev,
+                  L.grid.radii, L.cell_count, L.cell_start, L.tile_sums, L.cell_atoms, L.cell_of, L.rank, L.nbr, L.rev,
                   L.cnt, L.cap, L.qref, md->rs, gated));
   return TERSOFF_OK;
 }
@@ -1010,7 +1061,7 @@ int tersoff_md_create(tersoff_ctx *ctx, const double *pos, const double *vel, co
   }
   md->sys.host.dt = dt_ps;
   for (int a = 0; a < MAX_TYPES; ++a) md->sys.host.kick[a] = a < P->nt ? 0.5 * dt_ps * ACCEL / P->masses[a] : 0.0;
-  if ((rc = build_list_sync(ctx, md->atoms, md->list, md->rs, box, P->rcmax, skin, md->sys)) != TERSOFF_OK)
+  if ((rc = build_list_sync(ctx, md->atoms, md->list, md->rs, box, P->rcmax, skin, md->sys, P)) != TERSOFF_OK)
     return fail(rc);
   if ((rc = ensure_scatter(ctx, md->atoms, N, md->list.cap, md->f32)) != TERSOFF_OK) return fail(rc);
   md->gen_slots = force_slots_for(std::max(1, md->list.maxcount));

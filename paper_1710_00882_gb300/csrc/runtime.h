@@ -59,7 +59,7 @@ struct SysDev {
 namespace tsf {
 
 // launchers defined in the kernel translation units
-cudaError_t launch_build(cudaStream_t, int, const int4 *, const SysTab *, const SysCtl *, int, float, int *, int *,
+cudaError_t launch_build(cudaStream_t, int, const int4 *, const SysTab *, const SysCtl *, int, const PairRadii &, int *, int *,
                          int *, int4 *, int *, int *, int *, int *, int *, int, int4 *, RunState *, int);
 int scan_tiles_for(int ncell);
 int force_slots_for(int need);
@@ -121,6 +121,7 @@ inline bool dreserve(T *&p, size_t &have, size_t bytes)
 
 Geom make_geom(const double box[3]);
 int make_grid(const double box[3], double rl, CellGrid *g);
+PairRadii uniform_radii(double rl);
 bool sys_alloc(SysDev &S, int cap);
 void sys_free(SysDev &S);
 void free_atoms(AtomState &A);
@@ -168,5 +169,6 @@ int ensure_atoms(tersoff_ctx *ctx, AtomState &A, int64_t N, bool need_v);
 int ensure_scatter(tersoff_ctx *ctx, AtomState &A, int64_t N, int cap, bool f32);
 int ensure_list(tersoff_ctx *ctx, ListState &L, int64_t N, int cap, int ncell);
 int check_box(tersoff_ctx *ctx, const double box[3], double rl);
+PairRadii pair_radii(const tersoff_params *P, double skin);
 void ctx_release(tersoff_ctx *ctx);   // drops one reference; frees the context at zero
 }  // namespace tsf

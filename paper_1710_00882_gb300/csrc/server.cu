@@ -196,6 +196,7 @@ struct tersoff_server {
   int prec = TERSOFF_FP64;
   bool f32 = false;             // float32 force arithmetic (mixed or single precision)
   double skin = 0, rl = 0;
+  PairRadii radii{};            // list radius per type pair of the shared table
   int max_slots = 0, chunk = 0, listcap = 32;
   int64_t cap_atoms = 0;
   cudaStream_t st = nullptr, cap_st = nullptr;
@@ -320,8 +321,7 @@ int srv_build(tersoff_server *s, cudaStream_t st, bool full)
 {
   AtomState &X = cur_atoms(s);
   ListState &L = s->L;
-  SK(launch_build(st, (int)s->natoms, X.q, s->S.tab, full ? nullptr : s->S.ctl, s->ncell,
-                  (float)(s->rl * s->rl * (1.0 + 1e-5)), L.cell_count, L.cell_start, L.tile_sums, L.cell_atoms,
+  SK(launch_build(st, (int)s->natoms, X.q, s->S.tab, full ? nullptr : s->S.ctl, s->ncell, s->radii, L.cell_count, L.cell_start, L.tile_sums, L.cell_atoms,
                   L.cell_of, L.rank, L.nbr, L.rev, L.cnt, L.cap, L.qref, s->rs, 0));
   return TERSOFF_OK;
 }
@@ -534,8 +534,7 @@ int launch_steps(tersoff_server *s, long long n)
     SKR(srv_vv(s, s->st));
     AtomState &X = cur_atoms(s);
     ListState &L = s->L;
-    SK(launch_build(s->st, (int)s->natoms, X.q, s->S.tab, s->S.ctl, s->ncell, (float)(s->rl * s->rl * (1.0 + 1e-5)),
-                    L.cell_count, L.cell_start, L.tile_sums, L.cell_atoms, L.cell_of, L.rank, L.nbr, L.rev, L.cnt,
+    SK(launch_build(s->st, (int)s->natoms, X.q, s->S.tab, s->S.ctl, s->ncell, s->radii, L.cell_count, L.cell_start, L.tile_sums, L.cell_atoms, L.cell_of, L.rank, L.nbr, L.rev, L.cnt,
                     L.cap, L.qref, s->rs, 1));
     SKR(srv_force(s, s->st));
     SK(launch_step_end(s->st, s->rs, s->S.ctl, (int)s->batch.size(), 0, 0));
@@ -793,13 +792,14 @@ int tersoff_server_create(tersoff_ctx *ctx, const tersoff_params *P, tersoff_pre
   s->f32 = prec != TERSOFF_FP64;
   s->skin = skin;
   s->rl = P->rcmax + skin;
+  s->radii = pair_radii(P, skin);
   s->max_slots = max_slots;
   s->chunk = chunk_steps;
   s->listcap = 32;
   s->fast_slots = (P->sym_angular && !ctx->general_only) ? 8 : 0;
   s->gen_slots = 16;
   s->use_graphs = !(getenv("TERSOFF_GRAPHS") && strcmp(getenv("TERSOFF_GRAPHS"), "0") == 0);
-  s->cap_atoms = (int64_t)(budget / bytes_per_atom(s->f32, s->listcap));
+  s->cap_atoms = std::min<int64_t>((int64_t)(budget / bytes_per_atom(s->f32, s->listcap)), MAX_LIST_ATOMS);
   auto fail = [&](int rc) {
     tersoff_server_destroy(s);
     return rc;

@@ -67,6 +67,7 @@ tersoff_params_create = _sig("tersoff_params_create", _I, _P, _I, _P, _P, _PP)
 tersoff_params_destroy = _sig("tersoff_params_destroy", None, _P)
 tersoff_params_cutoff = _sig("tersoff_params_cutoff", _D, _P)
 tersoff_neighbor_build = _sig("tersoff_neighbor_build", _I, _P, _P, _I64, _P, _D, _D, _I, _PP)
+tersoff_neighbor_build_typed = _sig("tersoff_neighbor_build_typed", _I, _P, _P, _P, _I64, _P, _P, _D, _I, _PP)
 tersoff_nlist_destroy = _sig("tersoff_nlist_destroy", None, _P)
 tersoff_nlist_get = _sig("tersoff_nlist_get", _I, _P, _P, _P, _P, _P, _P)
 tersoff_compute = _sig("tersoff_compute", _I, _P, _P, _P, _I64, _P, _P, _P, _I, _I, _P, _P, _P)
@@ -204,12 +205,19 @@ class Params:
 
 
 class NeighborList:
-    def __init__(self, ctx, pos, box, cutoff, skin):
+    def __init__(self, ctx, pos, box, cutoff, skin, types=None, params=None):
+        """One radius cutoff + skin (tersoff_neighbor_build), or with `params` and
+        `types` one radius per type pair (tersoff_neighbor_build_typed; cutoff unused)."""
         n = int(pos.shape[0])
         pos = _f64(pos, (n, 3))
         h = ctypes.c_void_p()
-        ctx.check(tersoff_neighbor_build(ctx.h, ptr(pos), n, ptr(_box(box)), float(cutoff), float(skin),
-                                         _dev_flag(pos), ctypes.byref(h)))
+        if params is None:
+            ctx.check(tersoff_neighbor_build(ctx.h, ptr(pos), n, ptr(_box(box)), float(cutoff), float(skin),
+                                             _dev_flag(pos), ctypes.byref(h)))
+        else:
+            types = _i32(types, n)
+            ctx.check(tersoff_neighbor_build_typed(ctx.h, ptr(pos), ptr(types), n, ptr(_box(box)), params.h,
+                                                   float(skin), _dev_flag(pos, types), ctypes.byref(h)))
         self.h, self.ctx, self.n = h, ctx, n
 
     def rebuild(self, pos, box, cutoff, skin):

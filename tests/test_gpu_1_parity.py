@@ -9,7 +9,7 @@ force max-abs <= 1e-3 eV/A (derived in gpu_common).  Virial: 1e-10 (FP64) / 1e-5
 import numpy as np
 import pytest
 
-from oracle import oracle
+from oracle import oracle, params as oparams
 from paper_1710_00882_gb300 import workloads as wl
 
 from gpu_common import (FP64_E_REL, FP64_F_ABS, MIX_E_REL, MIX_F_ABS, SGL_E_REL, SGL_F_ABS, assert_parity,
@@ -203,6 +203,44 @@ def test_neighbor_list_equals_brute_force(T, ctx, seed, box_cells, skin):
             dj = np.linalg.norm((s.pos[j] - s.pos[i] + s.box / 2) % s.box - s.box / 2)
             assert dj < (rc + skin) * (1 + 1e-5)
         assert list(idx[i, :counts[i]]) == sorted(got)
+
+
+@pytest.mark.parametrize("seed,cells,skin", [(5, 2, 0.3), (6, 4, 0.3), (7, 3, 0.0), (8, 5, 0.8)])
+def test_typed_neighbor_list_equals_brute_force(T, ctx, seed, cells, skin):
+    """Lists with one radius per type pair (the list the MD driver, the server and
+    tersoff_compute build): j is listed for i exactly when the minimum-image distance
+    is below r_C(t_i, t_j) + skin, with r_C = R + D from the oracle's own table."""
+    s = wl.sic_box(cells, seed=seed, T=2000.0)
+    P = product_params(ctx, s.species)
+    tab, _ = oracle_table(s.species)
+    nt = 2
+    rows = np.asarray(tab).reshape(nt, nt, nt, -1)
+    f_r, f_d = oparams.FIELDS.index("R"), oparams.FIELDS.index("D")
+    rc = np.array([[rows[a, b, b, f_r] + rows[a, b, b, f_d] for b in range(nt)] for a in range(nt)])
+    nl = T.NeighborList(ctx, s.pos, s.box, None, skin, types=s.types, params=P)
+    counts, idx = nl.get()
+    d = s.pos[None, :, :] - s.pos[:, None, :]
+    d -= s.box * np.round(d / s.box)
+    r = np.linalg.norm(d, axis=2)
+    lim = rc[s.types[:, None], s.types[None, :]] + skin
+    np.fill_diagonal(r, np.inf)
+    for i in range(s.n):
+        got = idx[i, :counts[i]]
+        want = np.nonzero(r[i] < lim[i])[0]
+        extra = set(got.tolist()) - set(want.tolist())
+        assert set(want.tolist()) <= set(got.tolist()), f"atom {i}: missing {set(want.tolist()) - set(got.tolist())}"
+        # float32 decisions with the build's 1e-5 relative margin
+        assert all(r[i, j] < lim[i, j] * (1 + 1e-5) for j in extra), f"atom {i}: extra {extra}"
+        assert list(got) == sorted(got)
+    # C atoms keep only their Si neighbours: the C-C second shell (3.08 A, thermal
+    # spread ~0.1 A) lies well beyond r_C(C,C) + skin = 2.1 + skin for skin <= 0.3 A
+    if skin <= 0.3:
+        cnt_c = counts[s.types == 1]
+        assert cnt_c.max() <= 4 and cnt_c.mean() > 3.5
+    # and the typed list gives the oracle's energy and forces
+    Eo, Fo, Wo = oracle.energy_forces(s.pos, s.types, s.box, tab)
+    E, F, W = T.compute(ctx, P, s.pos, s.types, s.box, prec=T.FP64, nlist=nl)
+    assert_parity(E, F, W, Eo, Fo, Wo, FP64_E_REL, FP64_F_ABS, 1e-10, "typed list")
 
 
 @pytest.mark.slow
