@@ -755,58 +755,71 @@ k_force_gen(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
     int nc = 0;
     unsigned long long mbits = 0ull;
     const int n = cnt[i];
-    for (int s = 0; s < n; ++s) {
-      const int j = nbr[(size_t)s * N + i];
-      R dx, dy, dz;
-      int tj;
-      if (MIXED) {
-        const int4 qj = q[j];
-        tj = type_of(qj.w);
-        dx = (R)q_scaled(qdiff(qj.x, qi.x), gp->q_to_f[0]);
-        dy = (R)q_scaled(qdiff(qj.y, qi.y), gp->q_to_f[1]);
-        dz = (R)q_scaled(qdiff(qj.z, qi.z), gp->q_to_f[2]);
-      } else {
-        const dbl4 xj = x[j];
-        tj = type_of((int)__double_as_longlong(xj.w));
-        dx = (R)min_image(__dsub_rn(xj.x, xi.x), gp->L[0], gp->invL[0]);
-        dy = (R)min_image(__dsub_rn(xj.y, xi.y), gp->L[1], gp->invL[1]);
-        dz = (R)min_image(__dsub_rn(xj.z, xi.z), gp->L[2], gp->invL[2]);
+    // GU list entries per round: their index and position loads are issued together
+    constexpr int GU = 4;
+    for (int s0 = 0; s0 < n; s0 += GU) {
+      int jj[GU];
+#pragma unroll
+      for (int k = 0; k < GU; ++k) jj[k] = s0 + k < n ? nbr[(size_t)(s0 + k) * N + i] : i;
+      int4 qq[GU];
+      dbl4 xx[GU];
+#pragma unroll
+      for (int k = 0; k < GU; ++k) {
+        if (MIXED) qq[k] = q[jj[k]];
+        else xx[k] = x[jj[k]];
       }
-      const R r2 = r2_decide(dx, dy, dz);
-      const PairP<R> &P = pairs[ti * nt + tj];
-      if (r2 < P.rc2) {
-        if (nc < MAXNC) {
-          R r, rlo, inv;
-          if (MIXED && M::fine) {
-            const int4 qj = q[j];
-            float dh[3], dl[3];
-            qd_fine(qdiff(qj.x, qi.x), gp->q_to_f[0], gp->q_to_f_lo[0], dh[0], dl[0]);
-            qd_fine(qdiff(qj.y, qi.y), gp->q_to_f[1], gp->q_to_f_lo[1], dh[1], dl[1]);
-            qd_fine(qdiff(qj.z, qi.z), gp->q_to_f[2], gp->q_to_f_lo[2], dh[2], dl[2]);
-            float rh_, rl_, irh_;
-            norm_fine(dh, dl, rh_, rl_, irh_);
-            dx = (R)dh[0]; dy = (R)dh[1]; dz = (R)dh[2];
-            r = (R)rh_; rlo = (R)rl_; inv = (R)irh_;
-          } else {
-            const R rf2 = r2_decide(dx, dy, dz);
-            inv = M::rsqrt(rf2);
-            r = rf2 * inv;
-            rlo = R(0);
-          }
-          R fcv, dfcv;
-          cutoff_fn<M>(r, rlo, P, fcv, dfcv);
-          SLOT(S_UX, nc) = dx * inv;
-          SLOT(S_UY, nc) = dy * inv;
-          SLOT(S_UZ, nc) = dz * inv;
-          SLOT(S_R, nc) = r;
-          SLOT(S_RL, nc) = rlo;
-          SLOT(S_IR, nc) = inv;
-          SLOT(S_FC, nc) = fcv;
-          SLOT(S_DFC, nc) = dfcv;
-          META(nc) = s | (tj << 8);
+#pragma unroll
+      for (int k = 0; k < GU; ++k) {
+        const int s = s0 + k;
+        if (s >= n) continue;
+        R dx, dy, dz;
+        int tj;
+        if (MIXED) {
+          tj = type_of(qq[k].w);
+          dx = (R)q_scaled(qdiff(qq[k].x, qi.x), gp->q_to_f[0]);
+          dy = (R)q_scaled(qdiff(qq[k].y, qi.y), gp->q_to_f[1]);
+          dz = (R)q_scaled(qdiff(qq[k].z, qi.z), gp->q_to_f[2]);
+        } else {
+          tj = type_of((int)__double_as_longlong(xx[k].w));
+          dx = (R)min_image(__dsub_rn(xx[k].x, xi.x), gp->L[0], gp->invL[0]);
+          dy = (R)min_image(__dsub_rn(xx[k].y, xi.y), gp->L[1], gp->invL[1]);
+          dz = (R)min_image(__dsub_rn(xx[k].z, xi.z), gp->L[2], gp->invL[2]);
         }
-        ++nc;
-        mbits |= 1ull << s;
+        const R r2 = r2_decide(dx, dy, dz);
+        const PairP<R> &P = pairs[ti * nt + tj];
+        if (r2 < P.rc2) {
+          if (nc < MAXNC) {
+            R r, rlo, inv;
+            if (MIXED && M::fine) {
+              float dh[3], dl[3];
+              qd_fine(qdiff(qq[k].x, qi.x), gp->q_to_f[0], gp->q_to_f_lo[0], dh[0], dl[0]);
+              qd_fine(qdiff(qq[k].y, qi.y), gp->q_to_f[1], gp->q_to_f_lo[1], dh[1], dl[1]);
+              qd_fine(qdiff(qq[k].z, qi.z), gp->q_to_f[2], gp->q_to_f_lo[2], dh[2], dl[2]);
+              float rh_, rl_, irh_;
+              norm_fine(dh, dl, rh_, rl_, irh_);
+              dx = (R)dh[0]; dy = (R)dh[1]; dz = (R)dh[2];
+              r = (R)rh_; rlo = (R)rl_; inv = (R)irh_;
+            } else {
+              const R rf2 = r2_decide(dx, dy, dz);
+              inv = M::rsqrt(rf2);
+              r = rf2 * inv;
+              rlo = R(0);
+            }
+            R fcv, dfcv;
+            cutoff_fn<M>(r, rlo, P, fcv, dfcv);
+            SLOT(S_UX, nc) = dx * inv;
+            SLOT(S_UY, nc) = dy * inv;
+            SLOT(S_UZ, nc) = dz * inv;
+            SLOT(S_R, nc) = r;
+            SLOT(S_RL, nc) = rlo;
+            SLOT(S_IR, nc) = inv;
+            SLOT(S_FC, nc) = fcv;
+            SLOT(S_DFC, nc) = dfcv;
+            META(nc) = s | (tj << 8);
+          }
+          ++nc;
+          mbits |= 1ull << s;
+        }
       }
     }
     maxnc = max(maxnc, nc);
