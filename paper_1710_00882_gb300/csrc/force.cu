@@ -61,14 +61,15 @@ int force_partial_rows(int N) { return (N + 31) / 32 + 2 + GEN_BLOCKS; }
 int force_queue_blocks(int N) { return (N + FAST_THREADS - 1) / FAST_THREADS + 2; }
 
 // One force evaluation in precision prec (PREC_FP64, PREC_MIXED or PREC_SINGLE).
-// fast_slots 4 or 8 runs the register kernel plus the general kernel (gen_slots
-// wide) over its overflow queue; fast_slots 0 runs the general kernel over all atoms.  routes (may be null: every atom in index order with
-// fast_slots) splits the register kernel into launches over atom subsets, each with
-// its own slot count.  Buffers: partial force_partial_rows(N) x 8 doubles; work
-// force_queue_blocks(N) x 128 ints; nwork force_queue_blocks(N) ints.  With
-// eflag/vflag the energy and virial are added to rs->epot / rs->virial.  part: 1
-// launches the register kernel(s) only, 2 the rest (general kernel and reduction),
-// 3 both.  stats: record the largest in-cutoff counts (rs->maxnc, rs->maxnc_t).
+// fast_slots 4 or 8 runs the register kernel plus the warp kernel over its overflow
+// queue; fast_slots 0 runs the general kernel (gen_slots wide) over all atoms.
+// routes (may be null: every atom in index order with fast_slots) splits the
+// register kernel into launches over atom subsets, each with its own slot count.
+// Buffers: partial force_partial_rows(N) x 8 doubles; work force_queue_blocks(N) x
+// 128 ints; nwork force_queue_blocks(N) ints.  With eflag/vflag the energy and
+// virial are added to rs->epot / rs->virial.  part: 1 launches the register
+// kernel(s) only, 2 the rest (overflow or general kernel and the reduction), 3 both.
+// stats: record the largest in-cutoff counts (rs->maxnc, rs->maxnc_t).
 cudaError_t launch_force_part(int part, cudaStream_t st, int prec, int fast_slots, bool one_type, int gen_slots,
                               int eflag, int vflag, int N, const dbl4 *x, const int4 *q, const int *nbr,
                               const int *cnt, const SysTab *sys, const void *pairs, const void *trips, int nt,

@@ -16,10 +16,14 @@
 // the angular constants of rows (i,j,k) and (i,k,j) agree (Tersoff's tables take
 // them from atom i), so each is evaluated once per pair instead of twice.  Atoms
 // with more in-cutoff neighbours than slots are queued, per block and in order,
-// for the general kernel.
+// for the warp kernel.
 //
-// General kernel (k_force_gen): slots in per-thread shared memory (8..64), loops
-// over ordered (j,k) as in Algorithm 1; handles any table and any neighbour count.
+// Warp kernel (k_force_warp): one warp per queued atom, up to 64 in-cutoff
+// neighbours in shared-memory slots, ordered (j,k) terms spread over the lanes.
+//
+// General kernel (k_force_gen): one thread per atom, slots in per-thread shared
+// memory (8..64), loops over ordered (j,k) as in Algorithm 1; runs every atom for
+// tables whose rows (i,j,k) and (i,k,j) differ in their angular constants.
 //
 // Scatter: all force contributions of i's terms on neighbour j are summed per j in
 // the thread and written once, to slot s of i's list (contrib[s][i]); the force of
@@ -697,9 +701,9 @@ struct GenCfg {
   static constexpr size_t smem_slots = (size_t)threads * MAXNC * slot_bytes;
 };
 
-// Evaluates atoms either all (work == nullptr: atom = global thread index) or the
-// overflow atoms queued by the fast kernel (work/nwork: per fast block, in order;
-// block b of this kernel takes a contiguous run of fast blocks as one flat queue).
+// Evaluates every atom (one thread per atom) with ordered (j,k) loops as in
+// Algorithm 1: the path for tables whose angular constants differ between rows
+// (i,j,k) and (i,k,j), and the reference the register kernel is tested against.
 template <class M, int MAXNC, bool EFLAG, bool VFLAG>
 __global__ void __launch_bounds__(GenCfg<typename M::R, MAXNC>::threads)
 k_force_gen(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const int *__restrict__ nbr,
@@ -707,8 +711,7 @@ k_force_gen(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
             const PairP<typename M::R> *__restrict__ gpairs, const TripP<typename M::R> *__restrict__ gtrips, int nt,
             typename V4t<typename M::R>::type *__restrict__ contrib,
             typename V4t<typename M::R>::type *__restrict__ selfF, unsigned long long *__restrict__ mask,
-            const int *__restrict__ work, const int *__restrict__ nwork, int nfast, double *__restrict__ partial,
-            RunState *rs, double *__restrict__ eatom)
+            double *__restrict__ partial, RunState *rs, double *__restrict__ eatom)
 {
   using R = typename M::R;
   using V4 = typename V4t<R>::type;
@@ -722,11 +725,6 @@ k_force_gen(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
   int *smeta = reinterpret_cast<int *>(sr + (size_t)NRF * MAXNC * T);
 
   if (rs->status != 0) return;   // uniform across the grid
-  if (work && rs->over_total == 0) {
-    // no atom was queued: leave zero partial sums and stop
-    if ((EFLAG || VFLAG) && threadIdx.x < 8) partial[(size_t)blockIdx.x * 8 + threadIdx.x] = 0.0;
-    return;
-  }
   for (int k = threadIdx.x; k < nt * nt; k += T) pairs[k] = gpairs[k];
   for (int k = threadIdx.x; k < nt * nt * nt; k += T) trips[k] = gtrips[k];
   __syncthreads();
@@ -943,30 +941,9 @@ k_force_gen(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
     if (eatom) eatom[i] = (double)e_atom;
   };
 
-  if (!work) {
+  {
     const int i = (int)blockIdx.x * T + t;
     if (i < N) process(i);
-  } else {
-    // Overflow queues of the register kernel: block b takes the contiguous run of
-    // fast blocks [b G, (b + 1) G), G = ceil(nfast / gridDim.x), as one flat queue in
-    // order (GEN_SUB fast blocks per pass) and its threads take entries t, t + T, ...
-    __shared__ int qoff[GEN_SUB + 1];
-    const int G = (nfast + (int)gridDim.x - 1) / (int)gridDim.x;
-    const int fb0 = (int)blockIdx.x * G, fb1 = min(fb0 + G, nfast);
-    for (int sb = fb0; sb < fb1; sb += GEN_SUB) {
-      const int ns = min(GEN_SUB, fb1 - sb);
-      block_exclusive_offsets<T>(nwork + sb, ns, qoff);
-      const int total = qoff[ns];
-      for (int pidx = t; pidx < total; pidx += T) {
-        int lo = 0, hi = ns - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (qoff[mid] <= pidx) lo = mid; else hi = mid - 1;
-        }
-        process(work[(size_t)(sb + lo) * FAST_THREADS + (pidx - qoff[lo])]);
-      }
-      __syncthreads();
-    }
   }
   if (overflow) atomicOr(&rs->status, ST_NC_OVERFLOW);
   if (maxnc > 0) atomicMax(&rs->maxnc, maxnc);
@@ -975,13 +952,297 @@ k_force_gen(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
 #undef META
 }
 
+// ============================================================================
+// warp kernel: one warp per atom of the register kernel's overflow queues
+
+constexpr int WARP_BLOCK = 128;   // 4 warps per block
+constexpr int WSLOTS = MAX_CAP;   // slots per warp: a list holds at most MAX_CAP entries
+
+// The atoms the register kernel queued (more in-cutoff neighbours than its slots)
+// are evaluated one per warp, with ordered (j,k) terms as in Algorithm 1:
+//   - the lanes test list entries lane, lane + 32, ...; a ballot packs the in-cutoff
+//     ones into the warp's shared-memory slots in list order;
+//   - lane a computes zeta for slot a (Eq. 3) and its pair term (Eqs. 1-2);
+//   - lane c sums the whole force on neighbour c: its pair term, the derivatives of
+//     zeta(i,c,p) with respect to x_c and those of zeta(i,p,c), over p in slot order.
+// Every sum runs in a fixed order, so results are deterministic.  Block b takes the
+// contiguous run of register-kernel blocks [b G, (b + 1) G), G = ceil(nfast /
+// gridDim.x), as one flat queue in order; its warps take entries w, w + 4, ...
+template <class M, bool EFLAG, bool VFLAG>
+__global__ void __launch_bounds__(WARP_BLOCK)
+k_force_warp(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const int *__restrict__ nbr,
+             const int *__restrict__ cnt, const SysTab *__restrict__ sys,
+             const PairP<typename M::R> *__restrict__ gpairs, const TripP<typename M::R> *__restrict__ gtrips,
+             int nt, typename V4t<typename M::R>::type *__restrict__ contrib,
+             typename V4t<typename M::R>::type *__restrict__ selfF, unsigned long long *__restrict__ mask,
+             const int *__restrict__ work, const int *__restrict__ nwork, int nfast, double *__restrict__ partial,
+             RunState *rs, double *__restrict__ eatom)
+{
+  using R = typename M::R;
+  using V4 = typename V4t<R>::type;
+  constexpr int T = WARP_BLOCK, NW = T / 32;
+  constexpr bool MIXED = sizeof(R) == 4;
+  __shared__ PairP<R> pairs[MAX_TYPES * MAX_TYPES];
+  __shared__ TripP<R> trips[MAX_TYPES * MAX_TYPES * MAX_TYPES];
+  __shared__ R sl[NW][NRF][WSLOTS];
+  __shared__ int smeta[NW][WSLOTS];
+  __shared__ int qoff[GEN_SUB + 1];
+
+  if (rs->status != 0) return;   // uniform across the grid
+  if (rs->over_total == 0) {
+    // no atom was queued: leave zero partial sums and stop
+    if ((EFLAG || VFLAG) && threadIdx.x < 8) partial[(size_t)blockIdx.x * 8 + threadIdx.x] = 0.0;
+    return;
+  }
+  for (int k = threadIdx.x; k < nt * nt; k += T) pairs[k] = gpairs[k];
+  for (int k = threadIdx.x; k < nt * nt * nt; k += T) trips[k] = gtrips[k];
+  __syncthreads();
+
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  R(&S)[NRF][WSLOTS] = sl[w];
+  int *meta = smeta[w];
+  R red[7] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
+  int maxnc = 0;
+
+  // atom i, by all 32 lanes of the warp
+  auto process = [&](const int i) {
+    int w_i;
+    int4 qi = make_int4(0, 0, 0, 0);
+    dbl4 xi = make_dbl4(0, 0, 0, 0);
+    if (MIXED) {
+      qi = q[i];
+      w_i = qi.w;
+    } else {
+      xi = x[i];
+      w_i = (int)__double_as_longlong(xi.w);
+    }
+    const int ti = type_of(w_i);
+    const Geom *gp = &sys[sys_of(w_i)].geo;
+    const int n = cnt[i];
+    unsigned long long mbits = 0ull;
+    int nc = 0;
+    for (int s0 = 0; s0 < n; s0 += 32) {
+      const int s = s0 + lane;
+      bool inc = false;
+      int tj = 0;
+      int4 qj = make_int4(0, 0, 0, 0);
+      dbl4 xj = make_dbl4(0, 0, 0, 0);
+      R dx = R(0), dy = R(0), dz = R(0);
+      if (s < n) {
+        const int j = nbr[(size_t)s * N + i];
+        if (MIXED) {
+          qj = q[j];
+          tj = type_of(qj.w);
+          dx = (R)q_scaled(qdiff(qj.x, qi.x), gp->q_to_f[0]);
+          dy = (R)q_scaled(qdiff(qj.y, qi.y), gp->q_to_f[1]);
+          dz = (R)q_scaled(qdiff(qj.z, qi.z), gp->q_to_f[2]);
+        } else {
+          xj = x[j];
+          tj = type_of((int)__double_as_longlong(xj.w));
+          dx = (R)min_image(__dsub_rn(xj.x, xi.x), gp->L[0], gp->invL[0]);
+          dy = (R)min_image(__dsub_rn(xj.y, xi.y), gp->L[1], gp->invL[1]);
+          dz = (R)min_image(__dsub_rn(xj.z, xi.z), gp->L[2], gp->invL[2]);
+        }
+        inc = r2_decide(dx, dy, dz) < pairs[ti * nt + tj].rc2;
+      }
+      const unsigned b = __ballot_sync(0xffffffffu, inc);
+      if (inc) {
+        const int slot = nc + __popc(b & ((1u << lane) - 1u));
+        const PairP<R> &P = pairs[ti * nt + tj];
+        R r, rlo, inv;
+        if (MIXED && M::fine) {
+          float dh[3], dl[3];
+          qd_fine(qdiff(qj.x, qi.x), gp->q_to_f[0], gp->q_to_f_lo[0], dh[0], dl[0]);
+          qd_fine(qdiff(qj.y, qi.y), gp->q_to_f[1], gp->q_to_f_lo[1], dh[1], dl[1]);
+          qd_fine(qdiff(qj.z, qi.z), gp->q_to_f[2], gp->q_to_f_lo[2], dh[2], dl[2]);
+          float rh_, rl_, irh_;
+          norm_fine(dh, dl, rh_, rl_, irh_);
+          dx = (R)dh[0]; dy = (R)dh[1]; dz = (R)dh[2];
+          r = (R)rh_; rlo = (R)rl_; inv = (R)irh_;
+        } else {
+          const R rf2 = r2_decide(dx, dy, dz);
+          inv = M::rsqrt(rf2);
+          r = rf2 * inv;
+          rlo = R(0);
+        }
+        R fcv, dfcv;
+        cutoff_fn<M>(r, rlo, P, fcv, dfcv);
+        S[S_UX][slot] = dx * inv;
+        S[S_UY][slot] = dy * inv;
+        S[S_UZ][slot] = dz * inv;
+        S[S_R][slot] = r;
+        S[S_RL][slot] = rlo;
+        S[S_IR][slot] = inv;
+        S[S_FC][slot] = fcv;
+        S[S_DFC][slot] = dfcv;
+        meta[slot] = s | (tj << 8);
+      }
+      mbits |= (unsigned long long)b << s0;
+      nc += __popc(b);
+    }
+    maxnc = max(maxnc, nc);
+    __syncwarp();
+
+    // zeta and the pair term of slot a
+    R e_lane = R(0);
+    for (int a = lane; a < nc; a += 32) {
+      const int ta = meta[a] >> 8;
+      const R uax = S[S_UX][a], uay = S[S_UY][a], uaz = S[S_UZ][a], ra = S[S_R][a];
+      const TripP<R> *Ta = trips + (ti * nt + ta) * nt;
+      R zeta = R(0);
+      for (int p = 0; p < nc; ++p) {
+        if (p == a) continue;
+        const TripP<R> &Tp = Ta[meta[p] >> 8];
+        const R cost = uax * S[S_UX][p] + uay * S[S_UY][p] + uaz * S[S_UZ][p];
+        const R u = Tp.h - cost;
+        const R u2 = u * u;
+        const R g = Tp.gamma + Tp.K * u2 * M::rcp(Tp.d2 + u2);
+        R ex = R(1);
+        if (Tp.lam3 != R(0)) {
+          R arg = Tp.lam3 * (ra - S[S_R][p]);
+          if (Tp.m3 != R(0)) arg = arg * arg * arg;
+          ex = M::expv(arg);
+        }
+        zeta += S[S_FC][p] * g * ex;
+      }
+      const PairP<R> &P = pairs[ti * nt + ta];
+      const R fcv = S[S_FC][a], dfcv = S[S_DFC][a];
+      const R fR = P.A * M::expneg(P.lam1, P.lam1_lo, ra, S[S_RL][a]);
+      const R fA = -P.B * M::expneg(P.lam2, P.lam2_lo, ra, S[S_RL][a]);
+      R bij, dbij;
+      bond_order<M>(zeta, P, bij, dbij);
+      const R pr = fR + bij * fA;
+      e_lane += R(0.5) * fcv * pr;
+      const R dvdr = R(0.5) * (dfcv * pr + fcv * (-P.lam1 * fR - bij * P.lam2 * fA));
+      S[S_DZ][a] = R(0.5) * fcv * fA * dbij;
+      S[S_FX][a] = -dvdr * uax;
+      S[S_FY][a] = -dvdr * uay;
+      S[S_FZ][a] = -dvdr * uaz;
+    }
+    __syncwarp();
+
+    // the force on neighbour c
+    R sx = R(0), sy = R(0), sz = R(0);
+    for (int c = lane; c < nc; c += 32) {
+      const int tc = meta[c] >> 8;
+      const R ucx = S[S_UX][c], ucy = S[S_UY][c], ucz = S[S_UZ][c], rc = S[S_R][c], irc = S[S_IR][c];
+      const R fcc = S[S_FC][c], dfcc = S[S_DFC][c], dzc = S[S_DZ][c];
+      R fx = S[S_FX][c], fy = S[S_FY][c], fz = S[S_FZ][c];
+      for (int p = 0; p < nc; ++p) {
+        if (p == c) continue;
+        const int tp = meta[p] >> 8;
+        const R upx = S[S_UX][p], upy = S[S_UY][p], upz = S[S_UZ][p], rp = S[S_R][p];
+        const R cost = ucx * upx + ucy * upy + ucz * upz;
+        if (dzc != R(0)) {
+          // zeta(i,c,p) with respect to x_c (c as j): row (ti, tc, tp)
+          const TripP<R> &Tp = trips[(ti * nt + tc) * nt + tp];
+          const R u = Tp.h - cost;
+          const R u2 = u * u;
+          const R inv = M::rcp(Tp.d2 + u2);
+          const R g = Tp.gamma + Tp.K * u2 * inv;
+          const R dg = -Tp.G2 * u * inv * inv;
+          R ex = R(1), darg = R(0);
+          if (Tp.lam3 != R(0)) {
+            const R tt = Tp.lam3 * (rc - rp);
+            R arg = tt;
+            darg = Tp.lam3;
+            if (Tp.m3 != R(0)) {
+              arg = tt * tt * tt;
+              darg = R(3) * Tp.lam3 * tt * tt;
+            }
+            ex = M::expv(arg);
+          }
+          const R fcp = S[S_FC][p];
+          const R a1 = fcp * ex * dg;
+          const R a2 = fcp * ex * g * darg;
+          const R cj = a1 * irc;
+          fx -= dzc * (cj * (upx - cost * ucx) + a2 * ucx);
+          fy -= dzc * (cj * (upy - cost * ucy) + a2 * ucy);
+          fz -= dzc * (cj * (upz - cost * ucz) + a2 * ucz);
+        }
+        const R dzp = S[S_DZ][p];
+        if (dzp != R(0)) {
+          // zeta(i,p,c) with respect to x_c (c as k): row (ti, tp, tc)
+          const TripP<R> &Tp = trips[(ti * nt + tp) * nt + tc];
+          const R u = Tp.h - cost;
+          const R u2 = u * u;
+          const R inv = M::rcp(Tp.d2 + u2);
+          const R g = Tp.gamma + Tp.K * u2 * inv;
+          const R dg = -Tp.G2 * u * inv * inv;
+          R ex = R(1), darg = R(0);
+          if (Tp.lam3 != R(0)) {
+            const R tt = Tp.lam3 * (rp - rc);
+            R arg = tt;
+            darg = Tp.lam3;
+            if (Tp.m3 != R(0)) {
+              arg = tt * tt * tt;
+              darg = R(3) * Tp.lam3 * tt * tt;
+            }
+            ex = M::expv(arg);
+          }
+          const R a1 = fcc * ex * dg;
+          const R a2 = fcc * ex * g * darg;
+          const R a3 = dfcc * g * ex;
+          const R ck = a1 * irc;
+          fx -= dzp * ((a3 - a2) * ucx + ck * (upx - cost * ucx));
+          fy -= dzp * ((a3 - a2) * ucy + ck * (upy - cost * ucy));
+          fz -= dzp * ((a3 - a2) * ucz + ck * (upz - cost * ucz));
+        }
+      }
+      V4 o;
+      o.x = fx; o.y = fy; o.z = fz; o.w = R(0);
+      contrib[(size_t)(meta[c] & 0xff) * N + i] = o;
+      sx -= fx;
+      sy -= fy;
+      sz -= fz;
+      if (VFLAG) {
+        const R dx = rc * ucx, dy = rc * ucy, dzz = rc * ucz;
+        red[1] += dx * fx; red[2] += dy * fy; red[3] += dzz * fz;
+        red[4] += dx * fy; red[5] += dx * fz; red[6] += dy * fz;
+      }
+    }
+    red[0] += e_lane;
+    sx = warp_sum(sx);
+    sy = warp_sum(sy);
+    sz = warp_sum(sz);
+    const R e_atom = warp_sum(e_lane);
+    if (lane == 0) {
+      V4 o;
+      o.x = sx; o.y = sy; o.z = sz; o.w = R(0);
+      selfF[i] = o;
+      mask[i] = mbits;
+      if (eatom) eatom[i] = (double)e_atom;
+    }
+    __syncwarp();   // the slots are reused by the warp's next atom
+  };
+
+  const int G = (nfast + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int fb0 = (int)blockIdx.x * G, fb1 = min(fb0 + G, nfast);
+  for (int sb = fb0; sb < fb1; sb += GEN_SUB) {
+    const int ns = min(GEN_SUB, fb1 - sb);
+    block_exclusive_offsets<T>(nwork + sb, ns, qoff);
+    const int total = qoff[ns];
+    for (int pidx = w; pidx < total; pidx += NW) {
+      int lo = 0, hi = ns - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (qoff[mid] <= pidx) lo = mid; else hi = mid - 1;
+      }
+      process(work[(size_t)(sb + lo) * FAST_THREADS + (pidx - qoff[lo])]);
+    }
+    __syncthreads();
+  }
+  if (lane == 0 && maxnc > 0) atomicMax(&rs->maxnc, maxnc);
+  if (EFLAG || VFLAG) block_partial<R, T, MIXED && !M::fine>(red, EFLAG, VFLAG, partial + (size_t)blockIdx.x * 8);
+}
+
+
 // ---- host-side launch ------------------------------------------------------
 
 template <class M, int MAXNC, bool EFLAG, bool VFLAG>
 static cudaError_t launch_gen_t(cudaStream_t st, int N, const dbl4 *x, const int4 *q, const int *nbr, const int *cnt,
                                 const SysTab *sys, const void *pairs, const void *trips, int nt, void *contrib,
-                                void *selfF, unsigned long long *mask, const int *work, const int *nwork, int nfast,
-                                int gen_blocks, double *partial, RunState *rs, double *eatom)
+                                void *selfF, unsigned long long *mask, double *partial, RunState *rs, double *eatom)
 {
   using R = typename M::R;
   using C = GenCfg<R, MAXNC>;
@@ -995,28 +1256,27 @@ static cudaError_t launch_gen_t(cudaStream_t st, int N, const dbl4 *x, const int
     attr_set = true;
   }
   if (N == 0) return cudaSuccess;
-  const int blocks = work ? gen_blocks : (N + C::threads - 1) / C::threads;
+  const int blocks = (N + C::threads - 1) / C::threads;
   kern<<<blocks, C::threads, smem, st>>>(N, x, q, nbr, cnt, sys, (const PairP<R> *)pairs, (const TripP<R> *)trips,
                                          nt, (typename V4t<R>::type *)contrib, (typename V4t<R>::type *)selfF, mask,
-                                         work, nwork, nfast, partial, rs, eatom);
+                                         partial, rs, eatom);
   return cudaGetLastError();
 }
 
 template <class M, int MAXNC>
 static cudaError_t launch_gen(cudaStream_t st, int eflag, int vflag, int N, const dbl4 *x, const int4 *q,
                               const int *nbr, const int *cnt, const SysTab *sys, const void *pairs, const void *trips,
-                              int nt, void *contrib, void *selfF, unsigned long long *mask, const int *work,
-                              const int *nwork, int nfast, int gen_blocks, double *partial, RunState *rs,
-                              double *eatom)
+                              int nt, void *contrib, void *selfF, unsigned long long *mask, double *partial,
+                              RunState *rs, double *eatom)
 {
   if (vflag)
-    return launch_gen_t<M, MAXNC, true, true>(st, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib, selfF, mask, work,
-                                              nwork, nfast, gen_blocks, partial, rs, eatom);
+    return launch_gen_t<M, MAXNC, true, true>(st, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib, selfF, mask,
+                                              partial, rs, eatom);
   if (eflag)
     return launch_gen_t<M, MAXNC, true, false>(st, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib, selfF, mask,
-                                               work, nwork, nfast, gen_blocks, partial, rs, eatom);
+                                               partial, rs, eatom);
   return launch_gen_t<M, MAXNC, false, false>(st, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib, selfF, mask,
-                                              work, nwork, nfast, gen_blocks, partial, rs, eatom);
+                                              partial, rs, eatom);
 }
 
 template <class R>
@@ -1034,13 +1294,12 @@ template <class M>
 static cudaError_t launch_gen_any(cudaStream_t st, int slots, int eflag, int vflag, int N, const dbl4 *x,
                                   const int4 *q, const int *nbr, const int *cnt, const SysTab *sys, const void *pairs,
                                   const void *trips, int nt, void *contrib, void *selfF, unsigned long long *mask,
-                                  const int *work, const int *nwork, int nfast, int gen_blocks, double *partial,
-                                  RunState *rs, double *eatom)
+                                  double *partial, RunState *rs, double *eatom)
 {
 #define TSF_GEN(NC)                                                                                                \
   case NC:                                                                                                         \
-    return launch_gen<M, NC>(st, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib, selfF, mask, work, \
-                             nwork, nfast, gen_blocks, partial, rs, eatom);
+    return launch_gen<M, NC>(st, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib, selfF, mask,     \
+                             partial, rs, eatom);
   switch (slots) {
     TSF_GEN(8)
     TSF_GEN(16)
@@ -1049,6 +1308,32 @@ static cudaError_t launch_gen_any(cudaStream_t st, int slots, int eflag, int vfl
   }
 #undef TSF_GEN
   return cudaErrorInvalidValue;
+}
+
+// the warp kernel over the register kernel's overflow queues (GEN_BLOCKS blocks)
+template <class M>
+static cudaError_t launch_warp(cudaStream_t st, int eflag, int vflag, int N, const dbl4 *x, const int4 *q,
+                               const int *nbr, const int *cnt, const SysTab *sys, const void *pairs, const void *trips,
+                               int nt, void *contrib, void *selfF, unsigned long long *mask, const int *work,
+                               const int *nwork, int nfast, double *partial, RunState *rs, double *eatom)
+{
+  using R = typename M::R;
+  using P = const PairP<R> *;
+  using Tt = const TripP<R> *;
+  using V = typename V4t<R>::type *;
+  if (vflag)
+    k_force_warp<M, true, true><<<GEN_BLOCKS, WARP_BLOCK, 0, st>>>(N, x, q, nbr, cnt, sys, (P)pairs, (Tt)trips, nt,
+                                                                   (V)contrib, (V)selfF, mask, work, nwork, nfast,
+                                                                   partial, rs, eatom);
+  else if (eflag)
+    k_force_warp<M, true, false><<<GEN_BLOCKS, WARP_BLOCK, 0, st>>>(N, x, q, nbr, cnt, sys, (P)pairs, (Tt)trips, nt,
+                                                                    (V)contrib, (V)selfF, mask, work, nwork, nfast,
+                                                                    partial, rs, eatom);
+  else
+    k_force_warp<M, false, false><<<GEN_BLOCKS, WARP_BLOCK, 0, st>>>(N, x, q, nbr, cnt, sys, (P)pairs, (Tt)trips, nt,
+                                                                     (V)contrib, (V)selfF, mask, work, nwork, nfast,
+                                                                     partial, rs, eatom);
+  return cudaGetLastError();
 }
 
 template <class M, int MAXNC, bool ONE>
@@ -1112,13 +1397,13 @@ cudaError_t launch_force_m(int part, cudaStream_t st, int fast_slots, bool one_t
     }
     if (!(part & 2)) return cudaSuccess;
     double *gp = partial + (size_t)nfast * 8;
-    e = launch_gen_any<M>(st, gen_slots, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib, selfF, mask,
-                          work, nwork, nfast, GEN_BLOCKS, gp, rs, eatom);
+    e = launch_warp<M>(st, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib, selfF, mask, work, nwork,
+                       nfast, gp, rs, eatom);
     if (e == cudaSuccess) *rows = nfast + GEN_BLOCKS;
   } else {
     if (!(part & 2)) return cudaSuccess;
     e = launch_gen_any<M>(st, gen_slots, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib, selfF, mask,
-                          nullptr, nullptr, 0, 0, partial, rs, eatom);
+                          partial, rs, eatom);
     const int T = gen_threads<R>(gen_slots);
     if (e == cudaSuccess) *rows = (N + T - 1) / T;
   }

@@ -1072,7 +1072,7 @@ int tersoff_md_create(tersoff_ctx *ctx, const double *pos, const double *vel, co
   if ((rc = read_rs(ctx, md->rs, &h)) != TERSOFF_OK) return fail(rc);
   if (h.status != 0) return fail(status_to_code(ctx, h.status, h));
   // register kernel with 4 slots when no atom has more than 4 in-cutoff neighbours
-  // (diamond-like solids), else 8; atoms beyond that go to the general kernel
+  // (diamond-like solids), else 8; atoms beyond that go to the warp kernel
   if (md->fast_slots > 0 && h.maxnc <= 4) md->fast_slots = 4;
   // several types with different neighbour counts (C atoms in SiC have 4, Si atoms up
   // to 8): one register-kernel launch per slot count over the atoms of those types, so
@@ -1103,9 +1103,9 @@ int tersoff_md_create(tersoff_ctx *ctx, const double *pos, const double *vel, co
       md->routed = true;
     }
   }
-  // the general kernel needs slots for in-cutoff neighbours only (not the whole
-  // list): size it from the largest count seen plus headroom; a later overflow
-  // widens it (recovery in md_finish)
+  // the general kernel (the path without the register kernel) needs slots for
+  // in-cutoff neighbours only (not the whole list): size it from the largest count
+  // seen plus headroom; a later overflow widens it (recovery in md_finish)
   md->gen_slots = force_slots_for(std::max(8, h.maxnc + 2));
   md->steps_done = md->steps_target = 0;
   md->pe_valid = true;
