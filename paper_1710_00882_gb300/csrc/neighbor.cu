@@ -219,24 +219,24 @@ __device__ __forceinline__ void add_pair(int i, int j, int N, int cap, int *__re
 // system with an axis of fewer than 3 cells scans its whole (deduplicated) stencil
 // and keeps j > i.  Candidates of one stencil row are one run of cell_atoms (two
 // where the row wraps).
-__global__ void __launch_bounds__(128) k_build(int N, const int4 *__restrict__ q, const SysTab *__restrict__ sys,
-                                               const SysCtl *__restrict__ ctl, PairRadii radii,
+__global__ void __launch_bounds__(128, 12) k_build(int N, const int4 *__restrict__ q, const SysTab *__restrict__ sys,
+                                               const SysCtl *__restrict__ ctl,
+                                               const __grid_constant__ PairRadii radii,
                                                const int *__restrict__ cell_start,
                                                const int4 *__restrict__ cell_atoms, int *__restrict__ nbr,
                                                int *__restrict__ cnt, int cap, int4 *__restrict__ qref, RunState *rs,
                                                int gated)
 {
-  __shared__ float s_rl2[MAX_TYPES * MAX_TYPES];
   if (skip_build(rs, gated)) return;
-#pragma unroll
-  for (int k = 0; k < MAX_TYPES * MAX_TYPES; ++k)
-    if (threadIdx.x == k) s_rl2[k] = radii.rl2[k];
-  __syncthreads();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= N) return;
   const int i = cell_atoms[t].w & CELL_IDX_MASK;
   const int4 pi = q[i];
-  const float *lim = s_rl2 + type_of(pi.w) * MAX_TYPES;   // row of i's type
+  // Most candidates fail the largest radius of i's row; only the others decode j's
+  // type and read their pair's radius (from the constant bank).
+  const float *lrow = radii.rl2 + type_of(pi.w) * MAX_TYPES;
+  const float lmax = fmaxf(fmaxf(lrow[0], lrow[1]), fmaxf(lrow[2], lrow[3]));
+  auto limit = [&](int tj) { return lrow[tj]; };
   // per-system builds: a system none of whose atoms moved skin/2 keeps its lists
   if (ctl && ctl[sys_of(pi.w)].rebuild == 0) return;
   qref[i] = pi;
@@ -254,16 +254,17 @@ __global__ void __launch_bounds__(128) k_build(int N, const int4 *__restrict__ q
     for (int u = b; u < e; u += 4) {
       int4 pj[4];
 #pragma unroll
+      // padding record: index 0, never > i
       for (int k = 0; k < 4; ++k) pj[k] = u + k < e ? cell_atoms[u + k] : make_int4(0, 0, 0, 0);
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const int j = pj[k].w & CELL_IDX_MASK;
-        const int tj = (int)((unsigned)pj[k].w >> CELL_IDX_BITS);
         const float dx = q_scaled(qdiff(pj[k].x, pi.x), s0);
         const float dy = q_scaled(qdiff(pj[k].y, pi.y), s1);
         const float dz = q_scaled(qdiff(pj[k].z, pi.z), s2);
         const float r2 = r2_decide(dx, dy, dz);
-        if (u + k < e && j > i && r2 < lim[tj]) add_pair(i, j, N, cap, nbr, cnt, nf);
+        if (j > i && r2 < lmax && r2 < limit((int)((unsigned)pj[k].w >> CELL_IDX_BITS)))
+          add_pair(i, j, N, cap, nbr, cnt, nf);
       }
     }
   };
@@ -293,16 +294,16 @@ __global__ void __launch_bounds__(128) k_build(int N, const int4 *__restrict__ q
       for (int u = b; u < e; u += 4) {
         int4 pj[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) pj[k] = u + k < e ? cell_atoms[u + k] : make_int4(0, 0, 0, 0);
+        // padding record: word -1, which no atom has (indices stay below 2^30 - 1)
+        for (int k = 0; k < 4; ++k) pj[k] = u + k < e ? cell_atoms[u + k] : make_int4(0, 0, 0, -1);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          const int j = pj[k].w & CELL_IDX_MASK;
-          const int tj = (int)((unsigned)pj[k].w >> CELL_IDX_BITS);
           const float dx = q_scaled(qdiff(pj[k].x, pi.x), s0);
           const float dy = q_scaled(qdiff(pj[k].y, pi.y), s1);
           const float dz = q_scaled(qdiff(pj[k].z, pi.z), s2);
           const float r2 = r2_decide(dx, dy, dz);
-          if (u + k < e && r2 < lim[tj]) add_pair(i, j, N, cap, nbr, cnt, nf);
+          if (pj[k].w != -1 && r2 < lmax && r2 < limit((int)((unsigned)pj[k].w >> CELL_IDX_BITS)))
+            add_pair(i, pj[k].w & CELL_IDX_MASK, N, cap, nbr, cnt, nf);
         }
       }
     };
