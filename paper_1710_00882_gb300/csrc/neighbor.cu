@@ -219,6 +219,7 @@ __device__ __forceinline__ void add_pair(int i, int j, int N, int cap, int *__re
 // system with an axis of fewer than 3 cells scans its whole (deduplicated) stencil
 // and keeps j > i.  Candidates of one stencil row are one run of cell_atoms (two
 // where the row wraps).
+template <bool TYPED>
 __global__ void __launch_bounds__(128, 12) k_build(int N, const int4 *__restrict__ q, const SysTab *__restrict__ sys,
                                                const SysCtl *__restrict__ ctl,
                                                const __grid_constant__ PairRadii radii,
@@ -263,7 +264,7 @@ __global__ void __launch_bounds__(128, 12) k_build(int N, const int4 *__restrict
         const float dy = q_scaled(qdiff(pj[k].y, pi.y), s1);
         const float dz = q_scaled(qdiff(pj[k].z, pi.z), s2);
         const float r2 = r2_decide(dx, dy, dz);
-        if (j > i && r2 < lmax && r2 < limit((int)((unsigned)pj[k].w >> CELL_IDX_BITS)))
+        if (j > i && r2 < lmax && (!TYPED || r2 < limit((int)((unsigned)pj[k].w >> CELL_IDX_BITS))))
           add_pair(i, j, N, cap, nbr, cnt, nf);
       }
     }
@@ -302,7 +303,7 @@ __global__ void __launch_bounds__(128, 12) k_build(int N, const int4 *__restrict
           const float dy = q_scaled(qdiff(pj[k].y, pi.y), s1);
           const float dz = q_scaled(qdiff(pj[k].z, pi.z), s2);
           const float r2 = r2_decide(dx, dy, dz);
-          if (pj[k].w != -1 && r2 < lmax && r2 < limit((int)((unsigned)pj[k].w >> CELL_IDX_BITS)))
+          if (pj[k].w != -1 && r2 < lmax && (!TYPED || r2 < limit((int)((unsigned)pj[k].w >> CELL_IDX_BITS))))
             add_pair(i, pj[k].w & CELL_IDX_MASK, N, cap, nbr, cnt, nf);
         }
       }
@@ -487,7 +488,14 @@ cudaError_t launch_build(cudaStream_t st, int N, const int4 *q, const SysTab *sy
   k_scan_add<<<(ncell + T - 1) / T, T, 0, st>>>(ncell, cell_start, tile_sums, cell_count, rs, gated);
   k_cell_fill<<<BN, T, 0, st>>>(N, q, cell_of, rank, cell_start, cell_atoms, rs, gated);
   const int BN128 = (N + 127) / 128;
-  k_build<<<BN128, 128, 0, st>>>(N, q, sys, ctl, radii, cell_start, cell_atoms, nbr, cnt, cap, qref, rs, gated);
+  // one radius for every type pair (one-type tables, or lists built with one cutoff):
+  // the row's largest radius decides alone
+  bool typed = false;
+  for (int k = 1; k < MAX_TYPES * MAX_TYPES; ++k) typed = typed || radii.rl2[k] != radii.rl2[0];
+  if (typed)
+    k_build<true><<<BN128, 128, 0, st>>>(N, q, sys, ctl, radii, cell_start, cell_atoms, nbr, cnt, cap, qref, rs, gated);
+  else
+    k_build<false><<<BN128, 128, 0, st>>>(N, q, sys, ctl, radii, cell_start, cell_atoms, nbr, cnt, cap, qref, rs, gated);
   k_sort_lists<<<BN128, 128, 0, st>>>(N, q, ctl, nbr, cnt, cap, rs, gated);
   k_reverse<<<BN128, 128, 0, st>>>(N, q, ctl, nbr, cnt, rev, rs, gated);
   k_build_done<<<1, 1, 0, st>>>(rs, gated);
