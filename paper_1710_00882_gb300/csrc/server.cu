@@ -43,6 +43,17 @@ __device__ __forceinline__ int range_of(const int *__restrict__ off, int n, int 
   return lo;
 }
 
+// Register-kernel routes of a layout: atom d of system k goes to position
+// route_off[k] + (d - dst_off[k]) of the route order.
+__global__ void k_route_order(int n, const int *__restrict__ dst_off, const int *__restrict__ route_off, int nsys,
+                              int *__restrict__ order)
+{
+  const int d = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= n) return;
+  const int k = range_of(dst_off, nsys, d);
+  order[route_off[k] + (d - dst_off[k])] = d;
+}
+
 // Survivors of a repack: atom d of the new layout (systems 0..nsurv-1 come first)
 // is atom src_off[k] + (d - atom_off[k]) of the old layout; its word gets the new
 // system index.
@@ -212,6 +223,13 @@ struct tersoff_server {
   char *hstage = nullptr;       // pinned host staging
   size_t hstage_b = 0;
   int *dtabs = nullptr;         // device index tables of a repack / retire (4 x (max_slots + 1) ints)
+  // register-kernel routes: atoms of one-species jobs (at most 4 in-cutoff
+  // neighbours in the solids served) through the 4-slot kernel, the others through
+  // the 8-slot kernel.  A job's route follows from its own atoms only, so its
+  // arithmetic does not depend on the batch.
+  ForceRoutes routes{};
+  bool routed = false;
+  int *d_order = nullptr;       // [capacity] atom order of the two routes
   std::vector<SysTab> tab;
   std::vector<Job *> batch;      // resident jobs in layout order (owned by `jobs`; touched by the worker only)
   int64_t natoms = 0;
@@ -268,7 +286,7 @@ size_t bytes_per_atom(bool f32, int listcap)
   const size_t v4 = f32 ? 16 : 32;
   return 2 * (32 + 32 + 16)                        // two copies of x, v, q
          + (size_t)listcap * (v4 + 8)              // contrib + nbr/rev
-         + v4 + 8 + 8 + 4 + 16 + 12 + 8 + 16;      // selfF, mask, work, cnt, qref, cells, eatom, slack
+         + v4 + 8 + 8 + 4 + 16 + 12 + 8 + 4 + 16;  // selfF, mask, work, cnt, qref, cells, eatom, route order, slack
 }
 
 // pinned host staging of at least `bytes` (contents not kept)
@@ -303,7 +321,7 @@ int srv_force(tersoff_server *s, cudaStream_t st)
   SK(launch_force_part(3, st, s->prec, s->fast_slots, P->nt == 1, s->gen_slots, 0, 0, (int)s->natoms, X.x, X.q,
                        s->L.nbr, s->L.cnt, s->S.tab, s->f32 ? P->pair_f : P->pair_d,
                        s->f32 ? P->trip_f : P->trip_d, P->nt, s->SC.contrib, s->SC.selfF, s->SC.mask, s->SC.work,
-                       s->SC.nwork, s->SC.partial, s->rs, s->eatom, nullptr, 0));
+                       s->SC.nwork, s->SC.partial, s->rs, s->eatom, s->routed ? &s->routes : nullptr, 0));
   return TERSOFF_OK;
 }
 
@@ -431,8 +449,9 @@ int repack(tersoff_server *s, const std::vector<Job *> &order, const std::vector
   for (size_t k = 0; k < s->batch.size(); ++k) prev[s->batch[k]] = s->tab[k].atom_off;
   // index tables: [0, S) new atom offsets, [S+1, ...) survivor source offsets, then
   // staging offsets of the new jobs
-  std::vector<int> itab(3 * (size_t)(S + 1), 0);
-  int *dst_off = itab.data(), *src_off = itab.data() + (S + 1), *st_off = itab.data() + 2 * (S + 1);
+  std::vector<int> itab(4 * (size_t)(S + 1), 0);
+  int *dst_off = itab.data(), *src_off = itab.data() + (S + 1), *st_off = itab.data() + 2 * (S + 1),
+      *route_off = itab.data() + 3 * (S + 1);
   int64_t off = 0, staged = 0;
   int coff = 0, nsurv = 0, nnew = 0;
   for (int k = 0; k < S; ++k) {
@@ -462,6 +481,27 @@ int repack(tersoff_server *s, const std::vector<Job *> &order, const std::vector
     coff += gr.ncell;
   }
   const int64_t surv_atoms = nsurv < S ? dst_off[nsurv] : off;
+  // routes: one-species jobs first (4 slots), then the others (8 slots)
+  int64_t n4 = 0;
+  std::vector<char> one_species(S, 0);
+  for (int k = 0; k < S; ++k) {
+    const Job &J = *order[k];
+    one_species[k] = std::all_of(J.types.begin(), J.types.end(), [&](int32_t t) { return t == J.types[0]; });
+    if (one_species[k]) n4 += J.n;
+  }
+  {
+    int64_t r4 = 0, r8 = n4;
+    for (int k = 0; k < S; ++k) {
+      route_off[k] = (int)(one_species[k] ? r4 : r8);
+      (one_species[k] ? r4 : r8) += order[k]->n;
+    }
+  }
+  s->routed = s->fast_slots > 0 && n4 > 0;
+  if (s->routed) {
+    s->routes.n = n4 < off ? 2 : 1;
+    s->routes.r[0] = ForceRoute{n4 < off ? s->d_order : nullptr, 0, (int)n4, 4, 0};
+    s->routes.r[1] = ForceRoute{s->d_order, (int)n4, (int)(off - n4), 8, 0};
+  }
   s->natoms = off;
   s->ncell = coff;
   if (!sys_alloc(s->S, std::max(1, S))) return srv_err(s, TERSOFF_ERR_NOMEM, "system tables");
@@ -504,6 +544,11 @@ int repack(tersoff_server *s, const std::vector<Job *> &order, const std::vector
     SK(cudaMemcpyAsync(dpos, hpos, nbytes, cudaMemcpyHostToDevice, s->st));
     k_ingest_batch<<<(int)((staged + 255) / 256), 256, 0, s->st>>>((int)staged, dpos, dvel, dty, d_st, nnew, nsurv,
                                                                    s->S.tab, P->nt, dst.x, dst.v, dst.q, s->rs);
+    SK(cudaGetLastError());
+  }
+  if (s->routed && s->routes.n == 2) {
+    k_route_order<<<(int)((off + 255) / 256), 256, 0, s->st>>>((int)off, d_dst, s->dtabs + 3 * (S + 1), S,
+                                                               s->d_order);
     SK(cudaGetLastError());
   }
   s->cur = 1 - s->cur;
@@ -819,7 +864,8 @@ int tersoff_server_create(tersoff_ctx *ctx, const tersoff_params *P, tersoff_pre
       ensure_list(pc, s->L, cap, s->listcap, 1) != TERSOFF_OK || !sys_alloc(s->S, max_slots) ||
       cudaMalloc((void **)&s->eatom, sizeof(double) * cap) != cudaSuccess ||
       cudaMalloc((void **)&s->sysE, sizeof(double) * 2 * max_slots) != cudaSuccess ||
-      cudaMalloc((void **)&s->dtabs, sizeof(int) * 3 * (size_t)(max_slots + 1)) != cudaSuccess) {
+      cudaMalloc((void **)&s->dtabs, sizeof(int) * 4 * (size_t)(max_slots + 1)) != cudaSuccess ||
+      cudaMalloc((void **)&s->d_order, sizeof(int) * (size_t)std::max<int64_t>(cap, 1)) != cudaSuccess) {
     cudaGetLastError();
     return fail(set_err(ctx, TERSOFF_ERR_NOMEM, "cannot allocate the packed layout for %lld atoms", (long long)cap));
   }
@@ -963,6 +1009,7 @@ void tersoff_server_destroy(tersoff_server *s)
   dfree(s->sysE);
   dfree(s->stage);
   dfree(s->dtabs);
+  dfree(s->d_order);
   if (s->hstage) cudaFreeHost(s->hstage);
   if (s->st) cudaStreamDestroy(s->st);
   if (s->cap_st) cudaStreamDestroy(s->cap_st);
