@@ -107,10 +107,21 @@ def force_traffic():
     m_h = re.search(r"source_sha256 = ([0-9a-f]{16})", txt)
     if not (m_t and m_h):
         return None
-    h = hashlib.sha256()
-    for f in ("force_kernels.cuh", "force_mixed.cu", "internal.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_1710_00882_gb300", "csrc", f), "rb").read())
-    return int(m_t.group(1)) if h.hexdigest()[:16] == m_h.group(1) else None
+    return int(m_t.group(1)) if force_kernel_source_hash() == m_h.group(1) else None
+
+
+def force_kernel_source_hash():
+    """First 16 hex digits of the sha256 of the register force kernel's source: the
+    part of force_kernels.cuh up to the end of k_force_reg (math helpers and the
+    kernel), force_mixed.cu (its instantiation) and internal.cuh."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_1710_00882_gb300", "csrc")
+    kern = open(os.path.join(csrc, "force_kernels.cuh"), "rb").read()
+    kern = kern[:kern.index(b"// off[k] = sum of in[0..k)")]
+    h = hashlib.sha256(kern)
+    for f in ("force_mixed.cu", "internal.cuh"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def workload_counts(s, rc, r_in):

@@ -1249,13 +1249,11 @@ static cudaError_t launch_gen_t(cudaStream_t st, int N, const dbl4 *x, const int
   const size_t smem = sizeof(PairP<R>) * MAX_TYPES * MAX_TYPES + sizeof(TripP<R>) * MAX_TYPES * MAX_TYPES * MAX_TYPES +
                       C::smem_slots;
   auto kern = k_force_gen<M, MAXNC, EFLAG, VFLAG>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
   if (N == 0) return cudaSuccess;
+  // set on every launch: the attribute is per device, and launches come from the
+  // caller's threads and the server's worker alike
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
   const int blocks = (N + C::threads - 1) / C::threads;
   kern<<<blocks, C::threads, smem, st>>>(N, x, q, nbr, cnt, sys, (const PairP<R> *)pairs, (const TripP<R> *)trips,
                                          nt, (typename V4t<R>::type *)contrib, (typename V4t<R>::type *)selfF, mask,
