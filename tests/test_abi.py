@@ -57,7 +57,17 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert t.tersoff_params_create(None, 1, None, None, None) == t.ERR_ARG
     assert t.tersoff_compute(None, None, None, 0, None, None, None, 0, 0, None, None, None) == t.ERR_ARG
     assert t.tersoff_md_step(None, 1, None) == t.ERR_ARG
+    assert t.tersoff_neighbor_build_typed(None, None, None, 0, None, None, 0.3, 0, None) == t.ERR_ARG
     assert t.tersoff_version().startswith(b"tersoff-gb300")
+
+
+def test_precision_values_match_header():
+    """The binding's precision constants are the header's enum values."""
+    from paper_1710_00882_gb300 import tersoff as t
+    src = open(os.path.join(ROOT, "include", "tersoff.h")).read()
+    m = re.search(r"typedef enum \{([^}]*)\} tersoff_precision;", src)
+    vals = dict((k.strip(), int(v)) for k, v in re.findall(r"TERSOFF_(\w+)\s*=\s*(\d+)", m.group(1)))
+    assert vals == {"FP64": t.FP64, "MIXED": t.MIXED, "SINGLE": t.SINGLE}
 
 
 def test_ctx_create_fails_cleanly_without_device(lib):
