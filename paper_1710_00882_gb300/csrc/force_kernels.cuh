@@ -253,7 +253,7 @@ __device__ __forceinline__ void block_partial(const R (&v)[7], bool eflag, bool 
 // fast kernel: register slots, unordered neighbour pairs
 
 template <class M, int MAXNC, bool ONE, bool EFLAG, bool VFLAG>
-__global__ void __launch_bounds__(FAST_THREADS, (sizeof(typename M::R) == 4 && MAXNC == 4) ? 7 : 1)
+__global__ void __launch_bounds__(FAST_THREADS, sizeof(typename M::R) == 4 ? (MAXNC == 4 ? 7 : 5) : 1)
 k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const int *__restrict__ nbr,
             const int *__restrict__ cnt, const SysTab *__restrict__ sys,
             const PairP<typename M::R> *__restrict__ gpairs,
@@ -311,14 +311,26 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
   constexpr bool SORT = MAXNC == 8;
   const bool direct = !SORT && active && n <= MAXNC;
 
-  R ux[MAXNC], uy[MAXNC], uz[MAXNC], rr[MAXNC], rl[MAXNC], ir[MAXNC], fc[MAXNC], dfc[MAXNC];
-  int meta[MAXNC];
+  // Slot fields.  The 8-slot kernels keep the four that the K loops read least (the
+  // distance tail, 1/r, f_C' and the slot's list entry and type) in shared memory,
+  // one column per thread, so that more blocks fit an SM; the others stay in registers.
+  constexpr bool SMEM = MAXNC == 8;
+  __shared__ R s_rl[SMEM ? MAXNC : 1][T], s_ir[SMEM ? MAXNC : 1][T], s_dfc[SMEM ? MAXNC : 1][T];
+  __shared__ int s_meta[SMEM ? MAXNC : 1][T];
+  R ux[MAXNC], uy[MAXNC], uz[MAXNC], rr[MAXNC], fc[MAXNC];
+  R rl_r[SMEM ? 1 : MAXNC], ir_r[SMEM ? 1 : MAXNC], dfc_r[SMEM ? 1 : MAXNC];
+  int meta_r[SMEM ? 1 : MAXNC];
+  auto rl = [&](int s) -> R & { if constexpr (SMEM) return s_rl[s][t]; else return rl_r[s]; };
+  auto ir = [&](int s) -> R & { if constexpr (SMEM) return s_ir[s][t]; else return ir_r[s]; };
+  auto dfc = [&](int s) -> R & { if constexpr (SMEM) return s_dfc[s][t]; else return dfc_r[s]; };
+  auto meta = [&](int s) -> int & { if constexpr (SMEM) return s_meta[s][t]; else return meta_r[s]; };
 #pragma unroll
   for (int s = 0; s < MAXNC; ++s) {
     ux[s] = uy[s] = uz[s] = R(0);
-    rr[s] = ir[s] = R(1);
-    rl[s] = fc[s] = dfc[s] = R(0);
-    meta[s] = 0;
+    rr[s] = R(1);
+    ir(s) = R(1);
+    rl(s) = fc[s] = dfc(s) = R(0);
+    meta(s) = 0;
   }
 
   // geometry of slot s from list entry e (neighbour j): unit vector, r, 1/r, f_C, f_C'
@@ -354,10 +366,10 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
     uy[s] = dy * inv;
     uz[s] = dz * inv;
     rr[s] = r;
-    rl[s] = rlo;
-    ir[s] = inv;
-    cutoff_fn<M>(r, rlo, pairs[ONE ? 0 : ti * nt + tj], fc[s], dfc[s]);
-    meta[s] = e | (tj << 8);
+    rl(s) = rlo;
+    ir(s) = inv;
+    cutoff_fn<M>(r, rlo, pairs[ONE ? 0 : ti * nt + tj], fc[s], dfc(s));
+    meta(s) = e | (tj << 8);
   };
 
   // cheap in-cutoff test of entry (i, j)
@@ -394,7 +406,7 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
           mb |= 1ull << s;
           fill_slot(s, s, jj[s], qq[s], xx[s], tj);
         } else {
-          meta[s] = s | (tj << 8);
+          meta(s) = s | (tj << 8);
         }
       }
     }
@@ -532,7 +544,7 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
 #pragma unroll
     for (int b = a + 1; b < MAXNC; ++b) {
       if (b < nc) {
-        const TripP<R> &Tp = trips[ONE ? 0 : (ti * nt + (meta[a] >> 8)) * nt + (meta[b] >> 8)];
+        const TripP<R> &Tp = trips[ONE ? 0 : (ti * nt + (meta(a) >> 8)) * nt + (meta(b) >> 8)];
         const R cost = ux[a] * ux[b] + uy[a] * uy[b] + uz[a] * uz[b];
         const R u = Tp.h - cost;
         const R u2 = u * u;
@@ -557,14 +569,14 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
   for (int a = 0; a < MAXNC; ++a) {
     dz[a] = Fx[a] = Fy[a] = Fz[a] = R(0);
     if (a < nc) {
-      const PairP<R> &P = pairs[ONE ? 0 : ti * nt + (meta[a] >> 8)];
-      const R fR = P.A * M::expneg(P.lam1, P.lam1_lo, rr[a], rl[a]);
-      const R fA = -P.B * M::expneg(P.lam2, P.lam2_lo, rr[a], rl[a]);
+      const PairP<R> &P = pairs[ONE ? 0 : ti * nt + (meta(a) >> 8)];
+      const R fR = P.A * M::expneg(P.lam1, P.lam1_lo, rr[a], rl(a));
+      const R fA = -P.B * M::expneg(P.lam2, P.lam2_lo, rr[a], rl(a));
       R bij, dbij;
       bond_order<M>(zeta[a], P, bij, dbij);
       const R pr = fR + bij * fA;
       e_i += R(0.5) * fc[a] * pr;
-      const R dvdr = R(0.5) * (dfc[a] * pr + fc[a] * (-P.lam1 * fR - bij * P.lam2 * fA));
+      const R dvdr = R(0.5) * (dfc(a) * pr + fc[a] * (-P.lam1 * fR - bij * P.lam2 * fA));
       dz[a] = R(0.5) * fc[a] * fA * dbij;
       Fx[a] = -dvdr * ux[a];
       Fy[a] = -dvdr * uy[a];
@@ -582,7 +594,7 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
 #pragma unroll
     for (int b = a + 1; b < MAXNC; ++b) {
       if (b < nc) {
-        const TripP<R> &Tp = trips[ONE ? 0 : (ti * nt + (meta[a] >> 8)) * nt + (meta[b] >> 8)];
+        const TripP<R> &Tp = trips[ONE ? 0 : (ti * nt + (meta(a) >> 8)) * nt + (meta(b) >> 8)];
         const R cost = ux[a] * ux[b] + uy[a] * uy[b] + uz[a] * uz[b];
         const R u = Tp.h - cost;
         const R u2 = u * u;
@@ -605,10 +617,10 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
         const R Qv = dz[b] * fc[a] * eba;
         const R S = (Pv + Qv) * dg;
         const R PQd = (Pv - Qv) * g * darg;
-        const R cj = S * ir[a];
-        const R ck = S * ir[b];
-        const R ca = dz[b] * dfc[a] * g * eba - cj * cost + PQd;
-        const R cb = dz[a] * dfc[b] * g * eab - ck * cost - PQd;
+        const R cj = S * ir(a);
+        const R ck = S * ir(b);
+        const R ca = dz[b] * dfc(a) * g * eba - cj * cost + PQd;
+        const R cb = dz[a] * dfc(b) * g * eab - ck * cost - PQd;
         Fx[a] -= cj * ux[b] + ca * ux[a];
         Fy[a] -= cj * uy[b] + ca * uy[a];
         Fz[a] -= cj * uz[b] + ca * uz[a];
@@ -625,13 +637,13 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
     R fix = R(0), fiy = R(0), fiz = R(0);
 #pragma unroll
     for (int a = 0; a < MAXNC; ++a) {
-      if (a < nc && ((mb >> (meta[a] & 0xff)) & 1ull)) {
+      if (a < nc && ((mb >> (meta(a) & 0xff)) & 1ull)) {
         fix -= Fx[a];
         fiy -= Fy[a];
         fiz -= Fz[a];
         V4 c;
         c.x = Fx[a]; c.y = Fy[a]; c.z = Fz[a]; c.w = R(0);
-        contrib[(size_t)(meta[a] & 0xff) * N + i] = c;
+        contrib[(size_t)(meta(a) & 0xff) * N + i] = c;
         if (VFLAG) {
           const R dx = rr[a] * ux[a], dy = rr[a] * uy[a], dzz = rr[a] * uz[a];
           red[1] += dx * Fx[a]; red[2] += dy * Fy[a]; red[3] += dzz * Fz[a];
