@@ -407,8 +407,11 @@ __global__ void __launch_bounds__(128) k_sort_lists(int N, const int4 *__restric
 // rev[s][i] = where the force gather finds the contribution of the terms of i's
 // neighbour j = nbr[s][i] on i: the flat index s2 * N + j of i's slot s2 in j's
 // (sorted) list, found by binary search (a 32-bit unsigned value: cap * N < 2^32).
-// One thread per atom; the searches of up to RS slots run interleaved, level by
-// level, so their loads are in flight together.
+// Lists are symmetric, so one search serves both entries of a pair: atom i takes the
+// entries with j > i (the tail of its sorted list), finds s2, and writes rev[s][i]
+// and rev[s2][j]; every entry has exactly one writer.  One thread per atom; the
+// searches of up to RS slots run interleaved, level by level, so their loads are in
+// flight together.
 constexpr int RS = 8;
 __global__ void k_reverse(int N, const int4 *__restrict__ q, const SysCtl *__restrict__ ctl,
                           const int *__restrict__ nbr, const int *__restrict__ cnt, int *__restrict__ rev, RunState *rs,
@@ -419,8 +422,19 @@ __global__ void k_reverse(int N, const int4 *__restrict__ q, const SysCtl *__res
   if (i >= N) return;
   if (ctl && ctl[sys_of(q[i].w)].rebuild == 0) return;
   const int n = cnt[i];
+  // the entries with j > i start at the first index above i (lists are sorted); their
+  // searches then fill whole rounds
+  int first = 0;
+  {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (nbr[(size_t)mid * N + i] > i) hi = mid; else lo = mid + 1;
+    }
+    first = lo;
+  }
   bool missing = false;
-  for (int s0 = 0; s0 < n; s0 += RS) {
+  for (int s0 = first; s0 < n; s0 += RS) {
     int j[RS], lo[RS], hi[RS], found[RS];
 #pragma unroll
     for (int k = 0; k < RS; ++k) j[k] = s0 + k < n ? nbr[(size_t)(s0 + k) * N + i] : -1;
@@ -448,9 +462,13 @@ __global__ void k_reverse(int N, const int4 *__restrict__ q, const SysCtl *__res
 #pragma unroll
     for (int k = 0; k < RS; ++k) {
       if (j[k] < 0) continue;
-      if (found[k] < 0) missing = true;
-      rev[(size_t)(s0 + k) * N + i] =
-          (int)((unsigned)(found[k] < 0 ? 0 : found[k]) * (unsigned)N + (unsigned)j[k]);
+      if (found[k] < 0) {
+        missing = true;
+        rev[(size_t)(s0 + k) * N + i] = (int)(unsigned)j[k];
+        continue;
+      }
+      rev[(size_t)(s0 + k) * N + i] = (int)((unsigned)found[k] * (unsigned)N + (unsigned)j[k]);
+      rev[(size_t)found[k] * N + j[k]] = (int)((unsigned)(s0 + k) * (unsigned)N + (unsigned)i);
     }
   }
   if (missing) atomicOr(&rs->status, ST_REV_MISSING);
