@@ -111,16 +111,23 @@ def force_traffic():
 
 
 def force_kernel_source_hash():
-    """First 16 hex digits of the sha256 of the register force kernel's source: the
-    part of force_kernels.cuh up to the end of k_force_reg (math helpers and the
-    kernel), force_mixed.cu (its instantiation) and internal.cuh."""
+    """First 16 hex digits of the sha256 of the register force kernel's source code:
+    the part of force_kernels.cuh up to the end of k_force_reg (math helpers and the
+    kernel), force_mixed.cu (its instantiation) and internal.cuh, with comments and
+    whitespace removed (an edit of a comment leaves the compiled kernel as it was)."""
     import hashlib
+    import re
     csrc = os.path.join(ROOT, "paper_1710_00882_gb300", "csrc")
-    kern = open(os.path.join(csrc, "force_kernels.cuh"), "rb").read()
-    kern = kern[:kern.index(b"// off[k] = sum of in[0..k)")]
-    h = hashlib.sha256(kern)
+
+    def code(text):
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        return re.sub(r"\s+", "", text).encode()
+
+    kern = open(os.path.join(csrc, "force_kernels.cuh")).read()
+    h = hashlib.sha256(code(kern[:kern.index("// off[k] = sum of in[0..k)")]))
     for f in ("force_mixed.cu", "internal.cuh"):
-        h.update(open(os.path.join(csrc, f), "rb").read())
+        h.update(code(open(os.path.join(csrc, f)).read()))
     return h.hexdigest()[:16]
 
 

@@ -1,4 +1,5 @@
-// Tersoff energy/force kernels: Algorithm 1 of the paper, one thread per atom i.
+// Tersoff energy/force kernels: Algorithm 1 of the paper, one thread (or, for
+// atoms with many neighbours, one warp) per atom i.
 //
 // Per atom i the thread
 //   0. walks i's Verlet list once and marks the in-cutoff entries (Sec. 3: skin
@@ -11,7 +12,9 @@
 //      restructuring of Sec. 2: zeta is complete before any derivative is formed).
 //
 // Fast kernel (k_force_reg): slots live in registers (compile-time slot count 4
-// or 8, loops fully unrolled).  Both K loops run over unordered neighbour pairs
+// or 8, loops fully unrolled; the 8-slot kernel keeps four slot fields in shared
+// memory and sorts its block's atoms by in-cutoff count before the K loops, so that
+// each warp's lanes share their trip counts).  Both K loops run over unordered neighbour pairs
 // {j,k}: cos(theta), g and g' are shared by zeta(i,j,k) and zeta(i,k,j) whenever
 // the angular constants of rows (i,j,k) and (i,k,j) agree (Tersoff's tables take
 // them from atom i), so each is evaluated once per pair instead of twice.  Atoms
@@ -30,8 +33,8 @@
 // i's terms on i itself is minus their sum (translation invariance).  No atomics:
 // the gather (integrate.cu) reads, for each atom m and in-cutoff slot s of its list,
 // the contribution at the flat index rev[s][m] (m's slot in its neighbour's list)
-// and adds them in list order, so forces are bitwise reproducible.  Energy and virial go to per-block partial sums that a
-// single block reduces in a fixed order.
+// and adds them in list order, so forces are bitwise reproducible.  Energy and
+// virial go to per-block partial sums that a single block reduces in a fixed order.
 //
 // Precision: the math policy M (MathD: FP64 mode; MathF: mixed mode; MathS:
 // single mode) fixes the real type R and how distances and exponentials are formed.
