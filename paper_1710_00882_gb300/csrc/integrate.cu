@@ -179,7 +179,7 @@ constexpr int VV_THREADS = 128;   // integrator block size (more resident blocks
 //           some atom moved more than skin/2 since the last build
 // KE: accumulate sum m v^2 of the full-step velocity (after FINISH, before START).
 template <class A, bool KE>
-__global__ void k_vv(int N, int mode, dbl4 *__restrict__ x, dbl4 *__restrict__ v, int4 *__restrict__ q,
+__global__ void __launch_bounds__(VV_THREADS, sizeof(typename A::V) == 16 ? 12 : 1) k_vv(int N, int mode, dbl4 *__restrict__ x, dbl4 *__restrict__ v, int4 *__restrict__ q,
                      const int4 *__restrict__ qref, const typename A::V *__restrict__ contrib,
                      const typename A::V *__restrict__ selfF, const unsigned long long *__restrict__ mask,
                      const int *__restrict__ rev, const SysTab *__restrict__ sys, SysCtl *__restrict__ ctl,
@@ -192,9 +192,11 @@ __global__ void k_vv(int N, int mode, dbl4 *__restrict__ x, dbl4 *__restrict__ v
   double ke = 0.0;
   bool moved = false;
   if (active) {
-    int4 qi = q[i];
-    const int t = type_of(qi.w);
-    const int sid = sys_of(qi.w);
+    // the atom's word (type, system) from the w field of its float64 position (the
+    // drift reads the rest of that line later); the fixed-point copy is only written
+    const int w = (int)__double_as_longlong(reinterpret_cast<const double *>(x + i)[3]);
+    const int t = type_of(w);
+    const int sid = sys_of(w);
     const SysTab &T = sys[sid];
     const Geom &geo = T.geo;
     const double c = T.kick[t];
@@ -223,9 +225,7 @@ __global__ void k_vv(int N, int mode, dbl4 *__restrict__ x, dbl4 *__restrict__ v
       xi.y = fma(dt, vi.y, xi.y);
       xi.z = fma(dt, vi.z, xi.z);
       x[i] = xi;
-      qi.x = fixed_q(xi.x, geo.to_q[0]);
-      qi.y = fixed_q(xi.y, geo.to_q[1]);
-      qi.z = fixed_q(xi.z, geo.to_q[2]);
+      const int4 qi = make_int4(fixed_q(xi.x, geo.to_q[0]), fixed_q(xi.y, geo.to_q[1]), fixed_q(xi.z, geo.to_q[2]), w);
       q[i] = qi;
       const int4 qr = qref[i];
       const float dx = (float)qdiff(qi.x, qr.x) * geo.q_to_f[0];
