@@ -94,6 +94,27 @@ def test_compressed_many_neighbours(T, ctx):
     check(T, out, ref, "compressed", mixed_f_rel=4e-6)
 
 
+def test_more_than_32_neighbours(T, ctx):
+    """Si compressed to a = 2.9 A: 33-35 in-cutoff neighbours per atom, so every atom
+    leaves the register kernel for the warp kernel with two slots per lane.  Energy and
+    forces (|F| up to ~80 eV/A, bounds relative to the largest force as for the other
+    compressed case)."""
+    rng = np.random.default_rng(12)
+    s = wl.diamond(4, 4, 4, 2.9)
+    s.pos = s.pos + rng.normal(0, 0.03, size=s.pos.shape)
+    P = product_params(ctx, s.species)
+    nl = T.NeighborList(ctx, s.pos, s.box, P.cutoff, 0.0)
+    counts, _ = nl.get()
+    assert counts.min() > 32
+    tab, _ = oracle_table(s.species)
+    Eo, Fo, _ = oracle.energy_forces(s.pos, s.types, s.box, tab)
+    fmax = np.abs(Fo).max()
+    for prec, er, fa in ((T.FP64, FP64_E_REL, FP64_F_ABS), (T.MIXED, MIX_E_REL, max(MIX_F_ABS, 4e-6 * fmax)),
+                         (T.SINGLE, SGL_E_REL, max(SGL_F_ABS, 4e-5 * fmax))):
+        E, F, _ = T.compute(ctx, P, s.pos, s.types, s.box, prec=prec)
+        assert_parity(E, F, None, Eo, Fo, None, er, fa, 0, f"dense prec {prec}")
+
+
 def test_two_cells_per_side(T, ctx):
     """Smallest legal boxes: 2 cells per side (box < 3 * r_list)."""
     s = wl.sic_box(2, seed=43, T=1000.0)
