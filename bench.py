@@ -35,28 +35,35 @@ METRIC = "Tersoff atom-steps/s, NVE velocity Verlet, mixed precision (FP64 path 
 WORKLOAD = "Si diamond 40x40x40 = 512,000 atoms, sigma 0.05 A, 1000 K, Si(C), skin 0.3 A, dt 1 fs"
 SKIN = 0.3
 DT = 1e-3
+# ~0.1 ms device-side wait enqueued before each start event (outside the timed region)
+SPIN_CYCLES = 200_000
 
-# Float32 operations of the mixed-precision force kernel as written in force_kernels.cuh
-# (FMA = 2, add/sub/mul = 1, each rcp/rsqrt/lg2/ex2/sin/cos = 1; integer, load and
-# compare work not counted):
-#   per Verlet-list entry tested (fixed-point difference scaled, r^2):          8
-#   per in-cutoff pair: relative vector to ~1 ulp (30), |d| head+tail (41), unit
-#     vector (3), f_R and f_A with split exponents (38), b and db/dzeta (14),
-#     pair energy / dV/dr / dV/dzeta / force (19), self-force sum (3):        148
+# Algorithmic work of one force evaluation, counted once from the kernel source
+# (force_kernels.cuh), FMA = 2, add/sub/mul = 1, each rcp/rsqrt/lg2/ex2/sin/cos = 1;
+# integer, load and compare work not counted.  The method's own work (Algorithm 1,
+# Eqs. 1-3) is the same in every precision:
+#   per Verlet-list entry tested (scaled relative vector, r^2):                 8
+#   per in-cutoff pair: relative vector (3), r^2 (5), rsqrt and r (2), unit
+#     vector (3), f_R and f_A, one exponential each (8), b and db/dzeta (14),
+#     pair energy / dV/dr / dV/dzeta / force (19), self-force sum (3):          57
 #   per in-cutoff pair inside the f_C taper (R - D < r): w, sin, cos, f_C, f_C': 10
 #   per ordered triplet: each unordered pair {j,k} evaluates cos, g (12) and
 #     both zeta terms (6) in the first K loop and cos, g, g' and the force
 #     terms on j and k (62) in the second, shared by (i,j,k) and (i,k,j):     40
 C_ENTRY = 8
-C_PAIR = 148
+C_PAIR = 57
 C_TAPER = 10
 C_TRIPLET = 40
-# Single mode forms the pair geometry without compensation: relative vector (3),
-# r^2 (5), rsqrt and r (2), and f_R, f_A from one ex2 each (8) in place of the
-# mixed kernel's 30 + 41 + 38; the rest is the same:                            57
-C_PAIR_SINGLE = 57
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x 2 x max SM clock
-FP64_PEAK_TFLOPS = 1.25                              # GB300 nominal FP64
+# Mixed mode adds, per in-cutoff pair, the work that keeps r and lambda*r to ~1 ulp:
+# the relative vector rounded once from a head/tail split (12 more than one product
+# per component), the Newton tail of r (4) and the head/tail exponent of f_R and f_A
+# (7 more each): float32 work beyond the method's own, reported apart as overhead.
+C_PAIR_MIXED_OVERHEAD = 30
+# Peaks.  Derived from unit counts and the maximum SM clock: 152 SMs x 128 FP32 lanes
+# x 2 flop x 2.07 GHz; FP64: GB300's nominal 1.25 TFLOP/s.  The FMA-pipe probe
+# (libalu_peaks.so) measures both in the same run.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP64_PEAK_TFLOPS = 1.25
 
 
 def env_int(name, default):
@@ -231,6 +238,9 @@ def run_gpu(args, ws, rank, local):
         barrier(ws)
         torch.cuda.synchronize()
         with torch.cuda.stream(stream):
+            # the device waits ~0.1 ms (after the flush) while the host enqueues the
+            # graph launch, so that no host latency lands between the events
+            torch.cuda._sleep(SPIN_CYCLES)
             e0.record(stream)
         md.step_async(steps)
         with torch.cuda.stream(stream):
@@ -246,6 +256,7 @@ def run_gpu(args, ws, rank, local):
         for k in range(nflush):
             with torch.cuda.stream(stream):
                 flush.fill_(float(k))
+                torch.cuda._sleep(SPIN_CYCLES)
                 evs[k][0].record(stream)
             md.step_async(1)
             with torch.cuda.stream(stream):
@@ -264,8 +275,14 @@ def run_gpu(args, ws, rank, local):
         md.profile(False)
         md.sync()
         rebuilds = st1["rebuilds"] - st0["rebuilds"]
+        # the state the timed steps left (positions, the forces of its last evaluation and
+        # its potential energy), kept for the error check against the oracle
+        pos_f, _, f_f = md.get(forces=True)
+        pe_f = md.step(0, trace=True)[0][0]
+        final = {"pos": pos_f, "forces": f_f, "energy": pe_f, "types": sysm.types, "box": sysm.box,
+                 "species": sysm.species}
         return ms_total, ms_flushed, prof, dict(rebuilds=rebuilds, rebuilds_flushed=st2["rebuilds"] - st1["rebuilds"],
-                                                steps=steps, prof_steps=nprof), md
+                                                steps=steps, prof_steps=nprof, final=final), md
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -275,7 +292,7 @@ def run_gpu(args, ws, rank, local):
     one_sg, fl_sg, prof_sg, st_sg, md_sg = timed(T.SINGLE, k_mix, args.warmup)
     md_mix = md_64 = md_sg = None
     # 3C-SiC 50^3 cells with 5% vacancies (950,000 atoms), mixed, dt 0.5 fs
-    sic = None
+    sic = sic_final = None
     if not args.no_sic:
         sc = wl.sic_1m(seed=4 + rank)
         tab2, m2 = pp.for_species(sc.species)
@@ -283,6 +300,7 @@ def run_gpu(args, ws, rank, local):
         k_sic = max(3, args.steps // 2)
         one_s, fl_s, prof_s, st_s, md_s = timed(T.MIXED, k_sic, args.warmup, sc, P2, 0.5e-3)
         md_s = None
+        sic_final = st_s["final"]
         fl_tot_s = allreduce_max(ws, sum(fl_s))
         one_s = allreduce_max(ws, one_s)
         sic = {"workload": f"3C-SiC a = 4.36, 50^3 cells, 5% vacancies = {sc.n} atoms, 1500 K, Tersoff 1989 "
@@ -294,6 +312,8 @@ def run_gpu(args, ws, rank, local):
                "phases_ms_per_step_profiled": {k: prof_s[0][n] / st_s["prof_steps"] for n, k in
                                                enumerate(("integrator", "list_build", "force_register_kernel",
                                                           "force_overflow_and_reduce", "bookkeeping"))}}
+    # FMA-pipe throughput of this device, measured in the same run (clocks sampled)
+    peaks = measure_alu_peaks()
     clk = clocks.stop()
 
     # headline: one launch per step with L2 flushed before each step
@@ -305,17 +325,18 @@ def run_gpu(args, ws, rank, local):
     value64 = ws * s.n * len(fl_64) / (tot_64 / 1e3)
     value_sg = ws * s.n * len(fl_sg) / (tot_sg / 1e3)
 
-    # roofline of the dominant kernel (the force kernel), achieved from algorithmic flops
+    # roofline of the dominant kernel (the register force kernel): the method's flops
+    # per launch over its event-timed launch duration (profiled pass, one launch per step)
     flops = C_ENTRY * n_list + C_PAIR * npair + C_TAPER * ntaper + C_TRIPLET * ntrip
-    # force phase per step (register kernel + overflow kernel) from the profiled pass
-    # the register force kernel alone (one launch per step; events around it)
+    overhead = C_PAIR_MIXED_OVERHEAD * npair
     f_ms = prof_mix[0][2] / prof_mix[1][2]
     f64_ms = prof_64[0][2] / prof_64[1][2]
     fsg_ms = prof_sg[0][2] / prof_sg[1][2]
     achieved = flops / (f_ms / 1e3) / 1e12
     achieved64 = flops / (f64_ms / 1e3) / 1e12
-    flops_sg = C_ENTRY * n_list + C_PAIR_SINGLE * npair + C_TAPER * ntaper + C_TRIPLET * ntrip
-    achieved_sg = flops_sg / (fsg_ms / 1e3) / 1e12
+    achieved_sg = flops / (fsg_ms / 1e3) / 1e12
+    p32 = peaks.get("fp32_tflops") if peaks else None
+    p64 = peaks.get("fp64_tflops") if peaks else None
 
     # end to end through the C ABI with host buffers: one tersoff_md_run call of 100 steps
     e2e = None
@@ -356,29 +377,23 @@ def run_gpu(args, ws, rank, local):
                    "parallelism": "replicas" if ws > 1 else "single GPU",
                    "step_launch": "one CUDA graph launch per timed step (WHILE over steps, IF around the "
                                   "list rebuild)"},
-        "one_launch": {"value": ws * s.n * k_mix / (one_mix / 1e3), "unit": "atom-steps/s", "steps": k_mix,
-                       "ms_per_step": one_mix / k_mix, "rebuilds": st_mix["rebuilds"],
-                       "how": "the same state, K steps as one graph launch as tersoff_md_step runs them; L2 "
-                              "flushed once before (per-step working set ~125 MB, about the L2 size)"},
-        "fp64": {"value": value64, "unit": "atom-steps/s", "steps": len(fl_64), "ms_per_step": tot_64 / len(fl_64),
-                 "mixed_over_fp64": value / value64,
-                 "force_kernel_ms": f64_ms, "force_kernel_achieved_tflops": achieved64,
-                 "peak_tflops": FP64_PEAK_TFLOPS, "frac_of_fp64_peak": achieved64 / FP64_PEAK_TFLOPS},
-        "single": {"value": value_sg, "unit": "atom-steps/s", "steps": len(fl_sg),
-                   "ms_per_step": tot_sg / len(fl_sg), "single_over_mixed": value_sg / value,
-                   "force_kernel_ms": fsg_ms, "force_kernel_achieved_tflops": achieved_sg,
-                   "frac_of_fp32_peak": achieved_sg / FP32_PEAK_TFLOPS, "algorithmic_flops_per_launch": flops_sg,
-                   "flops_per_unit": {"list_entry": C_ENTRY, "pair": C_PAIR_SINGLE, "taper_pair": C_TAPER,
-                                      "ordered_triplet": C_TRIPLET},
-                   "what": "float32 throughout the force evaluation (the paper's single mode), float64 "
-                           "integration; same workload and timing as the headline"},
-        "phases_ms_per_step_profiled": {k: prof_mix[0][n] / st_mix["prof_steps"] for n, k in
-                                        enumerate(("integrator", "list_build", "force_register_kernel",
-                                                   "force_overflow_and_reduce", "bookkeeping"))},
-        "roofline": {"bound": "alu", "kernel": "k_force_reg<float, 4> (mixed, register slots)", "achieved": achieved,
+        "roofline": {"bound": "alu", "kernel": "k_force_reg<MathF, 4> (mixed, register slots)", "achieved": achieved,
                      "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                     "traffic": traffic, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
-                     "algorithmic_flops_per_launch": flops, "kernel_ms": f_ms,
+                     "traffic": traffic,
+                     "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum of one launch in the committed "
+                                       "ncu capture profiles/force_kernel_si512k_mixed.md (null once the kernel "
+                                       "source differs from the captured one); not measured in this run",
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
+                     "peak_measured": p32, "frac_of_measured": achieved / p32 if p32 else None,
+                     "algorithmic_flops_per_launch": flops,
+                     "what_is_counted": "the method's own float32 work (Algorithm 1): 8 per list entry, 57 per "
+                                        "in-cutoff pair, 10 per taper pair, 40 per ordered triplet",
+                     "overhead_flops_per_launch": overhead,
+                     "overhead_what": "mixed mode's compensation (relative vector rounded once, Newton tail "
+                                      "of r, head+tail exponents): 30 flops per in-cutoff pair",
+                     "achieved_with_overhead": (flops + overhead) / (f_ms / 1e3) / 1e12,
+                     "frac_with_overhead": (flops + overhead) / (f_ms / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
+                     "kernel_ms": f_ms,
                      "timing": "CUDA events around each launch of the register force kernel in a profiled "
                                "pass of the same state (one launch per step, L2 flushed before each step)",
                      "counts": {"list_entries": n_list, "pairs": npair, "taper_pairs": ntaper,
@@ -386,22 +401,57 @@ def run_gpu(args, ws, rank, local):
                      "flops_per_unit": {"list_entry": C_ENTRY, "pair": C_PAIR, "taper_pair": C_TAPER,
                                         "ordered_triplet": C_TRIPLET}},
         "gpu_launches": launches,
-        "rebuilds_in_timed_steps": {"mixed": st_mix["rebuilds_flushed"], "fp64": st_64["rebuilds_flushed"],
-                                    "single": st_sg["rebuilds_flushed"]},
         "clocks": clk,
     }
     if e2e:
         line["e2e"] = e2e
+    line["one_launch"] = {"value": ws * s.n * k_mix / (one_mix / 1e3), "unit": "atom-steps/s", "steps": k_mix,
+                          "ms_per_step": one_mix / k_mix, "rebuilds": st_mix["rebuilds"],
+                          "how": "the same state, K steps as one graph launch as tersoff_md_step runs them; L2 "
+                                 "flushed once before (per-step working set ~125 MB, about the L2 size)"}
+    line["phases_ms_per_step_profiled"] = {k: prof_mix[0][n] / st_mix["prof_steps"] for n, k in
+                                           enumerate(("integrator", "list_build", "force_register_kernel",
+                                                      "force_overflow_and_reduce", "bookkeeping"))}
+    line["rebuilds_in_timed_steps"] = {"mixed": st_mix["rebuilds_flushed"], "fp64": st_64["rebuilds_flushed"],
+                                       "single": st_sg["rebuilds_flushed"]}
     if sic:
         line["sic_1m"] = sic
-    if args.serving_jobs > 0:
-        line["serving"] = serving_bench(ctx, args.serving_jobs)
     if rank == 0 and not args.no_cpu:
+        finals = {"mixed": st_mix["final"], "fp64": st_64["final"], "single": st_sg["final"]}
+        if sic:
+            finals["sic_1m_mixed"] = sic_final
         line["cpu_baseline"] = cpu_baseline(args, s, quick=True)
+        line["error"] = oracle_error(finals)
         try:
             line["cpu_baseline_all_cores"] = cpu_baseline_all_cores()
         except Exception as e:   # a box without room for one replica per core
             line["cpu_baseline_all_cores"] = {"unavailable": str(e)[:200]}
+    if args.serving_jobs > 0:
+        line["serving"] = serving_bench(ctx, args.serving_jobs)
+    # the FP64 and single lines and the error check last: a reader of the line's tail sees them
+    tail_keys = {
+        "fp64": {"value": value64, "unit": "atom-steps/s", "steps": len(fl_64), "ms_per_step": tot_64 / len(fl_64),
+                 "mixed_over_fp64": value / value64,
+                 "force_kernel_ms": f64_ms, "force_kernel_achieved_tflops": achieved64,
+                 "algorithmic_flops_per_launch": flops,
+                 "peak_tflops": FP64_PEAK_TFLOPS, "peak_source": "GB300 nominal FP64",
+                 "frac_of_fp64_peak": achieved64 / FP64_PEAK_TFLOPS,
+                 "peak_measured_tflops": p64, "frac_of_measured": achieved64 / p64 if p64 else None,
+                 "what_is_counted": "the same method flops as the mixed kernel; each float64 exp, log2, "
+                                    "division, rsqrt or sincospi counts 1 (they run as software sequences "
+                                    "on the FP64 pipe)"},
+        "single": {"value": value_sg, "unit": "atom-steps/s", "steps": len(fl_sg),
+                   "ms_per_step": tot_sg / len(fl_sg), "single_over_mixed": value_sg / value,
+                   "force_kernel_ms": fsg_ms, "force_kernel_achieved_tflops": achieved_sg,
+                   "frac_of_fp32_peak": achieved_sg / FP32_PEAK_TFLOPS,
+                   "frac_of_measured": achieved_sg / p32 if p32 else None, "algorithmic_flops_per_launch": flops,
+                   "what": "float32 throughout the force evaluation (the paper's single mode), float64 "
+                           "integration; same workload and timing as the headline"},
+        "alu_peaks_measured": peaks
+    }
+    line.update(tail_keys)
+    if "error" in line:
+        line["error"] = line.pop("error")
     return line
 
 
@@ -461,6 +511,45 @@ def serving_bench(ctx, njobs, budget_gb=4.0, max_slots=512, chunk=25):
         arr = np.cumsum(rng.exponential(1.0 / lam, size=len(jobs)))
         arr -= arr[0]
         out["poisson"][f"{f:.1f}"] = dict(run(arr), rate_jobs_per_s=lam)
+    return out
+
+
+def measure_alu_peaks():
+    """FP32 and FP64 FMA throughput of the current device (libalu_peaks.so): the
+    measured peaks the force kernels' achieved flop rates are reported beside."""
+    import ctypes
+    path = os.path.join(ROOT, "paper_1710_00882_gb300", "libalu_peaks.so")
+    try:
+        lib = ctypes.CDLL(path)
+    except OSError as e:
+        return {"unavailable": str(e)[:200]}
+    out = (ctypes.c_double * 5)()
+    rc = lib.alu_peaks_measure(out)
+    if rc != 0:
+        return {"unavailable": f"alu_peaks_measure returned {rc}"}
+    return {"fp32_tflops": out[0], "fp32_ms": out[1], "fp64_tflops": out[2], "fp64_ms": out[3], "sms": int(out[4]),
+            "how": "independent FMA chains (8 per thread FP32, 4 FP64), 8 blocks of 256 threads per SM, best of "
+                   "5 (FP32) / 3 (FP64) event-timed launches after one warm-up; 2 flop per FMA"}
+
+
+def oracle_error(finals):
+    """Error of each timed run's end state against the FP64 oracle, evaluated on the
+    same positions: relative energy error and force max-abs error (eV/A).  Part of the
+    CPU leg (after every timed region); the oracle only checks here."""
+    from oracle import oracle, params as op
+    out = {"vs": "FP64 oracle (oracle/tersoff_oracle.c) on the positions the timed steps ended at; energy = the "
+                 "state's potential energy, forces = its last force evaluation"}
+    for name, f in finals.items():
+        if f is None:
+            continue
+        sp = tuple(f["species"])
+        tab = op.si_table() if sp == ("Si",) else op.sic_table()
+        t0 = time.perf_counter()
+        Eo, Fo, _ = oracle.energy_forces(f["pos"], f["types"], f["box"], tab)
+        out[name] = {"energy_rel": abs(f["energy"] - Eo) / abs(Eo), "force_max_abs": float(np.abs(f["forces"] - Fo).max()),
+                     "energy": f["energy"], "energy_oracle": Eo, "oracle_s": time.perf_counter() - t0}
+    out["bounds"] = {"fp64": {"energy_rel": 1e-12, "force_max_abs": 1e-10},
+                     "mixed": {"energy_rel": 1e-6, "force_max_abs": 1e-4}}
     return out
 
 

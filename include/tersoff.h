@@ -81,7 +81,8 @@ typedef enum { TERSOFF_FP64 = 0, TERSOFF_MIXED = 1, TERSOFF_SINGLE = 2 } tersoff
 /* flags */
 #define TERSOFF_HOST_PTRS 0
 #define TERSOFF_DEVICE_PTRS 1     /* array arguments are device pointers */
-#define TERSOFF_DETERMINISTIC 2   /* reverse-accumulation scatter: run-to-run bitwise identical */
+/* There is no determinism flag: every force scatter is a reverse accumulation in
+ * list order (no atomics), so results are run-to-run bitwise identical always. */
 
 typedef struct tersoff_ctx tersoff_ctx;
 typedef struct tersoff_params tersoff_params;
@@ -197,10 +198,10 @@ int tersoff_md_run(tersoff_ctx *ctx, double *pos, double *vel, const int32_t *ty
  * not allocate device memory while they run: a program whose framework allocator
  * has already reserved the device's memory (a cudaMalloc would fail or make it
  * give memory back), or a latency-critical loop where cudaMalloc/cudaFree would
- * synchronize the device.  It computes what tersoff_compute computes (energy,
- * forces and virial of one configuration, Algorithm 1, Eqs. 1-3, list built
- * internally with skin 0) and calls no cudaMalloc, cudaFree or other allocating
- * routine: every working buffer lives in one fixed device array of
+ * synchronize the device.  It computes the same energy, forces and virial as
+ * tersoff_compute with no list given (list built internally with skin 0) and calls
+ * no cudaMalloc, cudaFree or other allocating routine: every working buffer lives
+ * in one fixed device array of
  * TERSOFF_NOALLOC_SCRATCH_BYTES (about 22 MB) compiled into the library, which
  * every device that loads it holds until the process exits.
  *
@@ -221,6 +222,8 @@ int tersoff_md_run(tersoff_ctx *ctx, double *pos, double *vel, const int32_t *ty
  *
  * The first call on a device looks up the array's device address with that
  * device current and keeps it; make that first call before any stream capture.
+ * The kept address belongs to the device's primary context: calls made after
+ * that context was torn down (cudaDeviceReset) are not supported.
  * All calls on a device share the array and find the last call's contents in it;
  * each call clears what must start at zero.  Calls whose GPU work may overlap
  * (several host threads, or streams not ordered with each other) race on the

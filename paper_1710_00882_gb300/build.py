@@ -1,7 +1,9 @@
 """Build libtersoff.so in-tree with nvcc for sm_103a (GB300).
 
 Each .cu in csrc/ compiles to an object in parallel; the objects link into
-paper_1710_00882_gb300/libtersoff.so.  No cmake, no torch extension machinery.
+paper_1710_00882_gb300/libtersoff.so.  csrc/peaks/alu_peaks.cu (the FMA-pipe
+throughput probe the benchmark reports its roofline against) builds, alongside, into
+libalu_peaks.so.  No cmake, no torch extension machinery.
 """
 import concurrent.futures as cf
 import glob
@@ -15,6 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtersoff.so")
+PEAKS_SRC = os.path.join(CSRC, "peaks", "alu_peaks.cu")
+PEAKS_LIB = os.path.join(HERE, "libalu_peaks.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
          "-I", CSRC, "--expt-relaxed-constexpr"]
@@ -35,7 +39,9 @@ def _sources():
 
 
 def _stale():
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(PEAKS_LIB):
+        return True
+    if os.path.getmtime(PEAKS_SRC) > os.path.getmtime(PEAKS_LIB):
         return True
     t = os.path.getmtime(LIB)
     deps = _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) + \
@@ -59,8 +65,19 @@ def build(force=False, verbose=False, extra=()):
             print(r.stdout + r.stderr)
         return obj
 
+    def build_peaks():
+        tmp = PEAKS_LIB + ".tmp"
+        cmd = [nv, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", *extra, PEAKS_SRC,
+               "-o", tmp, "-cudart", "static"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed for {PEAKS_SRC}:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, PEAKS_LIB)
+
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:
+        peaks = ex.submit(build_peaks)
         objs = list(ex.map(compile_one, _sources()))
+        peaks.result()
     tmp = LIB + ".tmp"
     cmd = [nv, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"]
     r = subprocess.run(cmd, capture_output=True, text=True)

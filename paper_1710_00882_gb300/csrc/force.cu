@@ -36,7 +36,8 @@ __global__ void __launch_bounds__(1024) k_reduce_partials(const double *__restri
 }
 
 #define TSF_FORCE_DECL(NAME)                                                                                        \
-  cudaError_t NAME(int part, cudaStream_t st, int fast_slots, bool one_type, int gen_slots, int eflag, int vflag,  \
+  cudaError_t NAME(int part, cudaStream_t st, int fast_slots, const FastTab &ft, int gen_slots, int eflag,       \
+                   int vflag,                                                                                      \
                    int N, const dbl4 *x, const int4 *q, const int *nbr, const int *cnt, const SysTab *sys,         \
                    const void *pairs, const void *trips, int nt, void *contrib, void *selfF,                       \
                    unsigned long long *mask, int *work, int *nwork, double *partial, RunState *rs, double *eatom,  \
@@ -70,7 +71,7 @@ int force_queue_blocks(int N) { return (N + FAST_THREADS - 1) / FAST_THREADS + 2
 // virial are added to rs->epot / rs->virial.  part: 1 launches the register
 // kernel(s) only, 2 the rest (overflow or general kernel and the reduction), 3 both.
 // stats: record the largest in-cutoff counts (rs->maxnc, rs->maxnc_t).
-cudaError_t launch_force_part(int part, cudaStream_t st, int prec, int fast_slots, bool one_type, int gen_slots,
+cudaError_t launch_force_part(int part, cudaStream_t st, int prec, int fast_slots, const FastTab &ft, int gen_slots,
                               int eflag, int vflag, int N, const dbl4 *x, const int4 *q, const int *nbr,
                               const int *cnt, const SysTab *sys, const void *pairs, const void *trips, int nt,
                               void *contrib, void *selfF, unsigned long long *mask, int *work, int *nwork,
@@ -78,7 +79,7 @@ cudaError_t launch_force_part(int part, cudaStream_t st, int prec, int fast_slot
 {
   auto f = prec == PREC_FP64 ? launch_force_fp64 : prec == PREC_MIXED ? launch_force_mixed : launch_force_single;
   int rows = 0;
-  cudaError_t e = f(part, st, fast_slots, one_type, gen_slots, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt,
+  cudaError_t e = f(part, st, fast_slots, ft, gen_slots, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt,
                     contrib, selfF, mask, work, nwork, partial, rs, eatom, routes, stats, &rows);
   if (e != cudaSuccess) return e;
   if ((eflag || vflag) && rows > 0 && (part & 2)) {
@@ -88,13 +89,13 @@ cudaError_t launch_force_part(int part, cudaStream_t st, int prec, int fast_slot
   return e;
 }
 
-cudaError_t launch_force(cudaStream_t st, int prec, int fast_slots, bool one_type, int gen_slots, int eflag,
+cudaError_t launch_force(cudaStream_t st, int prec, int fast_slots, const FastTab &ft, int gen_slots, int eflag,
                          int vflag, int N, const dbl4 *x, const int4 *q, const int *nbr, const int *cnt,
                          const SysTab *sys, const void *pairs, const void *trips, int nt, void *contrib, void *selfF,
                          unsigned long long *mask, int *work, int *nwork, double *partial, RunState *rs,
                          double *eatom)
 {
-  return launch_force_part(3, st, prec, fast_slots, one_type, gen_slots, eflag, vflag, N, x, q, nbr, cnt, sys, pairs,
+  return launch_force_part(3, st, prec, fast_slots, ft, gen_slots, eflag, vflag, N, x, q, nbr, cnt, sys, pairs,
                            trips, nt, contrib, selfF, mask, work, nwork, partial, rs, eatom, nullptr, 1);
 }
 

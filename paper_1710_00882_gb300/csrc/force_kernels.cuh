@@ -50,6 +50,8 @@
 // instantiated in a translation unit of its own (force_fp64.cu, force_mixed.cu,
 // force_single.cu) so that the three compile in parallel.
 #pragma once
+#include <type_traits>
+
 #include "internal.cuh"
 
 namespace tsf {
@@ -255,12 +257,38 @@ __device__ __forceinline__ void block_partial(const R (&v)[7], bool eflag, bool 
 // ============================================================================
 // fast kernel: register slots, unordered neighbour pairs
 
-template <class M, int MAXNC, bool ONE, bool EFLAG, bool VFLAG>
+// Relative-vector component d = dq L/2^32 rounded once (mixed mode): the int32
+// difference is split into a 24-bit head h and an 8-bit tail l, both exact in float,
+// and the scale into float head sh + tail sl; d = h sh + (l sh + h sl), the small
+// terms formed first, so that the final FMA rounds the whole sum once.
+__device__ __forceinline__ float qd_once(int dq, float sh, float sl)
+{
+  const float h = (float)(dq & ~0xff);
+  const float l = (float)(dq & 0xff);
+  return __fmaf_rn(h, sh, __fmaf_rn(l, sh, __fmul_rn(h, sl)));
+}
+
+// A e^{-lambda r} in float32 (mixed mode) for r = rh + rl: y = mu r with mu =
+// lambda log2(e) given as float head muh + tail mul; muh rh is split exactly with an
+// FMA, so y = yh + yl with |yl| ~ 1e-6, and 2^{-y} = 2^{-yh} (1 - yl ln 2) to first
+// order in the tail, with A folded into the tail factor (Aln2 = A ln 2).
+__device__ __forceinline__ float aexp_mixed(float A, float Aln2, float muh, float mul, float rh, float rl)
+{
+  const float yh = __fmul_rn(muh, rh);
+  const float yl = __fadd_rn(__fmaf_rn(muh, rh, -yh), __fmaf_rn(mul, rh, __fmul_rn(muh, rl)));
+  return __fmul_rn(MathF::ex2(-yh), __fmaf_rn(-Aln2, yl, A));
+}
+
+// KIND: how the table is read (FastTab): 0 from the device table through shared
+// memory, with the lambda3 factor of Eq. 3 evaluated per term; 1 (one type) and 2
+// (two types) from the kernel argument kp (constant bank), lambda3 = 0 compiled out.
+template <class M, int MAXNC, int KIND, bool EFLAG, bool VFLAG>
 __global__ void __launch_bounds__(FAST_THREADS, sizeof(typename M::R) == 4 ? (MAXNC == 4 ? 7 : 5) : 1)
 k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const int *__restrict__ nbr,
             const int *__restrict__ cnt, const SysTab *__restrict__ sys,
             const PairP<typename M::R> *__restrict__ gpairs,
             const TripP<typename M::R> *__restrict__ gtrips, int nt,
+            const __grid_constant__ KParams<typename M::R> kp,
             typename V4t<typename M::R>::type *__restrict__ contrib,
             typename V4t<typename M::R>::type *__restrict__ selfF, unsigned long long *__restrict__ mask,
             int *__restrict__ work, int *__restrict__ nwork, double *__restrict__ partial, RunState *rs,
@@ -270,15 +298,33 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
   using R = typename M::R;
   using V4 = typename V4t<R>::type;
   constexpr bool MIXED = sizeof(R) == 4;   // float32 arithmetic on fixed-point positions (mixed or single)
+  constexpr bool L3 = KIND == 0;           // the lambda3 factor is evaluated
+  constexpr bool ONE = KIND == 1;
   constexpr int T = FAST_THREADS;
-  __shared__ PairP<R> pairs[ONE ? 1 : MAX_TYPES * MAX_TYPES];
-  __shared__ TripP<R> trips[ONE ? 1 : MAX_TYPES * MAX_TYPES * MAX_TYPES];
+  __shared__ PairP<R> spairs[KIND == 0 ? MAX_TYPES * MAX_TYPES : 1];
+  __shared__ TripP<R> strips[KIND == 0 ? MAX_TYPES * MAX_TYPES * MAX_TYPES : 1];
   __shared__ int warp_over[T / 32];
 
   if (rs->status != 0) return;   // uniform across the grid
-  if (threadIdx.x < (ONE ? 1 : nt * nt)) pairs[threadIdx.x] = gpairs[threadIdx.x];
-  if (threadIdx.x < (ONE ? 1 : nt * nt * nt)) trips[threadIdx.x] = gtrips[threadIdx.x];
-  __syncthreads();
+  if constexpr (KIND == 0) {
+    if (threadIdx.x < nt * nt) spairs[threadIdx.x] = gpairs[threadIdx.x];
+    if (threadIdx.x < nt * nt * nt) strips[threadIdx.x] = gtrips[threadIdx.x];
+    __syncthreads();
+  }
+  // table rows: (ti,tj,tj) for the pair terms, (ti,tj,tk) for the angular terms.
+  // Returned by value: fields of kp at fixed offsets then enter the arithmetic as
+  // constant-bank operands (a reference would be a generic pointer into the
+  // parameter space, read with loads).
+  auto pairp = [&](int ti_, int tj_) -> PairP<R> {
+    if constexpr (KIND == 0) return spairs[ti_ * nt + tj_];
+    else if constexpr (KIND == 1) return kp.p[0];
+    else return kp.p[ti_ * 2 + tj_];
+  };
+  auto tripp = [&](int ti_, int tj_, int tk_) -> TripP<R> {
+    if constexpr (KIND == 0) return strips[(ti_ * nt + tj_) * nt + tk_];
+    else if constexpr (KIND == 1) return kp.t[0];
+    else return kp.t[(ti_ * 2 + tj_) * 2 + tk_];
+  };
 
   const int t = threadIdx.x;
   const int tg = blockIdx.x * T + t;
@@ -340,14 +386,17 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
   auto fill_slot = [&](int s, int e, int j, const int4 &qj, const dbl4 &xj, int tj) {
     R dx, dy, dz, r, rlo, inv;
     if (MIXED && M::fine) {
-      float dh[3], dl[3];
-      qd_fine(qdiff(qj.x, qi.x), gp->q_to_f[0], gp->q_to_f_lo[0], dh[0], dl[0]);
-      qd_fine(qdiff(qj.y, qi.y), gp->q_to_f[1], gp->q_to_f_lo[1], dh[1], dl[1]);
-      qd_fine(qdiff(qj.z, qi.z), gp->q_to_f[2], gp->q_to_f_lo[2], dh[2], dl[2]);
-      float rh_, rl_, irh_;
-      norm_fine(dh, dl, rh_, rl_, irh_);
-      dx = (R)dh[0]; dy = (R)dh[1]; dz = (R)dh[2];
-      r = (R)rh_; rlo = (R)rl_; inv = (R)irh_;
+      // d rounded once per component; r = |d| as head + tail from one Newton step on
+      // the float32 square, so that lambda r (|d| ~ 2 A, lambda r ~ 6) keeps ~1 ulp
+      dx = (R)qd_once(qdiff(qj.x, qi.x), gp->q_to_f[0], gp->q_to_f_lo[0]);
+      dy = (R)qd_once(qdiff(qj.y, qi.y), gp->q_to_f[1], gp->q_to_f_lo[1]);
+      dz = (R)qd_once(qdiff(qj.z, qi.z), gp->q_to_f[2], gp->q_to_f_lo[2]);
+      const float r2f = __fmaf_rn((float)dx, (float)dx, __fmaf_rn((float)dy, (float)dy, __fmul_rn((float)dz, (float)dz)));
+      const float irs = MathF::rsqrt(r2f);
+      const float rh_ = __fmul_rn(r2f, irs);
+      r = (R)rh_;
+      rlo = (R)__fmul_rn(__fmaf_rn(-rh_, rh_, r2f), __fmul_rn(0.5f, irs));
+      inv = (R)irs;
     } else if (MIXED) {
       dx = (R)q_scaled(qdiff(qj.x, qi.x), gp->q_to_f[0]);
       dy = (R)q_scaled(qdiff(qj.y, qi.y), gp->q_to_f[1]);
@@ -371,7 +420,7 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
     rr[s] = r;
     rl(s) = rlo;
     ir(s) = inv;
-    cutoff_fn<M>(r, rlo, pairs[ONE ? 0 : ti * nt + tj], fc[s], dfc(s));
+    cutoff_fn<M>(r, rlo, pairp(ti, tj), fc[s], dfc(s));
     meta(s) = e | (tj << 8);
   };
 
@@ -386,7 +435,7 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
                      min_image(__dsub_rn(xj.y, xi.y), gp->L[1], gp->invL[1]),
                      min_image(__dsub_rn(xj.z, xi.z), gp->L[2], gp->invL[2]));
     }
-    return r2 < pairs[ONE ? 0 : ti * nt + tj].rc2;
+    return r2 < pairp(ti, tj).rc2;
   };
 
   int nc_all = 0;
@@ -539,6 +588,12 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
   }
 
   // ---- first K loop: zeta over unordered pairs --------------------------------
+  // The 4-slot kernels with a kernel-argument table keep cos, g and g' of their 6
+  // unordered pairs in registers for the second K loop (the 8-slot kernel's 28 would
+  // not fit): computed once, not twice.
+  constexpr bool CACHE = MAXNC == 4 && KIND != 0;
+  constexpr int CN = CACHE ? MAXNC : 1;
+  R c_cos[CN][CN], c_g[CN][CN], c_dg[CN][CN];
   R zeta[MAXNC];
 #pragma unroll
   for (int s = 0; s < MAXNC; ++s) zeta[s] = R(0);
@@ -547,43 +602,63 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
 #pragma unroll
     for (int b = a + 1; b < MAXNC; ++b) {
       if (b < nc) {
-        const TripP<R> &Tp = trips[ONE ? 0 : (ti * nt + (meta(a) >> 8)) * nt + (meta(b) >> 8)];
+        const TripP<R> Tp = tripp(ti, meta(a) >> 8, meta(b) >> 8);
         const R cost = ux[a] * ux[b] + uy[a] * uy[b] + uz[a] * uz[b];
         const R u = Tp.h - cost;
-        const R u2 = u * u;
-        const R g = Tp.gamma + Tp.K * u2 * M::rcp(Tp.d2 + u2);
-        R eab = R(1), eba = R(1);
-        if (Tp.lam3 != R(0)) {
-          R arg = Tp.lam3 * (rr[a] - rr[b]);
-          if (Tp.m3 != R(0)) arg = arg * arg * arg;
-          eab = M::expv(arg);
-          eba = M::expv(-arg);
+        const R inv = M::rcp(Tp.d2 + u * u);
+        const R w = u * inv;
+        const R g = Tp.gamma + Tp.K * u * w;   // gamma + K u^2/(d2 + u^2)
+        if constexpr (CACHE) {
+          c_cos[a][b] = cost;
+          c_g[a][b] = g;
+          c_dg[a][b] = -Tp.G2 * w * inv;       // dg/dcos = -G2 u/(d2 + u^2)^2
         }
-        zeta[a] += fc[b] * g * eab;
-        zeta[b] += fc[a] * g * eba;
+        if constexpr (L3) {
+          R eab = R(1), eba = R(1);
+          if (Tp.lam3 != R(0)) {
+            R arg = Tp.lam3 * (rr[a] - rr[b]);
+            if (Tp.m3 != R(0)) arg = arg * arg * arg;
+            eab = M::expv(arg);
+            eba = M::expv(-arg);
+          }
+          zeta[a] += fc[b] * g * eab;
+          zeta[b] += fc[a] * g * eba;
+        } else {
+          zeta[a] += fc[b] * g;
+          zeta[b] += fc[a] * g;
+        }
       }
     }
   }
 
-  // ---- pair terms -------------------------------------------------------------
-  R dz[MAXNC], Fx[MAXNC], Fy[MAXNC], Fz[MAXNC];
+  // ---- pair terms ---------------------------------------------------------------
+  // The force of i's terms on neighbour a is -(Ab[a] u_a + C_a): Ab collects every
+  // term along the bond i-a (the pair term's dV/dr first), C_a = (Fx, Fy, Fz) the
+  // terms along the other bonds, so that each term along a's own bond costs one
+  // scalar update instead of a vector one.
+  R dz[MAXNC], Ab[MAXNC], Fx[MAXNC], Fy[MAXNC], Fz[MAXNC];
   R e_i = R(0);
 #pragma unroll
   for (int a = 0; a < MAXNC; ++a) {
-    dz[a] = Fx[a] = Fy[a] = Fz[a] = R(0);
+    dz[a] = Ab[a] = Fx[a] = Fy[a] = Fz[a] = R(0);
     if (a < nc) {
-      const PairP<R> &P = pairs[ONE ? 0 : ti * nt + (meta(a) >> 8)];
-      const R fR = P.A * M::expneg(P.lam1, P.lam1_lo, rr[a], rl(a));
-      const R fA = -P.B * M::expneg(P.lam2, P.lam2_lo, rr[a], rl(a));
+      const PairP<R> P = pairp(ti, meta(a) >> 8);
+      R fR, fA;
+      if constexpr (MIXED && M::fine) {
+        fR = (R)aexp_mixed(P.A, P.Aln2, P.mu1h, P.mu1l, rr[a], rl(a));
+        fA = (R)aexp_mixed(-P.B, -P.Bln2, P.mu2h, P.mu2l, rr[a], rl(a));
+      } else {
+        fR = P.A * M::expneg(P.lam1, P.lam1_lo, rr[a], rl(a));
+        fA = -P.B * M::expneg(P.lam2, P.lam2_lo, rr[a], rl(a));
+      }
       R bij, dbij;
       bond_order<M>(zeta[a], P, bij, dbij);
-      const R pr = fR + bij * fA;
+      const R bfA = bij * fA;
+      const R pr = fR + bfA;
       e_i += R(0.5) * fc[a] * pr;
-      const R dvdr = R(0.5) * (dfc(a) * pr + fc[a] * (-P.lam1 * fR - bij * P.lam2 * fA));
+      // dV/dr of V = fc (fR + b fA)/2 at fixed zeta: fc' pr/2 - fc (lambda1 fR + lambda2 b fA)/2
+      Ab[a] = R(0.5) * dfc(a) * pr - fc[a] * (P.hlam1 * fR + P.hlam2 * bfA);
       dz[a] = R(0.5) * fc[a] * fA * dbij;
-      Fx[a] = -dvdr * ux[a];
-      Fy[a] = -dvdr * uy[a];
-      Fz[a] = -dvdr * uz[a];
     }
   }
 
@@ -592,44 +667,61 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
   // (e_jk the lambda3 factor, arg' its exponent's derivative):
   //   F_j -= S/r_j u_k + (dV/dzeta_ik fc'_j g e_kj - S/r_j cos + (P - Q) g arg') u_j
   //   F_k -= S/r_k u_j + (dV/dzeta_ij fc'_k g e_jk - S/r_k cos - (P - Q) g arg') u_k
+  // (the u_j and u_k coefficients go to Ab[j], Ab[k]).
 #pragma unroll
   for (int a = 0; a < MAXNC; ++a) {
 #pragma unroll
     for (int b = a + 1; b < MAXNC; ++b) {
       if (b < nc) {
-        const TripP<R> &Tp = trips[ONE ? 0 : (ti * nt + (meta(a) >> 8)) * nt + (meta(b) >> 8)];
-        const R cost = ux[a] * ux[b] + uy[a] * uy[b] + uz[a] * uz[b];
-        const R u = Tp.h - cost;
-        const R u2 = u * u;
-        const R inv = M::rcp(Tp.d2 + u2);
-        const R g = Tp.gamma + Tp.K * u2 * inv;
-        const R dg = -Tp.G2 * u * inv * inv;
-        R eab = R(1), eba = R(1), darg = R(0);
-        if (Tp.lam3 != R(0)) {
-          const R tt = Tp.lam3 * (rr[a] - rr[b]);
-          R arg = tt;
-          darg = Tp.lam3;
-          if (Tp.m3 != R(0)) {
-            arg = tt * tt * tt;
-            darg = R(3) * Tp.lam3 * tt * tt;
-          }
-          eab = M::expv(arg);
-          eba = M::expv(-arg);
+        const TripP<R> Tp = tripp(ti, meta(a) >> 8, meta(b) >> 8);
+        R cost, g, dg;
+        if constexpr (CACHE) {
+          cost = c_cos[a][b];
+          g = c_g[a][b];
+          dg = c_dg[a][b];
+        } else {
+          cost = ux[a] * ux[b] + uy[a] * uy[b] + uz[a] * uz[b];
+          const R u = Tp.h - cost;
+          const R inv = M::rcp(Tp.d2 + u * u);
+          const R w = u * inv;
+          g = Tp.gamma + Tp.K * u * w;
+          dg = -Tp.G2 * w * inv;
         }
-        const R Pv = dz[a] * fc[b] * eab;
-        const R Qv = dz[b] * fc[a] * eba;
-        const R S = (Pv + Qv) * dg;
-        const R PQd = (Pv - Qv) * g * darg;
-        const R cj = S * ir(a);
-        const R ck = S * ir(b);
-        const R ca = dz[b] * dfc(a) * g * eba - cj * cost + PQd;
-        const R cb = dz[a] * dfc(b) * g * eab - ck * cost - PQd;
-        Fx[a] -= cj * ux[b] + ca * ux[a];
-        Fy[a] -= cj * uy[b] + ca * uy[a];
-        Fz[a] -= cj * uz[b] + ca * uz[a];
-        Fx[b] -= ck * ux[a] + cb * ux[b];
-        Fy[b] -= ck * uy[a] + cb * uy[b];
-        Fz[b] -= ck * uz[a] + cb * uz[b];
+        R cj, ck;
+        if constexpr (L3) {
+          R eab = R(1), eba = R(1), darg = R(0);
+          if (Tp.lam3 != R(0)) {
+            const R tt = Tp.lam3 * (rr[a] - rr[b]);
+            R arg = tt;
+            darg = Tp.lam3;
+            if (Tp.m3 != R(0)) {
+              arg = tt * tt * tt;
+              darg = R(3) * Tp.lam3 * tt * tt;
+            }
+            eab = M::expv(arg);
+            eba = M::expv(-arg);
+          }
+          const R Pv = dz[a] * fc[b] * eab;
+          const R Qv = dz[b] * fc[a] * eba;
+          const R S = (Pv + Qv) * dg;
+          const R PQd = (Pv - Qv) * g * darg;
+          cj = S * ir(a);
+          ck = S * ir(b);
+          Ab[a] += dz[b] * dfc(a) * g * eba - cj * cost + PQd;
+          Ab[b] += dz[a] * dfc(b) * g * eab - ck * cost - PQd;
+        } else {
+          const R S = (dz[a] * fc[b] + dz[b] * fc[a]) * dg;
+          cj = S * ir(a);
+          ck = S * ir(b);
+          Ab[a] += dz[b] * dfc(a) * g - cj * cost;
+          Ab[b] += dz[a] * dfc(b) * g - ck * cost;
+        }
+        Fx[a] -= cj * ux[b];
+        Fy[a] -= cj * uy[b];
+        Fz[a] -= cj * uz[b];
+        Fx[b] -= ck * ux[a];
+        Fy[b] -= ck * uy[a];
+        Fz[b] -= ck * uz[a];
       }
     }
   }
@@ -641,6 +733,9 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
 #pragma unroll
     for (int a = 0; a < MAXNC; ++a) {
       if (a < nc && ((mb >> (meta(a) & 0xff)) & 1ull)) {
+        Fx[a] -= Ab[a] * ux[a];
+        Fy[a] -= Ab[a] * uy[a];
+        Fz[a] -= Ab[a] * uz[a];
         fix -= Fx[a];
         fiy -= Fy[a];
         fiz -= Fz[a];
@@ -1349,11 +1444,20 @@ static cudaError_t launch_warp(cudaStream_t st, int eflag, int vflag, int N, con
   return cudaGetLastError();
 }
 
-template <class M, int MAXNC, bool ONE>
+// the kernel-argument table of the precision R
+template <class R>
+inline const KParams<R> &kparams_of(const FastTab &ft)
+{
+  if constexpr (std::is_same<R, float>::value) return ft.f;
+  else return ft.d;
+}
+
+template <class M, int MAXNC, int KIND>
 static cudaError_t launch_reg(cudaStream_t st, int eflag, int vflag, int N, const dbl4 *x, const int4 *q,
                               const int *nbr, const int *cnt, const SysTab *sys, const void *pairs, const void *trips,
-                              int nt, void *contrib, void *selfF, unsigned long long *mask, int *work, int *nwork,
-                              double *partial, RunState *rs, double *eatom, const ForceRoute &rt, int stats)
+                              int nt, const FastTab &ft, void *contrib, void *selfF, unsigned long long *mask,
+                              int *work, int *nwork, double *partial, RunState *rs, double *eatom,
+                              const ForceRoute &rt, int stats)
 {
   const int blocks = (rt.count + FAST_THREADS - 1) / FAST_THREADS;
   if (blocks == 0) return cudaSuccess;
@@ -1361,17 +1465,18 @@ static cudaError_t launch_reg(cudaStream_t st, int eflag, int vflag, int N, cons
   using P = const PairP<R> *;
   using Tt = const TripP<R> *;
   using V = typename V4t<R>::type *;
+  const KParams<R> &kp = kparams_of<R>(ft);
   if (vflag)
-    k_force_reg<M, MAXNC, ONE, true, true><<<blocks, FAST_THREADS, 0, st>>>(
-        N, x, q, nbr, cnt, sys, (P)pairs, (Tt)trips, nt, (V)contrib, (V)selfF, mask, work, nwork, partial, rs,
+    k_force_reg<M, MAXNC, KIND, true, true><<<blocks, FAST_THREADS, 0, st>>>(
+        N, x, q, nbr, cnt, sys, (P)pairs, (Tt)trips, nt, kp, (V)contrib, (V)selfF, mask, work, nwork, partial, rs,
         eatom, rt.order, rt.begin, rt.count, rt.block_base, stats);
   else if (eflag)
-    k_force_reg<M, MAXNC, ONE, true, false><<<blocks, FAST_THREADS, 0, st>>>(
-        N, x, q, nbr, cnt, sys, (P)pairs, (Tt)trips, nt, (V)contrib, (V)selfF, mask, work, nwork, partial, rs,
+    k_force_reg<M, MAXNC, KIND, true, false><<<blocks, FAST_THREADS, 0, st>>>(
+        N, x, q, nbr, cnt, sys, (P)pairs, (Tt)trips, nt, kp, (V)contrib, (V)selfF, mask, work, nwork, partial, rs,
         eatom, rt.order, rt.begin, rt.count, rt.block_base, stats);
   else
-    k_force_reg<M, MAXNC, ONE, false, false><<<blocks, FAST_THREADS, 0, st>>>(
-        N, x, q, nbr, cnt, sys, (P)pairs, (Tt)trips, nt, (V)contrib, (V)selfF, mask, work, nwork, partial, rs,
+    k_force_reg<M, MAXNC, KIND, false, false><<<blocks, FAST_THREADS, 0, st>>>(
+        N, x, q, nbr, cnt, sys, (P)pairs, (Tt)trips, nt, kp, (V)contrib, (V)selfF, mask, work, nwork, partial, rs,
         eatom, rt.order, rt.begin, rt.count, rt.block_base, stats);
   return cudaGetLastError();
 }
@@ -1380,7 +1485,7 @@ static cudaError_t launch_reg(cudaStream_t st, int eflag, int vflag, int N, cons
 // force.cu, which adds the partial-sum reduction, documents the arguments).  *rows:
 // the partial-sum rows the launched kernels write (0: none launched).
 template <class M>
-cudaError_t launch_force_m(int part, cudaStream_t st, int fast_slots, bool one_type, int gen_slots, int eflag,
+cudaError_t launch_force_m(int part, cudaStream_t st, int fast_slots, const FastTab &ft, int gen_slots, int eflag,
                            int vflag, int N, const dbl4 *x, const int4 *q, const int *nbr, const int *cnt,
                            const SysTab *sys, const void *pairs, const void *trips, int nt, void *contrib,
                            void *selfF, unsigned long long *mask, int *work, int *nwork, double *partial, RunState *rs,
@@ -1399,13 +1504,14 @@ cudaError_t launch_force_m(int part, cudaStream_t st, int fast_slots, bool one_t
       rt.block_base = nfast;
       nfast += (rt.count + FAST_THREADS - 1) / FAST_THREADS;
       if (!(part & 1)) continue;
-#define TSF_REG(NC)                                                                                                 \
-  e = one_type ? launch_reg<M, NC, true>(st, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib, selfF, \
-                                         mask, work, nwork, partial, rs, eatom, rt, stats)                          \
-               : launch_reg<M, NC, false>(st, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib,      \
-                                          selfF, mask, work, nwork, partial, rs, eatom, rt, stats);
+#define TSF_REG_K(NC, K)                                                                                          \
+  launch_reg<M, NC, K>(st, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt, ft, contrib, selfF, mask, work, \
+                       nwork, partial, rs, eatom, rt, stats)
+#define TSF_REG(NC) \
+  e = ft.kind == 1 ? TSF_REG_K(NC, 1) : ft.kind == 2 ? TSF_REG_K(NC, 2) : TSF_REG_K(NC, 0);
       if (rt.slots <= 4) { TSF_REG(4) } else { TSF_REG(8) }
 #undef TSF_REG
+#undef TSF_REG_K
       if (e != cudaSuccess) return e;
     }
     if (!(part & 2)) return cudaSuccess;

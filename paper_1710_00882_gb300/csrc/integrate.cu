@@ -84,25 +84,43 @@ __device__ __forceinline__ void gather_force(int m, int N, const typename A::V *
   using V = typename A::V;
   constexpr int U = 4;   // slots whose loads are issued together
   A acc;
-  acc.init(selfF[m]);
+  // The reverse indices of the first U list slots are loaded together with the mask
+  // (every list holds at least U slots), so when all in-cutoff slots are among them
+  // (diamond-like solids: the whole list is the four nearest neighbours) the gather
+  // is two dependent loads deep instead of three.
+  unsigned g0[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) g0[u] = (unsigned)rev[(size_t)u * N + m];
+  const V self = selfF[m];
   unsigned long long mb = mask[m];
-  while (mb) {
-    int sl[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      sl[u] = mb ? __ffsll((long long)mb) - 1 : -1;
-      mb &= mb - 1;
-    }
-    unsigned g[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) g[u] = sl[u] >= 0 ? (unsigned)rev[(size_t)sl[u] * N + m] : 0u;
+  acc.init(self);
+  if ((mb >> U) == 0ull) {
     V c[U];
 #pragma unroll
     for (int u = 0; u < U; ++u)
-      if (sl[u] >= 0) c[u] = contrib[g[u]];
+      if ((mb >> u) & 1ull) c[u] = contrib[g0[u]];
 #pragma unroll
     for (int u = 0; u < U; ++u)
-      if (sl[u] >= 0) acc.add(c[u]);
+      if ((mb >> u) & 1ull) acc.add(c[u]);
+  } else {
+    while (mb) {
+      int sl[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        sl[u] = mb ? __ffsll((long long)mb) - 1 : -1;
+        mb &= mb - 1;
+      }
+      unsigned g[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) g[u] = sl[u] >= 0 ? (unsigned)rev[(size_t)sl[u] * N + m] : 0u;
+      V c[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (sl[u] >= 0) c[u] = contrib[g[u]];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (sl[u] >= 0) acc.add(c[u]);
+    }
   }
   acc.out(fx, fy, fz);
 }

@@ -41,6 +41,9 @@ struct PairP {
   R r_in, r_out, rc2;     // R - D, R + D, (R + D)^2
   R r_out_lo;             // float32 tables: (R + D) - (float)(R + D)
   R inv4D, dfc_scale;     // 1/(4D), -pi/(4D)
+  R mu1h, mu1l, mu2h, mu2l;   // float32 tables: lambda1,2 * log2(e) as float head + tail
+  R Aln2, Bln2;               // A ln 2, B ln 2 (the first-order tail factor of 2^-y)
+  R hlam1, hlam2;             // lambda1 / 2, lambda2 / 2
 };
 
 // Angular part of the table (row (ti,tj,tk)).
@@ -49,6 +52,25 @@ struct TripP {
   R gamma, lam3, K, G2, d2, h;   // g = gamma + K u^2/(d2 + u^2), dg/dcos = -G2 u/(d2 + u^2)^2, u = h - cos
   R m3;                          // 1 when the lambda3 exponent is cubed (m = 3), else 0
   R pad;
+};
+
+// Constants of the register force kernel passed by value as a kernel argument (they
+// then live in the constant bank and enter arithmetic as operands): kind 1 holds one
+// type's row in p[0], t[0]; kind 2 holds two types, p[ti*2 + tj], t[(ti*2 + tj)*2 + tk].
+template <class R>
+struct KParams {
+  PairP<R> p[4];
+  TripP<R> t[8];
+};
+
+// How the register force kernel reads the table.  kind 0: the device table, staged
+// in shared memory (any table with symmetric angular rows); kind 1 (one type) and
+// kind 2 (two types): the kernel-argument copies below, for tables whose rows all
+// have lambda3 = 0 (the lambda3 factor of Eq. 3 is then compiled out).
+struct FastTab {
+  int kind = 0;
+  KParams<float> f{};
+  KParams<double> d{};
 };
 
 // Box geometry.  Positions are also kept as 32-bit fixed point per axis:

@@ -188,7 +188,7 @@ extern "C" int tersoff_compute_noalloc(const tersoff_params *P, const double *po
   NK(launch_build(st, (int)N, q, sys, nullptr, g.ncell, g.radii, cell_count, cell_start, tile_sums, cell_atoms, cell_of, rank,
                   nbr, rev, cnt, kCap, qref, rs, 0));
   const int fast_slots = P->sym_angular ? 8 : 0;
-  NK(launch_force(st, prec, fast_slots, P->nt == 1, force_slots_for(kCap), 1, 1, (int)N, x, q, nbr, cnt, sys,
+  NK(launch_force(st, prec, fast_slots, P->fast, force_slots_for(kCap), 1, 1, (int)N, x, q, nbr, cnt, sys,
                   f32 ? P->pair_f : P->pair_d, f32 ? P->trip_f : P->trip_d, P->nt, contrib, selfF, mask, work,
                   nwork, partial, rs, nullptr));
   if (forces) NK(launch_gather_out(st, prec, (int)N, contrib, selfF, mask, rev, forces, rs));

@@ -526,6 +526,8 @@ int tersoff_params_create(tersoff_ctx *ctx, int ntypes, const double *entries, c
   std::vector<TripP<float>> tf(nrow);
   std::vector<TripP<double>> td(nrow);
   const double PI = 3.14159265358979323846;
+  const double LOG2E = 1.4426950408889634074;   // log2(e)
+  const double LN2 = 0.69314718055994530942;    // ln(2)
   for (int a = 0; a < nt; ++a)
     for (int b = 0; b < nt; ++b) {
       const double *p = row(a, b, b);
@@ -536,6 +538,9 @@ int tersoff_params_create(tersoff_ctx *ctx, int ntypes, const double *entries, c
       d.Rc = p[F_R]; d.Dc = p[F_DD];
       d.r_in = p[F_R] - p[F_DD]; d.r_out = p[F_R] + p[F_DD]; d.rc2 = d.r_out * d.r_out;
       d.inv4D = 1.0 / (4.0 * p[F_DD]); d.dfc_scale = -PI / (4.0 * p[F_DD]); d.r_out_lo = 0.0;
+      d.mu1h = d.lam1 * LOG2E; d.mu1l = 0.0; d.mu2h = d.lam2 * LOG2E; d.mu2l = 0.0;
+      d.Aln2 = d.A * LN2; d.Bln2 = d.B * LN2;
+      d.hlam1 = 0.5 * d.lam1; d.hlam2 = 0.5 * d.lam2;
       P->rcmax = std::max(P->rcmax, d.r_out);
       pd[a * nt + b] = d;
       PairP<float> f;
@@ -549,6 +554,12 @@ int tersoff_params_create(tersoff_ctx *ctx, int ntypes, const double *entries, c
       if ((double)f.rc2 > d.rc2) f.rc2 = std::nextafter(f.rc2, 0.0f);
       f.inv4D = (float)d.inv4D; f.dfc_scale = (float)d.dfc_scale;
       f.r_out_lo = (float)(d.r_out - (double)f.r_out);
+      // lambda log2(e) as float head + tail: the product is formed in float64, so the
+      // pair lambda r log2(e) carries the rounding of r only
+      f.mu1h = (float)d.mu1h; f.mu1l = (float)(d.mu1h - (double)f.mu1h);
+      f.mu2h = (float)d.mu2h; f.mu2l = (float)(d.mu2h - (double)f.mu2h);
+      f.Aln2 = (float)d.Aln2; f.Bln2 = (float)d.Bln2;
+      f.hlam1 = (float)d.hlam1; f.hlam2 = (float)d.hlam2;
       pf[a * nt + b] = f;
       for (int c = 0; c < nt; ++c) {
         const double *t = row(a, b, c);
@@ -564,6 +575,23 @@ int tersoff_params_create(tersoff_ctx *ctx, int ntypes, const double *entries, c
         tf[(a * nt + b) * nt + c] = g;
       }
     }
+  // the register kernel's kernel-argument table: one or two types whose rows all
+  // have lambda3 = 0 (else the kernel reads the device table, kind 0)
+  {
+    bool lam3_zero = true;
+    for (int r = 0; r < nrow; ++r) lam3_zero = lam3_zero && entries[(size_t)r * NFIELDS + F_LAM3] == 0.0;
+    P->fast.kind = (lam3_zero && P->sym_angular && nt <= 2) ? nt : 0;
+    if (P->fast.kind > 0) {
+      for (int k = 0; k < nt * nt; ++k) {
+        P->fast.f.p[k] = pf[k];
+        P->fast.d.p[k] = pd[k];
+      }
+      for (int k = 0; k < nrow; ++k) {
+        P->fast.f.t[k] = tf[k];
+        P->fast.d.t[k] = td[k];
+      }
+    }
+  }
   bool ok = cudaMalloc(&P->pair_f, pf.size() * sizeof(pf[0])) == cudaSuccess &&
             cudaMalloc(&P->pair_d, pd.size() * sizeof(pd[0])) == cudaSuccess &&
             cudaMalloc(&P->trip_f, tf.size() * sizeof(tf[0])) == cudaSuccess &&
@@ -735,7 +763,7 @@ int tersoff_compute(tersoff_ctx *ctx, const double *pos, const int32_t *types, i
   CKR(ensure_scatter(ctx, A, N, L->cap, f32));
   const int gen_slots = force_slots_for(std::max(1, L->maxcount));
   const int fast_slots = (P->sym_angular && !ctx->general_only) ? (L->maxcount <= 4 ? 4 : 8) : 0;
-  CK(launch_force(ctx->stream, prec, fast_slots, P->nt == 1, gen_slots, 1, virial != nullptr, (int)N, A.x, A.q,
+  CK(launch_force(ctx->stream, prec, fast_slots, P->fast, gen_slots, 1, virial != nullptr, (int)N, A.x, A.q,
                   L->nbr, L->cnt, ctx->csys.tab, f32 ? P->pair_f : P->pair_d, f32 ? P->trip_f : P->trip_d, P->nt,
                   A.contrib, A.selfF, A.mask, A.work, A.nwork, A.partial, rs, nullptr));
   double *dF = nullptr;
@@ -777,10 +805,21 @@ static cudaEvent_t md_event(tersoff_md *md)
   return md->ev_pool[md->ev_used++];
 }
 
+// Profiling only: a bounded busy wait of ~50 us on the device before a phase's start
+// event, so that the host has enqueued the phase's launches before the device reaches
+// the event; otherwise the host's launch latency would be counted as device time.
+__global__ void k_profile_spin(long long cycles)
+{
+  const long long t0 = clock64();
+  while (clock64() - t0 < cycles) {
+  }
+}
+
 // bracket one phase with events when profiling; returns the start index
 static size_t md_mark_begin(tersoff_md *md)
 {
   if (!md->prof) return 0;
+  k_profile_spin<<<1, 32, 0, md->ctx->stream>>>(100000);
   size_t i = md->ev_used;
   cudaEvent_t e = md_event(md);
   if (e) cudaEventRecord(e, md->ctx->stream);
@@ -804,7 +843,7 @@ static int md_force(tersoff_md *md, cudaStream_t st, int eflag, int part = 3, in
 {
   tersoff_ctx *ctx = md->ctx;
   const tersoff_params *P = md->params;
-  CK(launch_force_part(part, st, md->prec, md->fast_slots, P->nt == 1, md->gen_slots, eflag, 0, (int)md->atoms.N, md->atoms.x,
+  CK(launch_force_part(part, st, md->prec, md->fast_slots, P->fast, md->gen_slots, eflag, 0, (int)md->atoms.N, md->atoms.x,
                   md->atoms.q, md->list.nbr, md->list.cnt, md->sys.tab, md->f32 ? P->pair_f : P->pair_d,
                   md->f32 ? P->trip_f : P->trip_d, P->nt, md->atoms.contrib, md->atoms.selfF, md->atoms.mask,
                   md->atoms.work, md->atoms.nwork, md->atoms.partial, md->rs, nullptr, md->routed ? &md->routes : nullptr, stats));

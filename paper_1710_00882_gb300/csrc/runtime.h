@@ -65,10 +65,10 @@ int scan_tiles_for(int ncell);
 int force_slots_for(int need);
 int force_partial_rows(int N);
 int vv_blocks(int N);
-cudaError_t launch_force(cudaStream_t, int, int, bool, int, int, int, int, const dbl4 *, const int4 *, const int *,
+cudaError_t launch_force(cudaStream_t, int, int, const FastTab &, int, int, int, int, const dbl4 *, const int4 *, const int *,
                          const int *, const SysTab *, const void *, const void *, int, void *, void *,
                          unsigned long long *, int *, int *, double *, RunState *, double *);
-cudaError_t launch_force_part(int, cudaStream_t, int, int, bool, int, int, int, int, const dbl4 *, const int4 *,
+cudaError_t launch_force_part(int, cudaStream_t, int, int, const FastTab &, int, int, int, int, const dbl4 *, const int4 *,
                               const int *, const int *, const SysTab *, const void *, const void *, int, void *, void *,
                               unsigned long long *, int *, int *, double *, RunState *, double *,
                               const ForceRoutes *routes = nullptr, int stats = 1);
@@ -157,6 +157,7 @@ struct tersoff_params {
   void *pair_f = nullptr, *trip_f = nullptr, *pair_d = nullptr, *trip_d = nullptr;
   double *d_mass = nullptr;
   bool sym_angular = false;   // rows (i,j,k) and (i,k,j) share their angular constants
+  tsf::FastTab fast;          // the register force kernel's table kind and kernel-argument copies
 };
 
 

@@ -318,7 +318,7 @@ int srv_force(tersoff_server *s, cudaStream_t st)
 {
   const tersoff_params *P = s->P;
   AtomState &X = cur_atoms(s);
-  SK(launch_force_part(3, st, s->prec, s->fast_slots, P->nt == 1, s->gen_slots, 0, 0, (int)s->natoms, X.x, X.q,
+  SK(launch_force_part(3, st, s->prec, s->fast_slots, P->fast, s->gen_slots, 0, 0, (int)s->natoms, X.x, X.q,
                        s->L.nbr, s->L.cnt, s->S.tab, s->f32 ? P->pair_f : P->pair_d,
                        s->f32 ? P->trip_f : P->trip_d, P->nt, s->SC.contrib, s->SC.selfF, s->SC.mask, s->SC.work,
                        s->SC.nwork, s->SC.partial, s->rs, s->eatom, s->routed ? &s->routes : nullptr, 0));

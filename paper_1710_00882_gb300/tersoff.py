@@ -37,7 +37,6 @@ NOALLOC_MAX_ATOMS = 16384   # TERSOFF_NOALLOC_MAX_ATOMS
 
 HOST_PTRS = 0
 DEVICE_PTRS = 1
-DETERMINISTIC = 2
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"libtersoff.so not built ({LIB_PATH}); run __graft_entry__.build() or "

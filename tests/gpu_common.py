@@ -33,6 +33,26 @@ def product_params(ctx, species, **kw):
     return T.Params(ctx, tab, m)
 
 
+# Virial bounds, eV per atom (summed over the N atoms; the virial is extensive).  No
+# target is stated for the virial; these follow from the arithmetic of each mode: a
+# term's virial d F (|d| ~ 2.35 A) carries the relative error of its force, so an atom's
+# share is ~|d| x its force error: float64 ~1e-13 eV, mixed ~1e-5 eV (force error
+# ~4e-6 eV/A), single ~1e-4 eV (~4e-5 eV/A).
+FP64_W_ATOM, MIX_W_ATOM, SGL_W_ATOM = 1e-10, 1e-5, 1e-4
+
+# Force scale of the accuracy targets.  The float32 roundings of mixed and single mode
+# are relative to the terms that make up a force, so their absolute error grows with
+# the force scale: the 1e-4 eV/A target holds at the workloads' scale (largest
+# |F| <= F_SCALE), and stress cases far beyond it (atoms pushed into the repulsive wall,
+# |F| up to 80 eV/A) scale the float32 bounds by max|F| / F_SCALE.
+F_SCALE = 20.0
+
+
+def force_scale(Fo):
+    """max(1, largest oracle force component / F_SCALE)."""
+    return max(1.0, float(np.abs(Fo).max()) / F_SCALE) if len(Fo) else 1.0
+
+
 def assert_parity(E, F, W, Eo, Fo, Wo, e_rel, f_abs, w_abs_per_atom, what=""):
     """Energy relative, force max-abs and virial absolute (per atom, summed) bounds."""
     assert abs(E - Eo) <= e_rel * abs(Eo), f"{what} energy {E!r} vs {Eo!r} rel {abs(E - Eo) / abs(Eo):.3e}"
@@ -40,5 +60,5 @@ def assert_parity(E, F, W, Eo, Fo, Wo, e_rel, f_abs, w_abs_per_atom, what=""):
     assert err <= f_abs, f"{what} force max-abs err {err:.3e}"
     if W is not None and Wo is not None:
         werr = np.abs(np.asarray(W) - np.asarray(Wo)).max()
-        wtol = max(w_abs_per_atom * max(1, len(F)), e_rel * np.abs(Wo).max())
-        assert werr <= wtol, f"{what} virial err {werr:.3e}: {W} vs {Wo}"
+        wtol = w_abs_per_atom * max(1, len(F))
+        assert werr <= wtol, f"{what} virial err {werr:.3e} > {wtol:.3e}: {W} vs {Wo}"

@@ -4,7 +4,9 @@ Tolerances: FP64 energy rel <= 1e-12, force max-abs <= 1e-10 eV/A; mixed
 energy rel <= 1e-6, force max-abs <= 1e-4 eV/A (the accuracy targets the
 workloads are specified with); single (float32 throughout) energy rel <= 1e-5,
 force max-abs <= 1e-3 eV/A (derived in gpu_common).  Virial: 1e-10 (FP64) / 1e-5
-(mixed) / 1e-4 (single) eV per atom.
+(mixed) / 1e-4 (single) eV per atom.  Every case uses these bounds except the one
+stress case whose forces (up to 80 eV/A) are four times the workloads' scale: there
+the float32 bounds scale with max|F| (gpu_common.force_scale).
 """
 import numpy as np
 import pytest
@@ -12,8 +14,8 @@ import pytest
 from oracle import oracle, params as oparams
 from paper_1710_00882_gb300 import workloads as wl
 
-from gpu_common import (FP64_E_REL, FP64_F_ABS, MIX_E_REL, MIX_F_ABS, SGL_E_REL, SGL_F_ABS, assert_parity,
-                        oracle_table, product_params)
+from gpu_common import (FP64_E_REL, FP64_F_ABS, FP64_W_ATOM, MIX_E_REL, MIX_F_ABS, MIX_W_ATOM, SGL_E_REL, SGL_F_ABS,
+                        SGL_W_ATOM, assert_parity, force_scale, oracle_table, product_params)
 
 pytestmark = pytest.mark.gpu
 
@@ -43,22 +45,20 @@ def run_pair(T, ctx, s, species=None, prec=None, **kw):
     return out, (Eo, Fo, Wo)
 
 
-def check(T, out, ref, what, mixed_f_rel=None):
-    """mixed_f_rel: for stress cases with forces far above the workloads' (|F| up to
-    ~50 eV/A), bound the mixed force error relative to the largest force instead (10x
-    that for single mode)."""
+def check(T, out, ref, what, f_scale=1.0, w_scale=1.0):
+    """Every precision against the oracle at its bounds; f_scale, w_scale (>= 1) widen
+    the float32 force and virial bounds of stress cases beyond the workloads' force
+    scale."""
     Eo, Fo, Wo = ref
     if T.FP64 in out:
         E, F, W = out[T.FP64]
-        assert_parity(E, F, W, Eo, Fo, Wo, FP64_E_REL, FP64_F_ABS, 1e-10, what + " fp64")
+        assert_parity(E, F, W, Eo, Fo, Wo, FP64_E_REL, FP64_F_ABS, FP64_W_ATOM, what + " fp64")
     if T.MIXED in out:
         E, F, W = out[T.MIXED]
-        fa = MIX_F_ABS if mixed_f_rel is None else max(MIX_F_ABS, mixed_f_rel * np.abs(Fo).max())
-        assert_parity(E, F, W, Eo, Fo, Wo, MIX_E_REL, fa, 1e-5, what + " mixed")
+        assert_parity(E, F, W, Eo, Fo, Wo, MIX_E_REL, f_scale * MIX_F_ABS, w_scale * MIX_W_ATOM, what + " mixed")
     if T.SINGLE in out:
         E, F, W = out[T.SINGLE]
-        fa = SGL_F_ABS if mixed_f_rel is None else max(SGL_F_ABS, 10 * mixed_f_rel * np.abs(Fo).max())
-        assert_parity(E, F, W, Eo, Fo, Wo, SGL_E_REL, fa, 1e-4, what + " single")
+        assert_parity(E, F, W, Eo, Fo, Wo, SGL_E_REL, f_scale * SGL_F_ABS, w_scale * SGL_W_ATOM, what + " single")
 
 
 def test_si_512_config(T, ctx):
@@ -86,19 +86,24 @@ def test_lambda3_variants(T, ctx, lam3, m):
 
 def test_compressed_many_neighbours(T, ctx):
     """Si compressed to a = 4.1 A with displacements: the second shell (2.90 A) sits in
-    the f_C taper, ~16 in-cutoff neighbours per atom, exercises the wider slot kernels."""
+    the f_C taper, ~16 in-cutoff neighbours per atom, exercises the wider slot kernels.
+    Forces reach 78 eV/A, yet the workloads' absolute force bounds hold (measured mixed
+    error 2.2e-5 eV/A); the virial, a sum of terms four times the workloads' size, takes
+    the force-scaled bound (measured mixed error 1.8e-3 eV over 216 atoms)."""
     rng = np.random.default_rng(5)
     s = wl.diamond(3, 3, 3, 4.1)
     s.pos = s.pos + rng.normal(0, 0.12, size=s.pos.shape)
     out, ref = run_pair(T, ctx, s)
-    check(T, out, ref, "compressed", mixed_f_rel=4e-6)
+    check(T, out, ref, "compressed", w_scale=force_scale(ref[1]))
 
 
 def test_more_than_32_neighbours(T, ctx):
     """Si compressed to a = 2.9 A: 33-35 in-cutoff neighbours per atom, so every atom
     leaves the register kernel for the warp kernel with two slots per lane.  Energy and
-    forces (|F| up to ~80 eV/A, bounds relative to the largest force as for the other
-    compressed case)."""
+    forces.  The nearest neighbours sit at 1.26 A, deep in the repulsive wall: single
+    terms reach ~200 eV/A and forces 80 eV/A, four times the workloads' force scale, so
+    the float32 force bounds scale with max|F| / 20 eV/A (measured mixed error 1.1e-4
+    eV/A against a scaled bound of 4e-4)."""
     rng = np.random.default_rng(12)
     s = wl.diamond(4, 4, 4, 2.9)
     s.pos = s.pos + rng.normal(0, 0.03, size=s.pos.shape)
@@ -108,9 +113,10 @@ def test_more_than_32_neighbours(T, ctx):
     assert counts.min() > 32
     tab, _ = oracle_table(s.species)
     Eo, Fo, _ = oracle.energy_forces(s.pos, s.types, s.box, tab)
-    fmax = np.abs(Fo).max()
-    for prec, er, fa in ((T.FP64, FP64_E_REL, FP64_F_ABS), (T.MIXED, MIX_E_REL, max(MIX_F_ABS, 4e-6 * fmax)),
-                         (T.SINGLE, SGL_E_REL, max(SGL_F_ABS, 4e-5 * fmax))):
+    sc = force_scale(Fo)
+    assert sc > 3.5
+    for prec, er, fa in ((T.FP64, FP64_E_REL, FP64_F_ABS), (T.MIXED, MIX_E_REL, sc * MIX_F_ABS),
+                         (T.SINGLE, SGL_E_REL, sc * SGL_F_ABS)):
         E, F, _ = T.compute(ctx, P, s.pos, s.types, s.box, prec=prec)
         assert_parity(E, F, None, Eo, Fo, None, er, fa, 0, f"dense prec {prec}")
 
@@ -145,15 +151,16 @@ def test_edge_cases(T, ctx):
         pos = np.array(pos)
         types = np.zeros(len(pos), np.int32)
         Eo, Fo, Wo = oracle.energy_forces(pos, types, box, oracle_table(("Si",))[0])
-        # a lone bond's energy f_R + f_A is ~5x smaller than its two terms, so the
-        # float32 bound on it is looser than the workloads' 1e-6
-        for prec, (er, fa) in ((T.FP64, (FP64_E_REL, FP64_F_ABS)), (T.MIXED, (5e-6, MIX_F_ABS)),
-                               (T.SINGLE, (5e-5, SGL_F_ABS))):
+        # the workloads' bounds hold for a lone bond too (its energy f_R + f_A is ~5x
+        # smaller than its two terms; measured mixed error 1.2e-7, single 8.4e-7)
+        for prec, (er, fa, wa) in ((T.FP64, (FP64_E_REL, FP64_F_ABS, FP64_W_ATOM)),
+                                   (T.MIXED, (MIX_E_REL, MIX_F_ABS, MIX_W_ATOM)),
+                                   (T.SINGLE, (SGL_E_REL, SGL_F_ABS, SGL_W_ATOM))):
             E, F, W = T.compute(ctx, P, pos, types, box, prec=prec)
             if Eo == 0.0:
                 assert E == 0.0 and np.all(F == 0)
             else:
-                assert_parity(E, F, W, Eo, Fo, Wo, er, fa, 1e-4)
+                assert_parity(E, F, W, Eo, Fo, Wo, er, fa, wa)
 
 
 def test_errors_are_reported(T, ctx):
