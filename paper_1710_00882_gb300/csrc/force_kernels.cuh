@@ -587,143 +587,169 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
     }
   }
 
-  // ---- first K loop: zeta over unordered pairs --------------------------------
-  // The 4-slot kernels with a kernel-argument table keep cos, g and g' of their 6
-  // unordered pairs in registers for the second K loop (the 8-slot kernel's 28 would
-  // not fit): computed once, not twice.
-  constexpr bool CACHE = MAXNC == 4 && KIND != 0;
-  constexpr int CN = CACHE ? MAXNC : 1;
-  R c_cos[CN][CN], c_g[CN][CN], c_dg[CN][CN];
-  R zeta[MAXNC];
-#pragma unroll
-  for (int s = 0; s < MAXNC; ++s) zeta[s] = R(0);
-#pragma unroll
-  for (int a = 0; a < MAXNC; ++a) {
-#pragma unroll
-    for (int b = a + 1; b < MAXNC; ++b) {
-      if (b < nc) {
-        const TripP<R> Tp = tripp(ti, meta(a) >> 8, meta(b) >> 8);
-        const R cost = ux[a] * ux[b] + uy[a] * uy[b] + uz[a] * uz[b];
-        const R u = Tp.h - cost;
-        const R inv = M::rcp(Tp.d2 + u * u);
-        const R w = u * inv;
-        const R g = Tp.gamma + Tp.K * u * w;   // gamma + K u^2/(d2 + u^2)
-        if constexpr (CACHE) {
-          c_cos[a][b] = cost;
-          c_g[a][b] = g;
-          c_dg[a][b] = -Tp.G2 * w * inv;       // dg/dcos = -G2 u/(d2 + u^2)^2
-        }
-        if constexpr (L3) {
-          R eab = R(1), eba = R(1);
-          if (Tp.lam3 != R(0)) {
-            R arg = Tp.lam3 * (rr[a] - rr[b]);
-            if (Tp.m3 != R(0)) arg = arg * arg * arg;
-            eab = M::expv(arg);
-            eba = M::expv(-arg);
-          }
-          zeta[a] += fc[b] * g * eab;
-          zeta[b] += fc[a] * g * eba;
-        } else {
-          zeta[a] += fc[b] * g;
-          zeta[b] += fc[a] * g;
-        }
-      }
-    }
-  }
-
-  // ---- pair terms ---------------------------------------------------------------
-  // The force of i's terms on neighbour a is -(Ab[a] u_a + C_a): Ab collects every
-  // term along the bond i-a (the pair term's dV/dr first), C_a = (Fx, Fy, Fz) the
-  // terms along the other bonds, so that each term along a's own bond costs one
-  // scalar update instead of a vector one.
-  R dz[MAXNC], Ab[MAXNC], Fx[MAXNC], Fy[MAXNC], Fz[MAXNC];
+  // ---- K loops and pair terms ------------------------------------------------
+  // Evaluated in one of two forms: FULL, when every lane of the warp has all MAXNC
+  // slots within the cutoff and inside R - D (f_C = 1, f_C' = 0; the usual case of
+  // diamond-like solids), with no bounds test per slot pair and the f_C factors
+  // compiled out; else the general form.  Both compute the same terms.
+  R zeta[MAXNC], dz[MAXNC], Ab[MAXNC], Fx[MAXNC], Fy[MAXNC], Fz[MAXNC];
   R e_i = R(0);
+  auto evaluate = [&](auto full_c) {
+    constexpr bool FULL = decltype(full_c)::value;
+    const int ncx = FULL ? MAXNC : nc;
+    auto FC = [&](int s) -> R { if constexpr (FULL) return R(1); else return fc[s]; };
+    auto DFC = [&](int s) -> R { if constexpr (FULL) return R(0); else return dfc(s); };
+    // ---- first K loop: zeta over unordered pairs --------------------------------
+    // The 4-slot kernels with a kernel-argument table keep cos, g and g' of their 6
+    // unordered pairs in registers for the second K loop (the 8-slot kernel's 28 would
+    // not fit): computed once, not twice.
+    constexpr bool CACHE = MAXNC == 4 && KIND != 0;
+    constexpr int CN = CACHE ? MAXNC : 1;
+    R c_cos[CN][CN], c_g[CN][CN], c_dg[CN][CN];
 #pragma unroll
-  for (int a = 0; a < MAXNC; ++a) {
-    dz[a] = Ab[a] = Fx[a] = Fy[a] = Fz[a] = R(0);
-    if (a < nc) {
-      const PairP<R> P = pairp(ti, meta(a) >> 8);
-      R fR, fA;
-      if constexpr (MIXED && M::fine) {
-        fR = (R)aexp_mixed(P.A, P.Aln2, P.mu1h, P.mu1l, rr[a], rl(a));
-        fA = (R)aexp_mixed(-P.B, -P.Bln2, P.mu2h, P.mu2l, rr[a], rl(a));
-      } else {
-        fR = P.A * M::expneg(P.lam1, P.lam1_lo, rr[a], rl(a));
-        fA = -P.B * M::expneg(P.lam2, P.lam2_lo, rr[a], rl(a));
-      }
-      R bij, dbij;
-      bond_order<M>(zeta[a], P, bij, dbij);
-      const R bfA = bij * fA;
-      const R pr = fR + bfA;
-      e_i += R(0.5) * fc[a] * pr;
-      // dV/dr of V = fc (fR + b fA)/2 at fixed zeta: fc' pr/2 - fc (lambda1 fR + lambda2 b fA)/2
-      Ab[a] = R(0.5) * dfc(a) * pr - fc[a] * (P.hlam1 * fR + P.hlam2 * bfA);
-      dz[a] = R(0.5) * fc[a] * fA * dbij;
-    }
-  }
-
-  // ---- second K loop: zeta derivatives over unordered pairs -------------------
-  // With P = dV/dzeta_ij fc_k e_jk, Q = dV/dzeta_ik fc_j e_kj, S = (P + Q) g'
-  // (e_jk the lambda3 factor, arg' its exponent's derivative):
-  //   F_j -= S/r_j u_k + (dV/dzeta_ik fc'_j g e_kj - S/r_j cos + (P - Q) g arg') u_j
-  //   F_k -= S/r_k u_j + (dV/dzeta_ij fc'_k g e_jk - S/r_k cos - (P - Q) g arg') u_k
-  // (the u_j and u_k coefficients go to Ab[j], Ab[k]).
+    for (int s = 0; s < MAXNC; ++s) zeta[s] = R(0);
 #pragma unroll
-  for (int a = 0; a < MAXNC; ++a) {
+    for (int a = 0; a < MAXNC; ++a) {
 #pragma unroll
-    for (int b = a + 1; b < MAXNC; ++b) {
-      if (b < nc) {
-        const TripP<R> Tp = tripp(ti, meta(a) >> 8, meta(b) >> 8);
-        R cost, g, dg;
-        if constexpr (CACHE) {
-          cost = c_cos[a][b];
-          g = c_g[a][b];
-          dg = c_dg[a][b];
-        } else {
-          cost = ux[a] * ux[b] + uy[a] * uy[b] + uz[a] * uz[b];
+      for (int b = a + 1; b < MAXNC; ++b) {
+        if (b < ncx) {
+          const TripP<R> Tp = tripp(ti, meta(a) >> 8, meta(b) >> 8);
+          const R cost = ux[a] * ux[b] + uy[a] * uy[b] + uz[a] * uz[b];
           const R u = Tp.h - cost;
           const R inv = M::rcp(Tp.d2 + u * u);
           const R w = u * inv;
-          g = Tp.gamma + Tp.K * u * w;
-          dg = -Tp.G2 * w * inv;
-        }
-        R cj, ck;
-        if constexpr (L3) {
-          R eab = R(1), eba = R(1), darg = R(0);
-          if (Tp.lam3 != R(0)) {
-            const R tt = Tp.lam3 * (rr[a] - rr[b]);
-            R arg = tt;
-            darg = Tp.lam3;
-            if (Tp.m3 != R(0)) {
-              arg = tt * tt * tt;
-              darg = R(3) * Tp.lam3 * tt * tt;
-            }
-            eab = M::expv(arg);
-            eba = M::expv(-arg);
+          const R g = Tp.gamma + Tp.K * u * w;   // gamma + K u^2/(d2 + u^2)
+          if constexpr (CACHE) {
+            c_cos[a][b] = cost;
+            c_g[a][b] = g;
+            c_dg[a][b] = -Tp.G2 * w * inv;       // dg/dcos = -G2 u/(d2 + u^2)^2
           }
-          const R Pv = dz[a] * fc[b] * eab;
-          const R Qv = dz[b] * fc[a] * eba;
-          const R S = (Pv + Qv) * dg;
-          const R PQd = (Pv - Qv) * g * darg;
-          cj = S * ir(a);
-          ck = S * ir(b);
-          Ab[a] += dz[b] * dfc(a) * g * eba - cj * cost + PQd;
-          Ab[b] += dz[a] * dfc(b) * g * eab - ck * cost - PQd;
-        } else {
-          const R S = (dz[a] * fc[b] + dz[b] * fc[a]) * dg;
-          cj = S * ir(a);
-          ck = S * ir(b);
-          Ab[a] += dz[b] * dfc(a) * g - cj * cost;
-          Ab[b] += dz[a] * dfc(b) * g - ck * cost;
+          if constexpr (L3) {
+            R eab = R(1), eba = R(1);
+            if (Tp.lam3 != R(0)) {
+              R arg = Tp.lam3 * (rr[a] - rr[b]);
+              if (Tp.m3 != R(0)) arg = arg * arg * arg;
+              eab = M::expv(arg);
+              eba = M::expv(-arg);
+            }
+            zeta[a] += FC(b) * g * eab;
+            zeta[b] += FC(a) * g * eba;
+          } else {
+            zeta[a] += FC(b) * g;
+            zeta[b] += FC(a) * g;
+          }
         }
-        Fx[a] -= cj * ux[b];
-        Fy[a] -= cj * uy[b];
-        Fz[a] -= cj * uz[b];
-        Fx[b] -= ck * ux[a];
-        Fy[b] -= ck * uy[a];
-        Fz[b] -= ck * uz[a];
       }
     }
+
+    // ---- pair terms ---------------------------------------------------------------
+    // The force of i's terms on neighbour a is -(Ab[a] u_a + C_a): Ab collects every
+    // term along the bond i-a (the pair term's dV/dr first), C_a = (Fx, Fy, Fz) the
+    // terms along the other bonds, so that each term along a's own bond costs one
+    // scalar update instead of a vector one.
+#pragma unroll
+    for (int a = 0; a < MAXNC; ++a) {
+      dz[a] = Ab[a] = Fx[a] = Fy[a] = Fz[a] = R(0);
+      if (a < ncx) {
+        const PairP<R> P = pairp(ti, meta(a) >> 8);
+        R fR, fA;
+        if constexpr (MIXED && M::fine) {
+          fR = (R)aexp_mixed(P.A, P.Aln2, P.mu1h, P.mu1l, rr[a], rl(a));
+          fA = (R)aexp_mixed(-P.B, -P.Bln2, P.mu2h, P.mu2l, rr[a], rl(a));
+        } else {
+          fR = P.A * M::expneg(P.lam1, P.lam1_lo, rr[a], rl(a));
+          fA = -P.B * M::expneg(P.lam2, P.lam2_lo, rr[a], rl(a));
+        }
+        R bij, dbij;
+        bond_order<M>(zeta[a], P, bij, dbij);
+        const R bfA = bij * fA;
+        const R pr = fR + bfA;
+        e_i += R(0.5) * FC(a) * pr;
+        // dV/dr of V = fc (fR + b fA)/2 at fixed zeta: fc' pr/2 - fc (lambda1 fR + lambda2 b fA)/2
+        if constexpr (FULL) Ab[a] = -(P.hlam1 * fR + P.hlam2 * bfA);
+        else Ab[a] = R(0.5) * DFC(a) * pr - FC(a) * (P.hlam1 * fR + P.hlam2 * bfA);
+        dz[a] = R(0.5) * FC(a) * fA * dbij;
+      }
+    }
+
+    // ---- second K loop: zeta derivatives over unordered pairs -------------------
+    // With P = dV/dzeta_ij fc_k e_jk, Q = dV/dzeta_ik fc_j e_kj, S = (P + Q) g'
+    // (e_jk the lambda3 factor, arg' its exponent's derivative):
+    //   F_j -= S/r_j u_k + (dV/dzeta_ik fc'_j g e_kj - S/r_j cos + (P - Q) g arg') u_j
+    //   F_k -= S/r_k u_j + (dV/dzeta_ij fc'_k g e_jk - S/r_k cos - (P - Q) g arg') u_k
+    // (the u_j and u_k coefficients go to Ab[j], Ab[k]).
+#pragma unroll
+    for (int a = 0; a < MAXNC; ++a) {
+#pragma unroll
+      for (int b = a + 1; b < MAXNC; ++b) {
+        if (b < ncx) {
+          const TripP<R> Tp = tripp(ti, meta(a) >> 8, meta(b) >> 8);
+          R cost, g, dg;
+          if constexpr (CACHE) {
+            cost = c_cos[a][b];
+            g = c_g[a][b];
+            dg = c_dg[a][b];
+          } else {
+            cost = ux[a] * ux[b] + uy[a] * uy[b] + uz[a] * uz[b];
+            const R u = Tp.h - cost;
+            const R inv = M::rcp(Tp.d2 + u * u);
+            const R w = u * inv;
+            g = Tp.gamma + Tp.K * u * w;
+            dg = -Tp.G2 * w * inv;
+          }
+          R cj, ck;
+          if constexpr (L3) {
+            R eab = R(1), eba = R(1), darg = R(0);
+            if (Tp.lam3 != R(0)) {
+              const R tt = Tp.lam3 * (rr[a] - rr[b]);
+              R arg = tt;
+              darg = Tp.lam3;
+              if (Tp.m3 != R(0)) {
+                arg = tt * tt * tt;
+                darg = R(3) * Tp.lam3 * tt * tt;
+              }
+              eab = M::expv(arg);
+              eba = M::expv(-arg);
+            }
+            const R Pv = dz[a] * FC(b) * eab;
+            const R Qv = dz[b] * FC(a) * eba;
+            const R S = (Pv + Qv) * dg;
+            const R PQd = (Pv - Qv) * g * darg;
+            cj = S * ir(a);
+            ck = S * ir(b);
+            Ab[a] += dz[b] * DFC(a) * g * eba - cj * cost + PQd;
+            Ab[b] += dz[a] * DFC(b) * g * eab - ck * cost - PQd;
+          } else {
+            const R S = (dz[a] * FC(b) + dz[b] * FC(a)) * dg;
+            cj = S * ir(a);
+            ck = S * ir(b);
+            if constexpr (FULL) {
+              Ab[a] -= cj * cost;
+              Ab[b] -= ck * cost;
+            } else {
+              Ab[a] += dz[b] * DFC(a) * g - cj * cost;
+              Ab[b] += dz[a] * DFC(b) * g - ck * cost;
+            }
+          }
+          Fx[a] -= cj * ux[b];
+          Fy[a] -= cj * uy[b];
+          Fz[a] -= cj * uz[b];
+          Fx[b] -= ck * ux[a];
+          Fy[b] -= ck * uy[a];
+          Fz[b] -= ck * uz[a];
+        }
+      }
+    }
+  };
+  constexpr bool HAS_FULL = MAXNC == 4 && KIND != 0;
+  if constexpr (HAS_FULL) {
+    bool full = active && !over && nc == MAXNC && nc_all == MAXNC;
+#pragma unroll
+    for (int s = 0; s < MAXNC; ++s) full = full && fc[s] == R(1);
+    if (__all_sync(0xffffffffu, full)) evaluate(std::true_type{});
+    else evaluate(std::false_type{});
+  } else {
+    evaluate(std::false_type{});
   }
 
   // ---- outputs ------------------------------------------------------------------

@@ -22,6 +22,23 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
+// Exact float -> double widening on the integer pipe.  This GPU's FP64 pipe, which
+// runs at 1/65 of the FP32 rate and bounds the integrator, also executes the F2F
+// conversion; the bit construction below costs a few integer operations instead.  A
+// normal float's exponent moves from 8 to 11 bits (bias 127 -> 1023: + 896 << 20 in the
+// high word) and its 23-bit mantissa splits into the high word's top 20 bits and the
+// low word's top 3.  Zero and subnormal floats give +-0 (a force contribution is
+// either exactly 0 or far above 1e-38); Inf and NaN stay Inf and NaN.
+__device__ __forceinline__ double widen(float f)
+{
+  const unsigned u = __float_as_uint(f);
+  const unsigned a = u & 0x7fffffffu;
+  unsigned hi = a >= 0x7f800000u ? ((a >> 3) | 0x7ff00000u) : ((a >> 3) + 0x38000000u);
+  unsigned lo = u << 29;
+  if (a < 0x00800000u) hi = lo = 0u;
+  return __hiloint2double((int)(hi | (u & 0x80000000u)), (int)lo);
+}
+
 // Force accumulators of the gather, one per precision; V is the contribution type.
 
 // mixed mode: float32 contributions summed with TwoSum, a head and tail float per
@@ -44,9 +61,9 @@ struct AccMixed {
   }
   __device__ __forceinline__ void out(double &fx, double &fy, double &fz) const
   {
-    fx = (double)h[0] + (double)l[0];
-    fy = (double)h[1] + (double)l[1];
-    fz = (double)h[2] + (double)l[2];
+    fx = widen(h[0]) + widen(l[0]);
+    fy = widen(h[1]) + widen(l[1]);
+    fz = widen(h[2]) + widen(l[2]);
   }
 };
 
@@ -63,7 +80,7 @@ struct AccSingle {
   }
   __device__ __forceinline__ void out(double &fx, double &fy, double &fz) const
   {
-    fx = (double)f[0]; fy = (double)f[1]; fz = (double)f[2];
+    fx = widen(f[0]); fy = widen(f[1]); fz = widen(f[2]);
   }
 };
 
