@@ -293,6 +293,8 @@ def run_gpu(args, ws, rank, local):
     md_mix = md_64 = md_sg = None
     # 3C-SiC 50^3 cells with 5% vacancies (950,000 atoms), mixed, dt 0.5 fs
     sic = sic_final = None
+    tab2 = m2 = sc = None
+    prof_s = st_s = fl_s = None
     if not args.no_sic:
         sc = wl.sic_1m(seed=4 + rank)
         tab2, m2 = pp.for_species(sc.species)
@@ -312,6 +314,50 @@ def run_gpu(args, ws, rank, local):
                "phases_ms_per_step_profiled": {k: prof_s[0][n] / st_s["prof_steps"] for n, k in
                                                enumerate(("integrator", "list_build", "force_register_kernel",
                                                           "force_overflow_and_reduce", "bookkeeping"))}}
+    # Variants measured beside the headline (same workload, fewer steps): the literal
+    # float64 force accumulation of mixed mode, and the register kernel reading the
+    # shared-memory table instead of its kernel-argument table (Si one type; SiC two).
+    variants = {}
+    if not args.no_variants:
+        k_v = max(3, args.steps // 4)
+        os.environ["TERSOFF_MIXED_ACCUMULATE"] = "fp64"
+        try:
+            _, fl_a, prof_a, st_a, md_a = timed(T.MIXED, k_v, args.warmup)
+        finally:
+            del os.environ["TERSOFF_MIXED_ACCUMULATE"]
+        md_a = None
+        variants["mixed_fp64_accumulation"] = {
+            "what": "mixed mode with each atom's float32 contributions summed in float64 (one float64 add per "
+                    "contribution component) instead of the compensated float32 sum",
+            "ms_per_step": sum(fl_a) / len(fl_a), "steps": len(fl_a),
+            "integrator_ms_profiled": prof_a[0][0] / st_a["prof_steps"],
+            "headline_integrator_ms_profiled": prof_mix[0][0] / st_mix["prof_steps"]}
+        os.environ["TERSOFF_FORCE_TABLE"] = "generic"
+        try:
+            Pg = T.Params(ctx, tab, masses)
+            P2g = T.Params(ctx, tab2, m2) if sic is not None else None
+        finally:
+            del os.environ["TERSOFF_FORCE_TABLE"]
+        _, fl_g, prof_g, st_g, md_g = timed(T.MIXED, k_v, args.warmup, params=Pg)
+        md_g = None
+        variants["si_generic_table"] = {
+            "what": "Si 512k mixed, register kernel with the shared-memory table (kind 0) instead of the one-type "
+                    "kernel-argument table (kind 1)",
+            "force_register_kernel_ms": prof_g[0][2] / prof_g[1][2], "headline_force_register_kernel_ms": None,
+            "ms_per_step": sum(fl_g) / len(fl_g)}
+        if P2g is not None:
+            _, fl_g2, prof_g2, st_g2, md_g2 = timed(T.MIXED, max(3, args.steps // 4), args.warmup, sc, P2g, 0.5e-3)
+            md_g2 = None
+            variants["sic_generic_table"] = {
+                "what": "3C-SiC 950k mixed, register kernels with the shared-memory table (kind 0) instead of the "
+                        "two-type kernel-argument table (kind 2)",
+                "force_register_kernels_ms_per_step": prof_g2[0][2] / st_g2["prof_steps"],
+                "headline_force_register_kernels_ms_per_step": prof_s[0][2] / st_s["prof_steps"],
+                "ms_per_step": sum(fl_g2) / len(fl_g2), "headline_ms_per_step": sum(fl_s) / len(fl_s)}
+        variant_finals = {"mixed_fp64_accumulation": st_a["final"]}
+    else:
+        variant_finals = {}
+
     # FMA-pipe throughput of this device, measured in the same run (clocks sampled)
     peaks = measure_alu_peaks()
     clk = clocks.stop()
@@ -418,6 +464,7 @@ def run_gpu(args, ws, rank, local):
         line["sic_1m"] = sic
     if rank == 0 and not args.no_cpu:
         finals = {"mixed": st_mix["final"], "fp64": st_64["final"], "single": st_sg["final"]}
+        finals.update(variant_finals)
         if sic:
             finals["sic_1m_mixed"] = sic_final
         line["cpu_baseline"] = cpu_baseline(args, s, quick=True)
@@ -449,6 +496,10 @@ def run_gpu(args, ws, rank, local):
                            "integration; same workload and timing as the headline"},
         "alu_peaks_measured": peaks
     }
+    if variants:
+        if "si_generic_table" in variants:
+            variants["si_generic_table"]["headline_force_register_kernel_ms"] = f_ms
+        line["variants"] = variants
     line.update(tail_keys)
     if "error" in line:
         line["error"] = line.pop("error")
@@ -634,6 +685,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-sic", action="store_true", help="skip the 950k-atom SiC line")
     ap.add_argument("--serving-jobs", type=int, default=4096, help="jobs of the serving stream (0: skip serving)")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the float64-accumulation and generic-table comparison runs")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     ws, rank, local = dist_setup()

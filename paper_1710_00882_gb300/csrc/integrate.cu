@@ -67,6 +67,22 @@ struct AccMixed {
   }
 };
 
+// mixed mode, float64 sum: each float32 contribution widened and added in float64
+// (the literal reading of float64 force accumulation; on this GPU each add runs on
+// the FP64 pipe at 1/65 of the FP32 rate)
+struct AccMixed64 {
+  using V = float4;
+  double f[3];
+  __device__ __forceinline__ void init(const float4 &c) { f[0] = widen(c.x); f[1] = widen(c.y); f[2] = widen(c.z); }
+  __device__ __forceinline__ void add(const float4 &c)
+  {
+    f[0] += widen(c.x);
+    f[1] += widen(c.y);
+    f[2] += widen(c.z);
+  }
+  __device__ __forceinline__ void out(double &fx, double &fy, double &fz) const { fx = f[0]; fy = f[1]; fz = f[2]; }
+};
+
 // single mode: a plain float32 sum (the paper's all-float32 accumulation)
 struct AccSingle {
   using V = float4;
@@ -446,8 +462,10 @@ cudaError_t launch_vv(cudaStream_t st, int prec, bool ke, int N, int mode, dbl4 
 {
   if (N == 0) return cudaSuccess;
   const int B = (N + VV_THREADS - 1) / VV_THREADS;
-  auto f = prec == PREC_FP64 ? launch_vv_a<AccFP64> : prec == PREC_MIXED ? launch_vv_a<AccMixed>
-                                                                           : launch_vv_a<AccSingle>;
+  auto f = prec == PREC_FP64          ? launch_vv_a<AccFP64>
+           : prec == PREC_MIXED        ? launch_vv_a<AccMixed>
+           : prec == PREC_MIXED_ACC64  ? launch_vv_a<AccMixed64>
+                                       : launch_vv_a<AccSingle>;
   f(st, ke, B, N, mode, x, v, q, qref, contrib, selfF, mask, rev, sys, ctl, mass, disp2_lim, kepart, rs);
   if (ke) k_ke_reduce<<<1, 256, 0, st>>>(kepart, B, rs);
   return cudaGetLastError();
@@ -464,6 +482,8 @@ cudaError_t launch_gather_out(cudaStream_t st, int prec, int N, const void *cont
     k_gather_out<AccFP64><<<B, T, 0, st>>>(N, (const dbl4 *)contrib, (const dbl4 *)selfF, mask, rev, out, rs);
   else if (prec == PREC_MIXED)
     k_gather_out<AccMixed><<<B, T, 0, st>>>(N, (const float4 *)contrib, (const float4 *)selfF, mask, rev, out, rs);
+  else if (prec == PREC_MIXED_ACC64)
+    k_gather_out<AccMixed64><<<B, T, 0, st>>>(N, (const float4 *)contrib, (const float4 *)selfF, mask, rev, out, rs);
   else
     k_gather_out<AccSingle><<<B, T, 0, st>>>(N, (const float4 *)contrib, (const float4 *)selfF, mask, rev, out, rs);
   return cudaGetLastError();

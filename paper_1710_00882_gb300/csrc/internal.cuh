@@ -16,8 +16,10 @@ __host__ __device__ __forceinline__ dbl4 make_dbl4(double x, double y, double z,
 constexpr int MAX_TYPES = 4;
 constexpr int FAST_THREADS = 128;   // block size of the register force kernel
 
-// arithmetic precision of a run (the values of tersoff_precision)
-enum Prec : int { PREC_FP64 = 0, PREC_MIXED = 1, PREC_SINGLE = 2 };
+// arithmetic precision of a run (the values of tersoff_precision); the gather and the
+// integrator also take PREC_MIXED_ACC64: mixed-mode contributions summed in float64
+// (the literal float64 accumulation, measured beside the compensated float32 sum)
+enum Prec : int { PREC_FP64 = 0, PREC_MIXED = 1, PREC_SINGLE = 2, PREC_MIXED_ACC64 = 3 };
 constexpr int MAX_CAP = 64;       // neighbour-list capacity limit per atom (64-bit in-cutoff mask)
 constexpr int NFIELDS = 14;       // {m, gamma, lambda3, c, d, h, n, beta, lambda2, B, R, D, lambda1, A}
 enum Field { F_M = 0, F_GAMMA, F_LAM3, F_C, F_D, F_H, F_N, F_BETA, F_LAM2, F_B, F_R, F_DD, F_LAM1, F_A };

@@ -151,6 +151,7 @@ struct tersoff_md {
   size_t trace_cap = 0;
   double dt = 0, skin = 0;
   int prec = TERSOFF_FP64;
+  int gprec = TERSOFF_FP64;   // accumulation of the force gather (PREC_MIXED_ACC64: float64 sums)
   bool f32 = false;     // float32 force arithmetic (mixed or single precision)
   bool open = false;            // velocities are at the half step (a closing kick is pending)
   bool pe_valid = false;        // rs->epot_last holds the potential energy of the current positions
@@ -581,6 +582,10 @@ int tersoff_params_create(tersoff_ctx *ctx, int ntypes, const double *entries, c
     bool lam3_zero = true;
     for (int r = 0; r < nrow; ++r) lam3_zero = lam3_zero && entries[(size_t)r * NFIELDS + F_LAM3] == 0.0;
     P->fast.kind = (lam3_zero && P->sym_angular && nt <= 2) ? nt : 0;
+    // TERSOFF_FORCE_TABLE=generic: the register kernel reads the shared-memory table
+    // for every table (the same terms; a measurement switch for the specialised kinds)
+    const char *ft = getenv("TERSOFF_FORCE_TABLE");
+    if (ft && strcmp(ft, "generic") == 0) P->fast.kind = 0;
     if (P->fast.kind > 0) {
       for (int k = 0; k < nt * nt; ++k) {
         P->fast.f.p[k] = pf[k];
@@ -855,7 +860,7 @@ static int md_vv(tersoff_md *md, cudaStream_t st, int mode, bool ke)
 {
   tersoff_ctx *ctx = md->ctx;
   const float lim = (float)(0.25 * md->skin * md->skin);
-  CK(launch_vv(st, md->prec, ke, (int)md->atoms.N, mode, md->atoms.x, md->atoms.v, md->atoms.q, md->list.qref,
+  CK(launch_vv(st, md->gprec, ke, (int)md->atoms.N, mode, md->atoms.x, md->atoms.v, md->atoms.q, md->list.qref,
                md->atoms.contrib, md->atoms.selfF, md->atoms.mask, md->list.rev, md->sys.tab,
                md->sys.ctl, md->params->d_mass, lim, md->atoms.kepart, md->rs));
   return TERSOFF_OK;
@@ -1074,6 +1079,14 @@ int tersoff_md_create(tersoff_ctx *ctx, const double *pos, const double *vel, co
   md->skin = skin;
   md->prec = prec;
   md->f32 = prec != TERSOFF_FP64;
+  // TERSOFF_MIXED_ACCUMULATE=fp64: mixed-mode force contributions summed in float64
+  // instead of the compensated float32 sum (the same forces to ~1e-16 relative; a
+  // measurement switch for the accumulation reading)
+  md->gprec = prec;
+  {
+    const char *acc = getenv("TERSOFF_MIXED_ACCUMULATE");
+    if (prec == TERSOFF_MIXED && acc && strcmp(acc, "fp64") == 0) md->gprec = PREC_MIXED_ACC64;
+  }
   auto fail = [&](int rc) {
     tersoff_md_destroy(md);
     return rc;
@@ -1245,7 +1258,7 @@ int tersoff_md_get(tersoff_md *md, double *pos, double *vel, double *forces, int
   int rc = TERSOFF_OK;
   if (launch_extract(ctx->stream, (int)N, md->atoms.x, md->atoms.v, dp, dv) != cudaSuccess) rc = TERSOFF_ERR_CUDA;
   if (rc == TERSOFF_OK && df &&
-      launch_gather_out(ctx->stream, md->prec, (int)N, md->atoms.contrib, md->atoms.selfF, md->atoms.mask,
+      launch_gather_out(ctx->stream, md->gprec, (int)N, md->atoms.contrib, md->atoms.selfF, md->atoms.mask,
                         md->list.rev, df, md->rs) != cudaSuccess)
     rc = TERSOFF_ERR_CUDA;
   if (rc == TERSOFF_OK && !dev) {

@@ -308,3 +308,28 @@ def test_register_and_general_kernels_agree(T, prec_name, monkeypatch):
         assert abs(E1 - E2) <= 1e-6 * abs(E2) and np.abs(F1 - F2).max() < 1e-4
     else:
         assert abs(E1 - E2) <= 1e-5 * abs(E2) and np.abs(F1 - F2).max() < 1e-3
+
+
+@pytest.mark.parametrize("prec_name", ["FP64", "MIXED", "SINGLE"])
+@pytest.mark.parametrize("case", ["si", "sic"])
+def test_type_specialised_and_generic_tables_agree(T, prec_name, case, monkeypatch):
+    """The register kernel with its table in the kernel argument (one type: Si; two
+    types: SiC, lambda3 = 0) and with the shared-memory table every table can use
+    (TERSOFF_FORCE_TABLE=generic): the same terms, so the same forces within rounding,
+    and both match the oracle."""
+    prec = getattr(T, prec_name)
+    s = wl.si_box(5, 4, 3, seed=51, T=1000.0) if case == "si" else wl.sic_box(4, seed=52, T=1500.0)
+    c1 = T.Context(0)
+    P1 = product_params(c1, s.species)
+    E1, F1, W1 = T.compute(c1, P1, s.pos, s.types, s.box, prec=prec)
+    monkeypatch.setenv("TERSOFF_FORCE_TABLE", "generic")
+    c2 = T.Context(0)
+    P2 = product_params(c2, s.species)
+    E2, F2, W2 = T.compute(c2, P2, s.pos, s.types, s.box, prec=prec)
+    tab, _ = oracle_table(s.species)
+    Eo, Fo, Wo = oracle.energy_forces(s.pos, s.types, s.box, tab)
+    er, fa, wa = {T.FP64: (FP64_E_REL, FP64_F_ABS, FP64_W_ATOM), T.MIXED: (MIX_E_REL, MIX_F_ABS, MIX_W_ATOM),
+                  T.SINGLE: (SGL_E_REL, SGL_F_ABS, SGL_W_ATOM)}[prec]
+    assert_parity(E1, F1, W1, Eo, Fo, Wo, er, fa, wa, f"{case} kernel-argument table")
+    assert_parity(E2, F2, W2, Eo, Fo, Wo, er, fa, wa, f"{case} generic table")
+    assert_parity(E1, F1, W1, E2, F2, W2, er, fa, wa, f"{case} tables agree")

@@ -240,3 +240,26 @@ def test_profiled_steps_equal_graph_steps(T, ctx):
     assert (n[[0, 1, 2, 3, 4]] > 0).all()
     assert (ms[[0, 2, 4]] > 0).all()
     assert a.stats()["steps"] == b.stats()["steps"] == 12
+
+
+def test_float64_accumulation_variant(T, ctx, monkeypatch):
+    """Mixed mode with the contributions summed in float64 (TERSOFF_MIXED_ACCUMULATE=
+    fp64) against the compensated float32 sum of the default: after 20 steps from the
+    same state both trajectories and force sets agree to float64 rounding (the two sums
+    differ by ~1e-16 relative per step), and the float64-summed forces match the oracle
+    on the state reached."""
+    s = wl.si_box(6, 6, 6, seed=23, T=1000.0)
+    P = product_params(ctx, s.species)
+    tab, m = oracle_table(s.species)
+    a = T.MD(ctx, P, s.pos, s.vel, s.types, s.box, dt=1e-3, skin=0.3, prec=T.MIXED)
+    monkeypatch.setenv("TERSOFF_MIXED_ACCUMULATE", "fp64")
+    b = T.MD(ctx, P, s.pos, s.vel, s.types, s.box, dt=1e-3, skin=0.3, prec=T.MIXED)
+    monkeypatch.delenv("TERSOFF_MIXED_ACCUMULATE")
+    a.step(20)
+    b.step(20)
+    pa, va, fa_ = a.get(forces=True)
+    pb, vb, fb = b.get(forces=True)
+    assert np.abs(pa - pb).max() < 1e-12
+    assert np.abs(fa_ - fb).max() < 1e-10
+    Eo, Fo, _ = oracle.energy_forces(pb, s.types, s.box, tab)
+    assert np.abs(fb - Fo).max() < MIX_F_ABS
