@@ -55,10 +55,10 @@ C_PAIR = 57
 C_TAPER = 10
 C_TRIPLET = 40
 # Mixed mode adds, per in-cutoff pair, the work that keeps r and lambda*r to ~1 ulp:
-# the relative vector rounded once from a head/tail split (12 more than one product
-# per component), the Newton tail of r (4) and the head/tail exponent of f_R and f_A
-# (7 more each): float32 work beyond the method's own, reported apart as overhead.
-C_PAIR_MIXED_OVERHEAD = 30
+# the relative vector and |d| as exact head + tail (71 flops where the method's
+# geometry takes 10) and the head/tail exponent of f_R and f_A (7 more each): float32
+# work beyond the method's own, reported apart as overhead.
+C_PAIR_MIXED_OVERHEAD = 75
 # Peaks.  Derived from unit counts and the maximum SM clock: 152 SMs x 128 FP32 lanes
 # x 2 flop x 2.07 GHz; FP64: GB300's nominal 1.25 TFLOP/s.  The FMA-pipe probe
 # (libalu_peaks.so) measures both in the same run.
@@ -435,8 +435,8 @@ def run_gpu(args, ws, rank, local):
                      "what_is_counted": "the method's own float32 work (Algorithm 1): 8 per list entry, 57 per "
                                         "in-cutoff pair, 10 per taper pair, 40 per ordered triplet",
                      "overhead_flops_per_launch": overhead,
-                     "overhead_what": "mixed mode's compensation (relative vector rounded once, Newton tail "
-                                      "of r, head+tail exponents): 30 flops per in-cutoff pair",
+                     "overhead_what": "mixed mode's compensation (relative vector and |d| as exact head+tail, "
+                                      "head+tail exponents): 75 flops per in-cutoff pair",
                      "achieved_with_overhead": (flops + overhead) / (f_ms / 1e3) / 1e12,
                      "frac_with_overhead": (flops + overhead) / (f_ms / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
                      "kernel_ms": f_ms,

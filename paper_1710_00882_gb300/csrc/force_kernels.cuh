@@ -257,17 +257,6 @@ __device__ __forceinline__ void block_partial(const R (&v)[7], bool eflag, bool 
 // ============================================================================
 // fast kernel: register slots, unordered neighbour pairs
 
-// Relative-vector component d = dq L/2^32 rounded once (mixed mode): the int32
-// difference is split into a 24-bit head h and an 8-bit tail l, both exact in float,
-// and the scale into float head sh + tail sl; d = h sh + (l sh + h sl), the small
-// terms formed first, so that the final FMA rounds the whole sum once.
-__device__ __forceinline__ float qd_once(int dq, float sh, float sl)
-{
-  const float h = (float)(dq & ~0xff);
-  const float l = (float)(dq & 0xff);
-  return __fmaf_rn(h, sh, __fmaf_rn(l, sh, __fmul_rn(h, sl)));
-}
-
 // A e^{-lambda r} in float32 (mixed mode) for r = rh + rl: y = mu r with mu =
 // lambda log2(e) given as float head muh + tail mul; muh rh is split exactly with an
 // FMA, so y = yh + yl with |yl| ~ 1e-6, and 2^{-y} = 2^{-yh} (1 - yl ln 2) to first
@@ -382,14 +371,23 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
     meta(s) = 0;
   }
 
+  // 8-slot mixed kernels: the first pass over the list stages each in-cutoff
+  // neighbour's fixed-point record, list entry and type in shared memory, in the
+  // column of the thread that tested it; after the count sort the evaluating thread
+  // fills its slots from that column instead of gathering the neighbours again.
+  constexpr bool STAGE = SORT && MIXED;
+  __shared__ int4 s_qn[STAGE ? MAXNC : 1][STAGE ? T : 1];
+  __shared__ int s_en[STAGE ? MAXNC : 1][STAGE ? T : 1];
+  __shared__ int4 s_qi[STAGE ? T : 1];
+  __shared__ int s_src[STAGE ? T : 1];
+
   // geometry of slot s from list entry e (neighbour j): unit vector, r, 1/r, f_C, f_C'
   auto fill_slot = [&](int s, int e, int j, const int4 &qj, const dbl4 &xj, int tj) {
     R dx, dy, dz, r, rlo, inv;
-    if (MIXED && M::fine && MAXNC == 8) {
-      // 8-slot kernel (atoms with taper neighbours, e.g. Si in 3C-SiC): d and |d| as
-      // head + tail, so that R + D - r in the taper and lambda r keep their accuracy
-      // (measured on 3C-SiC 950k: force error 1.8e-5 eV/A, against 6.8e-5 with the
-      // single-rounding form below)
+    if (MIXED && M::fine) {
+      // d and |d| as head + tail, so that lambda r and, in the f_C taper, R + D - r keep
+      // their accuracy.  Both register kernels (4 and 8 slots) form the geometry the same
+      // way, so an atom's forces do not depend on which of them evaluates it.
       float dh[3], dl[3];
       qd_fine(qdiff(qj.x, qi.x), gp->q_to_f[0], gp->q_to_f_lo[0], dh[0], dl[0]);
       qd_fine(qdiff(qj.y, qi.y), gp->q_to_f[1], gp->q_to_f_lo[1], dh[1], dl[1]);
@@ -398,19 +396,6 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
       norm_fine(dh, dl, rh_, rl_, irh_);
       dx = (R)dh[0]; dy = (R)dh[1]; dz = (R)dh[2];
       r = (R)rh_; rlo = (R)rl_; inv = (R)irh_;
-    } else if (MIXED && M::fine) {
-      // 4-slot kernel: d rounded once per component; r = |d| as head + tail from one
-      // Newton step on the float32 square, so that lambda r (|d| ~ 2 A, lambda r ~ 6)
-      // keeps ~1 ulp
-      dx = (R)qd_once(qdiff(qj.x, qi.x), gp->q_to_f[0], gp->q_to_f_lo[0]);
-      dy = (R)qd_once(qdiff(qj.y, qi.y), gp->q_to_f[1], gp->q_to_f_lo[1]);
-      dz = (R)qd_once(qdiff(qj.z, qi.z), gp->q_to_f[2], gp->q_to_f_lo[2]);
-      const float r2f = __fmaf_rn((float)dx, (float)dx, __fmaf_rn((float)dy, (float)dy, __fmul_rn((float)dz, (float)dz)));
-      const float irs = MathF::rsqrt(r2f);
-      const float rh_ = __fmul_rn(r2f, irs);
-      r = (R)rh_;
-      rlo = (R)__fmul_rn(__fmaf_rn(-rh_, rh_, r2f), __fmul_rn(0.5f, irs));
-      inv = (R)irs;
     } else if (MIXED) {
       dx = (R)q_scaled(qdiff(qj.x, qi.x), gp->q_to_f[0]);
       dy = (R)q_scaled(qdiff(qj.y, qi.y), gp->q_to_f[1]);
@@ -480,6 +465,7 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
   } else if (active) {
     // PU list entries per round: their loads are issued together
     constexpr int PU = MIXED ? 4 : 2;
+    int staged = 0;
     for (int s0 = 0; s0 < n; s0 += PU) {
       int jj[PU];
 #pragma unroll
@@ -494,7 +480,16 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
 #pragma unroll
       for (int k = 0; k < PU; ++k) {
         const int tj = type_of(MIXED ? qq[k].w : (int)__double_as_longlong(xx[k].w));
-        if (s0 + k < n && in_cutoff(qq[k], xx[k], tj)) mb |= 1ull << (s0 + k);
+        if (s0 + k < n && in_cutoff(qq[k], xx[k], tj)) {
+          mb |= 1ull << (s0 + k);
+          if constexpr (STAGE) {
+            if (staged < MAXNC) {
+              s_qn[staged][t] = qq[k];
+              s_en[staged][t] = (s0 + k) | (tj << 8);
+            }
+            ++staged;
+          }
+        }
       }
     }
     nc_all = __popcll(mb);
@@ -561,6 +556,10 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
     for (int v = 0; v < w; ++v) r += s_cnt[v][key];
     s_atom[r] = key <= MAXNC ? i : -1;
     s_mb[r] = mb;
+    if constexpr (STAGE) {
+      s_src[r] = t;
+      s_qi[r] = qi;
+    }
     __syncthreads();
     const int inew = s_atom[t];
     active = inew >= 0;
@@ -570,7 +569,10 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
     nc_all = __popcll(mb);
     if (active) {
       int wn;
-      if (MIXED) {
+      if constexpr (STAGE) {
+        qi = s_qi[t];
+        wn = qi.w;
+      } else if (MIXED) {
         qi = q[i];
         wn = qi.w;
       } else {
@@ -583,7 +585,16 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
   }
   // slots in use: the whole list on the direct path, the packed in-cutoff entries else
   const int nc = direct ? n : (over ? 0 : nc_all);
-  if (!direct && !over && active) {
+  if (STAGE && active) {
+    const int src = s_src[t];
+#pragma unroll
+    for (int s = 0; s < MAXNC; ++s) {
+      if (s < nc) {
+        const int en = s_en[s][src];
+        fill_slot(s, en & 0xff, 0, s_qn[s][src], make_dbl4(0, 0, 0, 0), en >> 8);
+      }
+    }
+  } else if (!direct && !over && active) {
     unsigned long long rem = mb;
 #pragma unroll
     for (int s = 0; s < MAXNC; ++s) {
@@ -619,7 +630,7 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
     // not fit): computed once, not twice.
     constexpr bool CACHE = MAXNC == 4 && KIND != 0;
     constexpr int CN = CACHE ? MAXNC : 1;
-    R c_cos[CN][CN], c_g[CN][CN], c_dg[CN][CN];
+    [[maybe_unused]] R c_cos[CN][CN], c_g[CN][CN], c_dg[CN][CN];
 #pragma unroll
     for (int s = 0; s < MAXNC; ++s) zeta[s] = R(0);
 #pragma unroll
