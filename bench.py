@@ -544,7 +544,8 @@ def serving_bench(ctx, njobs, budget_gb=4.0, max_slots=512, chunk=25):
         lat = np.array(lat)
         return {"atom_steps_per_s": work / (t1 - t0), "seconds": t1 - t0,
                 "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
-                "chunks": st["chunks"], "repacks": st["repacks"], "busy_s": st["busy_s"],
+                "chunks": st["chunks"], "repacks": st["repacks"], "compactions": st["compactions"],
+                "layout_fill": st["layout_fill"], "busy_s": st["busy_s"],
                 "scheduler_s": {k: st[k] for k in ("retire_s", "repack_s", "graph_s", "run_s")},
                 "capacity_atoms": st["capacity_atoms"]}
 

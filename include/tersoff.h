@@ -244,9 +244,14 @@ int tersoff_compute_noalloc(const tersoff_params *params, const double *pos, con
  * chunks of steps run as one CUDA graph launch.  A scheduler thread owned by the
  * server retires finished jobs and admits queued ones at chunk boundaries, as
  * slots and the device-memory budget allow (continuous batching): requests that
- * arrive while others run join the next chunk.  A job's trajectory does not
- * depend on the other jobs in the batch (same arithmetic, same order): its result
- * is bitwise the same alone and in any mix.
+ * arrive while others run join the next chunk.  A job keeps its atom range for
+ * its whole run: a new job goes into a free range and only its own list and
+ * forces are computed on admission; the layout is compacted (resident jobs moved,
+ * every list rebuilt) only when no free range holds a new job or freed atoms pass
+ * 30% of the occupied range (environment TERSOFF_COMPACT_FREED=f sets that share).
+ * A job's trajectory does not depend on the other jobs in the batch or on where it
+ * sits (same arithmetic, same order): its result is bitwise the same alone and in
+ * any mix.
  *
  * params: shared by all jobs (job types index into it).  prec: precision of all
  * jobs.  skin: Verlet skin (A).  device_mem_budget: bytes the packed layout may
@@ -269,12 +274,15 @@ typedef struct {
 typedef struct {
   int64_t submitted, admitted, completed, failed, queued, running;
   int64_t atom_steps;    /* atom-steps of completed work */
-  int64_t chunks, repacks;
+  int64_t chunks, repacks;   /* chunks of steps run; admissions that placed new jobs */
   double busy_s;         /* wall time with jobs resident */
   int64_t capacity_atoms;
-  /* scheduler wall time by activity (s): retiring finished jobs, repacking the
-   * layout on admission, capturing graphs, running chunks of steps */
+  /* scheduler wall time by activity (s): retiring finished jobs, admitting new
+   * jobs (placement, their lists and first forces, compactions), capturing graphs,
+   * running chunks of steps */
   double retire_s, repack_s, graph_s, run_s;
+  int64_t compactions;   /* admissions that moved resident jobs (layout compacted) */
+  double layout_fill;    /* resident atoms / atoms the step kernels cover (freed ranges included), over chunks */
 } tersoff_server_stats;
 
 int tersoff_server_create(tersoff_ctx *ctx, const tersoff_params *params, tersoff_precision prec, double skin,

@@ -38,7 +38,8 @@ __global__ void __launch_bounds__(1024) k_reduce_partials(const double *__restri
 #define TSF_FORCE_DECL(NAME)                                                                                        \
   cudaError_t NAME(int part, cudaStream_t st, int fast_slots, const FastTab &ft, int gen_slots, int eflag,       \
                    int vflag,                                                                                      \
-                   int N, const dbl4 *x, const int4 *q, const int *nbr, const int *cnt, const SysTab *sys,         \
+                   int N, int ld, const dbl4 *x, const int4 *q, const int *nbr, const int *cnt,                   \
+                   const SysTab *sys,                                                                              \
                    const void *pairs, const void *trips, int nt, void *contrib, void *selfF,                       \
                    unsigned long long *mask, int *work, int *nwork, double *partial, RunState *rs, double *eatom,  \
                    const ForceRoutes *routes, int stats, int *rows);
@@ -64,6 +65,7 @@ int force_queue_blocks(int N) { return (N + FAST_THREADS - 1) / FAST_THREADS + 2
 // One force evaluation in precision prec (PREC_FP64, PREC_MIXED or PREC_SINGLE).
 // fast_slots 4 or 8 runs the register kernel plus the warp kernel over its overflow
 // queue; fast_slots 0 runs the general kernel (gen_slots wide) over all atoms.
+// ld: the list stride (slot s of atom i at s * ld + i of nbr and contrib, ld >= N).
 // routes (may be null: every atom in index order with fast_slots) splits the
 // register kernel into launches over atom subsets, each with its own slot count.
 // Buffers: partial force_partial_rows(N) x 8 doubles; work force_queue_blocks(N) x
@@ -72,14 +74,14 @@ int force_queue_blocks(int N) { return (N + FAST_THREADS - 1) / FAST_THREADS + 2
 // kernel(s) only, 2 the rest (overflow or general kernel and the reduction), 3 both.
 // stats: record the largest in-cutoff counts (rs->maxnc, rs->maxnc_t).
 cudaError_t launch_force_part(int part, cudaStream_t st, int prec, int fast_slots, const FastTab &ft, int gen_slots,
-                              int eflag, int vflag, int N, const dbl4 *x, const int4 *q, const int *nbr,
+                              int eflag, int vflag, int N, int ld, const dbl4 *x, const int4 *q, const int *nbr,
                               const int *cnt, const SysTab *sys, const void *pairs, const void *trips, int nt,
                               void *contrib, void *selfF, unsigned long long *mask, int *work, int *nwork,
                               double *partial, RunState *rs, double *eatom, const ForceRoutes *routes, int stats)
 {
   auto f = prec == PREC_FP64 ? launch_force_fp64 : prec == PREC_MIXED ? launch_force_mixed : launch_force_single;
   int rows = 0;
-  cudaError_t e = f(part, st, fast_slots, ft, gen_slots, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt,
+  cudaError_t e = f(part, st, fast_slots, ft, gen_slots, eflag, vflag, N, ld, x, q, nbr, cnt, sys, pairs, trips, nt,
                     contrib, selfF, mask, work, nwork, partial, rs, eatom, routes, stats, &rows);
   if (e != cudaSuccess) return e;
   if ((eflag || vflag) && rows > 0 && (part & 2)) {
@@ -95,7 +97,7 @@ cudaError_t launch_force(cudaStream_t st, int prec, int fast_slots, const FastTa
                          unsigned long long *mask, int *work, int *nwork, double *partial, RunState *rs,
                          double *eatom)
 {
-  return launch_force_part(3, st, prec, fast_slots, ft, gen_slots, eflag, vflag, N, x, q, nbr, cnt, sys, pairs,
+  return launch_force_part(3, st, prec, fast_slots, ft, gen_slots, eflag, vflag, N, N, x, q, nbr, cnt, sys, pairs,
                            trips, nt, contrib, selfF, mask, work, nwork, partial, rs, eatom, nullptr, 1);
 }
 

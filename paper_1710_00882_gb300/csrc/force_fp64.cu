@@ -4,12 +4,12 @@
 namespace tsf {
 
 cudaError_t launch_force_fp64(int part, cudaStream_t st, int fast_slots, const FastTab &ft, int gen_slots, int eflag,
-                              int vflag, int N, const dbl4 *x, const int4 *q, const int *nbr, const int *cnt,
+                              int vflag, int N, int ld, const dbl4 *x, const int4 *q, const int *nbr, const int *cnt,
                               const SysTab *sys, const void *pairs, const void *trips, int nt, void *contrib,
                               void *selfF, unsigned long long *mask, int *work, int *nwork, double *partial,
                               RunState *rs, double *eatom, const ForceRoutes *routes, int stats, int *rows)
 {
-  return launch_force_m<MathD>(part, st, fast_slots, ft, gen_slots, eflag, vflag, N, x, q, nbr, cnt, sys, pairs,
+  return launch_force_m<MathD>(part, st, fast_slots, ft, gen_slots, eflag, vflag, N, ld, x, q, nbr, cnt, sys, pairs,
                                trips, nt, contrib, selfF, mask, work, nwork, partial, rs, eatom, routes, stats, rows);
 }
 

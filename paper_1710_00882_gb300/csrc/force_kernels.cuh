@@ -273,7 +273,7 @@ __device__ __forceinline__ float aexp_mixed(float A, float Aln2, float muh, floa
 // (two types) from the kernel argument kp (constant bank), lambda3 = 0 compiled out.
 template <class M, int MAXNC, int KIND, bool EFLAG, bool VFLAG>
 __global__ void __launch_bounds__(FAST_THREADS, sizeof(typename M::R) == 4 ? (MAXNC == 4 ? 7 : 5) : 1)
-k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const int *__restrict__ nbr,
+k_force_reg(int ld, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const int *__restrict__ nbr,
             const int *__restrict__ cnt, const SysTab *__restrict__ sys,
             const PairP<typename M::R> *__restrict__ gpairs,
             const TripP<typename M::R> *__restrict__ gtrips, int nt,
@@ -282,7 +282,7 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
             typename V4t<typename M::R>::type *__restrict__ selfF, unsigned long long *__restrict__ mask,
             int *__restrict__ work, int *__restrict__ nwork, double *__restrict__ partial, RunState *rs,
             double *__restrict__ eatom, const int *__restrict__ order, int begin, int count, int block_base,
-            int stats)
+            int stats, int pf)
 {
   using R = typename M::R;
   using V4 = typename V4t<R>::type;
@@ -321,6 +321,14 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
   bool active = tg < count;
   int i = active ? (order ? order[begin + tg] : begin + tg) : 0;
   const int fb = block_base + (int)blockIdx.x;   // this block's queue and partial-sum row
+  // pf atoms ahead (one resident wave of blocks): the counts and list rows the next
+  // wave reads, from DRAM after a cold start, are requested into L2 now
+  if (pf > 0 && !order && tg + pf < count) {
+    const int ip = begin + tg + pf;
+    prefetch_l2(cnt + ip);
+#pragma unroll
+    for (int s = 0; s < MAXNC; ++s) prefetch_l2(nbr + (size_t)s * ld + ip);
+  }
 
   int ti = 0;
   int4 qi = make_int4(0, 0, 0, 0);
@@ -441,7 +449,7 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
   if (direct) {
     int jj[MAXNC];
 #pragma unroll
-    for (int s = 0; s < MAXNC; ++s) jj[s] = s < n ? nbr[(size_t)s * N + i] : i;
+    for (int s = 0; s < MAXNC; ++s) jj[s] = s < n ? nbr[(size_t)s * ld + i] : i;
     int4 qq[MAXNC];
     dbl4 xx[MAXNC];
 #pragma unroll
@@ -469,7 +477,7 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
     for (int s0 = 0; s0 < n; s0 += PU) {
       int jj[PU];
 #pragma unroll
-      for (int k = 0; k < PU; ++k) jj[k] = s0 + k < n ? nbr[(size_t)(s0 + k) * N + i] : i;
+      for (int k = 0; k < PU; ++k) jj[k] = s0 + k < n ? nbr[(size_t)(s0 + k) * ld + i] : i;
       int4 qq[PU];
       dbl4 xx[PU];
 #pragma unroll
@@ -601,7 +609,7 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
       if (s < nc) {
         const int e = __ffsll((long long)rem) - 1;
         rem &= rem - 1;
-        const int j = nbr[(size_t)e * N + i];
+        const int j = nbr[(size_t)e * ld + i];
         int4 qj = make_int4(0, 0, 0, 0);
         dbl4 xj = make_dbl4(0, 0, 0, 0);
         int tj;
@@ -792,7 +800,7 @@ k_force_reg(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
         fiz -= Fz[a];
         V4 c;
         c.x = Fx[a]; c.y = Fy[a]; c.z = Fz[a]; c.w = R(0);
-        contrib[(size_t)(meta(a) & 0xff) * N + i] = c;
+        contrib[(size_t)(meta(a) & 0xff) * ld + i] = c;
         if (VFLAG) {
           const R dx = rr[a] * ux[a], dy = rr[a] * uy[a], dzz = rr[a] * uz[a];
           red[1] += dx * Fx[a]; red[2] += dy * Fy[a]; red[3] += dzz * Fz[a];
@@ -867,7 +875,7 @@ struct GenCfg {
 // (i,j,k) and (i,k,j), and the reference the register kernel is tested against.
 template <class M, int MAXNC, bool EFLAG, bool VFLAG>
 __global__ void __launch_bounds__(GenCfg<typename M::R, MAXNC>::threads)
-k_force_gen(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const int *__restrict__ nbr,
+k_force_gen(int N, int ld, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const int *__restrict__ nbr,
             const int *__restrict__ cnt, const SysTab *__restrict__ sys,
             const PairP<typename M::R> *__restrict__ gpairs, const TripP<typename M::R> *__restrict__ gtrips, int nt,
             typename V4t<typename M::R>::type *__restrict__ contrib,
@@ -910,6 +918,8 @@ k_force_gen(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
       w = (int)__double_as_longlong(xi.w);
     }
     ti = type_of(w);
+    // atoms of a freed range of a packed layout belong to a system without atoms
+    if (sys[sys_of(w)].natoms == 0) return;
     const Geom *gp = &sys[sys_of(w)].geo;
     int nc = 0;
     unsigned long long mbits = 0ull;
@@ -919,7 +929,7 @@ k_force_gen(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
     for (int s0 = 0; s0 < n; s0 += GU) {
       int jj[GU];
 #pragma unroll
-      for (int k = 0; k < GU; ++k) jj[k] = s0 + k < n ? nbr[(size_t)(s0 + k) * N + i] : i;
+      for (int k = 0; k < GU; ++k) jj[k] = s0 + k < n ? nbr[(size_t)(s0 + k) * ld + i] : i;
       int4 qq[GU];
       dbl4 xx[GU];
 #pragma unroll
@@ -1087,7 +1097,7 @@ k_force_gen(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const
       fiz -= fz;
       V4 c;
       c.x = fx; c.y = fy; c.z = fz; c.w = R(0);
-      contrib[(size_t)(META(a) & 0xff) * N + i] = c;
+      contrib[(size_t)(META(a) & 0xff) * ld + i] = c;
       if (VFLAG) {
         const R r = SLOT(S_R, a);
         const R dx = r * SLOT(S_UX, a), dy = r * SLOT(S_UY, a), dz = r * SLOT(S_UZ, a);
@@ -1131,7 +1141,7 @@ constexpr int WSLOTS = MAX_CAP;   // slots per warp: a list holds at most MAX_CA
 // gridDim.x), as one flat queue in order; its warps take entries w, w + 4, ...
 template <class M, bool EFLAG, bool VFLAG>
 __global__ void __launch_bounds__(WARP_BLOCK)
-k_force_warp(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const int *__restrict__ nbr,
+k_force_warp(int ld, const dbl4 *__restrict__ x, const int4 *__restrict__ q, const int *__restrict__ nbr,
              const int *__restrict__ cnt, const SysTab *__restrict__ sys,
              const PairP<typename M::R> *__restrict__ gpairs, const TripP<typename M::R> *__restrict__ gtrips,
              int nt, typename V4t<typename M::R>::type *__restrict__ contrib,
@@ -1190,7 +1200,7 @@ k_force_warp(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, cons
       dbl4 xj = make_dbl4(0, 0, 0, 0);
       R dx = R(0), dy = R(0), dz = R(0);
       if (s < n) {
-        const int j = nbr[(size_t)s * N + i];
+        const int j = nbr[(size_t)s * ld + i];
         if (MIXED) {
           qj = q[j];
           tj = type_of(qj.w);
@@ -1352,7 +1362,7 @@ k_force_warp(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, cons
       }
       V4 o;
       o.x = fx; o.y = fy; o.z = fz; o.w = R(0);
-      contrib[(size_t)(meta[c] & 0xff) * N + i] = o;
+      contrib[(size_t)(meta[c] & 0xff) * ld + i] = o;
       sx -= fx;
       sy -= fy;
       sz -= fz;
@@ -1401,7 +1411,7 @@ k_force_warp(int N, const dbl4 *__restrict__ x, const int4 *__restrict__ q, cons
 // ---- host-side launch ------------------------------------------------------
 
 template <class M, int MAXNC, bool EFLAG, bool VFLAG>
-static cudaError_t launch_gen_t(cudaStream_t st, int N, const dbl4 *x, const int4 *q, const int *nbr, const int *cnt,
+static cudaError_t launch_gen_t(cudaStream_t st, int N, int ld, const dbl4 *x, const int4 *q, const int *nbr, const int *cnt,
                                 const SysTab *sys, const void *pairs, const void *trips, int nt, void *contrib,
                                 void *selfF, unsigned long long *mask, double *partial, RunState *rs, double *eatom)
 {
@@ -1416,25 +1426,25 @@ static cudaError_t launch_gen_t(cudaStream_t st, int N, const dbl4 *x, const int
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int blocks = (N + C::threads - 1) / C::threads;
-  kern<<<blocks, C::threads, smem, st>>>(N, x, q, nbr, cnt, sys, (const PairP<R> *)pairs, (const TripP<R> *)trips,
+  kern<<<blocks, C::threads, smem, st>>>(N, ld, x, q, nbr, cnt, sys, (const PairP<R> *)pairs, (const TripP<R> *)trips,
                                          nt, (typename V4t<R>::type *)contrib, (typename V4t<R>::type *)selfF, mask,
                                          partial, rs, eatom);
   return cudaGetLastError();
 }
 
 template <class M, int MAXNC>
-static cudaError_t launch_gen(cudaStream_t st, int eflag, int vflag, int N, const dbl4 *x, const int4 *q,
+static cudaError_t launch_gen(cudaStream_t st, int eflag, int vflag, int N, int ld, const dbl4 *x, const int4 *q,
                               const int *nbr, const int *cnt, const SysTab *sys, const void *pairs, const void *trips,
                               int nt, void *contrib, void *selfF, unsigned long long *mask, double *partial,
                               RunState *rs, double *eatom)
 {
   if (vflag)
-    return launch_gen_t<M, MAXNC, true, true>(st, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib, selfF, mask,
+    return launch_gen_t<M, MAXNC, true, true>(st, N, ld, x, q, nbr, cnt, sys, pairs, trips, nt, contrib, selfF, mask,
                                               partial, rs, eatom);
   if (eflag)
-    return launch_gen_t<M, MAXNC, true, false>(st, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib, selfF, mask,
+    return launch_gen_t<M, MAXNC, true, false>(st, N, ld, x, q, nbr, cnt, sys, pairs, trips, nt, contrib, selfF, mask,
                                                partial, rs, eatom);
-  return launch_gen_t<M, MAXNC, false, false>(st, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib, selfF, mask,
+  return launch_gen_t<M, MAXNC, false, false>(st, N, ld, x, q, nbr, cnt, sys, pairs, trips, nt, contrib, selfF, mask,
                                               partial, rs, eatom);
 }
 
@@ -1450,14 +1460,14 @@ static int gen_threads(int slots)
 }
 
 template <class M>
-static cudaError_t launch_gen_any(cudaStream_t st, int slots, int eflag, int vflag, int N, const dbl4 *x,
+static cudaError_t launch_gen_any(cudaStream_t st, int slots, int eflag, int vflag, int N, int ld, const dbl4 *x,
                                   const int4 *q, const int *nbr, const int *cnt, const SysTab *sys, const void *pairs,
                                   const void *trips, int nt, void *contrib, void *selfF, unsigned long long *mask,
                                   double *partial, RunState *rs, double *eatom)
 {
 #define TSF_GEN(NC)                                                                                                \
   case NC:                                                                                                         \
-    return launch_gen<M, NC>(st, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib, selfF, mask,     \
+    return launch_gen<M, NC>(st, eflag, vflag, N, ld, x, q, nbr, cnt, sys, pairs, trips, nt, contrib, selfF, mask,     \
                              partial, rs, eatom);
   switch (slots) {
     TSF_GEN(8)
@@ -1471,7 +1481,7 @@ static cudaError_t launch_gen_any(cudaStream_t st, int slots, int eflag, int vfl
 
 // the warp kernel over the register kernel's overflow queues (GEN_BLOCKS blocks)
 template <class M>
-static cudaError_t launch_warp(cudaStream_t st, int eflag, int vflag, int N, const dbl4 *x, const int4 *q,
+static cudaError_t launch_warp(cudaStream_t st, int eflag, int vflag, int ld, const dbl4 *x, const int4 *q,
                                const int *nbr, const int *cnt, const SysTab *sys, const void *pairs, const void *trips,
                                int nt, void *contrib, void *selfF, unsigned long long *mask, const int *work,
                                const int *nwork, int nfast, double *partial, RunState *rs, double *eatom)
@@ -1481,15 +1491,15 @@ static cudaError_t launch_warp(cudaStream_t st, int eflag, int vflag, int N, con
   using Tt = const TripP<R> *;
   using V = typename V4t<R>::type *;
   if (vflag)
-    k_force_warp<M, true, true><<<GEN_BLOCKS, WARP_BLOCK, 0, st>>>(N, x, q, nbr, cnt, sys, (P)pairs, (Tt)trips, nt,
+    k_force_warp<M, true, true><<<GEN_BLOCKS, WARP_BLOCK, 0, st>>>(ld, x, q, nbr, cnt, sys, (P)pairs, (Tt)trips, nt,
                                                                    (V)contrib, (V)selfF, mask, work, nwork, nfast,
                                                                    partial, rs, eatom);
   else if (eflag)
-    k_force_warp<M, true, false><<<GEN_BLOCKS, WARP_BLOCK, 0, st>>>(N, x, q, nbr, cnt, sys, (P)pairs, (Tt)trips, nt,
+    k_force_warp<M, true, false><<<GEN_BLOCKS, WARP_BLOCK, 0, st>>>(ld, x, q, nbr, cnt, sys, (P)pairs, (Tt)trips, nt,
                                                                     (V)contrib, (V)selfF, mask, work, nwork, nfast,
                                                                     partial, rs, eatom);
   else
-    k_force_warp<M, false, false><<<GEN_BLOCKS, WARP_BLOCK, 0, st>>>(N, x, q, nbr, cnt, sys, (P)pairs, (Tt)trips, nt,
+    k_force_warp<M, false, false><<<GEN_BLOCKS, WARP_BLOCK, 0, st>>>(ld, x, q, nbr, cnt, sys, (P)pairs, (Tt)trips, nt,
                                                                      (V)contrib, (V)selfF, mask, work, nwork, nfast,
                                                                      partial, rs, eatom);
   return cudaGetLastError();
@@ -1504,7 +1514,7 @@ inline const KParams<R> &kparams_of(const FastTab &ft)
 }
 
 template <class M, int MAXNC, int KIND>
-static cudaError_t launch_reg(cudaStream_t st, int eflag, int vflag, int N, const dbl4 *x, const int4 *q,
+static cudaError_t launch_reg(cudaStream_t st, int eflag, int vflag, int ld, const dbl4 *x, const int4 *q,
                               const int *nbr, const int *cnt, const SysTab *sys, const void *pairs, const void *trips,
                               int nt, const FastTab &ft, void *contrib, void *selfF, unsigned long long *mask,
                               int *work, int *nwork, double *partial, RunState *rs, double *eatom,
@@ -1517,18 +1527,29 @@ static cudaError_t launch_reg(cudaStream_t st, int eflag, int vflag, int N, cons
   using Tt = const TripP<R> *;
   using V = typename V4t<R>::type *;
   const KParams<R> &kp = kparams_of<R>(ft);
+  // one resident wave of blocks (SMs x resident blocks x threads) of the launched form
+  auto wave = [](auto kern) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, FAST_THREADS, 0);
+    return sms * per * FAST_THREADS;
+  };
+  static const int pf_v = wave(k_force_reg<M, MAXNC, KIND, true, true>);
+  static const int pf_e = wave(k_force_reg<M, MAXNC, KIND, true, false>);
+  static const int pf_0 = wave(k_force_reg<M, MAXNC, KIND, false, false>);
   if (vflag)
     k_force_reg<M, MAXNC, KIND, true, true><<<blocks, FAST_THREADS, 0, st>>>(
-        N, x, q, nbr, cnt, sys, (P)pairs, (Tt)trips, nt, kp, (V)contrib, (V)selfF, mask, work, nwork, partial, rs,
-        eatom, rt.order, rt.begin, rt.count, rt.block_base, stats);
+        ld, x, q, nbr, cnt, sys, (P)pairs, (Tt)trips, nt, kp, (V)contrib, (V)selfF, mask, work, nwork, partial, rs,
+        eatom, rt.order, rt.begin, rt.count, rt.block_base, stats, pf_v);
   else if (eflag)
     k_force_reg<M, MAXNC, KIND, true, false><<<blocks, FAST_THREADS, 0, st>>>(
-        N, x, q, nbr, cnt, sys, (P)pairs, (Tt)trips, nt, kp, (V)contrib, (V)selfF, mask, work, nwork, partial, rs,
-        eatom, rt.order, rt.begin, rt.count, rt.block_base, stats);
+        ld, x, q, nbr, cnt, sys, (P)pairs, (Tt)trips, nt, kp, (V)contrib, (V)selfF, mask, work, nwork, partial, rs,
+        eatom, rt.order, rt.begin, rt.count, rt.block_base, stats, pf_e);
   else
     k_force_reg<M, MAXNC, KIND, false, false><<<blocks, FAST_THREADS, 0, st>>>(
-        N, x, q, nbr, cnt, sys, (P)pairs, (Tt)trips, nt, kp, (V)contrib, (V)selfF, mask, work, nwork, partial, rs,
-        eatom, rt.order, rt.begin, rt.count, rt.block_base, stats);
+        ld, x, q, nbr, cnt, sys, (P)pairs, (Tt)trips, nt, kp, (V)contrib, (V)selfF, mask, work, nwork, partial, rs,
+        eatom, rt.order, rt.begin, rt.count, rt.block_base, stats, pf_0);
   return cudaGetLastError();
 }
 
@@ -1537,7 +1558,7 @@ static cudaError_t launch_reg(cudaStream_t st, int eflag, int vflag, int N, cons
 // the partial-sum rows the launched kernels write (0: none launched).
 template <class M>
 cudaError_t launch_force_m(int part, cudaStream_t st, int fast_slots, const FastTab &ft, int gen_slots, int eflag,
-                           int vflag, int N, const dbl4 *x, const int4 *q, const int *nbr, const int *cnt,
+                           int vflag, int N, int ld, const dbl4 *x, const int4 *q, const int *nbr, const int *cnt,
                            const SysTab *sys, const void *pairs, const void *trips, int nt, void *contrib,
                            void *selfF, unsigned long long *mask, int *work, int *nwork, double *partial, RunState *rs,
                            double *eatom, const ForceRoutes *routes, int stats, int *rows)
@@ -1556,7 +1577,7 @@ cudaError_t launch_force_m(int part, cudaStream_t st, int fast_slots, const Fast
       nfast += (rt.count + FAST_THREADS - 1) / FAST_THREADS;
       if (!(part & 1)) continue;
 #define TSF_REG_K(NC, K)                                                                                          \
-  launch_reg<M, NC, K>(st, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt, ft, contrib, selfF, mask, work, \
+  launch_reg<M, NC, K>(st, eflag, vflag, ld, x, q, nbr, cnt, sys, pairs, trips, nt, ft, contrib, selfF, mask, work, \
                        nwork, partial, rs, eatom, rt, stats)
 #define TSF_REG(NC) \
   e = ft.kind == 1 ? TSF_REG_K(NC, 1) : ft.kind == 2 ? TSF_REG_K(NC, 2) : TSF_REG_K(NC, 0);
@@ -1567,12 +1588,12 @@ cudaError_t launch_force_m(int part, cudaStream_t st, int fast_slots, const Fast
     }
     if (!(part & 2)) return cudaSuccess;
     double *gp = partial + (size_t)nfast * 8;
-    e = launch_warp<M>(st, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib, selfF, mask, work, nwork,
+    e = launch_warp<M>(st, eflag, vflag, ld, x, q, nbr, cnt, sys, pairs, trips, nt, contrib, selfF, mask, work, nwork,
                        nfast, gp, rs, eatom);
     if (e == cudaSuccess) *rows = nfast + GEN_BLOCKS;
   } else {
     if (!(part & 2)) return cudaSuccess;
-    e = launch_gen_any<M>(st, gen_slots, eflag, vflag, N, x, q, nbr, cnt, sys, pairs, trips, nt, contrib, selfF, mask,
+    e = launch_gen_any<M>(st, gen_slots, eflag, vflag, N, ld, x, q, nbr, cnt, sys, pairs, trips, nt, contrib, selfF, mask,
                           partial, rs, eatom);
     const int T = gen_threads<R>(gen_slots);
     if (e == cudaSuccess) *rows = (N + T - 1) / T;

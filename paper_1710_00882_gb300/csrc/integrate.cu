@@ -109,7 +109,7 @@ struct AccFP64 {
 };
 
 template <class A>
-__device__ __forceinline__ void gather_force(int m, int N, const typename A::V *__restrict__ contrib,
+__device__ __forceinline__ void gather_force(int m, int ld, const typename A::V *__restrict__ contrib,
                                              const typename A::V *__restrict__ selfF,
                                              const unsigned long long *__restrict__ mask, const int *__restrict__ rev,
                                              double &fx, double &fy, double &fz)
@@ -123,7 +123,7 @@ __device__ __forceinline__ void gather_force(int m, int N, const typename A::V *
   // is two dependent loads deep instead of three.
   unsigned g0[U];
 #pragma unroll
-  for (int u = 0; u < U; ++u) g0[u] = (unsigned)rev[(size_t)u * N + m];
+  for (int u = 0; u < U; ++u) g0[u] = (unsigned)rev[(size_t)u * ld + m];
   const V self = selfF[m];
   unsigned long long mb = mask[m];
   acc.init(self);
@@ -145,7 +145,7 @@ __device__ __forceinline__ void gather_force(int m, int N, const typename A::V *
       }
       unsigned g[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) g[u] = sl[u] >= 0 ? (unsigned)rev[(size_t)sl[u] * N + m] : 0u;
+      for (int u = 0; u < U; ++u) g[u] = sl[u] >= 0 ? (unsigned)rev[(size_t)sl[u] * ld + m] : 0u;
       V c[U];
 #pragma unroll
       for (int u = 0; u < U; ++u)
@@ -230,7 +230,7 @@ constexpr int VV_THREADS = 128;   // integrator block size (more resident blocks
 //           some atom moved more than skin/2 since the last build
 // KE: accumulate sum m v^2 of the full-step velocity (after FINISH, before START).
 template <class A, bool KE>
-__global__ void __launch_bounds__(VV_THREADS, sizeof(typename A::V) == 16 ? 12 : 1) k_vv(int N, int mode, dbl4 *__restrict__ x, dbl4 *__restrict__ v, int4 *__restrict__ q,
+__global__ void __launch_bounds__(VV_THREADS, sizeof(typename A::V) == 16 ? 12 : 1) k_vv(int N, int ld, int mode, dbl4 *__restrict__ x, dbl4 *__restrict__ v, int4 *__restrict__ q,
                      const int4 *__restrict__ qref, const typename A::V *__restrict__ contrib,
                      const typename A::V *__restrict__ selfF, const unsigned long long *__restrict__ mask,
                      const int *__restrict__ rev, const SysTab *__restrict__ sys, SysCtl *__restrict__ ctl,
@@ -258,9 +258,11 @@ __global__ void __launch_bounds__(VV_THREADS, sizeof(typename A::V) == 16 ? 12 :
       const SysCtl C = ctl[sid];
       mode_i = C.steps_left > 0 ? (C.open ? (VV_FINISH | VV_START) : VV_START) : (C.open ? VV_FINISH : 0);
     }
-    double fx, fy, fz;
-    gather_force<A>(i, N, contrib, selfF, mask, rev, fx, fy, fz);
-    dbl4 vi = v[i];
+    // a system that neither kicks nor drifts in this step (finished, or a freed range
+    // of a packed layout) needs no forces
+    double fx = 0.0, fy = 0.0, fz = 0.0;
+    if (mode_i != 0) gather_force<A>(i, ld, contrib, selfF, mask, rev, fx, fy, fz);
+    dbl4 vi = (mode_i != 0 || KE) ? v[i] : make_dbl4(0.0, 0.0, 0.0, 0.0);
     if (mode_i & VV_FINISH) {
       vi.x = fma(c, fx, vi.x);
       vi.y = fma(c, fy, vi.y);
@@ -285,7 +287,7 @@ __global__ void __launch_bounds__(VV_THREADS, sizeof(typename A::V) == 16 ? 12 :
       moved = dx * dx + dy * dy + dz * dz > disp2_lim;
       if (moved && ctl[sid].rebuild == 0) atomicOr(&ctl[sid].rebuild, 1);
     }
-    v[i] = vi;
+    if (mode_i != 0) v[i] = vi;
   }
   if (__any_sync(0xffffffffu, moved) && (threadIdx.x & 31) == 0) atomicOr(&rs->rebuild, 1);
   if (KE) {
@@ -441,21 +443,21 @@ __global__ void k_force_done(RunState *rs)
 }
 
 template <class A>
-static void launch_vv_a(cudaStream_t st, bool ke, int B, int N, int mode, dbl4 *x, dbl4 *v, int4 *q, const int4 *qref,
+static void launch_vv_a(cudaStream_t st, bool ke, int B, int N, int ld, int mode, dbl4 *x, dbl4 *v, int4 *q, const int4 *qref,
                         const void *contrib, const void *selfF, const unsigned long long *mask, const int *rev,
                         const SysTab *sys, SysCtl *ctl, const double *mass, float disp2_lim, double *kepart,
                         RunState *rs)
 {
   using V = const typename A::V *;
   if (ke)
-    k_vv<A, true><<<B, VV_THREADS, 0, st>>>(N, mode, x, v, q, qref, (V)contrib, (V)selfF, mask, rev, sys, ctl, mass,
+    k_vv<A, true><<<B, VV_THREADS, 0, st>>>(N, ld, mode, x, v, q, qref, (V)contrib, (V)selfF, mask, rev, sys, ctl, mass,
                                             disp2_lim, kepart, rs);
   else
-    k_vv<A, false><<<B, VV_THREADS, 0, st>>>(N, mode, x, v, q, qref, (V)contrib, (V)selfF, mask, rev, sys, ctl, mass,
+    k_vv<A, false><<<B, VV_THREADS, 0, st>>>(N, ld, mode, x, v, q, qref, (V)contrib, (V)selfF, mask, rev, sys, ctl, mass,
                                              disp2_lim, kepart, rs);
 }
 
-cudaError_t launch_vv(cudaStream_t st, int prec, bool ke, int N, int mode, dbl4 *x, dbl4 *v, int4 *q,
+cudaError_t launch_vv(cudaStream_t st, int prec, bool ke, int N, int ld, int mode, dbl4 *x, dbl4 *v, int4 *q,
                       const int4 *qref, const void *contrib, const void *selfF, const unsigned long long *mask,
                       const int *rev, const SysTab *sys, SysCtl *ctl, const double *mass, float disp2_lim,
                       double *kepart, RunState *rs)
@@ -466,7 +468,7 @@ cudaError_t launch_vv(cudaStream_t st, int prec, bool ke, int N, int mode, dbl4 
            : prec == PREC_MIXED        ? launch_vv_a<AccMixed>
            : prec == PREC_MIXED_ACC64  ? launch_vv_a<AccMixed64>
                                        : launch_vv_a<AccSingle>;
-  f(st, ke, B, N, mode, x, v, q, qref, contrib, selfF, mask, rev, sys, ctl, mass, disp2_lim, kepart, rs);
+  f(st, ke, B, N, ld, mode, x, v, q, qref, contrib, selfF, mask, rev, sys, ctl, mass, disp2_lim, kepart, rs);
   if (ke) k_ke_reduce<<<1, 256, 0, st>>>(kepart, B, rs);
   return cudaGetLastError();
 }

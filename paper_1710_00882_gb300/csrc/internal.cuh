@@ -120,6 +120,9 @@ struct ForceRoutes {
   ForceRoute r[2];
 };
 
+// Ask L2 for the line holding p (no register result, no wait).
+__device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 // minimum-image difference of two fixed-point coordinates, in units of L / 2^32
 __host__ __device__ __forceinline__ int qdiff(int qj, int qi)
 {

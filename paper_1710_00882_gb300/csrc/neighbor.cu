@@ -6,7 +6,8 @@
 //
 // Build sequence (all launches are skipped on the device unless rs->rebuild is
 // set, so an MD step can enqueue them unconditionally):
-//   k_cell_count  -> cell of each atom, rank inside its cell (atomic)
+//   k_cell_count  -> cell of each atom of a system that gets new lists, rank inside
+//                    its cell (atomic)
 //   k_scan_*      -> exclusive scan of the cell counts (three-phase block scan)
 //   k_cell_fill   -> atoms in cell order
 //   k_build       -> per atom: half stencil, each pair within its type pair's list
@@ -37,9 +38,15 @@ __global__ void k_cell_count(int N, const int4 *__restrict__ q, const SysTab *__
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   int4 p = q[i];
-  // list counts of the atoms that get new lists start at zero (pairs are appended)
-  if (!ctl || ctl[sys_of(p.w)].rebuild) cnt[i] = 0;
   const SysTab &T = sys[sys_of(p.w)];
+  // only the systems that get new lists take cells (atoms of a freed range of a
+  // packed layout, a system without atoms, never do); their list counts start at
+  // zero (pairs are appended)
+  if (T.natoms == 0 || (ctl && ctl[sys_of(p.w)].rebuild == 0)) {
+    cell_of[i] = -1;
+    return;
+  }
+  cnt[i] = 0;
   int cx = cell_coord((uint32_t)p.x, T.nc[0]);
   int cy = cell_coord((uint32_t)p.y, T.nc[1]);
   int cz = cell_coord((uint32_t)p.z, T.nc[2]);
@@ -149,8 +156,10 @@ __global__ void k_cell_fill(int N, const int4 *__restrict__ q, const int *__rest
   if (skip_build(rs, gated)) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
+  const int c = cell_of[i];
+  if (c < 0) return;
   const int4 p = q[i];
-  cell_atoms[cell_start[cell_of[i]] + rank[i]] = make_int4(p.x, p.y, p.z, i | (type_of(p.w) << CELL_IDX_BITS));
+  cell_atoms[cell_start[c] + rank[i]] = make_int4(p.x, p.y, p.z, i | (type_of(p.w) << CELL_IDX_BITS));
 }
 
 // Stencil range along one axis: 3 neighbouring cells, or every cell when the axis
@@ -181,19 +190,6 @@ __device__ __forceinline__ void bitonic(int (&v)[W])
   else if constexpr (K < W) bitonic<W, 2 * K, K>(v);
 }
 
-// Sort the first n (<= W) entries of atom i's column in registers (padding with INT_MAX).
-template <int W>
-__device__ __forceinline__ void sort_column(int *__restrict__ nbr, int N, int i, int n)
-{
-  int v[W];
-#pragma unroll
-  for (int s = 0; s < W; ++s) v[s] = (s < n) ? nbr[(size_t)s * N + i] : 0x7fffffff;
-  bitonic<W, 2, 1>(v);
-#pragma unroll
-  for (int s = 0; s < W; ++s)
-    if (s < n) nbr[(size_t)s * N + i] = v[s];
-}
-
 // List counts during a build: the low 16 bits count the entries an atom found itself
 // ("forward", written from slot 0 up by its own thread), the high 16 bits the entries
 // other atoms appended to it ("backward", written from slot cap - 1 down, slot from
@@ -202,13 +198,13 @@ constexpr int BACK = 1 << 16;
 
 // Append the pair (i, j) found by i: j goes to i's forward range (no atomic), i to
 // j's backward range.
-__device__ __forceinline__ void add_pair(int i, int j, int N, int cap, int *__restrict__ nbr, int *__restrict__ cnt,
+__device__ __forceinline__ void add_pair(int i, int j, int ld, int cap, int *__restrict__ nbr, int *__restrict__ cnt,
                                          int &nf)
 {
-  if (nf < cap) nbr[(size_t)nf * N + i] = j;
+  if (nf < cap) nbr[(size_t)nf * ld + i] = j;
   ++nf;
   const int b = atomicAdd(&cnt[j], BACK) >> 16;
-  if (b < cap) nbr[(size_t)(cap - 1 - b) * N + j] = i;
+  if (b < cap) nbr[(size_t)(cap - 1 - b) * ld + j] = i;
 }
 
 // One thread per atom, atoms taken in cell order (threads of a warp share most of
@@ -220,7 +216,7 @@ __device__ __forceinline__ void add_pair(int i, int j, int N, int cap, int *__re
 // and keeps j > i.  Candidates of one stencil row are one run of cell_atoms (two
 // where the row wraps).
 template <bool TYPED>
-__global__ void __launch_bounds__(128, 12) k_build(int N, const int4 *__restrict__ q, const SysTab *__restrict__ sys,
+__global__ void __launch_bounds__(128, 12) k_build(int ld, int ncell, const int4 *__restrict__ q, const SysTab *__restrict__ sys,
                                                const SysCtl *__restrict__ ctl,
                                                const __grid_constant__ PairRadii radii,
                                                const int *__restrict__ cell_start,
@@ -230,7 +226,7 @@ __global__ void __launch_bounds__(128, 12) k_build(int N, const int4 *__restrict
 {
   if (skip_build(rs, gated)) return;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= N) return;
+  if (t >= cell_start[ncell]) return;   // atoms with a cell (systems that get new lists)
   const int i = cell_atoms[t].w & CELL_IDX_MASK;
   const int4 pi = q[i];
   // Most candidates fail the largest radius of i's row; only the others decode j's
@@ -265,7 +261,7 @@ __global__ void __launch_bounds__(128, 12) k_build(int N, const int4 *__restrict
         const float dz = q_scaled(qdiff(pj[k].z, pi.z), s2);
         const float r2 = r2_decide(dx, dy, dz);
         if (j > i && r2 < lmax && (!TYPED || r2 < limit((int)((unsigned)pj[k].w >> CELL_IDX_BITS))))
-          add_pair(i, j, N, cap, nbr, cnt, nf);
+          add_pair(i, j, ld, cap, nbr, cnt, nf);
       }
     }
   };
@@ -304,7 +300,7 @@ __global__ void __launch_bounds__(128, 12) k_build(int N, const int4 *__restrict
           const float dz = q_scaled(qdiff(pj[k].z, pi.z), s2);
           const float r2 = r2_decide(dx, dy, dz);
           if (pj[k].w != -1 && r2 < lmax && (!TYPED || r2 < limit((int)((unsigned)pj[k].w >> CELL_IDX_BITS))))
-            add_pair(i, pj[k].w & CELL_IDX_MASK, N, cap, nbr, cnt, nf);
+            add_pair(i, pj[k].w & CELL_IDX_MASK, ld, cap, nbr, cnt, nf);
         }
       }
     };
@@ -337,14 +333,15 @@ __global__ void __launch_bounds__(128, 12) k_build(int N, const int4 *__restrict
 
 // Sort each rebuilt list by neighbour index, so that the list order depends only on
 // the set of neighbours; flag lists longer than the capacity.
-__global__ void __launch_bounds__(128) k_sort_lists(int N, const int4 *__restrict__ q, const SysCtl *__restrict__ ctl,
+__global__ void __launch_bounds__(128) k_sort_lists(int N, int ld, const int4 *__restrict__ q,
+                                                    const SysCtl *__restrict__ ctl, const int *__restrict__ cell_of,
                                                     int *__restrict__ nbr, int *__restrict__ cnt, int cap,
                                                     RunState *rs, int gated)
 {
   __shared__ int sbuf[32][128];
   if (skip_build(rs, gated)) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
+  if (i >= N || cell_of[i] < 0) return;
   if (ctl && ctl[sys_of(q[i].w)].rebuild == 0) return;
   const int c = cnt[i];
   const int nf = c & (BACK - 1), nb = c >> 16, n = nf + nb;
@@ -355,7 +352,7 @@ __global__ void __launch_bounds__(128) k_sort_lists(int N, const int4 *__restric
   }
   cnt[i] = n;
   // entry s of the list: forward entries first, then the backward ones
-  auto entry = [&](int s) -> size_t { return (size_t)(s < nf ? s : cap - nb + (s - nf)) * N + i; };
+  auto entry = [&](int s) -> size_t { return (size_t)(s < nf ? s : cap - nb + (s - nf)) * ld + i; };
   if (n <= 16) {
     int v[16];
 #pragma unroll
@@ -367,12 +364,12 @@ __global__ void __launch_bounds__(128) k_sort_lists(int N, const int4 *__restric
       bitonic<8, 2, 1>(w);
 #pragma unroll
       for (int s = 0; s < 8; ++s)
-        if (s < n) nbr[(size_t)s * N + i] = w[s];
+        if (s < n) nbr[(size_t)s * ld + i] = w[s];
     } else {
       bitonic<16, 2, 1>(v);
 #pragma unroll
       for (int s = 0; s < 16; ++s)
-        if (s < n) nbr[(size_t)s * N + i] = v[s];
+        if (s < n) nbr[(size_t)s * ld + i] = v[s];
     }
   } else if (n <= 32) {
     // insertion sort in this thread's shared-memory column (stride 128: no bank conflicts)
@@ -385,41 +382,41 @@ __global__ void __launch_bounds__(128) k_sort_lists(int N, const int4 *__restric
       }
       sbuf[k + 1][threadIdx.x] = v;
     }
-    for (int s1 = 0; s1 < n; ++s1) nbr[(size_t)s1 * N + i] = sbuf[s1][threadIdx.x];
+    for (int s1 = 0; s1 < n; ++s1) nbr[(size_t)s1 * ld + i] = sbuf[s1][threadIdx.x];
   } else {
     // move the backward entries down behind the forward ones (cap - nb >= nf), then
     // insertion sort in place
-    for (int k = 0; k < nb; ++k) nbr[(size_t)(nf + k) * N + i] = nbr[(size_t)(cap - nb + k) * N + i];
+    for (int k = 0; k < nb; ++k) nbr[(size_t)(nf + k) * ld + i] = nbr[(size_t)(cap - nb + k) * ld + i];
     for (int s1 = 1; s1 < n; ++s1) {
-      const int v = nbr[(size_t)s1 * N + i];
+      const int v = nbr[(size_t)s1 * ld + i];
       int k = s1 - 1;
       while (k >= 0) {
-        const int w = nbr[(size_t)k * N + i];
+        const int w = nbr[(size_t)k * ld + i];
         if (w <= v) break;
-        nbr[(size_t)(k + 1) * N + i] = w;
+        nbr[(size_t)(k + 1) * ld + i] = w;
         --k;
       }
-      nbr[(size_t)(k + 1) * N + i] = v;
+      nbr[(size_t)(k + 1) * ld + i] = v;
     }
   }
 }
 
 // rev[s][i] = where the force gather finds the contribution of the terms of i's
-// neighbour j = nbr[s][i] on i: the flat index s2 * N + j of i's slot s2 in j's
-// (sorted) list, found by binary search (a 32-bit unsigned value: cap * N < 2^32).
+// neighbour j = nbr[s][i] on i: the flat index s2 * ld + j of i's slot s2 in j's
+// (sorted) list, found by binary search (a 32-bit unsigned value: cap * ld < 2^32).
 // Lists are symmetric, so one search serves both entries of a pair: atom i takes the
 // entries with j > i (the tail of its sorted list), finds s2, and writes rev[s][i]
 // and rev[s2][j]; every entry has exactly one writer.  One thread per atom; the
 // searches of up to RS slots run interleaved, level by level, so their loads are in
 // flight together.
 constexpr int RS = 8;
-__global__ void k_reverse(int N, const int4 *__restrict__ q, const SysCtl *__restrict__ ctl,
-                          const int *__restrict__ nbr, const int *__restrict__ cnt, int *__restrict__ rev, RunState *rs,
-                          int gated)
+__global__ void k_reverse(int N, int ld, const int4 *__restrict__ q, const SysCtl *__restrict__ ctl,
+                          const int *__restrict__ cell_of, const int *__restrict__ nbr, const int *__restrict__ cnt,
+                          int *__restrict__ rev, RunState *rs, int gated)
 {
   if (skip_build(rs, gated)) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
+  if (i >= N || cell_of[i] < 0) return;
   if (ctl && ctl[sys_of(q[i].w)].rebuild == 0) return;
   const int n = cnt[i];
   // the entries with j > i start at the first index above i (lists are sorted); their
@@ -429,7 +426,7 @@ __global__ void k_reverse(int N, const int4 *__restrict__ q, const SysCtl *__res
     int lo = 0, hi = n;
     while (lo < hi) {
       const int mid = (lo + hi) >> 1;
-      if (nbr[(size_t)mid * N + i] > i) hi = mid; else lo = mid + 1;
+      if (nbr[(size_t)mid * ld + i] > i) hi = mid; else lo = mid + 1;
     }
     first = lo;
   }
@@ -437,7 +434,7 @@ __global__ void k_reverse(int N, const int4 *__restrict__ q, const SysCtl *__res
   for (int s0 = first; s0 < n; s0 += RS) {
     int j[RS], lo[RS], hi[RS], found[RS];
 #pragma unroll
-    for (int k = 0; k < RS; ++k) j[k] = s0 + k < n ? nbr[(size_t)(s0 + k) * N + i] : -1;
+    for (int k = 0; k < RS; ++k) j[k] = s0 + k < n ? nbr[(size_t)(s0 + k) * ld + i] : -1;
 #pragma unroll
     for (int k = 0; k < RS; ++k) {
       lo[k] = 0;
@@ -451,7 +448,7 @@ __global__ void k_reverse(int N, const int4 *__restrict__ q, const SysCtl *__res
       for (int k = 0; k < RS; ++k) {
         if (found[k] < 0 && lo[k] <= hi[k]) {
           const int mid = (lo[k] + hi[k]) >> 1;
-          const int v = nbr[(size_t)mid * N + j[k]];
+          const int v = nbr[(size_t)mid * ld + j[k]];
           if (v == i) found[k] = mid;
           else if (v < i) lo[k] = mid + 1;
           else hi[k] = mid - 1;
@@ -464,11 +461,11 @@ __global__ void k_reverse(int N, const int4 *__restrict__ q, const SysCtl *__res
       if (j[k] < 0) continue;
       if (found[k] < 0) {
         missing = true;
-        rev[(size_t)(s0 + k) * N + i] = (int)(unsigned)j[k];
+        rev[(size_t)(s0 + k) * ld + i] = (int)(unsigned)j[k];
         continue;
       }
-      rev[(size_t)(s0 + k) * N + i] = (int)((unsigned)found[k] * (unsigned)N + (unsigned)j[k]);
-      rev[(size_t)found[k] * N + j[k]] = (int)((unsigned)(s0 + k) * (unsigned)N + (unsigned)i);
+      rev[(size_t)(s0 + k) * ld + i] = (int)((unsigned)found[k] * (unsigned)ld + (unsigned)j[k]);
+      rev[(size_t)found[k] * ld + j[k]] = (int)((unsigned)(s0 + k) * (unsigned)ld + (unsigned)i);
     }
   }
   if (missing) atomicOr(&rs->status, ST_REV_MISSING);
@@ -487,11 +484,12 @@ __global__ void k_build_done(RunState *rs, int gated)
 namespace tsf {
 
 // Enqueue one list build on st (ctl non-null: only the systems whose rebuild flag is
-// set get new lists; null: every atom).  N <= MAX_LIST_ATOMS; radii: list radius
-// per type pair.  Buffers: cell_count[ncell] (zero on entry, zero
-// on exit), cell_start[ncell+1], tile_sums[ceil(ncell/SCAN_TILE)], cell_atoms[N] (int4),
-// cell_of[N], rank[N]; list nbr/rev [cap][N], cnt[N]; qref[N].
-cudaError_t launch_build(cudaStream_t st, int N, const int4 *q, const SysTab *sys, const SysCtl *ctl, int ncell,
+// set get new lists; null: every atom).  N <= MAX_LIST_ATOMS atoms; atoms of a
+// system without atoms (freed ranges of a packed layout) are left out.  ld >= N:
+// the list stride.  radii: list radius per type pair.  Buffers: cell_count[ncell]
+// (zero on entry, zero on exit), cell_start[ncell+1], tile_sums[ceil(ncell/SCAN_TILE)],
+// cell_atoms[N] (int4), cell_of[N], rank[N]; list nbr/rev [cap][ld], cnt[N]; qref[N].
+cudaError_t launch_build(cudaStream_t st, int N, int ld, const int4 *q, const SysTab *sys, const SysCtl *ctl, int ncell,
                          const PairRadii &radii,
                          int *cell_count, int *cell_start, int *tile_sums, int4 *cell_atoms, int *cell_of, int *rank,
                          int *nbr, int *rev, int *cnt, int cap, int4 *qref, RunState *rs, int gated)
@@ -511,11 +509,11 @@ cudaError_t launch_build(cudaStream_t st, int N, const int4 *q, const SysTab *sy
   bool typed = false;
   for (int k = 1; k < MAX_TYPES * MAX_TYPES; ++k) typed = typed || radii.rl2[k] != radii.rl2[0];
   if (typed)
-    k_build<true><<<BN128, 128, 0, st>>>(N, q, sys, ctl, radii, cell_start, cell_atoms, nbr, cnt, cap, qref, rs, gated);
+    k_build<true><<<BN128, 128, 0, st>>>(ld, ncell, q, sys, ctl, radii, cell_start, cell_atoms, nbr, cnt, cap, qref, rs, gated);
   else
-    k_build<false><<<BN128, 128, 0, st>>>(N, q, sys, ctl, radii, cell_start, cell_atoms, nbr, cnt, cap, qref, rs, gated);
-  k_sort_lists<<<BN128, 128, 0, st>>>(N, q, ctl, nbr, cnt, cap, rs, gated);
-  k_reverse<<<BN128, 128, 0, st>>>(N, q, ctl, nbr, cnt, rev, rs, gated);
+    k_build<false><<<BN128, 128, 0, st>>>(ld, ncell, q, sys, ctl, radii, cell_start, cell_atoms, nbr, cnt, cap, qref, rs, gated);
+  k_sort_lists<<<BN128, 128, 0, st>>>(N, ld, q, ctl, cell_of, nbr, cnt, cap, rs, gated);
+  k_reverse<<<BN128, 128, 0, st>>>(N, ld, q, ctl, cell_of, nbr, cnt, rev, rs, gated);
   k_build_done<<<1, 1, 0, st>>>(rs, gated);
   return cudaGetLastError();
 }

@@ -185,7 +185,7 @@ extern "C" int tersoff_compute_noalloc(const tersoff_params *P, const double *po
   T.natoms = (int)N;
   NK(cudaMemcpyAsync(sys, &T, sizeof(SysTab), cudaMemcpyHostToDevice, st));
   NK(launch_ingest(st, (int)N, pos, types, P->nt, 0, sys, x, q, rs));
-  NK(launch_build(st, (int)N, q, sys, nullptr, g.ncell, g.radii, cell_count, cell_start, tile_sums, cell_atoms, cell_of, rank,
+  NK(launch_build(st, (int)N, (int)N, q, sys, nullptr, g.ncell, g.radii, cell_count, cell_start, tile_sums, cell_atoms, cell_of, rank,
                   nbr, rev, cnt, kCap, qref, rs, 0));
   const int fast_slots = P->sym_angular ? 8 : 0;
   NK(launch_force(st, prec, fast_slots, P->fast, force_slots_for(kCap), 1, 1, (int)N, x, q, nbr, cnt, sys,

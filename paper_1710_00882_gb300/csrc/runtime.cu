@@ -337,7 +337,7 @@ int build_list_sync(tersoff_ctx *ctx, const AtomState &A, ListState &L, RunState
   for (int attempt = 0; attempt < 3; ++attempt) {
     CKR(ensure_list(ctx, L, A.N, cap, g.ncell));
     CK(cudaMemsetAsync(&rs->maxcount, 0, sizeof(int), ctx->stream));
-    CK(launch_build(ctx->stream, (int)A.N, A.q, S.tab, nullptr, g.ncell, g.radii, L.cell_count, L.cell_start, L.tile_sums,
+    CK(launch_build(ctx->stream, (int)A.N, (int)A.N, A.q, S.tab, nullptr, g.ncell, g.radii, L.cell_count, L.cell_start, L.tile_sums,
                     L.cell_atoms, L.cell_of, L.rank, L.nbr, L.rev, L.cnt, cap, L.qref, rs, 0));
     RunState h;
     CKR(read_rs(ctx, rs, &h));
@@ -848,7 +848,8 @@ static int md_force(tersoff_md *md, cudaStream_t st, int eflag, int part = 3, in
 {
   tersoff_ctx *ctx = md->ctx;
   const tersoff_params *P = md->params;
-  CK(launch_force_part(part, st, md->prec, md->fast_slots, P->fast, md->gen_slots, eflag, 0, (int)md->atoms.N, md->atoms.x,
+  CK(launch_force_part(part, st, md->prec, md->fast_slots, P->fast, md->gen_slots, eflag, 0, (int)md->atoms.N,
+                       (int)md->atoms.N, md->atoms.x,
                   md->atoms.q, md->list.nbr, md->list.cnt, md->sys.tab, md->f32 ? P->pair_f : P->pair_d,
                   md->f32 ? P->trip_f : P->trip_d, P->nt, md->atoms.contrib, md->atoms.selfF, md->atoms.mask,
                   md->atoms.work, md->atoms.nwork, md->atoms.partial, md->rs, nullptr, md->routed ? &md->routes : nullptr, stats));
@@ -860,7 +861,7 @@ static int md_vv(tersoff_md *md, cudaStream_t st, int mode, bool ke)
 {
   tersoff_ctx *ctx = md->ctx;
   const float lim = (float)(0.25 * md->skin * md->skin);
-  CK(launch_vv(st, md->gprec, ke, (int)md->atoms.N, mode, md->atoms.x, md->atoms.v, md->atoms.q, md->list.qref,
+  CK(launch_vv(st, md->gprec, ke, (int)md->atoms.N, (int)md->atoms.N, mode, md->atoms.x, md->atoms.v, md->atoms.q, md->list.qref,
                md->atoms.contrib, md->atoms.selfF, md->atoms.mask, md->list.rev, md->sys.tab,
                md->sys.ctl, md->params->d_mass, lim, md->atoms.kepart, md->rs));
   return TERSOFF_OK;
@@ -872,7 +873,7 @@ static int md_build(tersoff_md *md, cudaStream_t st, int gated, bool full = fals
 {
   tersoff_ctx *ctx = md->ctx;
   ListState &L = md->list;
-  CK(launch_build(st, (int)md->atoms.N, md->atoms.q, md->sys.tab, full ? nullptr : md->sys.ctl, L.grid.ncell,
+  CK(launch_build(st, (int)md->atoms.N, (int)md->atoms.N, md->atoms.q, md->sys.tab, full ? nullptr : md->sys.ctl, L.grid.ncell,
                   L.grid.radii, L.cell_count, L.cell_start, L.tile_sums, L.cell_atoms, L.cell_of, L.rank, L.nbr, L.rev,
                   L.cnt, L.cap, L.qref, md->rs, gated));
   return TERSOFF_OK;

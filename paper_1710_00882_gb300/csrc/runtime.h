@@ -59,7 +59,7 @@ struct SysDev {
 namespace tsf {
 
 // launchers defined in the kernel translation units
-cudaError_t launch_build(cudaStream_t, int, const int4 *, const SysTab *, const SysCtl *, int, const PairRadii &, int *, int *,
+cudaError_t launch_build(cudaStream_t, int, int, const int4 *, const SysTab *, const SysCtl *, int, const PairRadii &, int *, int *,
                          int *, int4 *, int *, int *, int *, int *, int *, int, int4 *, RunState *, int);
 int scan_tiles_for(int ncell);
 int force_slots_for(int need);
@@ -68,12 +68,13 @@ int vv_blocks(int N);
 cudaError_t launch_force(cudaStream_t, int, int, const FastTab &, int, int, int, int, const dbl4 *, const int4 *, const int *,
                          const int *, const SysTab *, const void *, const void *, int, void *, void *,
                          unsigned long long *, int *, int *, double *, RunState *, double *);
-cudaError_t launch_force_part(int, cudaStream_t, int, int, const FastTab &, int, int, int, int, const dbl4 *, const int4 *,
+cudaError_t launch_force_part(int, cudaStream_t, int, int, const FastTab &, int, int, int, int, int, const dbl4 *,
+                              const int4 *,
                               const int *, const int *, const SysTab *, const void *, const void *, int, void *, void *,
                               unsigned long long *, int *, int *, double *, RunState *, double *,
                               const ForceRoutes *routes = nullptr, int stats = 1);
 int force_queue_blocks(int N);
-cudaError_t launch_vv(cudaStream_t, int, bool, int, int, dbl4 *, dbl4 *, int4 *, const int4 *, const void *,
+cudaError_t launch_vv(cudaStream_t, int, bool, int, int, int, dbl4 *, dbl4 *, int4 *, const int4 *, const void *,
                       const void *, const unsigned long long *, const int *, const SysTab *, SysCtl *,
                       const double *, float, double *, RunState *);
 cudaError_t launch_gather_out(cudaStream_t, int, int, const void *, const void *, const unsigned long long *,

@@ -9,8 +9,10 @@
 //   WHILE(chunk steps left) { vv -> decide -> IF(rebuild) { build } -> force -> step_end }
 // Jobs whose steps run out take their closing half kick in the next step and then
 // stay frozen until the chunk ends.  Between chunks the scheduler thread retires
-// finished jobs (results copied out), admits queued jobs that fit the slots and the
-// atom capacity implied by the device-memory budget, and repacks the layout.
+// finished jobs (results copied out, their atoms freed) and admits queued jobs that
+// fit the slots and the atom capacity implied by the device-memory budget: each new
+// job gets a free system slot and a free atom range, and only the new jobs' lists
+// and forces are computed (the layout section below).
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -43,20 +45,21 @@ __device__ __forceinline__ int range_of(const int *__restrict__ off, int n, int 
   return lo;
 }
 
-// Register-kernel routes of a layout: atom d of system k goes to position
-// route_off[k] + (d - dst_off[k]) of the route order.
-__global__ void k_route_order(int n, const int *__restrict__ dst_off, const int *__restrict__ route_off, int nsys,
+// Register-kernel route order of a set of systems: the systems' atoms back to back
+// (route_off ascending, route_off[k] the first position of system k, nsys systems),
+// position t holding atom atom_off[k] + (t - route_off[k]).
+__global__ void k_route_order(int n, const int *__restrict__ route_off, const int *__restrict__ atom_off, int nsys,
                               int *__restrict__ order)
 {
-  const int d = blockIdx.x * blockDim.x + threadIdx.x;
-  if (d >= n) return;
-  const int k = range_of(dst_off, nsys, d);
-  order[route_off[k] + (d - dst_off[k])] = d;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int k = range_of(route_off, nsys, t);
+  order[t] = atom_off[k] + (t - route_off[k]);
 }
 
-// Survivors of a repack: atom d of the new layout (systems 0..nsurv-1 come first)
-// is atom src_off[k] + (d - atom_off[k]) of the old layout; its word gets the new
-// system index.
+// Survivors of a compaction: atom d of the new layout (survivors come first, dst_off
+// ascending) is atom src_off[k] + (d - dst_off[k]) of the old one.  System indices
+// are slots and do not change, so the atom words are copied as they are.
 __global__ void k_move(int n, const dbl4 *__restrict__ sx, const dbl4 *__restrict__ sv, const int4 *__restrict__ sq,
                        dbl4 *__restrict__ dx, dbl4 *__restrict__ dv, int4 *__restrict__ dq,
                        const int *__restrict__ dst_off, const int *__restrict__ src_off, int nsurv)
@@ -65,27 +68,22 @@ __global__ void k_move(int n, const dbl4 *__restrict__ sx, const dbl4 *__restric
   if (d >= n) return;
   const int k = range_of(dst_off, nsurv, d);
   const int src = src_off[k] + (d - dst_off[k]);
-  dbl4 x = sx[src];
-  int4 q = sq[src];
-  const int w = make_w(type_of(q.w), k);
-  q.w = w;
-  x.w = __longlong_as_double((long long)w);
-  dx[d] = x;
-  dq[d] = q;
+  dx[d] = sx[src];
+  dq[d] = sq[src];
   dv[d] = sv[src];
 }
 
-// New jobs of a repack, staged back to back (pos [n][3], vel [n][3], types [n]):
-// staged atom t belongs to new job k (staging offsets st_off), system sys0 + k.
+// New jobs, staged back to back (pos [n][3], vel [n][3], types [n]): staged atom t
+// belongs to new job k (staging offsets st_off), system slot[k].
 __global__ void k_ingest_batch(int n, const double *__restrict__ pos, const double *__restrict__ vel,
-                               const int *__restrict__ types, const int *__restrict__ st_off, int nnew, int sys0,
-                               const SysTab *__restrict__ sys, int nt, dbl4 *__restrict__ x, dbl4 *__restrict__ v,
-                               int4 *__restrict__ q, RunState *rs)
+                               const int *__restrict__ types, const int *__restrict__ st_off, int nnew,
+                               const int *__restrict__ slot, const SysTab *__restrict__ sys, int nt,
+                               dbl4 *__restrict__ x, dbl4 *__restrict__ v, int4 *__restrict__ q, RunState *rs)
 {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   const int k = range_of(st_off, nnew, t);
-  const int sid = sys0 + k;
+  const int sid = slot[k];
   const SysTab &T = sys[sid];
   const int d = T.atom_off + (t - st_off[k]);
   int ty = types[t];
@@ -111,16 +109,21 @@ __global__ void k_ingest_batch(int n, const double *__restrict__ pos, const doub
 }
 
 // Finished jobs: staged atom t belongs to retiring job k (offsets r_off), system
-// r_sys[k]; positions and velocities go out back to back as AoS float64.
-__global__ void k_extract_batch(int n, const dbl4 *__restrict__ x, const dbl4 *__restrict__ v,
+// r_sys[k]; positions and velocities go out back to back as AoS float64.  The atoms
+// then get the word dead_w (the system without atoms): every kernel of the layout
+// leaves them alone until a new job is placed over them.
+__global__ void k_extract_batch(int n, dbl4 *__restrict__ x, const dbl4 *__restrict__ v, int4 *__restrict__ q,
                                 const int *__restrict__ r_off, const int *__restrict__ r_sys, int nret,
-                                const SysTab *__restrict__ sys, double *__restrict__ pos, double *__restrict__ vel)
+                                const SysTab *__restrict__ sys, int dead_w, double *__restrict__ pos,
+                                double *__restrict__ vel)
 {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   const int k = range_of(r_off, nret, t);
   const int d = sys[r_sys[k]].atom_off + (t - r_off[k]);
   const dbl4 a = x[d], b = v[d];
+  reinterpret_cast<double *>(x + d)[3] = __longlong_as_double((long long)dead_w);
+  reinterpret_cast<int *>(q + d)[3] = dead_w;
   pos[3 * (size_t)t] = a.x;
   pos[3 * (size_t)t + 1] = a.y;
   pos[3 * (size_t)t + 2] = a.z;
@@ -129,12 +132,14 @@ __global__ void k_extract_batch(int n, const dbl4 *__restrict__ x, const dbl4 *_
   vel[3 * (size_t)t + 2] = b.z;
 }
 
-// Per-system potential and kinetic energy: one block per system, fixed-order sums.
+// Potential and kinetic energy of the systems sys_ids[0..gridDim.x): one block per
+// system, fixed-order sums.
 __global__ void k_sys_energy(const double *__restrict__ eatom, const dbl4 *__restrict__ v, const int4 *__restrict__ q,
-                             const double *__restrict__ mass, const SysTab *__restrict__ sys, double *__restrict__ out)
+                             const double *__restrict__ mass, const SysTab *__restrict__ sys,
+                             const int *__restrict__ sys_ids, double *__restrict__ out)
 {
   __shared__ double sp[256], sk[256];
-  const SysTab &T = sys[blockIdx.x];
+  const SysTab &T = sys[sys_ids[blockIdx.x]];
   double pe = 0.0, ke = 0.0;
   for (int k = threadIdx.x; k < T.natoms; k += 256) {
     const int i = T.atom_off + k;
@@ -187,12 +192,15 @@ struct Job {
   int64_t n = 0;
   std::vector<double> pos, vel;
   std::vector<int32_t> types;
+  bool one_species = false;   // every atom of one type: the 4-slot register route
   double box[3] = {0, 0, 0};
   double dt = 0;
   int64_t nsteps = 0;
   int state = 0;   // 0 queued, 1 running, 2 done, 3 failed
   int err = 0;
   double t_submit = 0, t_admit = 0, t_done = 0;
+  int slot = -1;        // system index while resident
+  int64_t off = 0;      // first atom while resident
   SysCtl ctl{};    // device step control at the last chunk boundary
   double epot = 0, ekin = 0;
   std::vector<double> rpos, rvel;
@@ -209,30 +217,33 @@ struct tersoff_server {
   double skin = 0, rl = 0;
   PairRadii radii{};            // list radius per type pair of the shared table
   int max_slots = 0, chunk = 0, listcap = 32;
-  int64_t cap_atoms = 0;
+  int64_t cap_atoms = 0;        // atom capacity; also the stride of every [slot][atom] list array
   cudaStream_t st = nullptr, cap_st = nullptr;
-  AtomState A[2];          // packed positions/velocities (x, v, q); repacks copy between the two
+  AtomState A[2];          // packed positions/velocities (x, v, q); compactions copy between the two
   int cur = 0;
   AtomState SC;            // force scatter buffers of the packed layout
   ListState L;
-  SysDev S;
+  SysDev S;                // [max_slots + 1] system tables; system index = slot, slot max_slots: freed atoms
   RunState *rs = nullptr;
   double *eatom = nullptr, *sysE = nullptr;
   double *stage = nullptr;      // device staging (new jobs in, finished jobs out)
   size_t stage_b = 0;
   char *hstage = nullptr;       // pinned host staging
   size_t hstage_b = 0;
-  int *dtabs = nullptr;         // device index tables of a repack / retire (4 x (max_slots + 1) ints)
+  int *dtabs = nullptr;         // device index tables of an admission / retirement (TAB_INTS ints)
   // register-kernel routes: atoms of one-species jobs (at most 4 in-cutoff
   // neighbours in the solids served) through the 4-slot kernel, the others through
   // the 8-slot kernel.  A job's route follows from its own atoms only, so its
   // arithmetic does not depend on the batch.
-  ForceRoutes routes{};
-  bool routed = false;
-  int *d_order = nullptr;       // [capacity] atom order of the two routes
-  std::vector<SysTab> tab;
-  std::vector<Job *> batch;      // resident jobs in layout order (owned by `jobs`; touched by the worker only)
-  int64_t natoms = 0;
+  ForceRoutes routes{};         // every resident atom (the step graph)
+  ForceRoutes new_routes{};     // the atoms of the jobs admitted last (their first force evaluation)
+  int *d_order = nullptr;       // [capacity] route order of every resident atom
+  int *d_order_new = nullptr;   // [capacity] route order of the newly admitted atoms
+  std::vector<SysTab> tab;      // host copy of the system tables [max_slots + 1]
+  std::vector<Job *> slot_job;  // resident job of each slot (owned by `jobs`; touched by the worker only)
+  int64_t hw = 0;               // atoms [0, hw) hold every resident job (the rest of the range is freed atoms)
+  int64_t live = 0;             // resident atoms
+  int nres = 0;                 // resident jobs
   int ncell = 0;
   int fast_slots = 8, gen_slots = 32;
   cudaGraph_t g = nullptr;
@@ -251,8 +262,11 @@ struct tersoff_server {
   std::thread worker;
   tersoff_server_stats stats{};   // published under mu
   // worker-side counters, published into stats under mu once per loop
-  int64_t w_chunks = 0, w_repacks = 0;
+  int64_t w_chunks = 0, w_repacks = 0, w_compactions = 0;
   double w_retire = 0, w_repack = 0, w_graph = 0, w_run = 0;
+  double w_hw = 0, w_live = 0;  // sums over chunks of the layout's atoms [0, hw) and of the resident atoms
+  double compact_frac = 0.3;    // compaction threshold: share of freed atoms below hw ...
+  int64_t compact_min = 1 << 16;   // ... and their least number
   std::string msg;              // last error reported to the caller (under mu)
 };
 
@@ -286,7 +300,7 @@ size_t bytes_per_atom(bool f32, int listcap)
   const size_t v4 = f32 ? 16 : 32;
   return 2 * (32 + 32 + 16)                        // two copies of x, v, q
          + (size_t)listcap * (v4 + 8)              // contrib + nbr/rev
-         + v4 + 8 + 8 + 4 + 16 + 12 + 8 + 4 + 16;  // selfF, mask, work, cnt, qref, cells, eatom, route order, slack
+         + v4 + 8 + 8 + 4 + 16 + 12 + 8 + 8 + 16;  // selfF, mask, work, cnt, qref, cells, eatom, route orders, slack
 }
 
 // pinned host staging of at least `bytes` (contents not kept)
@@ -318,10 +332,24 @@ int srv_force(tersoff_server *s, cudaStream_t st)
 {
   const tersoff_params *P = s->P;
   AtomState &X = cur_atoms(s);
-  SK(launch_force_part(3, st, s->prec, s->fast_slots, P->fast, s->gen_slots, 0, 0, (int)s->natoms, X.x, X.q,
-                       s->L.nbr, s->L.cnt, s->S.tab, s->f32 ? P->pair_f : P->pair_d,
+  SK(launch_force_part(3, st, s->prec, s->fast_slots, P->fast, s->gen_slots, 0, 0, (int)s->hw, (int)s->cap_atoms,
+                       X.x, X.q, s->L.nbr, s->L.cnt, s->S.tab, s->f32 ? P->pair_f : P->pair_d,
                        s->f32 ? P->trip_f : P->trip_d, P->nt, s->SC.contrib, s->SC.selfF, s->SC.mask, s->SC.work,
-                       s->SC.nwork, s->SC.partial, s->rs, s->eatom, s->routed ? &s->routes : nullptr, 0));
+                       s->SC.nwork, s->SC.partial, s->rs, s->eatom, s->fast_slots > 0 ? &s->routes : nullptr, 0));
+  return TERSOFF_OK;
+}
+
+// First force evaluation of the jobs admitted last (the others keep theirs): their
+// own route order with the register kernels, or every atom with the general kernel.
+int srv_force_new(tersoff_server *s)
+{
+  if (s->fast_slots == 0) return srv_force(s, s->st);
+  const tersoff_params *P = s->P;
+  AtomState &X = cur_atoms(s);
+  SK(launch_force_part(3, s->st, s->prec, s->fast_slots, P->fast, s->gen_slots, 0, 0, (int)s->hw,
+                       (int)s->cap_atoms, X.x, X.q, s->L.nbr, s->L.cnt, s->S.tab, s->f32 ? P->pair_f : P->pair_d,
+                       s->f32 ? P->trip_f : P->trip_d, P->nt, s->SC.contrib, s->SC.selfF, s->SC.mask, s->SC.work,
+                       s->SC.nwork, s->SC.partial, s->rs, s->eatom, &s->new_routes, 0));
   return TERSOFF_OK;
 }
 
@@ -329,17 +357,17 @@ int srv_vv(tersoff_server *s, cudaStream_t st)
 {
   AtomState &X = cur_atoms(s);
   const float lim = (float)(0.25 * s->skin * s->skin);
-  SK(launch_vv(st, s->prec, false, (int)s->natoms, -1, X.x, X.v, X.q, s->L.qref, s->SC.contrib, s->SC.selfF,
+  SK(launch_vv(st, s->prec, false, (int)s->hw, (int)s->cap_atoms, -1, X.x, X.v, X.q, s->L.qref, s->SC.contrib, s->SC.selfF,
                s->SC.mask, s->L.rev, s->S.tab, s->S.ctl, s->P->d_mass, lim, s->SC.kepart, s->rs));
   return TERSOFF_OK;
 }
 
-// full: every atom gets a new list; else only systems whose rebuild flag is set
+// full: every resident atom gets a new list; else only systems whose rebuild flag is set
 int srv_build(tersoff_server *s, cudaStream_t st, bool full)
 {
   AtomState &X = cur_atoms(s);
   ListState &L = s->L;
-  SK(launch_build(st, (int)s->natoms, X.q, s->S.tab, full ? nullptr : s->S.ctl, s->ncell, s->radii, L.cell_count, L.cell_start, L.tile_sums, L.cell_atoms,
+  SK(launch_build(st, (int)s->hw, (int)s->cap_atoms, X.q, s->S.tab, full ? nullptr : s->S.ctl, s->ncell, s->radii, L.cell_count, L.cell_start, L.tile_sums, L.cell_atoms,
                   L.cell_of, L.rank, L.nbr, L.rev, L.cnt, L.cap, L.qref, s->rs, 0));
   return TERSOFF_OK;
 }
@@ -398,7 +426,7 @@ int graph_build(tersoff_server *s)
   SK(cudaGraphAddNode(&inode, body, deps, edges, nd, &ip));
   SK(cudaStreamUpdateCaptureDependencies(st, &inode, nullptr, 1, cudaStreamSetCaptureDependencies));
   SKR(srv_force(s, st));
-  SK(launch_step_end(st, s->rs, s->S.ctl, (int)s->batch.size(), hloop, 1));
+  SK(launch_step_end(st, s->rs, s->S.ctl, s->max_slots + 1, hloop, 1));
   cudaGraph_t bodyc = body;
   SK(cudaStreamEndCapture(st, &bodyc));
   cudaGraph_t ifbody = ip.conditional.phGraph_out[0];
@@ -436,127 +464,247 @@ int build_and_force(tersoff_server *s)
   return srv_err(s, TERSOFF_ERR_NLIST_OVERFLOW, "list build did not converge");
 }
 
-// Rebuild the packed layout from the jobs in `order` (survivors first, then new):
-// survivors move with one kernel, new jobs are staged back to back and ingested
-// with one copy and one kernel.
-int repack(tersoff_server *s, const std::vector<Job *> &order, const std::vector<bool> &is_new)
+// ---- layout: system slots, atom ranges, tables ------------------------------
+//
+// A resident job keeps its system slot and its atom range [off, off + n) for its
+// whole run: admissions place new jobs into free ranges (first fit, lowest address)
+// and build lists and forces for the new jobs only; retirements turn a job's atoms
+// into freed atoms (system max_slots, no atoms), which every kernel leaves alone.
+// The list arrays are strided by the capacity, so no resident job's list, reverse
+// indices or force contributions move.  When a job fits no free range, or freed
+// atoms below the high-water mark pass a share of it, the layout is compacted:
+// survivors move down in address order, and every list and force is rebuilt.
+
+int TAB_INTS(const tersoff_server *s) { return 8 * (s->max_slots + 2); }   // ints of dtabs
+
+constexpr double FREED_COMPACT_FRAC = 0.3;     // compact above this share of freed atoms below hw ...
+constexpr int64_t FREED_COMPACT_MIN = 1 << 16; // ... when they are at least this many
+
+int dead_word(const tersoff_server *s) { return make_w(0, s->max_slots); }
+
+// System tables (cell numbering in slot order), high-water mark and counts of the
+// resident jobs; entry max_slots (freed atoms) has no atoms and no cells.
+int layout_tables(tersoff_server *s)
 {
   const tersoff_params *P = s->P;
-  const int S = (int)order.size();
-  std::vector<SysTab> tab(S);
-  std::vector<SysCtl> ctl(S);
-  std::map<const Job *, int> prev;
-  for (size_t k = 0; k < s->batch.size(); ++k) prev[s->batch[k]] = s->tab[k].atom_off;
-  // index tables: [0, S) new atom offsets, [S+1, ...) survivor source offsets, then
-  // staging offsets of the new jobs
-  std::vector<int> itab(4 * (size_t)(S + 1), 0);
-  int *dst_off = itab.data(), *src_off = itab.data() + (S + 1), *st_off = itab.data() + 2 * (S + 1),
-      *route_off = itab.data() + 3 * (S + 1);
-  int64_t off = 0, staged = 0;
-  int coff = 0, nsurv = 0, nnew = 0;
-  for (int k = 0; k < S; ++k) {
-    Job &J = *order[k];
-    SysTab &T = tab[k];
-    T.geo = make_geom(J.box);
+  int coff = 0, nres = 0;
+  int64_t hw = 0, live = 0;
+  for (int k = 0; k <= s->max_slots; ++k) {
+    SysTab &T = s->tab[k];
+    T = SysTab{};
+    const Job *J = k < s->max_slots ? s->slot_job[k] : nullptr;
+    if (!J) continue;
     CellGrid gr;
-    if (make_grid(J.box, s->rl, &gr) != TERSOFF_OK) return srv_err(s, TERSOFF_ERR_ARG, "cell grid too large");
+    if (make_grid(J->box, s->rl, &gr) != TERSOFF_OK) return srv_err(s, TERSOFF_ERR_ARG, "cell grid too large");
+    T.geo = make_geom(J->box);
     for (int a = 0; a < 3; ++a) T.nc[a] = gr.nc[a];
     T.cell_off = coff;
-    T.atom_off = (int)off;
-    T.natoms = (int)J.n;
-    T.dt = J.dt;
-    for (int a = 0; a < MAX_TYPES; ++a) T.kick[a] = a < P->nt ? 0.5 * J.dt * ACCEL / P->masses[a] : 0.0;
-    ctl[k] = is_new[k] ? SysCtl{J.nsteps, 0, 0} : J.ctl;
-    J.ctl = ctl[k];
-    dst_off[k] = (int)off;
-    if (!is_new[k]) {
-      if (nnew > 0) return srv_err(s, TERSOFF_ERR_ARG, "survivors must precede new jobs");
-      src_off[k] = prev[order[k]];
-      ++nsurv;
-    } else {
-      st_off[nnew++] = (int)staged;
-      staged += J.n;
-    }
-    off += J.n;
+    T.atom_off = (int)J->off;
+    T.natoms = (int)J->n;
+    T.dt = J->dt;
+    for (int a = 0; a < MAX_TYPES; ++a) T.kick[a] = a < P->nt ? 0.5 * J->dt * ACCEL / P->masses[a] : 0.0;
     coff += gr.ncell;
+    hw = std::max<int64_t>(hw, J->off + J->n);
+    live += J->n;
+    ++nres;
   }
-  const int64_t surv_atoms = nsurv < S ? dst_off[nsurv] : off;
-  // routes: one-species jobs first (4 slots), then the others (8 slots)
-  int64_t n4 = 0;
-  std::vector<char> one_species(S, 0);
-  for (int k = 0; k < S; ++k) {
-    const Job &J = *order[k];
-    one_species[k] = std::all_of(J.types.begin(), J.types.end(), [&](int32_t t) { return t == J.types[0]; });
-    if (one_species[k]) n4 += J.n;
-  }
-  {
-    int64_t r4 = 0, r8 = n4;
-    for (int k = 0; k < S; ++k) {
-      route_off[k] = (int)(one_species[k] ? r4 : r8);
-      (one_species[k] ? r4 : r8) += order[k]->n;
-    }
-  }
-  s->routed = s->fast_slots > 0 && n4 > 0;
-  if (s->routed) {
-    s->routes.n = n4 < off ? 2 : 1;
-    s->routes.r[0] = ForceRoute{n4 < off ? s->d_order : nullptr, 0, (int)n4, 4, 0};
-    s->routes.r[1] = ForceRoute{s->d_order, (int)n4, (int)(off - n4), 8, 0};
-  }
-  s->natoms = off;
   s->ncell = coff;
-  if (!sys_alloc(s->S, std::max(1, S))) return srv_err(s, TERSOFF_ERR_NOMEM, "system tables");
+  s->hw = hw;
+  s->live = live;
+  s->nres = nres;
   if (ensure_list(&s->priv, s->L, s->cap_atoms, s->listcap, std::max(1, coff)) != TERSOFF_OK)
     return srv_err(s, TERSOFF_ERR_NOMEM, "cell arrays for %d cells", coff);
+  return TERSOFF_OK;
+}
+
+// Route table of the jobs js (one-species jobs first, each group in the given order)
+// appended to the host int table `it`; R gets the launches over order[0, total).
+void route_table(const std::vector<Job *> &js, int *order, std::vector<int> &it, size_t *at, int *nsys,
+                 int64_t *total, ForceRoutes &R)
+{
+  std::vector<const Job *> o;
+  for (const Job *J : js)
+    if (J->one_species) o.push_back(J);
+  const size_t n4j = o.size();
+  for (const Job *J : js)
+    if (!J->one_species) o.push_back(J);
+  const int n = (int)o.size();
+  *at = it.size();
+  it.resize(it.size() + 2 * (size_t)n + 1);
+  int *ro = it.data() + *at, *ao = ro + n + 1;
+  int64_t pos = 0, n4 = 0;
+  for (int k = 0; k < n; ++k) {
+    ro[k] = (int)pos;
+    ao[k] = (int)o[k]->off;
+    pos += o[k]->n;
+    if ((size_t)k < n4j) n4 += o[k]->n;
+  }
+  ro[n] = (int)pos;
+  *nsys = n;
+  *total = pos;
+  R = ForceRoutes{};
+  if (n4 > 0 && n4 < pos) {
+    R.n = 2;
+    R.r[0] = ForceRoute{order, 0, (int)n4, 4, 0};
+    R.r[1] = ForceRoute{order, (int)n4, (int)(pos - n4), 8, 0};
+  } else {
+    R.n = 1;
+    R.r[0] = ForceRoute{order, 0, (int)pos, n4 > 0 ? 4 : 8, 0};
+  }
+}
+
+std::vector<Job *> resident(const tersoff_server *s)
+{
+  std::vector<Job *> r;
+  for (Job *J : s->slot_job)
+    if (J) r.push_back(J);
+  return r;
+}
+
+// First-fit placement of a job of n atoms among the resident ranges (sorted by
+// offset, updated in place); -1 when no free range holds it.
+int64_t place(std::vector<std::pair<int64_t, int64_t>> &ranges, int64_t n, int64_t cap)
+{
+  int64_t prev = 0;
+  for (size_t k = 0; k <= ranges.size(); ++k) {
+    const int64_t next = k < ranges.size() ? ranges[k].first : cap;
+    if (next - prev >= n) {
+      ranges.insert(ranges.begin() + k, {prev, n});
+      return prev;
+    }
+    if (k < ranges.size()) prev = ranges[k].first + ranges[k].second;
+  }
+  return -1;
+}
+
+// Status of an admission's list build and force evaluation: a list overflow grows
+// the lists and rebuilds every job (build_and_force); a neighbour count above the
+// general kernel's slots widens it.
+int check_admission(tersoff_server *s)
+{
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    RunState h;
+    SKR(read_state(s, &h));
+    if (h.status == 0) return TERSOFF_OK;
+    SK(cudaMemsetAsync(&s->rs->status, 0, sizeof(int), s->st));
+    if (h.status & ST_NLIST_OVERFLOW) {
+      SKR(build_and_force(s));
+    } else if (h.status & ST_NC_OVERFLOW) {
+      if (h.maxnc > MAX_CAP) return srv_err(s, TERSOFF_ERR_NLIST_OVERFLOW, "%d in-cutoff neighbours", h.maxnc);
+      s->gen_slots = force_slots_for(h.maxnc);
+      SKR(srv_force(s, s->st));
+    } else {
+      return srv_err(s, h.status & ST_NONFINITE ? TERSOFF_ERR_NONFINITE : TERSOFF_ERR_CUDA, "device status %d",
+                     h.status);
+    }
+  }
+  return srv_err(s, TERSOFF_ERR_NLIST_OVERFLOW, "admission did not converge");
+}
+
+// Make the resident set of slot_job current on the device.  fresh: the jobs placed
+// since the last layout (slot, offset and step control set).  compacted: survivors
+// moved to the offsets they now hold, from old_off (same order as surv).
+int apply_layout(tersoff_server *s, const std::vector<Job *> &fresh, const std::vector<Job *> &surv,
+                 const std::vector<int64_t> &old_off, bool compacted)
+{
+  const tersoff_params *P = s->P;
+  SKR(layout_tables(s));
+  const int NS = s->max_slots + 1;
+  const int nnew = (int)fresh.size();
+  const int nsurv = compacted ? (int)surv.size() : 0;
+  // int tables: new jobs' staging offsets [nnew + 1] and slots [nnew]; survivors'
+  // destination and source offsets [nsurv] each; the two route tables
+  std::vector<int> it(2 * (size_t)nnew + 1 + 2 * (size_t)nsurv, 0);
+  int *st_off = it.data(), *nslot = st_off + nnew + 1, *dst_off = nslot + nnew, *src_off = dst_off + nsurv;
+  int64_t staged = 0, moved = 0;
+  for (int k = 0; k < nnew; ++k) {
+    st_off[k] = (int)staged;
+    nslot[k] = fresh[k]->slot;
+    staged += fresh[k]->n;
+  }
+  st_off[nnew] = (int)staged;
+  for (int k = 0; k < nsurv; ++k) {
+    dst_off[k] = (int)surv[k]->off;
+    src_off[k] = (int)old_off[k];
+    moved = std::max<int64_t>(moved, surv[k]->off + surv[k]->n);
+  }
+  size_t at_all = 0, at_new = 0;
+  int ns_all = 0, ns_new = 0;
+  int64_t tot_all = 0, tot_new = 0;
+  route_table(resident(s), s->d_order, it, &at_all, &ns_all, &tot_all, s->routes);
+  route_table(fresh, s->d_order_new, it, &at_new, &ns_new, &tot_new, s->new_routes);
+  st_off = it.data();   // the route tables grew the vector
+  if (it.size() > (size_t)TAB_INTS(s)) return srv_err(s, TERSOFF_ERR_ARG, "index tables exceed their buffer");
+  // step control: resident jobs as the last chunk left them, new jobs from the start;
+  // copy A flags the new jobs for their first list build, copy B clears the flags
+  std::vector<SysCtl> ctlA(NS, SysCtl{0, 0, 0}), ctlB;
+  for (Job *J : resident(s)) ctlA[J->slot] = SysCtl{J->ctl.steps_left, J->ctl.open, 0};
+  ctlB = ctlA;
+  for (Job *J : fresh) ctlA[J->slot].rebuild = 1;
   // pinned staging: tables, then the new jobs' positions, velocities and types
-  const size_t tbytes = sizeof(SysTab) * S + sizeof(SysCtl) * S + sizeof(int) * itab.size();
+  const size_t b_tab = sizeof(SysTab) * NS, b_ctl = sizeof(SysCtl) * NS, b_int = sizeof(int) * it.size();
+  const size_t tbytes = b_tab + 2 * b_ctl + b_int;
   const size_t tpad = (tbytes + 255) / 256 * 256;
   const size_t nbytes = (size_t)staged * (6 * sizeof(double) + sizeof(int32_t));
   if (!host_reserve(s, tpad + nbytes)) return srv_err(s, TERSOFF_ERR_NOMEM, "pinned staging");
   if (nbytes && !dreserve(s->stage, s->stage_b, nbytes)) return srv_err(s, TERSOFF_ERR_NOMEM, "staging");
   char *h = s->hstage;
-  memcpy(h, tab.data(), sizeof(SysTab) * S);
-  memcpy(h + sizeof(SysTab) * S, ctl.data(), sizeof(SysCtl) * S);
-  memcpy(h + sizeof(SysTab) * S + sizeof(SysCtl) * S, itab.data(), sizeof(int) * itab.size());
+  memcpy(h, s->tab.data(), b_tab);
+  memcpy(h + b_tab, ctlA.data(), b_ctl);
+  memcpy(h + b_tab + b_ctl, ctlB.data(), b_ctl);
+  memcpy(h + b_tab + 2 * b_ctl, it.data(), b_int);
   double *hpos = (double *)(h + tpad);
   double *hvel = hpos + 3 * staged;
   int32_t *hty = (int32_t *)(hvel + 3 * staged);
-  for (int k = nsurv, m = 0; k < S; ++k, ++m) {
-    const Job &J = *order[k];
-    memcpy(hpos + 3 * (size_t)st_off[m], J.pos.data(), sizeof(double) * 3 * J.n);
-    memcpy(hvel + 3 * (size_t)st_off[m], J.vel.data(), sizeof(double) * 3 * J.n);
-    memcpy(hty + st_off[m], J.types.data(), sizeof(int32_t) * J.n);
+  for (int k = 0; k < nnew; ++k) {
+    const Job &J = *fresh[k];
+    memcpy(hpos + 3 * (size_t)st_off[k], J.pos.data(), sizeof(double) * 3 * J.n);
+    memcpy(hvel + 3 * (size_t)st_off[k], J.vel.data(), sizeof(double) * 3 * J.n);
+    memcpy(hty + st_off[k], J.types.data(), sizeof(int32_t) * J.n);
   }
-  SK(cudaMemcpyAsync(s->S.tab, h, sizeof(SysTab) * S, cudaMemcpyHostToDevice, s->st));
-  SK(cudaMemcpyAsync(s->S.ctl, h + sizeof(SysTab) * S, sizeof(SysCtl) * S, cudaMemcpyHostToDevice, s->st));
-  SK(cudaMemcpyAsync(s->dtabs, h + sizeof(SysTab) * S + sizeof(SysCtl) * S, sizeof(int) * itab.size(),
-                     cudaMemcpyHostToDevice, s->st));
+  SK(cudaMemcpyAsync(s->S.tab, h, b_tab, cudaMemcpyHostToDevice, s->st));
+  SK(cudaMemcpyAsync(s->S.ctl, h + b_tab + (compacted ? b_ctl : 0), b_ctl, cudaMemcpyHostToDevice, s->st));
+  SK(cudaMemcpyAsync(s->dtabs, h + b_tab + 2 * b_ctl, b_int, cudaMemcpyHostToDevice, s->st));
+  const int *d_st = s->dtabs, *d_slot = d_st + nnew + 1, *d_dst = d_slot + nnew, *d_src = d_dst + nsurv;
   AtomState &src = s->A[s->cur];
-  AtomState &dst = s->A[1 - s->cur];
-  const int *d_dst = s->dtabs, *d_src = s->dtabs + (S + 1), *d_st = s->dtabs + 2 * (S + 1);
-  if (surv_atoms > 0) {
-    k_move<<<(int)((surv_atoms + 255) / 256), 256, 0, s->st>>>((int)surv_atoms, src.x, src.v, src.q, dst.x, dst.v,
-                                                                dst.q, d_dst, d_src, nsurv);
+  AtomState &dst = s->A[compacted ? 1 - s->cur : s->cur];
+  if (nsurv > 0 && moved > 0) {
+    k_move<<<(int)((moved + 255) / 256), 256, 0, s->st>>>((int)moved, src.x, src.v, src.q, dst.x, dst.v, dst.q, d_dst,
+                                                          d_src, nsurv);
     SK(cudaGetLastError());
   }
   if (staged > 0) {
     double *dpos = s->stage, *dvel = dpos + 3 * staged;
     int *dty = (int *)(dvel + 3 * staged);
     SK(cudaMemcpyAsync(dpos, hpos, nbytes, cudaMemcpyHostToDevice, s->st));
-    k_ingest_batch<<<(int)((staged + 255) / 256), 256, 0, s->st>>>((int)staged, dpos, dvel, dty, d_st, nnew, nsurv,
+    k_ingest_batch<<<(int)((staged + 255) / 256), 256, 0, s->st>>>((int)staged, dpos, dvel, dty, d_st, nnew, d_slot,
                                                                    s->S.tab, P->nt, dst.x, dst.v, dst.q, s->rs);
     SK(cudaGetLastError());
   }
-  if (s->routed && s->routes.n == 2) {
-    k_route_order<<<(int)((off + 255) / 256), 256, 0, s->st>>>((int)off, d_dst, s->dtabs + 3 * (S + 1), S,
-                                                               s->d_order);
+  if (tot_all > 0) {
+    k_route_order<<<(int)((tot_all + 255) / 256), 256, 0, s->st>>>((int)tot_all, s->dtabs + at_all,
+                                                                   s->dtabs + at_all + ns_all + 1, ns_all, s->d_order);
     SK(cudaGetLastError());
   }
-  s->cur = 1 - s->cur;
-  s->tab = tab;
-  s->batch = order;
+  if (tot_new > 0 && !compacted) {
+    k_route_order<<<(int)((tot_new + 255) / 256), 256, 0, s->st>>>(
+        (int)tot_new, s->dtabs + at_new, s->dtabs + at_new + ns_new + 1, ns_new, s->d_order_new);
+    SK(cudaGetLastError());
+  }
+  if (compacted) s->cur = 1 - s->cur;
   graph_free(s);
-  SKR(build_and_force(s));
-  s->w_repacks += 1;
+  if (compacted) {
+    SKR(build_and_force(s));
+    s->w_compactions += 1;
+  } else if (nnew > 0) {
+    // lists of the new jobs only (their rebuild flags), then their first forces
+    SK(cudaMemsetAsync(&s->rs->maxcount, 0, sizeof(int), s->st));
+    SKR(srv_build(s, s->st, false));
+    SK(cudaMemcpyAsync(s->S.ctl, h + b_tab + b_ctl, b_ctl, cudaMemcpyHostToDevice, s->st));
+    SKR(srv_force_new(s));
+    SKR(check_admission(s));
+  }
+  if (nnew > 0) s->w_repacks += 1;
   return TERSOFF_OK;
 }
 
@@ -579,10 +727,11 @@ int launch_steps(tersoff_server *s, long long n)
     SKR(srv_vv(s, s->st));
     AtomState &X = cur_atoms(s);
     ListState &L = s->L;
-    SK(launch_build(s->st, (int)s->natoms, X.q, s->S.tab, s->S.ctl, s->ncell, s->radii, L.cell_count, L.cell_start, L.tile_sums, L.cell_atoms, L.cell_of, L.rank, L.nbr, L.rev, L.cnt,
-                    L.cap, L.qref, s->rs, 1));
+    SK(launch_build(s->st, (int)s->hw, (int)s->cap_atoms, X.q, s->S.tab, s->S.ctl, s->ncell, s->radii, L.cell_count,
+                    L.cell_start, L.tile_sums, L.cell_atoms, L.cell_of, L.rank, L.nbr, L.rev, L.cnt, L.cap, L.qref,
+                    s->rs, 1));
     SKR(srv_force(s, s->st));
-    SK(launch_step_end(s->st, s->rs, s->S.ctl, (int)s->batch.size(), 0, 0));
+    SK(launch_step_end(s->st, s->rs, s->S.ctl, s->max_slots + 1, 0, 0));
   }
   return TERSOFF_OK;
 }
@@ -609,7 +758,7 @@ int run_chunk(tersoff_server *s)
       return srv_err(s, h.status & ST_NONFINITE ? TERSOFF_ERR_NONFINITE : TERSOFF_ERR_CUDA, "device status %d",
                      h.status);
     }
-    SK(launch_step_end(s->st, s->rs, s->S.ctl, (int)s->batch.size(), 0, 0));
+    SK(launch_step_end(s->st, s->rs, s->S.ctl, s->max_slots + 1, 0, 0));
     const long long rest = h.steps_left - 1;
     if (rest > 0) SKR(launch_steps(s, rest));
   }
@@ -618,31 +767,33 @@ int run_chunk(tersoff_server *s)
 }
 
 // Copy results of jobs whose run is over (steps done, closing kick applied): one
-// energy kernel, one extraction kernel and one copy for all of them.
+// energy kernel, one extraction kernel and one copy for all of them.  Their slots
+// are freed and their atoms become freed atoms.
 int retire(tersoff_server *s, std::vector<Job *> &done)
 {
-  const int S = (int)s->batch.size();
-  if (!S) return TERSOFF_OK;
-  std::vector<SysCtl> ctl(S);
-  SK(cudaMemcpyAsync(ctl.data(), s->S.ctl, sizeof(SysCtl) * S, cudaMemcpyDeviceToHost, s->st));
+  if (s->nres == 0) return TERSOFF_OK;
+  const int NS = s->max_slots + 1;
+  std::vector<SysCtl> ctl(NS);
+  SK(cudaMemcpyAsync(ctl.data(), s->S.ctl, sizeof(SysCtl) * NS, cudaMemcpyDeviceToHost, s->st));
   SK(cudaStreamSynchronize(s->st));
   std::vector<int> rtab;   // [nret + 1] staging offsets, then [nret] systems
   std::vector<int> rsys;
   int64_t staged = 0;
-  for (int k = 0; k < S; ++k) {
-    Job &J = *s->batch[k];
-    J.ctl = ctl[k];
+  for (int k = 0; k < s->max_slots; ++k) {
+    Job *J = s->slot_job[k];
+    if (!J) continue;
+    J->ctl = ctl[k];
     if (ctl[k].steps_left == 0 && ctl[k].open == 0) {
       rtab.push_back((int)staged);
       rsys.push_back(k);
-      staged += J.n;
+      staged += J->n;
     }
   }
   const int nret = (int)rsys.size();
   if (!nret) return TERSOFF_OK;
   rtab.push_back((int)staged);
   rtab.insert(rtab.end(), rsys.begin(), rsys.end());
-  const size_t ebytes = sizeof(double) * 2 * S;
+  const size_t ebytes = sizeof(double) * 2 * nret;
   const size_t tbytes = (sizeof(int) * rtab.size() + 255) / 256 * 256;
   const size_t nbytes = (size_t)staged * 6 * sizeof(double);
   if (!host_reserve(s, ebytes + tbytes + nbytes) || !dreserve(s->stage, s->stage_b, nbytes))
@@ -653,23 +804,26 @@ int retire(tersoff_server *s, std::vector<Job *> &done)
   double *hpos = (double *)(h + ebytes + tbytes);
   memcpy(ht, rtab.data(), sizeof(int) * rtab.size());
   AtomState &X = cur_atoms(s);
-  k_sys_energy<<<S, 256, 0, s->st>>>(s->eatom, X.v, X.q, s->P->d_mass, s->S.tab, s->sysE);
-  SK(cudaGetLastError());
   SK(cudaMemcpyAsync(s->dtabs, ht, sizeof(int) * rtab.size(), cudaMemcpyHostToDevice, s->st));
+  k_sys_energy<<<nret, 256, 0, s->st>>>(s->eatom, X.v, X.q, s->P->d_mass, s->S.tab, s->dtabs + nret + 1, s->sysE);
+  SK(cudaGetLastError());
   double *dpos = s->stage, *dvel = dpos + 3 * staged;
-  k_extract_batch<<<(int)((staged + 255) / 256), 256, 0, s->st>>>((int)staged, X.x, X.v, s->dtabs,
-                                                                   s->dtabs + nret + 1, nret, s->S.tab, dpos, dvel);
+  k_extract_batch<<<(int)((staged + 255) / 256), 256, 0, s->st>>>((int)staged, X.x, X.v, X.q, s->dtabs,
+                                                                   s->dtabs + nret + 1, nret, s->S.tab,
+                                                                   dead_word(s), dpos, dvel);
   SK(cudaGetLastError());
   SK(cudaMemcpyAsync(hE, s->sysE, ebytes, cudaMemcpyDeviceToHost, s->st));
   SK(cudaMemcpyAsync(hpos, dpos, nbytes, cudaMemcpyDeviceToHost, s->st));
   SK(cudaStreamSynchronize(s->st));
   const double *hvel = hpos + 3 * staged;
   for (int m = 0; m < nret; ++m) {
-    Job &J = *s->batch[rsys[m]];
+    Job &J = *s->slot_job[rsys[m]];
     J.rpos.assign(hpos + 3 * (size_t)rtab[m], hpos + 3 * (size_t)rtab[m] + 3 * J.n);
     J.rvel.assign(hvel + 3 * (size_t)rtab[m], hvel + 3 * (size_t)rtab[m] + 3 * J.n);
-    J.epot = hE[2 * rsys[m]];
-    J.ekin = hE[2 * rsys[m] + 1];
+    J.epot = hE[2 * m];
+    J.ekin = hE[2 * m + 1];
+    s->slot_job[J.slot] = nullptr;
+    J.slot = -1;
     done.push_back(&J);
   }
   return TERSOFF_OK;
@@ -679,19 +833,72 @@ void fail_all(tersoff_server *s, int code)
 {
   std::lock_guard<std::mutex> lk(s->mu);
   s->msg = s->priv.err;
-  for (Job *jp : s->batch) {
+  for (Job *&jp : s->slot_job) {
+    if (!jp) continue;
     Job &J = *jp;
     J.state = 3;
     J.err = code;
     J.t_done = now_s();
+    J.slot = -1;
     s->stats.failed += 1;
     s->stats.running -= 1;
+    jp = nullptr;
   }
-  s->batch.clear();
-  s->tab.clear();
-  s->natoms = 0;
+  s->nres = 0;
+  s->live = 0;
+  s->hw = 0;
   s->broken = true;
   s->cv_done.notify_all();
+}
+
+// Places the admitted jobs `fresh` (slots, offsets, step control) and applies the
+// layout: in place when every job fits a free range and freed atoms stay below
+// the compaction threshold, else compacted.
+int admit(tersoff_server *s, const std::vector<Job *> &fresh)
+{
+  std::vector<std::pair<int64_t, int64_t>> ranges;
+  for (Job *J : resident(s)) ranges.push_back({J->off, J->n});
+  std::sort(ranges.begin(), ranges.end());
+  bool compacted = false;
+  int64_t live = 0, hw = 0;
+  for (auto &r : ranges) live += r.second;
+  for (Job *J : fresh) {
+    const int64_t off = place(ranges, J->n, s->cap_atoms);
+    if (off < 0) {
+      compacted = true;
+      break;
+    }
+    J->off = off;
+    live += J->n;
+  }
+  if (!compacted) {
+    for (auto &r : ranges) hw = std::max(hw, r.first + r.second);
+    compacted = !fresh.empty() && hw - live >= s->compact_min && (double)(hw - live) > s->compact_frac * hw;
+  }
+  std::vector<Job *> surv;
+  std::vector<int64_t> old_off;
+  if (compacted) {
+    surv = resident(s);
+    std::sort(surv.begin(), surv.end(), [](const Job *a, const Job *b) { return a->off < b->off; });
+    int64_t off = 0;
+    for (Job *J : surv) {
+      old_off.push_back(J->off);
+      J->off = off;
+      off += J->n;
+    }
+    for (Job *J : fresh) {
+      J->off = off;
+      off += J->n;
+    }
+  }
+  int k = 0;
+  for (Job *J : fresh) {
+    while (s->slot_job[k]) ++k;
+    s->slot_job[k] = J;
+    J->slot = k;
+    J->ctl = SysCtl{J->nsteps, 0, 0};
+  }
+  return apply_layout(s, fresh, surv, old_off, compacted);
 }
 
 void worker_loop(tersoff_server *s)
@@ -701,7 +908,7 @@ void worker_loop(tersoff_server *s)
   for (;;) {
     {
       std::unique_lock<std::mutex> lk(s->mu);
-      s->cv_work.wait(lk, [&] { return s->stop || !s->queue.empty() || !s->batch.empty(); });
+      s->cv_work.wait(lk, [&] { return s->stop || !s->queue.empty() || s->nres > 0; });
       if (s->stop) break;
     }
     if (s->broken) {
@@ -728,14 +935,14 @@ void worker_loop(tersoff_server *s)
       fail_all(s, rc);
       continue;
     }
-    std::vector<Job *> order;
-    std::vector<bool> is_new;
-    bool changed = !done.empty();
+    std::vector<Job *> fresh;
     {
       std::lock_guard<std::mutex> lk(s->mu);
       const double t = now_s();
       s->stats.chunks = s->w_chunks;
       s->stats.repacks = s->w_repacks;
+      s->stats.compactions = s->w_compactions;
+      s->stats.layout_fill = s->w_hw > 0 ? s->w_live / s->w_hw : 1.0;
       s->stats.retire_s = s->w_retire;
       s->stats.repack_s = s->w_repack;
       s->stats.graph_s = s->w_graph;
@@ -747,54 +954,38 @@ void worker_loop(tersoff_server *s)
         s->stats.running -= 1;
         s->stats.atom_steps += jp->n * jp->nsteps;
       }
+      int nres = 0;
       int64_t atoms = 0;
-      for (Job *jp : s->batch) {
-        if (std::find(done.begin(), done.end(), jp) != done.end()) continue;
-        order.push_back(jp);
-        is_new.push_back(false);
-        atoms += jp->n;
-      }
+      for (const Job *J : s->slot_job)
+        if (J) {
+          ++nres;
+          atoms += J->n;
+        }
       // admit queued jobs in arrival order while slots and atom capacity allow
       while (!s->queue.empty()) {
         Job &J = *s->jobs.at(s->queue.front());
-        if ((int)order.size() >= s->max_slots || atoms + J.n > s->cap_atoms) break;
+        if (nres + (int)fresh.size() >= s->max_slots || atoms + J.n > s->cap_atoms) break;
         s->queue.pop_front();
         J.state = 1;
         J.t_admit = t;
-        order.push_back(&J);
-        is_new.push_back(true);
+        fresh.push_back(&J);
         atoms += J.n;
         s->stats.admitted += 1;
         s->stats.queued -= 1;
         s->stats.running += 1;
-        changed = true;
       }
       if (!done.empty()) s->cv_done.notify_all();
     }
-    if (changed) {
-      if (order.empty()) {
-        s->batch.clear();
-        s->tab.clear();
-        s->natoms = 0;
-        graph_free(s);
-      } else {
-        t0 = now_s();
-        rc = repack(s, order, is_new);
-        s->w_repack += now_s() - t0;
-        if (rc != TERSOFF_OK) {
-          s->batch = order;
-          fail_all(s, rc);
-          continue;
-        }
+    if (!done.empty() || !fresh.empty()) {
+      t0 = now_s();
+      rc = admit(s, fresh);
+      s->w_repack += now_s() - t0;
+      if (rc != TERSOFF_OK) {
+        fail_all(s, rc);
+        continue;
       }
     }
-    // nothing left to integrate (all resident jobs finished): retire without stepping
-    bool active = false;
-    for (size_t k = 0; k < s->batch.size(); ++k) {
-      const SysCtl &c = s->batch[k]->ctl;
-      if (c.steps_left > 0 || c.open) active = true;
-    }
-    if (s->batch.empty()) {
+    if (s->nres == 0) {
       if (busy_since > 0) {
         std::lock_guard<std::mutex> lk(s->mu);
         s->stats.busy_s += now_s() - busy_since;
@@ -803,7 +994,13 @@ void worker_loop(tersoff_server *s)
       continue;
     }
     if (busy_since == 0) busy_since = now_s();
+    // nothing left to integrate (all resident jobs finished): retire without stepping
+    bool active = false;
+    for (const Job *J : s->slot_job)
+      if (J && (J->ctl.steps_left > 0 || J->ctl.open)) active = true;
     if (active) {
+      s->w_hw += (double)s->hw;
+      s->w_live += (double)s->live;
       t0 = now_s();
       const double g0 = s->w_graph;
       rc = run_chunk(s);
@@ -844,12 +1041,21 @@ int tersoff_server_create(tersoff_ctx *ctx, const tersoff_params *P, tersoff_pre
   s->fast_slots = (P->sym_angular && !ctx->general_only) ? 8 : 0;
   s->gen_slots = 16;
   s->use_graphs = !(getenv("TERSOFF_GRAPHS") && strcmp(getenv("TERSOFF_GRAPHS"), "0") == 0);
+  s->compact_frac = FREED_COMPACT_FRAC;
+  s->compact_min = FREED_COMPACT_MIN;
+  if (const char *c = getenv("TERSOFF_COMPACT_FREED")) {
+    // compact whenever freed atoms below the high-water mark pass this share of it
+    s->compact_frac = std::max(0.0, atof(c));
+    s->compact_min = 1;
+  }
   s->cap_atoms = std::min<int64_t>((int64_t)(budget / bytes_per_atom(s->f32, s->listcap)), MAX_LIST_ATOMS);
   auto fail = [&](int rc) {
     tersoff_server_destroy(s);
     return rc;
   };
   if (s->cap_atoms < 1) return fail(set_err(ctx, TERSOFF_ERR_NOMEM, "budget below one atom"));
+  s->tab.assign((size_t)max_slots + 1, SysTab{});
+  s->slot_job.assign((size_t)max_slots, nullptr);
   if (cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&s->cap_st, cudaStreamNonBlocking) != cudaSuccess)
     return fail(set_err(ctx, TERSOFF_ERR_CUDA, "streams"));
@@ -861,11 +1067,12 @@ int tersoff_server_create(tersoff_ctx *ctx, const tersoff_params *P, tersoff_pre
   const int64_t cap = s->cap_atoms;
   if (ensure_atoms(pc, s->A[0], cap, true) != TERSOFF_OK || ensure_atoms(pc, s->A[1], cap, true) != TERSOFF_OK ||
       ensure_scatter(pc, s->SC, cap, s->listcap, s->f32) != TERSOFF_OK ||
-      ensure_list(pc, s->L, cap, s->listcap, 1) != TERSOFF_OK || !sys_alloc(s->S, max_slots) ||
+      ensure_list(pc, s->L, cap, s->listcap, 1) != TERSOFF_OK || !sys_alloc(s->S, max_slots + 1) ||
       cudaMalloc((void **)&s->eatom, sizeof(double) * cap) != cudaSuccess ||
       cudaMalloc((void **)&s->sysE, sizeof(double) * 2 * max_slots) != cudaSuccess ||
-      cudaMalloc((void **)&s->dtabs, sizeof(int) * 4 * (size_t)(max_slots + 1)) != cudaSuccess ||
-      cudaMalloc((void **)&s->d_order, sizeof(int) * (size_t)std::max<int64_t>(cap, 1)) != cudaSuccess) {
+      cudaMalloc((void **)&s->dtabs, sizeof(int) * (size_t)TAB_INTS(s)) != cudaSuccess ||
+      cudaMalloc((void **)&s->d_order, sizeof(int) * (size_t)std::max<int64_t>(cap, 1)) != cudaSuccess ||
+      cudaMalloc((void **)&s->d_order_new, sizeof(int) * (size_t)std::max<int64_t>(cap, 1)) != cudaSuccess) {
     cudaGetLastError();
     return fail(set_err(ctx, TERSOFF_ERR_NOMEM, "cannot allocate the packed layout for %lld atoms", (long long)cap));
   }
@@ -900,6 +1107,7 @@ int tersoff_server_submit(tersoff_server *s, const tersoff_job *job, uint64_t *j
   J->types.assign(job->types, job->types + n);
   for (int64_t i = 0; i < n; ++i)
     if (J->types[i] < 0 || J->types[i] >= s->P->nt) return reject(TERSOFF_ERR_ARG, "atom type out of range");
+  J->one_species = std::all_of(J->types.begin(), J->types.end(), [&](int32_t t) { return t == J->types[0]; });
   for (int64_t i = 0; i < 3 * n; ++i)
     if (!std::isfinite(J->pos[i]) || !std::isfinite(J->vel[i])) return reject(TERSOFF_ERR_ARG, "non-finite input");
   for (int a = 0; a < 3; ++a) J->box[a] = job->box[a];
@@ -1010,6 +1218,7 @@ void tersoff_server_destroy(tersoff_server *s)
   dfree(s->stage);
   dfree(s->dtabs);
   dfree(s->d_order);
+  dfree(s->d_order_new);
   if (s->hstage) cudaFreeHost(s->hstage);
   if (s->st) cudaStreamDestroy(s->st);
   if (s->cap_st) cudaStreamDestroy(s->cap_st);

@@ -93,7 +93,8 @@ class tersoff_server_stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in ("submitted", "admitted", "completed", "failed", "queued", "running",
                                               "atom_steps", "chunks", "repacks")] + \
                [("busy_s", ctypes.c_double), ("capacity_atoms", ctypes.c_int64)] + \
-               [(k, ctypes.c_double) for k in ("retire_s", "repack_s", "graph_s", "run_s")]
+               [(k, ctypes.c_double) for k in ("retire_s", "repack_s", "graph_s", "run_s")] + \
+               [("compactions", ctypes.c_int64), ("layout_fill", ctypes.c_double)]
 
 
 _U64 = ctypes.c_uint64

@@ -113,6 +113,27 @@ def test_admission_limited_by_budget_and_slots(T, ctx, P):
         assert t[0] >= 0 and t[1] > 0 and abs(t[2] - t[0] - t[1]) < 1e-9
 
 
+def test_freed_ranges_and_compaction_keep_results(T, ctx, P, monkeypatch):
+    """Jobs keep their atom ranges: a retired job leaves a freed range that a later
+    job may fill, and a job that fits no free range compacts the layout (resident
+    jobs move, every list and force is rebuilt).  Results stay bitwise those of the
+    jobs run alone, with and without compaction at every admission."""
+    a, b, c = jobs_mix()
+    # about 1050 atoms of capacity, three slots: b (205 atoms) leaves a hole below a
+    # (512) that c (480) does not fit, so c's admission compacts the layout
+    jobs = [b, a, c, b, a]
+    ref = {id(j): run_jobs(T, ctx, P, [j], T.MIXED, chunk=9)[0][0] for j in (a, b, c)}
+    for env in (None, "0"):
+        if env is not None:
+            monkeypatch.setenv("TERSOFF_COMPACT_FREED", env)
+        res, st = run_jobs(T, ctx, P, jobs, T.MIXED, chunk=5, budget=1200 * 900, slots=3)
+        assert st["completed"] == len(jobs) and st["failed"] == 0
+        assert st["compactions"] >= 1
+        for job, (p, v, e, _) in zip(jobs, res):
+            pr, vr, er, _ = ref[id(job)]
+            assert np.array_equal(p, pr) and np.array_equal(v, vr) and e == er
+
+
 def test_wait_timeout_poll_and_errors(T, ctx, P):
     srv = T.Server(ctx, P, prec=T.MIXED, skin=0.3, budget_bytes=1 << 26, max_slots=4, chunk_steps=50)
     s = wl.si_box(4, 4, 4, seed=41, T=1000.0)
