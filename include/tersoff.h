@@ -279,7 +279,8 @@ typedef struct {
   int64_t capacity_atoms;
   /* scheduler wall time by activity (s): retiring finished jobs, admitting new
    * jobs (placement, their lists and first forces, compactions), capturing graphs,
-   * running chunks of steps */
+   * running chunks of steps.  Handing results to retired jobs and staging the
+   * next queued jobs run on the host while a chunk runs and count in run_s. */
   double retire_s, repack_s, graph_s, run_s;
   int64_t compactions;   /* admissions that moved resident jobs (layout compacted) */
   double layout_fill;    /* resident atoms / atoms the step kernels cover (freed ranges included), over chunks */

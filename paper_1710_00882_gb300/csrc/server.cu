@@ -73,19 +73,23 @@ __global__ void k_move(int n, const dbl4 *__restrict__ sx, const dbl4 *__restric
   dv[d] = sv[src];
 }
 
-// New jobs, staged back to back (pos [n][3], vel [n][3], types [n]): staged atom t
-// belongs to new job k (staging offsets st_off), system slot[k].
-__global__ void k_ingest_batch(int n, const double *__restrict__ pos, const double *__restrict__ vel,
-                               const int *__restrict__ types, const int *__restrict__ st_off, int nnew,
-                               const int *__restrict__ slot, const SysTab *__restrict__ sys, int nt,
-                               dbl4 *__restrict__ x, dbl4 *__restrict__ v, int4 *__restrict__ q, RunState *rs)
+// New jobs, one staging block each at stage + boff[k] doubles (pos [n_k][3], vel
+// [n_k][3], types [n_k] int32): atom t0 of the admission belongs to new job k (atom
+// offsets st_off, st_off[nnew] = n), system slot[k].
+__global__ void k_ingest_batch(int n, const double *__restrict__ stage, const int *__restrict__ boff,
+                               const int *__restrict__ st_off, int nnew, const int *__restrict__ slot,
+                               const SysTab *__restrict__ sys, int nt, dbl4 *__restrict__ x, dbl4 *__restrict__ v,
+                               int4 *__restrict__ q, RunState *rs)
 {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n) return;
-  const int k = range_of(st_off, nnew, t);
+  const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t0 >= n) return;
+  const int k = range_of(st_off, nnew, t0);
+  const int t = t0 - st_off[k], nk = st_off[k + 1] - st_off[k];
+  const double *pos = stage + boff[k], *vel = pos + 3 * (size_t)nk;
+  const int *types = reinterpret_cast<const int *>(vel + 3 * (size_t)nk);
   const int sid = slot[k];
   const SysTab &T = sys[sid];
-  const int d = T.atom_off + (t - st_off[k]);
+  const int d = T.atom_off + t;
   int ty = types[t];
   if (ty < 0 || ty >= nt) {
     atomicOr(&rs->status, ST_BAD_TYPE);
@@ -230,6 +234,20 @@ struct tersoff_server {
   size_t stage_b = 0;
   char *hstage = nullptr;       // pinned host staging
   size_t hstage_b = 0;
+  // results of the jobs retired last: copied to pinned memory on the stream, then
+  // handed to the jobs while the next chunk runs
+  char *hres = nullptr;
+  size_t hres_b = 0;
+  double *rstage = nullptr;     // their device staging
+  size_t rstage_b = 0;
+  cudaEvent_t ev_res = nullptr; // recorded after their copy to hres
+  std::vector<Job *> pending;   // retired jobs whose results are in flight
+  std::vector<int64_t> pend_off;   // their atom offsets in hres, size pending + 1
+  // staging blocks of the first queued jobs, written while a chunk runs
+  char *hpre = nullptr;
+  size_t hpre_b = 0;
+  std::vector<Job *> pre_jobs;  // those jobs, in queue order (a prefix of the queue)
+  std::vector<size_t> pre_off;  // their block offsets in hpre (bytes), size pre_jobs + 1
   int *dtabs = nullptr;         // device index tables of an admission / retirement (TAB_INTS ints)
   // register-kernel routes: atoms of one-species jobs (at most 4 in-cutoff
   // neighbours in the solids served) through the 4-slot kernel, the others through
@@ -304,19 +322,33 @@ size_t bytes_per_atom(bool f32, int listcap)
 }
 
 // pinned host staging of at least `bytes` (contents not kept)
-bool host_reserve(tersoff_server *s, size_t bytes)
+bool pinned_reserve(char *&p, size_t &have, size_t bytes)
 {
-  if (bytes <= s->hstage_b && s->hstage) return true;
-  if (s->hstage) cudaFreeHost(s->hstage);
-  s->hstage = nullptr;
-  s->hstage_b = 0;
+  if (bytes <= have && p) return true;
+  if (p) cudaFreeHost(p);
+  p = nullptr;
+  have = 0;
   bytes = std::max<size_t>(bytes + bytes / 4, 1 << 20);
-  if (cudaHostAlloc((void **)&s->hstage, bytes, cudaHostAllocDefault) != cudaSuccess) {
+  if (cudaHostAlloc((void **)&p, bytes, cudaHostAllocDefault) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  s->hstage_b = bytes;
+  have = bytes;
   return true;
+}
+
+bool host_reserve(tersoff_server *s, size_t bytes) { return pinned_reserve(s->hstage, s->hstage_b, bytes); }
+
+// Staging block of a job of n atoms: positions [n][3] and velocities [n][3] as
+// float64, then types [n] as int32, padded to whole doubles.
+size_t block_doubles(int64_t n) { return 6 * (size_t)n + ((size_t)n + 1) / 2; }
+
+void write_block(char *dst, const Job &J)
+{
+  double *d = reinterpret_cast<double *>(dst);
+  memcpy(d, J.pos.data(), sizeof(double) * 3 * J.n);
+  memcpy(d + 3 * J.n, J.vel.data(), sizeof(double) * 3 * J.n);
+  memcpy(d + 6 * J.n, J.types.data(), sizeof(int32_t) * J.n);
 }
 
 int read_state(tersoff_server *s, RunState *h)
@@ -475,7 +507,7 @@ int build_and_force(tersoff_server *s)
 // atoms below the high-water mark pass a share of it, the layout is compacted:
 // survivors move down in address order, and every list and force is rebuilt.
 
-int TAB_INTS(const tersoff_server *s) { return 8 * (s->max_slots + 2); }   // ints of dtabs
+int TAB_INTS(const tersoff_server *s) { return 10 * (s->max_slots + 2); }   // ints of dtabs
 
 constexpr double FREED_COMPACT_FRAC = 0.3;     // compact above this share of freed atoms below hw ...
 constexpr int64_t FREED_COMPACT_MIN = 1 << 16; // ... when they are at least this many
@@ -612,14 +644,27 @@ int apply_layout(tersoff_server *s, const std::vector<Job *> &fresh, const std::
   const int NS = s->max_slots + 1;
   const int nnew = (int)fresh.size();
   const int nsurv = compacted ? (int)surv.size() : 0;
-  // int tables: new jobs' staging offsets [nnew + 1] and slots [nnew]; survivors'
-  // destination and source offsets [nsurv] each; the two route tables
-  std::vector<int> it(2 * (size_t)nnew + 1 + 2 * (size_t)nsurv, 0);
-  int *st_off = it.data(), *nslot = st_off + nnew + 1, *dst_off = nslot + nnew, *src_off = dst_off + nsurv;
+  // int tables: new jobs' atom offsets [nnew + 1], slots [nnew] and staging block
+  // offsets [nnew] (doubles); survivors' destination and source offsets [nsurv]
+  // each; the two route tables
+  std::vector<int> it(3 * (size_t)nnew + 1 + 2 * (size_t)nsurv, 0);
+  int *st_off = it.data(), *nslot = st_off + nnew + 1, *boff = nslot + nnew, *dst_off = boff + nnew,
+      *src_off = dst_off + nsurv;
+  // the first new jobs may be staged already (prestage, while the last chunk ran)
+  size_t npre = 0;
+  while (npre < s->pre_jobs.size() && npre < (size_t)nnew && s->pre_jobs[npre] == fresh[npre]) ++npre;
+  const size_t pre_bytes = npre ? s->pre_off[npre] - s->pre_off[0] : 0;
   int64_t staged = 0, moved = 0;
+  size_t rest_doubles = 0;
   for (int k = 0; k < nnew; ++k) {
     st_off[k] = (int)staged;
     nslot[k] = fresh[k]->slot;
+    if ((size_t)k < npre) {
+      boff[k] = (int)((s->pre_off[k] - s->pre_off[0]) / sizeof(double));
+    } else {
+      boff[k] = (int)(pre_bytes / sizeof(double) + rest_doubles);
+      rest_doubles += block_doubles(fresh[k]->n);
+    }
     staged += fresh[k]->n;
   }
   st_off[nnew] = (int)staged;
@@ -633,7 +678,12 @@ int apply_layout(tersoff_server *s, const std::vector<Job *> &fresh, const std::
   int64_t tot_all = 0, tot_new = 0;
   route_table(resident(s), s->d_order, it, &at_all, &ns_all, &tot_all, s->routes);
   route_table(fresh, s->d_order_new, it, &at_new, &ns_new, &tot_new, s->new_routes);
-  st_off = it.data();   // the route tables grew the vector
+  // the route tables grew the vector: take its pointers again
+  st_off = it.data();
+  nslot = st_off + nnew + 1;
+  boff = nslot + nnew;
+  dst_off = boff + nnew;
+  src_off = dst_off + nsurv;
   if (it.size() > (size_t)TAB_INTS(s)) return srv_err(s, TERSOFF_ERR_ARG, "index tables exceed their buffer");
   // step control: resident jobs as the last chunk left them, new jobs from the start;
   // copy A flags the new jobs for their first list build, copy B clears the flags
@@ -641,31 +691,26 @@ int apply_layout(tersoff_server *s, const std::vector<Job *> &fresh, const std::
   for (Job *J : resident(s)) ctlA[J->slot] = SysCtl{J->ctl.steps_left, J->ctl.open, 0};
   ctlB = ctlA;
   for (Job *J : fresh) ctlA[J->slot].rebuild = 1;
-  // pinned staging: tables, then the new jobs' positions, velocities and types
+  // pinned staging: tables, then the blocks of the new jobs not staged already
   const size_t b_tab = sizeof(SysTab) * NS, b_ctl = sizeof(SysCtl) * NS, b_int = sizeof(int) * it.size();
   const size_t tbytes = b_tab + 2 * b_ctl + b_int;
   const size_t tpad = (tbytes + 255) / 256 * 256;
-  const size_t nbytes = (size_t)staged * (6 * sizeof(double) + sizeof(int32_t));
-  if (!host_reserve(s, tpad + nbytes)) return srv_err(s, TERSOFF_ERR_NOMEM, "pinned staging");
-  if (nbytes && !dreserve(s->stage, s->stage_b, nbytes)) return srv_err(s, TERSOFF_ERR_NOMEM, "staging");
+  const size_t rest_bytes = rest_doubles * sizeof(double);
+  if (!host_reserve(s, tpad + rest_bytes)) return srv_err(s, TERSOFF_ERR_NOMEM, "pinned staging");
+  if (pre_bytes + rest_bytes && !dreserve(s->stage, s->stage_b, pre_bytes + rest_bytes))
+    return srv_err(s, TERSOFF_ERR_NOMEM, "staging");
   char *h = s->hstage;
   memcpy(h, s->tab.data(), b_tab);
   memcpy(h + b_tab, ctlA.data(), b_ctl);
   memcpy(h + b_tab + b_ctl, ctlB.data(), b_ctl);
   memcpy(h + b_tab + 2 * b_ctl, it.data(), b_int);
-  double *hpos = (double *)(h + tpad);
-  double *hvel = hpos + 3 * staged;
-  int32_t *hty = (int32_t *)(hvel + 3 * staged);
-  for (int k = 0; k < nnew; ++k) {
-    const Job &J = *fresh[k];
-    memcpy(hpos + 3 * (size_t)st_off[k], J.pos.data(), sizeof(double) * 3 * J.n);
-    memcpy(hvel + 3 * (size_t)st_off[k], J.vel.data(), sizeof(double) * 3 * J.n);
-    memcpy(hty + st_off[k], J.types.data(), sizeof(int32_t) * J.n);
-  }
+  for (int k = (int)npre; k < nnew; ++k)
+    write_block(h + tpad + ((size_t)boff[k] * sizeof(double) - pre_bytes), *fresh[k]);
   SK(cudaMemcpyAsync(s->S.tab, h, b_tab, cudaMemcpyHostToDevice, s->st));
   SK(cudaMemcpyAsync(s->S.ctl, h + b_tab + (compacted ? b_ctl : 0), b_ctl, cudaMemcpyHostToDevice, s->st));
   SK(cudaMemcpyAsync(s->dtabs, h + b_tab + 2 * b_ctl, b_int, cudaMemcpyHostToDevice, s->st));
-  const int *d_st = s->dtabs, *d_slot = d_st + nnew + 1, *d_dst = d_slot + nnew, *d_src = d_dst + nsurv;
+  const int *d_st = s->dtabs, *d_slot = d_st + nnew + 1, *d_boff = d_slot + nnew, *d_dst = d_boff + nnew,
+            *d_src = d_dst + nsurv;
   AtomState &src = s->A[s->cur];
   AtomState &dst = s->A[compacted ? 1 - s->cur : s->cur];
   if (nsurv > 0 && moved > 0) {
@@ -674,13 +719,18 @@ int apply_layout(tersoff_server *s, const std::vector<Job *> &fresh, const std::
     SK(cudaGetLastError());
   }
   if (staged > 0) {
-    double *dpos = s->stage, *dvel = dpos + 3 * staged;
-    int *dty = (int *)(dvel + 3 * staged);
-    SK(cudaMemcpyAsync(dpos, hpos, nbytes, cudaMemcpyHostToDevice, s->st));
-    k_ingest_batch<<<(int)((staged + 255) / 256), 256, 0, s->st>>>((int)staged, dpos, dvel, dty, d_st, nnew, d_slot,
+    if (pre_bytes)
+      SK(cudaMemcpyAsync(s->stage, s->hpre + s->pre_off[0], pre_bytes, cudaMemcpyHostToDevice, s->st));
+    if (rest_bytes)
+      SK(cudaMemcpyAsync((char *)s->stage + pre_bytes, h + tpad, rest_bytes, cudaMemcpyHostToDevice, s->st));
+    k_ingest_batch<<<(int)((staged + 255) / 256), 256, 0, s->st>>>((int)staged, s->stage, d_boff, d_st, nnew, d_slot,
                                                                    s->S.tab, P->nt, dst.x, dst.v, dst.q, s->rs);
     SK(cudaGetLastError());
   }
+  // the prestaged blocks used here stay valid until this admission's copies are
+  // done (the synchronisation below); the entries go now
+  s->pre_jobs.erase(s->pre_jobs.begin(), s->pre_jobs.begin() + npre);
+  s->pre_off.erase(s->pre_off.begin(), s->pre_off.begin() + npre);
   if (tot_all > 0) {
     k_route_order<<<(int)((tot_all + 255) / 256), 256, 0, s->st>>>((int)tot_all, s->dtabs + at_all,
                                                                    s->dtabs + at_all + ns_all + 1, ns_all, s->d_order);
@@ -736,10 +786,12 @@ int launch_steps(tersoff_server *s, long long n)
   return TERSOFF_OK;
 }
 
-// One chunk of steps for the whole batch (recovering from list or slot overflow).
-int run_chunk(tersoff_server *s)
+// One chunk of steps for the whole batch: launched, then waited for.
+int chunk_launch(tersoff_server *s) { return launch_steps(s, s->chunk); }
+
+// Wait for the chunk (recovering from list or slot overflow).
+int chunk_wait(tersoff_server *s)
 {
-  SKR(launch_steps(s, s->chunk));
   for (int attempt = 0; attempt < 8; ++attempt) {
     RunState h;
     SKR(read_state(s, &h));
@@ -766,10 +818,11 @@ int run_chunk(tersoff_server *s)
   return TERSOFF_OK;
 }
 
-// Copy results of jobs whose run is over (steps done, closing kick applied): one
-// energy kernel, one extraction kernel and one copy for all of them.  Their slots
-// are freed and their atoms become freed atoms.
-int retire(tersoff_server *s, std::vector<Job *> &done)
+// Jobs whose run is over (steps done, closing kick applied): one energy kernel, one
+// extraction kernel and one copy to pinned memory for all of them, enqueued on the
+// stream (the event ev_res follows the copy).  Their slots are freed at once and
+// their atoms become freed atoms; finish_retire hands the results to the jobs.
+int retire(tersoff_server *s)
 {
   if (s->nres == 0) return TERSOFF_OK;
   const int NS = s->max_slots + 1;
@@ -794,39 +847,103 @@ int retire(tersoff_server *s, std::vector<Job *> &done)
   rtab.push_back((int)staged);
   rtab.insert(rtab.end(), rsys.begin(), rsys.end());
   const size_t ebytes = sizeof(double) * 2 * nret;
-  const size_t tbytes = (sizeof(int) * rtab.size() + 255) / 256 * 256;
+  const size_t epad = (ebytes + 255) / 256 * 256;
+  const size_t tbytes = sizeof(int) * rtab.size();
   const size_t nbytes = (size_t)staged * 6 * sizeof(double);
-  if (!host_reserve(s, ebytes + tbytes + nbytes) || !dreserve(s->stage, s->stage_b, nbytes))
-    return srv_err(s, TERSOFF_ERR_NOMEM, "staging");
-  char *h = s->hstage;
-  double *hE = (double *)h;
-  int *ht = (int *)(h + ebytes);
-  double *hpos = (double *)(h + ebytes + tbytes);
-  memcpy(ht, rtab.data(), sizeof(int) * rtab.size());
+  if (!pinned_reserve(s->hres, s->hres_b, epad + nbytes + tbytes) || !dreserve(s->rstage, s->rstage_b, nbytes))
+    return srv_err(s, TERSOFF_ERR_NOMEM, "result staging");
+  char *h = s->hres;
+  int *ht = (int *)(h + epad + nbytes);
+  memcpy(ht, rtab.data(), tbytes);
   AtomState &X = cur_atoms(s);
-  SK(cudaMemcpyAsync(s->dtabs, ht, sizeof(int) * rtab.size(), cudaMemcpyHostToDevice, s->st));
+  SK(cudaMemcpyAsync(s->dtabs, ht, tbytes, cudaMemcpyHostToDevice, s->st));
   k_sys_energy<<<nret, 256, 0, s->st>>>(s->eatom, X.v, X.q, s->P->d_mass, s->S.tab, s->dtabs + nret + 1, s->sysE);
   SK(cudaGetLastError());
-  double *dpos = s->stage, *dvel = dpos + 3 * staged;
+  double *dpos = s->rstage, *dvel = dpos + 3 * staged;
   k_extract_batch<<<(int)((staged + 255) / 256), 256, 0, s->st>>>((int)staged, X.x, X.v, X.q, s->dtabs,
                                                                    s->dtabs + nret + 1, nret, s->S.tab,
                                                                    dead_word(s), dpos, dvel);
   SK(cudaGetLastError());
-  SK(cudaMemcpyAsync(hE, s->sysE, ebytes, cudaMemcpyDeviceToHost, s->st));
-  SK(cudaMemcpyAsync(hpos, dpos, nbytes, cudaMemcpyDeviceToHost, s->st));
-  SK(cudaStreamSynchronize(s->st));
-  const double *hvel = hpos + 3 * staged;
+  SK(cudaMemcpyAsync(h, s->sysE, ebytes, cudaMemcpyDeviceToHost, s->st));
+  SK(cudaMemcpyAsync(h + epad, dpos, nbytes, cudaMemcpyDeviceToHost, s->st));
+  SK(cudaEventRecord(s->ev_res, s->st));
+  s->pend_off.assign(rtab.begin(), rtab.begin() + nret + 1);
   for (int m = 0; m < nret; ++m) {
     Job &J = *s->slot_job[rsys[m]];
-    J.rpos.assign(hpos + 3 * (size_t)rtab[m], hpos + 3 * (size_t)rtab[m] + 3 * J.n);
-    J.rvel.assign(hvel + 3 * (size_t)rtab[m], hvel + 3 * (size_t)rtab[m] + 3 * J.n);
-    J.epot = hE[2 * m];
-    J.ekin = hE[2 * m + 1];
     s->slot_job[J.slot] = nullptr;
     J.slot = -1;
-    done.push_back(&J);
+    s->pending.push_back(&J);
   }
   return TERSOFF_OK;
+}
+
+// Hand the results of the jobs retired last to them (after their copy, ev_res) and
+// report the jobs done; runs while the next chunk is on the device.
+int finish_retire(tersoff_server *s)
+{
+  if (s->pending.empty()) return TERSOFF_OK;
+  SK(cudaEventSynchronize(s->ev_res));
+  const int nret = (int)s->pending.size();
+  const int64_t staged = s->pend_off[nret];
+  const size_t epad = (sizeof(double) * 2 * nret + 255) / 256 * 256;
+  const double *hE = (const double *)s->hres;
+  const double *hpos = (const double *)(s->hres + epad), *hvel = hpos + 3 * staged;
+  for (int m = 0; m < nret; ++m) {
+    Job &J = *s->pending[m];
+    const size_t o = 3 * (size_t)s->pend_off[m];
+    J.rpos.assign(hpos + o, hpos + o + 3 * J.n);
+    J.rvel.assign(hvel + o, hvel + o + 3 * J.n);
+    J.epot = hE[2 * m];
+    J.ekin = hE[2 * m + 1];
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
+  const double t = now_s();
+  for (Job *jp : s->pending) {
+    jp->state = 2;
+    jp->t_done = t;
+    s->stats.completed += 1;
+    s->stats.running -= 1;
+    s->stats.atom_steps += jp->n * jp->nsteps;
+  }
+  s->pending.clear();
+  s->cv_done.notify_all();
+  return TERSOFF_OK;
+}
+
+// Stage the first queued jobs into hpre while a chunk runs, so that their admission
+// copies them to the device without a host copy of its own.  The blocks of jobs
+// still queued from last time move to the front first (their copies, if any, are
+// done: every admission that staged jobs waited for its copies).
+void prestage(tersoff_server *s)
+{
+  if (!s->hpre) return;
+  if (!s->pre_off.empty() && s->pre_off[0] > 0) {
+    const size_t base = s->pre_off[0];
+    memmove(s->hpre, s->hpre + base, s->pre_off.back() - base);
+    for (size_t &o : s->pre_off) o -= base;
+  }
+  if (s->pre_off.empty()) s->pre_off.push_back(0);
+  std::vector<Job *> add;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    size_t end = s->pre_off.back();
+    int64_t atoms = 0;
+    for (const Job *J : s->pre_jobs) atoms += J->n;
+    for (size_t k = s->pre_jobs.size(); k < s->queue.size() && k < (size_t)s->max_slots; ++k) {
+      Job *J = s->jobs.at(s->queue[k]).get();
+      const size_t b = block_doubles(J->n) * sizeof(double);
+      if (end + b > s->hpre_b || atoms + J->n > s->cap_atoms) break;
+      add.push_back(J);
+      end += b;
+      atoms += J->n;
+    }
+  }
+  for (Job *J : add) {
+    const size_t o = s->pre_off.back();
+    write_block(s->hpre + o, *J);
+    s->pre_jobs.push_back(J);
+    s->pre_off.push_back(o + block_doubles(J->n) * sizeof(double));
+  }
 }
 
 void fail_all(tersoff_server *s, int code)
@@ -844,6 +961,16 @@ void fail_all(tersoff_server *s, int code)
     s->stats.running -= 1;
     jp = nullptr;
   }
+  for (Job *jp : s->pending) {
+    jp->state = 3;
+    jp->err = code;
+    jp->t_done = now_s();
+    s->stats.failed += 1;
+    s->stats.running -= 1;
+  }
+  s->pending.clear();
+  s->pre_jobs.clear();
+  s->pre_off.clear();
   s->nres = 0;
   s->live = 0;
   s->hw = 0;
@@ -926,10 +1053,9 @@ void worker_loop(tersoff_server *s)
       s->cv_done.notify_all();
       continue;
     }
-    // retire finished jobs
-    std::vector<Job *> done;
+    // retire finished jobs (their results reach them while the next chunk runs)
     double t0 = now_s();
-    int rc = retire(s, done);
+    int rc = retire(s);
     s->w_retire += now_s() - t0;
     if (rc != TERSOFF_OK) {
       fail_all(s, rc);
@@ -947,13 +1073,6 @@ void worker_loop(tersoff_server *s)
       s->stats.repack_s = s->w_repack;
       s->stats.graph_s = s->w_graph;
       s->stats.run_s = s->w_run;
-      for (Job *jp : done) {
-        jp->state = 2;
-        jp->t_done = t;
-        s->stats.completed += 1;
-        s->stats.running -= 1;
-        s->stats.atom_steps += jp->n * jp->nsteps;
-      }
       int nres = 0;
       int64_t atoms = 0;
       for (const Job *J : s->slot_job)
@@ -974,9 +1093,8 @@ void worker_loop(tersoff_server *s)
         s->stats.queued -= 1;
         s->stats.running += 1;
       }
-      if (!done.empty()) s->cv_done.notify_all();
     }
-    if (!done.empty() || !fresh.empty()) {
+    if (!s->pending.empty() || !fresh.empty()) {
       t0 = now_s();
       rc = admit(s, fresh);
       s->w_repack += now_s() - t0;
@@ -985,6 +1103,31 @@ void worker_loop(tersoff_server *s)
         continue;
       }
     }
+    // nothing left to integrate (all resident jobs finished): retire without stepping
+    bool active = false;
+    for (const Job *J : s->slot_job)
+      if (J && (J->ctl.steps_left > 0 || J->ctl.open)) active = true;
+    double g0 = s->w_graph;
+    t0 = now_s();
+    if (active) {
+      s->w_hw += (double)s->hw;
+      s->w_live += (double)s->live;
+      rc = chunk_launch(s);
+      if (rc != TERSOFF_OK) {
+        fail_all(s, rc);
+        continue;
+      }
+    }
+    // on the host while the chunk runs: results of the retired jobs, staging of the
+    // next queued jobs
+    const double tf = now_s();
+    rc = finish_retire(s);
+    if (rc != TERSOFF_OK) {
+      fail_all(s, rc);
+      continue;
+    }
+    prestage(s);
+    if (!active) s->w_retire += now_s() - tf;
     if (s->nres == 0) {
       if (busy_since > 0) {
         std::lock_guard<std::mutex> lk(s->mu);
@@ -993,17 +1136,9 @@ void worker_loop(tersoff_server *s)
       }
       continue;
     }
-    if (busy_since == 0) busy_since = now_s();
-    // nothing left to integrate (all resident jobs finished): retire without stepping
-    bool active = false;
-    for (const Job *J : s->slot_job)
-      if (J && (J->ctl.steps_left > 0 || J->ctl.open)) active = true;
+    if (busy_since == 0) busy_since = t0;
     if (active) {
-      s->w_hw += (double)s->hw;
-      s->w_live += (double)s->live;
-      t0 = now_s();
-      const double g0 = s->w_graph;
-      rc = run_chunk(s);
+      rc = chunk_wait(s);
       s->w_run += now_s() - t0 - (s->w_graph - g0);
       if (rc != TERSOFF_OK) fail_all(s, rc);
     }
@@ -1076,6 +1211,11 @@ int tersoff_server_create(tersoff_ctx *ctx, const tersoff_params *P, tersoff_pre
     cudaGetLastError();
     return fail(set_err(ctx, TERSOFF_ERR_NOMEM, "cannot allocate the packed layout for %lld atoms", (long long)cap));
   }
+  if (cudaEventCreateWithFlags(&s->ev_res, cudaEventDisableTiming) != cudaSuccess)
+    return fail(set_err(ctx, TERSOFF_ERR_CUDA, "event"));
+  // staging of queued jobs while chunks run: about 30 MB of pinned memory (without
+  // it, admissions stage every job themselves)
+  pinned_reserve(s->hpre, s->hpre_b, (size_t)24 << 20);
   if (cudaStreamSynchronize(s->st) != cudaSuccess) return fail(set_err(ctx, TERSOFF_ERR_CUDA, "server set-up"));
   s->stats.capacity_atoms = cap;
   s->worker = std::thread(worker_loop, s);
@@ -1219,7 +1359,11 @@ void tersoff_server_destroy(tersoff_server *s)
   dfree(s->dtabs);
   dfree(s->d_order);
   dfree(s->d_order_new);
+  dfree(s->rstage);
   if (s->hstage) cudaFreeHost(s->hstage);
+  if (s->hres) cudaFreeHost(s->hres);
+  if (s->hpre) cudaFreeHost(s->hpre);
+  if (s->ev_res) cudaEventDestroy(s->ev_res);
   if (s->st) cudaStreamDestroy(s->st);
   if (s->cap_st) cudaStreamDestroy(s->cap_st);
   tersoff_ctx *ctx = s->ctx;
