@@ -205,10 +205,11 @@ __global__ void k_ingest_vel(int N, const double *__restrict__ vel, dbl4 *__rest
 }
 
 // reverse gather into AoS float64 forces; flags non-finite values
+// (perm non-null: atom i's row of out is perm[i], the caller's order of a permuted state)
 template <class A>
 __global__ void k_gather_out(int N, const typename A::V *__restrict__ contrib, const typename A::V *__restrict__ selfF,
                              const unsigned long long *__restrict__ mask, const int *__restrict__ rev,
-                             double *__restrict__ out, RunState *rs)
+                             double *__restrict__ out, const int *__restrict__ perm, RunState *rs)
 {
   if (rs->status != 0) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -216,9 +217,10 @@ __global__ void k_gather_out(int N, const typename A::V *__restrict__ contrib, c
   double fx, fy, fz;
   gather_force<A>(i, N, contrib, selfF, mask, rev, fx, fy, fz);
   if (!isfinite(fx) || !isfinite(fy) || !isfinite(fz)) atomicOr(&rs->status, ST_NONFINITE);
-  out[3 * (size_t)i] = fx;
-  out[3 * (size_t)i + 1] = fy;
-  out[3 * (size_t)i + 2] = fz;
+  const size_t o = perm ? (size_t)perm[i] : (size_t)i;
+  out[3 * o] = fx;
+  out[3 * o + 1] = fy;
+  out[3 * o + 2] = fz;
 }
 
 enum { VV_FINISH = 1, VV_START = 2 };
@@ -318,24 +320,38 @@ __global__ void k_ke_reduce(const double *__restrict__ kepart, int n, RunState *
   if (threadIdx.x == 0) rs->ekin2 += sh[0];
 }
 
-// AoS copies out of the device state
+// AoS copies out of the device state (perm non-null: atom i goes to row perm[i])
 __global__ void k_extract(int N, const dbl4 *__restrict__ x, const dbl4 *__restrict__ v, double *__restrict__ pos,
-                          double *__restrict__ vel)
+                          double *__restrict__ vel, const int *__restrict__ perm)
 {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
+  const size_t o = perm ? (size_t)perm[i] : (size_t)i;
   if (pos) {
     dbl4 a = x[i];
-    pos[3 * (size_t)i] = a.x;
-    pos[3 * (size_t)i + 1] = a.y;
-    pos[3 * (size_t)i + 2] = a.z;
+    pos[3 * o] = a.x;
+    pos[3 * o + 1] = a.y;
+    pos[3 * o + 2] = a.z;
   }
   if (vel) {
     dbl4 b = v[i];
-    vel[3 * (size_t)i] = b.x;
-    vel[3 * (size_t)i + 1] = b.y;
-    vel[3 * (size_t)i + 2] = b.z;
+    vel[3 * o] = b.x;
+    vel[3 * o + 1] = b.y;
+    vel[3 * o + 2] = b.z;
   }
+}
+
+// Atom k of the permuted state is atom perm[k] of the source (all three records).
+__global__ void k_permute_atoms(int N, const int *__restrict__ perm, const dbl4 *__restrict__ sx,
+                                const dbl4 *__restrict__ sv, const int4 *__restrict__ sq, dbl4 *__restrict__ dx,
+                                dbl4 *__restrict__ dv, int4 *__restrict__ dq)
+{
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const int i = perm[k];
+  dx[k] = sx[i];
+  dv[k] = sv[i];
+  dq[k] = sq[i];
 }
 
 // End of an MD step: record (PE_k, KE_{k-1}) in the trace (row k = rs->trace_k),
@@ -476,18 +492,22 @@ cudaError_t launch_vv(cudaStream_t st, int prec, bool ke, int N, int ld, int mod
 int vv_blocks(int N) { return (N + VV_THREADS - 1) / VV_THREADS; }
 
 cudaError_t launch_gather_out(cudaStream_t st, int prec, int N, const void *contrib, const void *selfF,
-                              const unsigned long long *mask, const int *rev, double *out, RunState *rs)
+                              const unsigned long long *mask, const int *rev, double *out, RunState *rs,
+                              const int *perm)
 {
   if (N == 0) return cudaSuccess;
   const int T = 256, B = (N + T - 1) / T;
   if (prec == PREC_FP64)
-    k_gather_out<AccFP64><<<B, T, 0, st>>>(N, (const dbl4 *)contrib, (const dbl4 *)selfF, mask, rev, out, rs);
+    k_gather_out<AccFP64><<<B, T, 0, st>>>(N, (const dbl4 *)contrib, (const dbl4 *)selfF, mask, rev, out, perm, rs);
   else if (prec == PREC_MIXED)
-    k_gather_out<AccMixed><<<B, T, 0, st>>>(N, (const float4 *)contrib, (const float4 *)selfF, mask, rev, out, rs);
+    k_gather_out<AccMixed><<<B, T, 0, st>>>(N, (const float4 *)contrib, (const float4 *)selfF, mask, rev, out, perm,
+                                            rs);
   else if (prec == PREC_MIXED_ACC64)
-    k_gather_out<AccMixed64><<<B, T, 0, st>>>(N, (const float4 *)contrib, (const float4 *)selfF, mask, rev, out, rs);
+    k_gather_out<AccMixed64><<<B, T, 0, st>>>(N, (const float4 *)contrib, (const float4 *)selfF, mask, rev, out,
+                                              perm, rs);
   else
-    k_gather_out<AccSingle><<<B, T, 0, st>>>(N, (const float4 *)contrib, (const float4 *)selfF, mask, rev, out, rs);
+    k_gather_out<AccSingle><<<B, T, 0, st>>>(N, (const float4 *)contrib, (const float4 *)selfF, mask, rev, out, perm,
+                                             rs);
   return cudaGetLastError();
 }
 
@@ -510,10 +530,19 @@ cudaError_t launch_ingest_vel(cudaStream_t st, int N, const double *vel, dbl4 *v
   return cudaGetLastError();
 }
 
-cudaError_t launch_extract(cudaStream_t st, int N, const dbl4 *x, const dbl4 *v, double *pos, double *vel)
+cudaError_t launch_extract(cudaStream_t st, int N, const dbl4 *x, const dbl4 *v, double *pos, double *vel,
+                           const int *perm)
 {
   if (N == 0) return cudaSuccess;
-  k_extract<<<(N + 255) / 256, 256, 0, st>>>(N, x, v, pos, vel);
+  k_extract<<<(N + 255) / 256, 256, 0, st>>>(N, x, v, pos, vel, perm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_permute_atoms(cudaStream_t st, int N, const int *perm, const dbl4 *sx, const dbl4 *sv,
+                                 const int4 *sq, dbl4 *dx, dbl4 *dv, int4 *dq)
+{
+  if (N == 0) return cudaSuccess;
+  k_permute_atoms<<<(N + 255) / 256, 256, 0, st>>>(N, perm, sx, sv, sq, dx, dv, dq);
   return cudaGetLastError();
 }
 

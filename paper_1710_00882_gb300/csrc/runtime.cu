@@ -162,6 +162,7 @@ struct tersoff_md {
   bool routed = false;  // register kernel split by atom type into a 4-slot and an 8-slot launch
   ForceRoutes routes{};
   int *d_order = nullptr;
+  int *perm = nullptr;   // [N] caller index of each atom (atoms grouped by type), or null: caller order
   // phase profiling: event pairs per phase, reused across reads
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -1112,6 +1113,42 @@ int tersoff_md_create(tersoff_ctx *ctx, const double *pos, const double *vel, co
     if (tmp) cudaFree(tmp);
     if (e != cudaSuccess) return fail(cuda_err(ctx, e, "ingest velocities"));
   }
+  // Atoms grouped by type (stable; an order fixed by the types alone, so a state
+  // copied out and created again gets the same one): the per-type register-kernel
+  // launches then read whole rows of the per-atom arrays.  md_get scatters back to
+  // the caller's order.
+  if (N > 0 && P->nt > 1) {
+    std::vector<int4> hq((size_t)N);
+    if (cudaMemcpy(hq.data(), md->atoms.q, sizeof(int4) * N, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(set_err(ctx, TERSOFF_ERR_CUDA, "types for grouping"));
+    std::vector<int> perm;
+    perm.reserve((size_t)N);
+    for (int t = 0; t < P->nt; ++t)
+      for (int64_t i = 0; i < N; ++i)
+        if (type_of(hq[i].w) == t) perm.push_back((int)i);
+    bool identity = true;
+    for (int64_t k = 0; k < N && identity; ++k) identity = perm[k] == (int)k;
+    if (!identity) {
+      void *tmp = nullptr;
+      const size_t nb = (size_t)N * (2 * sizeof(dbl4) + sizeof(int4));
+      if (cudaMalloc((void **)&md->perm, sizeof(int) * N) != cudaSuccess || cudaMalloc(&tmp, nb) != cudaSuccess) {
+        if (tmp) cudaFree(tmp);
+        cudaGetLastError();
+        return fail(set_err(ctx, TERSOFF_ERR_NOMEM, "atom grouping"));
+      }
+      dbl4 *tx = (dbl4 *)tmp, *tv = tx + N;
+      int4 *tq = (int4 *)(tv + N);
+      cudaError_t e = cudaMemcpyAsync(md->perm, perm.data(), sizeof(int) * N, cudaMemcpyHostToDevice, ctx->stream);
+      if (e == cudaSuccess)
+        e = launch_permute_atoms(ctx->stream, (int)N, md->perm, md->atoms.x, md->atoms.v, md->atoms.q, tx, tv, tq);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(md->atoms.x, tx, sizeof(dbl4) * N, cudaMemcpyDeviceToDevice, ctx->stream);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(md->atoms.v, tv, sizeof(dbl4) * N, cudaMemcpyDeviceToDevice, ctx->stream);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(md->atoms.q, tq, sizeof(int4) * N, cudaMemcpyDeviceToDevice, ctx->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+      cudaFree(tmp);
+      if (e != cudaSuccess) return fail(cuda_err(ctx, e, "atom grouping"));
+    }
+  }
   md->sys.host.dt = dt_ps;
   for (int a = 0; a < MAX_TYPES; ++a) md->sys.host.kick[a] = a < P->nt ? 0.5 * dt_ps * ACCEL / P->masses[a] : 0.0;
   if ((rc = build_list_sync(ctx, md->atoms, md->list, md->rs, box, P->rcmax, skin, md->sys, P)) != TERSOFF_OK)
@@ -1147,12 +1184,25 @@ int tersoff_md_create(tersoff_ctx *ctx, const double *pos, const double *vel, co
         for (int64_t i = 0; i < N; ++i)
           if (slots_t[type_of(hq[i].w)] == pass) order.push_back((int)i);
       const int n4 = (int)std::count_if(hq.begin(), hq.end(), [&](const int4 &a) { return slots_t[type_of(a.w)] == 4; });
-      if (cudaMalloc((void **)&md->d_order, sizeof(int) * N) != cudaSuccess ||
-          cudaMemcpy(md->d_order, order.data(), sizeof(int) * N, cudaMemcpyHostToDevice) != cudaSuccess)
-        return fail(set_err(ctx, TERSOFF_ERR_NOMEM, "routing order"));
-      md->routes.n = 2;
-      md->routes.r[0] = ForceRoute{md->d_order, 0, n4, 4, 0};
-      md->routes.r[1] = ForceRoute{md->d_order, n4, (int)N - n4, 8, 0};
+      // each launch over a contiguous range of atoms (atoms grouped by type) needs no
+      // order array
+      auto contiguous = [&](int b, int n) {
+        for (int k = 1; k < n; ++k)
+          if (order[b + k] != order[b] + k) return false;
+        return true;
+      };
+      if (contiguous(0, n4) && contiguous(n4, (int)N - n4)) {
+        md->routes.n = 2;
+        md->routes.r[0] = ForceRoute{nullptr, n4 > 0 ? order[0] : 0, n4, 4, 0};
+        md->routes.r[1] = ForceRoute{nullptr, n4 < N ? order[n4] : 0, (int)N - n4, 8, 0};
+      } else {
+        if (cudaMalloc((void **)&md->d_order, sizeof(int) * N) != cudaSuccess ||
+            cudaMemcpy(md->d_order, order.data(), sizeof(int) * N, cudaMemcpyHostToDevice) != cudaSuccess)
+          return fail(set_err(ctx, TERSOFF_ERR_NOMEM, "routing order"));
+        md->routes.n = 2;
+        md->routes.r[0] = ForceRoute{md->d_order, 0, n4, 4, 0};
+        md->routes.r[1] = ForceRoute{md->d_order, n4, (int)N - n4, 8, 0};
+      }
       md->routed = true;
     }
   }
@@ -1257,10 +1307,11 @@ int tersoff_md_get(tersoff_md *md, double *pos, double *vel, double *forces, int
     df = forces ? (double *)tmp + 6 * N : nullptr;
   }
   int rc = TERSOFF_OK;
-  if (launch_extract(ctx->stream, (int)N, md->atoms.x, md->atoms.v, dp, dv) != cudaSuccess) rc = TERSOFF_ERR_CUDA;
+  if (launch_extract(ctx->stream, (int)N, md->atoms.x, md->atoms.v, dp, dv, md->perm) != cudaSuccess)
+    rc = TERSOFF_ERR_CUDA;
   if (rc == TERSOFF_OK && df &&
       launch_gather_out(ctx->stream, md->gprec, (int)N, md->atoms.contrib, md->atoms.selfF, md->atoms.mask,
-                        md->list.rev, df, md->rs) != cudaSuccess)
+                        md->list.rev, df, md->rs, md->perm) != cudaSuccess)
     rc = TERSOFF_ERR_CUDA;
   if (rc == TERSOFF_OK && !dev) {
     if (pos) cudaMemcpyAsync(pos, dp, bytes, cudaMemcpyDeviceToHost, ctx->stream);
@@ -1326,6 +1377,7 @@ void tersoff_md_destroy(tersoff_md *md)
   dfree(md->rs);
   dfree(md->d_trace);
   dfree(md->d_order);
+  dfree(md->perm);
   ctx_release(md->ctx);
   delete md;
 }

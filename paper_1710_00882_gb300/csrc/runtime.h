@@ -77,12 +77,15 @@ int force_queue_blocks(int N);
 cudaError_t launch_vv(cudaStream_t, int, bool, int, int, int, dbl4 *, dbl4 *, int4 *, const int4 *, const void *,
                       const void *, const unsigned long long *, const int *, const SysTab *, SysCtl *,
                       const double *, float, double *, RunState *);
+cudaError_t launch_permute_atoms(cudaStream_t, int, const int *, const dbl4 *, const dbl4 *, const int4 *, dbl4 *,
+                                 dbl4 *, int4 *);
 cudaError_t launch_gather_out(cudaStream_t, int, int, const void *, const void *, const unsigned long long *,
-                              const int *, double *, RunState *);
+                              const int *, double *, RunState *, const int *perm = nullptr);
 cudaError_t launch_ingest(cudaStream_t, int, const double *, const int *, int, int, const SysTab *, dbl4 *, int4 *,
                           RunState *);
 cudaError_t launch_ingest_vel(cudaStream_t, int, const double *, dbl4 *);
-cudaError_t launch_extract(cudaStream_t, int, const dbl4 *, const dbl4 *, double *, double *);
+cudaError_t launch_extract(cudaStream_t, int, const dbl4 *, const dbl4 *, double *, double *,
+                           const int *perm = nullptr);
 cudaError_t launch_step_end(cudaStream_t, RunState *, SysCtl *, int, cudaGraphConditionalHandle, int);
 cudaError_t launch_loop_start(cudaStream_t, RunState *, SysCtl *, long long, double *, long long, int,
                               cudaGraphConditionalHandle);
