@@ -197,6 +197,7 @@ struct Job {
   std::vector<double> pos, vel;
   std::vector<int32_t> types;
   bool one_species = false;   // every atom of one type: the 4-slot register route
+  std::vector<int> perm;      // caller index of each stored atom (atoms grouped by type), or empty
   double box[3] = {0, 0, 0};
   double dt = 0;
   int64_t nsteps = 0;
@@ -891,8 +892,20 @@ int finish_retire(tersoff_server *s)
   for (int m = 0; m < nret; ++m) {
     Job &J = *s->pending[m];
     const size_t o = 3 * (size_t)s->pend_off[m];
-    J.rpos.assign(hpos + o, hpos + o + 3 * J.n);
-    J.rvel.assign(hvel + o, hvel + o + 3 * J.n);
+    if (J.perm.empty()) {
+      J.rpos.assign(hpos + o, hpos + o + 3 * J.n);
+      J.rvel.assign(hvel + o, hvel + o + 3 * J.n);
+    } else {
+      J.rpos.resize(3 * J.n);
+      J.rvel.resize(3 * J.n);
+      for (int64_t k = 0; k < J.n; ++k) {
+        const size_t c = 3 * (size_t)J.perm[k];
+        for (int a = 0; a < 3; ++a) {
+          J.rpos[c + a] = hpos[o + 3 * k + a];
+          J.rvel[c + a] = hvel[o + 3 * k + a];
+        }
+      }
+    }
     J.epot = hE[2 * m];
     J.ekin = hE[2 * m + 1];
   }
@@ -1248,6 +1261,29 @@ int tersoff_server_submit(tersoff_server *s, const tersoff_job *job, uint64_t *j
   for (int64_t i = 0; i < n; ++i)
     if (J->types[i] < 0 || J->types[i] >= s->P->nt) return reject(TERSOFF_ERR_ARG, "atom type out of range");
   J->one_species = std::all_of(J->types.begin(), J->types.end(), [&](int32_t t) { return t == J->types[0]; });
+  if (!J->one_species) {
+    // atoms grouped by type (stable): the register kernel reads whole rows of the
+    // per-atom arrays; results go back to the caller's order
+    std::vector<int> perm;
+    perm.reserve((size_t)n);
+    for (int t = 0; t < s->P->nt; ++t)
+      for (int64_t i = 0; i < n; ++i)
+        if (J->types[i] == t) perm.push_back((int)i);
+    std::vector<double> p(3 * n), v(3 * n);
+    std::vector<int32_t> ty(n);
+    for (int64_t k = 0; k < n; ++k) {
+      const int64_t i = perm[k];
+      for (int a = 0; a < 3; ++a) {
+        p[3 * k + a] = J->pos[3 * i + a];
+        v[3 * k + a] = J->vel[3 * i + a];
+      }
+      ty[k] = J->types[i];
+    }
+    J->pos.swap(p);
+    J->vel.swap(v);
+    J->types.swap(ty);
+    J->perm.swap(perm);
+  }
   for (int64_t i = 0; i < 3 * n; ++i)
     if (!std::isfinite(J->pos[i]) || !std::isfinite(J->vel[i])) return reject(TERSOFF_ERR_ARG, "non-finite input");
   for (int a = 0; a < 3; ++a) J->box[a] = job->box[a];
