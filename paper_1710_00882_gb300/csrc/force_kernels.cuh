@@ -320,6 +320,11 @@ k_force_reg(int ld, const dbl4 *__restrict__ x, const int4 *__restrict__ q, cons
   // (both reassigned by the count sort of the 8-slot kernels, below)
   bool active = tg < count;
   int i = active ? (order ? order[begin + tg] : begin + tg) : 0;
+  if (i < 0) {
+    // padding entry of a route order (segments that start a warp): nothing here
+    active = false;
+    i = 0;
+  }
   const int fb = block_base + (int)blockIdx.x;   // this block's queue and partial-sum row
   // pf atoms ahead (one resident wave of blocks): the counts and list rows the next
   // wave reads, from DRAM after a cold start, are requested into L2 now
@@ -624,7 +629,10 @@ k_force_reg(int ld, const dbl4 *__restrict__ x, const int4 *__restrict__ q, cons
   // Evaluated in one of two forms: FULL, when every lane of the warp has all MAXNC
   // slots within the cutoff and inside R - D (f_C = 1, f_C' = 0; the usual case of
   // diamond-like solids), with no bounds test per slot pair and the f_C factors
-  // compiled out; else the general form.  Both compute the same terms.
+  // compiled out; else the general form.  Both compute the same terms; the sums into
+  // Ab and e_i are explicit fma, so the terms the general form adds on top are exact
+  // zeros when f_C = 1 and f_C' = 0.  Callers that need an atom's result independent
+  // of the other atoms in its warp give each independent set of atoms its own warps.
   R zeta[MAXNC], dz[MAXNC], Ab[MAXNC], Fx[MAXNC], Fy[MAXNC], Fz[MAXNC];
   R e_i = R(0);
   auto evaluate = [&](auto full_c) {
@@ -697,10 +705,11 @@ k_force_reg(int ld, const dbl4 *__restrict__ x, const int4 *__restrict__ q, cons
         bond_order<M>(zeta[a], P, bij, dbij);
         const R bfA = bij * fA;
         const R pr = fR + bfA;
-        e_i += R(0.5) * FC(a) * pr;
+        e_i = fma(R(0.5) * FC(a), pr, e_i);
         // dV/dr of V = fc (fR + b fA)/2 at fixed zeta: fc' pr/2 - fc (lambda1 fR + lambda2 b fA)/2
-        if constexpr (FULL) Ab[a] = -(P.hlam1 * fR + P.hlam2 * bfA);
-        else Ab[a] = R(0.5) * DFC(a) * pr - FC(a) * (P.hlam1 * fR + P.hlam2 * bfA);
+        const R lam = fma(P.hlam1, fR, P.hlam2 * bfA);
+        if constexpr (FULL) Ab[a] = -lam;
+        else Ab[a] = fma(R(0.5) * DFC(a), pr, -(FC(a) * lam));
         dz[a] = R(0.5) * FC(a) * fA * dbij;
       }
     }
@@ -756,12 +765,11 @@ k_force_reg(int ld, const dbl4 *__restrict__ x, const int4 *__restrict__ q, cons
             const R S = (dz[a] * FC(b) + dz[b] * FC(a)) * dg;
             cj = S * ir(a);
             ck = S * ir(b);
-            if constexpr (FULL) {
-              Ab[a] -= cj * cost;
-              Ab[b] -= ck * cost;
-            } else {
-              Ab[a] += dz[b] * DFC(a) * g - cj * cost;
-              Ab[b] += dz[a] * DFC(b) * g - ck * cost;
+            Ab[a] = fma(-cj, cost, Ab[a]);
+            Ab[b] = fma(-ck, cost, Ab[b]);
+            if constexpr (!FULL) {
+              Ab[a] = fma(dz[b] * DFC(a), g, Ab[a]);
+              Ab[b] = fma(dz[a] * DFC(b), g, Ab[b]);
             }
           }
           Fx[a] -= cj * ux[b];
@@ -778,7 +786,8 @@ k_force_reg(int ld, const dbl4 *__restrict__ x, const int4 *__restrict__ q, cons
   if constexpr (HAS_FULL) {
     bool full = active && !over && nc == MAXNC && nc_all == MAXNC;
 #pragma unroll
-    for (int s = 0; s < MAXNC; ++s) full = full && fc[s] == R(1);
+    // f_C' = 0 too: near R - D the taper's f_C can round to 1 while its slope does not
+    for (int s = 0; s < MAXNC; ++s) full = full && fc[s] == R(1) && dfc(s) == R(0);
     if (__all_sync(0xffffffffu, full)) evaluate(std::true_type{});
     else evaluate(std::false_type{});
   } else {

@@ -45,16 +45,30 @@ __device__ __forceinline__ int range_of(const int *__restrict__ off, int n, int 
   return lo;
 }
 
-// Register-kernel route order of a set of systems: the systems' atoms back to back
-// (route_off ascending, route_off[k] the first position of system k, nsys systems),
-// position t holding atom atom_off[k] + (t - route_off[k]).
-__global__ void k_route_order(int n, const int *__restrict__ route_off, const int *__restrict__ atom_off, int nsys,
-                              int *__restrict__ order)
+// Register-kernel route order of nseg segments of atoms: segment k starts at
+// position route_off[k] (ascending) and holds atoms atom_off[k] .. atom_off[k] +
+// len[k] - 1; the positions between segments hold -1 (nothing to evaluate).
+__global__ void k_route_order(int n, const int *__restrict__ route_off, const int *__restrict__ atom_off,
+                              const int *__restrict__ len, int nseg, int *__restrict__ order)
 {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
-  const int k = range_of(route_off, nsys, t);
-  order[t] = atom_off[k] + (t - route_off[k]);
+  const int k = range_of(route_off, nseg, t);
+  const int u = t - route_off[k];
+  order[t] = u < len[k] ? atom_off[k] + u : -1;
+}
+
+// Largest in-cutoff count (bits of the in-cutoff mask) per system and atom type of
+// the atoms order[0, n).
+__global__ void k_type_ncmax(int n, const int *__restrict__ order, const int4 *__restrict__ q,
+                             const unsigned long long *__restrict__ mask, int *__restrict__ ncmax)
+{
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int i = order[t];
+  if (i < 0) return;
+  const int w = q[i].w;
+  atomicMax(&ncmax[sys_of(w) * MAX_TYPES + type_of(w)], __popcll(mask[i]));
 }
 
 // Survivors of a compaction: atom d of the new layout (survivors come first, dst_off
@@ -198,6 +212,8 @@ struct Job {
   std::vector<int32_t> types;
   bool one_species = false;   // every atom of one type: the 4-slot register route
   std::vector<int> perm;      // caller index of each stored atom (atoms grouped by type), or empty
+  int tcount[MAX_TYPES] = {0, 0, 0, 0};   // atoms of each type (stored in type order)
+  int cls[MAX_TYPES] = {8, 8, 8, 8};      // register-kernel slots of each type's atoms (multi-species jobs)
   double box[3] = {0, 0, 0};
   double dt = 0;
   int64_t nsteps = 0;
@@ -256,8 +272,9 @@ struct tersoff_server {
   // arithmetic does not depend on the batch.
   ForceRoutes routes{};         // every resident atom (the step graph)
   ForceRoutes new_routes{};     // the atoms of the jobs admitted last (their first force evaluation)
-  int *d_order = nullptr;       // [capacity] route order of every resident atom
-  int *d_order_new = nullptr;   // [capacity] route order of the newly admitted atoms
+  int *d_order = nullptr;       // [capacity + padding] route order of every resident atom
+  int *d_order_new = nullptr;   // [capacity + padding] route order of the newly admitted atoms
+  int *d_ncmax = nullptr;       // [max_slots + 1][MAX_TYPES] largest in-cutoff count per system and type
   std::vector<SysTab> tab;      // host copy of the system tables [max_slots + 1]
   std::vector<Job *> slot_job;  // resident job of each slot (owned by `jobs`; touched by the worker only)
   int64_t hw = 0;               // atoms [0, hw) hold every resident job (the rest of the range is freed atoms)
@@ -508,7 +525,11 @@ int build_and_force(tersoff_server *s)
 // atoms below the high-water mark pass a share of it, the layout is compacted:
 // survivors move down in address order, and every list and force is rebuilt.
 
-int TAB_INTS(const tersoff_server *s) { return 10 * (s->max_slots + 2); }   // ints of dtabs
+int TAB_INTS(const tersoff_server *s) { return 32 * (s->max_slots + 2); }   // ints of dtabs
+
+// most padding a route order holds: a warp's worth before each segment (a job, or one
+// type of a multi-species job) and before the 8-slot group
+int64_t route_pad(const tersoff_server *s) { return 32 * ((int64_t)s->max_slots * MAX_TYPES + 2); }
 
 constexpr double FREED_COMPACT_FRAC = 0.3;     // compact above this share of freed atoms below hw ...
 constexpr int64_t FREED_COMPACT_MIN = 1 << 16; // ... when they are at least this many
@@ -550,39 +571,59 @@ int layout_tables(tersoff_server *s)
   return TERSOFF_OK;
 }
 
-// Route table of the jobs js (one-species jobs first, each group in the given order)
-// appended to the host int table `it`; R gets the launches over order[0, total).
+// Route table of the jobs js appended to the host int table `it`: segments of atoms
+// (a one-species job, or the atoms of one type of a multi-species job, stored grouped
+// by type), those for 4 slots first, then those for 8, each group in job order; R
+// gets the launches over order[0, total).  A type of a multi-species job takes 4
+// slots when the job's first force evaluation saw at most 4 in-cutoff neighbours on
+// every atom of that type (classify), else 8 (8 until then).  Every segment starts a
+// warp (the positions between segments hold -1), so the atoms a warp evaluates
+// together, and the choice of route, depend on the job alone: its results do not
+// depend on the batch.
 void route_table(const std::vector<Job *> &js, int *order, std::vector<int> &it, size_t *at, int *nsys,
                  int64_t *total, ForceRoutes &R)
 {
-  std::vector<const Job *> o;
-  for (const Job *J : js)
-    if (J->one_species) o.push_back(J);
-  const size_t n4j = o.size();
-  for (const Job *J : js)
-    if (!J->one_species) o.push_back(J);
-  const int n = (int)o.size();
+  std::vector<std::pair<int64_t, int64_t>> s4, s8;   // (first atom, atoms)
+  for (const Job *J : js) {
+    if (J->one_species) {
+      s4.push_back({J->off, J->n});
+      continue;
+    }
+    int64_t o = J->off;
+    for (int t = 0; t < MAX_TYPES; ++t) {
+      if (!J->tcount[t]) continue;
+      (J->cls[t] == 4 ? s4 : s8).push_back({o, J->tcount[t]});
+      o += J->tcount[t];
+    }
+  }
+  const size_t n4s = s4.size();
+  s4.insert(s4.end(), s8.begin(), s8.end());
+  const int n = (int)s4.size();
   *at = it.size();
-  it.resize(it.size() + 2 * (size_t)n + 1);
-  int *ro = it.data() + *at, *ao = ro + n + 1;
-  int64_t pos = 0, n4 = 0;
+  it.resize(it.size() + 3 * (size_t)n + 1);
+  int *ro = it.data() + *at, *ao = ro + n + 1, *ln = ao + n;
+  auto warp_up = [](int64_t p) { return (p + 31) & ~(int64_t)31; };
+  int64_t pos = 0, end4 = 0;
   for (int k = 0; k < n; ++k) {
+    pos = warp_up(pos);
     ro[k] = (int)pos;
-    ao[k] = (int)o[k]->off;
-    pos += o[k]->n;
-    if ((size_t)k < n4j) n4 += o[k]->n;
+    ao[k] = (int)s4[k].first;
+    ln[k] = (int)s4[k].second;
+    pos += s4[k].second;
+    if ((size_t)k + 1 == n4s) end4 = pos;
   }
   ro[n] = (int)pos;
   *nsys = n;
   *total = pos;
   R = ForceRoutes{};
-  if (n4 > 0 && n4 < pos) {
+  if (n4s > 0 && n4s < (size_t)n) {
+    const int64_t b8 = warp_up(end4);
     R.n = 2;
-    R.r[0] = ForceRoute{order, 0, (int)n4, 4, 0};
-    R.r[1] = ForceRoute{order, (int)n4, (int)(pos - n4), 8, 0};
+    R.r[0] = ForceRoute{order, 0, (int)end4, 4, 0};
+    R.r[1] = ForceRoute{order, (int)b8, (int)(pos - b8), 8, 0};
   } else {
     R.n = 1;
-    R.r[0] = ForceRoute{order, 0, (int)pos, n4 > 0 ? 4 : 8, 0};
+    R.r[0] = ForceRoute{order, 0, (int)pos, n4s > 0 ? 4 : 8, 0};
   }
 }
 
@@ -632,6 +673,49 @@ int check_admission(tersoff_server *s)
     }
   }
   return srv_err(s, TERSOFF_ERR_NLIST_OVERFLOW, "admission did not converge");
+}
+
+// Register-kernel slots of the types of the new multi-species jobs, from their first
+// force evaluation (in-cutoff count = bits of each atom's mask), then the route order
+// of every resident atom again when a type moved to the 4-slot kernel.  Runs after
+// that evaluation's synchronisation (the admission's tables and staging are free).
+int classify(tersoff_server *s, const std::vector<Job *> &fresh, int64_t tot_new)
+{
+  bool multi = false;
+  for (const Job *J : fresh) multi = multi || !J->one_species;
+  if (!multi || tot_new == 0) return TERSOFF_OK;
+  const size_t nb = sizeof(int) * (size_t)(s->max_slots + 1) * MAX_TYPES;
+  SK(cudaMemsetAsync(s->d_ncmax, 0, nb, s->st));
+  AtomState &X = cur_atoms(s);
+  k_type_ncmax<<<(int)((tot_new + 255) / 256), 256, 0, s->st>>>((int)tot_new, s->d_order_new, X.q, s->SC.mask,
+                                                                 s->d_ncmax);
+  SK(cudaGetLastError());
+  std::vector<int> h((size_t)(s->max_slots + 1) * MAX_TYPES);
+  SK(cudaMemcpyAsync(h.data(), s->d_ncmax, nb, cudaMemcpyDeviceToHost, s->st));
+  SK(cudaStreamSynchronize(s->st));
+  bool changed = false;
+  for (Job *J : fresh) {
+    if (J->one_species) continue;
+    for (int t = 0; t < MAX_TYPES; ++t) {
+      const int c = J->tcount[t] && h[(size_t)J->slot * MAX_TYPES + t] <= 4 ? 4 : 8;
+      changed = changed || c != J->cls[t];
+      J->cls[t] = c;
+    }
+  }
+  if (!changed) return TERSOFF_OK;
+  std::vector<int> it;
+  size_t at = 0;
+  int ns = 0;
+  int64_t tot = 0;
+  route_table(resident(s), s->d_order, it, &at, &ns, &tot, s->routes);
+  SK(cudaMemcpy(s->dtabs, it.data(), sizeof(int) * it.size(), cudaMemcpyHostToDevice));
+  if (tot > 0) {
+    k_route_order<<<(int)((tot + 255) / 256), 256, 0, s->st>>>((int)tot, s->dtabs, s->dtabs + ns + 1,
+                                                               s->dtabs + 2 * ns + 1, ns, s->d_order);
+    SK(cudaGetLastError());
+  }
+  graph_free(s);
+  return TERSOFF_OK;
 }
 
 // Make the resident set of slot_job current on the device.  fresh: the jobs placed
@@ -733,13 +817,15 @@ int apply_layout(tersoff_server *s, const std::vector<Job *> &fresh, const std::
   s->pre_jobs.erase(s->pre_jobs.begin(), s->pre_jobs.begin() + npre);
   s->pre_off.erase(s->pre_off.begin(), s->pre_off.begin() + npre);
   if (tot_all > 0) {
-    k_route_order<<<(int)((tot_all + 255) / 256), 256, 0, s->st>>>((int)tot_all, s->dtabs + at_all,
-                                                                   s->dtabs + at_all + ns_all + 1, ns_all, s->d_order);
+    const int *t = s->dtabs + at_all;
+    k_route_order<<<(int)((tot_all + 255) / 256), 256, 0, s->st>>>((int)tot_all, t, t + ns_all + 1,
+                                                                   t + 2 * ns_all + 1, ns_all, s->d_order);
     SK(cudaGetLastError());
   }
-  if (tot_new > 0 && !compacted) {
-    k_route_order<<<(int)((tot_new + 255) / 256), 256, 0, s->st>>>(
-        (int)tot_new, s->dtabs + at_new, s->dtabs + at_new + ns_new + 1, ns_new, s->d_order_new);
+  if (tot_new > 0) {
+    const int *t = s->dtabs + at_new;
+    k_route_order<<<(int)((tot_new + 255) / 256), 256, 0, s->st>>>((int)tot_new, t, t + ns_new + 1,
+                                                                   t + 2 * ns_new + 1, ns_new, s->d_order_new);
     SK(cudaGetLastError());
   }
   if (compacted) s->cur = 1 - s->cur;
@@ -755,6 +841,7 @@ int apply_layout(tersoff_server *s, const std::vector<Job *> &fresh, const std::
     SKR(srv_force_new(s));
     SKR(check_admission(s));
   }
+  if (nnew > 0 && s->fast_slots > 0) SKR(classify(s, fresh, tot_new));
   if (nnew > 0) s->w_repacks += 1;
   return TERSOFF_OK;
 }
@@ -1219,8 +1306,13 @@ int tersoff_server_create(tersoff_ctx *ctx, const tersoff_params *P, tersoff_pre
       cudaMalloc((void **)&s->eatom, sizeof(double) * cap) != cudaSuccess ||
       cudaMalloc((void **)&s->sysE, sizeof(double) * 2 * max_slots) != cudaSuccess ||
       cudaMalloc((void **)&s->dtabs, sizeof(int) * (size_t)TAB_INTS(s)) != cudaSuccess ||
-      cudaMalloc((void **)&s->d_order, sizeof(int) * (size_t)std::max<int64_t>(cap, 1)) != cudaSuccess ||
-      cudaMalloc((void **)&s->d_order_new, sizeof(int) * (size_t)std::max<int64_t>(cap, 1)) != cudaSuccess) {
+      cudaMalloc((void **)&s->d_order, sizeof(int) * (size_t)(cap + route_pad(s))) != cudaSuccess ||
+      cudaMalloc((void **)&s->d_order_new, sizeof(int) * (size_t)(cap + route_pad(s))) != cudaSuccess ||
+      // the register-kernel queues cover the padded route orders
+      !dreserve(s->SC.work, s->SC.work_b,
+                (size_t)force_queue_blocks((int)(cap + route_pad(s))) * FAST_THREADS * sizeof(int)) ||
+      !dreserve(s->SC.nwork, s->SC.nwork_b, (size_t)force_queue_blocks((int)(cap + route_pad(s))) * sizeof(int)) ||
+      cudaMalloc((void **)&s->d_ncmax, sizeof(int) * (size_t)(max_slots + 1) * MAX_TYPES) != cudaSuccess) {
     cudaGetLastError();
     return fail(set_err(ctx, TERSOFF_ERR_NOMEM, "cannot allocate the packed layout for %lld atoms", (long long)cap));
   }
@@ -1261,6 +1353,7 @@ int tersoff_server_submit(tersoff_server *s, const tersoff_job *job, uint64_t *j
   for (int64_t i = 0; i < n; ++i)
     if (J->types[i] < 0 || J->types[i] >= s->P->nt) return reject(TERSOFF_ERR_ARG, "atom type out of range");
   J->one_species = std::all_of(J->types.begin(), J->types.end(), [&](int32_t t) { return t == J->types[0]; });
+  for (int64_t i = 0; i < n; ++i) J->tcount[J->types[i]] += 1;
   if (!J->one_species) {
     // atoms grouped by type (stable): the register kernel reads whole rows of the
     // per-atom arrays; results go back to the caller's order
@@ -1395,6 +1488,7 @@ void tersoff_server_destroy(tersoff_server *s)
   dfree(s->dtabs);
   dfree(s->d_order);
   dfree(s->d_order_new);
+  dfree(s->d_ncmax);
   dfree(s->rstage);
   if (s->hstage) cudaFreeHost(s->hstage);
   if (s->hres) cudaFreeHost(s->hres);
