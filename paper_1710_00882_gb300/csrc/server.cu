@@ -275,6 +275,7 @@ struct tersoff_server {
   int *d_order = nullptr;       // [capacity + padding] route order of every resident atom
   int *d_order_new = nullptr;   // [capacity + padding] route order of the newly admitted atoms
   int *d_ncmax = nullptr;       // [max_slots + 1][MAX_TYPES] largest in-cutoff count per system and type
+  int *h_ncmax = nullptr;       // its pinned host copy
   std::vector<SysTab> tab;      // host copy of the system tables [max_slots + 1]
   std::vector<Job *> slot_job;  // resident job of each slot (owned by `jobs`; touched by the worker only)
   int64_t hw = 0;               // atoms [0, hw) hold every resident job (the rest of the range is freed atoms)
@@ -654,12 +655,14 @@ int64_t place(std::vector<std::pair<int64_t, int64_t>> &ranges, int64_t n, int64
 // Status of an admission's list build and force evaluation: a list overflow grows
 // the lists and rebuilds every job (build_and_force); a neighbour count above the
 // general kernel's slots widens it.
-int check_admission(tersoff_server *s)
+int check_admission(tersoff_server *s, bool *recovered)
 {
+  *recovered = false;
   for (int attempt = 0; attempt < 4; ++attempt) {
     RunState h;
     SKR(read_state(s, &h));
     if (h.status == 0) return TERSOFF_OK;
+    *recovered = true;
     SK(cudaMemsetAsync(&s->rs->status, 0, sizeof(int), s->st));
     if (h.status & ST_NLIST_OVERFLOW) {
       SKR(build_and_force(s));
@@ -675,29 +678,38 @@ int check_admission(tersoff_server *s)
   return srv_err(s, TERSOFF_ERR_NLIST_OVERFLOW, "admission did not converge");
 }
 
-// Register-kernel slots of the types of the new multi-species jobs, from their first
-// force evaluation (in-cutoff count = bits of each atom's mask), then the route order
-// of every resident atom again when a type moved to the 4-slot kernel.  Runs after
-// that evaluation's synchronisation (the admission's tables and staging are free).
-int classify(tersoff_server *s, const std::vector<Job *> &fresh, int64_t tot_new)
+bool any_multi(const std::vector<Job *> &fresh)
 {
-  bool multi = false;
-  for (const Job *J : fresh) multi = multi || !J->one_species;
-  if (!multi || tot_new == 0) return TERSOFF_OK;
+  for (const Job *J : fresh)
+    if (!J->one_species) return true;
+  return false;
+}
+
+// Largest in-cutoff count per system and type of the new atoms (bits of their
+// in-cutoff masks, after their first force evaluation), copied to h_ncmax; the copy
+// is complete after the stream's next synchronisation.
+int count_enqueue(tersoff_server *s, int64_t tot_new)
+{
   const size_t nb = sizeof(int) * (size_t)(s->max_slots + 1) * MAX_TYPES;
   SK(cudaMemsetAsync(s->d_ncmax, 0, nb, s->st));
   AtomState &X = cur_atoms(s);
   k_type_ncmax<<<(int)((tot_new + 255) / 256), 256, 0, s->st>>>((int)tot_new, s->d_order_new, X.q, s->SC.mask,
                                                                  s->d_ncmax);
   SK(cudaGetLastError());
-  std::vector<int> h((size_t)(s->max_slots + 1) * MAX_TYPES);
-  SK(cudaMemcpyAsync(h.data(), s->d_ncmax, nb, cudaMemcpyDeviceToHost, s->st));
-  SK(cudaStreamSynchronize(s->st));
+  SK(cudaMemcpyAsync(s->h_ncmax, s->d_ncmax, nb, cudaMemcpyDeviceToHost, s->st));
+  return TERSOFF_OK;
+}
+
+// Register-kernel slots of the types of the new multi-species jobs from h_ncmax (at
+// most 4 in-cutoff neighbours on every atom of a type: 4 slots, else 8), then the
+// route order of every resident atom again when a type moved to the 4-slot kernel.
+int classify(tersoff_server *s, const std::vector<Job *> &fresh)
+{
   bool changed = false;
   for (Job *J : fresh) {
     if (J->one_species) continue;
     for (int t = 0; t < MAX_TYPES; ++t) {
-      const int c = J->tcount[t] && h[(size_t)J->slot * MAX_TYPES + t] <= 4 ? 4 : 8;
+      const int c = J->tcount[t] && s->h_ncmax[(size_t)J->slot * MAX_TYPES + t] <= 4 ? 4 : 8;
       changed = changed || c != J->cls[t];
       J->cls[t] = c;
     }
@@ -830,18 +842,31 @@ int apply_layout(tersoff_server *s, const std::vector<Job *> &fresh, const std::
   }
   if (compacted) s->cur = 1 - s->cur;
   graph_free(s);
+  // the new multi-species jobs' in-cutoff counts per type decide their routes
+  const bool counts = nnew > 0 && s->fast_slots > 0 && tot_new > 0 && any_multi(fresh);
   if (compacted) {
     SKR(build_and_force(s));
     s->w_compactions += 1;
+    if (counts) {
+      SKR(count_enqueue(s, tot_new));
+      SK(cudaStreamSynchronize(s->st));
+    }
   } else if (nnew > 0) {
-    // lists of the new jobs only (their rebuild flags), then their first forces
+    // lists of the new jobs only (their rebuild flags), then their first forces and
+    // in-cutoff counts, read at one synchronisation
     SK(cudaMemsetAsync(&s->rs->maxcount, 0, sizeof(int), s->st));
     SKR(srv_build(s, s->st, false));
     SK(cudaMemcpyAsync(s->S.ctl, h + b_tab + b_ctl, b_ctl, cudaMemcpyHostToDevice, s->st));
     SKR(srv_force_new(s));
-    SKR(check_admission(s));
+    if (counts) SKR(count_enqueue(s, tot_new));
+    bool recovered = false;
+    SKR(check_admission(s, &recovered));
+    if (counts && recovered) {
+      SKR(count_enqueue(s, tot_new));
+      SK(cudaStreamSynchronize(s->st));
+    }
   }
-  if (nnew > 0 && s->fast_slots > 0) SKR(classify(s, fresh, tot_new));
+  if (counts) SKR(classify(s, fresh));
   if (nnew > 0) s->w_repacks += 1;
   return TERSOFF_OK;
 }
@@ -1321,6 +1346,9 @@ int tersoff_server_create(tersoff_ctx *ctx, const tersoff_params *P, tersoff_pre
   // staging of queued jobs while chunks run: about 30 MB of pinned memory (without
   // it, admissions stage every job themselves)
   pinned_reserve(s->hpre, s->hpre_b, (size_t)24 << 20);
+  if (cudaHostAlloc((void **)&s->h_ncmax, sizeof(int) * (size_t)(max_slots + 1) * MAX_TYPES, cudaHostAllocDefault) !=
+      cudaSuccess)
+    return fail(set_err(ctx, TERSOFF_ERR_NOMEM, "pinned counts"));
   if (cudaStreamSynchronize(s->st) != cudaSuccess) return fail(set_err(ctx, TERSOFF_ERR_CUDA, "server set-up"));
   s->stats.capacity_atoms = cap;
   s->worker = std::thread(worker_loop, s);
@@ -1493,6 +1521,7 @@ void tersoff_server_destroy(tersoff_server *s)
   if (s->hstage) cudaFreeHost(s->hstage);
   if (s->hres) cudaFreeHost(s->hres);
   if (s->hpre) cudaFreeHost(s->hpre);
+  if (s->h_ncmax) cudaFreeHost(s->h_ncmax);
   if (s->ev_res) cudaEventDestroy(s->ev_res);
   if (s->st) cudaStreamDestroy(s->st);
   if (s->cap_st) cudaStreamDestroy(s->cap_st);
