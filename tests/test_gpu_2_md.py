@@ -263,3 +263,23 @@ def test_float64_accumulation_variant(T, ctx, monkeypatch):
     assert np.abs(fa_ - fb).max() < 1e-10
     Eo, Fo, _ = oracle.energy_forces(pb, s.types, s.box, tab)
     assert np.abs(fb - Fo).max() < MIX_F_ABS
+
+
+@pytest.mark.parametrize("kind", ["si", "sic"])
+def test_forces_after_rebuilds_match_a_fresh_evaluation(T, ctx, kind):
+    """After many list rebuilds (per-type radii, sorted lists, reverse indices, the
+    atoms of SiC grouped by type) the MD state's forces equal an evaluation of the same
+    positions with a fresh list, in the caller's atom order."""
+    if kind == "si":
+        s, dt = wl.si_box(6, 6, 6, seed=51, T=1500.0), 1e-3
+    else:
+        s, dt = wl.sic_box(5, seed=52, T=1500.0), 0.5e-3
+    P = product_params(ctx, s.species)
+    md = T.MD(ctx, P, s.pos, s.vel, s.types, s.box, dt=dt, skin=0.3, prec=T.FP64)
+    md.step(120)
+    assert md.stats()["rebuilds"] >= 4
+    pos, _, f_md = md.get(forces=True)
+    _, f_fresh, _ = T.compute(ctx, P, pos, s.types, s.box, prec=T.FP64)
+    scale = np.abs(f_fresh).max()
+    assert np.abs(f_md - f_fresh).max() <= 1e-12 * scale
+
