@@ -165,8 +165,11 @@ int tersoff_compute(tersoff_ctx *ctx, const double *pos, const int32_t *types, i
  * [nsteps+1][2]) receives (potential, kinetic) energy in eV after each step,
  * row 0 = the state before the call.  tersoff_md_step_async only enqueues the
  * steps on the context's stream (no trace, no error check; follow with
- * tersoff_md_sync).  tersoff_md_get copies positions/velocities out (host or,
- * with TERSOFF_DEVICE_PTRS, device buffers). */
+ * tersoff_md_sync).  tersoff_md_get copies positions/velocities (and the forces of
+ * the last evaluation) out (host or, with TERSOFF_DEVICE_PTRS, device buffers), in
+ * the caller's atom order: a state with several atom types stores its atoms
+ * grouped by type, in an order fixed by the types alone, so a state read out and
+ * created again continues bitwise as the original would have. */
 int tersoff_md_create(tersoff_ctx *ctx, const double *pos, const double *vel, const int32_t *types, int64_t N,
                       const double box[3], const tersoff_params *params, double dt_ps, double skin,
                       tersoff_precision prec, int flags, tersoff_md **out);
