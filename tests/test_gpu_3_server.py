@@ -182,7 +182,7 @@ def test_close_with_jobs_in_flight(T, ctx, P):
 
 
 def test_many_jobs_admitted_together(T, ctx, P):
-    """A stream of jobs queued at once: many new systems enter one repack, jobs
+    """A stream of jobs queued at once: many new systems enter one admission, jobs
     leave at different chunks, and a sample of them matches its run alone bitwise."""
     stream = wl.serving_stream(48, seed=7, max_atoms=3000)
     jobs = [(j.system, j.dt, j.steps) for j in stream]
