@@ -134,6 +134,31 @@ def test_freed_ranges_and_compaction_keep_results(T, ctx, P, monkeypatch):
             assert np.array_equal(p, pr) and np.array_equal(v, vr) and e == er
 
 
+def test_tiny_jobs_in_a_mix(T, ctx, P):
+    """Jobs of one, two and three atoms (a lone atom drifts, a dimer and an Si-C pair
+    vibrate) next to a bulk job: each route segment is a fraction of a warp, and every
+    result matches the same job run alone (bitwise) and the FP64 oracle."""
+    box = np.array([12.0, 12.0, 12.0])
+    def job(pos, types, vel, n=40):
+        s = wl.System(pos=np.array(pos, float), types=np.array(types, np.int32), box=box, species=("Si", "C"),
+                      vel=np.array(vel, float))
+        return (s, 0.5e-3, n)
+    tiny = [job([[1.0, 2.0, 3.0]], [0], [[0.5, -0.2, 0.1]]),
+            job([[5.0, 5.0, 5.0], [7.3, 5.0, 5.0]], [0, 0], [[0.0, 0.0, 0.0], [0.0, 0.0, 0.0]]),
+            job([[5.0, 5.0, 5.0], [6.8, 5.3, 5.0]], [0, 1], [[0.1, 0.0, 0.0], [-0.2, 0.0, 0.0]]),
+            job([[5.0, 5.0, 5.0], [7.3, 5.0, 5.0], [4.2, 7.2, 5.0]], [0, 1, 0], [[0.0] * 3] * 3)]
+    jobs = tiny + [jobs_mix()[1]]
+    mixed, st = run_jobs(T, ctx, P, jobs, T.FP64, chunk=7)
+    assert st["completed"] == len(jobs) and st["failed"] == 0
+    tab, m = oracle_table(("Si", "C"))
+    for k, (s, dt, n) in enumerate(tiny):
+        alone, _ = run_jobs(T, ctx, P, [(s, dt, n)], T.FP64, chunk=11)
+        assert np.array_equal(alone[0][0], mixed[k][0]) and np.array_equal(alone[0][1], mixed[k][1])
+        po, vo, tro = oracle.md_run(s.pos, s.vel, s.types, s.box, tab, m, dt, n)
+        assert np.abs(mixed[k][0] - po).max() < 1e-9
+        assert np.abs(mixed[k][1] - vo).max() < 1e-8
+
+
 def test_wait_timeout_poll_and_errors(T, ctx, P):
     srv = T.Server(ctx, P, prec=T.MIXED, skin=0.3, budget_bytes=1 << 26, max_slots=4, chunk_steps=50)
     s = wl.si_box(4, 4, 4, seed=41, T=1000.0)
