@@ -252,9 +252,11 @@ int tersoff_compute_noalloc(const tersoff_params *params, const double *pos, con
  * forces are computed on admission; the layout is compacted (resident jobs moved,
  * every list rebuilt) only when no free range holds a new job or freed atoms pass
  * 30% of the occupied range (environment TERSOFF_COMPACT_FREED=f sets that share).
- * A job's trajectory does not depend on the other jobs in the batch or on where it
- * sits (same arithmetic, same order): its result is bitwise the same alone and in
- * any mix.
+ * A job with several atom types is stored grouped by type and each type is routed
+ * to the register kernel its own first force evaluation calls for; results come
+ * back in the caller's atom order.  A job's trajectory does not depend on the other
+ * jobs in the batch or on where it sits (same arithmetic, same order, its own warps):
+ * its result is bitwise the same alone and in any mix.
  *
  * params: shared by all jobs (job types index into it).  prec: precision of all
  * jobs.  skin: Verlet skin (A).  device_mem_budget: bytes the packed layout may
