@@ -10,6 +10,7 @@ namespace tsf {
 __global__ void __launch_bounds__(1024) k_reduce_partials(const double *__restrict__ partial, int n, RunState *rs)
 {
   __shared__ double sh[32][7];
+  griddep_wait();
   if (rs->status != 0) return;
   double a[7] = {0, 0, 0, 0, 0, 0, 0};
   for (int k = threadIdx.x; k < n; k += 1024)
@@ -85,8 +86,7 @@ cudaError_t launch_force_part(int part, cudaStream_t st, int prec, int fast_slot
                     contrib, selfF, mask, work, nwork, partial, rs, eatom, routes, stats, &rows);
   if (e != cudaSuccess) return e;
   if ((eflag || vflag) && rows > 0 && (part & 2)) {
-    k_reduce_partials<<<1, 1024, 0, st>>>(partial, rows, rs);
-    e = cudaGetLastError();
+    e = launch_dep(k_reduce_partials, 1, 1024, 0, st, (const double *)partial, rows, rs);
   }
   return e;
 }

@@ -294,6 +294,7 @@ k_force_reg(int ld, const dbl4 *__restrict__ x, const int4 *__restrict__ q, cons
   __shared__ TripP<R> strips[KIND == 0 ? MAX_TYPES * MAX_TYPES * MAX_TYPES : 1];
   __shared__ int warp_over[T / 32];
 
+  griddep_wait();
   if (rs->status != 0) return;   // uniform across the grid
   if constexpr (KIND == 0) {
     if (threadIdx.x < nt * nt) spairs[threadIdx.x] = gpairs[threadIdx.x];
@@ -1168,6 +1169,7 @@ k_force_warp(int ld, const dbl4 *__restrict__ x, const int4 *__restrict__ q, con
   __shared__ int smeta[NW][WSLOTS];
   __shared__ int qoff[GEN_SUB + 1];
 
+  griddep_wait();
   if (rs->status != 0) return;   // uniform across the grid
   if (rs->over_total == 0) {
     // no atom was queued: leave zero partial sums and stop
@@ -1499,19 +1501,9 @@ static cudaError_t launch_warp(cudaStream_t st, int eflag, int vflag, int ld, co
   using P = const PairP<R> *;
   using Tt = const TripP<R> *;
   using V = typename V4t<R>::type *;
-  if (vflag)
-    k_force_warp<M, true, true><<<GEN_BLOCKS, WARP_BLOCK, 0, st>>>(ld, x, q, nbr, cnt, sys, (P)pairs, (Tt)trips, nt,
-                                                                   (V)contrib, (V)selfF, mask, work, nwork, nfast,
-                                                                   partial, rs, eatom);
-  else if (eflag)
-    k_force_warp<M, true, false><<<GEN_BLOCKS, WARP_BLOCK, 0, st>>>(ld, x, q, nbr, cnt, sys, (P)pairs, (Tt)trips, nt,
-                                                                    (V)contrib, (V)selfF, mask, work, nwork, nfast,
-                                                                    partial, rs, eatom);
-  else
-    k_force_warp<M, false, false><<<GEN_BLOCKS, WARP_BLOCK, 0, st>>>(ld, x, q, nbr, cnt, sys, (P)pairs, (Tt)trips, nt,
-                                                                     (V)contrib, (V)selfF, mask, work, nwork, nfast,
-                                                                     partial, rs, eatom);
-  return cudaGetLastError();
+  auto k = vflag ? k_force_warp<M, true, true> : eflag ? k_force_warp<M, true, false> : k_force_warp<M, false, false>;
+  return launch_dep(k, GEN_BLOCKS, WARP_BLOCK, 0, st, ld, x, q, nbr, cnt, sys, (P)pairs, (Tt)trips, nt, (V)contrib,
+                    (V)selfF, mask, work, nwork, nfast, partial, rs, eatom);
 }
 
 // the kernel-argument table of the precision R
@@ -1547,19 +1539,11 @@ static cudaError_t launch_reg(cudaStream_t st, int eflag, int vflag, int ld, con
   static const int pf_v = wave(k_force_reg<M, MAXNC, KIND, true, true>);
   static const int pf_e = wave(k_force_reg<M, MAXNC, KIND, true, false>);
   static const int pf_0 = wave(k_force_reg<M, MAXNC, KIND, false, false>);
-  if (vflag)
-    k_force_reg<M, MAXNC, KIND, true, true><<<blocks, FAST_THREADS, 0, st>>>(
-        ld, x, q, nbr, cnt, sys, (P)pairs, (Tt)trips, nt, kp, (V)contrib, (V)selfF, mask, work, nwork, partial, rs,
-        eatom, rt.order, rt.begin, rt.count, rt.block_base, stats, pf_v);
-  else if (eflag)
-    k_force_reg<M, MAXNC, KIND, true, false><<<blocks, FAST_THREADS, 0, st>>>(
-        ld, x, q, nbr, cnt, sys, (P)pairs, (Tt)trips, nt, kp, (V)contrib, (V)selfF, mask, work, nwork, partial, rs,
-        eatom, rt.order, rt.begin, rt.count, rt.block_base, stats, pf_e);
-  else
-    k_force_reg<M, MAXNC, KIND, false, false><<<blocks, FAST_THREADS, 0, st>>>(
-        ld, x, q, nbr, cnt, sys, (P)pairs, (Tt)trips, nt, kp, (V)contrib, (V)selfF, mask, work, nwork, partial, rs,
-        eatom, rt.order, rt.begin, rt.count, rt.block_base, stats, pf_0);
-  return cudaGetLastError();
+  auto k = vflag ? k_force_reg<M, MAXNC, KIND, true, true>
+                 : eflag ? k_force_reg<M, MAXNC, KIND, true, false> : k_force_reg<M, MAXNC, KIND, false, false>;
+  return launch_dep(k, blocks, FAST_THREADS, 0, st, ld, x, q, nbr, cnt, sys, (P)pairs, (Tt)trips, nt, kp, (V)contrib,
+                    (V)selfF, mask, work, nwork, partial, rs, eatom, rt.order, rt.begin, rt.count, rt.block_base, stats,
+                    vflag ? pf_v : eflag ? pf_e : pf_0);
 }
 
 // The force kernels of one evaluation in the precision of M (launch_force_part in

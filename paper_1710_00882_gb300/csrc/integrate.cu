@@ -360,6 +360,7 @@ __global__ void k_permute_atoms(int N, const int *__restrict__ perm, const dbl4 
 // per-system step control.
 __global__ void k_step_end(RunState *rs, SysCtl *ctl, int nsys, cudaGraphConditionalHandle loop, int use_cond)
 {
+  griddep_wait();
   if (rs->status != 0) {
     if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(loop, 0);
     return;
@@ -419,6 +420,7 @@ __global__ void k_loop_start(RunState *rs, SysCtl *ctl, long long steps, double 
 // after the integrator of a step: rebuild the list in this step?
 __global__ void k_decide(RunState *rs, cudaGraphConditionalHandle build)
 {
+  griddep_wait();
   cudaGraphSetConditional(build, (rs->status == 0 && rs->rebuild != 0) ? 1u : 0u);
 }
 
@@ -549,8 +551,7 @@ cudaError_t launch_permute_atoms(cudaStream_t st, int N, const int *perm, const 
 cudaError_t launch_step_end(cudaStream_t st, RunState *rs, SysCtl *ctl, int nsys, cudaGraphConditionalHandle loop,
                             int use_cond)
 {
-  k_step_end<<<1, nsys > 1 ? 256 : 32, 0, st>>>(rs, ctl, nsys, loop, use_cond);
-  return cudaGetLastError();
+  return launch_dep(k_step_end, 1, nsys > 1 ? 256 : 32, 0, st, rs, ctl, nsys, loop, use_cond);
 }
 
 cudaError_t launch_loop_start(cudaStream_t st, RunState *rs, SysCtl *ctl, long long steps, double *trace,
@@ -577,8 +578,7 @@ cudaError_t set_loop_start(cudaGraphExec_t exec, cudaGraphNode_t node, RunState 
 
 cudaError_t launch_decide(cudaStream_t st, RunState *rs, cudaGraphConditionalHandle build)
 {
-  k_decide<<<1, 1, 0, st>>>(rs, build);
-  return cudaGetLastError();
+  return launch_dep(k_decide, 1, 1, 0, st, rs, build);
 }
 
 cudaError_t launch_set_control(cudaStream_t st, RunState *rs, SysCtl *ctl, long long steps, double *trace,

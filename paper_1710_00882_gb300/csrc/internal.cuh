@@ -123,6 +123,55 @@ struct ForceRoutes {
 // Ask L2 for the line holding p (no register result, no wait).
 __device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
+// Programmatic dependent launch.  A kernel launched with launch_dep while pdl_scope
+// is active and its stream is being captured right behind a single kernel node may be
+// scheduled before that kernel has drained; its first statement, griddep_wait(), holds
+// it until that kernel has completed and its writes are visible (in a kernel launched
+// the ordinary way it returns at once).  Every kernel launched with launch_dep calls
+// griddep_wait() ahead of any global memory access.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+struct PdlFlag {
+  static bool &on()
+  {
+    static thread_local bool f = false;
+    return f;
+  }
+};
+// Active for its lifetime on this host thread (graph captures of the step loop).
+struct pdl_scope {
+  bool prev;
+  pdl_scope() : prev(PdlFlag::on()) { PdlFlag::on() = true; }
+  ~pdl_scope() { PdlFlag::on() = prev; }
+};
+
+template <typename... K, typename... A>
+inline cudaError_t launch_dep(void (*kernel)(K...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, A... args)
+{
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 0;
+  if (PdlFlag::on()) {
+    // only behind exactly one kernel node of the graph being captured
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    cudaGraphNodeType ty = cudaGraphNodeTypeEmpty;
+    if (cudaStreamGetCaptureInfo(st, &cs, nullptr, nullptr, &deps, nullptr, &nd) == cudaSuccess &&
+        cs == cudaStreamCaptureStatusActive && nd == 1 && cudaGraphNodeGetType(deps[0], &ty) == cudaSuccess &&
+        ty == cudaGraphNodeTypeKernel)
+      cfg.numAttrs = 1;
+  }
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // minimum-image difference of two fixed-point coordinates, in units of L / 2^32
 __host__ __device__ __forceinline__ int qdiff(int qj, int qi)
 {

@@ -92,6 +92,7 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *total)
 __global__ void k_scan_tiles(int n, const int *__restrict__ in, int *__restrict__ out, int *__restrict__ tile_sums,
                              const RunState *rs, int gated)
 {
+  griddep_wait();
   if (skip_build(rs, gated)) return;
   int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
   int v[SCAN_ITEMS], s = 0;
@@ -114,6 +115,7 @@ __global__ void k_scan_tiles(int n, const int *__restrict__ in, int *__restrict_
 __global__ void k_scan_sums(int ntiles, int *__restrict__ tile_sums, int *__restrict__ grand_total,
                             const RunState *rs, int gated)
 {
+  griddep_wait();
   if (skip_build(rs, gated)) return;
   int carry = 0;
   for (int base = 0; base < ntiles; base += SCAN_TILE) {
@@ -140,6 +142,7 @@ __global__ void k_scan_sums(int ntiles, int *__restrict__ tile_sums, int *__rest
 __global__ void k_scan_add(int n, int *__restrict__ out, const int *__restrict__ tile_sums, int *__restrict__ counts,
                            const RunState *rs, int gated)
 {
+  griddep_wait();
   if (skip_build(rs, gated)) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -153,6 +156,7 @@ __global__ void k_cell_fill(int N, const int4 *__restrict__ q, const int *__rest
                             const int *__restrict__ rank, const int *__restrict__ cell_start,
                             int4 *__restrict__ cell_atoms, const RunState *rs, int gated)
 {
+  griddep_wait();
   if (skip_build(rs, gated)) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
@@ -224,6 +228,7 @@ __global__ void __launch_bounds__(128, 12) k_build(int ld, int ncell, const int4
                                                int *__restrict__ cnt, int cap, int4 *__restrict__ qref, RunState *rs,
                                                int gated)
 {
+  griddep_wait();
   if (skip_build(rs, gated)) return;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= cell_start[ncell]) return;   // atoms with a cell (systems that get new lists)
@@ -339,6 +344,7 @@ __global__ void __launch_bounds__(128) k_sort_lists(int N, int ld, const int4 *_
                                                     RunState *rs, int gated)
 {
   __shared__ int sbuf[32][128];
+  griddep_wait();
   if (skip_build(rs, gated)) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N || cell_of[i] < 0) return;
@@ -414,6 +420,7 @@ __global__ void k_reverse(int N, int ld, const int4 *__restrict__ q, const SysCt
                           const int *__restrict__ cell_of, const int *__restrict__ nbr, const int *__restrict__ cnt,
                           int *__restrict__ rev, RunState *rs, int gated)
 {
+  griddep_wait();
   if (skip_build(rs, gated)) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N || cell_of[i] < 0) return;
@@ -474,6 +481,7 @@ __global__ void k_reverse(int N, int ld, const int4 *__restrict__ q, const SysCt
 // close a build: count it, clear the request
 __global__ void k_build_done(RunState *rs, int gated)
 {
+  griddep_wait();
   if (skip_build(rs, gated)) return;
   rs->nrebuild += 1;
   rs->rebuild = 0;
@@ -499,23 +507,35 @@ cudaError_t launch_build(cudaStream_t st, int N, int ld, const int4 *q, const Sy
   const int BN = (N + T - 1) / T;
   const int ntiles = (ncell + SCAN_TILE - 1) / SCAN_TILE;
   k_cell_count<<<BN, T, 0, st>>>(N, q, sys, ctl, cell_of, rank, cell_count, cnt, rs, gated);
-  k_scan_tiles<<<ntiles, SCAN_THREADS, 0, st>>>(ncell, cell_count, cell_start, tile_sums, rs, gated);
-  k_scan_sums<<<1, SCAN_THREADS, 0, st>>>(ntiles, tile_sums, cell_start + ncell, rs, gated);
-  k_scan_add<<<(ncell + T - 1) / T, T, 0, st>>>(ncell, cell_start, tile_sums, cell_count, rs, gated);
-  k_cell_fill<<<BN, T, 0, st>>>(N, q, cell_of, rank, cell_start, cell_atoms, rs, gated);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if ((e = launch_dep(k_scan_tiles, ntiles, SCAN_THREADS, 0, st, ncell, (const int *)cell_count, cell_start, tile_sums,
+                      (const RunState *)rs, gated)) != cudaSuccess)
+    return e;
+  if ((e = launch_dep(k_scan_sums, 1, SCAN_THREADS, 0, st, ntiles, tile_sums, cell_start + ncell,
+                      (const RunState *)rs, gated)) != cudaSuccess)
+    return e;
+  if ((e = launch_dep(k_scan_add, (ncell + T - 1) / T, T, 0, st, ncell, cell_start, (const int *)tile_sums, cell_count,
+                      (const RunState *)rs, gated)) != cudaSuccess)
+    return e;
+  if ((e = launch_dep(k_cell_fill, BN, T, 0, st, N, q, (const int *)cell_of, (const int *)rank,
+                      (const int *)cell_start, cell_atoms, (const RunState *)rs, gated)) != cudaSuccess)
+    return e;
   const int BN128 = (N + 127) / 128;
   // one radius for every type pair (one-type tables, or lists built with one cutoff):
   // the row's largest radius decides alone
   bool typed = false;
   for (int k = 1; k < MAX_TYPES * MAX_TYPES; ++k) typed = typed || radii.rl2[k] != radii.rl2[0];
-  if (typed)
-    k_build<true><<<BN128, 128, 0, st>>>(ld, ncell, q, sys, ctl, radii, cell_start, cell_atoms, nbr, cnt, cap, qref, rs, gated);
-  else
-    k_build<false><<<BN128, 128, 0, st>>>(ld, ncell, q, sys, ctl, radii, cell_start, cell_atoms, nbr, cnt, cap, qref, rs, gated);
-  k_sort_lists<<<BN128, 128, 0, st>>>(N, ld, q, ctl, cell_of, nbr, cnt, cap, rs, gated);
-  k_reverse<<<BN128, 128, 0, st>>>(N, ld, q, ctl, cell_of, nbr, cnt, rev, rs, gated);
-  k_build_done<<<1, 1, 0, st>>>(rs, gated);
-  return cudaGetLastError();
+  if ((e = launch_dep(typed ? k_build<true> : k_build<false>, BN128, 128, 0, st, ld, ncell, q, sys, ctl, radii,
+                      (const int *)cell_start, (const int4 *)cell_atoms, nbr, cnt, cap, qref, rs, gated)) != cudaSuccess)
+    return e;
+  if ((e = launch_dep(k_sort_lists, BN128, 128, 0, st, N, ld, q, ctl, (const int *)cell_of, nbr, cnt, cap, rs,
+                      gated)) != cudaSuccess)
+    return e;
+  if ((e = launch_dep(k_reverse, BN128, 128, 0, st, N, ld, q, ctl, (const int *)cell_of, (const int *)nbr,
+                      (const int *)cnt, rev, rs, gated)) != cudaSuccess)
+    return e;
+  return launch_dep(k_build_done, 1, 1, 0, st, rs, gated);
 }
 
 int scan_tiles_for(int ncell) { return (ncell + SCAN_TILE - 1) / SCAN_TILE; }

@@ -901,6 +901,8 @@ static int md_graph_build(tersoff_md *md, int which)
   const bool tr = which == 1;
   MdGraph &G = md->graph[which];
   cudaStream_t st = md->cap_stream;
+  // kernels captured right behind another kernel become programmatic dependents
+  pdl_scope pdl;
   const cudaStreamCaptureMode mode = cudaStreamCaptureModeRelaxed;
   cudaGraph_t g = nullptr;
   CK(cudaGraphCreate(&g, 0));

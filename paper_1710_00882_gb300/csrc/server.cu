@@ -438,6 +438,8 @@ int graph_build(tersoff_server *s)
   graph_free(s);
   cudaStream_t st = s->cap_st;
   const cudaStreamCaptureMode mode = cudaStreamCaptureModeRelaxed;
+  // kernels captured right behind another kernel become programmatic dependents
+  pdl_scope pdl;
   cudaGraph_t g = nullptr;
   SK(cudaGraphCreate(&g, 0));
   s->g = g;
