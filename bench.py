@@ -8,8 +8,10 @@ evaluation).  The headline is mixed precision; the FP64 path is timed the same
 way and reported beside it.
 
 Timing: one graph launch per timed step, CUDA events on the library's stream
-around each, and a 256 MB buffer written on the same stream between steps so every
-step starts with a cold L2 (the flush is outside the events).  The same state run
+around each, and between steps (outside the events) a 256 MB buffer written and
+then another 256 MB read on the same stream, so every step starts with none of
+its data in L2 and no dirty lines there to write back.  Steps after a flush that
+only writes are timed beside it for comparison.  The same state run
 as K steps in one graph launch (as tersoff_md_step runs them) is reported beside
 it as "one_launch".  Under torchrun each rank runs its own
 replica of the workload on its own GPU (the path does not shard across GPUs);
@@ -220,12 +222,24 @@ def run_gpu(args, ws, rank, local):
     si = pp.SILICON
     n_list, npair, ntaper, ntrip = workload_counts(s, P.cutoff, si.R1)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
+    flush_r = torch.ones(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
+    flush_sink = torch.zeros(1, dtype=torch.float32, device=f"cuda:{local}")
 
-    def timed(prec, steps, warmup, sysm=None, params=None, dt=DT):
+    def flush_l2(k, read=True):
+        """On the current stream: write 256 MB, then read another 256 MB, so that the next
+        step finds none of its data in L2 and no dirty lines there either (after the write
+        alone, the step's first kernel would also write back ~129 MB of the flush's lines
+        as it evicts them)."""
+        flush.fill_(float(k))
+        if read:
+            flush_sink.add_(flush_r.sum())
+
+    def timed(prec, steps, warmup, sysm=None, params=None, dt=DT, write_only=0):
         """K steps as one graph launch (the way the library runs MD) bracketed by CUDA
         events after an L2 flush; then the timed steps of the headline, one graph launch
         each with L2 flushed before it; then a profiled pass (kernel by kernel, events
-        around each phase) for the per-kernel times the roofline uses."""
+        around each phase) for the per-kernel times the roofline uses.  write_only > 0:
+        that many more steps, each after a flush that only writes (for comparison)."""
         sysm = s if sysm is None else sysm
         md = T.MD(ctx, P if params is None else params, sysm.pos, sysm.vel, sysm.types, sysm.box, dt=dt, skin=SKIN,
                   prec=prec)
@@ -234,7 +248,7 @@ def run_gpu(args, ws, rank, local):
         st0 = md.stats()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with torch.cuda.stream(stream):
-            flush.fill_(-1.0)
+            flush_l2(-1)
         barrier(ws)
         torch.cuda.synchronize()
         with torch.cuda.stream(stream):
@@ -255,7 +269,7 @@ def run_gpu(args, ws, rank, local):
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nflush)]
         for k in range(nflush):
             with torch.cuda.stream(stream):
-                flush.fill_(float(k))
+                flush_l2(k)
                 torch.cuda._sleep(SPIN_CYCLES)
                 evs[k][0].record(stream)
             md.step_async(1)
@@ -265,11 +279,27 @@ def run_gpu(args, ws, rank, local):
         ms_flushed = [a.elapsed_time(b) for a, b in evs]
         md.sync()
         st2 = md.stats()
+        ms_write_only = []
+        if write_only > 0:
+            evw = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(write_only)]
+            for k in range(write_only):
+                with torch.cuda.stream(stream):
+                    flush_l2(k, read=False)
+                    torch.cuda._sleep(SPIN_CYCLES)
+                    evw[k][0].record(stream)
+                md.step_async(1)
+                with torch.cuda.stream(stream):
+                    evw[k][1].record(stream)
+            torch.cuda.synchronize()
+            ms_write_only = [a.elapsed_time(b) for a, b in evw]
+            md.sync()
+        st3 = md.stats()
         md.profile(True)
         nprof = max(10, min(steps, 40))
         for k in range(nprof):
             with torch.cuda.stream(stream):
-                flush.fill_(float(k))
+                flush_l2(k)
             md.step_async(1)
         prof = md.profile_read()
         md.profile(False)
@@ -282,12 +312,14 @@ def run_gpu(args, ws, rank, local):
         final = {"pos": pos_f, "forces": f_f, "energy": pe_f, "types": sysm.types, "box": sysm.box,
                  "species": sysm.species}
         return ms_total, ms_flushed, prof, dict(rebuilds=rebuilds, rebuilds_flushed=st2["rebuilds"] - st1["rebuilds"],
+                                                ms_write_only=ms_write_only,
+                                                rebuilds_write_only=st3["rebuilds"] - st2["rebuilds"],
                                                 steps=steps, prof_steps=nprof, final=final), md
 
     clocks = ClockSampler(local)
     clocks.start()
     k_mix, k_64 = args.steps, max(3, args.steps // 4)
-    one_mix, fl_mix, prof_mix, st_mix, md_mix = timed(T.MIXED, k_mix, args.warmup)
+    one_mix, fl_mix, prof_mix, st_mix, md_mix = timed(T.MIXED, k_mix, args.warmup, write_only=k_mix)
     one_64, fl_64, prof_64, st_64, md_64 = timed(T.FP64, k_64, args.warmup)
     one_sg, fl_sg, prof_sg, st_sg, md_sg = timed(T.SINGLE, k_mix, args.warmup)
     md_mix = md_64 = md_sg = None
@@ -419,7 +451,8 @@ def run_gpu(args, ws, rank, local):
         "dtype": "f32+f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "atoms": s.n, "precision": "mixed",
-                   "l2": "flushed before every timed step (256 MB write outside the events)",
+                   "l2": "flushed before every timed step (outside the events): 256 MB written, then another "
+                         "256 MB read, so no line of the step's data and no dirty line is left in L2",
                    "parallelism": "replicas" if ws > 1 else "single GPU",
                    "step_launch": "one CUDA graph launch per timed step (WHILE over steps, IF around the "
                                   "list rebuild)"},
@@ -455,6 +488,14 @@ def run_gpu(args, ws, rank, local):
                           "ms_per_step": one_mix / k_mix, "rebuilds": st_mix["rebuilds"],
                           "how": "the same state, K steps as one graph launch as tersoff_md_step runs them; L2 "
                                  "flushed once before (per-step working set ~125 MB, about the L2 size)"}
+    wo = st_mix["ms_write_only"]
+    if wo:
+        wo_tot = allreduce_max(ws, sum(wo))
+        line["l2_write_only_flush"] = {
+            "value": ws * s.n * len(wo) / (wo_tot / 1e3), "unit": "atom-steps/s", "steps": len(wo),
+            "ms_per_step": wo_tot / len(wo), "rebuilds": st_mix["rebuilds_write_only"],
+            "how": "the next steps of the same state, each after a flush that only writes the 256 MB buffer: the "
+                   "step then also writes back the flush's dirty lines as it evicts them"}
     line["phases_ms_per_step_profiled"] = {k: prof_mix[0][n] / st_mix["prof_steps"] for n, k in
                                            enumerate(("integrator", "list_build", "force_register_kernel",
                                                       "force_overflow_and_reduce", "bookkeeping"))}
