@@ -386,6 +386,25 @@ def run_gpu(args, ws, rank, local):
                 "force_register_kernels_ms_per_step": prof_g2[0][2] / st_g2["prof_steps"],
                 "headline_force_register_kernels_ms_per_step": prof_s[0][2] / st_s["prof_steps"],
                 "ms_per_step": sum(fl_g2) / len(fl_g2), "headline_ms_per_step": sum(fl_s) / len(fl_s)}
+        # list builds: sort + reverse indices in one kernel (the default for lists of up to
+        # 16 slots) against the two-kernel path, from the same state over the same steps
+        # (the two give bitwise the same trajectory, hence the same rebuilds)
+        _, fl_f, prof_f, st_f, md_f = timed(T.MIXED, k_v, args.warmup)
+        md_f = None
+        os.environ["TERSOFF_LIST_FUSED"] = "0"
+        try:
+            _, fl_u, prof_u, st_u, md_u = timed(T.MIXED, k_v, args.warmup)
+        finally:
+            del os.environ["TERSOFF_LIST_FUSED"]
+        md_u = None
+        variants["list_sort_reverse_two_kernels"] = {
+            "what": "Si 512k mixed, list builds sorting each list (k_sort_lists) and then searching the reverse "
+                    "indices (k_reverse) instead of the one kernel of the default; same state, same steps",
+            "list_build_ms_per_step_profiled": prof_u[0][1] / st_u["prof_steps"],
+            "default_list_build_ms_per_step_profiled": prof_f[0][1] / st_f["prof_steps"],
+            "ms_per_step": sum(fl_u) / len(fl_u), "default_ms_per_step": sum(fl_f) / len(fl_f),
+            "steps": len(fl_u), "rebuilds": st_u["rebuilds"] + st_u["rebuilds_flushed"],
+            "default_rebuilds": st_f["rebuilds"] + st_f["rebuilds_flushed"]}
         variant_finals = {"mixed_fp64_accumulation": st_a["final"]}
     else:
         variant_finals = {}

@@ -14,6 +14,8 @@
 //                    radius r_C(ti,tj) + skin appended to both lists
 //   k_sort_lists  -> each list sorted by j; overflow check
 //   k_reverse     -> for each entry (i,s) the flat index of i's slot in j's list
+//   (k_sort_reverse does both in one kernel when the caller gives scratch for the
+//   raw lists and the lists hold at most 16 slots)
 #include "internal.cuh"
 
 namespace tsf {
@@ -478,6 +480,79 @@ __global__ void k_reverse(int N, int ld, const int4 *__restrict__ q, const SysCt
   if (missing) atomicOr(&rs->status, ST_REV_MISSING);
 }
 
+// Sorted lists and reverse indices in one pass, for lists of up to 16 slots.  k_build
+// then wrote its raw lists to raw/rawcnt (forward entries from slot 0, backward ones
+// from slot cap - 1 down, packed counts), which no thread writes here.  Thread i sorts
+// its own raw list in registers and writes it to nbr; the slot of i in the sorted list
+// of its neighbour j is the number of entries of j's raw list below i, so rev[s][i]
+// needs no search in a sorted list and every atom writes only its own entries.  The
+// lists, counts and reverse indices equal those of k_sort_lists + k_reverse.
+__global__ void __launch_bounds__(128) k_sort_reverse(int N, int ld, const int4 *__restrict__ q,
+                                                      const SysCtl *__restrict__ ctl, const int *__restrict__ cell_of,
+                                                      const int *__restrict__ raw, const int *__restrict__ rawcnt,
+                                                      int *__restrict__ nbr, int *__restrict__ cnt,
+                                                      int *__restrict__ rev, int cap, RunState *rs, int gated)
+{
+  griddep_wait();
+  if (skip_build(rs, gated)) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N || cell_of[i] < 0) return;
+  if (ctl && ctl[sys_of(q[i].w)].rebuild == 0) return;
+  const int c = rawcnt[i];
+  const int nf = c & (BACK - 1), nb = c >> 16, n = nf + nb;
+  atomicMax(&rs->maxcount, n);
+  if (n > cap) {
+    atomicOr(&rs->status, ST_NLIST_OVERFLOW);
+    return;
+  }
+  cnt[i] = n;
+  auto slot = [&](int s, int f, int b) { return s < f ? s : cap - b + (s - f); };
+  int v[16];
+#pragma unroll
+  for (int s = 0; s < 16; ++s) v[s] = s < n ? raw[(size_t)slot(s, nf, nb) * ld + i] : 0x7fffffff;
+  if (n <= 8) {
+    int w[8];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) w[s] = v[s];
+    bitonic<8, 2, 1>(w);
+#pragma unroll
+    for (int s = 0; s < 8; ++s) v[s] = w[s];
+  } else {
+    bitonic<16, 2, 1>(v);
+  }
+  int cj[16];
+#pragma unroll
+  for (int s = 0; s < 16; ++s) {
+    if (s < n) nbr[(size_t)s * ld + i] = v[s];
+    cj[s] = s < n ? rawcnt[v[s]] : 0;
+  }
+  bool missing = false;
+#pragma unroll
+  for (int s = 0; s < 16; ++s) {
+    if (s < n) {
+      const int j = v[s];
+      // a neighbour whose list overflowed (it flags that itself) is not read: its
+      // ranges may overlap or start below slot 0
+      const int fj = cj[s] & (BACK - 1), bj = cj[s] >> 16, nj = fj + bj <= cap ? fj + bj : 0;
+      int below = 0;
+      bool found = false;
+      for (int t0 = 0; t0 < nj; t0 += 4) {
+        int e[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) e[k] = t0 + k < nj ? raw[(size_t)slot(t0 + k, fj, bj) * ld + j] : 0x7fffffff;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          below += e[k] < i;
+          found = found || e[k] == i;
+        }
+      }
+      missing = missing || !found;
+      rev[(size_t)s * ld + i] = found ? (int)((unsigned)below * (unsigned)ld + (unsigned)j) : (int)(unsigned)j;
+    }
+  }
+  if (missing) atomicOr(&rs->status, ST_REV_MISSING);
+}
+
 // close a build: count it, clear the request
 __global__ void k_build_done(RunState *rs, int gated)
 {
@@ -497,16 +572,24 @@ namespace tsf {
 // the list stride.  radii: list radius per type pair.  Buffers: cell_count[ncell]
 // (zero on entry, zero on exit), cell_start[ncell+1], tile_sums[ceil(ncell/SCAN_TILE)],
 // cell_atoms[N] (int4), cell_of[N], rank[N]; list nbr/rev [cap][ld], cnt[N]; qref[N].
+// raw [cap][ld] and rawcnt[N] (optional): scratch for the raw lists, every column of
+// an atom that gets a new list free to overwrite (the build's atoms only).
 cudaError_t launch_build(cudaStream_t st, int N, int ld, const int4 *q, const SysTab *sys, const SysCtl *ctl, int ncell,
                          const PairRadii &radii,
                          int *cell_count, int *cell_start, int *tile_sums, int4 *cell_atoms, int *cell_of, int *rank,
-                         int *nbr, int *rev, int *cnt, int cap, int4 *qref, RunState *rs, int gated)
+                         int *nbr, int *rev, int *cnt, int cap, int4 *qref, RunState *rs, int gated, int *raw,
+                         int *rawcnt)
 {
   if (N == 0) return cudaSuccess;
+  // lists of up to 16 slots with raw scratch: k_build appends there and one kernel
+  // sorts and finds the reverse indices; else k_build appends in place, then
+  // k_sort_lists and k_reverse
+  const bool fused = raw && rawcnt && cap <= 16;
+  int *bnbr = fused ? raw : nbr, *bcnt = fused ? rawcnt : cnt;
   const int T = 256;
   const int BN = (N + T - 1) / T;
   const int ntiles = (ncell + SCAN_TILE - 1) / SCAN_TILE;
-  k_cell_count<<<BN, T, 0, st>>>(N, q, sys, ctl, cell_of, rank, cell_count, cnt, rs, gated);
+  k_cell_count<<<BN, T, 0, st>>>(N, q, sys, ctl, cell_of, rank, cell_count, bcnt, rs, gated);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if ((e = launch_dep(k_scan_tiles, ntiles, SCAN_THREADS, 0, st, ncell, (const int *)cell_count, cell_start, tile_sums,
@@ -527,8 +610,14 @@ cudaError_t launch_build(cudaStream_t st, int N, int ld, const int4 *q, const Sy
   bool typed = false;
   for (int k = 1; k < MAX_TYPES * MAX_TYPES; ++k) typed = typed || radii.rl2[k] != radii.rl2[0];
   if ((e = launch_dep(typed ? k_build<true> : k_build<false>, BN128, 128, 0, st, ld, ncell, q, sys, ctl, radii,
-                      (const int *)cell_start, (const int4 *)cell_atoms, nbr, cnt, cap, qref, rs, gated)) != cudaSuccess)
+                      (const int *)cell_start, (const int4 *)cell_atoms, bnbr, bcnt, cap, qref, rs, gated)) != cudaSuccess)
     return e;
+  if (fused) {
+    if ((e = launch_dep(k_sort_reverse, BN128, 128, 0, st, N, ld, q, ctl, (const int *)cell_of, (const int *)raw,
+                        (const int *)rawcnt, nbr, cnt, rev, cap, rs, gated)) != cudaSuccess)
+      return e;
+    return launch_dep(k_build_done, 1, 1, 0, st, rs, gated);
+  }
   if ((e = launch_dep(k_sort_lists, BN128, 128, 0, st, N, ld, q, ctl, (const int *)cell_of, nbr, cnt, cap, rs,
                       gated)) != cudaSuccess)
     return e;

@@ -153,6 +153,7 @@ struct tersoff_md {
   int prec = TERSOFF_FP64;
   int gprec = TERSOFF_FP64;   // accumulation of the force gather (PREC_MIXED_ACC64: float64 sums)
   bool f32 = false;     // float32 force arithmetic (mixed or single precision)
+  bool fused_lists = true;   // list builds sort and find reverse indices in one kernel (lists <= 16 slots)
   bool open = false;            // velocities are at the half step (a closing kick is pending)
   bool pe_valid = false;        // rs->epot_last holds the potential energy of the current positions
   long long steps_done = 0;     // host count of completed steps
@@ -874,9 +875,17 @@ static int md_build(tersoff_md *md, cudaStream_t st, int gated, bool full = fals
 {
   tersoff_ctx *ctx = md->ctx;
   ListState &L = md->list;
+  // Raw-list scratch: the force scatter buffers, which hold nothing between the
+  // integrator's gather and the force evaluation that follows every build of an MD
+  // state (one system: every atom gets a new list).
+  const size_t n = (size_t)md->atoms.N;
+  const bool scratch = md->fused_lists && md->atoms.contrib_b >= n * (size_t)L.cap * sizeof(int) &&
+                       md->atoms.selfF_b >= n * sizeof(int);
+  int *raw = scratch ? (int *)md->atoms.contrib : nullptr;
+  int *rawcnt = scratch ? (int *)md->atoms.selfF : nullptr;
   CK(launch_build(st, (int)md->atoms.N, (int)md->atoms.N, md->atoms.q, md->sys.tab, full ? nullptr : md->sys.ctl, L.grid.ncell,
                   L.grid.radii, L.cell_count, L.cell_start, L.tile_sums, L.cell_atoms, L.cell_of, L.rank, L.nbr, L.rev,
-                  L.cnt, L.cap, L.qref, md->rs, gated));
+                  L.cnt, L.cap, L.qref, md->rs, gated, raw, rawcnt));
   return TERSOFF_OK;
 }
 
@@ -1090,6 +1099,10 @@ int tersoff_md_create(tersoff_ctx *ctx, const double *pos, const double *vel, co
   {
     const char *acc = getenv("TERSOFF_MIXED_ACCUMULATE");
     if (prec == TERSOFF_MIXED && acc && strcmp(acc, "fp64") == 0) md->gprec = PREC_MIXED_ACC64;
+    // TERSOFF_LIST_FUSED=0: the step's list builds sort the lists and search the
+    // reverse indices in two kernels (the same lists and indices; a comparison switch)
+    const char *fl = getenv("TERSOFF_LIST_FUSED");
+    md->fused_lists = !(fl && strcmp(fl, "0") == 0);
   }
   auto fail = [&](int rc) {
     tersoff_md_destroy(md);

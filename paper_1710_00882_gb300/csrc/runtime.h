@@ -60,7 +60,8 @@ namespace tsf {
 
 // launchers defined in the kernel translation units
 cudaError_t launch_build(cudaStream_t, int, int, const int4 *, const SysTab *, const SysCtl *, int, const PairRadii &, int *, int *,
-                         int *, int4 *, int *, int *, int *, int *, int *, int, int4 *, RunState *, int);
+                         int *, int4 *, int *, int *, int *, int *, int *, int, int4 *, RunState *, int, int *raw = nullptr,
+                         int *rawcnt = nullptr);
 int scan_tiles_for(int ncell);
 int force_slots_for(int need);
 int force_partial_rows(int N);

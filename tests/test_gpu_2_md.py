@@ -265,6 +265,31 @@ def test_float64_accumulation_variant(T, ctx, monkeypatch):
     assert np.abs(fb - Fo).max() < MIX_F_ABS
 
 
+@pytest.mark.parametrize("skin", [0.3, 0.6])
+@pytest.mark.parametrize("prec_name", ["FP64", "MIXED"])
+def test_one_kernel_sort_and_reverse_equal_two_kernels(T, ctx, monkeypatch, prec_name, skin):
+    """The step's list builds sort each list and find its reverse indices in one kernel
+    (lists of up to 16 slots); with TERSOFF_LIST_FUSED=0 they take the two-kernel path
+    (sort, then binary searches in the sorted lists).  Both give the same lists and
+    reverse indices, so trajectories through many rebuilds are bitwise equal.  Skin
+    0.6 A lists hold some second-shell atoms (up to ~10 entries: the 16-wide sort)."""
+    s = wl.si_box(6, 6, 6, seed=53, T=1500.0)
+    P = product_params(ctx, s.species)
+    prec = getattr(T, prec_name)
+    a = T.MD(ctx, P, s.pos, s.vel, s.types, s.box, dt=1e-3, skin=skin, prec=prec)
+    monkeypatch.setenv("TERSOFF_LIST_FUSED", "0")
+    b = T.MD(ctx, P, s.pos, s.vel, s.types, s.box, dt=1e-3, skin=skin, prec=prec)
+    monkeypatch.delenv("TERSOFF_LIST_FUSED")
+    assert a.stats()["stride"] <= 16
+    a.step(120)
+    b.step(120)
+    sa, sb = a.stats(), b.stats()
+    assert sa["rebuilds"] >= 3 and sa["rebuilds"] == sb["rebuilds"] and sa["stride"] == sb["stride"]
+    pa, va, fa = a.get(forces=True)
+    pb, vb, fb = b.get(forces=True)
+    assert np.array_equal(pa, pb) and np.array_equal(va, vb) and np.array_equal(fa, fb)
+
+
 @pytest.mark.parametrize("kind", ["si", "sic"])
 def test_forces_after_rebuilds_match_a_fresh_evaluation(T, ctx, kind):
     """After many list rebuilds (per-type radii, sorted lists, reverse indices, the
