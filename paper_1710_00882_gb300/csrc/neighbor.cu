@@ -483,11 +483,15 @@ __global__ void k_reverse(int N, int ld, const int4 *__restrict__ q, const SysCt
 // Sorted lists and reverse indices in one pass, for lists of up to 16 slots.  k_build
 // then wrote its raw lists to raw/rawcnt (forward entries from slot 0, backward ones
 // from slot cap - 1 down, packed counts), which no thread writes here.  Thread i sorts
-// its own raw list in registers and writes it to nbr; the slot of i in the sorted list
-// of its neighbour j is the number of entries of j's raw list below i, so rev[s][i]
-// needs no search in a sorted list and every atom writes only its own entries.  The
-// lists, counts and reverse indices equal those of k_sort_lists + k_reverse.
-__global__ void __launch_bounds__(128) k_sort_reverse(int N, int ld, const int4 *__restrict__ q,
+// its own raw list in registers and writes it to nbr.  The slot of i in the sorted list
+// of a neighbour j is the number of entries of j's raw list below i, so no search in a
+// sorted list is needed: for each neighbour j > i (the tail of i's sorted list) thread
+// i counts them and writes both reverse entries of the pair, as k_reverse does, so
+// every entry has one writer.  The lists, counts and reverse indices equal those of
+// k_sort_lists + k_reverse.  (Longer lists keep those two kernels: for the 3C-SiC lists
+// of ~16 entries a shared-memory sort and ~100 neighbour-list loads per atom were
+// slower than the binary searches.)
+__global__ void __launch_bounds__(128, 8) k_sort_reverse(int N, int ld, const int4 *__restrict__ q,
                                                       const SysCtl *__restrict__ ctl, const int *__restrict__ cell_of,
                                                       const int *__restrict__ raw, const int *__restrict__ rawcnt,
                                                       int *__restrict__ nbr, int *__restrict__ cnt,
@@ -520,20 +524,18 @@ __global__ void __launch_bounds__(128) k_sort_reverse(int N, int ld, const int4 
   } else {
     bitonic<16, 2, 1>(v);
   }
-  int cj[16];
 #pragma unroll
-  for (int s = 0; s < 16; ++s) {
+  for (int s = 0; s < 16; ++s)
     if (s < n) nbr[(size_t)s * ld + i] = v[s];
-    cj[s] = s < n ? rawcnt[v[s]] : 0;
-  }
   bool missing = false;
 #pragma unroll
   for (int s = 0; s < 16; ++s) {
-    if (s < n) {
+    if (s < n && v[s] > i) {
       const int j = v[s];
+      const int cj = rawcnt[j];
       // a neighbour whose list overflowed (it flags that itself) is not read: its
       // ranges may overlap or start below slot 0
-      const int fj = cj[s] & (BACK - 1), bj = cj[s] >> 16, nj = fj + bj <= cap ? fj + bj : 0;
+      const int fj = cj & (BACK - 1), bj = cj >> 16, nj = fj + bj <= cap ? fj + bj : 0;
       int below = 0;
       bool found = false;
       for (int t0 = 0; t0 < nj; t0 += 4) {
@@ -546,8 +548,13 @@ __global__ void __launch_bounds__(128) k_sort_reverse(int N, int ld, const int4 
           found = found || e[k] == i;
         }
       }
-      missing = missing || !found;
-      rev[(size_t)s * ld + i] = found ? (int)((unsigned)below * (unsigned)ld + (unsigned)j) : (int)(unsigned)j;
+      if (found) {
+        rev[(size_t)s * ld + i] = (int)((unsigned)below * (unsigned)ld + (unsigned)j);
+        rev[(size_t)below * ld + j] = (int)((unsigned)s * (unsigned)ld + (unsigned)i);
+      } else {
+        missing = true;
+        rev[(size_t)s * ld + i] = (int)(unsigned)j;
+      }
     }
   }
   if (missing) atomicOr(&rs->status, ST_REV_MISSING);

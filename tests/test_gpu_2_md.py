@@ -265,22 +265,29 @@ def test_float64_accumulation_variant(T, ctx, monkeypatch):
     assert np.abs(fb - Fo).max() < MIX_F_ABS
 
 
-@pytest.mark.parametrize("skin", [0.3, 0.6])
+@pytest.mark.parametrize("case", ["si-0.3", "si-0.6", "sic-0.3"])
 @pytest.mark.parametrize("prec_name", ["FP64", "MIXED"])
-def test_one_kernel_sort_and_reverse_equal_two_kernels(T, ctx, monkeypatch, prec_name, skin):
+def test_one_kernel_sort_and_reverse_equal_two_kernels(T, ctx, monkeypatch, prec_name, case):
     """The step's list builds sort each list and find its reverse indices in one kernel
     (lists of up to 16 slots); with TERSOFF_LIST_FUSED=0 they take the two-kernel path
     (sort, then binary searches in the sorted lists).  Both give the same lists and
-    reverse indices, so trajectories through many rebuilds are bitwise equal.  Skin
-    0.6 A lists hold some second-shell atoms (up to ~10 entries: the 16-wide sort)."""
-    s = wl.si_box(6, 6, 6, seed=53, T=1500.0)
+    reverse indices, so trajectories through many rebuilds are bitwise equal.  Si with
+    a 0.6 A skin holds some second-shell atoms (the 16-wide register sort); 3C-SiC
+    lists of ~16 entries (capacity above 16) take the two-kernel path either way."""
+    kind, skin = case.split("-")
+    skin = float(skin)
+    if kind == "si":
+        s, dt = wl.si_box(6, 6, 6, seed=53, T=1500.0), 1e-3
+    else:
+        s, dt = wl.sic_box(5, seed=54, T=1500.0), 0.5e-3
     P = product_params(ctx, s.species)
     prec = getattr(T, prec_name)
-    a = T.MD(ctx, P, s.pos, s.vel, s.types, s.box, dt=1e-3, skin=skin, prec=prec)
+    a = T.MD(ctx, P, s.pos, s.vel, s.types, s.box, dt=dt, skin=skin, prec=prec)
     monkeypatch.setenv("TERSOFF_LIST_FUSED", "0")
-    b = T.MD(ctx, P, s.pos, s.vel, s.types, s.box, dt=1e-3, skin=skin, prec=prec)
+    b = T.MD(ctx, P, s.pos, s.vel, s.types, s.box, dt=dt, skin=skin, prec=prec)
     monkeypatch.delenv("TERSOFF_LIST_FUSED")
-    assert a.stats()["stride"] <= 16
+    stride = a.stats()["stride"]
+    assert stride <= 32 and (kind == "si" or stride > 16)
     a.step(120)
     b.step(120)
     sa, sb = a.stats(), b.stats()
