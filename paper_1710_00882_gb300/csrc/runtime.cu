@@ -314,8 +314,8 @@ int check_box(tersoff_ctx *ctx, const double box[3], double rl)
   return TERSOFF_OK;
 }
 
-// Host-visible list build from A.q: grows the capacity on overflow and sizes it to
-// the longest list plus headroom.
+// Host-visible list build from A.q: the first capacity from the mean density, grown
+// on overflow to the longest list plus headroom.
 int build_list_sync(tersoff_ctx *ctx, const AtomState &A, ListState &L, RunState *rs, const double box[3],
                     double cutoff, double skin, SysDev &S, const tersoff_params *P)
 {
@@ -335,7 +335,15 @@ int build_list_sync(tersoff_ctx *ctx, const AtomState &A, ListState &L, RunState
   S.host.atom_off = 0;
   S.host.natoms = (int)A.N;
   CK(cudaMemcpyAsync(S.tab, &S.host, sizeof(SysTab), cudaMemcpyHostToDevice, ctx->stream));
-  int cap = L.cap > 0 ? L.cap : MAX_CAP;
+  int cap = L.cap;
+  if (cap <= 0) {
+    // first build: room for 1.5 x the mean number of atoms within the list radius plus
+    // 4 (at least 8, a multiple of 4); a list that overflows it makes the next attempt
+    // size the capacity from the longest list found
+    const double nexp = (double)A.N / (box[0] * box[1] * box[2]) * (4.0 / 3.0) * M_PI * rl * rl * rl;
+    cap = (int)std::min<double>(MAX_CAP, std::ceil(1.5 * nexp + 4.0));
+    cap = std::min(MAX_CAP, std::max(8, (cap + 3) & ~3));
+  }
   for (int attempt = 0; attempt < 3; ++attempt) {
     CKR(ensure_list(ctx, L, A.N, cap, g.ncell));
     CK(cudaMemsetAsync(&rs->maxcount, 0, sizeof(int), ctx->stream));

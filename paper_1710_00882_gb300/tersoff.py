@@ -317,11 +317,19 @@ class MD:
             self.h = None
 
 
-def md_run(ctx, params, pos, vel, types, box, dt, nsteps, skin, prec=MIXED, trace=True):
-    """One call: returns (pos, vel, trace) after nsteps (host arrays)."""
+def md_run(ctx, params, pos, vel, types, box, dt, nsteps, skin, prec=MIXED, trace=True, inplace=False):
+    """One call: returns (pos, vel, trace) after nsteps (host arrays).  inplace: pos and
+    vel (C-contiguous float64 [N][3]) are updated in place, as tersoff_md_run does with
+    the caller's buffers, and returned; else copies are."""
     n = int(pos.shape[0])
-    pos = np.array(pos, dtype=np.float64).reshape(n, 3)
-    vel = np.array(vel, dtype=np.float64).reshape(n, 3)
+    if inplace:
+        for a in (pos, vel):
+            if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.shape == (n, 3)
+                    and a.flags["C_CONTIGUOUS"] and a.flags["WRITEABLE"]):
+                raise ValueError("inplace needs writeable C-contiguous float64 [N][3] pos and vel")
+    else:
+        pos = np.array(pos, dtype=np.float64).reshape(n, 3)
+        vel = np.array(vel, dtype=np.float64).reshape(n, 3)
     types = _i32(types, n)
     tr = np.zeros((nsteps + 1, 2)) if trace else None
     ctx.check(tersoff_md_run(ctx.h, ptr(pos), ptr(vel), ptr(types), n, ptr(_box(box)), params.h, float(dt),

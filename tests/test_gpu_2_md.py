@@ -181,6 +181,11 @@ def test_md_run_one_call(T, ctx):
     p2, v2 = md.get()
     assert np.array_equal(p, p2) and np.array_equal(v, v2)
     assert np.allclose(tr, tr2, rtol=1e-13)
+    # in place: the caller's arrays are the C call's buffers
+    p3, v3 = np.array(s.pos, dtype=np.float64), np.array(s.vel, dtype=np.float64)
+    p4, v4, _ = T.md_run(ctx, P, p3, v3, s.types, s.box, 1e-3, 30, 0.3, prec=T.FP64, trace=False, inplace=True)
+    assert p4 is p3 and v4 is v3
+    assert np.array_equal(p3, p) and np.array_equal(v3, v)
 
 
 def test_list_grows_during_run(T, ctx):
