@@ -581,6 +581,21 @@ cudaError_t launch_decide(cudaStream_t st, RunState *rs, cudaGraphConditionalHan
   return launch_dep(k_decide, 1, 1, 0, st, rs, build);
 }
 
+// New parameters of a captured k_set_control node in an instantiated graph.
+cudaError_t set_control_node(cudaGraphExec_t exec, cudaGraphNode_t node, RunState *rs, SysCtl *ctl, long long steps,
+                             double *trace, long long trace_k, int open)
+{
+  void *args[] = {&rs, &ctl, &steps, &trace, &trace_k, &open};
+  cudaKernelNodeParams p = {};
+  p.func = (void *)k_set_control;
+  p.gridDim = dim3(1, 1, 1);
+  p.blockDim = dim3(1, 1, 1);
+  p.sharedMemBytes = 0;
+  p.kernelParams = args;
+  p.extra = nullptr;
+  return cudaGraphExecKernelNodeSetParams(exec, node, &p);
+}
+
 cudaError_t launch_set_control(cudaStream_t st, RunState *rs, SysCtl *ctl, long long steps, double *trace,
                                long long trace_k, int open)
 {

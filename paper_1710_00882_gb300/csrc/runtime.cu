@@ -139,7 +139,7 @@ constexpr int TSF_PHASES = 5;
 struct tersoff_md {
   tersoff_ctx *ctx = nullptr;
   cudaStream_t cap_stream = nullptr;   // stream used only to capture the step graphs
-  MdGraph graph[2];                    // step loop without / with energy trace
+  MdGraph graph[3];                    // step loop without / with energy trace; one step without trace
   bool use_graphs = true;
   bool pending = false;                // async steps launched and not yet checked
   const tersoff_params *params = nullptr;
@@ -912,6 +912,9 @@ static void md_graphs_free(tersoff_md *md)
 // launch in the instantiated graph, and sets the first loop condition.
 // step_end decrements steps_left and sets the loop condition, so one launch runs any
 // number of steps, and a step without a rebuild launches no build kernel.
+// which = 2: one step without trace, with no loop node (a conditional node costs
+// microseconds of device-side scheduling per launch):
+//   set_control -> vv -> decide -> IF(rebuild) { list build } -> force -> step_end
 static int md_graph_build(tersoff_md *md, int which)
 {
   tersoff_ctx *ctx = md->ctx;
@@ -924,6 +927,42 @@ static int md_graph_build(tersoff_md *md, int which)
   cudaGraph_t g = nullptr;
   CK(cudaGraphCreate(&g, 0));
   G.g = g;
+  if (which == 2) {
+    cudaGraphConditionalHandle hbuild;
+    CK(cudaGraphConditionalHandleCreate(&hbuild, g, 0, cudaGraphCondAssignDefault));
+    CK(cudaStreamBeginCaptureToGraph(st, g, nullptr, nullptr, 0, mode));
+    CK(launch_set_control(st, md->rs, md->sys.ctl, 1, nullptr, 0, 0));
+    cudaStreamCaptureStatus cs;
+    const cudaGraphNode_t *deps = nullptr;
+    const cudaGraphEdgeData *edges = nullptr;
+    size_t nd = 0;
+    CK(cudaStreamGetCaptureInfo(st, &cs, nullptr, nullptr, &deps, &edges, &nd));
+    if (nd != 1) return set_err(ctx, TERSOFF_ERR_CUDA, "unexpected graph capture state");
+    G.start = deps[0];
+    CKR(md_vv(md, st, -1, false));
+    CK(launch_decide(st, md->rs, hbuild));
+    CK(cudaStreamGetCaptureInfo(st, &cs, nullptr, nullptr, &deps, &edges, &nd));
+    cudaGraphNodeParams ip = {};
+    ip.type = cudaGraphNodeTypeConditional;
+    ip.conditional.handle = hbuild;
+    ip.conditional.type = cudaGraphCondTypeIf;
+    ip.conditional.size = 1;
+    cudaGraphNode_t inode;
+    CK(cudaGraphAddNode(&inode, g, deps, edges, nd, &ip));
+    CK(cudaStreamUpdateCaptureDependencies(st, &inode, nullptr, 1, cudaStreamSetCaptureDependencies));
+    CKR(md_force(md, st, 0));
+    CK(launch_step_end(st, md->rs, md->sys.ctl, 1, 0, 0));
+    cudaGraph_t gc = g;
+    CK(cudaStreamEndCapture(st, &gc));
+    cudaGraph_t ifbody = ip.conditional.phGraph_out[0];
+    CK(cudaStreamBeginCaptureToGraph(st, ifbody, nullptr, nullptr, 0, mode));
+    CKR(md_build(md, st, 0));
+    cudaGraph_t ifc = ifbody;
+    CK(cudaStreamEndCapture(st, &ifc));
+    CK(cudaGraphInstantiate(&G.exec, g, 0));
+    G.valid = true;
+    return TERSOFF_OK;
+  }
   cudaGraphConditionalHandle hloop, hbuild;
   CK(cudaGraphConditionalHandleCreate(&hloop, g, 0, cudaGraphCondAssignDefault));
   CK(cudaStreamBeginCaptureToGraph(st, g, nullptr, nullptr, 0, mode));
@@ -985,9 +1024,10 @@ static int md_launch_steps(tersoff_md *md, long long n, double *d_trace, long lo
   if (n <= 0) return TERSOFF_OK;
   const bool tr = d_trace != nullptr;
   if (!md->prof && md->use_graphs) {
-    MdGraph &G = md->graph[tr ? 1 : 0];
+    const int which = tr ? 1 : (n == 1 ? 2 : 0);
+    MdGraph &G = md->graph[which];
     if (!G.valid) {
-      int rc = md_graph_build(md, tr ? 1 : 0);
+      int rc = md_graph_build(md, which);
       if (rc != TERSOFF_OK) {
         // fall back to kernel-by-kernel launches for this state
         cudaGetLastError();
@@ -997,7 +1037,10 @@ static int md_launch_steps(tersoff_md *md, long long n, double *d_trace, long lo
     }
     if (md->use_graphs) {
       // the launch's controls go into the graph's first node
-      CK(set_loop_start(G.exec, G.start, md->rs, md->sys.ctl, n, d_trace, k0, md->open ? 1 : 0, G.hloop));
+      if (which == 2)
+        CK(set_control_node(G.exec, G.start, md->rs, md->sys.ctl, 1, nullptr, k0, md->open ? 1 : 0));
+      else
+        CK(set_loop_start(G.exec, G.start, md->rs, md->sys.ctl, n, d_trace, k0, md->open ? 1 : 0, G.hloop));
       CK(cudaGraphLaunch(G.exec, st));
       md->launches[0] += n;
       md->open = true;

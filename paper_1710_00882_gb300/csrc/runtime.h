@@ -94,6 +94,8 @@ cudaError_t set_loop_start(cudaGraphExec_t, cudaGraphNode_t, RunState *, SysCtl 
                            cudaGraphConditionalHandle);
 cudaError_t launch_decide(cudaStream_t, RunState *, cudaGraphConditionalHandle);
 cudaError_t launch_set_control(cudaStream_t, RunState *, SysCtl *, long long, double *, long long, int);
+cudaError_t set_control_node(cudaGraphExec_t, cudaGraphNode_t, RunState *, SysCtl *, long long, double *, long long,
+                             int);
 cudaError_t launch_final(cudaStream_t, RunState *, SysCtl *);
 cudaError_t launch_force_done(cudaStream_t, RunState *);
 

@@ -159,6 +159,32 @@ def test_async_steps_equal_sync_steps(T, ctx):
     assert np.array_equal(pa, pb) and np.array_equal(va, vb)
 
 
+@pytest.mark.parametrize("prec_name", ["FP64", "MIXED"])
+def test_single_step_launches_equal_one_launch(T, ctx, prec_name):
+    """A one-step launch runs a graph without the loop node; 60 of them (through
+    several list rebuilds, in the async and the synchronous call) equal one 60-step
+    launch bitwise, energy trace included where a later traced launch reads it."""
+    s = wl.si_box(6, 6, 6, seed=24, T=1500.0)
+    P = product_params(ctx, s.species)
+    prec = getattr(T, prec_name)
+    a = T.MD(ctx, P, s.pos, s.vel, s.types, s.box, dt=1e-3, skin=0.3, prec=prec)
+    for k in range(60):
+        if k % 2:
+            a.step(1)
+        else:
+            a.step_async(1)
+    a.sync()
+    b = T.MD(ctx, P, s.pos, s.vel, s.types, s.box, dt=1e-3, skin=0.3, prec=prec)
+    b.step(60)
+    assert a.stats()["rebuilds"] == b.stats()["rebuilds"] >= 3
+    assert a.stats()["steps"] == b.stats()["steps"] == 60
+    pa, va, fa = a.get(forces=True)
+    pb, vb, fb = b.get(forces=True)
+    assert np.array_equal(pa, pb) and np.array_equal(va, vb) and np.array_equal(fa, fb)
+    ta, tb = a.step(5, trace=True), b.step(5, trace=True)
+    assert np.array_equal(ta, tb)
+
+
 def test_time_reversible_fp64(T, ctx):
     s = wl.si_box(6, 6, 6, seed=24, T=1000.0)
     P = product_params(ctx, s.species)
