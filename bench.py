@@ -454,9 +454,11 @@ def run_gpu(args, ws, rank, local):
 
     traffic = force_traffic()
 
-    # kernels per timed step on the graph path: loop_start per launch, then integrator,
-    # decide, force (register + overflow), step_end; 9 more on rebuilds
-    launches = len(fl_mix) * (1 + 5) + 9 * st_mix["rebuilds_flushed"]
+    # kernels per timed step (one graph launch of one step, 512,000 atoms: the list build
+    # gated on the device): set_control, integrator, the 8 list-build kernels (count, 3
+    # scans, fill, build, sort + reverse indices, done; they exit at once without a
+    # rebuild), the register and overflow force kernels, step_end
+    launches = len(fl_mix) * (1 + 1 + 8 + 2 + 1)
     line = {
         "metric": METRIC,
         "value": value,

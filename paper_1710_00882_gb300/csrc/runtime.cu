@@ -914,6 +914,8 @@ static void md_graphs_free(tersoff_md *md)
 // number of steps, and a step without a rebuild launches no build kernel.
 // which = 2: one step without trace, with no loop node (a conditional node costs
 // microseconds of device-side scheduling per launch):
+//   set_control -> vv -> list build (gated on the device) -> force -> step_end
+// or, above kGatedBuildAtoms atoms,
 //   set_control -> vv -> decide -> IF(rebuild) { list build } -> force -> step_end
 static int md_graph_build(tersoff_md *md, int which)
 {
@@ -928,6 +930,32 @@ static int md_graph_build(tersoff_md *md, int which)
   CK(cudaGraphCreate(&g, 0));
   G.g = g;
   if (which == 2) {
+    // Up to kGatedBuildAtoms atoms the list-build kernels follow the integrator
+    // unconditionally and exit at once on the device when no atom moved skin/2: eight
+    // empty launches over grids of that size cost less than an IF node in a graph
+    // launched for one step (Si 512k: 83.5 against 89.5 us per flushed step); over the
+    // larger grids of a 3C-SiC 950k state they cost more (328 against 324 us).  In the
+    // step loop the IF node is the cheaper of the two at both sizes.
+    constexpr int64_t kGatedBuildAtoms = 750000;
+    if (md->atoms.N <= kGatedBuildAtoms) {
+      CK(cudaStreamBeginCaptureToGraph(st, g, nullptr, nullptr, 0, mode));
+      CK(launch_set_control(st, md->rs, md->sys.ctl, 1, nullptr, 0, 0));
+      cudaStreamCaptureStatus cs;
+      const cudaGraphNode_t *deps = nullptr;
+      size_t nd = 0;
+      CK(cudaStreamGetCaptureInfo(st, &cs, nullptr, nullptr, &deps, nullptr, &nd));
+      if (nd != 1) return set_err(ctx, TERSOFF_ERR_CUDA, "unexpected graph capture state");
+      G.start = deps[0];
+      CKR(md_vv(md, st, -1, false));
+      CKR(md_build(md, st, 1));
+      CKR(md_force(md, st, 0));
+      CK(launch_step_end(st, md->rs, md->sys.ctl, 1, 0, 0));
+      cudaGraph_t gc = g;
+      CK(cudaStreamEndCapture(st, &gc));
+      CK(cudaGraphInstantiate(&G.exec, g, 0));
+      G.valid = true;
+      return TERSOFF_OK;
+    }
     cudaGraphConditionalHandle hbuild;
     CK(cudaGraphConditionalHandleCreate(&hbuild, g, 0, cudaGraphCondAssignDefault));
     CK(cudaStreamBeginCaptureToGraph(st, g, nullptr, nullptr, 0, mode));
