@@ -337,11 +337,11 @@ int build_list_sync(tersoff_ctx *ctx, const AtomState &A, ListState &L, RunState
   CK(cudaMemcpyAsync(S.tab, &S.host, sizeof(SysTab), cudaMemcpyHostToDevice, ctx->stream));
   int cap = L.cap;
   if (cap <= 0) {
-    // first build: room for 1.5 x the mean number of atoms within the list radius plus
-    // 4 (at least 8, a multiple of 4); a list that overflows it makes the next attempt
-    // size the capacity from the longest list found
+    // first build: room for the mean number of atoms within the list radius plus 4 (at
+    // least 8, a multiple of 4); a list that overflows it makes the next attempt size
+    // the capacity from the longest list found
     const double nexp = (double)A.N / (box[0] * box[1] * box[2]) * (4.0 / 3.0) * M_PI * rl * rl * rl;
-    cap = (int)std::min<double>(MAX_CAP, std::ceil(1.5 * nexp + 4.0));
+    cap = (int)std::min<double>(MAX_CAP, std::ceil(nexp + 4.0));
     cap = std::min(MAX_CAP, std::max(8, (cap + 3) & ~3));
   }
   for (int attempt = 0; attempt < 3; ++attempt) {
