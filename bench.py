@@ -476,8 +476,8 @@ def run_gpu(args, ws, rank, local):
                    "l2": "flushed before every timed step (outside the events): 256 MB written, then another "
                          "256 MB read, so no line of the step's data and no dirty line is left in L2",
                    "parallelism": "replicas" if ws > 1 else "single GPU",
-                   "step_launch": "one CUDA graph launch per timed step (WHILE over steps, IF around the "
-                                  "list rebuild)"},
+                   "step_launch": "one CUDA graph launch per timed step (tersoff_md_step(md, 1): the one-step "
+                                  "graph, list build gated on the device)"},
         "roofline": {"bound": "alu", "kernel": "k_force_reg<MathF, 4> (mixed, register slots)", "achieved": achieved,
                      "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
                      "traffic": traffic,
