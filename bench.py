@@ -56,11 +56,14 @@ C_ENTRY = 8
 C_PAIR = 57
 C_TAPER = 10
 C_TRIPLET = 40
-# Mixed mode adds, per in-cutoff pair, the work that keeps r and lambda*r to ~1 ulp:
-# the relative vector and |d| as exact head + tail (71 flops where the method's
-# geometry takes 10) and the head/tail exponent of f_R and f_A (7 more each): float32
-# work beyond the method's own, reported apart as overhead.
-C_PAIR_MIXED_OVERHEAD = 75
+# Mixed mode adds float32 work beyond the method's own, reported apart as overhead:
+# per in-cutoff pair the head/tail exponent of f_R and f_A (7 more flops each), and,
+# for the pairs whose geometry it forms as exact head + tail (inside the f_C taper,
+# r > R - D, or shorter than 0.7 R), the relative vector and |d| as head + tail (71
+# flops where the method's geometry takes 10).
+C_PAIR_MIXED_EXP = 14
+C_PAIR_MIXED_GEOM = 61
+R_SHORT_OF_R = 0.7
 # Peaks.  Derived from unit counts and the maximum SM clock: 152 SMs x 128 FP32 lanes
 # x 2 flop x 2.07 GHz; FP64: GB300's nominal 1.25 TFLOP/s.  The FMA-pipe probe
 # (libalu_peaks.so) measures both in the same run.
@@ -140,10 +143,11 @@ def force_kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def workload_counts(s, rc, r_in):
+def workload_counts(s, rc, r_in, r_short=0.0):
     """Verlet-list entries (r < rc + skin), in-cutoff ordered pairs P, ordered pairs
-    inside the cutoff taper (r_in < r < rc) and ordered triplets T of the starting
-    configuration, counted with a periodic k-d tree (single-type cutoffs)."""
+    inside the cutoff taper (r_in < r < rc), ordered pairs shorter than r_short and
+    ordered triplets T of the starting configuration, counted with a periodic k-d tree
+    (single-type cutoffs)."""
     from scipy.spatial import cKDTree
     pos = np.mod(s.pos, s.box)
     tree = cKDTree(pos, boxsize=s.box)
@@ -152,8 +156,9 @@ def workload_counts(s, rc, r_in):
     deg = np.bincount(pairs.ravel(), minlength=s.n)
     P = int(deg.sum())
     P_taper = P - tree.query_pairs(r_in, output_type="ndarray").shape[0] * 2
+    P_short = tree.query_pairs(r_short, output_type="ndarray").shape[0] * 2 if r_short > 0 else 0
     T = int(np.sum(deg * (deg - 1)))
-    return n_list, P, P_taper, T
+    return n_list, P, P_taper, P_short, T
 
 
 class ClockSampler:
@@ -220,7 +225,7 @@ def run_gpu(args, ws, rank, local):
     tab, masses = pp.for_species(s.species)
     P = T.Params(ctx, tab, masses)
     si = pp.SILICON
-    n_list, npair, ntaper, ntrip = workload_counts(s, P.cutoff, si.R1)
+    n_list, npair, ntaper, nshort, ntrip = workload_counts(s, P.cutoff, si.R1, R_SHORT_OF_R * 0.5 * (si.R1 + si.S))
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
     flush_r = torch.ones(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
     flush_sink = torch.zeros(1, dtype=torch.float32, device=f"cuda:{local}")
@@ -425,7 +430,7 @@ def run_gpu(args, ws, rank, local):
     # roofline of the dominant kernel (the register force kernel): the method's flops
     # per launch over its event-timed launch duration (profiled pass, one launch per step)
     flops = C_ENTRY * n_list + C_PAIR * npair + C_TAPER * ntaper + C_TRIPLET * ntrip
-    overhead = C_PAIR_MIXED_OVERHEAD * npair
+    overhead = C_PAIR_MIXED_EXP * npair + C_PAIR_MIXED_GEOM * (ntaper + nshort)
     f_ms = prof_mix[0][2] / prof_mix[1][2]
     f64_ms = prof_64[0][2] / prof_64[1][2]
     fsg_ms = prof_sg[0][2] / prof_sg[1][2]
@@ -490,15 +495,16 @@ def run_gpu(args, ws, rank, local):
                      "what_is_counted": "the method's own float32 work (Algorithm 1): 8 per list entry, 57 per "
                                         "in-cutoff pair, 10 per taper pair, 40 per ordered triplet",
                      "overhead_flops_per_launch": overhead,
-                     "overhead_what": "mixed mode's compensation (relative vector and |d| as exact head+tail, "
-                                      "head+tail exponents): 75 flops per in-cutoff pair",
+                     "overhead_what": "mixed mode's compensation: head+tail exponents of f_R and f_A, 14 flops "
+                                      "per in-cutoff pair; the relative vector and |d| as exact head+tail, 61 "
+                                      "more per pair in the f_C taper or shorter than 0.7 R",
                      "achieved_with_overhead": (flops + overhead) / (f_ms / 1e3) / 1e12,
                      "frac_with_overhead": (flops + overhead) / (f_ms / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
                      "kernel_ms": f_ms,
                      "timing": "CUDA events around each launch of the register force kernel in a profiled "
                                "pass of the same state (one launch per step, L2 flushed before each step)",
                      "counts": {"list_entries": n_list, "pairs": npair, "taper_pairs": ntaper,
-                                "triplets": ntrip},
+                                "short_pairs": nshort, "triplets": ntrip},
                      "flops_per_unit": {"list_entry": C_ENTRY, "pair": C_PAIR, "taper_pair": C_TAPER,
                                         "ordered_triplet": C_TRIPLET}},
         "gpu_launches": launches,

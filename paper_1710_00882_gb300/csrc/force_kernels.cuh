@@ -216,6 +216,36 @@ __device__ __forceinline__ void norm_fine(const float (&dh)[3], const float (&dl
   rl = __fmul_rn(__fmul_rn(__fadd_rn(__fmaf_rn(-rh, rh, s2), r2l), 0.5f), irh);
 }
 
+// Mixed-mode geometry of the pair (i, j): relative vector d, r = rh + rl and 1/rh.
+// A pair with 0.7 R <= r <= R - D (r from the rounded float32 difference) keeps that
+// float32 geometry, rl = 0: the bulk of the pairs of solids (f_C = 1), whose energy
+// and forces are insensitive to r's last bits (a relative error of ~1e-7; the
+// exponents keep lambda as head + tail).  A pair in the f_C taper, where R + D - r
+// must keep its relative accuracy, or a short, strongly repulsive pair (large forces)
+// takes head + tail geometry.  Every kernel forms a pair's geometry with this one
+// function, so it does not depend on the kernel that evaluates the pair.
+__device__ __forceinline__ void pair_geom_mixed(const int4 &qj, const int4 &qi, const Geom *gp, float r_short,
+                                                float r_in, float &dx, float &dy, float &dz, float &r, float &rl,
+                                                float &inv)
+{
+  const int ex = qdiff(qj.x, qi.x), ey = qdiff(qj.y, qi.y), ez = qdiff(qj.z, qi.z);
+  const float fx = q_scaled(ex, gp->q_to_f[0]), fy = q_scaled(ey, gp->q_to_f[1]), fz = q_scaled(ez, gp->q_to_f[2]);
+  const float r2 = r2_decide(fx, fy, fz);
+  const float is = MathF::rsqrt(r2);
+  const float rs = __fmul_rn(r2, is);
+  if (rs <= r_in && rs >= r_short) {
+    dx = fx; dy = fy; dz = fz;
+    r = rs; rl = 0.0f; inv = is;
+  } else {
+    float dh[3], dl[3];
+    qd_fine(ex, gp->q_to_f[0], gp->q_to_f_lo[0], dh[0], dl[0]);
+    qd_fine(ey, gp->q_to_f[1], gp->q_to_f_lo[1], dh[1], dl[1]);
+    qd_fine(ez, gp->q_to_f[2], gp->q_to_f_lo[2], dh[2], dl[2]);
+    norm_fine(dh, dl, r, rl, inv);
+    dx = dh[0]; dy = dh[1]; dz = dh[2];
+  }
+}
+
 template <class R> __device__ __forceinline__ R warp_sum(R v)
 {
 #pragma unroll
@@ -398,18 +428,14 @@ k_force_reg(int ld, const dbl4 *__restrict__ x, const int4 *__restrict__ q, cons
   // geometry of slot s from list entry e (neighbour j): unit vector, r, 1/r, f_C, f_C'
   auto fill_slot = [&](int s, int e, int j, const int4 &qj, const dbl4 &xj, int tj) {
     R dx, dy, dz, r, rlo, inv;
+    const PairP<R> Pp = pairp(ti, tj);
     if (MIXED && M::fine) {
-      // d and |d| as head + tail, so that lambda r and, in the f_C taper, R + D - r keep
-      // their accuracy.  Both register kernels (4 and 8 slots) form the geometry the same
-      // way, so an atom's forces do not depend on which of them evaluates it.
-      float dh[3], dl[3];
-      qd_fine(qdiff(qj.x, qi.x), gp->q_to_f[0], gp->q_to_f_lo[0], dh[0], dl[0]);
-      qd_fine(qdiff(qj.y, qi.y), gp->q_to_f[1], gp->q_to_f_lo[1], dh[1], dl[1]);
-      qd_fine(qdiff(qj.z, qi.z), gp->q_to_f[2], gp->q_to_f_lo[2], dh[2], dl[2]);
-      float rh_, rl_, irh_;
-      norm_fine(dh, dl, rh_, rl_, irh_);
-      dx = (R)dh[0]; dy = (R)dh[1]; dz = (R)dh[2];
-      r = (R)rh_; rlo = (R)rl_; inv = (R)irh_;
+      // the kernels share pair_geom_mixed, so an atom's forces do not depend on which
+      // of them evaluates it
+      float gx, gy, gz, gr, grl, gi;
+      pair_geom_mixed(qj, qi, gp, (float)Pp.r_short, (float)Pp.r_in, gx, gy, gz, gr, grl, gi);
+      dx = (R)gx; dy = (R)gy; dz = (R)gz;
+      r = (R)gr; rlo = (R)grl; inv = (R)gi;
     } else if (MIXED) {
       dx = (R)q_scaled(qdiff(qj.x, qi.x), gp->q_to_f[0]);
       dy = (R)q_scaled(qdiff(qj.y, qi.y), gp->q_to_f[1]);
@@ -433,7 +459,7 @@ k_force_reg(int ld, const dbl4 *__restrict__ x, const int4 *__restrict__ q, cons
     rr[s] = r;
     rl(s) = rlo;
     ir(s) = inv;
-    cutoff_fn<M>(r, rlo, pairp(ti, tj), fc[s], dfc(s));
+    cutoff_fn<M>(r, rlo, Pp, fc[s], dfc(s));
     meta(s) = e | (tj << 8);
   };
 
@@ -970,14 +996,10 @@ k_force_gen(int N, int ld, const dbl4 *__restrict__ x, const int4 *__restrict__ 
           if (nc < MAXNC) {
             R r, rlo, inv;
             if (MIXED && M::fine) {
-              float dh[3], dl[3];
-              qd_fine(qdiff(qq[k].x, qi.x), gp->q_to_f[0], gp->q_to_f_lo[0], dh[0], dl[0]);
-              qd_fine(qdiff(qq[k].y, qi.y), gp->q_to_f[1], gp->q_to_f_lo[1], dh[1], dl[1]);
-              qd_fine(qdiff(qq[k].z, qi.z), gp->q_to_f[2], gp->q_to_f_lo[2], dh[2], dl[2]);
-              float rh_, rl_, irh_;
-              norm_fine(dh, dl, rh_, rl_, irh_);
-              dx = (R)dh[0]; dy = (R)dh[1]; dz = (R)dh[2];
-              r = (R)rh_; rlo = (R)rl_; inv = (R)irh_;
+              float gx, gy, gz, gr, grl, gi;
+              pair_geom_mixed(qq[k], qi, gp, (float)P.r_short, (float)P.r_in, gx, gy, gz, gr, grl, gi);
+              dx = (R)gx; dy = (R)gy; dz = (R)gz;
+              r = (R)gr; rlo = (R)grl; inv = (R)gi;
             } else {
               const R rf2 = r2_decide(dx, dy, dz);
               inv = M::rsqrt(rf2);
@@ -1233,14 +1255,10 @@ k_force_warp(int ld, const dbl4 *__restrict__ x, const int4 *__restrict__ q, con
         const PairP<R> &P = pairs[ti * nt + tj];
         R r, rlo, inv;
         if (MIXED && M::fine) {
-          float dh[3], dl[3];
-          qd_fine(qdiff(qj.x, qi.x), gp->q_to_f[0], gp->q_to_f_lo[0], dh[0], dl[0]);
-          qd_fine(qdiff(qj.y, qi.y), gp->q_to_f[1], gp->q_to_f_lo[1], dh[1], dl[1]);
-          qd_fine(qdiff(qj.z, qi.z), gp->q_to_f[2], gp->q_to_f_lo[2], dh[2], dl[2]);
-          float rh_, rl_, irh_;
-          norm_fine(dh, dl, rh_, rl_, irh_);
-          dx = (R)dh[0]; dy = (R)dh[1]; dz = (R)dh[2];
-          r = (R)rh_; rlo = (R)rl_; inv = (R)irh_;
+          float gx, gy, gz, gr, grl, gi;
+          pair_geom_mixed(qj, qi, gp, (float)P.r_short, (float)P.r_in, gx, gy, gz, gr, grl, gi);
+          dx = (R)gx; dy = (R)gy; dz = (R)gz;
+          r = (R)gr; rlo = (R)grl; inv = (R)gi;
         } else {
           const R rf2 = r2_decide(dx, dy, dz);
           inv = M::rsqrt(rf2);

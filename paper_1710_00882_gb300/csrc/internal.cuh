@@ -41,6 +41,7 @@ struct PairP {
   R beta, n, neg_inv2n;   // b = (1 + (beta zeta)^n)^(-1/(2n))
   R Rc, Dc;               // cutoff centre and half width
   R r_in, r_out, rc2;     // R - D, R + D, (R + D)^2
+  R r_short;              // 0.7 R: mixed mode forms shorter pairs' geometry as head + tail
   R r_out_lo;             // float32 tables: (R + D) - (float)(R + D)
   R inv4D, dfc_scale;     // 1/(4D), -pi/(4D)
   R mu1h, mu1l, mu2h, mu2l;   // float32 tables: lambda1,2 * log2(e) as float head + tail

@@ -548,6 +548,7 @@ int tersoff_params_create(tersoff_ctx *ctx, int ntypes, const double *entries, c
       d.beta = p[F_BETA]; d.n = p[F_N]; d.neg_inv2n = -1.0 / (2.0 * p[F_N]);
       d.Rc = p[F_R]; d.Dc = p[F_DD];
       d.r_in = p[F_R] - p[F_DD]; d.r_out = p[F_R] + p[F_DD]; d.rc2 = d.r_out * d.r_out;
+      d.r_short = 0.7 * p[F_R];
       d.inv4D = 1.0 / (4.0 * p[F_DD]); d.dfc_scale = -PI / (4.0 * p[F_DD]); d.r_out_lo = 0.0;
       d.mu1h = d.lam1 * LOG2E; d.mu1l = 0.0; d.mu2h = d.lam2 * LOG2E; d.mu2l = 0.0;
       d.Aln2 = d.A * LN2; d.Bln2 = d.B * LN2;
@@ -560,6 +561,7 @@ int tersoff_params_create(tersoff_ctx *ctx, int ntypes, const double *entries, c
       f.lam2_lo = (float)(d.lam2 - (double)f.lam2);
       f.beta = (float)d.beta; f.n = (float)d.n; f.neg_inv2n = (float)d.neg_inv2n;
       f.Rc = (float)d.Rc; f.Dc = (float)d.Dc; f.r_in = (float)d.r_in; f.r_out = (float)d.r_out;
+      f.r_short = (float)d.r_short;
       // float cutoff test must not admit a pair the float64 test rejects: use the float below r_out^2
       f.rc2 = (float)d.rc2;
       if ((double)f.rc2 > d.rc2) f.rc2 = std::nextafter(f.rc2, 0.0f);

@@ -12,19 +12,25 @@ from paper_1710_00882_gb300 import workloads as wl
 def test_perfect_diamond_counts():
     pytest.importorskip("scipy")
     s = wl.diamond(5, 5, 5, 5.432)
-    n_list, P, P_taper, T = bench.workload_counts(s, 3.0, 2.7)
-    assert (n_list, P, P_taper, T) == (4 * s.n, 4 * s.n, 0, 12 * s.n)
+    n_list, P, P_taper, P_short, T = bench.workload_counts(s, 3.0, 2.7, 1.995)
+    assert (n_list, P, P_taper, P_short, T) == (4 * s.n, 4 * s.n, 0, 0, 12 * s.n)
+    # every pair of a lattice compressed to a = 3.9 A (bonds of 1.69 A) is short
+    c = wl.diamond(5, 5, 5, 3.9)
+    _, Pc, _, Pc_short, _ = bench.workload_counts(c, 3.0, 2.7, 1.995)
+    assert Pc_short == 4 * c.n and Pc > Pc_short
 
 
 def test_flops_per_launch_for_si_512k_counts():
     """0.379 GFLOP of the method's own work per launch for the 512,000-atom box at the
-    perfect-lattice counts (740 flops per atom), plus 75 flops per pair of mixed-mode
-    compensation reported apart (154 MFLOP)."""
+    perfect-lattice counts (740 flops per atom), plus the mixed-mode compensation
+    reported apart: 14 flops per pair (head+tail exponents; 28.7 MFLOP) with no pair in
+    the taper or shorter than 0.7 R, 75 per pair where the geometry is head+tail too."""
     n = 512_000
     flops = bench.C_ENTRY * 4 * n + bench.C_PAIR * 4 * n + bench.C_TAPER * 0 + bench.C_TRIPLET * 12 * n
     assert flops == pytest.approx(0.379e9, rel=1e-3)
     assert flops / n == 740
-    assert bench.C_PAIR_MIXED_OVERHEAD * 4 * n == pytest.approx(153.6e6, rel=1e-3)
+    assert bench.C_PAIR_MIXED_EXP * 4 * n == pytest.approx(28.67e6, rel=1e-3)
+    assert bench.C_PAIR_MIXED_EXP + bench.C_PAIR_MIXED_GEOM == 75
 
 
 def test_source_hash_ignores_comments(tmp_path, monkeypatch):
