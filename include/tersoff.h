@@ -67,8 +67,10 @@ extern "C" {
  * three.
  * TERSOFF_FP64: all arithmetic in float64.
  * TERSOFF_MIXED: relative vectors formed exactly from 32-bit fixed-point
- *   positions and converted to float32 as head + tail; r and lambda*r kept to
- *   ~1 ulp; f_C, g, exp, pow and all per-term arithmetic in float32; the float32
+ *   positions and converted to float32, as head + tail (r to ~1 ulp) for pairs in
+ *   the cutoff taper or shorter than 0.7 R, rounded once for the others; lambda*r
+ *   with lambda as head + tail; f_C, g, exp, pow and all per-term arithmetic in
+ *   float32; the float32
  *   force contributions on each atom summed with compensation (TwoSum), so the sum
  *   has float64 accuracy; energy and virial summed over atoms in float64.
  * TERSOFF_SINGLE: the paper's single mode: float32 throughout the evaluation:

@@ -39,10 +39,12 @@
 // Precision: the math policy M (MathD: FP64 mode; MathF: mixed mode; MathS:
 // single mode) fixes the real type R and how distances and exponentials are formed.
 // Mixed and single modes both form the relative vector d_ij from the exact int32
-// difference of 32-bit fixed-point coordinates.  Mixed mode converts it to float
-// split into head and tail so that d_ij is within ~1 ulp, and exp(-lambda r) forms
-// lambda r with an FMA-exact product, because the pair term's r-derivative is a
-// difference of two terms ~10x larger than itself.  Single mode (the paper's
+// difference of 32-bit fixed-point coordinates.  Mixed mode rounds it once to float
+// for pairs with 0.7 R <= r <= R - D and splits it into head and tail (d_ij within
+// ~1 ulp, r = rh + rl) for pairs in the f_C taper or shorter (pair_geom_mixed), and
+// exp(-lambda r) forms lambda r with an FMA-exact product from lambda as head + tail,
+// because the pair term's r-derivative is a difference of two terms ~10x larger than
+// itself and a rounded lambda would bias every pair alike.  Single mode (the paper's
 // all-float32 variant, Sec. 4) rounds the difference once to float, takes r from
 // rsqrt and exp from one ex2, and sums everything in float32.
 //
@@ -67,7 +69,7 @@ constexpr float L2E_F_LO = 1.925963033500011e-08f;     // log2(e) - L2E_F
 
 struct MathF {
   using R = float;
-  static constexpr bool fine = true;   // head+tail distances and exponents
+  static constexpr bool fine = true;   // head+tail exponents; head+tail distances where pair_geom_mixed asks
   static __device__ __forceinline__ float rcp(float x)
   {
     float y;
