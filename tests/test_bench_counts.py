@@ -52,3 +52,12 @@ def test_source_hash_ignores_comments(tmp_path, monkeypatch):
     (dst / "force_kernels.cuh").write_text(k.replace("constexpr float L2E_F = 1.44269502f;",
                                                      "constexpr float L2E_F = 1.44269503f;", 1))
     assert bench.force_kernel_source_hash() != h0
+
+
+def test_committed_capture_is_of_the_current_kernel():
+    """The DRAM traffic the bench line reports comes from the committed ncu capture of
+    the mixed register kernel; it is reported only while that capture was taken with the
+    kernel's current source (same hash), so a kernel change without a new capture shows
+    here, before a bench run reports a null traffic."""
+    assert bench.force_traffic() is not None
+    assert bench.force_traffic() > 0
